@@ -1,0 +1,545 @@
+"""FP64 CPU oracle for the semi-Lagrangian Gauss-Newton-Krylov hot path of
+"CLAIRE at scale" (arXiv 2209.08189).
+
+TEST INFRASTRUCTURE.  Only tests/, ``__graft_entry__.smoke()`` and the CPU
+baseline / reference legs of ``bench.py`` may import this package.  It shares
+no code with the CUDA path: the pointwise kernels live in ``kernels.c``
+(plain double-precision loops) and everything else is numpy.
+
+What it computes, step by step, in the paper's order and notation:
+
+* Objective, Eq. (1a): J(v) = 1/2 ||m(1) - m1||^2 + beta_v/2 reg_v(v)
+  + beta_w/2 reg_w(div v), with reg_v the H1 seminorm (or H2) and reg_w the
+  H1 norm (Sec. 2.1), evaluated spectrally: 1/2 <v, S v>.
+* State, Eqs. (1b)-(1c): semi-Lagrangian (SL) transport with RK2
+  characteristics (Sec. 2.2 "Discretization").
+* Adjoint, Eq. (4): -d_t lambda - div(lambda v) = 0, lambda(1) = m1 - m(1),
+  solved by SL along +v with the source lambda * div v integrated by Heun.
+* Reduced gradient, Eq. (3): g = beta_v A v + K int_0^1 lambda grad m dt.
+  Default ("exact" form): g = S v + b with the symbol
+  S(k) = beta_v |k|^2 I + beta_w (1 + |k|^2) k k^T, the exact gradient of J
+  in the continuum.  Opt-in paper form: g = K (S v + b) = beta_v A v + K b.
+* Gauss-Newton Hessian matvec, Eq. (6), with the incremental state and
+  incremental adjoint solves.
+* Gauss-Newton-Krylov with Armijo line search, Eq. (5), matrix-free PCG,
+  spectral preconditioner S^{-1}.
+* Jacobian determinant det grad y of the deformation map (Sec. 4.1).
+
+Readings where the paper is silent are listed in the module docstrings below
+(interpolation nodes, Heun variant, trapezoidal time quadrature, Nyquist
+handling of odd symbols, discrete inner product h1*h2*h3*sum).
+"""
+from __future__ import annotations
+
+import ctypes
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+from . import build as _build
+
+__all__ = [
+    "Params", "spacing", "interp", "interp_points", "interp_T", "backtrace",
+    "fd8_grad", "fd8_div", "reg_apply", "reg_inverse", "project_K", "reg_energy",
+    "characteristics", "forward_solve", "adjoint_solve", "state_at", "objective",
+    "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
+    "transport", "deformation_map", "detj", "cfl", "inner", "num_threads",
+]
+
+_lib = None
+
+
+def _load():
+    global _lib
+    if _lib is None:
+        path = _build.build()
+        lib = ctypes.CDLL(path)
+        dp = ctypes.POINTER(ctypes.c_double)
+        lp = ctypes.POINTER(ctypes.c_long)
+        lib.orc_interp.argtypes = [lp, dp, dp, ctypes.c_int, dp]
+        lib.orc_interp_points.argtypes = [lp, dp, dp, ctypes.c_long, ctypes.c_int, dp]
+        lib.orc_interp_transpose.argtypes = [lp, dp, dp, ctypes.c_int, dp]
+        lib.orc_backtrace.argtypes = [lp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+        lib.orc_fd8_grad.argtypes = [lp, dp, dp]
+        lib.orc_fd8_div.argtypes = [lp, dp, dp]
+        lib.orc_num_threads.restype = ctypes.c_int
+        _lib = lib
+    return _lib
+
+
+def _dp(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double))
+
+
+def _n(shape):
+    return (ctypes.c_long * 3)(*[int(s) for s in shape])
+
+
+def _f64(a):
+    return np.ascontiguousarray(a, dtype=np.float64)
+
+
+def num_threads() -> int:
+    """Threads the C kernels use (OpenMP), for reporting the CPU baseline."""
+    return int(_load().orc_num_threads())
+
+
+# ----------------------------------------------------------------------------
+# Grid, inner product
+# ----------------------------------------------------------------------------
+
+def spacing(n):
+    """h_c = 2 pi / N_c on the periodic domain [0, 2 pi)^3 (Sec. 2.2)."""
+    return np.array([2.0 * math.pi / int(s) for s in n])
+
+
+def inner(a, b, n):
+    """Discrete L2 inner product h1 h2 h3 sum(a * b) (reading: plain Riemann sum)."""
+    return float(np.prod(spacing(n)) * np.sum(_f64(a) * _f64(b)))
+
+
+# ----------------------------------------------------------------------------
+# Pointwise kernels (C)
+# ----------------------------------------------------------------------------
+
+def interp(f, d, order=3):
+    """f(x + d) at every grid node; d in grid units, shape (3, *f.shape).
+
+    Sec. 3 "IP kernel": cubic Lagrange (order 3, nodes floor-1..floor+2) or
+    linear (order 1), periodic wrap.
+    """
+    f = _f64(f); d = _f64(d)
+    out = np.empty_like(f)
+    _load().orc_interp(_n(f.shape), _dp(f), _dp(d), int(order), _dp(out))
+    return out
+
+
+def interp_points(f, y, order=3):
+    """Interpolant of f at explicit grid-unit points y, shape (3, M)."""
+    f = _f64(f); y = _f64(y)
+    out = np.empty(y.shape[1])
+    _load().orc_interp_points(_n(f.shape), _dp(f), _dp(y), int(y.shape[1]), int(order), _dp(out))
+    return out
+
+
+def interp_T(yv, d, order=3):
+    """Exact transpose of interp(., d): scatter of point values to nodes."""
+    yv = _f64(yv); d = _f64(d)
+    out = np.empty_like(yv)
+    _load().orc_interp_transpose(_n(yv.shape), _dp(yv), _dp(d), int(order), _dp(out))
+    return out
+
+
+def backtrace(v, dt, sign=+1, order=3):
+    """RK2 (Heun) characteristic displacement in grid units (Sec. 2.2).
+
+    sign=+1: X = x - dt/2 [v(x) + v(x - dt v(x))] (state); sign=-1: the
+    adjoint characteristic X+ along +v.
+    """
+    v = _f64(v)
+    n = v.shape[1:]
+    d = np.empty_like(v)
+    _load().orc_backtrace(_n(n), _dp(v), float(dt), int(sign), int(order), _dp(d))
+    return d
+
+
+def fd8_grad(f):
+    """8th-order central FD gradient (Sec. 2.2 / Sec. 3 "FD kernel"), periodic."""
+    f = _f64(f)
+    g = np.empty((3,) + f.shape)
+    _load().orc_fd8_grad(_n(f.shape), _dp(f), _dp(g))
+    return g
+
+
+def fd8_div(v):
+    """8th-order central FD divergence, periodic."""
+    v = _f64(v)
+    d = np.empty(v.shape[1:])
+    _load().orc_fd8_div(_n(v.shape[1:]), _dp(v), _dp(d))
+    return d
+
+
+# ----------------------------------------------------------------------------
+# Spectral operators (Sec. 2.2: "two FFTs and one Hadamard product")
+# ----------------------------------------------------------------------------
+
+@dataclass
+class Params:
+    """Solver parameters (Sec. 3 "Key Solver Parameters")."""
+    beta_v: float = 1e-2
+    beta_w: float = 1e-4
+    reg: int = 1            # 1 = H1 seminorm on v, 2 = H2 seminorm
+    nt: int = 4
+    order: int = 3          # 3 = cubic Lagrange, 1 = linear
+    grad_form: int = 0      # 0 = S v + b (exact gradient of J); 1 = beta_v A v + K b
+    gtol: float = 5e-2
+    max_gn: int = 50
+    max_pcg: int = 10
+    pcg_rtol_max: float = 0.5
+    armijo_c1: float = 1e-4
+    max_ls: int = 10
+    adjoint: str = "sl"     # "sl" = paper's SL adjoint (OTD); "scatter" = exact transpose (DTO)
+    extra: dict = field(default_factory=dict)
+
+    @property
+    def dt(self):
+        return 1.0 / self.nt
+
+
+def _symbols(n, p: Params):
+    """Per-mode pieces of S(k) = a(k) I + c(k) u u^T on the rfft half grid.
+
+    a = beta_v |k|^2 (H1) or beta_v |k|^4 (H2); c = beta_w (1 + |k|^2);
+    u = k with the Nyquist component set to zero (reading: the first-
+    derivative symbol is odd, so on a Nyquist plane it is taken as 0 to keep
+    the operator real-symmetric); |k|^2 keeps the Nyquist value (even).
+    """
+    n0, n1, n2 = (int(s) for s in n)
+    k0 = np.fft.fftfreq(n0, 1.0 / n0)
+    k1 = np.fft.fftfreq(n1, 1.0 / n1)
+    k2 = np.fft.rfftfreq(n2, 1.0 / n2)
+    K0, K1, K2 = np.meshgrid(k0, k1, k2, indexing="ij")
+    kk = K0 ** 2 + K1 ** 2 + K2 ** 2
+    u = np.stack([np.where(np.abs(K0) == n0 / 2, 0.0, K0),
+                  np.where(np.abs(K1) == n1 / 2, 0.0, K1),
+                  np.where(np.abs(K2) == n2 / 2, 0.0, K2)])
+    a = p.beta_v * (kk if p.reg == 1 else kk ** 2)
+    c = p.beta_w * (1.0 + kk)
+    return a, c, u, kk
+
+
+def _fft3(v):
+    return np.fft.rfftn(_f64(v), axes=(-3, -2, -1))
+
+
+def _ifft3(vh, n):
+    return np.fft.irfftn(vh, s=tuple(int(s) for s in n), axes=(-3, -2, -1))
+
+
+def reg_apply(v, p: Params):
+    """S v = F^{-1}[a v^ + c u (u . v^)] (first variation of the regulariser)."""
+    v = _f64(v); n = v.shape[1:]
+    a, c, u, _ = _symbols(n, p)
+    vh = _fft3(v)
+    ud = np.sum(u * vh, axis=0)
+    return _ifft3(a * vh + c * u * ud, n)
+
+
+def reg_inverse(r, p: Params):
+    """Preconditioner S^{-1} (Sherman-Morrison on a I + c u u^T); identity at k = 0."""
+    r = _f64(r); n = r.shape[1:]
+    a, c, u, kk = _symbols(n, p)
+    rh = _fft3(r)
+    ud = np.sum(u * rh, axis=0)
+    nz = kk > 0
+    a_safe = np.where(nz, a, 1.0)
+    den = a_safe + c * np.sum(u * u, axis=0)
+    zh = np.where(nz, (rh - c * u * ud / den) / a_safe, rh)
+    return _ifft3(zh, n)
+
+
+def project_K(b, p: Params):
+    """Leray-like operator K = a S^{-1} = I - c u u^T / (a + c |u|^2); K = I at k = 0.
+
+    Reading of Eq. (3): eliminating w and the multiplier p of Eq. (2) gives
+    g = beta_v A v + K b with this K; it tends to the Leray projection as
+    beta_w -> infinity and to I as beta_w -> 0.
+    """
+    b = _f64(b); n = b.shape[1:]
+    a, c, u, kk = _symbols(n, p)
+    bh = _fft3(b)
+    ud = np.sum(u * bh, axis=0)
+    nz = kk > 0
+    den = np.where(nz, a + c * np.sum(u * u, axis=0), 1.0)
+    return _ifft3(np.where(nz, bh - c * u * ud / den, bh), n)
+
+
+def reg_energy(v, p: Params):
+    """beta_v/2 reg_v(v) + beta_w/2 reg_w(div v) = 1/2 <v, S v>."""
+    return 0.5 * inner(v, reg_apply(v, p), v.shape[1:])
+
+
+# ----------------------------------------------------------------------------
+# Semi-Lagrangian solves
+# ----------------------------------------------------------------------------
+
+def _weights(nt):
+    """Trapezoidal weights in time for int_0^1 (.) dt on nt+1 points."""
+    dt = 1.0 / nt
+    w = np.full(nt + 1, dt)
+    w[0] = w[-1] = 0.5 * dt
+    return w
+
+
+def characteristics(v, p: Params):
+    """Per-velocity data reused by every solve: X (state), X+ (adjoint),
+    d = div v and d(X+)."""
+    v = _f64(v)
+    d_state = backtrace(v, p.dt, +1, p.order)
+    d_adj = backtrace(v, p.dt, -1, p.order)
+    div = fd8_div(v)
+    return {"d": d_state, "dp": d_adj, "div": div, "div_Xp": interp(div, d_adj, p.order)}
+
+
+def forward_solve(m0, ch, p: Params):
+    """m^{j+1} = m^j(X), j = 0..nt-1 (Eq. (1b)-(1c)); returns all nt+1 states."""
+    ms = [_f64(m0)]
+    for _ in range(p.nt):
+        ms.append(interp(ms[-1], ch["d"], p.order))
+    return ms
+
+
+def _adjoint_step(lam_next, ch, p: Params):
+    """One SL step of Eq. (4) backwards in time.
+
+    Along the characteristic traced along +v the adjoint obeys
+    d lambda / d tau = lambda div v; Heun gives
+    lambda^j = a + dt/2 [a d(X+) + (a + dt a d(X+)) d(x)], a = lambda^{j+1}(X+).
+    """
+    dt = p.dt
+    a = interp(lam_next, ch["dp"], p.order)
+    pred = a + dt * a * ch["div_Xp"]
+    return a + 0.5 * dt * (a * ch["div_Xp"] + pred * ch["div"])
+
+
+def adjoint_solve(lam_end, ch, gms, p: Params, mode=None):
+    """Backward solve from lambda^{nt} and body b = sum_j w_j lambda^j grad m^j.
+
+    mode "sl": the paper's SL adjoint (optimise-then-discretise);
+    mode "scatter": lambda^j = T^T lambda^{j+1}, the exact transpose of the
+    state step (discretise-then-optimise), used by the symmetry pins.
+    Returns (b, lambda^0).
+    """
+    mode = mode or p.adjoint
+    w = _weights(p.nt)
+    lam = _f64(lam_end)
+    b = w[p.nt] * lam[None] * gms[p.nt]
+    for j in range(p.nt - 1, -1, -1):
+        if mode == "sl":
+            lam = _adjoint_step(lam, ch, p)
+        else:
+            lam = interp_T(lam, ch["d"], p.order)
+        b = b + w[j] * lam[None] * gms[j]
+    return b, lam
+
+
+class State:
+    """Linearisation point of the Gauss-Newton step: v, characteristics,
+    states m^j and their FD8 gradients."""
+
+    def __init__(self, v, m0, m1, p: Params):
+        self.v = _f64(v)
+        self.m0 = _f64(m0)
+        self.m1 = _f64(m1)
+        self.p = p
+        self.n = self.m0.shape
+        self.ch = characteristics(self.v, p)
+        self.ms = forward_solve(self.m0, self.ch, p)
+        self.gms = [fd8_grad(m) for m in self.ms]
+        self.reg_v = reg_apply(self.v, p)
+        res = self.ms[-1] - self.m1
+        self.mismatch = 0.5 * inner(res, res, self.n)
+        self.reg = 0.5 * inner(self.v, self.reg_v, self.n)
+        self.J = self.mismatch + self.reg
+
+
+def state_at(v, m0, m1, p: Params):
+    return State(v, m0, m1, p)
+
+
+def objective(v, m0, m1, p: Params):
+    """J(v), the mismatch term and the regularisation term (Eq. (1a))."""
+    v = _f64(v)
+    ch = {"d": backtrace(v, p.dt, +1, p.order)}
+    m = _f64(m0)
+    for _ in range(p.nt):
+        m = interp(m, ch["d"], p.order)
+    res = m - _f64(m1)
+    mis = 0.5 * inner(res, res, m.shape)
+    reg = reg_energy(v, p)
+    return mis + reg, mis, reg
+
+
+def _apply_form(x, p: Params):
+    return project_K(x, p) if p.grad_form == 1 else x
+
+
+def gradient(st: State, mode=None):
+    """Reduced gradient, Eq. (3): g = S v + b (or K(S v + b) = beta_v A v + K b)."""
+    b, _ = adjoint_solve(st.m1 - st.ms[-1], st.ch, st.gms, st.p, mode)
+    return _apply_form(st.reg_v + b, st.p)
+
+
+def incremental_state(st: State, vt):
+    """Incremental state of the linearised Eq. (1b):
+    d_t mt + v . grad mt = -vt . grad m, mt(0) = 0, SL with Heun sources:
+    mt^{j+1} = (mt^j + dt/2 f^j)(X) + dt/2 f^{j+1}, f^j = -vt . grad m^j."""
+    p = st.p
+    dt = p.dt
+    vt = _f64(vt)
+    f = [-np.sum(vt * gm, axis=0) for gm in st.gms]
+    mt = np.zeros(st.n)
+    for j in range(p.nt):
+        mt = interp(mt + 0.5 * dt * f[j], st.ch["d"], p.order) + 0.5 * dt * f[j + 1]
+    return mt
+
+
+def hessian_matvec(st: State, vt, mode=None):
+    """Gauss-Newton Hessian matvec, Eq. (6): H vt = S vt + int lt grad m dt
+    (or K applied to it), with the incremental adjoint lt(1) = -mt(1)."""
+    mt = incremental_state(st, vt)
+    bt, _ = adjoint_solve(-mt, st.ch, st.gms, st.p, mode)
+    return _apply_form(reg_apply(vt, st.p) + bt, st.p)
+
+
+def precond(r, p: Params):
+    """Spectral preconditioner: inverse of the regularisation operator
+    (K-form: S^{-1} restricted so that it inverts beta_v A)."""
+    if p.grad_form == 1:
+        # g = K(S v + b) with K S = a I: precondition with (a I)^{-1}
+        r = _f64(r); n = r.shape[1:]
+        a, c, u, kk = _symbols(n, p)
+        rh = _fft3(r)
+        return _ifft3(np.where(kk > 0, rh / np.where(kk > 0, a, 1.0), rh), n)
+    return reg_inverse(r, p)
+
+
+def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False):
+    """Matrix-free PCG for H x = rhs (Sec. 2.2), x0 = 0; stops when
+    ||r|| <= rtol ||r0|| or after maxit matvecs.  Returns (x, iterations)."""
+    n = st.n
+    x = np.zeros_like(rhs)
+    r = _f64(rhs).copy()
+    r0 = math.sqrt(inner(r, r, n))
+    if r0 == 0.0:
+        return x, 0
+    z = precond(r, st.p)
+    pv = z.copy()
+    rz = inner(r, z, n)
+    it = 0
+    for it in range(1, maxit + 1):
+        q = hessian_matvec(st, pv, mode)
+        pq = inner(pv, q, n)
+        if pq <= 0.0:
+            if it == 1:
+                x = pv.copy()
+            break
+        alpha = rz / pq
+        x = x + alpha * pv
+        r = r - alpha * q
+        if not fixed_iters and math.sqrt(inner(r, r, n)) <= rtol * r0:
+            break
+        z = precond(r, st.p)
+        rz_new = inner(r, z, n)
+        pv = z + (rz_new / rz) * pv
+        rz = rz_new
+    return x, it
+
+
+def register(m0, m1, p: Params, v0=None, mode=None, log=None):
+    """Gauss-Newton-Krylov with Armijo line search, Eq. (5).
+
+    PCG forcing eta_k = min(pcg_rtol_max, sqrt(||g_k|| / ||g_0||)); Armijo
+    alpha_0 = 1, halving, sufficient decrease c1; stop when
+    ||g|| / ||g_0|| <= gtol or after max_gn steps.
+    """
+    m0 = _f64(m0); m1 = _f64(m1)
+    n = m0.shape
+    v = np.zeros((3,) + n) if v0 is None else _f64(v0).copy()
+    st = State(v, m0, m1, p)
+    g = gradient(st, mode)
+    g0 = math.sqrt(inner(g, g, n))
+    rep = {"gn_iters": 0, "pcg_iters": [], "alpha": [], "J": [st.J], "gnorm_rel": [1.0],
+           "status": "not_converged", "g0": g0}
+    if g0 == 0.0:
+        rep["status"] = "converged"
+        return v, rep
+    for _ in range(p.max_gn):
+        rel = math.sqrt(inner(g, g, n)) / g0
+        if rel <= p.gtol:
+            rep["status"] = "converged"
+            break
+        eta = min(p.pcg_rtol_max, math.sqrt(rel))
+        vt, its = pcg(st, -g, eta, p.max_pcg, mode)
+        gtv = inner(g, vt, n)
+        alpha, ok = 1.0, False
+        for _ls in range(p.max_ls):
+            Jt, _, _ = objective(v + alpha * vt, m0, m1, p)
+            if Jt <= st.J + p.armijo_c1 * alpha * gtv:
+                ok = True
+                break
+            alpha *= 0.5
+        rep["pcg_iters"].append(its)
+        if not ok:
+            rep["status"] = "line_search_failed"
+            break
+        rep["alpha"].append(alpha)
+        v = v + alpha * vt
+        st = State(v, m0, m1, p)
+        g = gradient(st, mode)
+        rep["gn_iters"] += 1
+        rep["J"].append(st.J)
+        rep["gnorm_rel"].append(math.sqrt(inner(g, g, n)) / g0)
+        if log is not None:
+            log(rep)
+    else:
+        if rep["gnorm_rel"][-1] <= p.gtol:
+            rep["status"] = "converged"
+    rep["mismatch"] = st.mismatch
+    den = inner(m0 - m1, m0 - m1, n)
+    rep["r"] = (2.0 * st.mismatch / den) if den > 0 else 0.0
+    return v, rep
+
+
+# ----------------------------------------------------------------------------
+# Transport entry points, deformation map, Jacobian determinant, CFL
+# ----------------------------------------------------------------------------
+
+def transport(m_in, v, p: Params, direction="fwd"):
+    """"fwd": m(1) from m(0) by Eq. (1b); "adj": lambda(0) from lambda(1) by Eq. (4)."""
+    v = _f64(v)
+    if direction == "fwd":
+        d = backtrace(v, p.dt, +1, p.order)
+        m = _f64(m_in)
+        for _ in range(p.nt):
+            m = interp(m, d, p.order)
+        return m
+    ch = characteristics(v, p)
+    lam = _f64(m_in)
+    for _ in range(p.nt):
+        lam = _adjoint_step(lam, ch, p)
+    return lam
+
+
+def deformation_map(v, p: Params):
+    """Displacement u of the map y = x + u with m(1) = m0(y): u^0 = 0,
+    u^{j+1} = u^j(X) + (X - x) (reading: transport of the map by the same SL
+    steps as the state)."""
+    v = _f64(v)
+    n = v.shape[1:]
+    h = spacing(n)
+    d = backtrace(v, p.dt, +1, p.order)
+    u = np.zeros_like(v)
+    for _ in range(p.nt):
+        u = np.stack([interp(u[c], d, p.order) + d[c] * h[c] for c in range(3)])
+    return u
+
+
+def detj(v, p: Params):
+    """det F, F = grad y = I + grad u (FD8), in FP64 (Sec. 3 "J_min")."""
+    u = deformation_map(v, p)
+    F = np.empty((3, 3) + u.shape[1:])
+    for c in range(3):
+        gu = fd8_grad(u[c])
+        for e in range(3):
+            F[c, e] = gu[e] + (1.0 if c == e else 0.0)
+    return (F[0, 0] * (F[1, 1] * F[2, 2] - F[1, 2] * F[2, 1])
+            - F[0, 1] * (F[1, 0] * F[2, 2] - F[1, 2] * F[2, 0])
+            + F[0, 2] * (F[1, 0] * F[2, 1] - F[1, 1] * F[2, 0]))
+
+
+def cfl(v, p: Params):
+    """CFL number: max over x of |v(x)|_2 * dt / min_c h_c."""
+    v = _f64(v)
+    return float(np.sqrt(np.max(np.sum(v * v, axis=0))) * p.dt / np.min(spacing(v.shape[1:])))

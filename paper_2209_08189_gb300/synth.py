@@ -1,0 +1,140 @@
+"""Seeded synthetic inputs for the registration hot path.
+
+This module only draws inputs: templates and velocities on the periodic grid
+[0, 2 pi)^3 (C order, x3 fastest; vector fields component-major [3][N1][N2][N3]).
+It holds none of the method's arithmetic (no transport, no interpolation, no
+finite differences, no regularisation); the reference image m1 is made by
+whichever transport the caller trusts.
+
+Recipes (all float64, seeded with numpy's PCG64):
+
+* ``blob_template``: sum of Gaussian blobs with periodic minimum-image
+  distance (sigma 0.3, centres U[0, 2pi)^3, amplitudes U[0.5, 1]) plus
+  0.2 sin x1 sin x2 sin x3, clipped to [0, 1].
+* ``mode_velocity``: each component a sum of random Fourier modes
+  a cos(k . x + phi) with integer wave vectors 1 <= |k|_2 <= kmax, scaled so
+  that max_x |v(x)|_2 equals vmax.
+* ``bandlimited_velocity``: random complex spectrum on the ball |k|_2 <= kmax,
+  inverse real FFT, same max-norm scaling (fast at 256^3 and above).
+* ``label_template``: four nested ellipsoidal label regions with
+  intensities 0.2 / 0.5 / 0.8 / 1.0 on a zero background, smoothed by a
+  periodic Gaussian of sigma = 1 voxel (separable, direct convolution).
+* ``add_noise``: additive N(0, sigma^2) noise.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def coords(n):
+    """1-D node coordinates x_c = i * 2 pi / N_c for each axis."""
+    return [np.arange(int(s)) * (2.0 * math.pi / int(s)) for s in n]
+
+
+def _scale_to_max(v, vmax):
+    mx = float(np.sqrt(np.max(np.sum(v * v, axis=0))))
+    return v * (vmax / mx) if mx > 0 else v
+
+
+def blob_template(n, seed=0, nblobs=8, sigma=0.3, sine=0.2):
+    rng = np.random.default_rng(seed)
+    x1, x2, x3 = coords(n)
+    cen = rng.uniform(0.0, 2.0 * math.pi, size=(nblobs, 3))
+    amp = rng.uniform(0.5, 1.0, size=nblobs)
+    m = np.zeros(tuple(int(s) for s in n))
+    two_pi = 2.0 * math.pi
+
+    def mi(x, c):  # periodic minimum-image distance along one axis
+        d = np.abs(x - c)
+        return np.minimum(d, two_pi - d)
+
+    for b in range(nblobs):
+        d1 = mi(x1, cen[b, 0]) ** 2
+        d2 = mi(x2, cen[b, 1]) ** 2
+        d3 = mi(x3, cen[b, 2]) ** 2
+        r2 = d1[:, None, None] + d2[None, :, None] + d3[None, None, :]
+        m += amp[b] * np.exp(-r2 / (2.0 * sigma * sigma))
+    m += sine * (np.sin(x1)[:, None, None] * np.sin(x2)[None, :, None]
+                 * np.sin(x3)[None, None, :])
+    return np.clip(m, 0.0, 1.0)
+
+
+def _wavevectors(kmax, rng, count):
+    """`count` random integer wave vectors with 1 <= |k|_2 <= kmax."""
+    ks = []
+    r = int(math.floor(kmax))
+    while len(ks) < count:
+        k = rng.integers(-r, r + 1, size=3)
+        kk = float(np.dot(k, k))
+        if 1.0 <= kk <= kmax * kmax:
+            ks.append(k)
+    return np.array(ks, dtype=np.float64)
+
+
+def mode_velocity(n, seed=0, nmodes=6, kmax=4, vmax=0.5):
+    rng = np.random.default_rng(seed)
+    x1, x2, x3 = coords(n)
+    v = np.zeros((3,) + tuple(int(s) for s in n))
+    for c in range(3):
+        ks = _wavevectors(kmax, rng, nmodes)
+        amps = rng.uniform(0.5, 1.0, size=nmodes)
+        phis = rng.uniform(0.0, 2.0 * math.pi, size=nmodes)
+        for k, a, ph in zip(ks, amps, phis):
+            e = (np.exp(1j * k[0] * x1)[:, None, None] * np.exp(1j * k[1] * x2)[None, :, None]
+                 * np.exp(1j * k[2] * x3)[None, None, :])
+            v[c] += a * np.real(np.exp(1j * ph) * e)
+    return _scale_to_max(v, vmax)
+
+
+def bandlimited_velocity(n, seed=0, kmax=8, vmax=1.0):
+    rng = np.random.default_rng(seed)
+    n0, n1, n2 = (int(s) for s in n)
+    k0 = np.fft.fftfreq(n0, 1.0 / n0)
+    k1 = np.fft.fftfreq(n1, 1.0 / n1)
+    k2 = np.fft.rfftfreq(n2, 1.0 / n2)
+    kk = k0[:, None, None] ** 2 + k1[None, :, None] ** 2 + k2[None, None, :] ** 2
+    mask = (kk >= 1.0) & (kk <= kmax * kmax)
+    # keep the random draw small: only the band's index set is drawn
+    idx = np.nonzero(mask)
+    v = np.empty((3, n0, n1, n2))
+    for c in range(3):
+        spec = np.zeros((n0, n1, n2 // 2 + 1), dtype=np.complex128)
+        cnt = idx[0].size
+        spec[idx] = (rng.standard_normal(cnt) + 1j * rng.standard_normal(cnt)) / np.sqrt(1.0 + kk[idx])
+        v[c] = np.fft.irfftn(spec, s=(n0, n1, n2))
+    return _scale_to_max(v, vmax)
+
+
+def _blur_axis(f, sigma, axis):
+    r = int(math.ceil(4.0 * sigma))
+    t = np.arange(-r, r + 1, dtype=np.float64)
+    w = np.exp(-t * t / (2.0 * sigma * sigma))
+    w /= w.sum()
+    out = np.zeros_like(f)
+    for s, ws in zip(range(-r, r + 1), w):
+        out += ws * np.roll(f, s, axis=axis)
+    return out
+
+
+def label_template(n, seed=0, levels=(0.2, 0.5, 0.8, 1.0), blur_sigma=1.0):
+    """Four nested ellipsoids (outermost first) centred near the domain centre."""
+    rng = np.random.default_rng(seed)
+    x1, x2, x3 = coords(n)
+    c = math.pi + rng.uniform(-0.2, 0.2, size=3)
+    radii0 = np.array([2.2, 1.9, 2.4]) * rng.uniform(0.9, 1.1, size=3)
+    m = np.zeros(tuple(int(s) for s in n))
+    for lvl, scale in zip(levels, (1.0, 0.75, 0.5, 0.28)):
+        r = radii0 * scale
+        q = (((x1 - c[0]) / r[0]) ** 2)[:, None, None] + (((x2 - c[1]) / r[1]) ** 2)[None, :, None] \
+            + (((x3 - c[2]) / r[2]) ** 2)[None, None, :]
+        m = np.where(q <= 1.0, lvl, m)
+    for ax in range(3):
+        m = _blur_axis(m, blur_sigma, ax)
+    return m
+
+
+def add_noise(f, sigma=0.02, seed=0):
+    rng = np.random.default_rng(seed)
+    return f + sigma * rng.standard_normal(f.shape)

@@ -1,0 +1,398 @@
+"""Benchmark of the semi-Lagrangian Gauss-Newton-Krylov registration hot path.
+
+One step = one full registration (Eq. (5)) of the 256^3 clinical-size
+synthetic workload from v = 0 to ||g|| / ||g0|| <= 5e-2: four nested smoothed
+label regions (0.2/0.5/0.8/1.0, Gaussian blur sigma = 1 voxel, N(0, 0.02^2)
+noise), reference made by a random band-limited velocity (|k| <= 8,
+max |v| = 1.0), nt = 4 RK2 steps, cubic Lagrange interpolation, H1
+regularisation beta_v = 1e-2 (middle of the 1e-1 / 1e-2 / 1e-3 sweep;
+--beta selects another), beta_w = 1e-4.
+
+value = SL interpolation throughput of the whole job: grid points x scalar
+fields interpolated by all gather kernels of the registration, divided by the
+wall time of the registration (Gpts/s); ms_per_step is the time to tolerance.
+roofline = the dominant kernel of the step, algorithmic bytes per launch over
+its CUDA-event time per launch, against the measured HBM copy bandwidth.
+
+--impl reference times the FP64 CPU oracle on the host cores on a bounded
+sample of the same workload (one gradient evaluation per step).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import re
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "SL interp Gpts/s (256^3 Gauss-Newton registration to gtol 5e-2, FP32, tricubic, nt=4)"
+UNIT = "Gpts/s"
+GATHER_KINDS = ("sl_interp", "sl_backtrace_rk2", "sl_adjoint_step", "sl_incremental_step",
+                "sl_incremental_last", "sl_map_step")
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--n", type=int, default=256, help="grid points per axis")
+    ap.add_argument("--beta", type=float, default=1e-2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    return ap.parse_args()
+
+
+def workload(n):
+    """Seeded inputs of the 256^3 clinical-size case (no transport here)."""
+    from paper_2209_08189_gb300 import synth
+    grid = (n, n, n)
+    base = synth.label_template(grid, seed=0)
+    vstar = synth.bandlimited_velocity(grid, seed=0, kmax=8, vmax=1.0)
+    return grid, base, vstar
+
+
+def config_dict(args, n_gpus):
+    return {"workload": "clinical-size synthetic: %d^3 nested-label template, band-limited v* "
+                        "|k|<=8 max|v|=1, Gauss-Newton-Krylov to gtol 5e-2 from v=0" % args.n,
+            "grid": [args.n] * 3, "nt": 4, "interp": "cubic Lagrange", "beta_v": args.beta,
+            "beta_w": 1e-4, "reg": "H1 seminorm", "gtol": 5e-2, "max_pcg": 50,
+            "l2_policy": "inputs larger than L2 (working set %.1f GB > 129 MB L2)"
+                         % (args.n ** 3 * 4 * 60 / 1e9),
+            "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured (MEASURED_PEAKS.json hbm_gbs)"
+    return 6800.0, "fallback 6.8 TB/s"
+
+
+def kernel_source_hash():
+    h = hashlib.sha1()
+    for f in ("sl_kernels.cu", "common.cuh", "vec_kernels.cu"):
+        with open(os.path.join(ROOT, "paper_2209_08189_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def ncu_traffic(kernel, src_hash):
+    """DRAM bytes per launch of `kernel` from the committed ncu summaries, if
+    they were taken on the current kernel source; else None."""
+    pdir = os.path.join(ROOT, "profiles")
+    if not os.path.isdir(pdir):
+        return None
+    pat = re.compile(r"^traffic_bytes_per_launch:\s+(\S+)\s+(\S+)\s+source=(\S+)", re.M)
+    for fn in sorted(os.listdir(pdir)):
+        if not fn.endswith((".md", ".txt")):
+            continue
+        with open(os.path.join(pdir, fn)) as f:
+            for k, val, hsh in pat.findall(f.read()):
+                if k == kernel and hsh == src_hash:
+                    return float(val)
+    return None
+
+
+class ClockSampler:
+    """nvidia-smi clocks / throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/claire_clocks_%d.csv" % index
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.FIELDS,
+                 "--format=csv,noheader,nounits", "-lms", "200"], stdout=self.fh,
+                stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                parts = [x.strip() for x in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    sm.append(float(parts[1]))
+                    mx.append(float(parts[2]))
+                except ValueError:
+                    continue
+                for name, val in zip(names, parts[5:9]):
+                    if val.lower().startswith("active"):
+                        reasons.add(name)
+        if not sm:
+            return None
+        loaded = [s for s in sm if s > 0.5 * max(sm)] or sm
+        return {"sm_mhz": statistics.median(loaded), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return world, rank, local
+
+
+# ---------------------------------------------------------------------------
+# reference arm: the FP64 oracle on the host cores
+# ---------------------------------------------------------------------------
+
+def oracle_sample(grid, m0, m1, beta):
+    """One gradient evaluation of the oracle (state, characteristics, adjoint)
+    on the workload; returns (seconds, interpolated point-fields)."""
+    import oracle
+    p = oracle.Params(nt=4, beta_v=beta, beta_w=1e-4)
+    v = np.zeros((3,) + grid)
+    t0 = time.perf_counter()
+    st = oracle.State(v, m0, m1, p)
+    oracle.gradient(st)
+    dt = time.perf_counter() - t0
+    N = float(np.prod(grid))
+    # backtraces (2 x 3 fields), div v at X+, nt state steps, nt adjoint steps
+    pts = N * (6 + 1 + 4 + 4)
+    return dt, pts
+
+
+def run_reference(args):
+    world, rank, _ = dist_setup(args)
+    if rank != 0:
+        return
+    import oracle
+    grid, base, vstar = workload(args.n)
+    from paper_2209_08189_gb300 import synth
+    p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
+    m1 = synth.add_noise(oracle.transport(base, vstar, p), 0.02, seed=1)
+    m0 = synth.add_noise(base, 0.02, seed=0)
+    for _ in range(args.warmup):
+        oracle_sample(grid, m0, m1, args.beta)
+    secs, pts = 0.0, 0.0
+    for _ in range(args.steps):
+        s, q = oracle_sample(grid, m0, m1, args.beta)
+        secs += s
+        pts += q
+    val = pts / secs / 1e9
+    cores = oracle.num_threads()
+    sample = "one oracle gradient evaluation (state + adjoint solve, nt=4) of the %d^3 workload per step" % args.n
+    print(json.dumps({
+        "impl": "reference", "metric": METRIC, "value": val, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * secs / args.steps,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic", "config": config_dict(args, args.gpus),
+        "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
+
+
+# ---------------------------------------------------------------------------
+# our arm
+# ---------------------------------------------------------------------------
+
+def run_ours(args):
+    import torch
+    world, rank, local = dist_setup(args)
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA GPU (no CPU fallback)")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    pg = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+        pg = dist
+    import __graft_entry__ as entry
+    if rank == 0:
+        entry.build()
+    if pg:
+        pg.barrier()
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth
+
+    grid, base, vstar = workload(args.n)
+    N = int(np.prod(grid))
+    stream = torch.cuda.current_stream(dev)
+    ctx = claire.Context(grid, args.beta, 4, stream=stream.cuda_stream, beta_w=1e-4, gtol=5e-2,
+                         max_gn=50, max_pcg=50)
+    # reference image by our own transport of the clean template, then noise
+    base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
+    vstar_d = torch.from_numpy(vstar.astype(np.float32)).to(dev)
+    m1c = torch.empty(grid, device=dev)
+    ctx.transport(vstar_d, base_d, m1c, claire.TRANSPORT_FWD)
+    m1 = (m1c.cpu().numpy().astype(np.float64))
+    m1 = synth.add_noise(m1, 0.02, seed=1).astype(np.float32)
+    m0 = synth.add_noise(base, 0.02, seed=0).astype(np.float32)
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.from_numpy(m1).to(dev)
+    ctx.set_images(m0_d, m1_d)
+    v = torch.zeros((3,) + grid, device=dev)
+
+    def step():
+        v.zero_()
+        st, rep = ctx.register(v)
+        if st < 0:
+            raise RuntimeError("registration failed: %s" % rep["status"])
+        return rep
+
+    for _ in range(args.warmup):
+        step()
+    ctx.set_timing(True)
+    ctx.kernel_stats(reset=True)
+    clocks = ClockSampler(local)
+    clocks.start()
+    if pg:
+        pg.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    reps = [step() for _ in range(args.steps)]
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if pg:
+        pg.barrier()
+    ck = clocks.stop()
+    secs = e0.elapsed_time(e1) * 1e-3
+    stats = ctx.kernel_stats(reset=True)
+    ctx.set_timing(False)
+    pts = sum(r["interp_points"] for r in reps)
+    tmax, pts_all = secs, pts
+    if pg:
+        t = torch.tensor([secs], device=dev, dtype=torch.float64)
+        pg.all_reduce(t, op=pg.ReduceOp.MAX)
+        tmax = float(t.item())
+        q = torch.tensor([pts], device=dev, dtype=torch.float64)
+        pg.all_reduce(q, op=pg.ReduceOp.SUM)
+        pts_all = float(q.item())
+    value = pts_all / tmax / 1e9
+
+    # dominant kernel of ours (cuFFT is a library call, not counted)
+    mine = [s for s in stats if s["name"] != "cufft" and s["launches"] > 0]
+    launches = int(sum(s["launches"] for s in mine))
+    top = max(mine, key=lambda s: s["seconds"])
+    peak, peak_src = measured_peaks()
+    per_launch_bytes = top["bytes"] / top["launches"]
+    per_launch_s = top["seconds"] / top["launches"]
+    achieved = per_launch_bytes / per_launch_s / 1e9
+    gathers = [s for s in stats if s["name"] in GATHER_KINDS and s["launches"] > 0]
+    g_bytes = sum(s["bytes"] for s in gathers)
+    g_secs = sum(s["seconds"] for s in gathers)
+    g_pts = sum(s["points"] for s in gathers)
+    total_kernel_s = sum(s["seconds"] for s in stats)
+    roofline = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
+                "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
+                "traffic": ncu_traffic(top["name"], kernel_source_hash()),
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "launch_ms": per_launch_s * 1e3,
+                "share_of_kernel_time": top["seconds"] / total_kernel_s if total_kernel_s else None,
+                "all_gathers": {"gpts_s": g_pts / g_secs / 1e9 if g_secs else None,
+                                "achieved_GBs": g_bytes / g_secs / 1e9 if g_secs else None,
+                                "frac": (g_bytes / g_secs / 1e9) / peak if g_secs else None}}
+
+    # end to end through the C ABI with host buffers (pinned), copies timed
+    e2e = None
+    if not args.no_e2e:
+        m0_h = torch.from_numpy(m0).pin_memory()
+        m1_h = torch.from_numpy(m1).pin_memory()
+        v_h = torch.zeros((3,) + grid).pin_memory()
+        ctx2 = ctx
+        if pg:
+            pg.barrier()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        pts_e = 0.0
+        for _ in range(args.steps):
+            v_h.zero_()
+            ctx2.set_images(m0_h.numpy(), m1_h.numpy())
+            st, rep = ctx2.register(v_h.numpy())
+            pts_e += rep["interp_points"]
+        torch.cuda.synchronize()
+        te = time.perf_counter() - t0
+        if pg:
+            t = torch.tensor([te], device=dev, dtype=torch.float64)
+            pg.all_reduce(t, op=pg.ReduceOp.MAX)
+            te = float(t.item())
+            q = torch.tensor([pts_e], device=dev, dtype=torch.float64)
+            pg.all_reduce(q, op=pg.ReduceOp.SUM)
+            pts_e = float(q.item())
+        e2e = {"value": pts_e / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * N * 5,
+               "d2h_bytes_per_step": 4 * N * 3, "ms_per_step": 1e3 * te / args.steps}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        import oracle
+        m0_64 = m0.astype(np.float64)
+        m1_64 = m1.astype(np.float64)
+        s, q = oracle_sample(grid, m0_64, m1_64, args.beta)
+        cpu = {"value": q / s / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "one oracle gradient evaluation (state + adjoint solve, nt=4) of the "
+                         "same %d^3 workload, %.1f s" % (args.n, s)}
+
+    r0 = reps[0]
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic", "config": config_dict(args, world),
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
+            "gpu_launches": launches,
+            "registration": {"gn_iters": r0["gn_iters"], "pcg_iters_total": r0["pcg_iters_total"],
+                             "gnorm_rel": r0["gnorm_rel"], "r": r0["r"], "J": r0["J"],
+                             "detj_min": r0["detj_min"], "detj_max": r0["detj_max"],
+                             "cfl": r0["cfl"], "status": r0["status"],
+                             "time_to_tol_s": tmax / args.steps},
+            "kernels": {s["name"]: {"launches": s["launches"], "ms": 1e3 * s["seconds"],
+                                    "GBs": (s["bytes"] / s["seconds"] / 1e9) if s["seconds"] else None}
+                        for s in stats if s["launches"] > 0},
+        }
+        print(json.dumps(line))
+    ctx.close()
+    if pg:
+        pg.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

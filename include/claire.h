@@ -1,0 +1,256 @@
+/*
+ * claire.h - C ABI of libclaire.so, a GB300 (sm_103a) implementation of the
+ * semi-Lagrangian Gauss-Newton-Krylov hot path of stationary-velocity
+ * diffeomorphic registration ("CLAIRE at scale", arXiv 2209.08189).
+ *
+ * Problem (Sec. 2.1, Eq. (1)): given a template m0 and a reference m1 on the
+ * periodic grid Omega = [0, 2 pi)^3, find a stationary velocity v minimising
+ *     J(v) = 1/2 ||m(1) - m1||^2 + beta_v/2 reg_v(v) + beta_w/2 reg_w(div v)
+ * subject to d_t m + v . grad m = 0, m(0) = m0.  reg_v is the H1 (or H2)
+ * seminorm of v and reg_w the H1 norm of w = div v (Sec. 2.1).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Grid: N1 x N2 x N3 nodes x = (i h1, j h2, k h3), h_c = 2 pi / N_c,
+ *    each N_c even and >= 8.  Scalar fields are float32 arrays of N = N1 N2 N3
+ *    values in C order (index (i N2 + j) N3 + k, x3 fastest).  Vector fields
+ *    are component-major: [3][N1][N2][N3].  Velocities are in physical units
+ *    (radians per unit time); displacements are in grid units.
+ *  - Discrete inner product: <a, b> = h1 h2 h3 sum(a b); J, the mismatch and
+ *    the regularisation energy use it.
+ *  - Pointers: unless an entry point says "device pointers", an array
+ *    argument may be a device pointer or a host pointer (pageable or
+ *    pinned); host arrays are staged through the context's workspace with
+ *    copies on the context's stream.  Arrays are owned by the caller and are
+ *    only read during the call, except outputs and v_inout.
+ *  - Streams: all device work is queued on the context's stream (default:
+ *    the legacy default stream; see claire_set_stream).  Every entry point
+ *    returns after its outputs are complete and visible to the host-side
+ *    caller's next operation on that stream; scalar outputs are host values.
+ *  - Errors: every entry point returns a claire_status and never throws.  A
+ *    negative status leaves outputs unspecified; claire_last_error() gives a
+ *    one-line message.  A context is not thread-safe: use one per host thread.
+ *  - There is no CPU fallback: without a usable CUDA device, claire_create
+ *    returns CLAIRE_ECUDA.
+ */
+#ifndef CLAIRE_H
+#define CLAIRE_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct claire_ctx claire_ctx;
+
+typedef enum {
+    CLAIRE_OK = 0,
+    CLAIRE_ENOTCONVERGED = 1,  /* warning: iteration cap hit; outputs hold the last iterate */
+    CLAIRE_EINVAL = -1,        /* bad argument (grid, sizes, null pointer, option value) */
+    CLAIRE_ENOMEM = -2,        /* device allocation failed (nothing was launched) */
+    CLAIRE_ECUDA = -3,         /* CUDA runtime error (message has the CUDA error string) */
+    CLAIRE_ECUFFT = -4,        /* cuFFT plan or execution error */
+    CLAIRE_ENONFINITE = -5,    /* a reduction saw NaN or Inf (input or iterate) */
+    CLAIRE_ELINESEARCH = -6,   /* Armijo line search found no acceptable step */
+    CLAIRE_ETIMEOUT = -7,      /* wall-clock limit reached; outputs hold the last iterate */
+    CLAIRE_ESTATE = -8,        /* call needs state that is not set (images, linearisation point) */
+    CLAIRE_ENOTIMPL = -9
+} claire_status;
+
+/* Interpolation order of the semi-Lagrangian gathers (Sec. 3, "IP kernel"). */
+#define CLAIRE_INTERP_CUBIC 3   /* cubic Lagrange, nodes floor-1 .. floor+2 */
+#define CLAIRE_INTERP_LINEAR 1  /* trilinear */
+
+/* claire_transport flags */
+#define CLAIRE_TRANSPORT_FWD 0  /* state, Eq. (1b)-(1c): m(1) from m(0) */
+#define CLAIRE_TRANSPORT_ADJ 1  /* adjoint, Eq. (4): lambda(0) from lambda(1) */
+
+/* claire_spectral ops (Sec. 2.2: "two FFTs and one Hadamard product") */
+#define CLAIRE_SPECTRAL_REG 0   /* S v: first variation of the regulariser */
+#define CLAIRE_SPECTRAL_INV 1   /* S^{-1} r (identity on the k = 0 mode): the preconditioner */
+#define CLAIRE_SPECTRAL_K   2   /* K b = b - c u (u . b) / (a + c |u|^2): the paper's K */
+
+typedef struct claire_opts {
+    int interp;          /* CLAIRE_INTERP_CUBIC (default) or CLAIRE_INTERP_LINEAR */
+    int reg;             /* 1 = H1 seminorm of v (default), 2 = H2 seminorm */
+    double beta_w;       /* weight of the H1 norm of div v; default 1e-4 */
+    int grad_form;       /* 0 = g = S v + b (default, exact gradient of J; H symmetric);
+                            1 = the paper's Eq. (3) form g = beta_v A v + K b */
+    double gtol;         /* stop when ||g|| / ||g0|| <= gtol; default 5e-2 (Sec. 4.2) */
+    int max_gn;          /* Gauss-Newton iteration cap; default 50 */
+    int max_pcg;         /* PCG iteration cap per Gauss-Newton step; default 50 */
+    double pcg_rtol_max; /* forcing eta_k = min(pcg_rtol_max, sqrt(||g_k||/||g_0||)); default 0.5 */
+    int pcg_fixed;       /* 1 = always run max_pcg PCG iterations (no residual exit); default 0 */
+    double armijo_c1;    /* sufficient-decrease constant; default 1e-4 */
+    int max_ls;          /* step halvings before CLAIRE_ELINESEARCH; default 10 */
+    double wall_limit_s; /* claire_register wall-clock cap in seconds; 0 = none (default) */
+    int timing;          /* 1 = time phases with CUDA events into claire_report.t_phase_s */
+} claire_opts;
+
+/* Phase slots of claire_report.t_phase_s (seconds, CUDA-event timed when opts.timing = 1). */
+#define CLAIRE_PHASE_BACKTRACE 0   /* RK2 characteristics, div v, div v at X+ */
+#define CLAIRE_PHASE_STATE 1       /* forward solve and FD8 gradients of m^j */
+#define CLAIRE_PHASE_ADJOINT 2     /* adjoint solve with gradient body */
+#define CLAIRE_PHASE_INCREMENTAL 3 /* incremental state + incremental adjoint solves */
+#define CLAIRE_PHASE_SPECTRAL 4    /* FFTs and spectral scaling */
+#define CLAIRE_PHASE_VECTOR 5      /* PCG / line-search vector updates and reductions */
+#define CLAIRE_PHASE_OBJECTIVE 6   /* line-search objective evaluations */
+#define CLAIRE_PHASE_GATHER 7      /* the SL gather kernels alone (subset of 0-3, 6) */
+#define CLAIRE_MAX_LOGGED_STEPS 64
+
+typedef struct claire_report {
+    int status;                 /* claire_status of the run */
+    int gn_iters;               /* Gauss-Newton updates taken */
+    int pcg_iters_total;        /* Hessian matvecs in all PCG solves */
+    int pcg_iters[CLAIRE_MAX_LOGGED_STEPS];   /* PCG iterations per GN step */
+    double alpha[CLAIRE_MAX_LOGGED_STEPS];    /* accepted step length per GN step */
+    double J;                   /* objective at the returned v */
+    double mismatch;            /* 1/2 ||m(1) - m1||^2 at the returned v */
+    double r;                   /* relative residual ||m(1)-m1||^2 / ||m0-m1||^2 (Sec. 4.1) */
+    double gnorm_rel;           /* ||g|| / ||g0|| at the returned v */
+    double detj_min, detj_max;  /* extrema of det grad y at the returned v (Sec. 3, J_min) */
+    double cfl;                 /* max_x |v(x)|_2 dt / min_c h_c at the returned v */
+    double t_total_s;           /* wall time of the call */
+    double t_phase_s[8];        /* see CLAIRE_PHASE_* */
+    double gather_launches;     /* SL gather kernel launches (CLAIRE_PHASE_GATHER count) */
+    double interp_points;       /* grid points x scalar fields interpolated by the gathers */
+    double interp_bytes;        /* algorithmic HBM bytes of the gather kernels (each value once) */
+} claire_report;
+
+/* Fill *opts with the defaults listed above.  Returns CLAIRE_EINVAL on NULL. */
+claire_status claire_default_opts(claire_opts* opts);
+
+/*
+ * Create a context for grid[3] = {N1, N2, N3}, regularisation weight beta_v > 0
+ * (Sec. 3, "beta_v") and nt >= 1 semi-Lagrangian time steps (Sec. 3, "n_t").
+ * opts may be NULL for the defaults.  Allocates every device workspace up
+ * front (see claire_query_workspace) and the cuFFT plans; returns
+ * CLAIRE_ENOMEM before any kernel runs if the device cannot hold them.
+ * *ctx receives the new context (NULL on error).
+ */
+claire_status claire_create(claire_ctx** ctx, const int grid[3], double beta_v, int nt,
+                            const claire_opts* opts);
+
+/* Free all device memory and plans of ctx.  NULL is accepted. */
+claire_status claire_destroy(claire_ctx* ctx);
+
+/* Queue all further work of ctx on stream (a cudaStream_t, e.g. torch's
+ * current stream handle); NULL selects the legacy default stream. */
+claire_status claire_set_stream(claire_ctx* ctx, void* stream);
+
+/* Device bytes claire_create would allocate for this grid, nt and options. */
+claire_status claire_query_workspace(const int grid[3], int nt, const claire_opts* opts,
+                                     size_t* bytes);
+
+/* Copy the template m0 and reference m1 (N floats each) into the context.
+ * Invalidates the linearisation point. */
+claire_status claire_set_images(claire_ctx* ctx, const float* m0, const float* m1);
+
+/* Objective J(v) of Eq. (1a) and its mismatch term at v (3N floats).
+ * Either output pointer may be NULL.  Does not change the linearisation point. */
+claire_status claire_objective(claire_ctx* ctx, const float* v, double* J, double* mismatch);
+
+/*
+ * Reduced gradient, Eq. (3), at v (3N floats) into g (3N floats):
+ *   grad_form 0: g = S v + b,  grad_form 1: g = beta_v A v + K b,
+ *   b = int_0^1 lambda grad m dt (trapezoid on the nt+1 time points),
+ * with the state by SL transport (Eq. (1b)) and the adjoint lambda by SL
+ * transport of Eq. (4) from lambda(1) = m1 - m(1).  Makes v the
+ * linearisation point of later claire_hessian_matvec calls.  J may be NULL.
+ */
+claire_status claire_gradient(claire_ctx* ctx, const float* v, float* g, double* J);
+
+/*
+ * Gauss-Newton Hessian matvec, Eq. (6), at the last claire_gradient's v:
+ *   Hvt = S vt + int_0^1 lt grad m dt   (grad_form 1: K applied to the body
+ *   and beta_v A to vt), with the incremental state mt (d_t mt + v . grad mt
+ *   = -vt . grad m, mt(0) = 0) and incremental adjoint lt (Eq. (4) with
+ *   lt(1) = -mt(1)).  vt, Hvt: 3N floats.  CLAIRE_ESTATE without a prior
+ *   claire_gradient on the current images.
+ */
+claire_status claire_hessian_matvec(claire_ctx* ctx, const float* vt, float* Hvt);
+
+/* Preconditioner of the PCG solve: the spectral inverse of the regulariser
+ * (S^{-1}, or (beta_v A)^{-1} for grad_form 1), identity on k = 0.  3N floats. */
+claire_status claire_precond(claire_ctx* ctx, const float* r, float* z);
+
+/*
+ * Gauss-Newton-Krylov registration, Eq. (5): v_{k+1} = v_k + alpha_k vt_k with
+ * H vt_k = -g_k solved by matrix-free PCG (forcing opts.pcg_rtol_max) and
+ * alpha_k from an Armijo line search (start 1, halve).  v_inout holds the
+ * initial guess (3N floats; zeros for a cold start) and receives the result.
+ * rep may be NULL.  Returns CLAIRE_OK on ||g||/||g0|| <= gtol,
+ * CLAIRE_ENOTCONVERGED after max_gn steps, or an error; v_inout then holds
+ * the last accepted iterate.
+ */
+claire_status claire_register(claire_ctx* ctx, float* v_inout, claire_report* rep);
+
+/*
+ * Semi-Lagrangian transport over t in [0, 1] with nt RK2 steps by the
+ * velocity v (3N floats):
+ *   CLAIRE_TRANSPORT_FWD: m_out = m(1) of Eq. (1b) with m(0) = m_in;
+ *   CLAIRE_TRANSPORT_ADJ: m_out = lambda(0) of Eq. (4) with lambda(1) = m_in.
+ * m_in and m_out are N floats and may alias.
+ */
+claire_status claire_transport(claire_ctx* ctx, const float* v, const float* m_in, float* m_out,
+                               int flags);
+
+/* Extrema of the Jacobian determinant det grad y of the deformation map of v
+ * (Sec. 3, "J_min"; y = x + u with u transported by the state's SL steps,
+ * F = I + FD8(u), det and extrema in FP64). */
+claire_status claire_detj(claire_ctx* ctx, const float* v, double* detj_min, double* detj_max);
+
+/* ---- kernel-level entry points (device pointers only; ctx gives grid and stream) ---- */
+
+/* out[p] = f(x_p + d_p): f, out N floats, d 3N floats (grid units); order 3 or 1.
+ * Sec. 3 "IP kernel". */
+claire_status claire_interp(claire_ctx* ctx, const float* f, const float* d, float* out, int order);
+
+/* RK2 (Heun) characteristic displacement (Sec. 2.2) of v in grid units:
+ * direction +1: X = x - dt/2 [v(x) + v(x - dt v(x))]; direction -1: X+ with +v.
+ * dt = 1/nt of ctx; the velocity at the predictor point uses ctx's order. */
+claire_status claire_backtrace(claire_ctx* ctx, const float* v, float* d, int direction);
+
+/* 8th-order central FD gradient (f: N -> g: 3N) and divergence (v: 3N -> dv: N),
+ * periodic (Sec. 2.2, Sec. 3 "FD kernel"). */
+claire_status claire_fd8_grad(claire_ctx* ctx, const float* f, float* g);
+claire_status claire_fd8_div(claire_ctx* ctx, const float* v, float* dv);
+
+/* out = F^{-1}[M(k) F[in]] for the 3N-float vector field in (op: CLAIRE_SPECTRAL_*),
+ * with the context's beta_v, beta_w and reg. */
+claire_status claire_spectral(claire_ctx* ctx, const float* in, float* out, int op);
+
+/* FP64 inner product h1 h2 h3 sum_i x_i y_i over n floats (device pointers). */
+claire_status claire_dot(claire_ctx* ctx, const float* x, const float* y, size_t n, double* out);
+
+/* ---- instrumentation ---- */
+
+/* Per-kernel counters of ctx since creation or the last reset: launches,
+ * CUDA-event time on the context's stream (only while timing is on),
+ * algorithmic HBM bytes (each value counted once) and grid points x scalar
+ * fields interpolated.  name is one of sl_interp, sl_backtrace_rk2,
+ * sl_adjoint_step, sl_incremental_step, sl_incremental_last, sl_pointwise,
+ * fd8, spectral_scale, cufft (library transforms), reduce_f64,
+ * vector_update, sl_map_step, detj_minmax. */
+typedef struct claire_kernel_stat {
+    char name[32];
+    double launches, seconds, bytes, points;
+} claire_kernel_stat;
+
+/* Copy up to capacity entries into out; *count (may be NULL) receives the
+ * number of kernel classes.  reset = 1 zeroes the counters afterwards. */
+claire_status claire_kernel_stats(claire_ctx* ctx, claire_kernel_stat* out, int capacity, int* count,
+                                  int reset);
+
+/* Turn per-launch CUDA-event timing on (1) or off (0) after creation. */
+claire_status claire_set_timing(claire_ctx* ctx, int on);
+
+/* One-line description of the last error on ctx (never NULL; "" if none). */
+const char* claire_last_error(const claire_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLAIRE_H */

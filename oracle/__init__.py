@@ -177,6 +177,7 @@ class Params:
     max_gn: int = 50
     max_pcg: int = 10
     pcg_rtol_max: float = 0.5
+    pcg_fixed: bool = False  # run exactly max_pcg PCG iterations (fixed schedule)
     armijo_c1: float = 1e-4
     max_ls: int = 10
     adjoint: str = "sl"     # "sl" = paper's SL adjoint (OTD); "scatter" = exact transpose (DTO)
@@ -461,7 +462,7 @@ def register(m0, m1, p: Params, v0=None, mode=None, log=None):
             rep["status"] = "converged"
             break
         eta = min(p.pcg_rtol_max, math.sqrt(rel))
-        vt, its = pcg(st, -g, eta, p.max_pcg, mode)
+        vt, its = pcg(st, -g, eta, p.max_pcg, mode, fixed_iters=p.pcg_fixed)
         gtv = inner(g, vt, n)
         alpha, ok = 1.0, False
         for _ls in range(p.max_ls):

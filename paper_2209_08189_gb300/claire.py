@@ -1,0 +1,360 @@
+"""Thin ctypes binding of libclaire.so (C ABI in include/claire.h).
+
+Argument marshalling only: every numeric step runs in the library's CUDA
+kernels (and cuFFT).  Arrays are passed as raw pointers: torch CUDA tensors
+(device) or numpy arrays / CPU tensors (host; the library stages them).
+Each ``claire_*`` function returns the C status and raises ``ClaireError``
+for negative statuses.  There is no fallback: if the library is missing or
+no CUDA device is usable, loading or ``claire_create`` fails loudly.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libclaire.so")
+
+CLAIRE_OK = 0
+CLAIRE_ENOTCONVERGED = 1
+STATUS_NAMES = {0: "CLAIRE_OK", 1: "CLAIRE_ENOTCONVERGED", -1: "CLAIRE_EINVAL",
+                -2: "CLAIRE_ENOMEM", -3: "CLAIRE_ECUDA", -4: "CLAIRE_ECUFFT",
+                -5: "CLAIRE_ENONFINITE", -6: "CLAIRE_ELINESEARCH", -7: "CLAIRE_ETIMEOUT",
+                -8: "CLAIRE_ESTATE", -9: "CLAIRE_ENOTIMPL"}
+INTERP_CUBIC, INTERP_LINEAR = 3, 1
+TRANSPORT_FWD, TRANSPORT_ADJ = 0, 1
+SPECTRAL_REG, SPECTRAL_INV, SPECTRAL_K = 0, 1, 2
+PHASES = ["backtrace", "state", "adjoint", "incremental", "spectral", "vector", "objective",
+          "gather"]
+MAX_LOGGED_STEPS = 64
+
+
+class ClaireError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, status), msg))
+        self.status = status
+
+
+class claire_opts(ctypes.Structure):
+    _fields_ = [("interp", ctypes.c_int), ("reg", ctypes.c_int), ("beta_w", ctypes.c_double),
+                ("grad_form", ctypes.c_int), ("gtol", ctypes.c_double), ("max_gn", ctypes.c_int),
+                ("max_pcg", ctypes.c_int), ("pcg_rtol_max", ctypes.c_double),
+                ("pcg_fixed", ctypes.c_int), ("armijo_c1", ctypes.c_double),
+                ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
+                ("timing", ctypes.c_int)]
+
+
+class claire_report(ctypes.Structure):
+    _fields_ = [("status", ctypes.c_int), ("gn_iters", ctypes.c_int),
+                ("pcg_iters_total", ctypes.c_int),
+                ("pcg_iters", ctypes.c_int * MAX_LOGGED_STEPS),
+                ("alpha", ctypes.c_double * MAX_LOGGED_STEPS),
+                ("J", ctypes.c_double), ("mismatch", ctypes.c_double), ("r", ctypes.c_double),
+                ("gnorm_rel", ctypes.c_double), ("detj_min", ctypes.c_double),
+                ("detj_max", ctypes.c_double), ("cfl", ctypes.c_double),
+                ("t_total_s", ctypes.c_double), ("t_phase_s", ctypes.c_double * 8),
+                ("gather_launches", ctypes.c_double), ("interp_points", ctypes.c_double),
+                ("interp_bytes", ctypes.c_double)]
+
+    def as_dict(self):
+        n = min(self.gn_iters, MAX_LOGGED_STEPS)
+        return {"status": STATUS_NAMES.get(self.status, self.status), "gn_iters": self.gn_iters,
+                "pcg_iters_total": self.pcg_iters_total,
+                "pcg_iters": [self.pcg_iters[i] for i in range(n + (1 if self.status < 0 else 0))
+                              if i < MAX_LOGGED_STEPS],
+                "alpha": [self.alpha[i] for i in range(n)], "J": self.J,
+                "mismatch": self.mismatch, "r": self.r, "gnorm_rel": self.gnorm_rel,
+                "detj_min": self.detj_min, "detj_max": self.detj_max, "cfl": self.cfl,
+                "t_total_s": self.t_total_s,
+                "t_phase_s": {k: self.t_phase_s[i] for i, k in enumerate(PHASES)},
+                "gather_launches": self.gather_launches, "interp_points": self.interp_points,
+                "interp_bytes": self.interp_bytes}
+
+
+class claire_kernel_stat(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_double),
+                ("seconds", ctypes.c_double), ("bytes", ctypes.c_double),
+                ("points", ctypes.c_double)]
+
+
+_lib = None
+_vp = ctypes.c_void_p
+_ST = ctypes.c_int
+
+# name -> argtypes (restype claire_status unless listed in _RESTYPE)
+_SIGS = {
+    "claire_default_opts": [ctypes.POINTER(claire_opts)],
+    "claire_create": [ctypes.POINTER(_vp), ctypes.POINTER(ctypes.c_int), ctypes.c_double,
+                      ctypes.c_int, ctypes.POINTER(claire_opts)],
+    "claire_destroy": [_vp],
+    "claire_set_stream": [_vp, _vp],
+    "claire_query_workspace": [ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                               ctypes.POINTER(claire_opts), ctypes.POINTER(ctypes.c_size_t)],
+    "claire_set_images": [_vp, _vp, _vp],
+    "claire_objective": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "claire_gradient": [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
+    "claire_hessian_matvec": [_vp, _vp, _vp],
+    "claire_precond": [_vp, _vp, _vp],
+    "claire_register": [_vp, _vp, ctypes.POINTER(claire_report)],
+    "claire_transport": [_vp, _vp, _vp, _vp, ctypes.c_int],
+    "claire_detj": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "claire_interp": [_vp, _vp, _vp, _vp, ctypes.c_int],
+    "claire_backtrace": [_vp, _vp, _vp, ctypes.c_int],
+    "claire_fd8_grad": [_vp, _vp, _vp],
+    "claire_fd8_div": [_vp, _vp, _vp],
+    "claire_spectral": [_vp, _vp, _vp, ctypes.c_int],
+    "claire_dot": [_vp, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
+    "claire_kernel_stats": [_vp, ctypes.POINTER(claire_kernel_stat), ctypes.c_int,
+                            ctypes.POINTER(ctypes.c_int), ctypes.c_int],
+    "claire_set_timing": [_vp, ctypes.c_int],
+    "claire_last_error": [_vp],
+}
+_RESTYPE = {"claire_last_error": ctypes.c_char_p}
+
+
+def lib():
+    """Load libclaire.so (built in-tree by __graft_entry__.build())."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise ImportError("libclaire.so is not built (%s); run __graft_entry__.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        for name, args in _SIGS.items():
+            fn = getattr(L, name)
+            fn.argtypes = args
+            fn.restype = _RESTYPE.get(name, _ST)
+        _lib = L
+    return _lib
+
+
+def exported_symbols():
+    return sorted(_SIGS)
+
+
+def _ptr(a):
+    """Raw address of a torch tensor or numpy array (contiguous float32)."""
+    if a is None:
+        return None
+    if isinstance(a, np.ndarray):
+        if a.dtype != np.float32 or not a.flags["C_CONTIGUOUS"]:
+            raise ValueError("numpy arrays must be contiguous float32")
+        return a.ctypes.data
+    if hasattr(a, "data_ptr"):
+        if a.dtype.__repr__() != "torch.float32" or not a.is_contiguous():
+            raise ValueError("tensors must be contiguous float32")
+        return a.data_ptr()
+    if isinstance(a, int):
+        return a
+    raise TypeError("unsupported array type %r" % type(a))
+
+
+def _check(ctx, status):
+    if status < 0:
+        msg = lib().claire_last_error(ctx).decode() if ctx else ""
+        raise ClaireError(status, msg)
+    return status
+
+
+# ---- functions with the C names (argument marshalling only) ----
+
+def claire_default_opts():
+    o = claire_opts()
+    _check(None, lib().claire_default_opts(ctypes.byref(o)))
+    return o
+
+
+def claire_create(grid, beta_v, nt, opts=None):
+    h = _vp()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    st = lib().claire_create(ctypes.byref(h), g, float(beta_v), int(nt),
+                             ctypes.byref(opts) if opts is not None else None)
+    if st < 0:
+        raise ClaireError(st, "claire_create(grid=%s, beta_v=%g, nt=%d)" % (tuple(grid), beta_v, nt))
+    return h
+
+
+def claire_destroy(ctx):
+    return lib().claire_destroy(ctx)
+
+
+def claire_set_stream(ctx, stream_handle):
+    return _check(ctx, lib().claire_set_stream(ctx, stream_handle))
+
+
+def claire_query_workspace(grid, nt, opts=None):
+    b = ctypes.c_size_t()
+    g = (ctypes.c_int * 3)(*[int(x) for x in grid])
+    _check(None, lib().claire_query_workspace(g, int(nt), ctypes.byref(opts) if opts else None,
+                                              ctypes.byref(b)))
+    return b.value
+
+
+def claire_set_images(ctx, m0, m1):
+    return _check(ctx, lib().claire_set_images(ctx, _ptr(m0), _ptr(m1)))
+
+
+def claire_objective(ctx, v):
+    J = ctypes.c_double()
+    mis = ctypes.c_double()
+    _check(ctx, lib().claire_objective(ctx, _ptr(v), ctypes.byref(J), ctypes.byref(mis)))
+    return J.value, mis.value
+
+
+def claire_gradient(ctx, v, g):
+    J = ctypes.c_double()
+    _check(ctx, lib().claire_gradient(ctx, _ptr(v), _ptr(g), ctypes.byref(J)))
+    return J.value
+
+
+def claire_hessian_matvec(ctx, vt, Hvt):
+    return _check(ctx, lib().claire_hessian_matvec(ctx, _ptr(vt), _ptr(Hvt)))
+
+
+def claire_precond(ctx, r, z):
+    return _check(ctx, lib().claire_precond(ctx, _ptr(r), _ptr(z)))
+
+
+def claire_register(ctx, v_inout):
+    rep = claire_report()
+    st = lib().claire_register(ctx, _ptr(v_inout), ctypes.byref(rep))
+    _check(ctx, st)
+    return st, rep
+
+
+def claire_transport(ctx, v, m_in, m_out, flags=TRANSPORT_FWD):
+    return _check(ctx, lib().claire_transport(ctx, _ptr(v), _ptr(m_in), _ptr(m_out), int(flags)))
+
+
+def claire_detj(ctx, v):
+    lo = ctypes.c_double()
+    hi = ctypes.c_double()
+    _check(ctx, lib().claire_detj(ctx, _ptr(v), ctypes.byref(lo), ctypes.byref(hi)))
+    return lo.value, hi.value
+
+
+def claire_interp(ctx, f, d, out, order=INTERP_CUBIC):
+    return _check(ctx, lib().claire_interp(ctx, _ptr(f), _ptr(d), _ptr(out), int(order)))
+
+
+def claire_backtrace(ctx, v, d, direction=1):
+    return _check(ctx, lib().claire_backtrace(ctx, _ptr(v), _ptr(d), int(direction)))
+
+
+def claire_fd8_grad(ctx, f, g):
+    return _check(ctx, lib().claire_fd8_grad(ctx, _ptr(f), _ptr(g)))
+
+
+def claire_fd8_div(ctx, v, dv):
+    return _check(ctx, lib().claire_fd8_div(ctx, _ptr(v), _ptr(dv)))
+
+
+def claire_spectral(ctx, x, out, op):
+    return _check(ctx, lib().claire_spectral(ctx, _ptr(x), _ptr(out), int(op)))
+
+
+def claire_dot(ctx, x, y, n):
+    out = ctypes.c_double()
+    _check(ctx, lib().claire_dot(ctx, _ptr(x), _ptr(y), int(n), ctypes.byref(out)))
+    return out.value
+
+
+def claire_kernel_stats(ctx, reset=False):
+    arr = (claire_kernel_stat * 32)()
+    cnt = ctypes.c_int()
+    _check(ctx, lib().claire_kernel_stats(ctx, arr, 32, ctypes.byref(cnt), int(bool(reset))))
+    return [{"name": arr[i].name.decode(), "launches": arr[i].launches,
+             "seconds": arr[i].seconds, "bytes": arr[i].bytes, "points": arr[i].points}
+            for i in range(cnt.value)]
+
+
+def claire_set_timing(ctx, on):
+    return _check(ctx, lib().claire_set_timing(ctx, int(bool(on))))
+
+
+def claire_last_error(ctx):
+    return lib().claire_last_error(ctx).decode()
+
+
+class Context:
+    """Owning wrapper: ``Context(grid, beta_v, nt, **opts)``; methods take
+    torch CUDA tensors (or host numpy arrays) and call the C ABI."""
+
+    def __init__(self, grid, beta_v, nt, stream=None, **opts):
+        o = claire_default_opts()
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %r" % k)
+            setattr(o, k, v)
+        self.grid = tuple(int(x) for x in grid)
+        self.N = int(np.prod(self.grid))
+        self.nt = int(nt)
+        self.beta_v = float(beta_v)
+        self.opts = o
+        self.handle = claire_create(self.grid, beta_v, nt, o)
+        if stream is not None:
+            claire_set_stream(self.handle, stream)
+
+    def close(self):
+        if getattr(self, "handle", None):
+            claire_destroy(self.handle)
+            self.handle = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_stream(self, stream_handle):
+        claire_set_stream(self.handle, stream_handle)
+
+    def set_images(self, m0, m1):
+        claire_set_images(self.handle, m0, m1)
+
+    def objective(self, v):
+        return claire_objective(self.handle, v)
+
+    def gradient(self, v, g):
+        return claire_gradient(self.handle, v, g)
+
+    def hessian_matvec(self, vt, Hvt):
+        claire_hessian_matvec(self.handle, vt, Hvt)
+
+    def precond(self, r, z):
+        claire_precond(self.handle, r, z)
+
+    def register(self, v_inout):
+        st, rep = claire_register(self.handle, v_inout)
+        return st, rep.as_dict()
+
+    def transport(self, v, m_in, m_out, flags=TRANSPORT_FWD):
+        claire_transport(self.handle, v, m_in, m_out, flags)
+
+    def detj(self, v):
+        return claire_detj(self.handle, v)
+
+    def interp(self, f, d, out, order=INTERP_CUBIC):
+        claire_interp(self.handle, f, d, out, order)
+
+    def backtrace(self, v, d, direction=1):
+        claire_backtrace(self.handle, v, d, direction)
+
+    def fd8_grad(self, f, g):
+        claire_fd8_grad(self.handle, f, g)
+
+    def fd8_div(self, v, dv):
+        claire_fd8_div(self.handle, v, dv)
+
+    def spectral(self, x, out, op):
+        claire_spectral(self.handle, x, out, op)
+
+    def dot(self, x, y, n=None):
+        return claire_dot(self.handle, x, y, n if n is not None else x.numel())
+
+    def kernel_stats(self, reset=False):
+        return claire_kernel_stats(self.handle, reset)
+
+    def set_timing(self, on):
+        claire_set_timing(self.handle, on)

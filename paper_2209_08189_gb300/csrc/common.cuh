@@ -1,0 +1,153 @@
+// Device-side building blocks shared by the sm_103a kernels of libclaire:
+// periodic index wrapping, 1-D interpolation weights and the off-grid gather
+// of one or three fields.  Internal header (not part of the C ABI).
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace claire {
+
+// Grid geometry passed by value to every kernel.
+struct Grid {
+    int n1, n2, n3;       // nodes per axis, x3 fastest
+    int n23;              // n2 * n3
+    uint32_t N;           // n1 * n2 * n3 (< 2^31)
+    float h1, h2, h3;     // 2 pi / n_c
+    float ih1, ih2, ih3;  // n_c / (2 pi)
+};
+
+__device__ __forceinline__ int wrap_index(int x, int n)
+{
+    int r = x % n;
+    return r < 0 ? r + n : r;
+}
+
+// Split a grid-unit displacement into its integer cell offset and fraction
+// t in [0,1).  The offset is clamped so that index arithmetic cannot
+// overflow for absurd inputs (the wrapped index then stays in range).
+__device__ __forceinline__ int split_disp(float d, float& t)
+{
+    float fl = floorf(d);
+    t = d - fl;
+    fl = fminf(fmaxf(fl, -1048576.0f), 1048576.0f);
+    return static_cast<int>(fl);
+}
+
+// Cubic Lagrange cardinal functions on the nodes -1, 0, 1, 2 at t in [0,1).
+__device__ __forceinline__ void cubic_weights(float t, float w[4])
+{
+    const float tp1 = t + 1.0f, tm1 = t - 1.0f, tm2 = t - 2.0f;
+    const float t_tm1 = t * tm1;
+    const float tp1_tm2 = tp1 * tm2;
+    w[0] = -(1.0f / 6.0f) * t_tm1 * tm2;
+    w[1] = 0.5f * tp1_tm2 * tm1;
+    w[2] = -0.5f * tp1_tm2 * t;
+    w[3] = (1.0f / 6.0f) * tp1 * t_tm1;
+}
+
+// Stencil of one axis: wrapped node indices and weights.
+template <int ORDER>
+struct Axis {
+    static constexpr int M = (ORDER == 3) ? 4 : 2;
+    int idx[M];
+    float w[M];
+    __device__ __forceinline__ void build(int node, float disp, int n)
+    {
+        float t;
+        int base = node + split_disp(disp, t) - (ORDER == 3 ? 1 : 0);
+        int b = wrap_index(base, n);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            int q = b + a;
+            idx[a] = q >= n ? q - n : q;
+        }
+        if constexpr (ORDER == 3) {
+            cubic_weights(t, w);
+        } else {
+            w[0] = 1.0f - t;
+            w[1] = t;
+        }
+    }
+};
+
+// Tensor-product stencil at the off-grid point (i + d1, j + d2, k + d3).
+template <int ORDER>
+struct Stencil {
+    Axis<ORDER> a1, a2, a3;
+    __device__ __forceinline__ void build(const Grid& g, int i, int j, int k, float d1, float d2,
+                                          float d3)
+    {
+        a1.build(i, d1, g.n1);
+        a2.build(j, d2, g.n2);
+        a3.build(k, d3, g.n3);
+#pragma unroll
+        for (int a = 0; a < Axis<ORDER>::M; ++a) {
+            a1.idx[a] *= g.n23;
+            a2.idx[a] *= g.n3;
+        }
+    }
+    // Separable contraction: x3 first (contiguous loads), then x2, then x1.
+    __device__ __forceinline__ float eval(const float* __restrict__ f) const
+    {
+        constexpr int M = Axis<ORDER>::M;
+        float r = 0.0f;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            float sa = 0.0f;
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                const float* row = f + a1.idx[a] + a2.idx[b];
+                float sb = 0.0f;
+#pragma unroll
+                for (int c = 0; c < M; ++c) sb = fmaf(a3.w[c], __ldg(row + a3.idx[c]), sb);
+                sa = fmaf(a2.w[b], sb, sa);
+            }
+            r = fmaf(a1.w[a], sa, r);
+        }
+        return r;
+    }
+    // Three fields sharing the stencil (f, f + stride, f + 2 stride).
+    __device__ __forceinline__ void eval3(const float* __restrict__ f, uint32_t stride,
+                                          float out[3]) const
+    {
+        constexpr int M = Axis<ORDER>::M;
+        float r0 = 0.0f, r1 = 0.0f, r2 = 0.0f;
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            float s0 = 0.0f, s1 = 0.0f, s2 = 0.0f;
+#pragma unroll
+            for (int b = 0; b < M; ++b) {
+                const float* row = f + a1.idx[a] + a2.idx[b];
+                float q0 = 0.0f, q1 = 0.0f, q2 = 0.0f;
+#pragma unroll
+                for (int c = 0; c < M; ++c) {
+                    const int o = a3.idx[c];
+                    q0 = fmaf(a3.w[c], __ldg(row + o), q0);
+                    q1 = fmaf(a3.w[c], __ldg(row + stride + o), q1);
+                    q2 = fmaf(a3.w[c], __ldg(row + 2 * stride + o), q2);
+                }
+                s0 = fmaf(a2.w[b], q0, s0);
+                s1 = fmaf(a2.w[b], q1, s1);
+                s2 = fmaf(a2.w[b], q2, s2);
+            }
+            r0 = fmaf(a1.w[a], s0, r0);
+            r1 = fmaf(a1.w[a], s1, r1);
+            r2 = fmaf(a1.w[a], s2, r2);
+        }
+        out[0] = r0;
+        out[1] = r1;
+        out[2] = r2;
+    }
+};
+
+// Grid coordinates of linear index p.
+__device__ __forceinline__ void coords_of(const Grid& g, uint32_t p, int& i, int& j, int& k)
+{
+    i = static_cast<int>(p / static_cast<uint32_t>(g.n23));
+    uint32_t r = p - static_cast<uint32_t>(i) * static_cast<uint32_t>(g.n23);
+    j = static_cast<int>(r / static_cast<uint32_t>(g.n3));
+    k = static_cast<int>(r - static_cast<uint32_t>(j) * static_cast<uint32_t>(g.n3));
+}
+
+}  // namespace claire

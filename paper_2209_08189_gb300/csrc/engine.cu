@@ -1,0 +1,1207 @@
+// Host engine and C ABI of libclaire: context and workspaces, the
+// semi-Lagrangian solves of the reduced-space Gauss-Newton-Krylov method
+// ("CLAIRE at scale", arXiv 2209.08189, Sec. 2.2, Eqs. (1), (3)-(6)),
+// matrix-free PCG and the Armijo line search.  Every numeric step runs in
+// the kernels of sl_kernels.cu / vec_kernels.cu or in cuFFT on the
+// context's stream; the host only sequences launches and reads FP64 scalars.
+#include "claire.h"
+#include "internal.h"
+
+#include <algorithm>
+#include <chrono>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+using namespace claire;
+
+namespace {
+
+// Kernel classes tracked for the per-kernel statistics (CUDA-event timed
+// when opts.timing is set; byte counts are algorithmic: each value once).
+enum KernelKind {
+    KK_INTERP = 0,   // state step / plain gather
+    KK_BACKTRACE,
+    KK_ADJ_STEP,
+    KK_INC_STEP,
+    KK_INC_LAST,
+    KK_POINTWISE,    // adj_init, inc_init
+    KK_FD8,
+    KK_SPECTRAL,
+    KK_FFT,          // cuFFT executions (library)
+    KK_REDUCE,
+    KK_VECTOR,
+    KK_MAP,
+    KK_DETJ,
+    KK_COUNT
+};
+
+const char* kKernelNames[KK_COUNT] = {
+    "sl_interp",  "sl_backtrace_rk2", "sl_adjoint_step", "sl_incremental_step",
+    "sl_incremental_last", "sl_pointwise", "fd8", "spectral_scale", "cufft", "reduce_f64",
+    "vector_update", "sl_map_step", "detj_minmax"};
+
+struct KernelStat {
+    double launches = 0, seconds = 0, bytes = 0, points = 0;
+};
+
+struct EventPair {
+    cudaEvent_t a, b;
+    int kind;
+    int phase;
+};
+
+}  // namespace
+
+struct claire_ctx {
+    Grid grid{};
+    int n[3]{};
+    size_t N = 0, M = 0;  // real points, complex modes per component
+    int nt = 0;
+    double dt = 0, beta_v = 0, hvol = 0;
+    claire_opts o{};
+    RegParams rp{};
+    cudaStream_t stream = nullptr;
+    int device = 0, nsm = 0, red_blocks = 0;
+    cufftHandle r2c = 0, c2r = 0;
+    bool plans = false;
+    std::string err;
+
+    // workspace arena
+    void* arena = nullptr;
+    size_t arena_bytes = 0;
+    float *m0 = nullptr, *m1 = nullptr;
+    float *v = nullptr;                   // linearisation point
+    float *dS = nullptr, *dA = nullptr;   // state / adjoint characteristics
+    float *divv = nullptr, *divXp = nullptr;
+    float *m = nullptr, *gm = nullptr;    // (nt+1) N and (nt+1) 3N
+    float *l0 = nullptr, *l1 = nullptr;   // rolling scalar fields
+    float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    cufftComplex* spec = nullptr;
+    double* partials = nullptr;           // 2 * red_blocks
+    double* dres = nullptr;               // device scalars
+    double* hres = nullptr;               // pinned host scalars
+
+    bool have_images = false, have_lin = false;
+    double J_lin = 0, mis_lin = 0, reg_lin = 0;
+
+    // statistics and timing
+    KernelStat ks[KK_COUNT];
+    double phase_s[8]{};
+    std::vector<EventPair> pending;
+    std::vector<cudaEvent_t> pool;
+    int cur_phase = -1;
+
+    ~claire_ctx() { release(); }
+
+    void release()
+    {
+        for (auto& e : pending) {
+            cudaEventDestroy(e.a);
+            cudaEventDestroy(e.b);
+        }
+        pending.clear();
+        for (auto e : pool) cudaEventDestroy(e);
+        pool.clear();
+        if (plans) {
+            cufftDestroy(r2c);
+            cufftDestroy(c2r);
+            plans = false;
+        }
+        if (arena) cudaFree(arena);
+        arena = nullptr;
+        if (hres) cudaFreeHost(hres);
+        hres = nullptr;
+    }
+};
+
+namespace {
+
+claire_status fail(claire_ctx* c, claire_status s, const char* fmt, ...)
+{
+    if (c) {
+        char buf[512];
+        va_list ap;
+        va_start(ap, fmt);
+        vsnprintf(buf, sizeof(buf), fmt, ap);
+        va_end(ap);
+        c->err = buf;
+    }
+    return s;
+}
+
+#define CL_CUDA(ctx, call)                                                                   \
+    do {                                                                                     \
+        cudaError_t e_ = (call);                                                             \
+        if (e_ != cudaSuccess) {                                                             \
+            return fail((ctx), e_ == cudaErrorMemoryAllocation ? CLAIRE_ENOMEM : CLAIRE_ECUDA, \
+                        "%s: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+        }                                                                                    \
+    } while (0)
+
+#define CL_FFT(ctx, call)                                                                   \
+    do {                                                                                    \
+        cufftResult e_ = (call);                                                            \
+        if (e_ != CUFFT_SUCCESS)                                                            \
+            return fail((ctx), e_ == CUFFT_ALLOC_FAILED ? CLAIRE_ENOMEM : CLAIRE_ECUFFT,    \
+                        "%s: cufft error %d (%s:%d)", #call, (int)e_, __FILE__, __LINE__); \
+    } while (0)
+
+#define CL_TRY(expr)                         \
+    do {                                     \
+        claire_status s_ = (expr);           \
+        if (s_ < 0) return s_;               \
+    } while (0)
+
+#define CL_LAUNCHED(ctx) CL_CUDA(ctx, cudaGetLastError())
+
+bool valid_grid(const int grid[3])
+{
+    if (!grid) return false;
+    long long N = 1;
+    for (int c = 0; c < 3; ++c) {
+        if (grid[c] < 8 || (grid[c] & 1)) return false;
+        N *= grid[c];
+    }
+    return N < (1LL << 31);
+}
+
+void fill_defaults(claire_opts* o)
+{
+    o->interp = CLAIRE_INTERP_CUBIC;
+    o->reg = 1;
+    o->beta_w = 1e-4;
+    o->grad_form = 0;
+    o->gtol = 5e-2;
+    o->max_gn = 50;
+    o->max_pcg = 50;
+    o->pcg_rtol_max = 0.5;
+    o->pcg_fixed = 0;
+    o->armijo_c1 = 1e-4;
+    o->max_ls = 10;
+    o->wall_limit_s = 0.0;
+    o->timing = 0;
+}
+
+bool valid_opts(const claire_opts& o)
+{
+    return (o.interp == 1 || o.interp == 3) && (o.reg == 1 || o.reg == 2) && o.beta_w >= 0 &&
+           (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
+           o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
+           o.max_ls >= 1 && o.wall_limit_s >= 0;
+}
+
+// Layout of the workspace arena in floats (each region 256-byte aligned).
+struct Layout {
+    size_t off[32];
+    int count = 0;
+    size_t total = 0;  // floats
+    size_t add(size_t floats)
+    {
+        size_t o = total;
+        off[count++] = o;
+        total += (floats + 63) / 64 * 64;
+        return o;
+    }
+};
+
+size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, Layout* L)
+{
+    Layout tmp;
+    Layout& l = L ? *L : tmp;
+    l.add(N);                 // m0
+    l.add(N);                 // m1
+    l.add(3 * N);             // v
+    l.add(3 * N);             // dS
+    l.add(3 * N);             // dA
+    l.add(N);                 // divv
+    l.add(N);                 // divXp
+    l.add((nt + 1) * N);      // m
+    l.add(3 * (nt + 1) * N);  // gm
+    l.add(N);                 // l0
+    l.add(N);                 // l1
+    for (int i = 0; i < 6; ++i) l.add(3 * N);  // g x r z p q
+    l.add(6 * M);             // spec (3 complex half-spectra)
+    l.add(4 * red_blocks);    // partials (2 * red_blocks doubles)
+    l.add(32);                // dres (16 doubles)
+    return l.total;
+}
+
+bool is_device_ptr(const void* ptr)
+{
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, ptr) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+// ---------------------------------------------------------------------------
+// timing
+// ---------------------------------------------------------------------------
+
+cudaEvent_t take_event(claire_ctx* c)
+{
+    if (!c->pool.empty()) {
+        cudaEvent_t e = c->pool.back();
+        c->pool.pop_back();
+        return e;
+    }
+    cudaEvent_t e = nullptr;
+    cudaEventCreate(&e);
+    return e;
+}
+
+struct KTimer {
+    claire_ctx* c;
+    int kind;
+    cudaEvent_t a = nullptr;
+    KTimer(claire_ctx* cc, int k, double bytes, double points, double launches = 1)
+        : c(cc), kind(k)
+    {
+        c->ks[k].launches += launches;
+        c->ks[k].bytes += bytes;
+        c->ks[k].points += points;
+        if (c->o.timing) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~KTimer()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({a, b, kind, c->cur_phase});
+        }
+    }
+};
+
+struct PhaseScope {
+    claire_ctx* c;
+    int prev;
+    cudaEvent_t a = nullptr;
+    int ph;
+    PhaseScope(claire_ctx* cc, int phase) : c(cc), prev(cc->cur_phase), ph(phase)
+    {
+        c->cur_phase = phase;
+        if (c->o.timing) {
+            a = take_event(c);
+            cudaEventRecord(a, c->stream);
+        }
+    }
+    ~PhaseScope()
+    {
+        if (a) {
+            cudaEvent_t b = take_event(c);
+            cudaEventRecord(b, c->stream);
+            c->pending.push_back({a, b, -1, ph});
+        }
+        c->cur_phase = prev;
+    }
+};
+
+// Fold finished event pairs into the statistics (synchronises the stream).
+void collect_timing(claire_ctx* c)
+{
+    if (c->pending.empty()) return;
+    cudaStreamSynchronize(c->stream);
+    for (auto& e : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, e.a, e.b) == cudaSuccess) {
+            if (e.kind >= 0) {
+                c->ks[e.kind].seconds += ms * 1e-3;
+                if (e.kind == KK_INTERP || e.kind == KK_ADJ_STEP || e.kind == KK_INC_STEP ||
+                    e.kind == KK_INC_LAST || e.kind == KK_BACKTRACE || e.kind == KK_MAP)
+                    c->phase_s[CLAIRE_PHASE_GATHER] += ms * 1e-3;
+            } else if (e.phase >= 0 && e.phase < 8) {
+                c->phase_s[e.phase] += ms * 1e-3;
+            }
+        }
+        c->pool.push_back(e.a);
+        c->pool.push_back(e.b);
+    }
+    cudaGetLastError();
+    c->pending.clear();
+}
+
+// ---------------------------------------------------------------------------
+// building blocks on the context's stream
+// ---------------------------------------------------------------------------
+
+claire_status sync_scalars(claire_ctx* c, int count)
+{
+    CL_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, count * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CLAIRE_OK;
+}
+
+// dres[slot] = scale * sum x*y  (device only; no sync)
+claire_status dot_async(claire_ctx* c, const float* x, const float* y, size_t n, double scale,
+                        int slot)
+{
+    KTimer t(c, KK_REDUCE, 8.0 * n, 0, 2);
+    launch_dot_partial(x, y, n, c->partials, c->red_blocks, c->stream);
+    launch_final_sum(c->partials, c->red_blocks, scale, c->dres + slot, c->stream);
+    CL_LAUNCHED(c);
+    return CLAIRE_OK;
+}
+
+claire_status dot(claire_ctx* c, const float* x, const float* y, size_t n, double* out)
+{
+    PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+    CL_TRY(dot_async(c, x, y, n, c->hvol, 0));
+    CL_TRY(sync_scalars(c, 1));
+    *out = c->hres[0];
+    if (!std::isfinite(*out)) return fail(c, CLAIRE_ENONFINITE, "non-finite inner product");
+    return CLAIRE_OK;
+}
+
+// out = F^{-1}[M(k) F[in]] for a 3N vector field
+claire_status spectral(claire_ctx* c, const float* in, float* out, SpectralOp op)
+{
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    {
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecR2C(c->r2c, const_cast<float*>(in), c->spec));
+    }
+    {
+        KTimer t(c, KK_SPECTRAL, 48.0 * c->M, 0);
+        launch_spectral(c->grid, c->spec, c->M, op, c->rp, static_cast<float>(1.0 / c->N), c->stream);
+        CL_LAUNCHED(c);
+    }
+    {
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecC2R(c->c2r, c->spec, out));
+    }
+    return CLAIRE_OK;
+}
+
+claire_status fd8_grad(claire_ctx* c, const float* f, float* out)
+{
+    KTimer t(c, KK_FD8, 16.0 * c->N, 0);
+    launch_fd8_grad(c->grid, f, out, c->stream);
+    CL_LAUNCHED(c);
+    return CLAIRE_OK;
+}
+
+claire_status backtrace(claire_ctx* c, const float* v, float* d, int sign)
+{
+    KTimer t(c, KK_BACKTRACE, 24.0 * c->N, 3.0 * c->N);
+    launch_backtrace(c->grid, c->o.interp, v, static_cast<float>(c->dt), sign, d, c->stream);
+    CL_LAUNCHED(c);
+    return CLAIRE_OK;
+}
+
+claire_status interp(claire_ctx* c, const float* f, const float* d, float* out)
+{
+    KTimer t(c, KK_INTERP, 20.0 * c->N, 1.0 * c->N);
+    launch_interp(c->grid, c->o.interp, f, d, out, c->stream);
+    CL_LAUNCHED(c);
+    return CLAIRE_OK;
+}
+
+// Per-velocity data: X, X+, div v, div v (X+).
+claire_status characteristics(claire_ctx* c, const float* v, float* dS, float* dA, float* divv,
+                              float* divXp)
+{
+    PhaseScope ps(c, CLAIRE_PHASE_BACKTRACE);
+    if (dS) CL_TRY(backtrace(c, v, dS, +1));
+    if (dA) {
+        CL_TRY(backtrace(c, v, dA, -1));
+        {
+            KTimer t(c, KK_FD8, 16.0 * c->N, 0);
+            launch_fd8_div(c->grid, v, divv, c->stream);
+            CL_LAUNCHED(c);
+        }
+        CL_TRY(interp(c, divv, dA, divXp));
+    }
+    return CLAIRE_OK;
+}
+
+double trap_w(const claire_ctx* c, int j) { return (j == 0 || j == c->nt) ? 0.5 * c->dt : c->dt; }
+
+// Set the linearisation point: characteristics, states m^j and grad m^j, S v,
+// objective pieces.  v (device) is copied into c->v unless it already is c->v.
+claire_status linearise(claire_ctx* c, const float* v)
+{
+    if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
+    c->have_lin = false;
+    if (v != c->v)
+        CL_CUDA(c, cudaMemcpyAsync(c->v, v, 3 * c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+    CL_TRY(characteristics(c, c->v, c->dS, c->dA, c->divv, c->divXp));
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_STATE);
+        CL_CUDA(c, cudaMemcpyAsync(c->m, c->m0, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
+                                   c->stream));
+        for (int j = 0; j < c->nt; ++j) CL_TRY(interp(c, c->m + j * c->N, c->dS, c->m + (j + 1) * c->N));
+        for (int j = 0; j <= c->nt; ++j) CL_TRY(fd8_grad(c, c->m + j * c->N, c->gm + 3 * j * c->N));
+    }
+    return CLAIRE_OK;
+}
+
+// g = S v + b (grad_form 0) or K(S v + b) at the current linearisation point;
+// also returns J, mismatch, reg energy.
+claire_status gradient_at_lin(claire_ctx* c, float* g)
+{
+    const size_t N = c->N;
+    CL_TRY(spectral(c, c->v, g, SPEC_REG));
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+        CL_TRY(dot_async(c, c->v, g, 3 * N, 0.5 * c->hvol, 0));
+        KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
+        launch_sqdiff_partial(c->m + c->nt * N, c->m1, N, c->partials, c->red_blocks, c->stream);
+        launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 1, c->stream);
+        CL_LAUNCHED(c);
+    }
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_ADJOINT);
+        float* lam = c->l0;
+        float* lnext = c->l1;
+        {
+            KTimer t(c, KK_POINTWISE, 48.0 * N, 0);
+            launch_adj_init(c->grid, c->m1, c->m + c->nt * N, static_cast<float>(trap_w(c, c->nt)),
+                            c->gm + 3 * c->nt * N, 1, lam, g, c->stream);
+            CL_LAUNCHED(c);
+        }
+        for (int j = c->nt - 1; j >= 0; --j) {
+            std::swap(lam, lnext);
+            KTimer t(c, KK_ADJ_STEP, 64.0 * N, 1.0 * N);
+            launch_adj_step(c->grid, c->o.interp, lnext, c->dA, c->divv, c->divXp,
+                            static_cast<float>(c->dt), static_cast<float>(trap_w(c, j)),
+                            c->gm + 3 * j * N, lam, g, c->stream);
+            CL_LAUNCHED(c);
+        }
+    }
+    if (c->o.grad_form == 1) CL_TRY(spectral(c, g, g, SPEC_K));
+    CL_TRY(sync_scalars(c, 2));
+    c->reg_lin = c->hres[0];
+    c->mis_lin = c->hres[1];
+    c->J_lin = c->reg_lin + c->mis_lin;
+    if (!std::isfinite(c->J_lin)) return fail(c, CLAIRE_ENONFINITE, "non-finite objective");
+    c->have_lin = true;
+    return CLAIRE_OK;
+}
+
+// H vt at the linearisation point into out (out != vt).
+claire_status matvec(claire_ctx* c, const float* vt, float* out)
+{
+    if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
+    const size_t N = c->N;
+    const int nt = c->nt;
+    const float dt = static_cast<float>(c->dt);
+    CL_TRY(spectral(c, vt, out, SPEC_REG));
+    PhaseScope ps(c, CLAIRE_PHASE_INCREMENTAL);
+    float* a = c->l0;
+    float* b = c->l1;
+    // incremental state: q^0 = dt/2 f^0, q^{j+1} = q^j(X) + dt f^{j+1}
+    {
+        KTimer t(c, KK_POINTWISE, 28.0 * N, 0);
+        launch_inc_init(c->grid, vt, c->gm, 0.5f * dt, a, c->stream);
+        CL_LAUNCHED(c);
+    }
+    for (int j = 0; j + 1 < nt; ++j) {
+        KTimer t(c, KK_INC_STEP, 44.0 * N, 1.0 * N);
+        launch_inc_step(c->grid, c->o.interp, a, c->dS, vt, c->gm + 3 * (j + 1) * N, dt, b, c->stream);
+        CL_LAUNCHED(c);
+        std::swap(a, b);
+    }
+    {
+        KTimer t(c, KK_INC_LAST, 68.0 * N, 1.0 * N);
+        launch_inc_last(c->grid, c->o.interp, a, c->dS, vt, c->gm + 3 * nt * N, 0.5f * dt,
+                        static_cast<float>(trap_w(c, nt)), 1, b, out, c->stream);
+        CL_LAUNCHED(c);
+    }
+    // incremental adjoint from lt^{nt} (in b), body accumulated into out
+    float* lam = b;
+    float* lnext = a;
+    for (int j = nt - 1; j >= 0; --j) {
+        std::swap(lam, lnext);
+        KTimer t(c, KK_ADJ_STEP, 64.0 * N, 1.0 * N);
+        launch_adj_step(c->grid, c->o.interp, lnext, c->dA, c->divv, c->divXp, dt,
+                        static_cast<float>(trap_w(c, j)), c->gm + 3 * j * N, lam, out, c->stream);
+        CL_LAUNCHED(c);
+    }
+    if (c->o.grad_form == 1) CL_TRY(spectral(c, out, out, SPEC_K));
+    return CLAIRE_OK;
+}
+
+claire_status precond(claire_ctx* c, const float* r, float* z)
+{
+    return spectral(c, r, z, c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV);
+}
+
+// J(v) for a trial v (device, 3N); uses z (displacement), l0/l1, r (S v).
+claire_status objective_at(claire_ctx* c, const float* v, double* J, double* mis)
+{
+    if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
+    const size_t N = c->N;
+    PhaseScope ps(c, CLAIRE_PHASE_OBJECTIVE);
+    CL_TRY(backtrace(c, v, c->z, +1));
+    const float* src = c->m0;
+    float* a = c->l0;
+    float* b = c->l1;
+    for (int j = 0; j < c->nt; ++j) {
+        CL_TRY(interp(c, src, c->z, a));
+        src = a;
+        std::swap(a, b);
+    }
+    CL_TRY(spectral(c, v, c->r, SPEC_REG));
+    CL_TRY(dot_async(c, v, c->r, 3 * N, 0.5 * c->hvol, 0));
+    {
+        KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
+        launch_sqdiff_partial(src, c->m1, N, c->partials, c->red_blocks, c->stream);
+        launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 1, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_TRY(sync_scalars(c, 2));
+    if (mis) *mis = c->hres[1];
+    if (J) *J = c->hres[0] + c->hres[1];
+    if (!std::isfinite(c->hres[0] + c->hres[1]))
+        return fail(c, CLAIRE_ENONFINITE, "non-finite objective");
+    return CLAIRE_OK;
+}
+
+// Extrema of det(I + grad u) of the deformation map of v (device, 3N).
+// Uses z (displacement), r and p (map), partials.
+claire_status detj_of(claire_ctx* c, const float* v, double* lo, double* hi)
+{
+    const size_t N = c->N;
+    CL_TRY(backtrace(c, v, c->z, +1));
+    float* a = c->r;
+    float* b = c->p;
+    CL_CUDA(c, cudaMemsetAsync(a, 0, 3 * N * sizeof(float), c->stream));
+    for (int j = 0; j < c->nt; ++j) {
+        KTimer t(c, KK_MAP, 36.0 * N, 3.0 * N);
+        launch_map_step(c->grid, c->o.interp, a, c->z, b, c->stream);
+        CL_LAUNCHED(c);
+        std::swap(a, b);
+    }
+    {
+        KTimer t(c, KK_DETJ, 12.0 * N, 0, 2);
+        launch_detj_minmax(c->grid, a, c->partials + c->red_blocks, c->partials, c->red_blocks,
+                           c->stream);
+        launch_final_minmax(c->partials + c->red_blocks, c->partials, c->red_blocks, c->dres + 4,
+                            c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_CUDA(c, cudaMemcpyAsync(c->hres + 4, c->dres + 4, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    *lo = c->hres[4];
+    *hi = c->hres[5];
+    return CLAIRE_OK;
+}
+
+claire_status cfl_of(claire_ctx* c, const float* v, double* cfl)
+{
+    {
+        KTimer t(c, KK_REDUCE, 12.0 * c->N, 0, 2);
+        launch_maxnorm3_partial(v, c->N, c->partials, c->red_blocks, c->stream);
+        launch_final_max(c->partials, c->red_blocks, c->dres + 6, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_CUDA(c, cudaMemcpyAsync(c->hres + 6, c->dres + 6, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                               c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double hmin = std::min(c->grid.h1, std::min(c->grid.h2, c->grid.h3));
+    *cfl = std::sqrt(c->hres[7]) * c->dt / hmin;
+    return CLAIRE_OK;
+}
+
+// Matrix-free PCG for H x = -g (x0 = 0).  Returns the iteration count in *its.
+claire_status pcg(claire_ctx* c, double eta, int* its)
+{
+    const size_t n3 = 3 * c->N;
+    *its = 0;
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+        CL_CUDA(c, cudaMemsetAsync(c->x, 0, n3 * sizeof(float), c->stream));
+        CL_CUDA(c, cudaMemsetAsync(c->r, 0, n3 * sizeof(float), c->stream));
+        KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
+        launch_axpy(-1.0f, c->g, c->r, n3, c->stream);
+        CL_LAUNCHED(c);
+    }
+    double r0;
+    CL_TRY(dot(c, c->r, c->r, n3, &r0));
+    r0 = std::sqrt(r0);
+    if (r0 == 0.0) return CLAIRE_OK;
+    CL_TRY(precond(c, c->r, c->z));
+    CL_CUDA(c, cudaMemcpyAsync(c->p, c->z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+    double rz;
+    CL_TRY(dot(c, c->r, c->z, n3, &rz));
+    for (int it = 1; it <= c->o.max_pcg; ++it) {
+        *its = it;
+        CL_TRY(matvec(c, c->p, c->q));
+        double pq;
+        CL_TRY(dot(c, c->p, c->q, n3, &pq));
+        if (pq <= 0.0) {
+            if (it == 1)
+                CL_CUDA(c, cudaMemcpyAsync(c->x, c->p, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
+                                           c->stream));
+            break;
+        }
+        const double alpha = rz / pq;
+        double rr;
+        {
+            PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+            {
+                KTimer t(c, KK_VECTOR, 24.0 * n3, 0, 2);
+                launch_pcg_update(static_cast<float>(alpha), c->p, c->q, c->x, c->r, n3,
+                                  c->partials, c->red_blocks, c->stream);
+                launch_final_sum(c->partials, c->red_blocks, c->hvol, c->dres, c->stream);
+                CL_LAUNCHED(c);
+            }
+            CL_TRY(sync_scalars(c, 1));
+            rr = c->hres[0];
+        }
+        if (!std::isfinite(rr)) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG residual");
+        if (!c->o.pcg_fixed && std::sqrt(rr) <= eta * r0) break;
+        if (it == c->o.max_pcg) break;
+        CL_TRY(precond(c, c->r, c->z));
+        double rz_new;
+        CL_TRY(dot(c, c->r, c->z, n3, &rz_new));
+        const double beta = rz_new / rz;
+        rz = rz_new;
+        {
+            PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+            KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
+            launch_xpay(c->z, static_cast<float>(beta), c->p, c->p, n3, c->stream);
+            CL_LAUNCHED(c);
+        }
+    }
+    return CLAIRE_OK;
+}
+
+// Copy an input array (host or device) to a device pointer usable by kernels.
+claire_status device_input(claire_ctx* c, const float* src, size_t n, float* scratch,
+                           const float** out)
+{
+    if (!src) return fail(c, CLAIRE_EINVAL, "null array argument");
+    if (is_device_ptr(src)) {
+        *out = src;
+        return CLAIRE_OK;
+    }
+    CL_CUDA(c, cudaMemcpyAsync(scratch, src, n * sizeof(float), cudaMemcpyHostToDevice, c->stream));
+    *out = scratch;
+    return CLAIRE_OK;
+}
+
+claire_status copy_out(claire_ctx* c, float* dst, const float* src, size_t n)
+{
+    if (!dst) return fail(c, CLAIRE_EINVAL, "null output argument");
+    if (dst == src) return CLAIRE_OK;
+    CL_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(float), cudaMemcpyDefault, c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CLAIRE_OK;
+}
+
+claire_status check_kernel_ptr(claire_ctx* c, const void* p)
+{
+    if (!p) return fail(c, CLAIRE_EINVAL, "null pointer");
+    if (!is_device_ptr(p)) return fail(c, CLAIRE_EINVAL, "kernel-level entry points take device pointers");
+    return CLAIRE_OK;
+}
+
+}  // namespace
+
+// ===========================================================================
+// C ABI
+// ===========================================================================
+
+extern "C" {
+
+claire_status claire_default_opts(claire_opts* opts)
+{
+    if (!opts) return CLAIRE_EINVAL;
+    fill_defaults(opts);
+    return CLAIRE_OK;
+}
+
+claire_status claire_query_workspace(const int grid[3], int nt, const claire_opts* opts,
+                                     size_t* bytes)
+{
+    (void)opts;
+    if (!valid_grid(grid) || nt < 1 || !bytes) return CLAIRE_EINVAL;
+    const size_t N = (size_t)grid[0] * grid[1] * grid[2];
+    const size_t M = (size_t)grid[0] * grid[1] * (grid[2] / 2 + 1);
+    *bytes = layout_floats(N, M, nt, 152 * 8, nullptr) * sizeof(float);
+    return CLAIRE_OK;
+}
+
+claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, int nt,
+                            const claire_opts* opts)
+{
+    if (!out) return CLAIRE_EINVAL;
+    *out = nullptr;
+    if (!valid_grid(grid) || !(beta_v > 0) || nt < 1) return CLAIRE_EINVAL;
+    claire_opts o;
+    if (opts)
+        o = *opts;
+    else
+        fill_defaults(&o);
+    if (!valid_opts(o)) return CLAIRE_EINVAL;
+    int ndev = 0;
+    if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+        cudaGetLastError();
+        return CLAIRE_ECUDA;
+    }
+    claire_ctx* c = new (std::nothrow) claire_ctx();
+    if (!c) return CLAIRE_ENOMEM;
+    c->o = o;
+    for (int i = 0; i < 3; ++i) c->n[i] = grid[i];
+    c->N = (size_t)grid[0] * grid[1] * grid[2];
+    c->M = (size_t)grid[0] * grid[1] * (grid[2] / 2 + 1);
+    c->nt = nt;
+    c->dt = 1.0 / nt;
+    c->beta_v = beta_v;
+    const double two_pi = 6.283185307179586476925286766559;
+    Grid& g = c->grid;
+    g.n1 = grid[0];
+    g.n2 = grid[1];
+    g.n3 = grid[2];
+    g.n23 = grid[1] * grid[2];
+    g.N = static_cast<uint32_t>(c->N);
+    g.h1 = static_cast<float>(two_pi / grid[0]);
+    g.h2 = static_cast<float>(two_pi / grid[1]);
+    g.h3 = static_cast<float>(two_pi / grid[2]);
+    g.ih1 = static_cast<float>(grid[0] / two_pi);
+    g.ih2 = static_cast<float>(grid[1] / two_pi);
+    g.ih3 = static_cast<float>(grid[2] / two_pi);
+    c->hvol = (two_pi / grid[0]) * (two_pi / grid[1]) * (two_pi / grid[2]);
+    c->rp.beta_v = static_cast<float>(beta_v);
+    c->rp.beta_w = static_cast<float>(o.beta_w);
+    c->rp.reg = o.reg;
+
+    claire_status st = CLAIRE_OK;
+    auto bail = [&](claire_status s) {
+        delete c;
+        return s;
+    };
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaDeviceGetAttribute(&c->nsm, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(CLAIRE_ECUDA);
+    }
+    c->red_blocks = std::max(1, c->nsm) * 4;
+    Layout L;
+    size_t floats = layout_floats(c->N, c->M, nt, c->red_blocks, &L);
+    cudaError_t e = cudaMalloc(&c->arena, floats * sizeof(float));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        c->arena = nullptr;
+        return bail(e == cudaErrorMemoryAllocation ? CLAIRE_ENOMEM : CLAIRE_ECUDA);
+    }
+    c->arena_bytes = floats * sizeof(float);
+    float* base = static_cast<float*>(c->arena);
+    int k = 0;
+    c->m0 = base + L.off[k++];
+    c->m1 = base + L.off[k++];
+    c->v = base + L.off[k++];
+    c->dS = base + L.off[k++];
+    c->dA = base + L.off[k++];
+    c->divv = base + L.off[k++];
+    c->divXp = base + L.off[k++];
+    c->m = base + L.off[k++];
+    c->gm = base + L.off[k++];
+    c->l0 = base + L.off[k++];
+    c->l1 = base + L.off[k++];
+    c->g = base + L.off[k++];
+    c->x = base + L.off[k++];
+    c->r = base + L.off[k++];
+    c->z = base + L.off[k++];
+    c->p = base + L.off[k++];
+    c->q = base + L.off[k++];
+    c->spec = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
+    c->partials = reinterpret_cast<double*>(base + L.off[k++]);
+    c->dres = reinterpret_cast<double*>(base + L.off[k++]);
+    if (cudaMallocHost(&c->hres, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        c->hres = nullptr;
+        return bail(CLAIRE_ENOMEM);
+    }
+    int nn[3] = {grid[0], grid[1], grid[2]};
+    cufftResult fr = cufftPlanMany(&c->r2c, 3, nn, nullptr, 1, (int)c->N, nullptr, 1, (int)c->M,
+                                   CUFFT_R2C, 3);
+    if (fr == CUFFT_SUCCESS) {
+        fr = cufftPlanMany(&c->c2r, 3, nn, nullptr, 1, (int)c->M, nullptr, 1, (int)c->N, CUFFT_C2R, 3);
+        if (fr != CUFFT_SUCCESS) cufftDestroy(c->r2c);
+    }
+    if (fr != CUFFT_SUCCESS) return bail(fr == CUFFT_ALLOC_FAILED ? CLAIRE_ENOMEM : CLAIRE_ECUFFT);
+    c->plans = true;
+    st = claire_set_stream(c, nullptr);
+    if (st != CLAIRE_OK) return bail(st);
+    *out = c;
+    return CLAIRE_OK;
+}
+
+claire_status claire_destroy(claire_ctx* ctx)
+{
+    if (!ctx) return CLAIRE_OK;
+    cudaStreamSynchronize(ctx->stream);
+    cudaGetLastError();
+    delete ctx;
+    return CLAIRE_OK;
+}
+
+claire_status claire_set_stream(claire_ctx* c, void* stream)
+{
+    if (!c) return CLAIRE_EINVAL;
+    c->stream = static_cast<cudaStream_t>(stream);
+    CL_FFT(c, cufftSetStream(c->r2c, c->stream));
+    CL_FFT(c, cufftSetStream(c->c2r, c->stream));
+    return CLAIRE_OK;
+}
+
+claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
+{
+    if (!c || !m0 || !m1) return c ? fail(c, CLAIRE_EINVAL, "null image") : CLAIRE_EINVAL;
+    const size_t bytes = c->N * sizeof(float);
+    CL_CUDA(c, cudaMemcpyAsync(c->m0, m0, bytes, cudaMemcpyDefault, c->stream));
+    CL_CUDA(c, cudaMemcpyAsync(c->m1, m1, bytes, cudaMemcpyDefault, c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    c->have_images = true;
+    c->have_lin = false;
+    return CLAIRE_OK;
+}
+
+claire_status claire_objective(claire_ctx* c, const float* v, double* J, double* mismatch)
+{
+    if (!c) return CLAIRE_EINVAL;
+    const float* dv;
+    CL_TRY(device_input(c, v, 3 * c->N, c->p, &dv));
+    claire_status s = objective_at(c, dv, J, mismatch);
+    collect_timing(c);
+    return s;
+}
+
+claire_status claire_gradient(claire_ctx* c, const float* v, float* g, double* J)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!v || !g) return fail(c, CLAIRE_EINVAL, "null argument");
+    if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
+    const float* dv;
+    CL_TRY(device_input(c, v, 3 * c->N, c->v, &dv));
+    CL_TRY(linearise(c, dv));
+    CL_TRY(gradient_at_lin(c, c->g));
+    if (J) *J = c->J_lin;
+    CL_TRY(copy_out(c, g, c->g, 3 * c->N));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!vt || !Hvt) return fail(c, CLAIRE_EINVAL, "null argument");
+    const float* dvt;
+    CL_TRY(device_input(c, vt, 3 * c->N, c->p, &dvt));
+    CL_TRY(matvec(c, dvt, c->q));
+    CL_TRY(copy_out(c, Hvt, c->q, 3 * c->N));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_precond(claire_ctx* c, const float* r, float* z)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!r || !z) return fail(c, CLAIRE_EINVAL, "null argument");
+    const float* dr;
+    CL_TRY(device_input(c, r, 3 * c->N, c->p, &dr));
+    CL_TRY(precond(c, dr, c->q));
+    CL_TRY(copy_out(c, z, c->q, 3 * c->N));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!v_inout) return fail(c, CLAIRE_EINVAL, "null v_inout");
+    if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
+    const auto t0 = std::chrono::steady_clock::now();
+    const size_t N = c->N, n3 = 3 * N;
+    claire_report R;
+    std::memset(&R, 0, sizeof(R));
+    collect_timing(c);
+    KernelStat ks0[KK_COUNT];
+    for (int k = 0; k < KK_COUNT; ++k) ks0[k] = c->ks[k];
+    double ph0[8];
+    for (int i = 0; i < 8; ++i) ph0[i] = c->phase_s[i];
+
+    CL_CUDA(c, cudaMemcpyAsync(c->v, v_inout, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    claire_status st = CLAIRE_ENOTCONVERGED;
+    auto elapsed = [&]() {
+        return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+    };
+    CL_TRY(linearise(c, c->v));
+    CL_TRY(gradient_at_lin(c, c->g));
+    double gn;
+    CL_TRY(dot(c, c->g, c->g, n3, &gn));
+    const double g0 = std::sqrt(gn);
+    double rel = 1.0;
+    if (g0 == 0.0) st = CLAIRE_OK;
+    for (int k = 0; st == CLAIRE_ENOTCONVERGED && k < c->o.max_gn; ++k) {
+        CL_TRY(dot(c, c->g, c->g, n3, &gn));
+        rel = std::sqrt(gn) / g0;
+        if (rel <= c->o.gtol) {
+            st = CLAIRE_OK;
+            break;
+        }
+        if (c->o.wall_limit_s > 0 && elapsed() > c->o.wall_limit_s) {
+            st = CLAIRE_ETIMEOUT;
+            break;
+        }
+        const double eta = std::min(c->o.pcg_rtol_max, std::sqrt(rel));
+        int its = 0;
+        CL_TRY(pcg(c, eta, &its));
+        if (k < CLAIRE_MAX_LOGGED_STEPS) R.pcg_iters[k] = its;
+        R.pcg_iters_total += its;
+        double gtx;
+        CL_TRY(dot(c, c->g, c->x, n3, &gtx));
+        double alpha = 1.0;
+        bool ok = false;
+        for (int ls = 0; ls < c->o.max_ls; ++ls) {
+            {
+                PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+                KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
+                launch_xpay(c->v, static_cast<float>(alpha), c->x, c->p, n3, c->stream);
+                CL_LAUNCHED(c);
+            }
+            double Jt;
+            CL_TRY(objective_at(c, c->p, &Jt, nullptr));
+            if (Jt <= c->J_lin + c->o.armijo_c1 * alpha * gtx) {
+                ok = true;
+                break;
+            }
+            alpha *= 0.5;
+        }
+        if (!ok) {
+            st = CLAIRE_ELINESEARCH;
+            break;
+        }
+        if (k < CLAIRE_MAX_LOGGED_STEPS) R.alpha[k] = alpha;
+        {
+            PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+            KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
+            launch_axpy(static_cast<float>(alpha), c->x, c->v, n3, c->stream);
+            CL_LAUNCHED(c);
+        }
+        R.gn_iters = k + 1;
+        CL_TRY(linearise(c, c->v));
+        CL_TRY(gradient_at_lin(c, c->g));
+        CL_TRY(dot(c, c->g, c->g, n3, &gn));
+        rel = std::sqrt(gn) / g0;
+        if (rel <= c->o.gtol) st = CLAIRE_OK;
+    }
+    R.gnorm_rel = rel;
+    R.J = c->J_lin;
+    R.mismatch = c->mis_lin;
+    {
+        double den;
+        {
+            KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
+            launch_sqdiff_partial(c->m0, c->m1, N, c->partials, c->red_blocks, c->stream);
+            launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 2, c->stream);
+            CL_LAUNCHED(c);
+        }
+        CL_CUDA(c, cudaMemcpyAsync(c->hres + 2, c->dres + 2, sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        CL_CUDA(c, cudaStreamSynchronize(c->stream));
+        den = c->hres[2];
+        R.r = den > 0 ? c->mis_lin / den : 0.0;
+    }
+    CL_TRY(detj_of(c, c->v, &R.detj_min, &R.detj_max));
+    CL_TRY(cfl_of(c, c->v, &R.cfl));
+    CL_CUDA(c, cudaMemcpyAsync(v_inout, c->v, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    R.status = st;
+    R.t_total_s = elapsed();
+    for (int i = 0; i < 8; ++i) R.t_phase_s[i] = c->phase_s[i] - ph0[i];
+    const int gk[] = {KK_INTERP, KK_BACKTRACE, KK_ADJ_STEP, KK_INC_STEP, KK_INC_LAST, KK_MAP};
+    for (int k : gk) {
+        R.gather_launches += c->ks[k].launches - ks0[k].launches;
+        R.interp_points += c->ks[k].points - ks0[k].points;
+        R.interp_bytes += c->ks[k].bytes - ks0[k].bytes;
+    }
+    if (rep) *rep = R;
+    if (st == CLAIRE_ELINESEARCH) return fail(c, st, "Armijo line search failed");
+    if (st == CLAIRE_ETIMEOUT) return fail(c, st, "wall-clock limit reached");
+    return st;
+}
+
+claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in, float* m_out,
+                               int flags)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!v || !m_in || !m_out) return fail(c, CLAIRE_EINVAL, "null argument");
+    if (flags != CLAIRE_TRANSPORT_FWD && flags != CLAIRE_TRANSPORT_ADJ)
+        return fail(c, CLAIRE_EINVAL, "unknown transport flags %d", flags);
+    const size_t N = c->N;
+    const float* dv;
+    CL_TRY(device_input(c, v, 3 * N, c->p, &dv));
+    const float* src;
+    CL_TRY(device_input(c, m_in, N, c->l0, &src));
+    float* a = c->l1;
+    float* b = c->l0;
+    if (flags == CLAIRE_TRANSPORT_FWD) {
+        CL_TRY(backtrace(c, dv, c->z, +1));
+        for (int j = 0; j < c->nt; ++j) {
+            CL_TRY(interp(c, src, c->z, a));
+            src = a;
+            std::swap(a, b);
+        }
+    } else {
+        float* divv = c->r;
+        float* divXp = c->r + N;
+        CL_TRY(characteristics(c, dv, nullptr, c->z, divv, divXp));
+        for (int j = 0; j < c->nt; ++j) {
+            KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
+            launch_adj_step(c->grid, c->o.interp, src, c->z, divv, divXp, static_cast<float>(c->dt), 0.0f,
+                            nullptr, a, nullptr, c->stream);
+            CL_LAUNCHED(c);
+            src = a;
+            std::swap(a, b);
+        }
+    }
+    CL_TRY(copy_out(c, m_out, src, N));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!v || !lo || !hi) return fail(c, CLAIRE_EINVAL, "null argument");
+    const float* dv;
+    CL_TRY(device_input(c, v, 3 * c->N, c->q, &dv));
+    CL_TRY(detj_of(c, dv, lo, hi));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_interp(claire_ctx* c, const float* f, const float* d, float* out, int order)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (order != 1 && order != 3) return fail(c, CLAIRE_EINVAL, "order must be 1 or 3");
+    CL_TRY(check_kernel_ptr(c, f));
+    CL_TRY(check_kernel_ptr(c, d));
+    CL_TRY(check_kernel_ptr(c, out));
+    {
+        KTimer t(c, KK_INTERP, 20.0 * c->N, 1.0 * c->N);
+        launch_interp(c->grid, order, f, d, out, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_backtrace(claire_ctx* c, const float* v, float* d, int direction)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (direction != 1 && direction != -1) return fail(c, CLAIRE_EINVAL, "direction must be +1 or -1");
+    CL_TRY(check_kernel_ptr(c, v));
+    CL_TRY(check_kernel_ptr(c, d));
+    CL_TRY(backtrace(c, v, d, direction));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_fd8_grad(claire_ctx* c, const float* f, float* g)
+{
+    if (!c) return CLAIRE_EINVAL;
+    CL_TRY(check_kernel_ptr(c, f));
+    CL_TRY(check_kernel_ptr(c, g));
+    CL_TRY(fd8_grad(c, f, g));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CLAIRE_OK;
+}
+
+claire_status claire_fd8_div(claire_ctx* c, const float* v, float* dv)
+{
+    if (!c) return CLAIRE_EINVAL;
+    CL_TRY(check_kernel_ptr(c, v));
+    CL_TRY(check_kernel_ptr(c, dv));
+    {
+        KTimer t(c, KK_FD8, 16.0 * c->N, 0);
+        launch_fd8_div(c->grid, v, dv, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    return CLAIRE_OK;
+}
+
+claire_status claire_spectral(claire_ctx* c, const float* in, float* out, int op)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (op < CLAIRE_SPECTRAL_REG || op > CLAIRE_SPECTRAL_K) return fail(c, CLAIRE_EINVAL, "bad op");
+    CL_TRY(check_kernel_ptr(c, in));
+    CL_TRY(check_kernel_ptr(c, out));
+    CL_TRY(spectral(c, in, out, static_cast<SpectralOp>(op)));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_dot(claire_ctx* c, const float* x, const float* y, size_t n, double* out)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!out) return fail(c, CLAIRE_EINVAL, "null output");
+    if (n == 0) {
+        *out = 0.0;
+        return CLAIRE_OK;
+    }
+    CL_TRY(check_kernel_ptr(c, x));
+    CL_TRY(check_kernel_ptr(c, y));
+    CL_TRY(dot(c, x, y, n, out));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_kernel_stats(claire_ctx* c, claire_kernel_stat* out, int capacity, int* count,
+                                  int reset)
+{
+    if (!c || capacity < 0 || (capacity > 0 && !out)) return CLAIRE_EINVAL;
+    collect_timing(c);
+    int n = 0;
+    for (int k = 0; k < KK_COUNT && n < capacity; ++k, ++n) {
+        std::memset(out[n].name, 0, sizeof(out[n].name));
+        std::strncpy(out[n].name, kKernelNames[k], sizeof(out[n].name) - 1);
+        out[n].launches = c->ks[k].launches;
+        out[n].seconds = c->ks[k].seconds;
+        out[n].bytes = c->ks[k].bytes;
+        out[n].points = c->ks[k].points;
+    }
+    if (count) *count = KK_COUNT;
+    if (reset) {
+        for (int k = 0; k < KK_COUNT; ++k) c->ks[k] = KernelStat();
+        std::fill(c->phase_s, c->phase_s + 8, 0.0);
+    }
+    return CLAIRE_OK;
+}
+
+claire_status claire_set_timing(claire_ctx* c, int on)
+{
+    if (!c) return CLAIRE_EINVAL;
+    collect_timing(c);
+    c->o.timing = on ? 1 : 0;
+    return CLAIRE_OK;
+}
+
+const char* claire_last_error(const claire_ctx* c)
+{
+    if (!c) return "null context";
+    return c->err.c_str();
+}
+
+}  // extern "C"

@@ -1,0 +1,132 @@
+// Internal declarations of libclaire: kernel launchers (one per kernel) and
+// block-level reduction helpers.  Not part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cufft.h>
+
+#include <cstddef>
+#include <cstdint>
+
+#include "common.cuh"
+
+namespace claire {
+
+// ---- block reductions (256-thread blocks, fixed order: deterministic) ----
+#ifdef __CUDACC__
+__device__ __forceinline__ double warp_sum(double x)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) x += __shfl_down_sync(0xffffffffu, x, o);
+    return x;
+}
+
+// Sum of x over the block written to out[blockIdx.x] by thread 0.
+__device__ __forceinline__ void block_sum(double x, double* out)
+{
+    __shared__ double sh[32];
+    x = warp_sum(x);
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) sh[wid] = x;
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double y = lane < nw ? sh[lane] : 0.0;
+        y = warp_sum(y);
+        if (lane == 0) out[blockIdx.x] = y;
+    }
+}
+
+__device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin, double* pmax)
+{
+    __shared__ double slo[32], shi[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        slo[wid] = lo;
+        shi[wid] = hi;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double a = lane < nw ? slo[lane] : 1e300;
+        double b = lane < nw ? shi[lane] : -1e300;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            a = fmin(a, __shfl_down_sync(0xffffffffu, a, o));
+            b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+        }
+        if (lane == 0) {
+            pmin[blockIdx.x] = a;
+            pmax[blockIdx.x] = b;
+        }
+    }
+}
+#endif
+
+// ---- semi-Lagrangian and FD kernels (sl_kernels.cu) ----
+void launch_interp(const Grid& g, int order, const float* f, const float* d, float* out,
+                   cudaStream_t st);
+void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
+                      cudaStream_t st);
+void launch_adj_init(const Grid& g, const float* a, const float* s, float w, const float* gm,
+                     int accumulate, float* lam, float* b, cudaStream_t st);
+void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
+                     const float* divv, const float* divXp, float dt, float w, const float* gm,
+                     float* lam, float* b, cudaStream_t st);
+void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef, float* q,
+                     cudaStream_t st);
+void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
+                     const float* gm, float coef, float* q, cudaStream_t st);
+void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
+                     const float* gm, float coef, float w, int accumulate, float* lam, float* b,
+                     cudaStream_t st);
+void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
+                     cudaStream_t st);
+void launch_fd8_grad(const Grid& g, const float* f, float* out, cudaStream_t st);
+void launch_fd8_div(const Grid& g, const float* v, float* out, cudaStream_t st);
+void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,
+                        cudaStream_t st);
+
+// ---- spectral scaling, vector ops and reductions (vec_kernels.cu) ----
+enum SpectralOp { SPEC_REG = 0, SPEC_INV = 1, SPEC_K = 2, SPEC_AINV = 3 };
+
+struct RegParams {
+    float beta_v, beta_w;
+    int reg;  // 1 = H1 seminorm, 2 = H2 seminorm
+};
+
+// In-place scaling of the three half-spectra xh[c], c = 0..2 (each
+// n1 * n2 * (n3/2+1) complex values, stride cstride) by the 3x3 symbol of op,
+// times scale (the 1/N of the unnormalised inverse transform).
+void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op,
+                     RegParams rp, float scale, cudaStream_t st);
+
+// Deterministic FP64 reductions: partial sums per block, then a one-block
+// final sum in fixed order.  `partials` holds at least nblocks doubles.
+void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,
+                        cudaStream_t st);
+void launch_sqdiff_partial(const float* a, const float* b, size_t n, double* partials, int nblocks,
+                           cudaStream_t st);
+void launch_maxnorm3_partial(const float* v, size_t N, double* partials, int nblocks,
+                             cudaStream_t st);
+void launch_final_sum(const double* partials, int nblocks, double scale, double* out,
+                      cudaStream_t st);
+void launch_final_max(const double* partials, int nblocks, double* out, cudaStream_t st);
+void launch_final_minmax(const double* pmin, const double* pmax, int nblocks, double* out2,
+                         cudaStream_t st);
+
+// y = a x + y
+void launch_axpy(float a, const float* x, float* y, size_t n, cudaStream_t st);
+// z = x + a y
+void launch_xpay(const float* x, float a, const float* y, float* z, size_t n, cudaStream_t st);
+// x += alpha p; r -= alpha q; partial sums of r . r
+void launch_pcg_update(float alpha, const float* p, const float* q, float* x, float* r, size_t n,
+                       double* partials, int nblocks, cudaStream_t st);
+void launch_fill(float* x, float value, size_t n, cudaStream_t st);
+
+}  // namespace claire

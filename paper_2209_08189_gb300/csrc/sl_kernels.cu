@@ -1,0 +1,361 @@
+// Semi-Lagrangian kernels of libclaire (sm_103a): RK2 backtrace, off-grid
+// gathers with the fused source terms of the state, adjoint and incremental
+// solves, 8th-order finite differences, deformation-map transport and the
+// Jacobian determinant.  Method: "CLAIRE at scale" (arXiv 2209.08189),
+// Sec. 2.2 (SL with RK2, FD8) and Sec. 3 (IP and FD kernels).
+#include "internal.h"
+
+namespace claire {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
+
+// ---------------------------------------------------------------------------
+// gathers
+// ---------------------------------------------------------------------------
+
+// out[p] = f(x_p + d_p)
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_interp(Grid g, const float* __restrict__ f,
+                                                      const float* __restrict__ d,
+                                                      float* __restrict__ out)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, __ldg(d + p), __ldg(d + g.N + p), __ldg(d + 2 * (size_t)g.N + p));
+    out[p] = s.eval(f);
+}
+
+// Heun characteristic: sign = +1 gives X = x - dt/2 [v(x) + v(x - dt v(x))],
+// sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))].  d in grid units.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __restrict__ v, float dt,
+                                                         float sign, float* __restrict__ d)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    const float u1 = __ldg(v + p) * g.ih1;
+    const float u2 = __ldg(v + N + p) * g.ih2;
+    const float u3 = __ldg(v + 2 * N + p) * g.ih3;
+    const float sdt = sign * dt;
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, -sdt * u1, -sdt * u2, -sdt * u3);
+    float vs[3];
+    s.eval3(v, g.N, vs);
+    const float c = -0.5f * sdt;
+    d[p] = c * (u1 + vs[0] * g.ih1);
+    d[N + p] = c * (u2 + vs[1] * g.ih2);
+    d[2 * N + p] = c * (u3 + vs[2] * g.ih3);
+}
+
+// Start of the backward solve at t = 1: lambda = a - s (s may be null),
+// b = (accumulate ? b : 0) + w lambda grad m.
+__global__ void __launch_bounds__(kThreads) k_adj_init(Grid g, const float* __restrict__ a,
+                                                        const float* __restrict__ s, float w,
+                                                        const float* __restrict__ gm, int accumulate,
+                                                        float* __restrict__ lam, float* __restrict__ b)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    const size_t N = g.N;
+    const float l = s ? a[p] - s[p] : a[p];
+    lam[p] = l;
+    const float wl = w * l;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float b0 = accumulate ? b[c * N + p] : 0.0f;
+        b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b0);
+    }
+}
+
+// One SL step of the adjoint equation (Eq. (4)) backwards in time:
+//   a = lambda^{j+1}(X+), lambda^j = a + dt/2 [a d(X+) + (a + dt a d(X+)) d(x)],
+// fused with the gradient body b += w_j lambda^j grad m^j (gm may be null).
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_adj_step(Grid g, const float* __restrict__ lam_next,
+                                                        const float* __restrict__ dA,
+                                                        const float* __restrict__ divv,
+                                                        const float* __restrict__ divXp, float dt,
+                                                        float w, const float* __restrict__ gm,
+                                                        float* __restrict__ lam,
+                                                        float* __restrict__ b)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, __ldg(dA + p), __ldg(dA + N + p), __ldg(dA + 2 * N + p));
+    const float a = s.eval(lam_next);
+    const float dX = __ldg(divXp + p);
+    const float dx = __ldg(divv + p);
+    const float adX = a * dX;
+    const float pred = fmaf(dt, adX, a);
+    const float l = fmaf(0.5f * dt, fmaf(pred, dx, adX), a);
+    lam[p] = l;
+    if (gm) {
+        const float wl = w * l;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b[c * N + p]);
+    }
+}
+
+// Incremental state source f = -vt . grad m.
+__device__ __forceinline__ float inc_source(const float* __restrict__ vt, const float* __restrict__ gm,
+                                            uint32_t p, size_t N)
+{
+    return -(__ldg(vt + p) * __ldg(gm + p) + __ldg(vt + N + p) * __ldg(gm + N + p) +
+             __ldg(vt + 2 * N + p) * __ldg(gm + 2 * N + p));
+}
+
+// q^0 = coef * f^0
+__global__ void __launch_bounds__(kThreads) k_inc_init(Grid g, const float* __restrict__ vt,
+                                                        const float* __restrict__ gm, float coef,
+                                                        float* __restrict__ q)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    q[p] = coef * inc_source(vt, gm, p, g.N);
+}
+
+// q^{j+1} = q^j(X) + coef f^{j+1}   (coef = dt: the Heun halves of two steps)
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_inc_step(Grid g, const float* __restrict__ q_prev,
+                                                        const float* __restrict__ d,
+                                                        const float* __restrict__ vt,
+                                                        const float* __restrict__ gm, float coef,
+                                                        float* __restrict__ q)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, __ldg(d + p), __ldg(d + N + p), __ldg(d + 2 * N + p));
+    q[p] = fmaf(coef, inc_source(vt, gm, p, N), s.eval(q_prev));
+}
+
+// Last incremental state step fused with the start of the incremental
+// adjoint: mt = q(X) + dt/2 f^{nt}, lt = -mt, b = (accumulate ? b : 0) + w lt grad m^{nt}.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_inc_last(Grid g, const float* __restrict__ q_prev,
+                                                        const float* __restrict__ d,
+                                                        const float* __restrict__ vt,
+                                                        const float* __restrict__ gm, float coef,
+                                                        float w, int accumulate,
+                                                        float* __restrict__ lam,
+                                                        float* __restrict__ b)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, __ldg(d + p), __ldg(d + N + p), __ldg(d + 2 * N + p));
+    const float mt = fmaf(coef, inc_source(vt, gm, p, N), s.eval(q_prev));
+    const float l = -mt;
+    lam[p] = l;
+    const float wl = w * l;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float b0 = accumulate ? b[c * N + p] : 0.0f;
+        b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b0);
+    }
+}
+
+// Deformation map step: u^{j+1} = u^j(X) + (X - x), three components.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_map_step(Grid g, const float* __restrict__ u_prev,
+                                                        const float* __restrict__ d,
+                                                        float* __restrict__ u)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    const float d1 = __ldg(d + p), d2 = __ldg(d + N + p), d3 = __ldg(d + 2 * N + p);
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, d1, d2, d3);
+    float r[3];
+    s.eval3(u_prev, g.N, r);
+    u[p] = fmaf(d1, g.h1, r[0]);
+    u[N + p] = fmaf(d2, g.h2, r[1]);
+    u[2 * N + p] = fmaf(d3, g.h3, r[2]);
+}
+
+// ---------------------------------------------------------------------------
+// 8th-order central finite differences
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ float fd8_axis(const float* __restrict__ f, uint32_t p, int idx, int n,
+                                          int stride)
+{
+    // c_s = 4/5, -1/5, 4/105, -1/280 for s = 1..4 (standard 8th-order stencil)
+    const float c1 = 0.8f, c2 = -0.2f, c3 = 0.0380952380952381f, c4 = -0.003571428571428571f;
+    float acc = 0.0f;
+    const float cs[4] = {c1, c2, c3, c4};
+    const long base = static_cast<long>(p) - static_cast<long>(idx) * stride;
+#pragma unroll
+    for (int s = 1; s <= 4; ++s) {
+        int ip = idx + s;
+        ip = ip >= n ? ip - n : ip;
+        int im = idx - s;
+        im = im < 0 ? im + n : im;
+        acc = fmaf(cs[s - 1], __ldg(f + base + static_cast<long>(ip) * stride) -
+                                  __ldg(f + base + static_cast<long>(im) * stride),
+                   acc);
+    }
+    return acc;
+}
+
+__global__ void __launch_bounds__(kThreads) k_fd8_grad(Grid g, const float* __restrict__ f,
+                                                        float* __restrict__ out)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    out[p] = fd8_axis(f, p, i, g.n1, g.n23) * g.ih1;
+    out[N + p] = fd8_axis(f, p, j, g.n2, g.n3) * g.ih2;
+    out[2 * N + p] = fd8_axis(f, p, k, g.n3, 1) * g.ih3;
+}
+
+__global__ void __launch_bounds__(kThreads) k_fd8_div(Grid g, const float* __restrict__ v,
+                                                       float* __restrict__ out)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    out[p] = fd8_axis(v, p, i, g.n1, g.n23) * g.ih1 + fd8_axis(v + N, p, j, g.n2, g.n3) * g.ih2 +
+             fd8_axis(v + 2 * N, p, k, g.n3, 1) * g.ih3;
+}
+
+// det(I + grad u) in FP64 with block-wise min / max partials.
+__global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* __restrict__ u,
+                                                           double* __restrict__ pmin,
+                                                           double* __restrict__ pmax)
+{
+    double lo = 1e300, hi = -1e300;
+    const size_t N = g.N;
+    for (uint32_t p = blockIdx.x * kThreads + threadIdx.x; p < g.N; p += gridDim.x * kThreads) {
+        int i, j, k;
+        coords_of(g, p, i, j, k);
+        double F[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float* uc = u + c * N;
+            F[c][0] = fd8_axis(uc, p, i, g.n1, g.n23) * g.ih1;
+            F[c][1] = fd8_axis(uc, p, j, g.n2, g.n3) * g.ih2;
+            F[c][2] = fd8_axis(uc, p, k, g.n3, 1) * g.ih3;
+            F[c][c] += 1.0;
+        }
+        const double det = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
+                           F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
+                           F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
+        lo = fmin(lo, det);
+        hi = fmax(hi, det);
+        if (det != det) {  // NaN propagates as NaN in both
+            lo = det;
+            hi = det;
+        }
+    }
+    block_minmax(lo, hi, pmin, pmax);
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------
+// launchers
+// ---------------------------------------------------------------------------
+
+#define CLAIRE_DISPATCH(order, KERNEL, ...)                                       \
+    do {                                                                          \
+        if ((order) == 3)                                                         \
+            KERNEL<3><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
+        else                                                                      \
+            KERNEL<1><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
+    } while (0)
+
+void launch_interp(const Grid& g, int order, const float* f, const float* d, float* out,
+                   cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_interp, g, f, d, out);
+}
+
+void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
+                      cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_backtrace, g, v, dt, static_cast<float>(sign), d);
+}
+
+void launch_adj_init(const Grid& g, const float* a, const float* s, float w, const float* gm,
+                     int accumulate, float* lam, float* b, cudaStream_t st)
+{
+    k_adj_init<<<blocks_for(g.N), kThreads, 0, st>>>(g, a, s, w, gm, accumulate, lam, b);
+}
+
+void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
+                     const float* divv, const float* divXp, float dt, float w, const float* gm,
+                     float* lam, float* b, cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_adj_step, g, lam_next, dA, divv, divXp, dt, w, gm, lam, b);
+}
+
+void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef, float* q,
+                     cudaStream_t st)
+{
+    k_inc_init<<<blocks_for(g.N), kThreads, 0, st>>>(g, vt, gm, coef, q);
+}
+
+void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
+                     const float* gm, float coef, float* q, cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_inc_step, g, q_prev, d, vt, gm, coef, q);
+}
+
+void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
+                     const float* gm, float coef, float w, int accumulate, float* lam, float* b,
+                     cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_inc_last, g, q_prev, d, vt, gm, coef, w, accumulate, lam, b);
+}
+
+void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
+                     cudaStream_t st)
+{
+    CLAIRE_DISPATCH(order, k_map_step, g, u_prev, d, u);
+}
+
+void launch_fd8_grad(const Grid& g, const float* f, float* out, cudaStream_t st)
+{
+    k_fd8_grad<<<blocks_for(g.N), kThreads, 0, st>>>(g, f, out);
+}
+
+void launch_fd8_div(const Grid& g, const float* v, float* out, cudaStream_t st)
+{
+    k_fd8_div<<<blocks_for(g.N), kThreads, 0, st>>>(g, v, out);
+}
+
+void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,
+                        cudaStream_t st)
+{
+    k_detj_minmax<<<nblocks, kThreads, 0, st>>>(g, u, pmin, pmax);
+}
+
+}  // namespace claire

@@ -103,7 +103,7 @@ def bandlimited_velocity(n, seed=0, kmax=8, vmax=1.0):
         spec = np.zeros((n0, n1, n2 // 2 + 1), dtype=np.complex128)
         cnt = idx[0].size
         spec[idx] = (rng.standard_normal(cnt) + 1j * rng.standard_normal(cnt)) / np.sqrt(1.0 + kk[idx])
-        v[c] = np.fft.irfftn(spec, s=(n0, n1, n2))
+        v[c] = np.fft.irfftn(spec, s=(n0, n1, n2), axes=(0, 1, 2))
     return _scale_to_max(v, vmax)
 
 

@@ -1,0 +1,90 @@
+"""Host-side checks of the C ABI that need no GPU: the library builds, loads,
+exports every entry point include/claire.h declares, and its host logic
+(option defaults, workspace sizing, argument validation) behaves."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import __graft_entry__ as entry
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def claire():
+    entry.build()
+    from paper_2209_08189_gb300 import claire as c
+    return c
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "claire.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(claire_[a-z0-9_]+)\s*\(", src)))
+
+
+def test_every_declared_symbol_is_exported(claire):
+    lib = claire.lib()
+    declared = _declared()
+    assert len(declared) >= 20
+    for name in declared:
+        assert hasattr(lib, name), name
+    # the binding wraps exactly the declared entry points
+    assert set(claire.exported_symbols()) == set(declared)
+
+
+def test_default_opts(claire):
+    o = claire.claire_default_opts()
+    assert o.interp == 3 and o.reg == 1 and abs(o.beta_w - 1e-4) < 1e-18
+    assert abs(o.gtol - 5e-2) < 1e-18 and o.grad_form == 0 and o.timing == 0
+
+
+def test_query_workspace_scales_with_grid_and_nt(claire):
+    b64 = claire.claire_query_workspace((64, 64, 64), 4)
+    b128 = claire.claire_query_workspace((128, 128, 128), 4)
+    assert 7.5 < b128 / b64 < 8.5
+    assert claire.claire_query_workspace((64, 64, 64), 8) > b64
+    # roughly (43 + 4 (nt+1)) float fields per point
+    assert 50 * 4 * 64 ** 3 < b64 < 70 * 4 * 64 ** 3
+
+
+@pytest.mark.parametrize("grid", [(7, 8, 8), (8, 8, 9), (6, 8, 8), (0, 8, 8)])
+def test_invalid_grids_rejected(claire, grid):
+    with pytest.raises(claire.ClaireError) as e:
+        claire.claire_query_workspace(grid, 4)
+    assert e.value.status == -1
+    with pytest.raises(claire.ClaireError) as e:
+        claire.claire_create(grid, 1e-2, 4)
+    assert e.value.status == -1
+
+
+def test_invalid_parameters_rejected(claire):
+    for beta, nt in ((0.0, 4), (-1.0, 4), (1e-2, 0)):
+        with pytest.raises(claire.ClaireError) as e:
+            claire.claire_create((8, 8, 8), beta, nt)
+        assert e.value.status == -1
+    o = claire.claire_default_opts()
+    o.interp = 2
+    with pytest.raises(claire.ClaireError) as e:
+        claire.claire_create((8, 8, 8), 1e-2, 4, o)
+    assert e.value.status == -1
+
+
+def test_null_context_calls_fail_cleanly(claire):
+    lib = claire.lib()
+    assert lib.claire_destroy(None) == 0
+    assert lib.claire_set_images(None, None, None) == -1
+    assert lib.claire_register(None, None, None) == -1
+    assert lib.claire_last_error(None) == b"null context"
+
+
+@pytest.mark.skipif(bool(os.environ.get("CUDA_VISIBLE_DEVICES_FORCE")), reason="gpu forced")
+def test_create_fails_loudly_without_gpu(claire):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    with pytest.raises(claire.ClaireError) as e:
+        claire.claire_create((8, 8, 8), 1e-2, 4)
+    assert e.value.status == -3

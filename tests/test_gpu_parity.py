@@ -1,0 +1,399 @@
+"""GPU parity: every entry point of the C ABI against the FP64 oracle on the
+same seeded FP32 inputs (the oracle reads the FP32 bits upcast to FP64).
+
+Tolerances (CUDA path computes in FP32, reductions in FP64):
+  * interpolation: relative L-infinity 1e-5 (stated requirement);
+  * transported image: relative L2 2e-4 (stated requirement);
+  * backtrace, FD8, spectral operators, single SL steps: 1e-5 relative — each
+    output is a short FP32 sum (<= 64 terms, |weights| summing to <= 2), so
+    the rounding error is a few units of 6e-8 times the largest term;
+  * gradient and Hessian matvec: relative L2 1e-4 — 2 nt SL steps of 1e-6
+    relative rounding each, amplified by the cancellation in m1 - m(1)
+    (|m| / |m - m1| <= 10 on these inputs);
+  * registration: final velocity relative L2 1e-3 and final relative
+    mismatch within 1 % of the oracle (stated requirements).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import __graft_entry__ as entry
+import oracle
+from paper_2209_08189_gb300 import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    entry.build()
+    from paper_2209_08189_gb300 import claire
+    return torch, claire
+
+
+def f32(a):
+    return np.ascontiguousarray(a, dtype=np.float32)
+
+
+def dev(torch, a):
+    return torch.from_numpy(f32(a)).cuda()
+
+
+def host(t):
+    return t.detach().cpu().numpy().astype(np.float64)
+
+
+def rel_l2(a, b):
+    return float(np.linalg.norm((a - b).ravel()) / max(np.linalg.norm(b.ravel()), 1e-300))
+
+
+def rel_linf(a, b):
+    return float(np.max(np.abs(a - b)) / max(np.max(np.abs(b)), 1e-300))
+
+
+def make_ctx(claire, torch, n, beta_v=1e-2, nt=4, **opts):
+    return claire.Context(n, beta_v, nt, stream=torch.cuda.current_stream().cuda_stream, **opts)
+
+
+SHAPES = [(32, 32, 32), (40, 36, 30), (16, 24, 8)]  # (40,36,30): N = 43200, ragged last block
+
+
+def _disp(n, seed, cfl):
+    """Smooth displacement (grid units) with max about cfl cells, plus a wrap-crossing offset."""
+    v = synth.mode_velocity(n, seed=seed, kmax=3, vmax=1.0)
+    h = oracle.spacing(n)
+    d = np.stack([v[c] / h[c] * cfl * h.min() for c in range(3)])
+    return d
+
+
+# ---------------------------------------------------------------------------
+# kernels
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("cfl", [0.4, 6.0])
+def test_interp_parity(env, n, order, cfl):
+    torch, claire = env
+    f = f32(synth.blob_template(n, seed=1))
+    d = f32(_disp(n, 2, cfl))
+    ctx = make_ctx(claire, torch, n)
+    out = torch.empty(n, device="cuda")
+    ctx.interp(dev(torch, f), dev(torch, d), out, order)
+    torch.cuda.synchronize()
+    ref = oracle.interp(f.astype(np.float64), d.astype(np.float64), order)
+    assert rel_linf(host(out), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("order", [3, 1])
+def test_interp_integer_shift_bit_exact(env, order):
+    torch, claire = env
+    n = (16, 12, 20)
+    rng = np.random.default_rng(0)
+    f = f32(rng.standard_normal(n))
+    d = np.zeros((3,) + n, np.float32)
+    d[0] = 5; d[1] = -13; d[2] = 21
+    ctx = make_ctx(claire, torch, n)
+    out = torch.empty(n, device="cuda")
+    ctx.interp(dev(torch, f), dev(torch, d), out, order)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), np.roll(f, (-5, 13, -21), axis=(0, 1, 2)))
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("direction", [1, -1])
+def test_backtrace_parity(env, n, direction):
+    torch, claire = env
+    v = f32(synth.mode_velocity(n, seed=4, vmax=1.0))
+    for order in (3, 1):
+        ctx = make_ctx(claire, torch, n, nt=4, interp=order)
+        d = torch.empty((3,) + n, device="cuda")
+        ctx.backtrace(dev(torch, v), d, direction)
+        torch.cuda.synchronize()
+        ref = oracle.backtrace(v.astype(np.float64), 0.25, direction, order)
+        assert rel_linf(host(d), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("n", SHAPES)
+def test_fd8_parity(env, n):
+    torch, claire = env
+    f = f32(synth.blob_template(n, seed=5))
+    v = f32(synth.mode_velocity(n, seed=6, vmax=1.0))
+    ctx = make_ctx(claire, torch, n)
+    g = torch.empty((3,) + n, device="cuda")
+    dv = torch.empty(n, device="cuda")
+    ctx.fd8_grad(dev(torch, f), g)
+    ctx.fd8_div(dev(torch, v), dv)
+    torch.cuda.synchronize()
+    assert rel_linf(host(g), oracle.fd8_grad(f.astype(np.float64))) <= 1e-5
+    assert rel_linf(host(dv), oracle.fd8_div(v.astype(np.float64))) <= 1e-5
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("reg", [1, 2])
+def test_spectral_parity(env, n, reg):
+    torch, claire = env
+    rng = np.random.default_rng(7)
+    x = f32(rng.standard_normal((3,) + n))
+    p = oracle.Params(beta_v=3e-2, beta_w=2e-3, reg=reg)
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, beta_w=p.beta_w, reg=reg)
+    xd = dev(torch, x)
+    x64 = x.astype(np.float64)
+    for op, ref in ((claire.SPECTRAL_REG, oracle.reg_apply(x64, p)),
+                    (claire.SPECTRAL_INV, oracle.reg_inverse(x64, p)),
+                    (claire.SPECTRAL_K, oracle.project_K(x64, p))):
+        out = torch.empty((3,) + n, device="cuda")
+        ctx.spectral(xd, out, op)
+        torch.cuda.synchronize()
+        assert rel_l2(host(out), ref) <= 1e-5, op
+
+
+def test_dot_parity(env):
+    torch, claire = env
+    n = (40, 36, 30)
+    rng = np.random.default_rng(8)
+    x = f32(rng.standard_normal(3 * int(np.prod(n))))
+    y = f32(rng.standard_normal(3 * int(np.prod(n))))
+    ctx = make_ctx(claire, torch, n)
+    hv = float(np.prod(oracle.spacing(n)))
+    ref = hv * float(np.dot(x.astype(np.float64), y.astype(np.float64)))
+    got = ctx.dot(dev(torch, x), dev(torch, y))
+    assert abs(got - ref) <= 1e-6 * hv * float(np.dot(np.abs(x), np.abs(y)))
+    # misaligned start and odd length take the scalar path
+    got2 = ctx.dot(dev(torch, x)[1:], dev(torch, y)[1:], x.size - 3)
+    ref2 = hv * float(np.dot(x[1:-2].astype(np.float64), y[1:-2].astype(np.float64)))
+    assert abs(got2 - ref2) <= 1e-6 * hv * float(np.dot(np.abs(x), np.abs(y)))
+
+
+# ---------------------------------------------------------------------------
+# solves and operators
+# ---------------------------------------------------------------------------
+
+def _problem(n, nt=4, seed=0, scale=0.5):
+    m0 = f32(synth.blob_template(n, seed=seed))
+    vs = f32(synth.mode_velocity(n, seed=seed + 10, vmax=0.5))
+    p = oracle.Params(nt=nt, beta_v=1e-2, beta_w=1e-4)
+    m1 = f32(oracle.transport(m0.astype(np.float64), vs.astype(np.float64), p))
+    v = f32(scale * vs)
+    return m0, m1, vs, v, p
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("order", [3, 1])
+def test_transport_parity(env, n, order):
+    torch, claire = env
+    m0, _, vs, _, p = _problem(n)
+    p.order = order
+    ctx = make_ctx(claire, torch, n, nt=p.nt, interp=order)
+    out = torch.empty(n, device="cuda")
+    ctx.transport(dev(torch, vs), dev(torch, m0), out, claire.TRANSPORT_FWD)
+    torch.cuda.synchronize()
+    ref = oracle.transport(m0.astype(np.float64), vs.astype(np.float64), p)
+    assert rel_l2(host(out), ref) <= 2e-4
+    lam1 = f32(synth.blob_template(n, seed=9))
+    ctx.transport(dev(torch, vs), dev(torch, lam1), out, claire.TRANSPORT_ADJ)
+    torch.cuda.synchronize()
+    ref = oracle.transport(lam1.astype(np.float64), vs.astype(np.float64), p, direction="adj")
+    assert rel_l2(host(out), ref) <= 2e-4
+
+
+@pytest.mark.parametrize("n", SHAPES)
+@pytest.mark.parametrize("grad_form", [0, 1])
+def test_gradient_matvec_precond_parity(env, n, grad_form):
+    torch, claire = env
+    m0, m1, vs, v, p = _problem(n)
+    p.grad_form = grad_form
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, grad_form=grad_form)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    g = torch.empty((3,) + n, device="cuda")
+    J = ctx.gradient(dev(torch, v), g)
+    st = oracle.State(v.astype(np.float64), m0.astype(np.float64), m1.astype(np.float64), p)
+    assert abs(J - st.J) <= 1e-5 * abs(st.J)
+    assert rel_l2(host(g), oracle.gradient(st)) <= 1e-4
+    vt = f32(synth.mode_velocity(n, seed=33, vmax=0.3))
+    Hv = torch.empty((3,) + n, device="cuda")
+    ctx.hessian_matvec(dev(torch, vt), Hv)
+    torch.cuda.synchronize()
+    assert rel_l2(host(Hv), oracle.hessian_matvec(st, vt.astype(np.float64))) <= 1e-4
+    z = torch.empty((3,) + n, device="cuda")
+    ctx.precond(g, z)
+    torch.cuda.synchronize()
+    assert rel_l2(host(z), oracle.precond(host(g), p)) <= 1e-5
+    Jo, mis = ctx.objective(dev(torch, v))
+    assert abs(Jo - st.J) <= 1e-5 * abs(st.J) and abs(mis - st.mismatch) <= 1e-5 * st.mismatch
+
+
+def test_gradient_nt1_linear_h2(env):
+    """Degenerate and alternative settings: one time step, trilinear, H2."""
+    torch, claire = env
+    n = (16, 16, 16)
+    m0, m1, vs, v, p = _problem(n, nt=1)
+    p.order, p.reg = 1, 2
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=1, beta_w=p.beta_w, interp=1, reg=2)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    g = torch.empty((3,) + n, device="cuda")
+    ctx.gradient(dev(torch, v), g)
+    st = oracle.State(v.astype(np.float64), m0.astype(np.float64), m1.astype(np.float64), p)
+    assert rel_l2(host(g), oracle.gradient(st)) <= 1e-4
+    Hv = torch.empty((3,) + n, device="cuda")
+    ctx.hessian_matvec(dev(torch, vs), Hv)
+    torch.cuda.synchronize()
+    assert rel_l2(host(Hv), oracle.hessian_matvec(st, vs.astype(np.float64))) <= 1e-4
+
+
+@pytest.mark.parametrize("n", [(32, 32, 32), (40, 36, 30)])
+def test_detj_parity(env, n):
+    torch, claire = env
+    vs = f32(synth.mode_velocity(n, seed=12, vmax=0.8))
+    p = oracle.Params(nt=4)
+    ctx = make_ctx(claire, torch, n, nt=4)
+    lo, hi = ctx.detj(dev(torch, vs))
+    ref = oracle.detj(vs.astype(np.float64), p)
+    assert abs(lo - ref.min()) <= 1e-5 * abs(ref.min()) and abs(hi - ref.max()) <= 1e-5 * ref.max()
+    assert ref.min() < 0.9 and ref.max() > 1.1  # a non-trivial map
+
+
+def test_state_errors_and_failure_detection(env):
+    torch, claire = env
+    n = (16, 16, 16)
+    m0, m1, vs, v, p = _problem(n)
+    ctx = make_ctx(claire, torch, n)
+    out = torch.empty((3,) + n, device="cuda")
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.gradient(dev(torch, v), out)
+    assert e.value.status == -8  # images not set
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.hessian_matvec(dev(torch, v), out)
+    assert e.value.status == -8  # no linearisation point
+    bad = m1.copy()
+    bad[3, 4, 5] = np.nan  # failure made on the host: a NaN in the reference image
+    ctx.set_images(dev(torch, m0), dev(torch, bad))
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.gradient(dev(torch, v), out)
+    assert e.value.status == -5
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.interp(np.zeros(n, np.float32), dev(torch, v), out[0])
+    assert e.value.status == -1  # kernel-level entry points reject host pointers
+
+
+def test_wall_clock_limit(env):
+    torch, claire = env
+    n = (32, 32, 32)
+    m0, m1, vs, v, p = _problem(n)
+    ctx = make_ctx(claire, torch, n, gtol=1e-9, wall_limit_s=1e-6, max_gn=20)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    vv = torch.zeros((3,) + n, device="cuda")
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.register(vv)
+    assert e.value.status == -7
+
+
+# ---------------------------------------------------------------------------
+# registration (Eq. (5)): 64^3 blob workload, 5 Gauss-Newton x 10 PCG
+# ---------------------------------------------------------------------------
+
+def _config1():
+    n = (64, 64, 64)
+    m0 = f32(synth.blob_template(n, seed=0))
+    vs = synth.mode_velocity(n, seed=0, nmodes=6, kmax=4, vmax=0.5)
+    p = oracle.Params(nt=4, beta_v=1e-2, beta_w=1e-4, gtol=0.0, max_gn=5, max_pcg=10,
+                      pcg_fixed=True)
+    m1 = f32(oracle.transport(m0.astype(np.float64), vs, p))
+    return n, m0, m1, p
+
+
+@pytest.fixture(scope="module")
+def config1_oracle():
+    n, m0, m1, p = _config1()
+    v, rep = oracle.register(m0.astype(np.float64), m1.astype(np.float64), p)
+    return n, m0, m1, p, v, rep
+
+
+def test_registration_fixed_schedule_parity(env, config1_oracle):
+    torch, claire = env
+    n, m0, m1, p, v_ref, rep_ref = config1_oracle
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, gtol=0.0,
+                   max_gn=5, max_pcg=10, pcg_fixed=1)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    v = torch.zeros((3,) + n, device="cuda")
+    st, rep = ctx.register(v)
+    assert rep["gn_iters"] == rep_ref["gn_iters"] == 5
+    assert rep["alpha"] == rep_ref["alpha"]
+    assert rel_l2(host(v), v_ref) <= 1e-3
+    assert abs(rep["r"] - rep_ref["r"]) <= 0.01 * rep_ref["r"]
+
+
+def test_registration_free_running_and_host_pointers(env):
+    """gtol 5e-2 with the default forcing: same final mismatch within 1 %;
+    the host-pointer call gives the same result as the device call."""
+    torch, claire = env
+    n, m0, m1, p = _config1()
+    p.gtol, p.pcg_fixed, p.max_gn = 5e-2, False, 20
+    v_ref, rep_ref = oracle.register(m0.astype(np.float64), m1.astype(np.float64), p)
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, gtol=p.gtol,
+                   max_gn=20, max_pcg=10)
+    ctx.set_images(m0, m1)  # host arrays
+    v_host = np.zeros((3,) + n, np.float32)
+    st, rep = ctx.register(v_host)
+    assert st == 0 and rep["gnorm_rel"] <= 5e-2
+    assert abs(rep["r"] - rep_ref["r"]) <= 0.01 * rep_ref["r"]
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    v_dev = torch.zeros((3,) + n, device="cuda")
+    st2, rep2 = ctx.register(v_dev)
+    assert np.array_equal(v_dev.cpu().numpy(), v_host)
+    assert rep2["gn_iters"] == rep["gn_iters"]
+
+
+# ---------------------------------------------------------------------------
+# full size (256^3): sampled points and size-independent properties
+# ---------------------------------------------------------------------------
+
+def test_full_size_interp_sampled(env):
+    torch, claire = env
+    n = (256, 256, 256)
+    m0 = f32(synth.label_template(n, seed=0))
+    vs = synth.bandlimited_velocity(n, seed=0, kmax=8, vmax=1.0)
+    ctx = make_ctx(claire, torch, n, nt=4)
+    d = torch.empty((3,) + n, device="cuda")
+    ctx.backtrace(dev(torch, vs), d, 1)
+    out = torch.empty(n, device="cuda")
+    f = dev(torch, m0)
+    ctx.interp(f, d, out, 3)
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(0)
+    idx = rng.integers(0, m0.size, size=20000)
+    dh = d.reshape(3, -1)[:, torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    I, J, K = np.unravel_index(idx, n)
+    y = np.stack([I + dh[0], J + dh[1], K + dh[2]])
+    ref = oracle.interp_points(m0.astype(np.float64), y, 3)
+    got = out.reshape(-1)[torch.from_numpy(idx).cuda()].cpu().numpy().astype(np.float64)
+    assert np.max(np.abs(got - ref)) <= 1e-5 * np.max(np.abs(m0))
+    # sampled backtrace: X = x - dt/2 (v(x) + v(x - dt v(x))) from the FP32 velocity
+    h = oracle.spacing(n)
+    v32 = f32(vs)
+    u = np.stack([v32[c].reshape(-1)[idx].astype(np.float64) / h[c] for c in range(3)])
+    ys = np.stack([I - 0.25 * u[0], J - 0.25 * u[1], K - 0.25 * u[2]])
+    us = np.stack([oracle.interp_points(v32[c].astype(np.float64), ys, 3) / h[c] for c in range(3)])
+    dref = -0.125 * (u + us)
+    assert np.max(np.abs(dh - dref)) <= 1e-5 * np.max(np.abs(dref))
+
+
+def test_full_size_transport_integer_shift_exact(env):
+    """Constant velocity moving dt v / h = (1, -2, 3) cells per step: the 256^3
+    transport is an exact periodic roll (interpolation weights are 0/1)."""
+    torch, claire = env
+    n = (256, 256, 256)
+    m0 = f32(synth.label_template(n, seed=1))
+    h = oracle.spacing(n)
+    shift = (1, -2, 3)
+    v = np.stack([np.full(n, s * h[c] * 4, np.float32) for c, s in enumerate(shift)])
+    ctx = make_ctx(claire, torch, n, nt=4)
+    out = torch.empty(n, device="cuda")
+    ctx.transport(dev(torch, v), dev(torch, m0), out, claire.TRANSPORT_FWD)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), np.roll(m0, (4, -8, 12), axis=(0, 1, 2)))

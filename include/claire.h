@@ -55,7 +55,8 @@ typedef enum {
     CLAIRE_ELINESEARCH = -6,   /* Armijo line search found no acceptable step */
     CLAIRE_ETIMEOUT = -7,      /* wall-clock limit reached; outputs hold the last iterate */
     CLAIRE_ESTATE = -8,        /* call needs state that is not set (images, linearisation point) */
-    CLAIRE_ENOTIMPL = -9
+    CLAIRE_ENOTIMPL = -9,
+    CLAIRE_ETOOLARGE = -10     /* size beyond the fixed maximum of claire_dot_noalloc */
 } claire_status;
 
 /* Interpolation order of the semi-Lagrangian gathers (Sec. 3, "IP kernel"). */
@@ -223,6 +224,32 @@ claire_status claire_spectral(claire_ctx* ctx, const float* in, float* out, int 
 
 /* FP64 inner product h1 h2 h3 sum_i x_i y_i over n floats (device pointers). */
 claire_status claire_dot(claire_ctx* ctx, const float* x, const float* y, size_t n, double* out);
+
+/*
+ * claire_dot_noalloc: the same FP64 inner product as claire_dot, for callers
+ * that cannot allocate device memory: a process whose device memory is fully
+ * reserved by another allocator, a latency-critical loop that cannot take the
+ * implicit device-wide synchronisation of cudaMalloc / cudaFree, or code that
+ * holds no claire context (creating one allocates all workspaces).  The paper
+ * has no counterpart; this is a library convenience.
+ *
+ *   *out = scale * sum_{i<n} x_i y_i    (scale = h1 h2 h3 gives claire_dot)
+ *
+ * x, y: device pointers to n floats; out: host pointer; stream: a
+ * cudaStream_t or NULL for the legacy default stream.  Allocates nothing:
+ * the partial sums live in a fixed device array of 1 MiB + 256 B that every
+ * GPU loading the library holds until the process exits.  n may be at most
+ * 2^30 (1,073,741,824); larger n returns CLAIRE_ETOOLARGE before any launch.
+ * The first call on each device looks up that array's device address (with
+ * the device current); make that first call before any stream capture.
+ * Calls share the array and overwrite the slots they use: calls whose work
+ * overlaps on the GPU (other streams or host threads) race and must be
+ * serialised by the caller.  Synchronises `stream` before returning.
+ * Returns CLAIRE_EINVAL for null or host input pointers, CLAIRE_ECUDA on a
+ * CUDA error.
+ */
+claire_status claire_dot_noalloc(const float* x, const float* y, size_t n, double scale,
+                                 void* stream, double* out);
 
 /* ---- instrumentation ---- */
 

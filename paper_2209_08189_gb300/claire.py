@@ -22,7 +22,7 @@ CLAIRE_ENOTCONVERGED = 1
 STATUS_NAMES = {0: "CLAIRE_OK", 1: "CLAIRE_ENOTCONVERGED", -1: "CLAIRE_EINVAL",
                 -2: "CLAIRE_ENOMEM", -3: "CLAIRE_ECUDA", -4: "CLAIRE_ECUFFT",
                 -5: "CLAIRE_ENONFINITE", -6: "CLAIRE_ELINESEARCH", -7: "CLAIRE_ETIMEOUT",
-                -8: "CLAIRE_ESTATE", -9: "CLAIRE_ENOTIMPL"}
+                -8: "CLAIRE_ESTATE", -9: "CLAIRE_ENOTIMPL", -10: "CLAIRE_ETOOLARGE"}
 INTERP_CUBIC, INTERP_LINEAR = 3, 1
 TRANSPORT_FWD, TRANSPORT_ADJ = 0, 1
 SPECTRAL_REG, SPECTRAL_INV, SPECTRAL_K = 0, 1, 2
@@ -106,6 +106,8 @@ _SIGS = {
     "claire_fd8_div": [_vp, _vp, _vp],
     "claire_spectral": [_vp, _vp, _vp, ctypes.c_int],
     "claire_dot": [_vp, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
+    "claire_dot_noalloc": [_vp, _vp, ctypes.c_size_t, ctypes.c_double, _vp,
+                           ctypes.POINTER(ctypes.c_double)],
     "claire_kernel_stats": [_vp, ctypes.POINTER(claire_kernel_stat), ctypes.c_int,
                             ctypes.POINTER(ctypes.c_int), ctypes.c_int],
     "claire_set_timing": [_vp, ctypes.c_int],
@@ -258,6 +260,18 @@ def claire_dot(ctx, x, y, n):
     out = ctypes.c_double()
     _check(ctx, lib().claire_dot(ctx, _ptr(x), _ptr(y), int(n), ctypes.byref(out)))
     return out.value
+
+
+def claire_dot_noalloc(x, y, n, scale, stream=None):
+    """FP64 scale * sum(x * y) over n floats without any device allocation
+    (for callers that cannot allocate; see include/claire.h).  Returns
+    (status, value); negative statuses raise ClaireError."""
+    out = ctypes.c_double()
+    st = lib().claire_dot_noalloc(_ptr(x), _ptr(y), int(n), float(scale), stream,
+                                  ctypes.byref(out))
+    if st < 0:
+        raise ClaireError(st, "claire_dot_noalloc(n=%d)" % int(n))
+    return st, out.value
 
 
 def claire_kernel_stats(ctx, reset=False):

@@ -86,10 +86,12 @@ typedef struct claire_opts {
     double armijo_c1;    /* sufficient-decrease constant; default 1e-4 */
     int max_ls;          /* step halvings before CLAIRE_ELINESEARCH; default 10 */
     double wall_limit_s; /* claire_register wall-clock cap in seconds; 0 = none (default) */
-    int timing;          /* 1 = time phases with CUDA events into claire_report.t_phase_s */
+    int timing;          /* 1 = time every kernel launch with CUDA events (read back lazily by
+                            claire_kernel_stats); 2 = also fill claire_report.t_phase_s at the end
+                            of each claire_register (one extra synchronisation) */
 } claire_opts;
 
-/* Phase slots of claire_report.t_phase_s (seconds, CUDA-event timed when opts.timing = 1). */
+/* Phase slots of claire_report.t_phase_s (seconds, CUDA-event timed when opts.timing = 2). */
 #define CLAIRE_PHASE_BACKTRACE 0   /* RK2 characteristics, div v, div v at X+ */
 #define CLAIRE_PHASE_STATE 1       /* forward solve and FD8 gradients of m^j */
 #define CLAIRE_PHASE_ADJOINT 2     /* adjoint solve with gradient body */

@@ -82,6 +82,8 @@ struct claire_ctx {
     float *l0 = nullptr, *l1 = nullptr;   // rolling scalar fields
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     cufftComplex* spec = nullptr;
+    cufftComplex* phat = nullptr;         // PCG search direction in Fourier space
+    cufftComplex* spec2 = nullptr;        // second transform buffer
     double* partials = nullptr;           // 2 * red_blocks
     double* dres = nullptr;               // device scalars
     double* hres = nullptr;               // pinned host scalars
@@ -226,6 +228,8 @@ size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, Layout* L)
     l.add(N);                 // l1
     for (int i = 0; i < 6; ++i) l.add(3 * N);  // g x r z p q
     l.add(6 * M);             // spec (3 complex half-spectra)
+    l.add(6 * M);             // phat
+    l.add(6 * M);             // spec2
     l.add(4 * red_blocks);    // partials (2 * red_blocks doubles)
     l.add(32);                // dres (16 doubles)
     return l.total;
@@ -336,7 +340,8 @@ void collect_timing(claire_ctx* c)
 
 claire_status sync_scalars(claire_ctx* c, int count)
 {
-    CL_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, count * sizeof(double), cudaMemcpyDeviceToHost,
+    (void)count;
+    CL_CUDA(c, cudaMemcpyAsync(c->hres, c->dres, 16 * sizeof(double), cudaMemcpyDeviceToHost,
                                c->stream));
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
     return CLAIRE_OK;
@@ -490,14 +495,15 @@ claire_status gradient_at_lin(claire_ctx* c, float* g)
     return CLAIRE_OK;
 }
 
-// H vt at the linearisation point into out (out != vt).
-claire_status matvec(claire_ctx* c, const float* vt, float* out)
+// H vt at the linearisation point into out (out != vt).  With s_in_out the
+// caller has already placed S vt in out.
+claire_status matvec(claire_ctx* c, const float* vt, float* out, bool s_in_out = false)
 {
     if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
     const size_t N = c->N;
     const int nt = c->nt;
     const float dt = static_cast<float>(c->dt);
-    CL_TRY(spectral(c, vt, out, SPEC_REG));
+    if (!s_in_out) CL_TRY(spectral(c, vt, out, SPEC_REG));
     PhaseScope ps(c, CLAIRE_PHASE_INCREMENTAL);
     float* a = c->l0;
     float* b = c->l1;
@@ -516,7 +522,7 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out)
     {
         KTimer t(c, KK_INC_LAST, 68.0 * N, 1.0 * N);
         launch_inc_last(c->grid, c->o.interp, a, c->dS, vt, c->gm + 3 * nt * N, 0.5f * dt,
-                        static_cast<float>(trap_w(c, nt)), 1, b, out, c->stream);
+                        static_cast<float>(trap_w(c, nt)), b, out, c->stream);
         CL_LAUNCHED(c);
     }
     // incremental adjoint from lt^{nt} (in b), body accumulated into out
@@ -616,7 +622,50 @@ claire_status cfl_of(claire_ctx* c, const float* v, double* cfl)
     return CLAIRE_OK;
 }
 
-// Matrix-free PCG for H x = -g (x0 = 0).  Returns the iteration count in *its.
+// Preconditioned residual in Fourier space: spec <- M r^ (scaled for the
+// inverse transform); returns <r, M r> (discrete inner product) by Parseval.
+claire_status precond_spectral(claire_ctx* c, const float* r, double* rz)
+{
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+        {
+            KTimer t(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecR2C(c->r2c, const_cast<float*>(r), c->spec));
+        }
+        KTimer t(c, KK_SPECTRAL, 48.0 * c->M, 0, 2);
+        launch_spectral_precond(c->grid, c->spec, c->M, c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV, c->rp,
+                                static_cast<float>(1.0 / c->N), c->partials, c->red_blocks, c->stream);
+        launch_final_sum(c->partials, c->red_blocks, c->hvol, c->dres, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_TRY(sync_scalars(c, 1));
+    *rz = c->hres[0];
+    if (!std::isfinite(*rz)) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG inner product");
+    return CLAIRE_OK;
+}
+
+// New search direction p^ = z^ + beta p^ in Fourier space; p and S p back in
+// real space (p into c->p, S p into c->z for the matvec).
+claire_status pcg_direction(claire_ctx* c, double beta, bool first)
+{
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    {
+        KTimer t(c, KK_SPECTRAL, 120.0 * c->M, 0);
+        launch_spectral_direction(c->grid, c->spec, c->phat, c->spec2, c->M, static_cast<float>(beta),
+                                  first ? 1 : 0, c->rp, c->stream);
+        CL_LAUNCHED(c);
+    }
+    KTimer t(c, KK_FFT, 0, 0, 2);
+    CL_FFT(c, cufftExecC2R(c->c2r, c->spec2, c->p));
+    CL_FFT(c, cufftExecC2R(c->c2r, c->spec, c->z));
+    return CLAIRE_OK;
+}
+
+// Matrix-free PCG for H x = -g (x0 = 0), preconditioned by the spectral
+// inverse of the regulariser.  The search direction is carried in Fourier
+// space, so each iteration takes one forward and two inverse transforms
+// (residual in; direction and its regularisation out) and the matvec gets
+// S p without transforming p again.  Returns the iteration count in *its.
 claire_status pcg(claire_ctx* c, double eta, int* its)
 {
     const size_t n3 = 3 * c->N;
@@ -633,15 +682,14 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
     CL_TRY(dot(c, c->r, c->r, n3, &r0));
     r0 = std::sqrt(r0);
     if (r0 == 0.0) return CLAIRE_OK;
-    CL_TRY(precond(c, c->r, c->z));
-    CL_CUDA(c, cudaMemcpyAsync(c->p, c->z, n3 * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
     double rz;
-    CL_TRY(dot(c, c->r, c->z, n3, &rz));
+    CL_TRY(precond_spectral(c, c->r, &rz));
+    CL_TRY(pcg_direction(c, 0.0, true));
     for (int it = 1; it <= c->o.max_pcg; ++it) {
         *its = it;
-        CL_TRY(matvec(c, c->p, c->q));
+        CL_TRY(matvec(c, c->p, c->z, true));  // z: S p in, H p out
         double pq;
-        CL_TRY(dot(c, c->p, c->q, n3, &pq));
+        CL_TRY(dot(c, c->p, c->z, n3, &pq));
         if (pq <= 0.0) {
             if (it == 1)
                 CL_CUDA(c, cudaMemcpyAsync(c->x, c->p, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
@@ -654,7 +702,7 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
             PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
             {
                 KTimer t(c, KK_VECTOR, 24.0 * n3, 0, 2);
-                launch_pcg_update(static_cast<float>(alpha), c->p, c->q, c->x, c->r, n3,
+                launch_pcg_update(static_cast<float>(alpha), c->p, c->z, c->x, c->r, n3,
                                   c->partials, c->red_blocks, c->stream);
                 launch_final_sum(c->partials, c->red_blocks, c->hvol, c->dres, c->stream);
                 CL_LAUNCHED(c);
@@ -665,17 +713,11 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         if (!std::isfinite(rr)) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG residual");
         if (!c->o.pcg_fixed && std::sqrt(rr) <= eta * r0) break;
         if (it == c->o.max_pcg) break;
-        CL_TRY(precond(c, c->r, c->z));
         double rz_new;
-        CL_TRY(dot(c, c->r, c->z, n3, &rz_new));
+        CL_TRY(precond_spectral(c, c->r, &rz_new));
         const double beta = rz_new / rz;
         rz = rz_new;
-        {
-            PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
-            KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
-            launch_xpay(c->z, static_cast<float>(beta), c->p, c->p, n3, c->stream);
-            CL_LAUNCHED(c);
-        }
+        CL_TRY(pcg_direction(c, beta, false));
     }
     return CLAIRE_OK;
 }
@@ -820,8 +862,14 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->p = base + L.off[k++];
     c->q = base + L.off[k++];
     c->spec = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
+    c->phat = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
+    c->spec2 = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->partials = reinterpret_cast<double*>(base + L.off[k++]);
     c->dres = reinterpret_cast<double*>(base + L.off[k++]);
+    if (cudaMemset(c->dres, 0, 16 * sizeof(double)) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(CLAIRE_ECUDA);
+    }
     if (cudaMallocHost(&c->hres, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         c->hres = nullptr;
@@ -1022,7 +1070,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
     CL_TRY(cfl_of(c, c->v, &R.cfl));
     CL_CUDA(c, cudaMemcpyAsync(v_inout, c->v, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
-    collect_timing(c);
+    if (c->o.timing >= 2 || c->pending.size() > 200000) collect_timing(c);
     R.status = st;
     R.t_total_s = elapsed();
     for (int i = 0; i < 8; ++i) R.t_phase_s[i] = c->phase_s[i] - ph0[i];
@@ -1072,6 +1120,7 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
             std::swap(a, b);
         }
     }
+    CL_TRY(sync_scalars(c, 0));
     CL_TRY(copy_out(c, m_out, src, N));
     collect_timing(c);
     return CLAIRE_OK;
@@ -1100,7 +1149,7 @@ claire_status claire_interp(claire_ctx* c, const float* f, const float* d, float
         launch_interp(c->grid, order, f, d, out, c->stream);
         CL_LAUNCHED(c);
     }
-    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    CL_TRY(sync_scalars(c, 0));
     collect_timing(c);
     return CLAIRE_OK;
 }

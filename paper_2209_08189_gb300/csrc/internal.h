@@ -82,8 +82,9 @@ void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef
                      cudaStream_t st);
 void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
                      const float* gm, float coef, float* q, cudaStream_t st);
+// last incremental state step; accumulates w lt grad m into b
 void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float w, int accumulate, float* lam, float* b,
+                     const float* gm, float coef, float w, float* lam, float* b,
                      cudaStream_t st);
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
                      cudaStream_t st);
@@ -105,6 +106,14 @@ struct RegParams {
 // times scale (the 1/N of the unnormalised inverse transform).
 void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op,
                      RegParams rp, float scale, cudaStream_t st);
+
+// PCG preconditioner in Fourier space: xh <- scale * M(k) xh (SPEC_INV or
+// SPEC_AINV) with block partial sums of sum_x r z (Parseval) in partials.
+void launch_spectral_precond(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op,
+                             RegParams rp, float scale, double* partials, int nblocks, cudaStream_t st);
+// PCG direction in Fourier space: ph = zh + beta ph (first: ph = zh), cp = ph, zh <- S ph.
+void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph, cufftComplex* cp,
+                               size_t cstride, float beta, int first, RegParams rp, cudaStream_t st);
 
 // Deterministic FP64 reductions: partial sums per block, then a one-block
 // final sum in fixed order.  `partials` holds at least nblocks doubles.

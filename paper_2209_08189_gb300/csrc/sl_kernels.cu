@@ -4,6 +4,7 @@
 // Jacobian determinant.  Method: "CLAIRE at scale" (arXiv 2209.08189),
 // Sec. 2.2 (SL with RK2, FD8) and Sec. 3 (IP and FD kernels).
 #include "internal.h"
+#include "sl_tiled.cuh"
 
 namespace claire {
 
@@ -16,21 +17,6 @@ inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
 // ---------------------------------------------------------------------------
 // gathers
 // ---------------------------------------------------------------------------
-
-// out[p] = f(x_p + d_p)
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_interp(Grid g, const float* __restrict__ f,
-                                                      const float* __restrict__ d,
-                                                      float* __restrict__ out)
-{
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
-    Stencil<ORDER> s;
-    s.build(g, i, j, k, __ldg(d + p), __ldg(d + g.N + p), __ldg(d + 2 * (size_t)g.N + p));
-    out[p] = s.eval(f);
-}
 
 // Heun characteristic: sign = +1 gives X = x - dt/2 [v(x) + v(x - dt v(x))],
 // sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))].  d in grid units.
@@ -77,39 +63,6 @@ __global__ void __launch_bounds__(kThreads) k_adj_init(Grid g, const float* __re
     }
 }
 
-// One SL step of the adjoint equation (Eq. (4)) backwards in time:
-//   a = lambda^{j+1}(X+), lambda^j = a + dt/2 [a d(X+) + (a + dt a d(X+)) d(x)],
-// fused with the gradient body b += w_j lambda^j grad m^j (gm may be null).
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_adj_step(Grid g, const float* __restrict__ lam_next,
-                                                        const float* __restrict__ dA,
-                                                        const float* __restrict__ divv,
-                                                        const float* __restrict__ divXp, float dt,
-                                                        float w, const float* __restrict__ gm,
-                                                        float* __restrict__ lam,
-                                                        float* __restrict__ b)
-{
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
-    const size_t N = g.N;
-    Stencil<ORDER> s;
-    s.build(g, i, j, k, __ldg(dA + p), __ldg(dA + N + p), __ldg(dA + 2 * N + p));
-    const float a = s.eval(lam_next);
-    const float dX = __ldg(divXp + p);
-    const float dx = __ldg(divv + p);
-    const float adX = a * dX;
-    const float pred = fmaf(dt, adX, a);
-    const float l = fmaf(0.5f * dt, fmaf(pred, dx, adX), a);
-    lam[p] = l;
-    if (gm) {
-        const float wl = w * l;
-#pragma unroll
-        for (int c = 0; c < 3; ++c) b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b[c * N + p]);
-    }
-}
-
 // Incremental state source f = -vt . grad m.
 __device__ __forceinline__ float inc_source(const float* __restrict__ vt, const float* __restrict__ gm,
                                             uint32_t p, size_t N)
@@ -126,53 +79,6 @@ __global__ void __launch_bounds__(kThreads) k_inc_init(Grid g, const float* __re
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
     q[p] = coef * inc_source(vt, gm, p, g.N);
-}
-
-// q^{j+1} = q^j(X) + coef f^{j+1}   (coef = dt: the Heun halves of two steps)
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_inc_step(Grid g, const float* __restrict__ q_prev,
-                                                        const float* __restrict__ d,
-                                                        const float* __restrict__ vt,
-                                                        const float* __restrict__ gm, float coef,
-                                                        float* __restrict__ q)
-{
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
-    const size_t N = g.N;
-    Stencil<ORDER> s;
-    s.build(g, i, j, k, __ldg(d + p), __ldg(d + N + p), __ldg(d + 2 * N + p));
-    q[p] = fmaf(coef, inc_source(vt, gm, p, N), s.eval(q_prev));
-}
-
-// Last incremental state step fused with the start of the incremental
-// adjoint: mt = q(X) + dt/2 f^{nt}, lt = -mt, b = (accumulate ? b : 0) + w lt grad m^{nt}.
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_inc_last(Grid g, const float* __restrict__ q_prev,
-                                                        const float* __restrict__ d,
-                                                        const float* __restrict__ vt,
-                                                        const float* __restrict__ gm, float coef,
-                                                        float w, int accumulate,
-                                                        float* __restrict__ lam,
-                                                        float* __restrict__ b)
-{
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
-    const size_t N = g.N;
-    Stencil<ORDER> s;
-    s.build(g, i, j, k, __ldg(d + p), __ldg(d + N + p), __ldg(d + 2 * N + p));
-    const float mt = fmaf(coef, inc_source(vt, gm, p, N), s.eval(q_prev));
-    const float l = -mt;
-    lam[p] = l;
-    const float wl = w * l;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float b0 = accumulate ? b[c * N + p] : 0.0f;
-        b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b0);
-    }
 }
 
 // Deformation map step: u^{j+1} = u^j(X) + (X - x), three components.
@@ -295,7 +201,11 @@ __global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* _
 void launch_interp(const Grid& g, int order, const float* f, const float* d, float* out,
                    cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_interp, g, f, d, out);
+    EpiStore e{out};
+    if (order == 3)
+        launch_tiled<3, EpiStore>(g, f, d, e, st);
+    else
+        launch_tiled<1, EpiStore>(g, f, d, e, st);
 }
 
 void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
@@ -314,7 +224,19 @@ void launch_adj_step(const Grid& g, int order, const float* lam_next, const floa
                      const float* divv, const float* divXp, float dt, float w, const float* gm,
                      float* lam, float* b, cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_adj_step, g, lam_next, dA, divv, divXp, dt, w, gm, lam, b);
+    if (gm) {
+        EpiAdjoint e{divv, divXp, gm, lam, b, dt, w, g.N};
+        if (order == 3)
+            launch_tiled<3, EpiAdjoint>(g, lam_next, dA, e, st);
+        else
+            launch_tiled<1, EpiAdjoint>(g, lam_next, dA, e, st);
+    } else {
+        EpiAdjointOnly e{divv, divXp, lam, dt};
+        if (order == 3)
+            launch_tiled<3, EpiAdjointOnly>(g, lam_next, dA, e, st);
+        else
+            launch_tiled<1, EpiAdjointOnly>(g, lam_next, dA, e, st);
+    }
 }
 
 void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef, float* q,
@@ -326,14 +248,22 @@ void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef
 void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
                      const float* gm, float coef, float* q, cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_inc_step, g, q_prev, d, vt, gm, coef, q);
+    EpiIncremental e{vt, gm, q, coef, g.N};
+    if (order == 3)
+        launch_tiled<3, EpiIncremental>(g, q_prev, d, e, st);
+    else
+        launch_tiled<1, EpiIncremental>(g, q_prev, d, e, st);
 }
 
 void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float w, int accumulate, float* lam, float* b,
+                     const float* gm, float coef, float w, float* lam, float* b,
                      cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_inc_last, g, q_prev, d, vt, gm, coef, w, accumulate, lam, b);
+    EpiIncrementalLast e{vt, gm, lam, b, coef, w, g.N};
+    if (order == 3)
+        launch_tiled<3, EpiIncrementalLast>(g, q_prev, d, e, st);
+    else
+        launch_tiled<1, EpiIncrementalLast>(g, q_prev, d, e, st);
 }
 
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,

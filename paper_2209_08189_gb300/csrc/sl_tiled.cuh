@@ -1,0 +1,432 @@
+// Tiled semi-Lagrangian gather for sm_103a.
+//
+// A CTA owns a TILE1 x TILE2 x TILE3 block of arrival points (x3 fastest; a
+// warp covers 32 consecutive x3 nodes of one x2 row, each thread TILE1
+// points along x1).  Because the velocity is smooth, the departure points of
+// a tile fall in a small box of the grid.  The CTA reduces the box bounds of
+// its stencils, copies the box (periodically wrapped) from global memory into
+// shared memory with cp.async, and then evaluates every stencil from shared
+// memory, so the 64 (cubic) or 8 (linear) reads per point hit on-chip memory
+// instead of issuing scattered L1/L2 requests.  A tile whose box does not fit
+// (very large local compression of the characteristic map) falls back to the
+// direct global-memory gather for that tile only.  The result of each point
+// goes to an epilogue functor that fuses the step's source terms.
+#pragma once
+
+#include <climits>
+
+#include "common.cuh"
+
+namespace claire {
+
+#ifndef CLAIRE_TILE1
+#define CLAIRE_TILE1 4  // arrival points per thread along x1
+#endif
+#ifndef CLAIRE_TILE_MIN_BLOCKS
+#define CLAIRE_TILE_MIN_BLOCKS 4  // resident CTAs per SM the register budget targets
+#endif
+
+#ifndef CLAIRE_LDS_ASM
+#define CLAIRE_LDS_ASM 1  // explicit 32-bit ld.shared with immediate offsets for the stencil reads
+#endif
+#ifndef CLAIRE_BOX_CAP
+#define CLAIRE_BOX_CAP 11776  // floats of dynamic shared memory per CTA (46 KB)
+#endif
+
+constexpr int TILE1 = CLAIRE_TILE1, TILE2 = 8, TILE3 = 32;
+constexpr int kTileThreads = TILE2 * 32;
+constexpr int kBoxCapFloats = CLAIRE_BOX_CAP;
+
+__device__ __forceinline__ void cp_async_f32(float* smem_dst, const float* gmem_src)
+{
+    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem_dst));
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+
+__device__ __forceinline__ void cp_async_wait_all()
+{
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+}
+
+template <int ORDER>
+__device__ __forceinline__ void axis_weights(float t, float w[4])
+{
+    if constexpr (ORDER == 3) {
+        cubic_weights(t, w);
+    } else {
+        w[0] = 1.0f - t;
+        w[1] = t;
+    }
+}
+
+// Direct global-memory gather for tiles whose departure box does not fit
+// (kept out of line so that it does not add to the register budget of the
+// shared-memory path).
+template <int ORDER>
+__device__ __noinline__ float gather_global(const Grid g, const float* __restrict__ f, int i, int j,
+                                            int k, float d1, float d2, float d3)
+{
+    Stencil<ORDER> s;
+    s.build(g, i, j, k, d1, d2, d3);
+    return s.eval(f);
+}
+
+// ---- building blocks of the tiled gathers ----
+
+// Geometry of the CTA's stencil box, shared by all threads of the CTA.
+struct BoxPar {
+    int O1, O2, O3;  // first node (unwrapped grid coordinates)
+    int E1, E2, E3;  // extents; E1 == 0 means "does not fit: gather from global memory"
+    int S3;          // row stride, a multiple of 32
+};
+
+// Block-wide bounds of the stencils whose first-node cells (before the
+// -OFF shift) span [lo, hi] per axis; thread 0 publishes the box in par.
+template <int ORDER>
+__device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
+                                           int hi3, int (*red)[TILE2], int* par, int lane, int warp)
+{
+    constexpr int M = (ORDER == 3) ? 4 : 2;
+    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    lo1 = __reduce_min_sync(0xffffffffu, lo1);
+    lo2 = __reduce_min_sync(0xffffffffu, lo2);
+    lo3 = __reduce_min_sync(0xffffffffu, lo3);
+    hi1 = __reduce_max_sync(0xffffffffu, hi1);
+    hi2 = __reduce_max_sync(0xffffffffu, hi2);
+    hi3 = __reduce_max_sync(0xffffffffu, hi3);
+    if (lane == 0) {
+        red[0][warp] = lo1; red[1][warp] = lo2; red[2][warp] = lo3;
+        red[3][warp] = hi1; red[4][warp] = hi2; red[5][warp] = hi3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a1 = INT_MAX, a2 = INT_MAX, a3 = INT_MAX, z1 = INT_MIN, z2 = INT_MIN, z3 = INT_MIN;
+#pragma unroll
+        for (int w = 0; w < TILE2; ++w) {
+            a1 = min(a1, red[0][w]); a2 = min(a2, red[1][w]); a3 = min(a3, red[2][w]);
+            z1 = max(z1, red[3][w]); z2 = max(z2, red[4][w]); z3 = max(z3, red[5][w]);
+        }
+        // box of the stencils: cells [a - OFF, z - OFF + M); the tile always
+        // holds at least one valid point
+        const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M,
+                        e3 = (long long)z3 - a3 + M;
+        const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
+        const bool fits = e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && e1 * e2 * s3 <= kBoxCapFloats;
+        par[0] = a1 - OFF; par[1] = a2 - OFF; par[2] = a3 - OFF;
+        par[3] = static_cast<int>(fits ? e1 : 0);
+        par[4] = static_cast<int>(fits ? e2 : 0);
+        par[5] = static_cast<int>(fits ? e3 : 0);
+        par[6] = static_cast<int>(fits ? s3 : 0);
+    }
+    __syncthreads();
+    BoxPar b;
+    b.O1 = par[0]; b.O2 = par[1]; b.O3 = par[2];
+    b.E1 = par[3]; b.E2 = par[4]; b.E3 = par[5]; b.S3 = par[6];
+    return b;
+}
+
+// Issue the cp.async copies of the (periodically wrapped) box of f.
+__device__ __forceinline__ void tile_load_box(const Grid& g, const float* __restrict__ f, float* box,
+                                              const BoxPar& bp, int lane, int warp)
+{
+    const int w1 = wrap_index(bp.O1, g.n1), w2 = wrap_index(bp.O2, g.n2), w3 = wrap_index(bp.O3, g.n3);
+    int gk0 = w3 + lane;
+    gk0 = gk0 >= g.n3 ? gk0 - g.n3 : gk0;
+    int gk1 = w3 + lane + 32;
+    gk1 = gk1 >= g.n3 ? gk1 - g.n3 : gk1;
+    for (int a = 0; a < bp.E1; ++a) {
+        int gi = w1 + a;
+        gi = gi >= g.n1 ? gi - g.n1 : gi;
+        const float* plane = f + static_cast<size_t>(gi) * g.n23;
+        for (int b = warp; b < bp.E2; b += TILE2) {
+            int gj = w2 + b;
+            gj = gj >= g.n2 ? gj - g.n2 : gj;
+            const float* src = plane + gj * g.n3;
+            float* dst = box + (a * bp.E2 + b) * bp.S3;
+            if (lane < bp.E3) cp_async_f32(dst + lane, src + gk0);
+            if (lane + 32 < bp.E3) cp_async_f32(dst + lane + 32, src + gk1);
+            for (int c = lane + 64; c < bp.E3; c += 32) {
+                int gk = w3 + c;
+                gk = gk >= g.n3 ? gk - g.n3 : gk;
+                cp_async_f32(dst + c, src + gk);
+            }
+        }
+    }
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+// 32-bit shared-memory load at a byte address plus an immediate byte offset.
+template <int BYTE_OFF>
+__device__ __forceinline__ float lds_f32(uint32_t addr)
+{
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1+%2];\n" : "=f"(v) : "r"(addr), "n"(BYTE_OFF));
+    return v;
+}
+
+template <int ORDER>
+__device__ __forceinline__ float row_dot(uint32_t addr, const float w[4])
+{
+    if constexpr (ORDER == 3) {
+        float s = w[0] * lds_f32<0>(addr);
+        s = fmaf(w[1], lds_f32<4>(addr), s);
+        s = fmaf(w[2], lds_f32<8>(addr), s);
+        return fmaf(w[3], lds_f32<12>(addr), s);
+    } else {
+        return fmaf(w[1], lds_f32<4>(addr), w[0] * lds_f32<0>(addr));
+    }
+}
+
+// Stencil value at node (i, j, k) + (d1, d2, d3) from the box in shared memory.
+template <int ORDER>
+__device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, int i, int j, int k, float d1,
+                                           float d2, float d3)
+{
+    constexpr int M = (ORDER == 3) ? 4 : 2;
+    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    const int P = bp.E2 * bp.S3;
+    float t1, t2, t3, w1[4], w2[4], w3[4];
+    const int o = (i + split_disp(d1, t1) - OFF - bp.O1) * P +
+                  (j + split_disp(d2, t2) - OFF - bp.O2) * bp.S3 + (k + split_disp(d3, t3) - OFF - bp.O3);
+    axis_weights<ORDER>(t1, w1);
+    axis_weights<ORDER>(t2, w2);
+    axis_weights<ORDER>(t3, w3);
+    float val = 0.0f;
+#if CLAIRE_LDS_ASM
+    const uint32_t base = smem_u32(box) + 4u * static_cast<uint32_t>(o);
+    const uint32_t P4 = 4u * static_cast<uint32_t>(P), S4 = 4u * static_cast<uint32_t>(bp.S3);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float sa = 0.0f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) sa = fmaf(w2[b], row_dot<ORDER>(base + a * P4 + b * S4, w3), sa);
+        val = fmaf(w1[a], sa, val);
+    }
+#else
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float sa = 0.0f;
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const int row = o + a * P + b * bp.S3;
+            float sb = 0.0f;
+#pragma unroll
+            for (int c = 0; c < M; ++c) sb = fmaf(w3[c], box[row + c], sb);
+            sa = fmaf(w2[b], sb, sa);
+        }
+        val = fmaf(w1[a], sa, val);
+    }
+#endif
+    return val;
+}
+
+// Gather f at x + d for the CTA's tile and hand each value to the epilogue.
+//
+// Shared-memory layout of the box: element (a, b, c) at (a E2 + b) S3 + c
+// with the row stride S3 a multiple of 32 floats, so an element's bank is its
+// column mod 32 whatever its row: the 32 lanes of a warp (consecutive x3
+// arrivals, hence consecutive departure columns, but rows that vary with the
+// x1/x2 displacement) read 32 different banks.  The epilogue's operands are
+// requested (prefetch) while the box is in flight and consumed (finish) after
+// the stencil is evaluated.
+template <int ORDER, class Epi>
+__global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
+    k_gather_tiled(Grid g, const float* __restrict__ f, const float* __restrict__ d, Epi epi)
+{
+    extern __shared__ float box[];
+    __shared__ int red[6][TILE2];
+    __shared__ int par[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * TILE3 + lane;
+    const int j = blockIdx.y * TILE2 + warp;
+    const int i0 = blockIdx.z * TILE1;
+    const size_t N = g.N;
+    const bool col_ok = (k < g.n3) && (j < g.n2);
+    const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
+
+    float d1[TILE1], d2[TILE1], d3[TILE1];
+    int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < TILE1; ++q) {
+        if (col_ok && i0 + q < g.n1) {
+            const uint32_t p = p0 + q * g.n23;
+            d1[q] = __ldg(d + p);
+            d2[q] = __ldg(d + N + p);
+            d3[q] = __ldg(d + 2 * N + p);
+            float t;
+            const int b1 = i0 + q + split_disp(d1[q], t);
+            const int b2 = j + split_disp(d2[q], t);
+            const int b3 = k + split_disp(d3[q], t);
+            lo1 = min(lo1, b1); hi1 = max(hi1, b1);
+            lo2 = min(lo2, b2); hi2 = max(hi2, b2);
+            lo3 = min(lo3, b3); hi3 = max(hi3, b3);
+        }
+    }
+    const BoxPar bp = tile_box<ORDER>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
+    const bool use_box = bp.E1 != 0;
+    if (use_box) tile_load_box(g, f, box, bp, lane, warp);
+    // epilogue operands of every point are requested while the box is in flight
+    typename Epi::Pre pre[TILE1];
+#pragma unroll
+    for (int q = 0; q < TILE1; ++q)
+        if (col_ok && i0 + q < g.n1) pre[q] = epi.prefetch(p0 + q * g.n23);
+    if (use_box) {
+        cp_async_wait_all();
+        __syncthreads();
+    }
+#pragma unroll
+    for (int q = 0; q < TILE1; ++q) {
+        const int i = i0 + q;
+        if (!(col_ok && i < g.n1)) continue;
+        const float val = use_box ? tile_eval<ORDER>(box, bp, i, j, k, d1[q], d2[q], d3[q])
+                                  : gather_global<ORDER>(g, f, i, j, k, d1[q], d2[q], d3[q]);
+        epi.finish(p0 + q * g.n23, val, pre[q]);
+    }
+}
+
+inline dim3 tiled_grid(const Grid& g)
+{
+    return dim3((g.n3 + TILE3 - 1) / TILE3, (g.n2 + TILE2 - 1) / TILE2, (g.n1 + TILE1 - 1) / TILE1);
+}
+
+constexpr size_t kTiledSmemBytes = kBoxCapFloats * sizeof(float);
+
+template <int ORDER, class Epi>
+inline void launch_tiled(const Grid& g, const float* f, const float* d, const Epi& e, cudaStream_t st)
+{
+    if (kTiledSmemBytes > 48 * 1024)
+        cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kTiledSmemBytes));
+    k_gather_tiled<ORDER, Epi><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
+}
+
+// ---- epilogues: prefetch(p) loads the point's operands early, finish(p, v, pre) completes ----
+
+// plain interpolation / state step: out = f(X)
+struct EpiStore {
+    float* __restrict__ out;
+    struct Pre {};
+    __device__ __forceinline__ Pre prefetch(uint32_t) const { return Pre{}; }
+    __device__ __forceinline__ void finish(uint32_t p, float v, const Pre&) const { out[p] = v; }
+};
+
+// adjoint step (Eq. (4), Heun along X+) with b += w lambda grad m
+struct EpiAdjoint {
+    const float* __restrict__ divv;
+    const float* __restrict__ divXp;
+    const float* __restrict__ gm;
+    float* __restrict__ lam;
+    float* __restrict__ b;
+    float dt, w;
+    size_t N;
+    struct Pre {
+        float dX, dx, g0, g1, g2, b0, b1, b2;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const
+    {
+        Pre r;
+        r.dX = __ldg(divXp + p);
+        r.dx = __ldg(divv + p);
+        r.g0 = __ldg(gm + p);
+        r.g1 = __ldg(gm + N + p);
+        r.g2 = __ldg(gm + 2 * N + p);
+        r.b0 = b[p];
+        r.b1 = b[N + p];
+        r.b2 = b[2 * N + p];
+        return r;
+    }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        const float adX = a * r.dX;
+        const float pred = fmaf(dt, adX, a);
+        const float l = fmaf(0.5f * dt, fmaf(pred, r.dx, adX), a);
+        lam[p] = l;
+        const float wl = w * l;
+        b[p] = fmaf(wl, r.g0, r.b0);
+        b[N + p] = fmaf(wl, r.g1, r.b1);
+        b[2 * N + p] = fmaf(wl, r.g2, r.b2);
+    }
+};
+
+// adjoint step without the gradient body (transport of the adjoint alone)
+struct EpiAdjointOnly {
+    const float* __restrict__ divv;
+    const float* __restrict__ divXp;
+    float* __restrict__ lam;
+    float dt;
+    struct Pre {
+        float dX, dx;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{__ldg(divXp + p), __ldg(divv + p)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        const float adX = a * r.dX;
+        const float pred = fmaf(dt, adX, a);
+        lam[p] = fmaf(0.5f * dt, fmaf(pred, r.dx, adX), a);
+    }
+};
+
+__device__ __forceinline__ float neg_vt_dot_gm(const float* __restrict__ vt, const float* __restrict__ gm,
+                                               uint32_t p, size_t N)
+{
+    return -(__ldg(vt + p) * __ldg(gm + p) + __ldg(vt + N + p) * __ldg(gm + N + p) +
+             __ldg(vt + 2 * N + p) * __ldg(gm + 2 * N + p));
+}
+
+// incremental state: q = f(X) + coef (-vt . grad m)
+struct EpiIncremental {
+    const float* __restrict__ vt;
+    const float* __restrict__ gm;
+    float* __restrict__ q;
+    float coef;
+    size_t N;
+    struct Pre {
+        float src;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{neg_vt_dot_gm(vt, gm, p, N)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        q[p] = fmaf(coef, r.src, a);
+    }
+};
+
+// last incremental state step + start of the incremental adjoint:
+// lt = -(f(X) + coef (-vt . grad m)), b += w lt grad m
+struct EpiIncrementalLast {
+    const float* __restrict__ vt;
+    const float* __restrict__ gm;
+    float* __restrict__ lam;
+    float* __restrict__ b;
+    float coef, w;
+    size_t N;
+    struct Pre {
+        float src, g0, g1, g2, b0, b1, b2;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const
+    {
+        Pre r;
+        r.g0 = __ldg(gm + p);
+        r.g1 = __ldg(gm + N + p);
+        r.g2 = __ldg(gm + 2 * N + p);
+        r.src = -(__ldg(vt + p) * r.g0 + __ldg(vt + N + p) * r.g1 + __ldg(vt + 2 * N + p) * r.g2);
+        r.b0 = b[p];
+        r.b1 = b[N + p];
+        r.b2 = b[2 * N + p];
+        return r;
+    }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        const float l = -fmaf(coef, r.src, a);
+        lam[p] = l;
+        const float wl = w * l;
+        b[p] = fmaf(wl, r.g0, r.b0);
+        b[N + p] = fmaf(wl, r.g1, r.b1);
+        b[2 * N + p] = fmaf(wl, r.g2, r.b2);
+    }
+};
+
+}  // namespace claire

@@ -13,8 +13,67 @@ constexpr int kThreads = 256;
 
 __device__ __forceinline__ float2 cmul(float s, float2 z) { return make_float2(s * z.x, s * z.y); }
 
-// Symbol S(k) = a I + c u u^T with a = beta_v |k|^2 (H1) or beta_v |k|^4 (H2),
-// c = beta_w (1 + |k|^2) and u = k with Nyquist components set to zero.
+// Per-mode pieces of the symbol S(k) = a I + c u u^T on the half spectrum:
+// a = beta_v |k|^2 (H1) or beta_v |k|^4 (H2), c = beta_w (1 + |k|^2), u = k
+// with Nyquist components set to zero; wt = multiplicity of the mode in the
+// full spectrum (1 on the x3 = 0 and Nyquist planes, else 2).
+struct Mode {
+    float u1, u2, u3, a, c, kk, wt;
+};
+
+__device__ __forceinline__ Mode mode_of(const Grid& g, size_t idx, int n3h, const RegParams& rp)
+{
+    Mode m;
+    const int k3i = static_cast<int>(idx % n3h);
+    const size_t r = idx / n3h;
+    const int j = static_cast<int>(r % g.n2);
+    const int i = static_cast<int>(r / g.n2);
+    const float k1 = static_cast<float>(i <= g.n1 / 2 ? i : i - g.n1);
+    const float k2 = static_cast<float>(j <= g.n2 / 2 ? j : j - g.n2);
+    const float k3 = static_cast<float>(k3i);
+    m.kk = k1 * k1 + k2 * k2 + k3 * k3;
+    m.u1 = (2 * i == g.n1) ? 0.0f : k1;
+    m.u2 = (2 * j == g.n2) ? 0.0f : k2;
+    m.u3 = (2 * k3i == g.n3) ? 0.0f : k3;
+    m.a = rp.beta_v * (rp.reg == 2 ? m.kk * m.kk : m.kk);
+    m.c = rp.beta_w * (1.0f + m.kk);
+    m.wt = (k3i == 0 || 2 * k3i == g.n3) ? 1.0f : 2.0f;
+    return m;
+}
+
+// y = S x for one mode
+__device__ __forceinline__ void apply_S(const Mode& m, float2 x0, float2 x1, float2 x2, float2& y0,
+                                        float2& y1, float2& y2)
+{
+    const float2 ud = make_float2(m.u1 * x0.x + m.u2 * x1.x + m.u3 * x2.x,
+                                  m.u1 * x0.y + m.u2 * x1.y + m.u3 * x2.y);
+    y0 = make_float2(m.a * x0.x + m.c * m.u1 * ud.x, m.a * x0.y + m.c * m.u1 * ud.y);
+    y1 = make_float2(m.a * x1.x + m.c * m.u2 * ud.x, m.a * x1.y + m.c * m.u2 * ud.y);
+    y2 = make_float2(m.a * x2.x + m.c * m.u3 * ud.x, m.a * x2.y + m.c * m.u3 * ud.y);
+}
+
+// y = S^{-1} x (op SPEC_INV) or (a I)^{-1} x (op SPEC_AINV); identity at k = 0
+__device__ __forceinline__ void apply_inv(const Mode& m, int op, float2 x0, float2 x1, float2 x2,
+                                          float2& y0, float2& y1, float2& y2)
+{
+    if (m.kk == 0.0f) {
+        y0 = x0; y1 = x1; y2 = x2;
+        return;
+    }
+    const float ia = 1.0f / m.a;
+    if (op == SPEC_AINV) {
+        y0 = cmul(ia, x0); y1 = cmul(ia, x1); y2 = cmul(ia, x2);
+        return;
+    }
+    const float2 ud = make_float2(m.u1 * x0.x + m.u2 * x1.x + m.u3 * x2.x,
+                                  m.u1 * x0.y + m.u2 * x1.y + m.u3 * x2.y);
+    const float f = m.c / (m.a + m.c * (m.u1 * m.u1 + m.u2 * m.u2 + m.u3 * m.u3));
+    y0 = cmul(ia, make_float2(x0.x - f * m.u1 * ud.x, x0.y - f * m.u1 * ud.y));
+    y1 = cmul(ia, make_float2(x1.x - f * m.u2 * ud.x, x1.y - f * m.u2 * ud.y));
+    y2 = cmul(ia, make_float2(x2.x - f * m.u3 * ud.x, x2.y - f * m.u3 * ud.y));
+}
+
+// In place: xh <- scale * M(k) xh for the three half-spectra.
 __global__ void __launch_bounds__(kThreads) k_spectral(Grid g, float2* __restrict__ xh, size_t cs,
                                                         int op, RegParams rp, float scale)
 {
@@ -68,6 +127,66 @@ __global__ void __launch_bounds__(kThreads) k_spectral(Grid g, float2* __restric
         xh[idx] = cmul(scale, y0);
         xh[cs + idx] = cmul(scale, y1);
         xh[2 * cs + idx] = cmul(scale, y2);
+    }
+}
+
+// Preconditioner in Fourier space: zh = scale * M(k) rh in place (M = S^{-1}
+// or (a I)^{-1}) and block partial sums of sum_k wt Re(conj(rh) zh), which is
+// sum_x r(x) z(x) by Parseval (zh already carries the 1/N of the inverse FFT).
+__global__ void __launch_bounds__(kThreads) k_spectral_precond(Grid g, float2* __restrict__ xh, size_t cs,
+                                                                int op, RegParams rp, float scale,
+                                                                double* __restrict__ partials)
+{
+    const int n3h = g.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
+    double acc = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        const Mode m = mode_of(g, idx, n3h, rp);
+        const float2 x0 = xh[idx], x1 = xh[cs + idx], x2 = xh[2 * cs + idx];
+        float2 y0, y1, y2;
+        apply_inv(m, op, x0, x1, x2, y0, y1, y2);
+        y0 = cmul(scale, y0); y1 = cmul(scale, y1); y2 = cmul(scale, y2);
+        xh[idx] = y0;
+        xh[cs + idx] = y1;
+        xh[2 * cs + idx] = y2;
+        const float re = x0.x * y0.x + x0.y * y0.y + x1.x * y1.x + x1.y * y1.y + x2.x * y2.x + x2.y * y2.y;
+        acc += static_cast<double>(m.wt * re);
+    }
+    block_sum(acc, partials);
+}
+
+// PCG direction in Fourier space: ph = zh + beta ph (ph = zh when first),
+// copy ph -> cp (consumed by the inverse FFT that yields p), and zh <- S ph
+// (inverse FFT yields S p for the matvec).
+__global__ void __launch_bounds__(kThreads) k_spectral_direction(Grid g, float2* __restrict__ zh,
+                                                                  float2* __restrict__ ph,
+                                                                  float2* __restrict__ cp, size_t cs,
+                                                                  float beta, int first, RegParams rp)
+{
+    const int n3h = g.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        float2 p[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 z = zh[c * cs + idx];
+            if (first) {
+                p[c] = z;
+            } else {
+                const float2 o = ph[c * cs + idx];
+                p[c] = make_float2(fmaf(beta, o.x, z.x), fmaf(beta, o.y, z.y));
+            }
+            ph[c * cs + idx] = p[c];
+            cp[c * cs + idx] = p[c];
+        }
+        const Mode m = mode_of(g, idx, n3h, rp);
+        float2 y0, y1, y2;
+        apply_S(m, p[0], p[1], p[2], y0, y1, y2);
+        zh[idx] = y0;
+        zh[cs + idx] = y1;
+        zh[2 * cs + idx] = y2;
     }
 }
 
@@ -162,21 +281,48 @@ __global__ void __launch_bounds__(kThreads) k_final_minmax(const double* __restr
     block_minmax(lo, hi, out2, out2 + 1);
 }
 
+// The vector updates take a float4 path when every pointer is 16-byte aligned
+// (the context's buffers always are) and a scalar loop for the tail.
 __global__ void __launch_bounds__(kThreads) k_axpy(float a, const float* __restrict__ x,
                                                     float* __restrict__ y, size_t n)
 {
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
-    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n; i += stride)
-        y[i] = fmaf(a, x[i], y[i]);
+    const size_t t0 = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
+    size_t done = 0;
+    if (aligned16(x) && aligned16(y)) {
+        const size_t n4 = n / 4;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        float4* y4 = reinterpret_cast<float4*>(y);
+        for (size_t i = t0; i < n4; i += stride) {
+            const float4 u = __ldg(x4 + i);
+            float4 w = y4[i];
+            w.x = fmaf(a, u.x, w.x); w.y = fmaf(a, u.y, w.y); w.z = fmaf(a, u.z, w.z); w.w = fmaf(a, u.w, w.w);
+            y4[i] = w;
+        }
+        done = n4 * 4;
+    }
+    for (size_t i = done + t0; i < n; i += stride) y[i] = fmaf(a, x[i], y[i]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_xpay(const float* __restrict__ x, float a,
-                                                    const float* __restrict__ y,
-                                                    float* __restrict__ z, size_t n)
+                                                    const float* y, float* z, size_t n)
 {
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
-    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n; i += stride)
-        z[i] = fmaf(a, y[i], x[i]);
+    const size_t t0 = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
+    size_t done = 0;
+    if (aligned16(x) && aligned16(y) && aligned16(z)) {
+        const size_t n4 = n / 4;
+        const float4* x4 = reinterpret_cast<const float4*>(x);
+        const float4* y4 = reinterpret_cast<const float4*>(y);
+        float4* z4 = reinterpret_cast<float4*>(z);
+        for (size_t i = t0; i < n4; i += stride) {
+            const float4 u = __ldg(x4 + i);
+            const float4 v = y4[i];
+            z4[i] = make_float4(fmaf(a, v.x, u.x), fmaf(a, v.y, u.y), fmaf(a, v.z, u.z), fmaf(a, v.w, u.w));
+        }
+        done = n4 * 4;
+    }
+    for (size_t i = done + t0; i < n; i += stride) z[i] = fmaf(a, y[i], x[i]);
 }
 
 __global__ void __launch_bounds__(kThreads) k_pcg_update(float alpha, const float* __restrict__ p,
@@ -187,7 +333,28 @@ __global__ void __launch_bounds__(kThreads) k_pcg_update(float alpha, const floa
 {
     double acc = 0.0;
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
-    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n; i += stride) {
+    const size_t t0 = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
+    size_t done = 0;
+    if (aligned16(p) && aligned16(q) && aligned16(x) && aligned16(r)) {
+        const size_t n4 = n / 4;
+        const float4* p4 = reinterpret_cast<const float4*>(p);
+        const float4* q4 = reinterpret_cast<const float4*>(q);
+        float4* x4 = reinterpret_cast<float4*>(x);
+        float4* r4 = reinterpret_cast<float4*>(r);
+        for (size_t i = t0; i < n4; i += stride) {
+            const float4 pp = __ldg(p4 + i), qq = __ldg(q4 + i);
+            float4 xx = x4[i], rr = r4[i];
+            xx.x = fmaf(alpha, pp.x, xx.x); xx.y = fmaf(alpha, pp.y, xx.y);
+            xx.z = fmaf(alpha, pp.z, xx.z); xx.w = fmaf(alpha, pp.w, xx.w);
+            rr.x = fmaf(-alpha, qq.x, rr.x); rr.y = fmaf(-alpha, qq.y, rr.y);
+            rr.z = fmaf(-alpha, qq.z, rr.z); rr.w = fmaf(-alpha, qq.w, rr.w);
+            x4[i] = xx;
+            r4[i] = rr;
+            acc += static_cast<double>(rr.x * rr.x + rr.y * rr.y + rr.z * rr.z + rr.w * rr.w);
+        }
+        done = n4 * 4;
+    }
+    for (size_t i = done + t0; i < n; i += stride) {
         x[i] = fmaf(alpha, p[i], x[i]);
         const float ri = fmaf(-alpha, q[i], r[i]);
         r[i] = ri;
@@ -218,6 +385,22 @@ void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
     k_spectral<<<stream_blocks(M), kThreads, 0, st>>>(g, reinterpret_cast<float2*>(xh), cstride,
                                                      static_cast<int>(op), rp, scale);
+}
+
+void launch_spectral_precond(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op,
+                             RegParams rp, float scale, double* partials, int nblocks, cudaStream_t st)
+{
+    k_spectral_precond<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<float2*>(xh), cstride,
+                                                    static_cast<int>(op), rp, scale, partials);
+}
+
+void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph, cufftComplex* cp,
+                               size_t cstride, float beta, int first, RegParams rp, cudaStream_t st)
+{
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
+    k_spectral_direction<<<stream_blocks(M), kThreads, 0, st>>>(
+        g, reinterpret_cast<float2*>(zh), reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
+        cstride, beta, first, rp);
 }
 
 void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,

@@ -90,6 +90,26 @@ def test_interp_parity(env, n, order, cfl):
 
 
 @pytest.mark.parametrize("order", [3, 1])
+def test_interp_parity_random_displacement_fallback(env, order):
+    """Uniform random displacements (+-9 cells, no spatial smoothness) give
+    departure boxes larger than the shared-memory tile, so the kernel takes
+    its direct global-memory gather; one half of the domain is smooth so both
+    paths run in the same launch."""
+    torch, claire = env
+    n = (32, 40, 64)
+    rng = np.random.default_rng(11)
+    f = f32(rng.standard_normal(n))
+    d = f32(_disp(n, 3, 2.0))
+    d[:, : n[0] // 2] = rng.uniform(-9, 9, size=(3, n[0] // 2) + n[1:])
+    ctx = make_ctx(claire, torch, n)
+    out = torch.empty(n, device="cuda")
+    ctx.interp(dev(torch, f), dev(torch, d), out, order)
+    torch.cuda.synchronize()
+    ref = oracle.interp(f.astype(np.float64), d.astype(np.float64), order)
+    assert rel_linf(host(out), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("order", [3, 1])
 def test_interp_integer_shift_bit_exact(env, order):
     torch, claire = env
     n = (16, 12, 20)

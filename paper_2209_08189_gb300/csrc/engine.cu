@@ -80,10 +80,13 @@ struct claire_ctx {
     float *divv = nullptr, *divXp = nullptr;
     float *m = nullptr, *gm = nullptr;    // (nt+1) N and (nt+1) 3N
     float *l0 = nullptr, *l1 = nullptr;   // rolling scalar fields
+    float* tl = nullptr;                  // (nt+1) N: adjoint levels lambda^j / incremental sources f^j
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     cufftComplex* spec = nullptr;
     cufftComplex* phat = nullptr;         // PCG search direction in Fourier space
     cufftComplex* spec2 = nullptr;        // second transform buffer
+    cufftComplex* xh = nullptr;           // PCG solution, Fourier space
+    cufftComplex* rh = nullptr;           // PCG residual, Fourier space
     double* partials = nullptr;           // 2 * red_blocks
     double* dres = nullptr;               // device scalars
     double* hres = nullptr;               // pinned host scalars
@@ -226,10 +229,13 @@ size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, Layout* L)
     l.add(3 * (nt + 1) * N);  // gm
     l.add(N);                 // l0
     l.add(N);                 // l1
+    l.add((nt + 1) * N);      // tl
     for (int i = 0; i < 6; ++i) l.add(3 * N);  // g x r z p q
     l.add(6 * M);             // spec (3 complex half-spectra)
     l.add(6 * M);             // phat
     l.add(6 * M);             // spec2
+    l.add(6 * M);             // xh
+    l.add(6 * M);             // rh
     l.add(4 * red_blocks);    // partials (2 * red_blocks doubles)
     l.add(32);                // dres (16 doubles)
     return l.total;
@@ -434,20 +440,52 @@ double trap_w(const claire_ctx* c, int j) { return (j == 0 || j == c->nt) ? 0.5 
 
 // Set the linearisation point: characteristics, states m^j and grad m^j, S v,
 // objective pieces.  v (device) is copied into c->v unless it already is c->v.
-claire_status linearise(claire_ctx* c, const float* v)
+// With have_state the state characteristic X (c->dS) and the states
+// m^1..m^nt of this v are already in place (an accepted line-search trial).
+claire_status linearise(claire_ctx* c, const float* v, bool have_state = false)
 {
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
     c->have_lin = false;
     if (v != c->v)
         CL_CUDA(c, cudaMemcpyAsync(c->v, v, 3 * c->N * sizeof(float), cudaMemcpyDeviceToDevice,
                                    c->stream));
-    CL_TRY(characteristics(c, c->v, c->dS, c->dA, c->divv, c->divXp));
+    CL_TRY(characteristics(c, c->v, have_state ? nullptr : c->dS, c->dA, c->divv, c->divXp));
     {
         PhaseScope ps(c, CLAIRE_PHASE_STATE);
         CL_CUDA(c, cudaMemcpyAsync(c->m, c->m0, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
                                    c->stream));
-        for (int j = 0; j < c->nt; ++j) CL_TRY(interp(c, c->m + j * c->N, c->dS, c->m + (j + 1) * c->N));
+        if (!have_state)
+            for (int j = 0; j < c->nt; ++j) CL_TRY(interp(c, c->m + j * c->N, c->dS, c->m + (j + 1) * c->N));
         for (int j = 0; j <= c->nt; ++j) CL_TRY(fd8_grad(c, c->m + j * c->N, c->gm + 3 * j * c->N));
+    }
+    return CLAIRE_OK;
+}
+
+// Backward SL solve of Eq. (4) from lambda^{nt} = a - s (s may be null) into
+// the levels tl[j], then out += sum_j w_j lambda^j grad m^j (trapezoid).
+// The levels tl[1..nt] may hold the incremental sources on entry (consumed).
+claire_status adjoint_and_body(claire_ctx* c, const float* a, const float* s, float* out,
+                               bool accumulate = true)
+{
+    const size_t N = c->N;
+    const int nt = c->nt;
+    PhaseScope ps(c, CLAIRE_PHASE_ADJOINT);
+    if (a) {
+        KTimer t(c, KK_POINTWISE, 12.0 * N, 0);
+        launch_xpay(a, -1.0f, s, c->tl + nt * N, N, c->stream);
+        CL_LAUNCHED(c);
+    }
+    for (int j = nt - 1; j >= 0; --j) {
+        KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
+        launch_adj_step(c->grid, c->o.interp, c->tl + (j + 1) * N, c->dA, c->divv, c->divXp,
+                        static_cast<float>(c->dt), c->tl + j * N, c->stream);
+        CL_LAUNCHED(c);
+    }
+    {
+        KTimer t(c, KK_POINTWISE, (16.0 * (nt + 1) + 24.0) * N, 0);
+        launch_body(c->grid, c->tl, c->gm, nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt),
+                    accumulate ? 1 : 0, out, c->stream);
+        CL_LAUNCHED(c);
     }
     return CLAIRE_OK;
 }
@@ -466,25 +504,7 @@ claire_status gradient_at_lin(claire_ctx* c, float* g)
         launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 1, c->stream);
         CL_LAUNCHED(c);
     }
-    {
-        PhaseScope ps(c, CLAIRE_PHASE_ADJOINT);
-        float* lam = c->l0;
-        float* lnext = c->l1;
-        {
-            KTimer t(c, KK_POINTWISE, 48.0 * N, 0);
-            launch_adj_init(c->grid, c->m1, c->m + c->nt * N, static_cast<float>(trap_w(c, c->nt)),
-                            c->gm + 3 * c->nt * N, 1, lam, g, c->stream);
-            CL_LAUNCHED(c);
-        }
-        for (int j = c->nt - 1; j >= 0; --j) {
-            std::swap(lam, lnext);
-            KTimer t(c, KK_ADJ_STEP, 64.0 * N, 1.0 * N);
-            launch_adj_step(c->grid, c->o.interp, lnext, c->dA, c->divv, c->divXp,
-                            static_cast<float>(c->dt), static_cast<float>(trap_w(c, j)),
-                            c->gm + 3 * j * N, lam, g, c->stream);
-            CL_LAUNCHED(c);
-        }
-    }
+    CL_TRY(adjoint_and_body(c, c->m1, c->m + c->nt * N, g));
     if (c->o.grad_form == 1) CL_TRY(spectral(c, g, g, SPEC_K));
     CL_TRY(sync_scalars(c, 2));
     c->reg_lin = c->hres[0];
@@ -495,46 +515,41 @@ claire_status gradient_at_lin(claire_ctx* c, float* g)
     return CLAIRE_OK;
 }
 
-// H vt at the linearisation point into out (out != vt).  With s_in_out the
-// caller has already placed S vt in out.
-claire_status matvec(claire_ctx* c, const float* vt, float* out, bool s_in_out = false)
+// H vt at the linearisation point into out (out != vt).  body_only: out gets
+// only the transport part int lt grad m dt (no S vt, no K), for callers that
+// add the regulariser in Fourier space.
+claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only = false)
 {
     if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
     const size_t N = c->N;
     const int nt = c->nt;
     const float dt = static_cast<float>(c->dt);
-    if (!s_in_out) CL_TRY(spectral(c, vt, out, SPEC_REG));
-    PhaseScope ps(c, CLAIRE_PHASE_INCREMENTAL);
-    float* a = c->l0;
-    float* b = c->l1;
-    // incremental state: q^0 = dt/2 f^0, q^{j+1} = q^j(X) + dt f^{j+1}
+    if (!body_only) CL_TRY(spectral(c, vt, out, SPEC_REG));
     {
-        KTimer t(c, KK_POINTWISE, 28.0 * N, 0);
-        launch_inc_init(c->grid, vt, c->gm, 0.5f * dt, a, c->stream);
+        PhaseScope ps(c, CLAIRE_PHASE_INCREMENTAL);
+        // sources f^j = -vt . grad m^j; Heun: q^0 = dt/2 f^0, q^{j+1} = q^j(X) + dt f^{j+1},
+        // mt^{nt} = q^{nt-1}(X) + dt/2 f^{nt}, lt^{nt} = -mt^{nt}
+        float* a = c->l0;
+        float* b = c->l1;
+        {
+            KTimer t(c, KK_POINTWISE, (12.0 + 16.0 * (nt + 1)) * N, 0);
+            launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->stream);
+            CL_LAUNCHED(c);
+        }
+        for (int j = 0; j + 1 < nt; ++j) {
+            KTimer t(c, KK_INC_STEP, 24.0 * N, 1.0 * N);
+            launch_inc_step_src(c->grid, c->o.interp, a, c->dS, c->tl + (j + 1) * N, dt, b, c->stream);
+            CL_LAUNCHED(c);
+            std::swap(a, b);
+        }
+        KTimer t(c, KK_INC_LAST, 24.0 * N, 1.0 * N);
+        launch_inc_last_src(c->grid, c->o.interp, a, c->dS, c->tl + nt * N, 0.5f * dt, c->tl + nt * N,
+                            c->stream);
         CL_LAUNCHED(c);
     }
-    for (int j = 0; j + 1 < nt; ++j) {
-        KTimer t(c, KK_INC_STEP, 44.0 * N, 1.0 * N);
-        launch_inc_step(c->grid, c->o.interp, a, c->dS, vt, c->gm + 3 * (j + 1) * N, dt, b, c->stream);
-        CL_LAUNCHED(c);
-        std::swap(a, b);
-    }
-    {
-        KTimer t(c, KK_INC_LAST, 68.0 * N, 1.0 * N);
-        launch_inc_last(c->grid, c->o.interp, a, c->dS, vt, c->gm + 3 * nt * N, 0.5f * dt,
-                        static_cast<float>(trap_w(c, nt)), b, out, c->stream);
-        CL_LAUNCHED(c);
-    }
-    // incremental adjoint from lt^{nt} (in b), body accumulated into out
-    float* lam = b;
-    float* lnext = a;
-    for (int j = nt - 1; j >= 0; --j) {
-        std::swap(lam, lnext);
-        KTimer t(c, KK_ADJ_STEP, 64.0 * N, 1.0 * N);
-        launch_adj_step(c->grid, c->o.interp, lnext, c->dA, c->divv, c->divXp, dt,
-                        static_cast<float>(trap_w(c, j)), c->gm + 3 * j * N, lam, out, c->stream);
-        CL_LAUNCHED(c);
-    }
+    // incremental adjoint from lt^{nt} and body, accumulated onto S vt in out
+    CL_TRY(adjoint_and_body(c, nullptr, nullptr, out, !body_only));
+    if (body_only) return CLAIRE_OK;
     if (c->o.grad_form == 1) CL_TRY(spectral(c, out, out, SPEC_K));
     return CLAIRE_OK;
 }
@@ -545,18 +560,25 @@ claire_status precond(claire_ctx* c, const float* r, float* z)
 }
 
 // J(v) for a trial v (device, 3N); uses z (displacement), l0/l1, r (S v).
-claire_status objective_at(claire_ctx* c, const float* v, double* J, double* mis)
+// With into_state the characteristic and the states m^1..m^nt are written to
+// c->dS and c->m (the line search, once the linearisation point is spent),
+// so that an accepted trial seeds the next linearisation.
+claire_status objective_at(claire_ctx* c, const float* v, double* J, double* mis,
+                           bool into_state = false)
 {
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
     const size_t N = c->N;
     PhaseScope ps(c, CLAIRE_PHASE_OBJECTIVE);
-    CL_TRY(backtrace(c, v, c->z, +1));
+    float* d = into_state ? c->dS : c->z;
+    if (into_state) c->have_lin = false;
+    CL_TRY(backtrace(c, v, d, +1));
     const float* src = c->m0;
     float* a = c->l0;
     float* b = c->l1;
     for (int j = 0; j < c->nt; ++j) {
-        CL_TRY(interp(c, src, c->z, a));
-        src = a;
+        float* dst = into_state ? c->m + (j + 1) * N : a;
+        CL_TRY(interp(c, src, d, dst));
+        src = dst;
         std::swap(a, b);
     }
     CL_TRY(spectral(c, v, c->r, SPEC_REG));
@@ -622,102 +644,101 @@ claire_status cfl_of(claire_ctx* c, const float* v, double* cfl)
     return CLAIRE_OK;
 }
 
-// Preconditioned residual in Fourier space: spec <- M r^ (scaled for the
-// inverse transform); returns <r, M r> (discrete inner product) by Parseval.
-claire_status precond_spectral(claire_ctx* c, const float* r, double* rz)
+// Final sums of the two partial-sum arrays of a Fourier-space PCG kernel
+// into dres[0], dres[1] (scaled to discrete inner products), then synchronise.
+claire_status fs_sums(claire_ctx* c, int count)
 {
-    {
-        PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
-        {
-            KTimer t(c, KK_FFT, 0, 0);
-            CL_FFT(c, cufftExecR2C(c->r2c, const_cast<float*>(r), c->spec));
-        }
-        KTimer t(c, KK_SPECTRAL, 48.0 * c->M, 0, 2);
-        launch_spectral_precond(c->grid, c->spec, c->M, c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV, c->rp,
-                                static_cast<float>(1.0 / c->N), c->partials, c->red_blocks, c->stream);
-        launch_final_sum(c->partials, c->red_blocks, c->hvol, c->dres, c->stream);
-        CL_LAUNCHED(c);
-    }
-    CL_TRY(sync_scalars(c, 1));
-    *rz = c->hres[0];
-    if (!std::isfinite(*rz)) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG inner product");
-    return CLAIRE_OK;
-}
-
-// New search direction p^ = z^ + beta p^ in Fourier space; p and S p back in
-// real space (p into c->p, S p into c->z for the matvec).
-claire_status pcg_direction(claire_ctx* c, double beta, bool first)
-{
-    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
-    {
-        KTimer t(c, KK_SPECTRAL, 120.0 * c->M, 0);
-        launch_spectral_direction(c->grid, c->spec, c->phat, c->spec2, c->M, static_cast<float>(beta),
-                                  first ? 1 : 0, c->rp, c->stream);
-        CL_LAUNCHED(c);
-    }
-    KTimer t(c, KK_FFT, 0, 0, 2);
-    CL_FFT(c, cufftExecC2R(c->c2r, c->spec2, c->p));
-    CL_FFT(c, cufftExecC2R(c->c2r, c->spec, c->z));
+    const double scale = c->hvol * static_cast<double>(c->N);  // Parseval on scaled spectra
+    launch_final_sum(c->partials, c->red_blocks, scale, c->dres, c->stream);
+    if (count > 1) launch_final_sum(c->partials + c->red_blocks, c->red_blocks, scale, c->dres + 1, c->stream);
+    CL_LAUNCHED(c);
+    CL_TRY(sync_scalars(c, count));
+    for (int i = 0; i < count; ++i)
+        if (!std::isfinite(c->hres[i])) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG inner product");
     return CLAIRE_OK;
 }
 
 // Matrix-free PCG for H x = -g (x0 = 0), preconditioned by the spectral
-// inverse of the regulariser.  The search direction is carried in Fourier
-// space, so each iteration takes one forward and two inverse transforms
-// (residual in; direction and its regularisation out) and the matvec gets
-// S p without transforming p again.  Returns the iteration count in *its.
+// inverse of the regulariser.  x, r and the direction p live in Fourier
+// space (scaled half spectra); the preconditioner, the regulariser part of
+// H p and every inner product (Parseval) are spectral.  Each iteration takes
+// one inverse transform (p, for the transport solves) and one forward
+// transform (the transport part of H p).  Returns the iteration count in *its.
 claire_status pcg(claire_ctx* c, double eta, int* its)
 {
-    const size_t n3 = 3 * c->N;
+    const SpectralOp op = c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV;
+    const float scale = static_cast<float>(1.0 / c->N);
+    const double M = static_cast<double>(c->M);
     *its = 0;
     {
-        PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
-        CL_CUDA(c, cudaMemsetAsync(c->x, 0, n3 * sizeof(float), c->stream));
-        CL_CUDA(c, cudaMemsetAsync(c->r, 0, n3 * sizeof(float), c->stream));
-        KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
-        launch_axpy(-1.0f, c->g, c->r, n3, c->stream);
-        CL_LAUNCHED(c);
+        PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+        {
+            KTimer t(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecR2C(c->r2c, c->g, c->spec));
+        }
+        KTimer t(c, KK_SPECTRAL, 96.0 * M, 0, 3);
+        launch_fs_start(c->grid, c->spec, c->rh, c->xh, c->M, op, c->rp, scale, c->partials,
+                        c->partials + c->red_blocks, c->red_blocks, c->stream);
     }
-    double r0;
-    CL_TRY(dot(c, c->r, c->r, n3, &r0));
-    r0 = std::sqrt(r0);
-    if (r0 == 0.0) return CLAIRE_OK;
-    double rz;
-    CL_TRY(precond_spectral(c, c->r, &rz));
-    CL_TRY(pcg_direction(c, 0.0, true));
+    CL_TRY(fs_sums(c, 2));
+    const double r0 = std::sqrt(c->hres[0]);
+    double rz = c->hres[1];
+    if (r0 == 0.0) {
+        CL_CUDA(c, cudaMemsetAsync(c->x, 0, 3 * c->N * sizeof(float), c->stream));
+        return CLAIRE_OK;
+    }
+    double rz_prev = rz;
     for (int it = 1; it <= c->o.max_pcg; ++it) {
         *its = it;
-        CL_TRY(matvec(c, c->p, c->z, true));  // z: S p in, H p out
-        double pq;
-        CL_TRY(dot(c, c->p, c->z, n3, &pq));
+        {
+            PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+            {
+                KTimer t(c, KK_SPECTRAL, 120.0 * M, 0);
+                launch_spectral_direction(c->grid, c->spec, c->phat, c->spec2, c->M,
+                                          static_cast<float>(it == 1 ? 0.0 : rz / rz_prev), it == 1 ? 1 : 0,
+                                          c->rp, c->stream);
+                CL_LAUNCHED(c);
+            }
+            KTimer t(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecC2R(c->c2r, c->spec2, c->p));
+        }
+        CL_TRY(matvec(c, c->p, c->z, true));  // transport part of H p
+        {
+            PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+            {
+                KTimer t(c, KK_FFT, 0, 0);
+                CL_FFT(c, cufftExecR2C(c->r2c, c->z, c->spec2));
+            }
+            KTimer t(c, KK_SPECTRAL, 96.0 * M, 0, 2);
+            launch_fs_hp(c->grid, c->spec, c->spec2, c->phat, c->M, c->o.grad_form, c->rp, scale,
+                         c->partials, c->red_blocks, c->stream);
+        }
+        CL_TRY(fs_sums(c, 1));
+        const double pq = c->hres[0];
         if (pq <= 0.0) {
             if (it == 1)
-                CL_CUDA(c, cudaMemcpyAsync(c->x, c->p, n3 * sizeof(float), cudaMemcpyDeviceToDevice,
-                                           c->stream));
+                CL_CUDA(c, cudaMemcpyAsync(c->xh, c->phat, 3 * c->M * sizeof(cufftComplex),
+                                           cudaMemcpyDeviceToDevice, c->stream));
             break;
         }
         const double alpha = rz / pq;
-        double rr;
         {
             PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
-            {
-                KTimer t(c, KK_VECTOR, 24.0 * n3, 0, 2);
-                launch_pcg_update(static_cast<float>(alpha), c->p, c->z, c->x, c->r, n3,
-                                  c->partials, c->red_blocks, c->stream);
-                launch_final_sum(c->partials, c->red_blocks, c->hvol, c->dres, c->stream);
-                CL_LAUNCHED(c);
-            }
-            CL_TRY(sync_scalars(c, 1));
-            rr = c->hres[0];
+            KTimer t(c, KK_SPECTRAL, 144.0 * M, 0, 3);
+            launch_fs_update(c->grid, c->spec, c->phat, c->xh, c->rh, c->M, static_cast<float>(alpha), op,
+                             c->rp, c->partials, c->partials + c->red_blocks, c->red_blocks, c->stream);
         }
-        if (!std::isfinite(rr)) return fail(c, CLAIRE_ENONFINITE, "non-finite PCG residual");
+        CL_TRY(fs_sums(c, 2));
+        const double rr = c->hres[0];
         if (!c->o.pcg_fixed && std::sqrt(rr) <= eta * r0) break;
         if (it == c->o.max_pcg) break;
-        double rz_new;
-        CL_TRY(precond_spectral(c, c->r, &rz_new));
-        const double beta = rz_new / rz;
-        rz = rz_new;
-        CL_TRY(pcg_direction(c, beta, false));
+        rz_prev = rz;
+        rz = c->hres[1];
+    }
+    {
+        PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecC2R(c->c2r, c->xh, c->x));
     }
     return CLAIRE_OK;
 }
@@ -855,6 +876,7 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->gm = base + L.off[k++];
     c->l0 = base + L.off[k++];
     c->l1 = base + L.off[k++];
+    c->tl = base + L.off[k++];
     c->g = base + L.off[k++];
     c->x = base + L.off[k++];
     c->r = base + L.off[k++];
@@ -864,6 +886,8 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->spec = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->phat = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->spec2 = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
+    c->xh = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
+    c->rh = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->partials = reinterpret_cast<double*>(base + L.off[k++]);
     c->dres = reinterpret_cast<double*>(base + L.off[k++]);
     if (cudaMemset(c->dres, 0, 16 * sizeof(double)) != cudaSuccess) {
@@ -1024,7 +1048,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
                 CL_LAUNCHED(c);
             }
             double Jt;
-            CL_TRY(objective_at(c, c->p, &Jt, nullptr));
+            CL_TRY(objective_at(c, c->p, &Jt, nullptr, true));
             if (Jt <= c->J_lin + c->o.armijo_c1 * alpha * gtx) {
                 ok = true;
                 break;
@@ -1043,7 +1067,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
             CL_LAUNCHED(c);
         }
         R.gn_iters = k + 1;
-        CL_TRY(linearise(c, c->v));
+        CL_TRY(linearise(c, c->v, true));  // c->v equals the accepted trial c->p bit for bit
         CL_TRY(gradient_at_lin(c, c->g));
         CL_TRY(dot(c, c->g, c->g, n3, &gn));
         rel = std::sqrt(gn) / g0;
@@ -1113,8 +1137,8 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
         CL_TRY(characteristics(c, dv, nullptr, c->z, divv, divXp));
         for (int j = 0; j < c->nt; ++j) {
             KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
-            launch_adj_step(c->grid, c->o.interp, src, c->z, divv, divXp, static_cast<float>(c->dt), 0.0f,
-                            nullptr, a, nullptr, c->stream);
+            launch_adj_step(c->grid, c->o.interp, src, c->z, divv, divXp, static_cast<float>(c->dt), a,
+                            c->stream);
             CL_LAUNCHED(c);
             src = a;
             std::swap(a, b);

@@ -73,19 +73,20 @@ void launch_interp(const Grid& g, int order, const float* f, const float* d, flo
                    cudaStream_t st);
 void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
                       cudaStream_t st);
-void launch_adj_init(const Grid& g, const float* a, const float* s, float w, const float* gm,
-                     int accumulate, float* lam, float* b, cudaStream_t st);
+// One SL step of Eq. (4): lam = Heun(lam_next(X+), div v(X+), div v).
 void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
-                     const float* divv, const float* divXp, float dt, float w, const float* gm,
-                     float* lam, float* b, cudaStream_t st);
-void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef, float* q,
-                     cudaStream_t st);
-void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float* q, cudaStream_t st);
-// last incremental state step; accumulates w lt grad m into b
-void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float w, float* lam, float* b,
-                     cudaStream_t st);
+                     const float* divv, const float* divXp, float dt, float* lam, cudaStream_t st);
+// f^j = -vt . grad m^j for j = 0..nt: q0 = coef0 f^0, F + j N <- f^j (j >= 1).
+void launch_inc_sources(const Grid& g, const float* vt, const float* gm, int nt, float coef0, float* q0,
+                        float* F, cudaStream_t st);
+// out (+)= sum_j w_j lam^j grad m^j (lam slots j N, trapezoid weights w_end / w_mid).
+void launch_body(const Grid& g, const float* lam, const float* gm, int nt, float w_end, float w_mid,
+                 int accumulate, float* out, cudaStream_t st);
+// q = q_prev(X) + coef F;   lam = -(q_prev(X) + coef F)  (F may alias lam)
+void launch_inc_step_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
+                         float coef, float* q, cudaStream_t st);
+void launch_inc_last_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
+                         float coef, float* lam, cudaStream_t st);
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
                      cudaStream_t st);
 void launch_fd8_grad(const Grid& g, const float* f, float* out, cudaStream_t st);
@@ -114,6 +115,20 @@ void launch_spectral_precond(const Grid& g, cufftComplex* xh, size_t cstride, Sp
 // PCG direction in Fourier space: ph = zh + beta ph (first: ph = zh), cp = ph, zh <- S ph.
 void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph, cufftComplex* cp,
                                size_t cstride, float beta, int first, RegParams rp, cudaStream_t st);
+
+// Fourier-space PCG (vectors are half spectra scaled by 1/N; partial sums are
+// of sum_k wt Re(conj(a) b), wt the multiplicity of the mode):
+//   start:  r~ = -scale spec, x~ = 0, spec <- M r~;  partials |r~|^2 (prr), <r~, M r~> (prz)
+//   hp:     spec <- spec + scale spec2 (K applied if kform);  partials <p~, H p~>
+//   update: x~ += alpha p~, r~ -= alpha spec, spec <- M r~;  partials as in start
+void launch_fs_start(const Grid& g, cufftComplex* spec, cufftComplex* rh, cufftComplex* xh, size_t cs,
+                     SpectralOp op, RegParams rp, float scale, double* prr, double* prz, int nblocks,
+                     cudaStream_t st);
+void launch_fs_hp(const Grid& g, cufftComplex* spec, const cufftComplex* spec2, const cufftComplex* ph,
+                  size_t cs, int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st);
+void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph, cufftComplex* xh,
+                      cufftComplex* rh, size_t cs, float alpha, SpectralOp op, RegParams rp, double* prr,
+                      double* prz, int nblocks, cudaStream_t st);
 
 // Deterministic FP64 reductions: partial sums per block, then a one-block
 // final sum in fixed order.  `partials` holds at least nblocks doubles.

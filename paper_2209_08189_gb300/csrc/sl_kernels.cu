@@ -43,42 +43,53 @@ __global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __r
     d[2 * N + p] = c * (u3 + vs[2] * g.ih3);
 }
 
-// Start of the backward solve at t = 1: lambda = a - s (s may be null),
-// b = (accumulate ? b : 0) + w lambda grad m.
-__global__ void __launch_bounds__(kThreads) k_adj_init(Grid g, const float* __restrict__ a,
-                                                        const float* __restrict__ s, float w,
-                                                        const float* __restrict__ gm, int accumulate,
-                                                        float* __restrict__ lam, float* __restrict__ b)
+// Sources of the incremental state for every time level at once:
+// f^j = -vt . grad m^j; q0 = coef0 f^0 starts the Heun recursion and
+// f^1..f^nt go to F (slot j at F + j N).
+__global__ void __launch_bounds__(kThreads) k_inc_sources(Grid g, const float* __restrict__ vt,
+                                                           const float* __restrict__ gm, int nt,
+                                                           float coef0, float* __restrict__ q0,
+                                                           float* __restrict__ F)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
     const size_t N = g.N;
-    const float l = s ? a[p] - s[p] : a[p];
-    lam[p] = l;
-    const float wl = w * l;
-#pragma unroll
-    for (int c = 0; c < 3; ++c) {
-        const float b0 = accumulate ? b[c * N + p] : 0.0f;
-        b[c * N + p] = fmaf(wl, __ldg(gm + c * N + p), b0);
+    const float v0 = __ldg(vt + p), v1 = __ldg(vt + N + p), v2 = __ldg(vt + 2 * N + p);
+    for (int j = 0; j <= nt; ++j) {
+        const float* gj = gm + 3 * j * N;
+        const float f = -(v0 * __ldg(gj + p) + v1 * __ldg(gj + N + p) + v2 * __ldg(gj + 2 * N + p));
+        if (j == 0)
+            q0[p] = coef0 * f;
+        else
+            F[j * N + p] = f;
     }
 }
 
-// Incremental state source f = -vt . grad m.
-__device__ __forceinline__ float inc_source(const float* __restrict__ vt, const float* __restrict__ gm,
-                                            uint32_t p, size_t N)
-{
-    return -(__ldg(vt + p) * __ldg(gm + p) + __ldg(vt + N + p) * __ldg(gm + N + p) +
-             __ldg(vt + 2 * N + p) * __ldg(gm + 2 * N + p));
-}
-
-// q^0 = coef * f^0
-__global__ void __launch_bounds__(kThreads) k_inc_init(Grid g, const float* __restrict__ vt,
-                                                        const float* __restrict__ gm, float coef,
-                                                        float* __restrict__ q)
+// Gradient body by trapezoid in time, added to out:
+// out_c (+)= sum_j w_j lambda^j grad_c m^j, w_0 = w_nt = w_end, else w_mid.
+__global__ void __launch_bounds__(kThreads) k_body(Grid g, const float* __restrict__ lam,
+                                                    const float* __restrict__ gm, int nt, float w_end,
+                                                    float w_mid, int accumulate, float* __restrict__ out)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
-    q[p] = coef * inc_source(vt, gm, p, g.N);
+    const size_t N = g.N;
+    float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+    for (int j = 0; j <= nt; ++j) {
+        const float wl = (j == 0 || j == nt ? w_end : w_mid) * __ldg(lam + j * N + p);
+        const float* gj = gm + 3 * j * N;
+        b0 = fmaf(wl, __ldg(gj + p), b0);
+        b1 = fmaf(wl, __ldg(gj + N + p), b1);
+        b2 = fmaf(wl, __ldg(gj + 2 * N + p), b2);
+    }
+    if (accumulate) {
+        b0 += out[p];
+        b1 += out[N + p];
+        b2 += out[2 * N + p];
+    }
+    out[p] = b0;
+    out[N + p] = b1;
+    out[2 * N + p] = b2;
 }
 
 // Deformation map step: u^{j+1} = u^j(X) + (X - x), three components.
@@ -214,56 +225,46 @@ void launch_backtrace(const Grid& g, int order, const float* v, float dt, int si
     CLAIRE_DISPATCH(order, k_backtrace, g, v, dt, static_cast<float>(sign), d);
 }
 
-void launch_adj_init(const Grid& g, const float* a, const float* s, float w, const float* gm,
-                     int accumulate, float* lam, float* b, cudaStream_t st)
-{
-    k_adj_init<<<blocks_for(g.N), kThreads, 0, st>>>(g, a, s, w, gm, accumulate, lam, b);
-}
-
 void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
-                     const float* divv, const float* divXp, float dt, float w, const float* gm,
-                     float* lam, float* b, cudaStream_t st)
+                     const float* divv, const float* divXp, float dt, float* lam, cudaStream_t st)
 {
-    if (gm) {
-        EpiAdjoint e{divv, divXp, gm, lam, b, dt, w, g.N};
-        if (order == 3)
-            launch_tiled<3, EpiAdjoint>(g, lam_next, dA, e, st);
-        else
-            launch_tiled<1, EpiAdjoint>(g, lam_next, dA, e, st);
-    } else {
-        EpiAdjointOnly e{divv, divXp, lam, dt};
-        if (order == 3)
-            launch_tiled<3, EpiAdjointOnly>(g, lam_next, dA, e, st);
-        else
-            launch_tiled<1, EpiAdjointOnly>(g, lam_next, dA, e, st);
-    }
-}
-
-void launch_inc_init(const Grid& g, const float* vt, const float* gm, float coef, float* q,
-                     cudaStream_t st)
-{
-    k_inc_init<<<blocks_for(g.N), kThreads, 0, st>>>(g, vt, gm, coef, q);
-}
-
-void launch_inc_step(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float* q, cudaStream_t st)
-{
-    EpiIncremental e{vt, gm, q, coef, g.N};
+    EpiAdjointOnly e{divv, divXp, lam, dt};
     if (order == 3)
-        launch_tiled<3, EpiIncremental>(g, q_prev, d, e, st);
+        launch_tiled<3, EpiAdjointOnly>(g, lam_next, dA, e, st);
     else
-        launch_tiled<1, EpiIncremental>(g, q_prev, d, e, st);
+        launch_tiled<1, EpiAdjointOnly>(g, lam_next, dA, e, st);
 }
 
-void launch_inc_last(const Grid& g, int order, const float* q_prev, const float* d, const float* vt,
-                     const float* gm, float coef, float w, float* lam, float* b,
-                     cudaStream_t st)
+void launch_inc_sources(const Grid& g, const float* vt, const float* gm, int nt, float coef0, float* q0,
+                        float* F, cudaStream_t st)
 {
-    EpiIncrementalLast e{vt, gm, lam, b, coef, w, g.N};
+    k_inc_sources<<<blocks_for(g.N), kThreads, 0, st>>>(g, vt, gm, nt, coef0, q0, F);
+}
+
+void launch_body(const Grid& g, const float* lam, const float* gm, int nt, float w_end, float w_mid,
+                 int accumulate, float* out, cudaStream_t st)
+{
+    k_body<<<blocks_for(g.N), kThreads, 0, st>>>(g, lam, gm, nt, w_end, w_mid, accumulate, out);
+}
+
+void launch_inc_step_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
+                         float coef, float* q, cudaStream_t st)
+{
+    EpiIncSource e{F, q, coef};
     if (order == 3)
-        launch_tiled<3, EpiIncrementalLast>(g, q_prev, d, e, st);
+        launch_tiled<3, EpiIncSource>(g, q_prev, d, e, st);
     else
-        launch_tiled<1, EpiIncrementalLast>(g, q_prev, d, e, st);
+        launch_tiled<1, EpiIncSource>(g, q_prev, d, e, st);
+}
+
+void launch_inc_last_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
+                         float coef, float* lam, cudaStream_t st)
+{
+    EpiIncSourceLast e{F, lam, coef};
+    if (order == 3)
+        launch_tiled<3, EpiIncSourceLast>(g, q_prev, d, e, st);
+    else
+        launch_tiled<1, EpiIncSourceLast>(g, q_prev, d, e, st);
 }
 
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,

@@ -26,6 +26,9 @@ namespace claire {
 #define CLAIRE_TILE_MIN_BLOCKS 4  // resident CTAs per SM the register budget targets
 #endif
 
+#ifndef CLAIRE_FFMA2
+#define CLAIRE_FFMA2 1  // packed FP32x2 FMA (sm_100+) for the separable stencil contraction
+#endif
 #ifndef CLAIRE_LDS_ASM
 #define CLAIRE_LDS_ASM 1  // explicit 32-bit ld.shared with immediate offsets for the stencil reads
 #endif
@@ -182,6 +185,15 @@ __device__ __forceinline__ float row_dot(uint32_t addr, const float w[4])
 }
 
 // Stencil value at node (i, j, k) + (d1, d2, d3) from the box in shared memory.
+// Split of a displacement known to be finite and within the box (the bounds
+// pass already clamped every value of the tile): floor and fraction.
+__device__ __forceinline__ int split_in_box(float d, float& t)
+{
+    const int fl = __float2int_rd(d);
+    t = d - static_cast<float>(fl);
+    return fl;
+}
+
 template <int ORDER>
 __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, int i, int j, int k, float d1,
                                            float d2, float d3)
@@ -190,13 +202,35 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
     constexpr int OFF = (ORDER == 3) ? 1 : 0;
     const int P = bp.E2 * bp.S3;
     float t1, t2, t3, w1[4], w2[4], w3[4];
-    const int o = (i + split_disp(d1, t1) - OFF - bp.O1) * P +
-                  (j + split_disp(d2, t2) - OFF - bp.O2) * bp.S3 + (k + split_disp(d3, t3) - OFF - bp.O3);
+    const int o = (i + split_in_box(d1, t1) - OFF - bp.O1) * P +
+                  (j + split_in_box(d2, t2) - OFF - bp.O2) * bp.S3 +
+                  (k + split_in_box(d3, t3) - OFF - bp.O3);
     axis_weights<ORDER>(t1, w1);
     axis_weights<ORDER>(t2, w2);
     axis_weights<ORDER>(t3, w3);
     float val = 0.0f;
-#if CLAIRE_LDS_ASM
+#if CLAIRE_FFMA2
+    // rows b and b+1 of plane a are contracted along x3 together in one
+    // packed FMA per node; then the x2 weights pair up the same way
+    const uint32_t base = smem_u32(box) + 4u * static_cast<uint32_t>(o);
+    const uint32_t P4 = 4u * static_cast<uint32_t>(P), S4 = 4u * static_cast<uint32_t>(bp.S3);
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float2 acc = make_float2(0.0f, 0.0f);
+#pragma unroll
+        for (int b = 0; b < M; b += 2) {
+            const uint32_t r0 = base + a * P4 + b * S4, r1 = r0 + S4;
+            float2 sb = make_float2(w3[0] * lds_f32<0>(r0), w3[0] * lds_f32<0>(r1));
+            sb = __ffma2_rn(make_float2(w3[1], w3[1]), make_float2(lds_f32<4>(r0), lds_f32<4>(r1)), sb);
+            if constexpr (ORDER == 3) {
+                sb = __ffma2_rn(make_float2(w3[2], w3[2]), make_float2(lds_f32<8>(r0), lds_f32<8>(r1)), sb);
+                sb = __ffma2_rn(make_float2(w3[3], w3[3]), make_float2(lds_f32<12>(r0), lds_f32<12>(r1)), sb);
+            }
+            acc = __ffma2_rn(make_float2(w2[b], w2[b + 1]), sb, acc);
+        }
+        val = fmaf(w1[a], acc.x + acc.y, val);
+    }
+#elif CLAIRE_LDS_ASM
     const uint32_t base = smem_u32(box) + 4u * static_cast<uint32_t>(o);
     const uint32_t P4 = 4u * static_cast<uint32_t>(P), S4 = 4u * static_cast<uint32_t>(bp.S3);
 #pragma unroll
@@ -314,45 +348,7 @@ struct EpiStore {
     __device__ __forceinline__ void finish(uint32_t p, float v, const Pre&) const { out[p] = v; }
 };
 
-// adjoint step (Eq. (4), Heun along X+) with b += w lambda grad m
-struct EpiAdjoint {
-    const float* __restrict__ divv;
-    const float* __restrict__ divXp;
-    const float* __restrict__ gm;
-    float* __restrict__ lam;
-    float* __restrict__ b;
-    float dt, w;
-    size_t N;
-    struct Pre {
-        float dX, dx, g0, g1, g2, b0, b1, b2;
-    };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const
-    {
-        Pre r;
-        r.dX = __ldg(divXp + p);
-        r.dx = __ldg(divv + p);
-        r.g0 = __ldg(gm + p);
-        r.g1 = __ldg(gm + N + p);
-        r.g2 = __ldg(gm + 2 * N + p);
-        r.b0 = b[p];
-        r.b1 = b[N + p];
-        r.b2 = b[2 * N + p];
-        return r;
-    }
-    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
-    {
-        const float adX = a * r.dX;
-        const float pred = fmaf(dt, adX, a);
-        const float l = fmaf(0.5f * dt, fmaf(pred, r.dx, adX), a);
-        lam[p] = l;
-        const float wl = w * l;
-        b[p] = fmaf(wl, r.g0, r.b0);
-        b[N + p] = fmaf(wl, r.g1, r.b1);
-        b[2 * N + p] = fmaf(wl, r.g2, r.b2);
-    }
-};
-
-// adjoint step without the gradient body (transport of the adjoint alone)
+// adjoint step (Eq. (4), Heun along X+): lambda^j from lambda^{j+1}(X+)
 struct EpiAdjointOnly {
     const float* __restrict__ divv;
     const float* __restrict__ divXp;
@@ -370,63 +366,28 @@ struct EpiAdjointOnly {
     }
 };
 
-__device__ __forceinline__ float neg_vt_dot_gm(const float* __restrict__ vt, const float* __restrict__ gm,
-                                               uint32_t p, size_t N)
-{
-    return -(__ldg(vt + p) * __ldg(gm + p) + __ldg(vt + N + p) * __ldg(gm + N + p) +
-             __ldg(vt + 2 * N + p) * __ldg(gm + 2 * N + p));
-}
-
-// incremental state: q = f(X) + coef (-vt . grad m)
-struct EpiIncremental {
-    const float* __restrict__ vt;
-    const float* __restrict__ gm;
+// incremental state with precomputed source: q = f(X) + coef F
+struct EpiIncSource {
+    const float* __restrict__ F;
     float* __restrict__ q;
     float coef;
-    size_t N;
     struct Pre {
-        float src;
+        float f;
     };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{neg_vt_dot_gm(vt, gm, p, N)}; }
-    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
-    {
-        q[p] = fmaf(coef, r.src, a);
-    }
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{__ldg(F + p)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const { q[p] = fmaf(coef, r.f, a); }
 };
 
-// last incremental state step + start of the incremental adjoint:
-// lt = -(f(X) + coef (-vt . grad m)), b += w lt grad m
-struct EpiIncrementalLast {
-    const float* __restrict__ vt;
-    const float* __restrict__ gm;
-    float* __restrict__ lam;
-    float* __restrict__ b;
-    float coef, w;
-    size_t N;
+// last incremental state step, start of the incremental adjoint: lt = -(f(X) + coef F)
+struct EpiIncSourceLast {
+    const float* F;  // may alias lam: each point reads its F before writing lam
+    float* lam;
+    float coef;
     struct Pre {
-        float src, g0, g1, g2, b0, b1, b2;
+        float f;
     };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const
-    {
-        Pre r;
-        r.g0 = __ldg(gm + p);
-        r.g1 = __ldg(gm + N + p);
-        r.g2 = __ldg(gm + 2 * N + p);
-        r.src = -(__ldg(vt + p) * r.g0 + __ldg(vt + N + p) * r.g1 + __ldg(vt + 2 * N + p) * r.g2);
-        r.b0 = b[p];
-        r.b1 = b[N + p];
-        r.b2 = b[2 * N + p];
-        return r;
-    }
-    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
-    {
-        const float l = -fmaf(coef, r.src, a);
-        lam[p] = l;
-        const float wl = w * l;
-        b[p] = fmaf(wl, r.g0, r.b0);
-        b[N + p] = fmaf(wl, r.g1, r.b1);
-        b[2 * N + p] = fmaf(wl, r.g2, r.b2);
-    }
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{F[p]}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const { lam[p] = -fmaf(coef, r.f, a); }
 };
 
 }  // namespace claire

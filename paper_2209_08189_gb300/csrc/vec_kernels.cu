@@ -190,6 +190,140 @@ __global__ void __launch_bounds__(kThreads) k_spectral_direction(Grid g, float2*
     }
 }
 
+// ---- PCG carried entirely in Fourier space ----
+// Vectors are scaled half-spectra u~ = F[u] / N, so that the unnormalised
+// inverse FFT returns u and sum_x u(x) w(x) = N sum_k wt Re(conj(u~) w~)
+// (Parseval on the half spectrum; wt = multiplicity of the mode).
+
+__device__ __forceinline__ void block_sum2(double a, double b, double* pa, double* pb)
+{
+    __shared__ double sa[32], sb[32];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        a += __shfl_down_sync(0xffffffffu, a, o);
+        b += __shfl_down_sync(0xffffffffu, b, o);
+    }
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    if (lane == 0) {
+        sa[wid] = a;
+        sb[wid] = b;
+    }
+    __syncthreads();
+    if (wid == 0) {
+        const int nw = (blockDim.x + 31) >> 5;
+        double x = lane < nw ? sa[lane] : 0.0;
+        double y = lane < nw ? sb[lane] : 0.0;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+            x += __shfl_down_sync(0xffffffffu, x, o);
+            y += __shfl_down_sync(0xffffffffu, y, o);
+        }
+        if (lane == 0) {
+            pa[blockIdx.x] = x;
+            pb[blockIdx.x] = y;
+        }
+    }
+}
+
+__device__ __forceinline__ float cdot3(float2 a0, float2 a1, float2 a2, float2 b0, float2 b1, float2 b2)
+{
+    return a0.x * b0.x + a0.y * b0.y + a1.x * b1.x + a1.y * b1.y + a2.x * b2.x + a2.y * b2.y;
+}
+
+// Start: r~ = -scale g^ (spec holds F[g]), x~ = 0, z~ = M r~ (into spec);
+// partials of |r~|^2 and <r~, z~>.
+__global__ void __launch_bounds__(kThreads) k_fs_start(Grid g, float2* __restrict__ spec,
+                                                        float2* __restrict__ rh, float2* __restrict__ xh,
+                                                        size_t cs, int op, RegParams rp, float scale,
+                                                        double* __restrict__ prr, double* __restrict__ prz)
+{
+    const int n3h = g.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
+    double arr = 0.0, arz = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        const Mode m = mode_of(g, idx, n3h, rp);
+        const float2 r0 = cmul(-scale, spec[idx]), r1 = cmul(-scale, spec[cs + idx]),
+                     r2 = cmul(-scale, spec[2 * cs + idx]);
+        float2 z0, z1, z2;
+        apply_inv(m, op, r0, r1, r2, z0, z1, z2);
+        rh[idx] = r0; rh[cs + idx] = r1; rh[2 * cs + idx] = r2;
+        xh[idx] = make_float2(0.f, 0.f); xh[cs + idx] = make_float2(0.f, 0.f); xh[2 * cs + idx] = make_float2(0.f, 0.f);
+        spec[idx] = z0; spec[cs + idx] = z1; spec[2 * cs + idx] = z2;
+        arr += static_cast<double>(m.wt * cdot3(r0, r1, r2, r0, r1, r2));
+        arz += static_cast<double>(m.wt * cdot3(r0, r1, r2, z0, z1, z2));
+    }
+    block_sum2(arr, arz, prr, prz);
+}
+
+// H p~ = S p~ (in spec) + scale F[body] (in spec2), or K of that for the
+// paper's gradient form; written into spec; partials of <p~, H p~>.
+__global__ void __launch_bounds__(kThreads) k_fs_hp(Grid g, float2* __restrict__ spec,
+                                                     const float2* __restrict__ spec2,
+                                                     const float2* __restrict__ ph, size_t cs, int kform,
+                                                     RegParams rp, float scale, double* __restrict__ ppq)
+{
+    const int n3h = g.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
+    double acc = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        float2 h[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 sp = spec[c * cs + idx], b = spec2[c * cs + idx];
+            h[c] = make_float2(fmaf(scale, b.x, sp.x), fmaf(scale, b.y, sp.y));
+        }
+        const Mode m = mode_of(g, idx, n3h, rp);
+        if (kform && m.kk != 0.0f) {
+            const float2 ud = make_float2(m.u1 * h[0].x + m.u2 * h[1].x + m.u3 * h[2].x,
+                                          m.u1 * h[0].y + m.u2 * h[1].y + m.u3 * h[2].y);
+            const float f = m.c / (m.a + m.c * (m.u1 * m.u1 + m.u2 * m.u2 + m.u3 * m.u3));
+            h[0] = make_float2(h[0].x - f * m.u1 * ud.x, h[0].y - f * m.u1 * ud.y);
+            h[1] = make_float2(h[1].x - f * m.u2 * ud.x, h[1].y - f * m.u2 * ud.y);
+            h[2] = make_float2(h[2].x - f * m.u3 * ud.x, h[2].y - f * m.u3 * ud.y);
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) spec[c * cs + idx] = h[c];
+        acc += static_cast<double>(m.wt * cdot3(ph[idx], ph[cs + idx], ph[2 * cs + idx], h[0], h[1], h[2]));
+    }
+    block_sum(acc, ppq);
+}
+
+// x~ += alpha p~, r~ -= alpha H p~ (H p~ in spec), then z~ = M r~ into spec;
+// partials of |r~|^2 and <r~, z~>.
+__global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, float2* __restrict__ spec,
+                                                         const float2* __restrict__ ph,
+                                                         float2* __restrict__ xh, float2* __restrict__ rh,
+                                                         size_t cs, float alpha, int op, RegParams rp,
+                                                         double* __restrict__ prr, double* __restrict__ prz)
+{
+    const int n3h = g.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
+    double arr = 0.0, arz = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        float2 r[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 p = ph[c * cs + idx], hp = spec[c * cs + idx];
+            float2 x = xh[c * cs + idx], rr = rh[c * cs + idx];
+            x = make_float2(fmaf(alpha, p.x, x.x), fmaf(alpha, p.y, x.y));
+            rr = make_float2(fmaf(-alpha, hp.x, rr.x), fmaf(-alpha, hp.y, rr.y));
+            xh[c * cs + idx] = x;
+            rh[c * cs + idx] = rr;
+            r[c] = rr;
+        }
+        const Mode m = mode_of(g, idx, n3h, rp);
+        float2 z0, z1, z2;
+        apply_inv(m, op, r[0], r[1], r[2], z0, z1, z2);
+        spec[idx] = z0; spec[cs + idx] = z1; spec[2 * cs + idx] = z2;
+        arr += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], r[0], r[1], r[2]));
+        arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z0, z1, z2));
+    }
+    block_sum2(arr, arz, prr, prz);
+}
+
 __device__ __forceinline__ bool aligned16(const void* p)
 {
     return (reinterpret_cast<uintptr_t>(p) & 15u) == 0;
@@ -401,6 +535,33 @@ void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph
     k_spectral_direction<<<stream_blocks(M), kThreads, 0, st>>>(
         g, reinterpret_cast<float2*>(zh), reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
         cstride, beta, first, rp);
+}
+
+void launch_fs_start(const Grid& g, cufftComplex* spec, cufftComplex* rh, cufftComplex* xh, size_t cs,
+                     SpectralOp op, RegParams rp, float scale, double* prr, double* prz, int nblocks,
+                     cudaStream_t st)
+{
+    k_fs_start<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<float2*>(spec), reinterpret_cast<float2*>(rh),
+                                             reinterpret_cast<float2*>(xh), cs, static_cast<int>(op), rp,
+                                             scale, prr, prz);
+}
+
+void launch_fs_hp(const Grid& g, cufftComplex* spec, const cufftComplex* spec2, const cufftComplex* ph,
+                  size_t cs, int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st)
+{
+    k_fs_hp<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<float2*>(spec),
+                                          reinterpret_cast<const float2*>(spec2),
+                                          reinterpret_cast<const float2*>(ph), cs, kform, rp, scale, ppq);
+}
+
+void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph, cufftComplex* xh,
+                      cufftComplex* rh, size_t cs, float alpha, SpectralOp op, RegParams rp, double* prr,
+                      double* prz, int nblocks, cudaStream_t st)
+{
+    k_fs_update<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<float2*>(spec),
+                                              reinterpret_cast<const float2*>(ph),
+                                              reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(rh),
+                                              cs, alpha, static_cast<int>(op), rp, prr, prz);
 }
 
 void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,

@@ -313,12 +313,22 @@ def run_ours(args):
     g_secs = sum(s["seconds"] for s in gathers)
     g_pts = sum(s["points"] for s in gathers)
     total_kernel_s = sum(s["seconds"] for s in stats)
+    # shared-memory (LSU) ceiling of the gathers: 128 B/clk/SM x SMs x max SM
+    # clock; a tricubic point needs 64 x 4 B of shared-memory reads
+    props = torch.cuda.get_device_properties(dev)
+    sm_mhz = ck["sm_max_mhz"] if ck else 2070.0
+    lsu_bytes_s = 128.0 * props.multi_processor_count * sm_mhz * 1e6
+    top_pts = top["points"] / top["launches"] if top["points"] else 0.0
     roofline = {"bound": "hbm", "kernel": top["name"], "achieved": achieved, "peak": peak,
                 "unit": "GB/s", "frac": achieved / peak, "peak_source": peak_src,
                 "traffic": ncu_traffic(top["name"], kernel_source_hash()),
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "launch_ms": per_launch_s * 1e3,
                 "share_of_kernel_time": top["seconds"] / total_kernel_s if total_kernel_s else None,
+                "lsu": {"achieved_gpts": top_pts / per_launch_s / 1e9,
+                        "peak_gpts": lsu_bytes_s / 256.0 / 1e9,
+                        "frac": (top_pts / per_launch_s) / (lsu_bytes_s / 256.0),
+                        "note": "shared-memory read ceiling of a tricubic gather (64 x 4 B per point)"},
                 "all_gathers": {"gpts_s": g_pts / g_secs / 1e9 if g_secs else None,
                                 "achieved_GBs": g_bytes / g_secs / 1e9 if g_secs else None,
                                 "frac": (g_bytes / g_secs / 1e9) / peak if g_secs else None}}

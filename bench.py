@@ -162,6 +162,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def aggregate_ranks(secs, pts, dist=None, device=None):
+    """Whole-job figures over replica ranks: the slowest rank's time and the
+    work of all ranks (no data-path collective; one reduction per figure)."""
+    if dist is None:
+        return secs, pts
+    import torch
+    t = torch.tensor([secs], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    q = torch.tensor([pts], dtype=torch.float64, device=device)
+    dist.all_reduce(q, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(q.item())
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -290,14 +303,7 @@ def run_ours(args):
     stats = ctx.kernel_stats(reset=True)
     ctx.set_timing(False)
     pts = sum(r["interp_points"] for r in reps)
-    tmax, pts_all = secs, pts
-    if pg:
-        t = torch.tensor([secs], device=dev, dtype=torch.float64)
-        pg.all_reduce(t, op=pg.ReduceOp.MAX)
-        tmax = float(t.item())
-        q = torch.tensor([pts], device=dev, dtype=torch.float64)
-        pg.all_reduce(q, op=pg.ReduceOp.SUM)
-        pts_all = float(q.item())
+    tmax, pts_all = aggregate_ranks(secs, pts, pg, dev)
     value = pts_all / tmax / 1e9
 
     # dominant kernel of ours (cuFFT is a library call, not counted)
@@ -352,13 +358,7 @@ def run_ours(args):
             pts_e += rep["interp_points"]
         torch.cuda.synchronize()
         te = time.perf_counter() - t0
-        if pg:
-            t = torch.tensor([te], device=dev, dtype=torch.float64)
-            pg.all_reduce(t, op=pg.ReduceOp.MAX)
-            te = float(t.item())
-            q = torch.tensor([pts_e], device=dev, dtype=torch.float64)
-            pg.all_reduce(q, op=pg.ReduceOp.SUM)
-            pts_e = float(q.item())
+        te, pts_e = aggregate_ranks(te, pts_e, pg, dev)
         e2e = {"value": pts_e / te / 1e9, "unit": UNIT, "h2d_bytes_per_step": 4 * N * 5,
                "d2h_bytes_per_step": 4 * N * 3, "ms_per_step": 1e3 * te / args.steps}
 

@@ -50,6 +50,8 @@ def parse_args():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--n", type=int, default=256, help="grid points per axis")
     ap.add_argument("--beta", type=float, default=1e-2)
+    ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
+                    help="storage precision of the solver's scalar fields (arithmetic is FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
@@ -69,6 +71,7 @@ def config_dict(args, n_gpus):
                         "|k|<=8 max|v|=1, Gauss-Newton-Krylov to gtol 5e-2 from v=0" % args.n,
             "grid": [args.n] * 3, "nt": 4, "interp": "cubic Lagrange", "beta_v": args.beta,
             "beta_w": 1e-4, "reg": "H1 seminorm", "gtol": 5e-2, "max_pcg": 50,
+            "storage": args.storage,
             "l2_policy": "inputs larger than L2 (working set %.1f GB > 129 MB L2)"
                          % (args.n ** 3 * 4 * 60 / 1e9),
             "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
@@ -259,8 +262,9 @@ def run_ours(args):
     grid, base, vstar = workload(args.n)
     N = int(np.prod(grid))
     stream = torch.cuda.current_stream(dev)
+    storage = {"f32": claire.STORAGE_F32, "f16": claire.STORAGE_F16, "bf16": claire.STORAGE_BF16}[args.storage]
     ctx = claire.Context(grid, args.beta, 4, stream=stream.cuda_stream, beta_w=1e-4, gtol=5e-2,
-                         max_gn=50, max_pcg=50)
+                         max_gn=50, max_pcg=50, storage=storage)
     # reference image by our own transport of the clean template, then noise
     base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
     vstar_d = torch.from_numpy(vstar.astype(np.float32)).to(dev)
@@ -377,7 +381,8 @@ def run_ours(args):
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * tmax / args.steps,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "f32" if args.storage == "f32" else "f32 math, %s storage" % args.storage,
             "data": "synthetic", "config": config_dict(args, world),
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e, "clocks": ck,
             "gpu_launches": launches,

@@ -89,7 +89,17 @@ typedef struct claire_opts {
     int timing;          /* 1 = time every kernel launch with CUDA events (read back lazily by
                             claire_kernel_stats); 2 = also fill claire_report.t_phase_s at the end
                             of each claire_register (one extra synchronisation) */
+    int storage;         /* storage precision of the scalar fields of the solver (images, states
+                            m^j and their gradients, adjoint levels, incremental fields, div v):
+                            CLAIRE_STORAGE_F32 (default), _F16 or _BF16.  Arithmetic is FP32,
+                            reductions FP64; velocities, displacements and the spectral/PCG
+                            vectors stay FP32.  API arrays are always float32. */
 } claire_opts;
+
+/* claire_opts.storage */
+#define CLAIRE_STORAGE_F32 0
+#define CLAIRE_STORAGE_F16 1
+#define CLAIRE_STORAGE_BF16 2
 
 /* Phase slots of claire_report.t_phase_s (seconds, CUDA-event timed when opts.timing = 2). */
 #define CLAIRE_PHASE_BACKTRACE 0   /* RK2 characteristics, div v, div v at X+ */

@@ -26,6 +26,7 @@ STATUS_NAMES = {0: "CLAIRE_OK", 1: "CLAIRE_ENOTCONVERGED", -1: "CLAIRE_EINVAL",
 INTERP_CUBIC, INTERP_LINEAR = 3, 1
 TRANSPORT_FWD, TRANSPORT_ADJ = 0, 1
 SPECTRAL_REG, SPECTRAL_INV, SPECTRAL_K = 0, 1, 2
+STORAGE_F32, STORAGE_F16, STORAGE_BF16 = 0, 1, 2
 PHASES = ["backtrace", "state", "adjoint", "incremental", "spectral", "vector", "objective",
           "gather"]
 MAX_LOGGED_STEPS = 64
@@ -43,7 +44,7 @@ class claire_opts(ctypes.Structure):
                 ("max_pcg", ctypes.c_int), ("pcg_rtol_max", ctypes.c_double),
                 ("pcg_fixed", ctypes.c_int), ("armijo_c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("storage", ctypes.c_int)]
 
 
 class claire_report(ctypes.Structure):

@@ -6,6 +6,8 @@
 #include <cstdint>
 #include <cuda_runtime.h>
 
+#include "storage.cuh"
+
 namespace claire {
 
 // Grid geometry passed by value to every kernel.
@@ -88,7 +90,8 @@ struct Stencil {
         }
     }
     // Separable contraction: x3 first (contiguous loads), then x2, then x1.
-    __device__ __forceinline__ float eval(const float* __restrict__ f) const
+    template <class S = float>
+    __device__ __forceinline__ float eval(const S* __restrict__ f) const
     {
         constexpr int M = Axis<ORDER>::M;
         float r = 0.0f;
@@ -97,10 +100,10 @@ struct Stencil {
             float sa = 0.0f;
 #pragma unroll
             for (int b = 0; b < M; ++b) {
-                const float* row = f + a1.idx[a] + a2.idx[b];
+                const S* row = f + a1.idx[a] + a2.idx[b];
                 float sb = 0.0f;
 #pragma unroll
-                for (int c = 0; c < M; ++c) sb = fmaf(a3.w[c], __ldg(row + a3.idx[c]), sb);
+                for (int c = 0; c < M; ++c) sb = fmaf(a3.w[c], ldf<S>(row + a3.idx[c]), sb);
                 sa = fmaf(a2.w[b], sb, sa);
             }
             r = fmaf(a1.w[a], sa, r);

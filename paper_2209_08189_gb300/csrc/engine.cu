@@ -74,13 +74,16 @@ struct claire_ctx {
     // workspace arena
     void* arena = nullptr;
     size_t arena_bytes = 0;
-    float *m0 = nullptr, *m1 = nullptr;
+    // scalar fields stored in the storage type `sto` (es bytes per value)
+    Storage sto = Storage::F32;
+    size_t es = 4;
+    char *m0 = nullptr, *m1 = nullptr;
     float *v = nullptr;                   // linearisation point
     float *dS = nullptr, *dA = nullptr;   // state / adjoint characteristics
-    float *divv = nullptr, *divXp = nullptr;
-    float *m = nullptr, *gm = nullptr;    // (nt+1) N and (nt+1) 3N
-    float *l0 = nullptr, *l1 = nullptr;   // rolling scalar fields
-    float* tl = nullptr;                  // (nt+1) N: adjoint levels lambda^j / incremental sources f^j
+    char *divv = nullptr, *divXp = nullptr;
+    char *m = nullptr, *gm = nullptr;     // (nt+1) N and (nt+1) 3N values
+    char *l0 = nullptr, *l1 = nullptr;    // rolling scalar fields (FP32-sized: transport uses them as FP32)
+    char* tl = nullptr;                   // (nt+1) N: adjoint levels lambda^j / incremental sources f^j
     float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
     cufftComplex* spec = nullptr;
     cufftComplex* phat = nullptr;         // PCG search direction in Fourier space
@@ -125,6 +128,9 @@ struct claire_ctx {
 };
 
 namespace {
+
+// Address of value `idx` of a storage-typed field.
+inline char* at(const claire_ctx* c, char* base, size_t idx) { return base + idx * c->es; }
 
 claire_status fail(claire_ctx* c, claire_status s, const char* fmt, ...)
 {
@@ -190,6 +196,7 @@ void fill_defaults(claire_opts* o)
     o->max_ls = 10;
     o->wall_limit_s = 0.0;
     o->timing = 0;
+    o->storage = CLAIRE_STORAGE_F32;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -197,7 +204,7 @@ bool valid_opts(const claire_opts& o)
     return (o.interp == 1 || o.interp == 3) && (o.reg == 1 || o.reg == 2) && o.beta_w >= 0 &&
            (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
            o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
-           o.max_ls >= 1 && o.wall_limit_s >= 0;
+           o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2;
 }
 
 // Layout of the workspace arena in floats (each region 256-byte aligned).
@@ -214,22 +221,23 @@ struct Layout {
     }
 };
 
-size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, Layout* L)
+size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, size_t es, Layout* L)
 {
     Layout tmp;
     Layout& l = L ? *L : tmp;
-    l.add(N);                 // m0
-    l.add(N);                 // m1
-    l.add(3 * N);             // v
-    l.add(3 * N);             // dS
-    l.add(3 * N);             // dA
-    l.add(N);                 // divv
-    l.add(N);                 // divXp
-    l.add((nt + 1) * N);      // m
-    l.add(3 * (nt + 1) * N);  // gm
-    l.add(N);                 // l0
-    l.add(N);                 // l1
-    l.add((nt + 1) * N);      // tl
+    auto S = [&](size_t values) { return (values * es + 3) / 4; };  // storage-typed region, in floats
+    l.add(S(N));                 // m0
+    l.add(S(N));                 // m1
+    l.add(3 * N);                // v
+    l.add(3 * N);                // dS
+    l.add(3 * N);                // dA
+    l.add(S(N));                 // divv
+    l.add(S(N));                 // divXp
+    l.add(S((nt + 1) * N));      // m
+    l.add(S(3 * (nt + 1) * N));  // gm
+    l.add(N);                    // l0 (FP32-sized)
+    l.add(N);                    // l1 (FP32-sized)
+    l.add(S((nt + 1) * N));      // tl
     for (int i = 0; i < 6; ++i) l.add(3 * N);  // g x r z p q
     l.add(6 * M);             // spec (3 complex half-spectra)
     l.add(6 * M);             // phat
@@ -394,10 +402,10 @@ claire_status spectral(claire_ctx* c, const float* in, float* out, SpectralOp op
     return CLAIRE_OK;
 }
 
-claire_status fd8_grad(claire_ctx* c, const float* f, float* out)
+claire_status fd8_grad(claire_ctx* c, const void* f, void* out, Storage sto)
 {
-    KTimer t(c, KK_FD8, 16.0 * c->N, 0);
-    launch_fd8_grad(c->grid, f, out, c->stream);
+    KTimer t(c, KK_FD8, 4.0 * storage_bytes(sto) * c->N, 0);
+    launch_fd8_grad(c->grid, f, out, sto, c->stream);
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
@@ -410,33 +418,33 @@ claire_status backtrace(claire_ctx* c, const float* v, float* d, int sign)
     return CLAIRE_OK;
 }
 
-claire_status interp(claire_ctx* c, const float* f, const float* d, float* out)
+claire_status interp(claire_ctx* c, const void* f, const float* d, void* out, Storage sto)
 {
-    KTimer t(c, KK_INTERP, 20.0 * c->N, 1.0 * c->N);
-    launch_interp(c->grid, c->o.interp, f, d, out, c->stream);
+    KTimer t(c, KK_INTERP, (12.0 + 2.0 * storage_bytes(sto)) * c->N, 1.0 * c->N);
+    launch_interp(c->grid, c->o.interp, f, d, out, sto, c->stream);
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
 
 // Per-velocity data: X, X+, div v, div v (X+).
-claire_status characteristics(claire_ctx* c, const float* v, float* dS, float* dA, float* divv,
-                              float* divXp)
+// div v and div v(X+) are stored in `sto`.
+claire_status characteristics(claire_ctx* c, const float* v, float* dS, float* dA, void* divv,
+                              void* divXp, Storage sto)
 {
     PhaseScope ps(c, CLAIRE_PHASE_BACKTRACE);
     if (dS) CL_TRY(backtrace(c, v, dS, +1));
     if (dA) {
         CL_TRY(backtrace(c, v, dA, -1));
         {
-            KTimer t(c, KK_FD8, 16.0 * c->N, 0);
-            launch_fd8_div(c->grid, v, divv, c->stream);
+            KTimer t(c, KK_FD8, (12.0 + storage_bytes(sto)) * c->N, 0);
+            launch_fd8_div(c->grid, v, divv, sto, c->stream);
             CL_LAUNCHED(c);
         }
-        CL_TRY(interp(c, divv, dA, divXp));
+        CL_TRY(interp(c, divv, dA, divXp, sto));
     }
     return CLAIRE_OK;
 }
 
-double trap_w(const claire_ctx* c, int j) { return (j == 0 || j == c->nt) ? 0.5 * c->dt : c->dt; }
 
 // Set the linearisation point: characteristics, states m^j and grad m^j, S v,
 // objective pieces.  v (device) is copied into c->v unless it already is c->v.
@@ -449,14 +457,16 @@ claire_status linearise(claire_ctx* c, const float* v, bool have_state = false)
     if (v != c->v)
         CL_CUDA(c, cudaMemcpyAsync(c->v, v, 3 * c->N * sizeof(float), cudaMemcpyDeviceToDevice,
                                    c->stream));
-    CL_TRY(characteristics(c, c->v, have_state ? nullptr : c->dS, c->dA, c->divv, c->divXp));
+    CL_TRY(characteristics(c, c->v, have_state ? nullptr : c->dS, c->dA, c->divv, c->divXp, c->sto));
     {
         PhaseScope ps(c, CLAIRE_PHASE_STATE);
-        CL_CUDA(c, cudaMemcpyAsync(c->m, c->m0, c->N * sizeof(float), cudaMemcpyDeviceToDevice,
-                                   c->stream));
+        const size_t N = c->N;
+        CL_CUDA(c, cudaMemcpyAsync(c->m, c->m0, N * c->es, cudaMemcpyDeviceToDevice, c->stream));
         if (!have_state)
-            for (int j = 0; j < c->nt; ++j) CL_TRY(interp(c, c->m + j * c->N, c->dS, c->m + (j + 1) * c->N));
-        for (int j = 0; j <= c->nt; ++j) CL_TRY(fd8_grad(c, c->m + j * c->N, c->gm + 3 * j * c->N));
+            for (int j = 0; j < c->nt; ++j)
+                CL_TRY(interp(c, at(c, c->m, j * N), c->dS, at(c, c->m, (j + 1) * N), c->sto));
+        for (int j = 0; j <= c->nt; ++j)
+            CL_TRY(fd8_grad(c, at(c, c->m, j * N), at(c, c->gm, 3 * j * N), c->sto));
     }
     return CLAIRE_OK;
 }
@@ -464,27 +474,28 @@ claire_status linearise(claire_ctx* c, const float* v, bool have_state = false)
 // Backward SL solve of Eq. (4) from lambda^{nt} = a - s (s may be null) into
 // the levels tl[j], then out += sum_j w_j lambda^j grad m^j (trapezoid).
 // The levels tl[1..nt] may hold the incremental sources on entry (consumed).
-claire_status adjoint_and_body(claire_ctx* c, const float* a, const float* s, float* out,
+claire_status adjoint_and_body(claire_ctx* c, const void* a, const void* s, float* out,
                                bool accumulate = true)
 {
     const size_t N = c->N;
     const int nt = c->nt;
     PhaseScope ps(c, CLAIRE_PHASE_ADJOINT);
+    const double es = static_cast<double>(c->es);
     if (a) {
-        KTimer t(c, KK_POINTWISE, 12.0 * N, 0);
-        launch_xpay(a, -1.0f, s, c->tl + nt * N, N, c->stream);
+        KTimer t(c, KK_POINTWISE, 3.0 * es * N, 0);
+        launch_sub(a, s, at(c, c->tl, nt * N), N, c->sto, c->stream);
         CL_LAUNCHED(c);
     }
     for (int j = nt - 1; j >= 0; --j) {
-        KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
-        launch_adj_step(c->grid, c->o.interp, c->tl + (j + 1) * N, c->dA, c->divv, c->divXp,
-                        static_cast<float>(c->dt), c->tl + j * N, c->stream);
+        KTimer t(c, KK_ADJ_STEP, (12.0 + 4.0 * es) * N, 1.0 * N);
+        launch_adj_step(c->grid, c->o.interp, at(c, c->tl, (j + 1) * N), c->dA, c->divv, c->divXp,
+                        static_cast<float>(c->dt), at(c, c->tl, j * N), c->sto, c->stream);
         CL_LAUNCHED(c);
     }
     {
-        KTimer t(c, KK_POINTWISE, (16.0 * (nt + 1) + 24.0) * N, 0);
+        KTimer t(c, KK_POINTWISE, (4.0 * es * (nt + 1) + (accumulate ? 24.0 : 12.0)) * N, 0);
         launch_body(c->grid, c->tl, c->gm, nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt),
-                    accumulate ? 1 : 0, out, c->stream);
+                    accumulate ? 1 : 0, out, c->sto, c->stream);
         CL_LAUNCHED(c);
     }
     return CLAIRE_OK;
@@ -500,11 +511,11 @@ claire_status gradient_at_lin(claire_ctx* c, float* g)
         PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
         CL_TRY(dot_async(c, c->v, g, 3 * N, 0.5 * c->hvol, 0));
         KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
-        launch_sqdiff_partial(c->m + c->nt * N, c->m1, N, c->partials, c->red_blocks, c->stream);
+        launch_sqdiff_partial(at(c, c->m, c->nt * N), c->m1, N, c->partials, c->red_blocks, c->sto, c->stream);
         launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 1, c->stream);
         CL_LAUNCHED(c);
     }
-    CL_TRY(adjoint_and_body(c, c->m1, c->m + c->nt * N, g));
+    CL_TRY(adjoint_and_body(c, c->m1, at(c, c->m, c->nt * N), g));
     if (c->o.grad_form == 1) CL_TRY(spectral(c, g, g, SPEC_K));
     CL_TRY(sync_scalars(c, 2));
     c->reg_lin = c->hres[0];
@@ -529,22 +540,24 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
         PhaseScope ps(c, CLAIRE_PHASE_INCREMENTAL);
         // sources f^j = -vt . grad m^j; Heun: q^0 = dt/2 f^0, q^{j+1} = q^j(X) + dt f^{j+1},
         // mt^{nt} = q^{nt-1}(X) + dt/2 f^{nt}, lt^{nt} = -mt^{nt}
-        float* a = c->l0;
-        float* b = c->l1;
+        const double es = static_cast<double>(c->es);
+        char* a = c->l0;
+        char* b = c->l1;
         {
-            KTimer t(c, KK_POINTWISE, (12.0 + 16.0 * (nt + 1)) * N, 0);
-            launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->stream);
+            KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es * (nt + 1)) * N, 0);
+            launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
             CL_LAUNCHED(c);
         }
         for (int j = 0; j + 1 < nt; ++j) {
-            KTimer t(c, KK_INC_STEP, 24.0 * N, 1.0 * N);
-            launch_inc_step_src(c->grid, c->o.interp, a, c->dS, c->tl + (j + 1) * N, dt, b, c->stream);
+            KTimer t(c, KK_INC_STEP, (12.0 + 3.0 * es) * N, 1.0 * N);
+            launch_inc_step_src(c->grid, c->o.interp, a, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
+                                c->stream);
             CL_LAUNCHED(c);
             std::swap(a, b);
         }
-        KTimer t(c, KK_INC_LAST, 24.0 * N, 1.0 * N);
-        launch_inc_last_src(c->grid, c->o.interp, a, c->dS, c->tl + nt * N, 0.5f * dt, c->tl + nt * N,
-                            c->stream);
+        KTimer t(c, KK_INC_LAST, (12.0 + 3.0 * es) * N, 1.0 * N);
+        launch_inc_last_src(c->grid, c->o.interp, a, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
+                            at(c, c->tl, nt * N), c->sto, c->stream);
         CL_LAUNCHED(c);
     }
     // incremental adjoint from lt^{nt} and body, accumulated onto S vt in out
@@ -572,12 +585,12 @@ claire_status objective_at(claire_ctx* c, const float* v, double* J, double* mis
     float* d = into_state ? c->dS : c->z;
     if (into_state) c->have_lin = false;
     CL_TRY(backtrace(c, v, d, +1));
-    const float* src = c->m0;
-    float* a = c->l0;
-    float* b = c->l1;
+    const char* src = c->m0;
+    char* a = c->l0;
+    char* b = c->l1;
     for (int j = 0; j < c->nt; ++j) {
-        float* dst = into_state ? c->m + (j + 1) * N : a;
-        CL_TRY(interp(c, src, d, dst));
+        char* dst = into_state ? at(c, c->m, (j + 1) * N) : a;
+        CL_TRY(interp(c, src, d, dst, c->sto));
         src = dst;
         std::swap(a, b);
     }
@@ -585,7 +598,7 @@ claire_status objective_at(claire_ctx* c, const float* v, double* J, double* mis
     CL_TRY(dot_async(c, v, c->r, 3 * N, 0.5 * c->hvol, 0));
     {
         KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
-        launch_sqdiff_partial(src, c->m1, N, c->partials, c->red_blocks, c->stream);
+        launch_sqdiff_partial(src, c->m1, N, c->partials, c->red_blocks, c->sto, c->stream);
         launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 1, c->stream);
         CL_LAUNCHED(c);
     }
@@ -791,11 +804,12 @@ claire_status claire_default_opts(claire_opts* opts)
 claire_status claire_query_workspace(const int grid[3], int nt, const claire_opts* opts,
                                      size_t* bytes)
 {
-    (void)opts;
     if (!valid_grid(grid) || nt < 1 || !bytes) return CLAIRE_EINVAL;
     const size_t N = (size_t)grid[0] * grid[1] * grid[2];
     const size_t M = (size_t)grid[0] * grid[1] * (grid[2] / 2 + 1);
-    *bytes = layout_floats(N, M, nt, 152 * 8, nullptr) * sizeof(float);
+    const int sto = opts ? opts->storage : 0;
+    if (sto < 0 || sto > 2) return CLAIRE_EINVAL;
+    *bytes = layout_floats(N, M, nt, 152 * 8, storage_bytes(static_cast<Storage>(sto)), nullptr) * sizeof(float);
     return CLAIRE_OK;
 }
 
@@ -855,7 +869,9 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     }
     c->red_blocks = std::max(1, c->nsm) * 4;
     Layout L;
-    size_t floats = layout_floats(c->N, c->M, nt, c->red_blocks, &L);
+    c->sto = static_cast<Storage>(o.storage);
+    c->es = storage_bytes(c->sto);
+    size_t floats = layout_floats(c->N, c->M, nt, c->red_blocks, c->es, &L);
     cudaError_t e = cudaMalloc(&c->arena, floats * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -865,18 +881,18 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->arena_bytes = floats * sizeof(float);
     float* base = static_cast<float*>(c->arena);
     int k = 0;
-    c->m0 = base + L.off[k++];
-    c->m1 = base + L.off[k++];
+    c->m0 = reinterpret_cast<char*>(base + L.off[k++]);
+    c->m1 = reinterpret_cast<char*>(base + L.off[k++]);
     c->v = base + L.off[k++];
     c->dS = base + L.off[k++];
     c->dA = base + L.off[k++];
-    c->divv = base + L.off[k++];
-    c->divXp = base + L.off[k++];
-    c->m = base + L.off[k++];
-    c->gm = base + L.off[k++];
-    c->l0 = base + L.off[k++];
-    c->l1 = base + L.off[k++];
-    c->tl = base + L.off[k++];
+    c->divv = reinterpret_cast<char*>(base + L.off[k++]);
+    c->divXp = reinterpret_cast<char*>(base + L.off[k++]);
+    c->m = reinterpret_cast<char*>(base + L.off[k++]);
+    c->gm = reinterpret_cast<char*>(base + L.off[k++]);
+    c->l0 = reinterpret_cast<char*>(base + L.off[k++]);
+    c->l1 = reinterpret_cast<char*>(base + L.off[k++]);
+    c->tl = reinterpret_cast<char*>(base + L.off[k++]);
     c->g = base + L.off[k++];
     c->x = base + L.off[k++];
     c->r = base + L.off[k++];
@@ -935,9 +951,20 @@ claire_status claire_set_stream(claire_ctx* c, void* stream)
 claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
 {
     if (!c || !m0 || !m1) return c ? fail(c, CLAIRE_EINVAL, "null image") : CLAIRE_EINVAL;
-    const size_t bytes = c->N * sizeof(float);
-    CL_CUDA(c, cudaMemcpyAsync(c->m0, m0, bytes, cudaMemcpyDefault, c->stream));
-    CL_CUDA(c, cudaMemcpyAsync(c->m1, m1, bytes, cudaMemcpyDefault, c->stream));
+    const size_t N = c->N;
+    if (c->sto == Storage::F32) {
+        CL_CUDA(c, cudaMemcpyAsync(c->m0, m0, N * sizeof(float), cudaMemcpyDefault, c->stream));
+        CL_CUDA(c, cudaMemcpyAsync(c->m1, m1, N * sizeof(float), cudaMemcpyDefault, c->stream));
+    } else {
+        // FP32 input (host or device) converted to the storage type on the device
+        const float* d0;
+        CL_TRY(device_input(c, m0, N, c->p, &d0));
+        launch_to_storage(d0, c->m0, N, c->sto, c->stream);
+        const float* d1;
+        CL_TRY(device_input(c, m1, N, c->z, &d1));
+        launch_to_storage(d1, c->m1, N, c->sto, c->stream);
+        CL_LAUNCHED(c);
+    }
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
     c->have_images = true;
     c->have_lin = false;
@@ -1080,7 +1107,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
         double den;
         {
             KTimer t(c, KK_REDUCE, 8.0 * N, 0, 2);
-            launch_sqdiff_partial(c->m0, c->m1, N, c->partials, c->red_blocks, c->stream);
+            launch_sqdiff_partial(c->m0, c->m1, N, c->partials, c->red_blocks, c->sto, c->stream);
             launch_final_sum(c->partials, c->red_blocks, 0.5 * c->hvol, c->dres + 2, c->stream);
             CL_LAUNCHED(c);
         }
@@ -1120,25 +1147,26 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
     const size_t N = c->N;
     const float* dv;
     CL_TRY(device_input(c, v, 3 * N, c->p, &dv));
+    // the user-facing transport runs in FP32 whatever the context's storage
     const float* src;
-    CL_TRY(device_input(c, m_in, N, c->l0, &src));
-    float* a = c->l1;
-    float* b = c->l0;
+    CL_TRY(device_input(c, m_in, N, reinterpret_cast<float*>(c->l0), &src));
+    float* a = reinterpret_cast<float*>(c->l1);
+    float* b = reinterpret_cast<float*>(c->l0);
     if (flags == CLAIRE_TRANSPORT_FWD) {
         CL_TRY(backtrace(c, dv, c->z, +1));
         for (int j = 0; j < c->nt; ++j) {
-            CL_TRY(interp(c, src, c->z, a));
+            CL_TRY(interp(c, src, c->z, a, Storage::F32));
             src = a;
             std::swap(a, b);
         }
     } else {
         float* divv = c->r;
         float* divXp = c->r + N;
-        CL_TRY(characteristics(c, dv, nullptr, c->z, divv, divXp));
+        CL_TRY(characteristics(c, dv, nullptr, c->z, divv, divXp, Storage::F32));
         for (int j = 0; j < c->nt; ++j) {
             KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
             launch_adj_step(c->grid, c->o.interp, src, c->z, divv, divXp, static_cast<float>(c->dt), a,
-                            c->stream);
+                            Storage::F32, c->stream);
             CL_LAUNCHED(c);
             src = a;
             std::swap(a, b);
@@ -1170,7 +1198,7 @@ claire_status claire_interp(claire_ctx* c, const float* f, const float* d, float
     CL_TRY(check_kernel_ptr(c, out));
     {
         KTimer t(c, KK_INTERP, 20.0 * c->N, 1.0 * c->N);
-        launch_interp(c->grid, order, f, d, out, c->stream);
+        launch_interp(c->grid, order, f, d, out, Storage::F32, c->stream);
         CL_LAUNCHED(c);
     }
     CL_TRY(sync_scalars(c, 0));
@@ -1195,7 +1223,7 @@ claire_status claire_fd8_grad(claire_ctx* c, const float* f, float* g)
     if (!c) return CLAIRE_EINVAL;
     CL_TRY(check_kernel_ptr(c, f));
     CL_TRY(check_kernel_ptr(c, g));
-    CL_TRY(fd8_grad(c, f, g));
+    CL_TRY(fd8_grad(c, f, g, Storage::F32));
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
     return CLAIRE_OK;
 }
@@ -1207,7 +1235,7 @@ claire_status claire_fd8_div(claire_ctx* c, const float* v, float* dv)
     CL_TRY(check_kernel_ptr(c, dv));
     {
         KTimer t(c, KK_FD8, 16.0 * c->N, 0);
-        launch_fd8_div(c->grid, v, dv, c->stream);
+        launch_fd8_div(c->grid, v, dv, Storage::F32, c->stream);
         CL_LAUNCHED(c);
     }
     CL_CUDA(c, cudaStreamSynchronize(c->stream));

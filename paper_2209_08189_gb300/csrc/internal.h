@@ -69,28 +69,35 @@ __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin,
 #endif
 
 // ---- semi-Lagrangian and FD kernels (sl_kernels.cu) ----
-void launch_interp(const Grid& g, int order, const float* f, const float* d, float* out,
+// Pointers typed void* hold scalar fields in the storage type `sto` (FP32,
+// FP16 or BF16); float* ones are always FP32 (displacements, velocities,
+// vector work fields).
+void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
                    cudaStream_t st);
 void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
                       cudaStream_t st);
 // One SL step of Eq. (4): lam = Heun(lam_next(X+), div v(X+), div v).
-void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
-                     const float* divv, const float* divXp, float dt, float* lam, cudaStream_t st);
+void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
+                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st);
 // f^j = -vt . grad m^j for j = 0..nt: q0 = coef0 f^0, F + j N <- f^j (j >= 1).
-void launch_inc_sources(const Grid& g, const float* vt, const float* gm, int nt, float coef0, float* q0,
-                        float* F, cudaStream_t st);
+void launch_inc_sources(const Grid& g, const float* vt, const void* gm, int nt, float coef0, void* q0,
+                        void* F, Storage sto, cudaStream_t st);
 // out (+)= sum_j w_j lam^j grad m^j (lam slots j N, trapezoid weights w_end / w_mid).
-void launch_body(const Grid& g, const float* lam, const float* gm, int nt, float w_end, float w_mid,
-                 int accumulate, float* out, cudaStream_t st);
+void launch_body(const Grid& g, const void* lam, const void* gm, int nt, float w_end, float w_mid,
+                 int accumulate, float* out, Storage sto, cudaStream_t st);
 // q = q_prev(X) + coef F;   lam = -(q_prev(X) + coef F)  (F may alias lam)
-void launch_inc_step_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
-                         float coef, float* q, cudaStream_t st);
-void launch_inc_last_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
-                         float coef, float* lam, cudaStream_t st);
+void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
+                         float coef, void* q, Storage sto, cudaStream_t st);
+void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
+                         float coef, void* lam, Storage sto, cudaStream_t st);
+// out = a - b; conversions FP32 <-> storage
+void launch_sub(const void* a, const void* b, void* out, size_t n, Storage sto, cudaStream_t st);
+void launch_to_storage(const float* in, void* out, size_t n, Storage sto, cudaStream_t st);
+void launch_from_storage(const void* in, float* out, size_t n, Storage sto, cudaStream_t st);
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
                      cudaStream_t st);
-void launch_fd8_grad(const Grid& g, const float* f, float* out, cudaStream_t st);
-void launch_fd8_div(const Grid& g, const float* v, float* out, cudaStream_t st);
+void launch_fd8_grad(const Grid& g, const void* f, void* out, Storage sto, cudaStream_t st);
+void launch_fd8_div(const Grid& g, const float* v, void* out, Storage sto, cudaStream_t st);
 void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,
                         cudaStream_t st);
 
@@ -134,8 +141,8 @@ void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph,
 // final sum in fixed order.  `partials` holds at least nblocks doubles.
 void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,
                         cudaStream_t st);
-void launch_sqdiff_partial(const float* a, const float* b, size_t n, double* partials, int nblocks,
-                           cudaStream_t st);
+void launch_sqdiff_partial(const void* a, const void* b, size_t n, double* partials, int nblocks,
+                           Storage sto, cudaStream_t st);
 void launch_maxnorm3_partial(const float* v, size_t N, double* partials, int nblocks,
                              cudaStream_t st);
 void launch_final_sum(const double* partials, int nblocks, double scale, double* out,

@@ -45,30 +45,32 @@ __global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __r
 
 // Sources of the incremental state for every time level at once:
 // f^j = -vt . grad m^j; q0 = coef0 f^0 starts the Heun recursion and
-// f^1..f^nt go to F (slot j at F + j N).
+// f^1..f^nt go to F (slot j at F + j N).  S: storage of grad m, q0, F.
+template <class S>
 __global__ void __launch_bounds__(kThreads) k_inc_sources(Grid g, const float* __restrict__ vt,
-                                                           const float* __restrict__ gm, int nt,
-                                                           float coef0, float* __restrict__ q0,
-                                                           float* __restrict__ F)
+                                                           const S* __restrict__ gm, int nt,
+                                                           float coef0, S* __restrict__ q0,
+                                                           S* __restrict__ F)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
     const size_t N = g.N;
     const float v0 = __ldg(vt + p), v1 = __ldg(vt + N + p), v2 = __ldg(vt + 2 * N + p);
     for (int j = 0; j <= nt; ++j) {
-        const float* gj = gm + 3 * j * N;
-        const float f = -(v0 * __ldg(gj + p) + v1 * __ldg(gj + N + p) + v2 * __ldg(gj + 2 * N + p));
+        const S* gj = gm + 3 * j * N;
+        const float f = -(v0 * ldf<S>(gj + p) + v1 * ldf<S>(gj + N + p) + v2 * ldf<S>(gj + 2 * N + p));
         if (j == 0)
-            q0[p] = coef0 * f;
+            stf<S>(q0 + p, coef0 * f);
         else
-            F[j * N + p] = f;
+            stf<S>(F + j * N + p, f);
     }
 }
 
-// Gradient body by trapezoid in time, added to out:
+// Gradient body by trapezoid in time, added to out (FP32):
 // out_c (+)= sum_j w_j lambda^j grad_c m^j, w_0 = w_nt = w_end, else w_mid.
-__global__ void __launch_bounds__(kThreads) k_body(Grid g, const float* __restrict__ lam,
-                                                    const float* __restrict__ gm, int nt, float w_end,
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_body(Grid g, const S* __restrict__ lam,
+                                                    const S* __restrict__ gm, int nt, float w_end,
                                                     float w_mid, int accumulate, float* __restrict__ out)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
@@ -76,11 +78,11 @@ __global__ void __launch_bounds__(kThreads) k_body(Grid g, const float* __restri
     const size_t N = g.N;
     float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
     for (int j = 0; j <= nt; ++j) {
-        const float wl = (j == 0 || j == nt ? w_end : w_mid) * __ldg(lam + j * N + p);
-        const float* gj = gm + 3 * j * N;
-        b0 = fmaf(wl, __ldg(gj + p), b0);
-        b1 = fmaf(wl, __ldg(gj + N + p), b1);
-        b2 = fmaf(wl, __ldg(gj + 2 * N + p), b2);
+        const float wl = (j == 0 || j == nt ? w_end : w_mid) * ldf<S>(lam + j * N + p);
+        const S* gj = gm + 3 * j * N;
+        b0 = fmaf(wl, ldf<S>(gj + p), b0);
+        b1 = fmaf(wl, ldf<S>(gj + N + p), b1);
+        b2 = fmaf(wl, ldf<S>(gj + 2 * N + p), b2);
     }
     if (accumulate) {
         b0 += out[p];
@@ -90,6 +92,24 @@ __global__ void __launch_bounds__(kThreads) k_body(Grid g, const float* __restri
     out[p] = b0;
     out[N + p] = b1;
     out[2 * N + p] = b2;
+}
+
+// out = a - s in storage S (start of the adjoint: lambda^{nt} = m1 - m^{nt})
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_sub(const S* __restrict__ a, const S* __restrict__ s,
+                                                   S* __restrict__ out, uint32_t n)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p < n) stf<S>(out + p, ldf<S>(a + p) - ldf<S>(s + p));
+}
+
+// out = convert(in): FP32 <-> storage S
+template <class Si, class So>
+__global__ void __launch_bounds__(kThreads) k_convert(const Si* __restrict__ in, So* __restrict__ out,
+                                                       uint32_t n)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p < n) stf<So>(out + p, ldf<Si>(in + p));
 }
 
 // Deformation map step: u^{j+1} = u^j(X) + (X - x), three components.
@@ -117,7 +137,8 @@ __global__ void __launch_bounds__(kThreads) k_map_step(Grid g, const float* __re
 // 8th-order central finite differences
 // ---------------------------------------------------------------------------
 
-__device__ __forceinline__ float fd8_axis(const float* __restrict__ f, uint32_t p, int idx, int n,
+template <class S = float>
+__device__ __forceinline__ float fd8_axis(const S* __restrict__ f, uint32_t p, int idx, int n,
                                           int stride)
 {
     // c_s = 4/5, -1/5, 4/105, -1/280 for s = 1..4 (standard 8th-order stencil)
@@ -131,36 +152,39 @@ __device__ __forceinline__ float fd8_axis(const float* __restrict__ f, uint32_t 
         ip = ip >= n ? ip - n : ip;
         int im = idx - s;
         im = im < 0 ? im + n : im;
-        acc = fmaf(cs[s - 1], __ldg(f + base + static_cast<long>(ip) * stride) -
-                                  __ldg(f + base + static_cast<long>(im) * stride),
+        acc = fmaf(cs[s - 1], ldf<S>(f + base + static_cast<long>(ip) * stride) -
+                                  ldf<S>(f + base + static_cast<long>(im) * stride),
                    acc);
     }
     return acc;
 }
 
-__global__ void __launch_bounds__(kThreads) k_fd8_grad(Grid g, const float* __restrict__ f,
-                                                        float* __restrict__ out)
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_fd8_grad(Grid g, const S* __restrict__ f,
+                                                        S* __restrict__ out)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
     int i, j, k;
     coords_of(g, p, i, j, k);
     const size_t N = g.N;
-    out[p] = fd8_axis(f, p, i, g.n1, g.n23) * g.ih1;
-    out[N + p] = fd8_axis(f, p, j, g.n2, g.n3) * g.ih2;
-    out[2 * N + p] = fd8_axis(f, p, k, g.n3, 1) * g.ih3;
+    stf<S>(out + p, fd8_axis<S>(f, p, i, g.n1, g.n23) * g.ih1);
+    stf<S>(out + N + p, fd8_axis<S>(f, p, j, g.n2, g.n3) * g.ih2);
+    stf<S>(out + 2 * N + p, fd8_axis<S>(f, p, k, g.n3, 1) * g.ih3);
 }
 
+// divergence of an FP32 vector field, stored as S
+template <class S>
 __global__ void __launch_bounds__(kThreads) k_fd8_div(Grid g, const float* __restrict__ v,
-                                                       float* __restrict__ out)
+                                                       S* __restrict__ out)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
     int i, j, k;
     coords_of(g, p, i, j, k);
     const size_t N = g.N;
-    out[p] = fd8_axis(v, p, i, g.n1, g.n23) * g.ih1 + fd8_axis(v + N, p, j, g.n2, g.n3) * g.ih2 +
-             fd8_axis(v + 2 * N, p, k, g.n3, 1) * g.ih3;
+    stf<S>(out + p, fd8_axis(v, p, i, g.n1, g.n23) * g.ih1 + fd8_axis(v + N, p, j, g.n2, g.n3) * g.ih2 +
+                        fd8_axis(v + 2 * N, p, k, g.n3, 1) * g.ih3);
 }
 
 // det(I + grad u) in FP64 with block-wise min / max partials.
@@ -209,14 +233,17 @@ __global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* _
             KERNEL<1><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
     } while (0)
 
-void launch_interp(const Grid& g, int order, const float* f, const float* d, float* out,
+void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
                    cudaStream_t st)
 {
-    EpiStore e{out};
-    if (order == 3)
-        launch_tiled<3, EpiStore>(g, f, d, e, st);
-    else
-        launch_tiled<1, EpiStore>(g, f, d, e, st);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiStore<SType> e{static_cast<SType*>(out)};
+        const SType* fs = static_cast<const SType*>(f);
+        if (order == 3)
+            launch_tiled<3, EpiStore<SType>, SType>(g, fs, d, e, st);
+        else
+            launch_tiled<1, EpiStore<SType>, SType>(g, fs, d, e, st);
+    });
 }
 
 void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
@@ -225,46 +252,88 @@ void launch_backtrace(const Grid& g, int order, const float* v, float dt, int si
     CLAIRE_DISPATCH(order, k_backtrace, g, v, dt, static_cast<float>(sign), d);
 }
 
-void launch_adj_step(const Grid& g, int order, const float* lam_next, const float* dA,
-                     const float* divv, const float* divXp, float dt, float* lam, cudaStream_t st)
+void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
+                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st)
 {
-    EpiAdjointOnly e{divv, divXp, lam, dt};
-    if (order == 3)
-        launch_tiled<3, EpiAdjointOnly>(g, lam_next, dA, e, st);
-    else
-        launch_tiled<1, EpiAdjointOnly>(g, lam_next, dA, e, st);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiAdjointOnly<SType> e{static_cast<const SType*>(divv), static_cast<const SType*>(divXp),
+                                static_cast<SType*>(lam), dt};
+        const SType* fs = static_cast<const SType*>(lam_next);
+        if (order == 3)
+            launch_tiled<3, EpiAdjointOnly<SType>, SType>(g, fs, dA, e, st);
+        else
+            launch_tiled<1, EpiAdjointOnly<SType>, SType>(g, fs, dA, e, st);
+    });
 }
 
-void launch_inc_sources(const Grid& g, const float* vt, const float* gm, int nt, float coef0, float* q0,
-                        float* F, cudaStream_t st)
+void launch_inc_sources(const Grid& g, const float* vt, const void* gm, int nt, float coef0, void* q0,
+                        void* F, Storage sto, cudaStream_t st)
 {
-    k_inc_sources<<<blocks_for(g.N), kThreads, 0, st>>>(g, vt, gm, nt, coef0, q0, F);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_inc_sources<SType><<<blocks_for(g.N), kThreads, 0, st>>>(
+            g, vt, static_cast<const SType*>(gm), nt, coef0, static_cast<SType*>(q0), static_cast<SType*>(F));
+    });
 }
 
-void launch_body(const Grid& g, const float* lam, const float* gm, int nt, float w_end, float w_mid,
-                 int accumulate, float* out, cudaStream_t st)
+void launch_body(const Grid& g, const void* lam, const void* gm, int nt, float w_end, float w_mid,
+                 int accumulate, float* out, Storage sto, cudaStream_t st)
 {
-    k_body<<<blocks_for(g.N), kThreads, 0, st>>>(g, lam, gm, nt, w_end, w_mid, accumulate, out);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_body<SType><<<blocks_for(g.N), kThreads, 0, st>>>(g, static_cast<const SType*>(lam),
+                                                           static_cast<const SType*>(gm), nt, w_end, w_mid,
+                                                           accumulate, out);
+    });
 }
 
-void launch_inc_step_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
-                         float coef, float* q, cudaStream_t st)
+void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
+                         float coef, void* q, Storage sto, cudaStream_t st)
 {
-    EpiIncSource e{F, q, coef};
-    if (order == 3)
-        launch_tiled<3, EpiIncSource>(g, q_prev, d, e, st);
-    else
-        launch_tiled<1, EpiIncSource>(g, q_prev, d, e, st);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiIncSource<SType> e{static_cast<const SType*>(F), static_cast<SType*>(q), coef};
+        const SType* fs = static_cast<const SType*>(q_prev);
+        if (order == 3)
+            launch_tiled<3, EpiIncSource<SType>, SType>(g, fs, d, e, st);
+        else
+            launch_tiled<1, EpiIncSource<SType>, SType>(g, fs, d, e, st);
+    });
 }
 
-void launch_inc_last_src(const Grid& g, int order, const float* q_prev, const float* d, const float* F,
-                         float coef, float* lam, cudaStream_t st)
+void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
+                         float coef, void* lam, Storage sto, cudaStream_t st)
 {
-    EpiIncSourceLast e{F, lam, coef};
-    if (order == 3)
-        launch_tiled<3, EpiIncSourceLast>(g, q_prev, d, e, st);
-    else
-        launch_tiled<1, EpiIncSourceLast>(g, q_prev, d, e, st);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiIncSourceLast<SType> e{static_cast<const SType*>(F), static_cast<SType*>(lam), coef};
+        const SType* fs = static_cast<const SType*>(q_prev);
+        if (order == 3)
+            launch_tiled<3, EpiIncSourceLast<SType>, SType>(g, fs, d, e, st);
+        else
+            launch_tiled<1, EpiIncSourceLast<SType>, SType>(g, fs, d, e, st);
+    });
+}
+
+void launch_sub(const void* a, const void* b, void* out, size_t n, Storage sto, cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_sub<SType><<<blocks_for(static_cast<uint32_t>(n)), kThreads, 0, st>>>(
+            static_cast<const SType*>(a), static_cast<const SType*>(b), static_cast<SType*>(out),
+            static_cast<uint32_t>(n));
+    });
+}
+
+void launch_to_storage(const float* in, void* out, size_t n, Storage sto, cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_convert<float, SType><<<blocks_for(static_cast<uint32_t>(n)), kThreads, 0, st>>>(
+            in, static_cast<SType*>(out), static_cast<uint32_t>(n));
+    });
+}
+
+void launch_from_storage(const void* in, float* out, size_t n, Storage sto, cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_convert<SType, float><<<blocks_for(static_cast<uint32_t>(n)), kThreads, 0, st>>>(
+            static_cast<const SType*>(in), out, static_cast<uint32_t>(n));
+    });
 }
 
 void launch_map_step(const Grid& g, int order, const float* u_prev, const float* d, float* u,
@@ -273,14 +342,19 @@ void launch_map_step(const Grid& g, int order, const float* u_prev, const float*
     CLAIRE_DISPATCH(order, k_map_step, g, u_prev, d, u);
 }
 
-void launch_fd8_grad(const Grid& g, const float* f, float* out, cudaStream_t st)
+void launch_fd8_grad(const Grid& g, const void* f, void* out, Storage sto, cudaStream_t st)
 {
-    k_fd8_grad<<<blocks_for(g.N), kThreads, 0, st>>>(g, f, out);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_fd8_grad<SType><<<blocks_for(g.N), kThreads, 0, st>>>(g, static_cast<const SType*>(f),
+                                                               static_cast<SType*>(out));
+    });
 }
 
-void launch_fd8_div(const Grid& g, const float* v, float* out, cudaStream_t st)
+void launch_fd8_div(const Grid& g, const float* v, void* out, Storage sto, cudaStream_t st)
 {
-    k_fd8_div<<<blocks_for(g.N), kThreads, 0, st>>>(g, v, out);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_fd8_div<SType><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, static_cast<SType*>(out));
+    });
 }
 
 void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,

@@ -65,13 +65,13 @@ __device__ __forceinline__ void axis_weights(float t, float w[4])
 // Direct global-memory gather for tiles whose departure box does not fit
 // (kept out of line so that it does not add to the register budget of the
 // shared-memory path).
-template <int ORDER>
-__device__ __noinline__ float gather_global(const Grid g, const float* __restrict__ f, int i, int j,
+template <int ORDER, class S>
+__device__ __noinline__ float gather_global(const Grid g, const S* __restrict__ f, int i, int j,
                                             int k, float d1, float d2, float d3)
 {
     Stencil<ORDER> s;
     s.build(g, i, j, k, d1, d2, d3);
-    return s.eval(f);
+    return s.template eval<S>(f);
 }
 
 // ---- building blocks of the tiled gathers ----
@@ -85,7 +85,9 @@ struct BoxPar {
 
 // Block-wide bounds of the stencils whose first-node cells (before the
 // -OFF shift) span [lo, hi] per axis; thread 0 publishes the box in par.
-template <int ORDER>
+// ES: bytes per stored value of the field (4, or 2 for FP16 / BF16 storage,
+// whose box is staged as raw 16-bit pairs before widening to FP32).
+template <int ORDER, int ES = 4>
 __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
                                            int hi3, int (*red)[TILE2], int* par, int lane, int warp)
 {
@@ -111,11 +113,19 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
         }
         // box of the stencils: cells [a - OFF, z - OFF + M); the tile always
         // holds at least one valid point
-        const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M,
-                        e3 = (long long)z3 - a3 + M;
+        long long o3 = (long long)a3 - OFF;
+        long long e3 = (long long)z3 - a3 + M;
+        if (ES == 2) {  // even x3 origin and extent: 4-byte aligned 16-bit pairs
+            const long long o3e = o3 & ~1LL;
+            e3 = (e3 + (o3 - o3e) + 1) & ~1LL;
+            o3 = o3e;
+        }
+        const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M;
         const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
-        const bool fits = e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && e1 * e2 * s3 <= kBoxCapFloats;
-        par[0] = a1 - OFF; par[1] = a2 - OFF; par[2] = a3 - OFF;
+        // FP32 box plus, for 16-bit storage, the staging copy (half its size)
+        const long long need = e1 * e2 * s3 * (ES == 2 ? 3 : 2) / 2;
+        const bool fits = e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && need <= kBoxCapFloats;
+        par[0] = a1 - OFF; par[1] = a2 - OFF; par[2] = static_cast<int>(o3);
         par[3] = static_cast<int>(fits ? e1 : 0);
         par[4] = static_cast<int>(fits ? e2 : 0);
         par[5] = static_cast<int>(fits ? e3 : 0);
@@ -128,8 +138,19 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
     return b;
 }
 
-// Issue the cp.async copies of the (periodically wrapped) box of f.
-__device__ __forceinline__ void tile_load_box(const Grid& g, const float* __restrict__ f, float* box,
+// Copy the (periodically wrapped) box of f into shared memory as FP32:
+// asynchronously (cp.async) for FP32 storage, converting loads otherwise.
+template <class S>
+__device__ __forceinline__ void box_copy(float* dst, const S* src)
+{
+    if constexpr (sizeof(S) == 4)
+        cp_async_f32(dst, reinterpret_cast<const float*>(src));
+    else
+        *dst = ldf<S>(src);
+}
+
+template <class S>
+__device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict__ f, float* box,
                                               const BoxPar& bp, int lane, int warp)
 {
     const int w1 = wrap_index(bp.O1, g.n1), w2 = wrap_index(bp.O2, g.n2), w3 = wrap_index(bp.O3, g.n3);
@@ -137,21 +158,62 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const float* __rest
     gk0 = gk0 >= g.n3 ? gk0 - g.n3 : gk0;
     int gk1 = w3 + lane + 32;
     gk1 = gk1 >= g.n3 ? gk1 - g.n3 : gk1;
-    for (int a = 0; a < bp.E1; ++a) {
-        int gi = w1 + a;
-        gi = gi >= g.n1 ? gi - g.n1 : gi;
-        const float* plane = f + static_cast<size_t>(gi) * g.n23;
-        for (int b = warp; b < bp.E2; b += TILE2) {
-            int gj = w2 + b;
-            gj = gj >= g.n2 ? gj - g.n2 : gj;
-            const float* src = plane + gj * g.n3;
-            float* dst = box + (a * bp.E2 + b) * bp.S3;
-            if (lane < bp.E3) cp_async_f32(dst + lane, src + gk0);
-            if (lane + 32 < bp.E3) cp_async_f32(dst + lane + 32, src + gk1);
-            for (int c = lane + 64; c < bp.E3; c += 32) {
-                int gk = w3 + c;
-                gk = gk >= g.n3 ? gk - g.n3 : gk;
-                cp_async_f32(dst + c, src + gk);
+    if constexpr (sizeof(S) == 4) {
+        for (int a = 0; a < bp.E1; ++a) {
+            int gi = w1 + a;
+            gi = gi >= g.n1 ? gi - g.n1 : gi;
+            const S* plane = f + static_cast<size_t>(gi) * g.n23;
+            for (int b = warp; b < bp.E2; b += TILE2) {
+                int gj = w2 + b;
+                gj = gj >= g.n2 ? gj - g.n2 : gj;
+                const S* src = plane + gj * g.n3;
+                float* dst = box + (a * bp.E2 + b) * bp.S3;
+                if (lane < bp.E3) box_copy<S>(dst + lane, src + gk0);
+                if (lane + 32 < bp.E3) box_copy<S>(dst + lane + 32, src + gk1);
+                for (int c = lane + 64; c < bp.E3; c += 32) {
+                    int gk = w3 + c;
+                    gk = gk >= g.n3 ? gk - g.n3 : gk;
+                    box_copy<S>(dst + c, src + gk);
+                }
+            }
+        }
+    } else {
+        // 16-bit storage: raw pairs (4 bytes, aligned: even origin, even n3)
+        // go asynchronously to a staging area behind the FP32 box; after they
+        // land, every thread widens a share of them to FP32 in the box.
+        const int rows = bp.E1 * bp.E2;
+        const int pairs = bp.E3 / 2;
+        uint32_t* stage = reinterpret_cast<uint32_t*>(box + rows * bp.S3);
+        for (int a = 0; a < bp.E1; ++a) {
+            int gi = w1 + a;
+            gi = gi >= g.n1 ? gi - g.n1 : gi;
+            const S* plane = f + static_cast<size_t>(gi) * g.n23;
+            for (int b = warp; b < bp.E2; b += TILE2) {
+                int gj = w2 + b;
+                gj = gj >= g.n2 ? gj - g.n2 : gj;
+                const S* src = plane + gj * g.n3;
+                uint32_t* dst = stage + (a * bp.E2 + b) * (bp.S3 / 2);
+                for (int c = lane; c < pairs; c += 32) {
+                    int gk = w3 + 2 * c;
+                    gk = gk >= g.n3 ? gk - g.n3 : gk;
+                    cp_async_f32(reinterpret_cast<float*>(dst + c), reinterpret_cast<const float*>(src + gk));
+                }
+            }
+        }
+        cp_async_wait_all();
+        __syncthreads();
+        for (int r = warp; r < rows; r += TILE2) {
+            const uint32_t* sp = stage + r * (bp.S3 / 2);
+            float* dst = box + r * bp.S3;
+            for (int c = lane; c < pairs; c += 32) {
+                const uint32_t w = sp[c];
+                S lo, hi;
+                const unsigned short ulo = static_cast<unsigned short>(w & 0xffffu);
+                const unsigned short uhi = static_cast<unsigned short>(w >> 16);
+                memcpy(&lo, &ulo, 2);
+                memcpy(&hi, &uhi, 2);
+                dst[2 * c] = to_f32<S>(lo);
+                dst[2 * c + 1] = to_f32<S>(hi);
             }
         }
     }
@@ -267,9 +329,9 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
 // x1/x2 displacement) read 32 different banks.  The epilogue's operands are
 // requested (prefetch) while the box is in flight and consumed (finish) after
 // the stencil is evaluated.
-template <int ORDER, class Epi>
+template <int ORDER, class Epi, class S>
 __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
-    k_gather_tiled(Grid g, const float* __restrict__ f, const float* __restrict__ d, Epi epi)
+    k_gather_tiled(Grid g, const S* __restrict__ f, const float* __restrict__ d, Epi epi)
 {
     extern __shared__ float box[];
     __shared__ int red[6][TILE2];
@@ -300,9 +362,9 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
             lo3 = min(lo3, b3); hi3 = max(hi3, b3);
         }
     }
-    const BoxPar bp = tile_box<ORDER>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
+    const BoxPar bp = tile_box<ORDER, sizeof(S)>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
     const bool use_box = bp.E1 != 0;
-    if (use_box) tile_load_box(g, f, box, bp, lane, warp);
+    if (use_box) tile_load_box<S>(g, f, box, bp, lane, warp);
     // epilogue operands of every point are requested while the box is in flight
     typename Epi::Pre pre[TILE1];
 #pragma unroll
@@ -317,7 +379,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
         const int i = i0 + q;
         if (!(col_ok && i < g.n1)) continue;
         const float val = use_box ? tile_eval<ORDER>(box, bp, i, j, k, d1[q], d2[q], d3[q])
-                                  : gather_global<ORDER>(g, f, i, j, k, d1[q], d2[q], d3[q]);
+                                  : gather_global<ORDER, S>(g, f, i, j, k, d1[q], d2[q], d3[q]);
         epi.finish(p0 + q * g.n23, val, pre[q]);
     }
 }
@@ -329,65 +391,76 @@ inline dim3 tiled_grid(const Grid& g)
 
 constexpr size_t kTiledSmemBytes = kBoxCapFloats * sizeof(float);
 
-template <int ORDER, class Epi>
-inline void launch_tiled(const Grid& g, const float* f, const float* d, const Epi& e, cudaStream_t st)
+template <int ORDER, class Epi, class S>
+inline void launch_tiled(const Grid& g, const S* f, const float* d, const Epi& e, cudaStream_t st)
 {
     if (kTiledSmemBytes > 48 * 1024)
-        cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kTiledSmemBytes));
-    k_gather_tiled<ORDER, Epi><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
+    k_gather_tiled<ORDER, Epi, S><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
 }
 
-// ---- epilogues: prefetch(p) loads the point's operands early, finish(p, v, pre) completes ----
+// ---- epilogues: prefetch(p) loads the point's operands early, finish(p, v, pre)
+// completes; S is the storage type of the fields they read and write ----
 
 // plain interpolation / state step: out = f(X)
+template <class S>
 struct EpiStore {
-    float* __restrict__ out;
+    S* __restrict__ out;
     struct Pre {};
     __device__ __forceinline__ Pre prefetch(uint32_t) const { return Pre{}; }
-    __device__ __forceinline__ void finish(uint32_t p, float v, const Pre&) const { out[p] = v; }
+    __device__ __forceinline__ void finish(uint32_t p, float v, const Pre&) const { stf<S>(out + p, v); }
 };
 
 // adjoint step (Eq. (4), Heun along X+): lambda^j from lambda^{j+1}(X+)
+template <class S>
 struct EpiAdjointOnly {
-    const float* __restrict__ divv;
-    const float* __restrict__ divXp;
-    float* __restrict__ lam;
+    const S* __restrict__ divv;
+    const S* __restrict__ divXp;
+    S* __restrict__ lam;
     float dt;
     struct Pre {
         float dX, dx;
     };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{__ldg(divXp + p), __ldg(divv + p)}; }
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{ldf<S>(divXp + p), ldf<S>(divv + p)}; }
     __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
     {
         const float adX = a * r.dX;
         const float pred = fmaf(dt, adX, a);
-        lam[p] = fmaf(0.5f * dt, fmaf(pred, r.dx, adX), a);
+        stf<S>(lam + p, fmaf(0.5f * dt, fmaf(pred, r.dx, adX), a));
     }
 };
 
 // incremental state with precomputed source: q = f(X) + coef F
+template <class S>
 struct EpiIncSource {
-    const float* __restrict__ F;
-    float* __restrict__ q;
+    const S* __restrict__ F;
+    S* __restrict__ q;
     float coef;
     struct Pre {
         float f;
     };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{__ldg(F + p)}; }
-    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const { q[p] = fmaf(coef, r.f, a); }
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{ldf<S>(F + p)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        stf<S>(q + p, fmaf(coef, r.f, a));
+    }
 };
 
 // last incremental state step, start of the incremental adjoint: lt = -(f(X) + coef F)
+template <class S>
 struct EpiIncSourceLast {
-    const float* F;  // may alias lam: each point reads its F before writing lam
-    float* lam;
+    const S* F;  // may alias lam: each point reads its F before writing lam
+    S* lam;
     float coef;
     struct Pre {
         float f;
     };
-    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{F[p]}; }
-    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const { lam[p] = -fmaf(coef, r.f, a); }
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{to_f32<S>(F[p])}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        stf<S>(lam + p, -fmaf(coef, r.f, a));
+    }
 };
 
 }  // namespace claire

@@ -351,27 +351,29 @@ __global__ void __launch_bounds__(kThreads) k_dot_partial(const float* __restric
     block_sum(acc, partials);
 }
 
-__global__ void __launch_bounds__(kThreads) k_sqdiff_partial(const float* __restrict__ a,
-                                                              const float* __restrict__ b, size_t n,
-                                                              double* __restrict__ partials)
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_sqdiff_partial(const S* __restrict__ a, const S* __restrict__ b,
+                                                              size_t n, double* __restrict__ partials)
 {
     double acc = 0.0;
     const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
     const size_t t0 = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
     size_t done = 0;
-    if (aligned16(a) && aligned16(b)) {
-        const size_t n4 = n / 4;
-        const float4* a4 = reinterpret_cast<const float4*>(a);
-        const float4* b4 = reinterpret_cast<const float4*>(b);
-        for (size_t i = t0; i < n4; i += stride) {
-            const float4 p = __ldg(a4 + i), q = __ldg(b4 + i);
-            const float d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z, d3 = p.w - q.w;
-            acc += static_cast<double>(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
+    if constexpr (sizeof(S) == 4) {
+        if (aligned16(a) && aligned16(b)) {
+            const size_t n4 = n / 4;
+            const float4* a4 = reinterpret_cast<const float4*>(a);
+            const float4* b4 = reinterpret_cast<const float4*>(b);
+            for (size_t i = t0; i < n4; i += stride) {
+                const float4 p = __ldg(a4 + i), q = __ldg(b4 + i);
+                const float d0 = p.x - q.x, d1 = p.y - q.y, d2 = p.z - q.z, d3 = p.w - q.w;
+                acc += static_cast<double>(d0 * d0 + d1 * d1 + d2 * d2 + d3 * d3);
+            }
+            done = n4 * 4;
         }
-        done = n4 * 4;
     }
     for (size_t i = done + t0; i < n; i += stride) {
-        const float d = a[i] - b[i];
+        const float d = ldf<S>(a + i) - ldf<S>(b + i);
         acc += static_cast<double>(d * d);
     }
     block_sum(acc, partials);
@@ -570,10 +572,13 @@ void launch_dot_partial(const float* x, const float* y, size_t n, double* partia
     k_dot_partial<<<nblocks, kThreads, 0, st>>>(x, y, n, partials);
 }
 
-void launch_sqdiff_partial(const float* a, const float* b, size_t n, double* partials, int nblocks,
-                           cudaStream_t st)
+void launch_sqdiff_partial(const void* a, const void* b, size_t n, double* partials, int nblocks,
+                           Storage sto, cudaStream_t st)
 {
-    k_sqdiff_partial<<<nblocks, kThreads, 0, st>>>(a, b, n, partials);
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_sqdiff_partial<SType><<<nblocks, kThreads, 0, st>>>(static_cast<const SType*>(a),
+                                                             static_cast<const SType*>(b), n, partials);
+    });
 }
 
 void launch_maxnorm3_partial(const float* v, size_t N, double* partials, int nblocks,

@@ -51,6 +51,22 @@ def test_query_workspace_scales_with_grid_and_nt(claire):
     assert 60 * 4 * 64 ** 3 < b64 < 85 * 4 * 64 ** 3
 
 
+def test_reduced_storage_shrinks_workspace(claire):
+    o32 = claire.claire_default_opts()
+    o16 = claire.claire_default_opts()
+    o16.storage = claire.STORAGE_F16
+    ob = claire.claire_default_opts()
+    ob.storage = claire.STORAGE_BF16
+    b32 = claire.claire_query_workspace((64, 64, 64), 4, o32)
+    b16 = claire.claire_query_workspace((64, 64, 64), 4, o16)
+    assert claire.claire_query_workspace((64, 64, 64), 4, ob) == b16
+    # 2 + 2 + 5 + 15 + 5 = 29 scalar fields per point drop from 4 to 2 bytes
+    assert abs((b32 - b16) - 29 * 2 * 64 ** 3) < 64 * 1024
+    o16.storage = 3
+    with pytest.raises(claire.ClaireError):
+        claire.claire_query_workspace((64, 64, 64), 4, o16)
+
+
 @pytest.mark.parametrize("grid", [(7, 8, 8), (8, 8, 9), (6, 8, 8), (0, 8, 8)])
 def test_invalid_grids_rejected(claire, grid):
     with pytest.raises(claire.ClaireError) as e:

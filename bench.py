@@ -53,6 +53,9 @@ def parse_args():
     ap.add_argument("--storage", default="f32", choices=["f32", "f16", "bf16"],
                     help="storage precision of the solver's scalar fields (arithmetic is FP32)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--mixed-report", action="store_true",
+                    help="FP32 vs FP16 vs BF16 storage on the blob workload at --n (default 512): "
+                         "time, throughput and each result's error against the FP64 oracle")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -401,8 +404,78 @@ def run_ours(args):
         pg.destroy_process_group()
 
 
+def run_mixed_report(args):
+    """Blob template (8 Gaussian blobs + sine, clipped) with a velocity of 6
+    random modes |k| <= 16 per component, max |v| = 0.5, at n^3; one
+    registration per storage type; errors against the FP64 oracle evaluated
+    at each returned velocity on the same FP32 images."""
+    import torch
+    import oracle
+    from paper_2209_08189_gb300 import claire, synth
+    import __graft_entry__ as entry
+    entry.build()
+    n = args.n if args.n != 256 else 512
+    grid = (n, n, n)
+    dev = torch.device("cuda", 0)
+    m0 = synth.blob_template(grid, seed=0).astype(np.float32)
+    vstar = synth.mode_velocity(grid, seed=0, nmodes=6, kmax=16, vmax=0.5).astype(np.float32)
+    ctx = claire.Context(grid, args.beta, 4, stream=torch.cuda.current_stream().cuda_stream)
+    m1d = torch.empty(grid, device=dev)
+    ctx.transport(torch.from_numpy(vstar).to(dev), torch.from_numpy(m0).to(dev), m1d, claire.TRANSPORT_FWD)
+    m1 = m1d.cpu().numpy()
+    ctx.close()
+    p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
+    m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
+    out = {"workload": "blob template, 6 modes |k|<=16 per component, max|v|=0.5, %d^3, nt=4, "
+                       "tricubic, beta_v=%g, gtol 5e-2" % (n, args.beta), "runs": {}}
+    vel = {}
+    for name, sto in (("f32", claire.STORAGE_F32), ("f16", claire.STORAGE_F16), ("bf16", claire.STORAGE_BF16)):
+        ctx = claire.Context(grid, args.beta, 4, stream=torch.cuda.current_stream().cuda_stream, beta_w=1e-4,
+                             gtol=5e-2, max_gn=50, max_pcg=50, storage=sto)
+        ctx.set_images(torch.from_numpy(m0).to(dev), torch.from_numpy(m1).to(dev))
+        v = torch.zeros((3,) + grid, device=dev)
+        ctx.register(v)  # warm-up
+        v.zero_()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        st, rep = ctx.register(v)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        vh = v.cpu().numpy()
+        vel[name] = vh
+        ctx.close()
+        v64 = vh.astype(np.float64)
+        J_o, mis_o, _ = oracle.objective(v64, m0_64, m1_64, p)
+        dj = oracle.detj(v64, p)
+        out["runs"][name] = {
+            "time_to_tol_s": secs, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+            "gnorm_rel": rep["gnorm_rel"], "interp_gpts_s": rep["interp_points"] / secs / 1e9,
+            "mismatch_rel_err_vs_oracle": abs(rep["mismatch"] - mis_o) / mis_o,
+            "J_rel_err_vs_oracle": abs(rep["J"] - J_o) / J_o,
+            "detj_min": rep["detj_min"], "detj_max": rep["detj_max"],
+            "detj_rel_err_vs_oracle": max(abs(rep["detj_min"] - dj.min()) / dj.min(),
+                                          abs(rep["detj_max"] - dj.max()) / dj.max()),
+            "r": rep["r"]}
+        del dj
+    ref = vel["f32"].astype(np.float64)
+    for name in ("f16", "bf16"):
+        out["runs"][name]["velocity_rel_l2_vs_f32"] = float(
+            np.linalg.norm(vel[name] - ref) / np.linalg.norm(ref))
+    # transport of m0 by the mixed velocity: GPU FP32 kernel vs oracle
+    ctx = claire.Context(grid, args.beta, 4, stream=torch.cuda.current_stream().cuda_stream)
+    mt = torch.empty(grid, device=dev)
+    ctx.transport(torch.from_numpy(vel["f16"]).to(dev), torch.from_numpy(m0).to(dev), mt, claire.TRANSPORT_FWD)
+    mo = oracle.transport(m0_64, vel["f16"].astype(np.float64), p)
+    out["transport_rel_l2_vs_oracle"] = float(np.linalg.norm(mt.cpu().numpy() - mo) / np.linalg.norm(mo))
+    ctx.close()
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.mixed_report:
+        run_mixed_report(args)
+        return
     if args.impl == "reference":
         run_reference(args)
     else:

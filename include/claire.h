@@ -209,6 +209,24 @@ claire_status claire_register(claire_ctx* ctx, float* v_inout, claire_report* re
 claire_status claire_transport(claire_ctx* ctx, const float* v, const float* m_in, float* m_out,
                                int flags);
 
+/*
+ * Reverse-mode derivative of the discrete forward transport m(1) = T(v)^nt m0
+ * (the same SL steps as CLAIRE_TRANSPORT_FWD: Heun characteristic X with the
+ * velocity interpolated at the predictor, nt gathers; Sec. 2.2).  Given
+ * gbar = dL/dm(1) (N floats) it returns the exact derivatives of the discrete
+ * map (discretise-then-differentiate): gm0 = dL/dm0 (N floats) and
+ * gv = dL/dv (3N floats, physical units); either output may be NULL.  The
+ * scatter transposes accumulate 64-bit fixed-point integers, so results are
+ * bitwise reproducible.  flags: CLAIRE_VJP_RECOMPUTE keeps only m0 and
+ * recomputes m^j during the backward sweep (time-step checkpointing: 2 N
+ * floats of states instead of (nt+1) N).  The first call allocates its
+ * scratch ((nt+1) N floats + N 64-bit accumulators); the call invalidates the
+ * linearisation point of claire_hessian_matvec.  Computes in FP32.
+ */
+#define CLAIRE_VJP_RECOMPUTE 1
+claire_status claire_transport_vjp(claire_ctx* ctx, const float* v, const float* m0, const float* gbar,
+                                   float* gm0, float* gv, int flags);
+
 /* Extrema of the Jacobian determinant det grad y of the deformation map of v
  * (Sec. 3, "J_min"; y = x + u with u transported by the state's SL steps,
  * F = I + FD8(u), det and extrema in FP64). */

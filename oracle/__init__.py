@@ -44,7 +44,8 @@ __all__ = [
     "fd8_grad", "fd8_div", "reg_apply", "reg_inverse", "project_K", "reg_energy",
     "characteristics", "forward_solve", "adjoint_solve", "state_at", "objective",
     "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
-    "transport", "deformation_map", "detj", "cfl", "inner", "num_threads",
+    "transport", "transport_vjp", "interp_grad", "deformation_map", "detj", "cfl", "inner",
+    "num_threads",
 ]
 
 _lib = None
@@ -60,6 +61,7 @@ def _load():
         lib.orc_interp.argtypes = [lp, dp, dp, ctypes.c_int, dp]
         lib.orc_interp_points.argtypes = [lp, dp, dp, ctypes.c_long, ctypes.c_int, dp]
         lib.orc_interp_transpose.argtypes = [lp, dp, dp, ctypes.c_int, dp]
+        lib.orc_interp_grad.argtypes = [lp, dp, dp, ctypes.c_int, dp]
         lib.orc_backtrace.argtypes = [lp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
         lib.orc_fd8_grad.argtypes = [lp, dp, dp]
         lib.orc_fd8_div.argtypes = [lp, dp, dp]
@@ -128,6 +130,14 @@ def interp_T(yv, d, order=3):
     yv = _f64(yv); d = _f64(d)
     out = np.empty_like(yv)
     _load().orc_interp_transpose(_n(yv.shape), _dp(yv), _dp(d), int(order), _dp(out))
+    return out
+
+
+def interp_grad(f, d, order=3):
+    """Gradient of the interpolant of f at x + d (grid units), shape (3, *f.shape)."""
+    f = _f64(f); d = _f64(d)
+    out = np.empty((3,) + f.shape)
+    _load().orc_interp_grad(_n(f.shape), _dp(f), _dp(d), int(order), _dp(out))
     return out
 
 
@@ -511,6 +521,44 @@ def transport(m_in, v, p: Params, direction="fwd"):
     for _ in range(p.nt):
         lam = _adjoint_step(lam, ch, p)
     return lam
+
+
+def transport_vjp(m0, v, gbar, p: Params):
+    """Exact reverse-mode derivative of the discrete forward transport
+    m(1) = T(v)^nt m0 (discretise-then-differentiate).
+
+    Forward, per node x (grid units u = v / h): predictor y = x - dt u(x),
+    U = I[u](y), displacement d = -dt/2 (u(x) + U), X = x + d and
+    m^{j+1}(x) = I[m^j](X(x)).  Given gbar = dL/dm(1) it returns
+    (dL/dm0, dL/dv) by the chain rule through the interpolation weights
+    (their t-derivatives), the scatter transposes at X and at y, and the
+    predictor; the interpolation of v uses the same scheme as the image.
+    """
+    m0 = _f64(m0); v = _f64(v)
+    n = m0.shape
+    h = spacing(n)
+    dt = p.dt
+    u = np.stack([v[c] / h[c] for c in range(3)])
+    dpred = -dt * u                       # y - x
+    U = np.stack([interp(u[c], dpred, p.order) for c in range(3)])
+    d = -0.5 * dt * (u + U)
+    ms = [m0]
+    for _ in range(p.nt):
+        ms.append(interp(ms[-1], d, p.order))
+    mbar = _f64(gbar)
+    dbar = np.zeros_like(u)
+    for j in range(p.nt - 1, -1, -1):
+        dbar += mbar[None] * interp_grad(ms[j], d, p.order)
+        mbar = interp_T(mbar, d, p.order)
+    ubar = -0.5 * dt * dbar               # direct term of d
+    Ubar = -0.5 * dt * dbar               # through U = I[u](y)
+    ybar = np.zeros_like(u)
+    for c in range(3):
+        ubar[c] += interp_T(Ubar[c], dpred, p.order)
+        ybar += Ubar[c][None] * interp_grad(u[c], dpred, p.order)
+    ubar += -dt * ybar                    # y = x - dt u
+    vbar = np.stack([ubar[c] / h[c] for c in range(3)])
+    return mbar, vbar
 
 
 def deformation_map(v, p: Params):

@@ -65,6 +65,32 @@ static int orc_basis(int order, double t, long off[4], double w[4])
     return 2;
 }
 
+/* Derivative of the 1-D basis with respect to t: d/dt of each cardinal
+ * polynomial, prod rule over its factors; linear: -1, 1. */
+static void orc_basis_deriv(int order, double t, double dw[4])
+{
+    if (order == 3) {
+        const double s[4] = {-1.0, 0.0, 1.0, 2.0};
+        for (int a = 0; a < 4; ++a) {
+            double den = 1.0;
+            for (int b = 0; b < 4; ++b)
+                if (b != a) den *= (s[a] - s[b]);
+            double sum = 0.0;
+            for (int skip = 0; skip < 4; ++skip) {
+                if (skip == a) continue;
+                double prod = 1.0;
+                for (int b = 0; b < 4; ++b)
+                    if (b != a && b != skip) prod *= (t - s[b]);
+                sum += prod;
+            }
+            dw[a] = sum / den;
+        }
+        return;
+    }
+    dw[0] = -1.0;
+    dw[1] = 1.0;
+}
+
 /* Stencil of the interpolant at grid-unit position y: wrapped node indices
  * and tensor-product weights.  Returns the node count per axis. */
 static int orc_stencil(const long n[3], const double y[3], int order,
@@ -92,6 +118,34 @@ static double orc_interp_at(const long n[3], const double *f, const double y[3],
                 s += w[0][a] * w[1][b] * w[2][c] *
                      f[(idx[0][a] * n[1] + idx[1][b]) * n[2] + idx[2][c]];
     return s;
+}
+
+/* Gradient (grid units, per axis) of the interpolant of f at x_p + d_p for
+ * every node p: out[c][p] = d/dy_c I[f](y) at y = x_p + d_p. */
+void orc_interp_grad(const long n[3], const double *f, const double *d, int order, double *out)
+{
+    const long N = n[0] * n[1] * n[2];
+#pragma omp parallel for schedule(static)
+    for (long p = 0; p < N; ++p) {
+        long i = p / (n[1] * n[2]), j = (p / n[2]) % n[1], k = p % n[2];
+        double y[3] = {i + d[p], j + d[N + p], k + d[2 * N + p]};
+        long idx[3][4];
+        double w[3][4], dw[3][4];
+        int m = orc_stencil(n, y, order, idx, w);
+        for (int c = 0; c < 3; ++c) orc_basis_deriv(order, y[c] - floor(y[c]), dw[c]);
+        double g0 = 0.0, g1 = 0.0, g2 = 0.0;
+        for (int a = 0; a < m; ++a)
+            for (int b = 0; b < m; ++b)
+                for (int c = 0; c < m; ++c) {
+                    double fv = f[(idx[0][a] * n[1] + idx[1][b]) * n[2] + idx[2][c]];
+                    g0 += dw[0][a] * w[1][b] * w[2][c] * fv;
+                    g1 += w[0][a] * dw[1][b] * w[2][c] * fv;
+                    g2 += w[0][a] * w[1][b] * dw[2][c] * fv;
+                }
+        out[p] = g0;
+        out[N + p] = g1;
+        out[2 * N + p] = g2;
+    }
 }
 
 int orc_num_threads(void)

@@ -101,6 +101,7 @@ _SIGS = {
     "claire_register": [_vp, _vp, ctypes.POINTER(claire_report)],
     "claire_transport": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_detj": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "claire_transport_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_interp": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_backtrace": [_vp, _vp, _vp, ctypes.c_int],
     "claire_fd8_grad": [_vp, _vp, _vp],
@@ -230,6 +231,14 @@ def claire_transport(ctx, v, m_in, m_out, flags=TRANSPORT_FWD):
     return _check(ctx, lib().claire_transport(ctx, _ptr(v), _ptr(m_in), _ptr(m_out), int(flags)))
 
 
+VJP_RECOMPUTE = 1
+
+
+def claire_transport_vjp(ctx, v, m0, gbar, gm0=None, gv=None, flags=0):
+    return _check(ctx, lib().claire_transport_vjp(ctx, _ptr(v), _ptr(m0), _ptr(gbar), _ptr(gm0), _ptr(gv),
+                                                  int(flags)))
+
+
 def claire_detj(ctx, v):
     lo = ctypes.c_double()
     hi = ctypes.c_double()
@@ -350,6 +359,9 @@ class Context:
     def detj(self, v):
         return claire_detj(self.handle, v)
 
+    def transport_vjp(self, v, m0, gbar, gm0=None, gv=None, recompute=False):
+        claire_transport_vjp(self.handle, v, m0, gbar, gm0, gv, VJP_RECOMPUTE if recompute else 0)
+
     def interp(self, f, d, out, order=INTERP_CUBIC):
         claire_interp(self.handle, f, d, out, order)
 
@@ -373,3 +385,34 @@ class Context:
 
     def set_timing(self, on):
         claire_set_timing(self.handle, on)
+
+
+def sl_transport(context, m0, v, recompute=False):
+    """Differentiable semi-Lagrangian transport m(1) = T(v)^nt m0 on the GPU.
+
+    Forward: claire_transport; backward: claire_transport_vjp (exact
+    derivative of the discrete map, hand-written scatter-transpose and
+    interpolant-gradient kernels).  m0: (N1,N2,N3), v: (3,N1,N2,N3) float32
+    CUDA tensors; context: a Context on the same grid.  torch is imported
+    here only for the autograd plumbing.
+    """
+    import torch
+
+    class _SLTransport(torch.autograd.Function):
+        @staticmethod
+        def forward(fctx, m0_, v_):
+            m0c, vc = m0_.detach().contiguous(), v_.detach().contiguous()
+            out = torch.empty_like(m0c)
+            context.transport(vc, m0c, out, TRANSPORT_FWD)
+            fctx.save_for_backward(m0c, vc)
+            return out
+
+        @staticmethod
+        def backward(fctx, gout):
+            m0c, vc = fctx.saved_tensors
+            gm0 = torch.empty_like(m0c) if fctx.needs_input_grad[0] else None
+            gv = torch.empty_like(vc) if fctx.needs_input_grad[1] else None
+            context.transport_vjp(vc, m0c, gout.detach().contiguous(), gm0, gv, recompute)
+            return gm0, gv
+
+    return _SLTransport.apply(m0, v)

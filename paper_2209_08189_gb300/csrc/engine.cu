@@ -37,13 +37,15 @@ enum KernelKind {
     KK_VECTOR,
     KK_MAP,
     KK_DETJ,
+    KK_VJP_GRAD,     // interpolant-gradient accumulation (reverse mode)
+    KK_VJP_SCATTER,  // fixed-point scatter transpose (reverse mode)
     KK_COUNT
 };
 
 const char* kKernelNames[KK_COUNT] = {
     "sl_interp",  "sl_backtrace_rk2", "sl_adjoint_step", "sl_incremental_step",
     "sl_incremental_last", "sl_pointwise", "fd8", "spectral_scale", "cufft", "reduce_f64",
-    "vector_update", "sl_map_step", "detj_minmax"};
+    "vector_update", "sl_map_step", "detj_minmax", "vjp_interp_grad", "vjp_scatter"};
 
 struct KernelStat {
     double launches = 0, seconds = 0, bytes = 0, points = 0;
@@ -94,6 +96,10 @@ struct claire_ctx {
     double* dres = nullptr;               // device scalars
     double* hres = nullptr;               // pinned host scalars
 
+    // reverse-mode transport scratch, allocated by the first claire_transport_vjp
+    float* vjp_states = nullptr;            // (nt+1) N, FP32 (2 N when checkpointing)
+    size_t vjp_states_n = 0;
+    unsigned long long* vjp_acc = nullptr;  // N fixed-point accumulators
     bool have_images = false, have_lin = false;
     double J_lin = 0, mis_lin = 0, reg_lin = 0;
 
@@ -122,6 +128,10 @@ struct claire_ctx {
         }
         if (arena) cudaFree(arena);
         arena = nullptr;
+        if (vjp_states) cudaFree(vjp_states);
+        vjp_states = nullptr;
+        if (vjp_acc) cudaFree(vjp_acc);
+        vjp_acc = nullptr;
         if (hres) cudaFreeHost(hres);
         hres = nullptr;
     }
@@ -1174,6 +1184,105 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
     }
     CL_TRY(sync_scalars(c, 0));
     CL_TRY(copy_out(c, m_out, src, N));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+namespace {
+
+// out = W(x + disp)^T yv (replacing, or added to out), times mult; disp = d or predictor of v.
+claire_status scatter_transpose(claire_ctx* c, const float* yv, const float* d, const float* v, float* out,
+                                bool accumulate, float mult)
+{
+    // the fixed-point scale follows max |yv|, computed on the device (no host round trip)
+    double* mx = c->dres + 8;
+    launch_maxabs(yv, c->N, c->partials, c->red_blocks, mx, c->stream);
+    CL_LAUNCHED(c);
+    {
+        KTimer t(c, KK_VJP_SCATTER, (4.0 + 12.0) * c->N, 1.0 * c->N);
+        launch_scatter_fixed(c->grid, c->o.interp, yv, d, v, static_cast<float>(c->dt), mx + 1, c->vjp_acc,
+                             c->stream);
+        CL_LAUNCHED(c);
+    }
+    launch_fixed_to_float(c->vjp_acc, mx + 1, accumulate ? 1 : 0, mult, out, c->N, c->stream);
+    CL_LAUNCHED(c);
+    return CLAIRE_OK;
+}
+
+}  // namespace
+
+extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, const float* m0,
+                                              const float* gbar, float* gm0, float* gv, int flags)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!v || !m0 || !gbar) return fail(c, CLAIRE_EINVAL, "null argument");
+    if (flags & ~CLAIRE_VJP_RECOMPUTE) return fail(c, CLAIRE_EINVAL, "unknown flags %d", flags);
+    const size_t N = c->N;
+    const int nt = c->nt;
+    const bool recompute = (flags & CLAIRE_VJP_RECOMPUTE) != 0;
+    if (!c->vjp_acc) {
+        CL_CUDA(c, cudaMalloc(&c->vjp_acc, N * sizeof(unsigned long long)));
+        CL_CUDA(c, cudaMemsetAsync(c->vjp_acc, 0, N * sizeof(unsigned long long), c->stream));
+    }
+    const size_t nstates = (recompute ? 2 : nt + 1) * N;
+    if (c->vjp_states_n < nstates) {
+        if (c->vjp_states) CL_CUDA(c, cudaFree(c->vjp_states));
+        c->vjp_states = nullptr;
+        c->vjp_states_n = 0;
+        CL_CUDA(c, cudaMalloc(&c->vjp_states, nstates * sizeof(float)));
+        c->vjp_states_n = nstates;
+    }
+    c->have_lin = false;  // the work vectors below are shared with the solver
+    // FP32 inputs on the device: v -> g, m0 -> states[0], gbar -> r (first N)
+    const float* dv;
+    CL_TRY(device_input(c, v, 3 * N, c->g, &dv));
+    CL_CUDA(c, cudaMemcpyAsync(c->vjp_states, m0, N * sizeof(float), cudaMemcpyDefault, c->stream));
+    float* d = c->z;                 // characteristic X (grid units)
+    float* dbar = c->x;              // cotangent of the displacement
+    float* mb = c->r;                // cotangent of the state, two rolling halves
+    float* mb2 = c->r + N;
+    CL_CUDA(c, cudaMemcpyAsync(mb, gbar, N * sizeof(float), cudaMemcpyDefault, c->stream));
+    CL_CUDA(c, cudaMemsetAsync(dbar, 0, 3 * N * sizeof(float), c->stream));
+    CL_TRY(backtrace(c, dv, d, +1));
+    float* S = c->vjp_states;
+    // states m^1..m^{nt} (all stored), or rolling recomputation from m^0
+    if (!recompute)
+        for (int j = 0; j < nt; ++j) CL_TRY(interp(c, S + j * N, d, S + (j + 1) * N, Storage::F32));
+    for (int j = nt - 1; j >= 0; --j) {
+        const float* mj = S + j * N;
+        if (recompute && j > 0) {
+            // checkpointing: rebuild m^j from m^0 in the second slot
+            float* a = S + N;
+            CL_TRY(interp(c, S, d, a, Storage::F32));
+            for (int q = 1; q < j; ++q) {
+                CL_TRY(interp(c, a, d, c->p, Storage::F32));
+                CL_CUDA(c, cudaMemcpyAsync(a, c->p, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+            }
+            mj = a;
+        }
+        {
+            KTimer t(c, KK_VJP_GRAD, 32.0 * N, 1.0 * N);
+            launch_grad_accum(c->grid, c->o.interp, mj, d, mb, dbar, c->stream);
+            CL_LAUNCHED(c);
+        }
+        CL_TRY(scatter_transpose(c, mb, d, nullptr, mb2, false, 1.0f));
+        std::swap(mb, mb2);
+    }
+    if (gm0) CL_TRY(copy_out(c, gm0, mb, N));
+    if (gv) {
+        float* ub = c->p;
+        float* Ub = c->q;
+        {
+            KTimer t(c, KK_VJP_GRAD, 48.0 * N, 3.0 * N);
+            launch_predictor_terms(c->grid, c->o.interp, dv, static_cast<float>(c->dt), dbar, ub, Ub, c->stream);
+            CL_LAUNCHED(c);
+        }
+        const float ih[3] = {c->grid.ih1, c->grid.ih2, c->grid.ih3};
+        for (int comp = 0; comp < 3; ++comp)
+            CL_TRY(scatter_transpose(c, Ub + comp * N, nullptr, dv, ub + comp * N, true, ih[comp]));
+        CL_TRY(copy_out(c, gv, ub, 3 * N));
+    }
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
     collect_timing(c);
     return CLAIRE_OK;
 }

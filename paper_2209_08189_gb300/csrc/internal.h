@@ -101,6 +101,23 @@ void launch_fd8_div(const Grid& g, const float* v, void* out, Storage sto, cudaS
 void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,
                         cudaStream_t st);
 
+// ---- reverse-mode transport (vjp.cu) ----
+// dbar_c += mbar * d_c I[m](X)   (interpolant gradient at x + d, grid units)
+void launch_grad_accum(const Grid& g, int order, const float* m, const float* d, const float* mbar, float* dbar,
+                       cudaStream_t st);
+// acc += fixed-point(W(x + disp)^T yv), scale from *maxabs = max |yv| (device);
+// disp = d, or -sdt v / h when d is null
+void launch_scatter_fixed(const Grid& g, int order, const float* yv, const float* d, const float* v, float sdt,
+                          const double* maxabs, unsigned long long* acc, cudaStream_t st);
+// out = mult ((accumulate ? out : 0) + acc / scale); clears acc
+void launch_fixed_to_float(unsigned long long* acc, const double* maxabs, int accumulate, float mult, float* out,
+                           size_t n, cudaStream_t st);
+// predictor terms of the velocity cotangent (grid units): ubar, Ubar from dbar
+void launch_predictor_terms(const Grid& g, int order, const float* v, float dt, const float* dbar, float* ubar,
+                            float* Ubar, cudaStream_t st);
+// out2[1] = max |x| (out2[0] scratch)
+void launch_maxabs(const float* x, size_t n, double* partials, int nblocks, double* out2, cudaStream_t st);
+
 // ---- spectral scaling, vector ops and reductions (vec_kernels.cu) ----
 enum SpectralOp { SPEC_REG = 0, SPEC_INV = 1, SPEC_K = 2, SPEC_AINV = 3 };
 

@@ -1,0 +1,286 @@
+// Reverse-mode derivative of the discrete semi-Lagrangian transport
+// (discretise-then-differentiate) for sm_103a.
+//
+// Forward map (grid units, u = v / h, per node x): predictor y = x - dt u(x),
+// U = I[u](y), displacement d = -dt/2 (u(x) + U), X = x + d,
+// m^{j+1}(x) = I[m^j](X(x)), j = 0..nt-1 (Sec. 2.2: SL with RK2).
+// Given gbar = dL/dm^{nt} the kernels below produce dL/dm^0 and dL/dv:
+//   dbar_c  += mbar^{j+1} d_c I[m^j](X)        (interpolant gradient at X)
+//   mbar^j   = W(X)^T mbar^{j+1}               (scatter transpose)
+//   Ubar     = -dt/2 dbar,  ubar = -dt/2 dbar - dt sum_c Ubar_c grad I[u_c](y)
+//              + W(y)^T Ubar                   (through the predictor)
+//   vbar     = ubar / h.
+// The scatter transposes accumulate 64-bit fixed-point integers, so their
+// sums do not depend on the order of the atomic additions: the result is
+// bitwise deterministic.
+#include "internal.h"
+
+#include <cmath>
+
+namespace claire {
+
+namespace {
+
+constexpr int kThreads = 256;
+
+inline unsigned blocks_for(size_t n) { return static_cast<unsigned>((n + kThreads - 1) / kThreads); }
+
+// 1-D basis and its t-derivative.
+template <int ORDER>
+__device__ __forceinline__ void basis_and_deriv(float t, float w[4], float dw[4])
+{
+    if constexpr (ORDER == 3) {
+        cubic_weights(t, w);
+        const float t2 = t * t;
+        dw[0] = -(1.0f / 6.0f) * (3.0f * t2 - 6.0f * t + 2.0f);
+        dw[1] = 0.5f * (3.0f * t2 - 4.0f * t - 1.0f);
+        dw[2] = -0.5f * (3.0f * t2 - 2.0f * t - 2.0f);
+        dw[3] = (1.0f / 6.0f) * (3.0f * t2 - 1.0f);
+    } else {
+        w[0] = 1.0f - t;
+        w[1] = t;
+        dw[0] = -1.0f;
+        dw[1] = 1.0f;
+    }
+}
+
+// Wrapped node offsets and weights (plus derivatives) of one axis.
+template <int ORDER>
+struct DAxis {
+    static constexpr int M = (ORDER == 3) ? 4 : 2;
+    int idx[M];
+    float w[4], dw[4];
+    __device__ __forceinline__ void build(int node, float disp, int n, int stride)
+    {
+        float t;
+        const int b = wrap_index(node + split_disp(disp, t) - (ORDER == 3 ? 1 : 0), n);
+#pragma unroll
+        for (int a = 0; a < M; ++a) {
+            const int q = b + a;
+            idx[a] = (q >= n ? q - n : q) * stride;
+        }
+        basis_and_deriv<ORDER>(t, w, dw);
+    }
+};
+
+// Gradient of the interpolant of f at node (i,j,k) + (d1,d2,d3), grid units.
+template <int ORDER>
+__device__ __forceinline__ void interp_gradient(const Grid& g, const float* __restrict__ f, int i, int j,
+                                                int k, float d1, float d2, float d3, float grad[3])
+{
+    constexpr int M = DAxis<ORDER>::M;
+    DAxis<ORDER> a1, a2, a3;
+    a1.build(i, d1, g.n1, g.n23);
+    a2.build(j, d2, g.n2, g.n3);
+    a3.build(k, d3, g.n3, 1);
+    float g0 = 0.f, g1 = 0.f, g2 = 0.f;
+#pragma unroll
+    for (int a = 0; a < M; ++a) {
+        float s0 = 0.f, s1 = 0.f, s2 = 0.f;  // d1-weighted, plain for d2 and d3 paths
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const float* row = f + a1.idx[a] + a2.idx[b];
+            float r = 0.f, rd = 0.f;
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                const float fv = __ldg(row + a3.idx[c]);
+                r = fmaf(a3.w[c], fv, r);
+                rd = fmaf(a3.dw[c], fv, rd);
+            }
+            s0 = fmaf(a2.w[b], r, s0);
+            s1 = fmaf(a2.dw[b], r, s1);
+            s2 = fmaf(a2.w[b], rd, s2);
+        }
+        g0 = fmaf(a1.dw[a], s0, g0);
+        g1 = fmaf(a1.w[a], s1, g1);
+        g2 = fmaf(a1.w[a], s2, g2);
+    }
+    grad[0] = g0;
+    grad[1] = g1;
+    grad[2] = g2;
+}
+
+// dbar_c(p) += mbar(p) * d_c I[m](X(p))
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_grad_accum(Grid g, const float* __restrict__ m,
+                                                          const float* __restrict__ d,
+                                                          const float* __restrict__ mbar,
+                                                          float* __restrict__ dbar)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    float gr[3];
+    interp_gradient<ORDER>(g, m, i, j, k, __ldg(d + p), __ldg(d + N + p), __ldg(d + 2 * N + p), gr);
+    const float mb = __ldg(mbar + p);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) dbar[c * N + p] = fmaf(mb, gr[c], dbar[c * N + p]);
+}
+
+// Fixed-point scale 2^(48 - e) with max|y| <= 2^e, so every scaled term
+// stays below 2^48 in magnitude and a node can receive 2^14 full-size terms
+// before the 64-bit sum could overflow.  0 for y = 0, NaN when max|y| is not
+// finite (the maximum kernel maps NaN to infinity).
+__device__ __forceinline__ double fixed_scale_of(double mx)
+{
+    if (mx == 0.0) return 0.0;
+    if (!isfinite(mx)) return __longlong_as_double(0x7ff8000000000000ll);
+    int e;
+    frexp(mx, &e);
+    return ldexp(1.0, 48 - e);
+}
+
+// acc[q] += round(scale * w(p, q) * y[p]) for the stencil of every point p at
+// x_p + disp_p; disp = d (if non-null) or -sdt * v / h (the RK2 predictor).
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_scatter_fixed(Grid g, const float* __restrict__ yv,
+                                                             const float* __restrict__ d,
+                                                             const float* __restrict__ v, float sdt,
+                                                             const double* __restrict__ maxabs,
+                                                             unsigned long long* __restrict__ acc)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    const double scale = fixed_scale_of(*maxabs);
+    const float y = __ldg(yv + p);
+    if (y == 0.0f || !(scale > 0.0)) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    float d1, d2, d3;
+    if (d) {
+        d1 = __ldg(d + p); d2 = __ldg(d + N + p); d3 = __ldg(d + 2 * N + p);
+    } else {
+        d1 = -sdt * __ldg(v + p) * g.ih1;
+        d2 = -sdt * __ldg(v + N + p) * g.ih2;
+        d3 = -sdt * __ldg(v + 2 * N + p) * g.ih3;
+    }
+    constexpr int M = DAxis<ORDER>::M;
+    DAxis<ORDER> a1, a2, a3;
+    a1.build(i, d1, g.n1, g.n23);
+    a2.build(j, d2, g.n2, g.n3);
+    a3.build(k, d3, g.n3, 1);
+    const double ys = scale * static_cast<double>(y);
+#pragma unroll
+    for (int a = 0; a < M; ++a)
+#pragma unroll
+        for (int b = 0; b < M; ++b) {
+            const double wab = ys * static_cast<double>(a1.w[a] * a2.w[b]);
+            const size_t row = static_cast<size_t>(a1.idx[a]) + a2.idx[b];
+#pragma unroll
+            for (int c = 0; c < M; ++c) {
+                const long long q = __double2ll_rn(wab * static_cast<double>(a3.w[c]));
+                atomicAdd(acc + row + a3.idx[c], static_cast<unsigned long long>(q));
+            }
+        }
+}
+
+// out = mult ((accumulate ? out : 0) + acc / scale); acc is cleared for reuse.
+__global__ void __launch_bounds__(kThreads) k_fixed_to_float(unsigned long long* __restrict__ acc,
+                                                              const double* __restrict__ maxabs,
+                                                              int accumulate, float mult,
+                                                              float* __restrict__ out, size_t n)
+{
+    const size_t p = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
+    if (p >= n) return;
+    const double scale = fixed_scale_of(*maxabs);
+    double val = 0.0;
+    if (scale > 0.0)
+        val = static_cast<double>(static_cast<long long>(acc[p])) / scale;
+    else if (scale != scale)
+        val = scale;  // non-finite cotangent: propagate NaN
+    acc[p] = 0ull;
+    out[p] = mult * static_cast<float>(accumulate ? val + static_cast<double>(out[p]) : val);
+}
+
+// Predictor terms: Ubar = -dt/2 dbar; ubar(x) = -dt/2 dbar(x) - dt sum_c Ubar_c grad I[u_c](y)
+// with y = x - dt u(x); writes ubar (grid units) and Ubar.
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_predictor_terms(Grid g, const float* __restrict__ v, float dt,
+                                                               const float* __restrict__ dbar,
+                                                               float* __restrict__ ubar,
+                                                               float* __restrict__ Ubar)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    const float ih[3] = {g.ih1, g.ih2, g.ih3};
+    const float e1 = -dt * __ldg(v + p) * g.ih1, e2 = -dt * __ldg(v + N + p) * g.ih2,
+                e3 = -dt * __ldg(v + 2 * N + p) * g.ih3;
+    float yb[3] = {0.f, 0.f, 0.f};
+    float Ub[3];
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Ub[c] = -0.5f * dt * __ldg(dbar + c * N + p);
+        float gr[3];
+        interp_gradient<ORDER>(g, v + c * N, i, j, k, e1, e2, e3, gr);  // gradient of v_c; u_c = v_c ih_c
+#pragma unroll
+        for (int e = 0; e < 3; ++e) yb[e] = fmaf(Ub[c] * ih[c], gr[e], yb[e]);
+    }
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        Ubar[c * N + p] = Ub[c];
+        ubar[c * N + p] = -0.5f * dt * __ldg(dbar + c * N + p) - dt * yb[c];
+    }
+}
+
+// max |x| over n values; partials hold 2 * gridDim.x doubles
+__global__ void __launch_bounds__(kThreads) k_maxabs_partial(const float* __restrict__ x, size_t n,
+                                                              double* __restrict__ partials)
+{
+    double hi = 0.0;
+    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * kThreads)
+    {
+        const double a = fabs(static_cast<double>(x[i]));
+        hi = fmax(hi, a <= 1.0e308 ? a : HUGE_VAL);  // NaN -> infinity, which the reductions keep
+    }
+    block_minmax(hi, hi, partials + gridDim.x, partials);
+}
+
+}  // namespace
+
+void launch_grad_accum(const Grid& g, int order, const float* m, const float* d, const float* mbar, float* dbar,
+                       cudaStream_t st)
+{
+    if (order == 3)
+        k_grad_accum<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, m, d, mbar, dbar);
+    else
+        k_grad_accum<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, m, d, mbar, dbar);
+}
+
+void launch_scatter_fixed(const Grid& g, int order, const float* yv, const float* d, const float* v, float sdt,
+                          const double* maxabs, unsigned long long* acc, cudaStream_t st)
+{
+    if (order == 3)
+        k_scatter_fixed<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, yv, d, v, sdt, maxabs, acc);
+    else
+        k_scatter_fixed<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, yv, d, v, sdt, maxabs, acc);
+}
+
+void launch_fixed_to_float(unsigned long long* acc, const double* maxabs, int accumulate, float mult, float* out,
+                           size_t n, cudaStream_t st)
+{
+    k_fixed_to_float<<<blocks_for(n), kThreads, 0, st>>>(acc, maxabs, accumulate, mult, out, n);
+}
+
+void launch_predictor_terms(const Grid& g, int order, const float* v, float dt, const float* dbar, float* ubar,
+                            float* Ubar, cudaStream_t st)
+{
+    if (order == 3)
+        k_predictor_terms<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, dt, dbar, ubar, Ubar);
+    else
+        k_predictor_terms<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, dt, dbar, ubar, Ubar);
+}
+
+void launch_maxabs(const float* x, size_t n, double* partials, int nblocks, double* out2, cudaStream_t st)
+{
+    k_maxabs_partial<<<nblocks, kThreads, 0, st>>>(x, n, partials);
+    launch_final_max(partials, nblocks, out2, st);
+}
+
+}  // namespace claire

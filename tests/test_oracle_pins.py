@@ -93,6 +93,48 @@ def test_interp_convergence_order(order, expect):
     assert 0.8 * expect < ratio < 1.25 * expect, ratio
 
 
+@pytest.mark.parametrize("order,deg", [(3, 3), (1, 1)])
+def test_interp_gradient_exact_on_polynomials(order, deg):
+    """The interpolant's gradient reproduces the derivative of tensor-product
+    polynomials of degree <= 3 (cubic) / <= 1 (linear) at non-wrapping points."""
+    n = (12, 10, 14)
+    rng = np.random.default_rng(9)
+    I, J, K = np.meshgrid(*[np.arange(s, dtype=float) for s in n], indexing="ij")
+    lo, hi = (1.0, 2.0) if order == 3 else (0.0, 1.0)
+    ok = (I >= lo + 1) & (I <= n[0] - 2 - hi) & (J >= lo + 1) & (J <= n[1] - 2 - hi) & \
+         (K >= lo + 1) & (K <= n[2] - 2 - hi)
+    d = rng.uniform(-0.9, 0.9, size=(3,) + n)
+    P = lambda x, y, z: (x / 7.0) ** deg * (y / 5.0) ** min(deg, 2) * (z / 9.0) ** 1
+    dP = [lambda x, y, z: deg * x ** (deg - 1) / 7.0 ** deg * (y / 5.0) ** min(deg, 2) * (z / 9.0),
+          lambda x, y, z: (x / 7.0) ** deg * min(deg, 2) * y ** (min(deg, 2) - 1) / 5.0 ** min(deg, 2) * (z / 9.0),
+          lambda x, y, z: (x / 7.0) ** deg * (y / 5.0) ** min(deg, 2) / 9.0]
+    got = oracle.interp_grad(P(I, J, K), d, order)
+    Y = (I + d[0], J + d[1], K + d[2])
+    for c in range(3):
+        assert np.max(np.abs(got[c] - dP[c](*Y))[ok]) < 1e-11
+
+
+@pytest.mark.parametrize("order", [3, 1])
+def test_transport_vjp_matches_finite_differences(order):
+    """The exact discrete VJP of nt SL steps (image and velocity cotangents)
+    agrees with central differences of the discrete forward map."""
+    n = (12, 10, 14)
+    rng = np.random.default_rng(0)
+    m0 = synth.blob_template(n, seed=1, sigma=0.8)
+    v = synth.mode_velocity(n, seed=2, vmax=0.6, kmax=2)
+    p = oracle.Params(nt=3, order=order)
+    gbar = rng.standard_normal(n)
+    gm0, gv = oracle.transport_vjp(m0, v, gbar, p)
+    L = lambda mm, vv: float(np.sum(gbar * oracle.transport(mm, vv, p)))
+    vt = rng.standard_normal(v.shape)
+    mt = rng.standard_normal(n)
+    eps = 1e-6
+    fdv = (L(m0, v + eps * vt) - L(m0, v - eps * vt)) / (2 * eps)
+    fdm = (L(m0 + eps * mt, v) - L(m0 - eps * mt, v)) / (2 * eps)
+    assert abs(fdv - np.sum(gv * vt)) <= 1e-7 * abs(fdv)
+    assert abs(fdm - np.sum(gm0 * mt)) <= 1e-7 * abs(fdm)
+
+
 def test_interp_transpose_dot_product():
     """<T x, y> = <x, T^T y> for the scatter transpose (DTO pin), wrapping points included."""
     n = (9, 8, 7)

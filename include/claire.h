@@ -94,6 +94,11 @@ typedef struct claire_opts {
                             CLAIRE_STORAGE_F32 (default), _F16 or _BF16.  Arithmetic is FP32,
                             reductions FP64; velocities, displacements and the spectral/PCG
                             vectors stay FP32.  API arrays are always float32. */
+    double g0_ref;       /* > 0: reference ||g0|| of the relative tolerance and of the PCG forcing in
+                            claire_register, instead of the gradient norm at the initial guess; a
+                            solve warm-started from a predicted velocity passes the norm of the
+                            gradient at v = 0 so that it stops at the same absolute gradient as a
+                            solve from zero.  Default 0 (use the initial guess's gradient). */
 } claire_opts;
 
 /* claire_opts.storage */
@@ -227,6 +232,27 @@ claire_status claire_transport(claire_ctx* ctx, const float* v, const float* m_i
 claire_status claire_transport_vjp(claire_ctx* ctx, const float* v, const float* m0, const float* gbar,
                                    float* gm0, float* gv, int flags);
 
+/*
+ * Grid transfer of ncomp periodic fields (component-major, each a full grid)
+ * from the grid `from` to the grid `to` (all extents even), as used to
+ * register downsampled images and carry the velocity back to the base grid
+ * (Sec. 4, downsampled registrations: images sampled by nearest neighbour,
+ * velocity upsampled by spectral prolongation).
+ *   CLAIRE_RESAMPLE_SPECTRAL: Fourier coefficients are copied between the
+ *     spectra (wavenumbers at or beyond either grid's Nyquist limit are
+ *     dropped, new ones are zero): band-limited interpolation / truncation.
+ *   CLAIRE_RESAMPLE_NEAREST: out[j] = in[floor(j * n_from / n_to)] per axis.
+ * `in` and `out` are device pointers (caller-owned, must not overlap); work
+ * is queued on `stream`.  The spectral mode allocates temporary spectra and
+ * cuFFT plans and synchronises the stream before returning.  Needs no
+ * context.  Errors: CLAIRE_EINVAL (shapes, mode), CLAIRE_ENOMEM,
+ * CLAIRE_ECUFFT, CLAIRE_ECUDA, CLAIRE_ETOOLARGE (a grid of 2^31 points or more).
+ */
+#define CLAIRE_RESAMPLE_SPECTRAL 0
+#define CLAIRE_RESAMPLE_NEAREST 1
+claire_status claire_resample(const float* in, const int from[3], float* out, const int to[3], int ncomp, int mode,
+                              void* stream);
+
 /* Extrema of the Jacobian determinant det grad y of the deformation map of v
  * (Sec. 3, "J_min"; y = x + u with u transported by the state's SL steps,
  * F = I + FD8(u), det and extrema in FP64). */
@@ -302,6 +328,14 @@ claire_status claire_kernel_stats(claire_ctx* ctx, claire_kernel_stat* out, int 
 
 /* Turn per-launch CUDA-event timing on (1) or off (0) after creation. */
 claire_status claire_set_timing(claire_ctx* ctx, int on);
+
+/* Replace the options of an existing context (e.g. gtol, max_gn, g0_ref
+ * between solves).  storage is fixed at claire_create: a different value is
+ * CLAIRE_EINVAL; invalid options are CLAIRE_EINVAL and leave the context
+ * unchanged.  Clears the linearisation point of claire_hessian_matvec. */
+claire_status claire_set_opts(claire_ctx* ctx, const claire_opts* opts);
+/* Current options of a context. */
+claire_status claire_get_opts(const claire_ctx* ctx, claire_opts* opts);
 
 /* One-line description of the last error on ctx (never NULL; "" if none). */
 const char* claire_last_error(const claire_ctx* ctx);

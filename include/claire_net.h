@@ -1,0 +1,126 @@
+/*
+ * libclaire network kernels: the learned warm start of the registration.
+ *
+ * The paper (Sec. 2.2, Sec. 4) solves every registration from v = 0 or from
+ * a coarser-grid solution.  This part adds a small 3D convolutional network
+ * (a U-Net over periodic volumes) that maps an image pair (m0, m1) to an
+ * initial velocity; Gauss-Newton-Krylov from that guess remains the solver
+ * and the judge of its error.  The paper has no network: these entry points
+ * are building blocks of that extension, with no counterpart in it.
+ *
+ * Conventions, for every entry point below:
+ *   - All array pointers are DEVICE pointers owned by the caller; nothing is
+ *     allocated, freed or retained.  Work is queued on `stream` (a
+ *     cudaStream_t, NULL = legacy default stream) and returns without
+ *     synchronising.
+ *   - Activations are BF16, channels-last [B][D][H][W][C] (C contiguous).  A
+ *     tensor may be a channel slice of a wider buffer: `*_stride` is the
+ *     channel stride (elements between consecutive voxels), the pointer is
+ *     the slice's first channel.  Strides and slice offsets must be
+ *     multiples of 8 channels and pointers 16-byte aligned.
+ *   - vol[4] = {B, D, H, W}: batch and grid of the tensor the operation
+ *     produces (for pool2/up2 and their backward passes: of the COARSE grid).
+ *     Boundaries are periodic (wrap-around), like the registration domain.
+ *   - 3x3x3 conv weights are BF16 [Cout][27][Cin], tap = kd*9 + kh*3 + kw
+ *     with offset (kd-1, kh-1, kw-1); biases FP32 [Cout].
+ *   - Errors: CLAIRE_EINVAL for a shape, stride or alignment the kernels do
+ *     not support (nothing is launched), CLAIRE_ECUDA for a failed launch;
+ *     the message is available from claire_net_last_error() (per thread).
+ */
+#ifndef CLAIRE_NET_H
+#define CLAIRE_NET_H
+
+#include <stddef.h>
+
+#include "claire.h"
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* Y = act(bias + conv3x3x3(X, W)): act 0 = identity, 1 = leaky ReLU with
+ * `slope` for negative inputs.  Cin a multiple of 16, Cout one of 16, 32,
+ * 48, 64, 96, 128, 192;
+ * D, H, W powers of two >= 4 with D*H*W >= 64 (any bias may be NULL).
+ * BF16 inputs and outputs, FP32 accumulation on the tensor cores. */
+claire_status claire_net_conv3d(const void* x, int x_stride, int cin, const void* w, const float* bias,
+                                float slope, int act, void* y, int y_stride, int cout, const int vol[4],
+                                void* stream);
+
+/* Weights of the adjoint convolution: wf[ci][tap][co] = w[co][26 - tap][ci]
+ * (BF16, Cin*27*Cout elements).  claire_net_conv3d(dY, wf) is then the
+ * input gradient dX of the convolution (no bias, no activation). */
+claire_status claire_net_conv3d_flip(const void* w, int cout, int cin, void* wf, void* stream);
+
+/* Number of voxel chunks the weight gradient is split into (fixed by the
+ * shapes and the device's SM count): `part` needs chunks*Cout*27*Cin floats
+ * and `part_bias` chunks*Cout floats. */
+claire_status claire_net_conv3d_wgrad_chunks(int cin, int cout, const int vol[4], int* chunks);
+
+/* Weight gradient of Y = conv3x3x3(X, W) for the output gradient dY (the
+ * pre-activation gradient): dw[co][tap][ci] = sum_p dY[p][co] X[p+off][ci]
+ * and db[co] = sum_p dY[p][co] (FP32; db may be NULL).  Per-chunk partials
+ * are summed in a fixed order, so the result is deterministic. */
+claire_status claire_net_conv3d_wgrad(const void* x, int x_stride, int cin, const void* dy, int dy_stride,
+                                      int cout, const int vol[4], int chunks, float* part, float* part_bias,
+                                      float* dw, float* db, void* stream);
+
+/* 2x2x2 average pooling: y (coarse vol) = mean of the 8 children of x. */
+claire_status claire_net_pool2(const void* x, int x_stride, int c, void* y, int y_stride, const int vol[4],
+                               void* stream);
+/* Its backward: dx (fine) = dy / 8, plus add (fine, may be NULL). */
+claire_status claire_net_pool2_bwd(const void* dy, int dy_stride, const void* add, int add_stride, int c, void* dx,
+                                   int dx_stride, const int vol[4], void* stream);
+/* Nearest 2x upsampling: every child of a coarse voxel gets its value. */
+claire_status claire_net_up2(const void* x, int x_stride, int c, void* y, int y_stride, const int vol[4],
+                             void* stream);
+/* Its backward: dx (coarse) = sum of dy over the 8 children. */
+claire_status claire_net_up2_bwd(const void* dy, int dy_stride, int c, void* dx, int dx_stride, const int vol[4],
+                                 void* stream);
+/* Leaky ReLU backward through its output y: dp = dy * (y > 0 ? 1 : slope). */
+claire_status claire_net_leaky_bwd(const void* dy, int dy_stride, const void* y, int y_stride, int c, float slope,
+                                   void* dp, int dp_stride, const int vol[4], void* stream);
+
+/* Network input: x[p] = (a0*m0[p], a1*m1[p], 0, ..., 0) over `stride`
+ * channels (even, >= 2); m0, m1 FP32 [nvox]. */
+claire_status claire_net_pack(const float* m0, const float* m1, float a0, float a1, size_t nvox, void* x,
+                              int stride, void* stream);
+
+/* Output head, a 1x1x1 conv to the three velocity components:
+ * v[b][c][p] = scale * (bh[c] + sum_ci x[b,p][ci] wh[c][ci]); v FP32
+ * [B][3][D][H][W] (physical units, the layout of claire_transport's v);
+ * wh FP32 [3][cin], cin 16 or 32. */
+claire_status claire_net_head(const void* x, int x_stride, int cin, const float* wh, const float* bh, float scale,
+                              void* v, const int vol[4], void* stream);
+/* Partial blocks of claire_net_head_bwd: `part` needs blocks*(3*cin+3) floats. */
+claire_status claire_net_head_bwd_blocks(const int vol[4], int* blocks);
+/* Head backward for dv (FP32, layout of v): dx[b,p][ci] = scale sum_c
+ * dv[b][c][p] wh[c][ci] (BF16, dx may be NULL) and dwb = [dwh (3*cin),
+ * dbh (3)] (FP32, fixed-order reduction). */
+claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, const float* wh, float scale,
+                                  const float* dv, void* dx, int dx_stride, const int vol[4], int blocks,
+                                  float* part, float* dwb, void* stream);
+
+/* One Adam step (bias-corrected, step >= 1) on FP32 master weights w with
+ * gradient gscale*g; m, s are the moment buffers; wb (may be NULL) receives
+ * the updated weights as BF16. */
+claire_status claire_net_adam(float* w, const float* g, float* m, float* s, size_t n, float lr, float beta1,
+                              float beta2, float eps, int step, float gscale, void* wb, void* stream);
+
+/* Training loss pieces (FP32 arrays of n values, `sum` one device double
+ * that is ADDED to, may be NULL; its rounding may differ between runs since
+ * blocks add their partials atomically):
+ * velocity term dv = a (v - vstar) + b gv (gv may be NULL), sum += |v - vstar|^2;
+ * residual r = x - y (r may be NULL), sum += |x - y|^2. */
+claire_status claire_net_vel_loss(const float* v, const float* vstar, const float* gv, float a, float b, size_t n,
+                                  float* dv, double* sum, void* stream);
+claire_status claire_net_residual(const float* x, const float* y, size_t n, float* r, double* sum, void* stream);
+
+/* Message of the last failing claire_net_* call on this thread. */
+const char* claire_net_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CLAIRE_NET_H */

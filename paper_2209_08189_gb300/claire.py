@@ -44,7 +44,7 @@ class claire_opts(ctypes.Structure):
                 ("max_pcg", ctypes.c_int), ("pcg_rtol_max", ctypes.c_double),
                 ("pcg_fixed", ctypes.c_int), ("armijo_c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int), ("storage", ctypes.c_int)]
+                ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double)]
 
 
 class claire_report(ctypes.Structure):
@@ -102,6 +102,10 @@ _SIGS = {
     "claire_transport": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_detj": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "claire_transport_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int],
+    "claire_set_opts": [_vp, ctypes.POINTER(claire_opts)],
+    "claire_get_opts": [_vp, ctypes.POINTER(claire_opts)],
+    "claire_resample": [_vp, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
+                        ctypes.c_int, _vp],
     "claire_interp": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_backtrace": [_vp, _vp, _vp, ctypes.c_int],
     "claire_fd8_grad": [_vp, _vp, _vp],
@@ -239,6 +243,28 @@ def claire_transport_vjp(ctx, v, m0, gbar, gm0=None, gv=None, flags=0):
                                                   int(flags)))
 
 
+RESAMPLE_SPECTRAL, RESAMPLE_NEAREST = 0, 1
+
+
+def claire_resample(inp, from_grid, out, to_grid, ncomp=1, mode=RESAMPLE_SPECTRAL, stream=None):
+    f = (ctypes.c_int * 3)(*[int(x) for x in from_grid])
+    t = (ctypes.c_int * 3)(*[int(x) for x in to_grid])
+    st = lib().claire_resample(_ptr(inp), f, _ptr(out), t, int(ncomp), int(mode), stream)
+    if st < 0:
+        raise ClaireError(st, "claire_resample %s -> %s" % (tuple(from_grid), tuple(to_grid)))
+    return st
+
+
+def claire_set_opts(ctx, opts):
+    return _check(ctx, lib().claire_set_opts(ctx, ctypes.byref(opts)))
+
+
+def claire_get_opts(ctx):
+    o = claire_opts()
+    _check(ctx, lib().claire_get_opts(ctx, ctypes.byref(o)))
+    return o
+
+
 def claire_detj(ctx, v):
     lo = ctypes.c_double()
     hi = ctypes.c_double()
@@ -333,6 +359,16 @@ class Context:
 
     def set_stream(self, stream_handle):
         claire_set_stream(self.handle, stream_handle)
+
+    def set_opts(self, **opts):
+        """Change options of the live context (storage excluded)."""
+        o = claire_get_opts(self.handle)
+        for k, v in opts.items():
+            if not hasattr(o, k):
+                raise TypeError("unknown option %r" % k)
+            setattr(o, k, v)
+        claire_set_opts(self.handle, o)
+        self.opts = o
 
     def set_images(self, m0, m1):
         claire_set_images(self.handle, m0, m1)

@@ -207,6 +207,7 @@ void fill_defaults(claire_opts* o)
     o->wall_limit_s = 0.0;
     o->timing = 0;
     o->storage = CLAIRE_STORAGE_F32;
+    o->g0_ref = 0.0;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -214,7 +215,8 @@ bool valid_opts(const claire_opts& o)
     return (o.interp == 1 || o.interp == 3) && (o.reg == 1 || o.reg == 2) && o.beta_w >= 0 &&
            (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
            o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
-           o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2;
+           o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
+           o.g0_ref >= 0;
 }
 
 // Layout of the workspace arena in floats (each region 256-byte aligned).
@@ -1054,7 +1056,9 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
     CL_TRY(gradient_at_lin(c, c->g));
     double gn;
     CL_TRY(dot(c, c->g, c->g, n3, &gn));
-    const double g0 = std::sqrt(gn);
+    // the tolerance and the PCG forcing are relative to g0_ref when given
+    // (a warm start stops at the same absolute gradient as a solve from zero)
+    const double g0 = c->o.g0_ref > 0 ? c->o.g0_ref : std::sqrt(gn);
     double rel = 1.0;
     if (g0 == 0.0) st = CLAIRE_OK;
     for (int k = 0; st == CLAIRE_ENOTCONVERGED && k < c->o.max_gn; ++k) {
@@ -1405,6 +1409,26 @@ claire_status claire_set_timing(claire_ctx* c, int on)
     if (!c) return CLAIRE_EINVAL;
     collect_timing(c);
     c->o.timing = on ? 1 : 0;
+    return CLAIRE_OK;
+}
+
+claire_status claire_set_opts(claire_ctx* c, const claire_opts* opts)
+{
+    if (!c || !opts) return CLAIRE_EINVAL;
+    if (!valid_opts(*opts)) return fail(c, CLAIRE_EINVAL, "invalid options");
+    if (opts->storage != c->o.storage) return fail(c, CLAIRE_EINVAL, "storage is fixed at claire_create");
+    collect_timing(c);
+    c->o = *opts;
+    c->rp.beta_w = static_cast<float>(opts->beta_w);
+    c->rp.reg = opts->reg;
+    c->have_lin = false;  // the linearisation point depends on interp / reg / beta_w / grad_form
+    return CLAIRE_OK;
+}
+
+claire_status claire_get_opts(const claire_ctx* c, claire_opts* opts)
+{
+    if (!c || !opts) return CLAIRE_EINVAL;
+    *opts = c->o;
     return CLAIRE_OK;
 }
 

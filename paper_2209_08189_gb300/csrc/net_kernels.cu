@@ -1,0 +1,1054 @@
+// Kernels of the learned warm start: a 3D U-Net over periodic volumes with
+// BF16 activations and weights and FP32 accumulation, for sm_103a.
+//
+// Layout: activations channels-last [B][D][H][W][C] (C contiguous, a
+// tensor may be a channel slice of a wider buffer: channel stride Cs >= C);
+// 3x3x3 conv weights [Cout][27][Cin] with tap = kd*9 + kh*3 + kw, offsets
+// (kd-1, kh-1, kw-1); padding is periodic, like the registration domain.
+//
+// The 3x3x3 convolution is an implicit GEMM on the tensor cores
+// (mma.sync m16n8k16 BF16 -> FP32): rows = output voxels, columns = output
+// channels, reduction over (tap, input channel).  A CTA owns a brick of 64
+// output voxels; per 16-channel slice of the input it stages the brick's halo
+// in shared memory (cp.async, XOR-swizzled 16-byte halves so that ldmatrix
+// rows hit distinct banks), then each warp runs 27 taps of m16 x (8 NT) x k16
+// products, with the weights read through the read-only cache.
+// Backward-data is the same kernel on flipped, transposed weights; the
+// weight gradient is a second implicit GEMM (rows = output channels, columns
+// = input channels, reduction over voxels) with per-chunk FP32 partials
+// reduced in a fixed order, so results are deterministic.
+#include "claire_net.h"
+
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdint>
+#include <cstdio>
+#include <cstdarg>
+#include <algorithm>
+
+namespace claire {
+namespace net {
+
+namespace {
+
+constexpr int kBrick = 64;       // output voxels per CTA
+constexpr int kHaloMax = 324;    // (BD+2)(BH+2)(BW+2) for the allowed bricks
+constexpr int kConvThreads = 128;
+
+__device__ __forceinline__ int wrapi(int x, int n) { return x < 0 ? x + n : (x >= n ? x - n : x); }
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p)
+{
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+
+__device__ __forceinline__ void cp_async_wait()
+{
+    asm volatile("cp.async.wait_all;\n" ::);
+}
+
+__device__ __forceinline__ void ldsm_x4(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void ldsm_x4_t(uint32_t addr, uint32_t& r0, uint32_t& r1, uint32_t& r2, uint32_t& r3)
+{
+    asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+                 : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+                 : "r"(addr));
+}
+
+__device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, uint32_t a2, uint32_t a3,
+                                         uint32_t b0, uint32_t b1)
+{
+    asm volatile(
+        "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, {%8,%9}, "
+        "{%0,%1,%2,%3};\n"
+        : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+        : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// byte offset of 16-byte half h of row s in a [rows][16 x bf16] swizzled tile
+__device__ __forceinline__ uint32_t swz(int s, int h) { return static_cast<uint32_t>((2 * s + (h ^ ((s >> 2) & 1))) * 16); }
+
+struct Vol {
+    int B, D, H, W;
+};
+
+struct Brick {
+    int bd, bh, bw;  // brick extent (bd * bh * bw = 64)
+    int nd, nh, nw;  // bricks per axis
+};
+
+// decode CTA index into the brick origin
+__device__ __forceinline__ void brick_origin(const Vol& v, const Brick& k, int cta, int& b, int& d0, int& h0,
+                                             int& w0)
+{
+    int r = cta;
+    const int iw = r % k.nw; r /= k.nw;
+    const int ih = r % k.nh; r /= k.nh;
+    const int id = r % k.nd; r /= k.nd;
+    b = r;
+    d0 = id * k.bd;
+    h0 = ih * k.bh;
+    w0 = iw * k.bw;
+}
+
+// stage 16 channels (c0..c0+15) of the halo of a brick into swizzled smem
+__device__ __forceinline__ void stage_halo(const __nv_bfloat16* __restrict__ X, int Cs, int c0, const Vol& v,
+                                           const Brick& k, int b, int d0, int h0, int w0, uint32_t sbase)
+{
+    const int hw = k.bw + 2, hh = k.bh + 2;
+    const int nslots = (k.bd + 2) * hh * hw;
+    for (int e = threadIdx.x; e < 2 * nslots; e += blockDim.x) {
+        const int s = e >> 1, half = e & 1;
+        const int sw = s % hw, sh = (s / hw) % hh, sd = s / (hw * hh);
+        const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + sh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
+        const size_t vox = ((static_cast<size_t>(b) * v.D + d) * v.H + h) * v.W + w;
+        cp_async16(sbase + swz(s, half), X + vox * Cs + c0 + 8 * half);
+    }
+}
+
+// Y[p][co] = act(bias[co] + sum_{tap,ci} X[p + off(tap)][ci] W[co][tap][ci])
+template <int NT>
+__global__ void __launch_bounds__(kConvThreads) k_conv3d(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
+                                                         const __nv_bfloat16* __restrict__ Wt,
+                                                         const float* __restrict__ bias, float slope, int act,
+                                                         __nv_bfloat16* __restrict__ Y, int Cys, Vol v, Brick k)
+{
+    __shared__ __align__(128) unsigned char halo[kHaloMax * 32];
+    int b, d0, h0, w0;
+    brick_origin(v, k, blockIdx.x, b, d0, h0, w0);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hw = k.bw + 2, hh = k.bh + 2;
+    // this lane's ldmatrix row: voxel r of the brick
+    const int r = 16 * warp + (lane & 7) + 8 * ((lane >> 3) & 1);
+    const int rw = r % k.bw, rh = (r / k.bw) % k.bh, rd = r / (k.bw * k.bh);
+    const int slot0 = (rd * hh + rh) * hw + rw;  // halo slot of tap (0,0,0) offset (-1,-1,-1)
+    const int khalf = lane >> 4;
+    const int g = lane >> 2, t = lane & 3;
+    const uint32_t sbase = smem_addr(halo);
+
+    float acc[NT][4];
+#pragma unroll
+    for (int n = 0; n < NT; ++n) acc[n][0] = acc[n][1] = acc[n][2] = acc[n][3] = 0.f;
+
+    for (int c0 = 0; c0 < Cin; c0 += 16) {
+        __syncthreads();
+        stage_halo(X, Cxs, c0, v, k, b, d0, h0, w0, sbase);
+        cp_async_wait();
+        __syncthreads();
+        const __nv_bfloat16* wrow = Wt + static_cast<size_t>(g) * 27 * Cin + c0 + 2 * t;
+#pragma unroll 1
+        for (int tap = 0; tap < 27; ++tap) {
+            const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+            const int s = slot0 + (kd * hh + kh) * hw + kw;
+            uint32_t a0, a1, a2, a3;
+            ldsm_x4(sbase + swz(s, khalf), a0, a1, a2, a3);
+            const __nv_bfloat16* wp = wrow + static_cast<size_t>(tap) * Cin;
+#pragma unroll
+            for (int n = 0; n < NT; ++n) {
+                const __nv_bfloat16* q = wp + static_cast<size_t>(n) * 8 * 27 * Cin;
+                const uint32_t b0 = __ldg(reinterpret_cast<const unsigned int*>(q));
+                const uint32_t b1 = __ldg(reinterpret_cast<const unsigned int*>(q + 8));
+                mma_bf16(acc[n], a0, a1, a2, a3, b0, b1);
+            }
+        }
+    }
+    // epilogue: rows g and g + 8 of this warp's 16 voxels
+#pragma unroll
+    for (int half = 0; half < 2; ++half) {
+        const int rr = 16 * warp + g + 8 * half;
+        const int ew = rr % k.bw, eh = (rr / k.bw) % k.bh, ed = rr / (k.bw * k.bh);
+        const size_t vox = ((static_cast<size_t>(b) * v.D + d0 + ed) * v.H + h0 + eh) * v.W + w0 + ew;
+        __nv_bfloat16* yrow = Y + vox * Cys;
+#pragma unroll
+        for (int n = 0; n < NT; ++n) {
+            const int co = 8 * n + 2 * t;
+            float y0 = acc[n][2 * half], y1 = acc[n][2 * half + 1];
+            if (bias) {
+                y0 += __ldg(bias + co);
+                y1 += __ldg(bias + co + 1);
+            }
+            if (act) {
+                y0 = y0 > 0.f ? y0 : slope * y0;
+                y1 = y1 > 0.f ? y1 : slope * y1;
+            }
+            *reinterpret_cast<__nv_bfloat162*>(yrow + co) = __floats2bfloat162_rn(y0, y1);
+        }
+    }
+}
+
+// Wgrad partials: P[pc][co][tap][ci] = sum over the chunk's voxels p of
+// dY[p][co] X[p + off(tap)][ci]; Pb[pc][co] = sum dY[p][co] (ci chunk 0 only).
+// grid: (Cin/16, Cout/16, chunks); each CTA loops over its bricks.
+__global__ void __launch_bounds__(kConvThreads) k_conv3d_wgrad(const __nv_bfloat16* __restrict__ X, int Cxs,
+                                                               int Cin, const __nv_bfloat16* __restrict__ dY,
+                                                               int Cys, int Cout, Vol v, Brick k, int nbricks,
+                                                               int per_chunk, float* __restrict__ P,
+                                                               float* __restrict__ Pb)
+{
+    __shared__ __align__(128) unsigned char halo[kHaloMax * 32];
+    __shared__ __align__(128) unsigned char dys[kBrick * 32];
+    const int ci0 = 16 * blockIdx.x, co0 = 16 * blockIdx.y, pc = blockIdx.z;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int hw = k.bw + 2, hh = k.bh + 2;
+    const uint32_t hbase = smem_addr(halo), dbase = smem_addr(dys);
+    const int i = lane >> 3, j = lane & 7;
+    const int g = lane >> 2, t = lane & 3;
+    // taps of this warp: warp, warp + 4, ... (7 or 6 taps)
+    float acc[7][2][4];
+#pragma unroll
+    for (int a = 0; a < 7; ++a)
+#pragma unroll
+        for (int n = 0; n < 2; ++n) acc[a][n][0] = acc[a][n][1] = acc[a][n][2] = acc[a][n][3] = 0.f;
+    float bsum = 0.f;  // thread tid < 16: column co0 + tid
+
+    const int first = pc * per_chunk;
+    const int last = min(nbricks, first + per_chunk);
+    for (int br = first; br < last; ++br) {
+        int b, d0, h0, w0;
+        brick_origin(v, k, br, b, d0, h0, w0);
+        __syncthreads();
+        stage_halo(X, Cxs, ci0, v, k, b, d0, h0, w0, hbase);
+        for (int e = threadIdx.x; e < 2 * kBrick; e += blockDim.x) {
+            const int p = e >> 1, half = e & 1;
+            const int pw = p % k.bw, ph = (p / k.bw) % k.bh, pd = p / (k.bw * k.bh);
+            const size_t vox = ((static_cast<size_t>(b) * v.D + d0 + pd) * v.H + h0 + ph) * v.W + w0 + pw;
+            cp_async16(dbase + swz(p, half), dY + vox * Cys + co0 + 8 * half);
+        }
+        cp_async_wait();
+        __syncthreads();
+        if (blockIdx.x == 0 && threadIdx.x < 16) {
+            const int h = threadIdx.x >> 3, c = threadIdx.x & 7;
+            for (int p = 0; p < kBrick; ++p)
+                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(dys + swz(p, h) + 2 * c));
+        }
+#pragma unroll 1
+        for (int ks = 0; ks < 4; ++ks) {
+            // A = dY^T (co x p): stored rows p, columns co
+            uint32_t a0, a1, a2, a3;
+            {
+                const int p = 16 * ks + j + 8 * (i >> 1);
+                ldsm_x4_t(dbase + swz(p, i & 1), a0, a1, a2, a3);
+            }
+            // B rows p (shifted by the tap), columns ci
+            const int p = 16 * ks + j + 8 * (i & 1);
+            const int pw = p % k.bw, ph = (p / k.bw) % k.bh, pd = p / (k.bw * k.bh);
+            const int slot0 = (pd * hh + ph) * hw + pw;
+#pragma unroll
+            for (int a = 0; a < 7; ++a) {
+                const int tap = warp + 4 * a;
+                if (tap < 27) {
+                    const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+                    const int s = slot0 + (kd * hh + kh) * hw + kw;
+                    uint32_t b0, b1, b2, b3;
+                    ldsm_x4_t(hbase + swz(s, i >> 1), b0, b1, b2, b3);
+                    mma_bf16(acc[a][0], a0, a1, a2, a3, b0, b1);
+                    mma_bf16(acc[a][1], a0, a1, a2, a3, b2, b3);
+                }
+            }
+        }
+    }
+    // write partials
+    float* Pp = P + static_cast<size_t>(pc) * Cout * 27 * Cin;
+#pragma unroll
+    for (int a = 0; a < 7; ++a) {
+        const int tap = warp + 4 * a;
+        if (tap >= 27) continue;
+#pragma unroll
+        for (int n = 0; n < 2; ++n)
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int co = co0 + g + 8 * half;
+                const int ci = ci0 + 8 * n + 2 * t;
+                float* q = Pp + (static_cast<size_t>(co) * 27 + tap) * Cin + ci;
+                q[0] = acc[a][n][2 * half];
+                q[1] = acc[a][n][2 * half + 1];
+            }
+    }
+    if (blockIdx.x == 0 && threadIdx.x < 16) {
+        const int h = threadIdx.x >> 3, c = threadIdx.x & 7;
+        Pb[static_cast<size_t>(pc) * Cout + co0 + 8 * h + c] = bsum;
+    }
+}
+
+// out[e] = sum_{pc < n} P[pc * stride + e]  (fixed order)
+__global__ void k_reduce_partials(const float* __restrict__ P, int nchunks, size_t stride,
+                                  float* __restrict__ out)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (e >= stride) return;
+    float s = 0.f;
+    for (int pc = 0; pc < nchunks; ++pc) s += P[pc * stride + e];
+    out[e] = s;
+}
+
+// W'[ci][tap][co] = W[co][26 - tap][ci]   (weights of the adjoint convolution)
+__global__ void k_flip_weights(const __nv_bfloat16* __restrict__ W, int Cout, int Cin,
+                               __nv_bfloat16* __restrict__ Wf)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    const size_t n = static_cast<size_t>(Cout) * 27 * Cin;
+    if (e >= n) return;
+    const int co = static_cast<int>(e % Cout);
+    const int tap = static_cast<int>((e / Cout) % 27);
+    const int ci = static_cast<int>(e / (static_cast<size_t>(Cout) * 27));
+    Wf[e] = W[(static_cast<size_t>(co) * 27 + (26 - tap)) * Cin + ci];
+}
+
+// 8 channels per thread (16 bytes) helpers
+struct V8 {
+    float f[8];
+};
+
+__device__ __forceinline__ V8 load8(const __nv_bfloat16* p)
+{
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    V8 r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        r.f[2 * q] = f.x;
+        r.f[2 * q + 1] = f.y;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void store8(__nv_bfloat16* p, const V8& r)
+{
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(r.f[2 * q], r.f[2 * q + 1]);
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
+// coarse voxel index and channel group of element e (groups of 8 channels)
+__device__ __forceinline__ bool decode8(size_t e, int C, const Vol& v, size_t& vox, int& c)
+{
+    const int G = C / 8;
+    const size_t nvox = static_cast<size_t>(v.B) * v.D * v.H * v.W;
+    if (e >= nvox * G) return false;
+    c = 8 * static_cast<int>(e % G);
+    vox = e / G;
+    return true;
+}
+
+__device__ __forceinline__ size_t fine_vox(const Vol& c, size_t vox, int a)
+{
+    // child a (bits d,h,w) of coarse voxel vox on the 2x finer grid
+    const int w = static_cast<int>(vox % c.W);
+    size_t r = vox / c.W;
+    const int h = static_cast<int>(r % c.H);
+    r /= c.H;
+    const int d = static_cast<int>(r % c.D);
+    const size_t b = r / c.D;
+    const int fd = 2 * d + ((a >> 2) & 1), fh = 2 * h + ((a >> 1) & 1), fw = 2 * w + (a & 1);
+    return ((b * (2 * c.D) + fd) * (2 * c.H) + fh) * (2 * c.W) + fw;
+}
+
+// Y (coarse) = mean of the 2x2x2 children of X (fine)
+__global__ void k_pool2(const __nv_bfloat16* __restrict__ X, int Cxs, int C, __nv_bfloat16* __restrict__ Y,
+                        int Cys, Vol coarse)
+{
+    size_t vox;
+    int c;
+    if (!decode8(blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x, C, coarse, vox, c)) return;
+    V8 s = {};
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+        const V8 x = load8(X + fine_vox(coarse, vox, a) * Cxs + c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s.f[q] += x.f[q];
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) s.f[q] *= 0.125f;
+    store8(Y + vox * Cys + c, s);
+}
+
+// dX (fine) = dY (coarse) / 8 [+ add (fine)]
+__global__ void k_pool2_bwd(const __nv_bfloat16* __restrict__ dY, int Cys, const __nv_bfloat16* __restrict__ add,
+                            int Cas, int C, __nv_bfloat16* __restrict__ dX, int Cxs, Vol coarse)
+{
+    size_t vox;
+    int c;
+    if (!decode8(blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x, C, coarse, vox, c)) return;
+    V8 d = load8(dY + vox * Cys + c);
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+        const size_t f = fine_vox(coarse, vox, a);
+        V8 o;
+        if (add) {
+            const V8 x = load8(add + f * Cas + c);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o.f[q] = fmaf(0.125f, d.f[q], x.f[q]);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) o.f[q] = 0.125f * d.f[q];
+        }
+        store8(dX + f * Cxs + c, o);
+    }
+}
+
+// Y (fine) = X (coarse) repeated over the 2x2x2 children
+__global__ void k_up2(const __nv_bfloat16* __restrict__ X, int Cxs, int C, __nv_bfloat16* __restrict__ Y, int Cys,
+                      Vol coarse)
+{
+    size_t vox;
+    int c;
+    if (!decode8(blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x, C, coarse, vox, c)) return;
+    const uint4 u = *reinterpret_cast<const uint4*>(X + vox * Cxs + c);
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) *reinterpret_cast<uint4*>(Y + fine_vox(coarse, vox, a) * Cys + c) = u;
+}
+
+// dX (coarse) = sum of dY over the 2x2x2 children (fine)
+__global__ void k_up2_bwd(const __nv_bfloat16* __restrict__ dY, int Cys, int C, __nv_bfloat16* __restrict__ dX,
+                          int Cxs, Vol coarse)
+{
+    size_t vox;
+    int c;
+    if (!decode8(blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x, C, coarse, vox, c)) return;
+    V8 s = {};
+#pragma unroll 1
+    for (int a = 0; a < 8; ++a) {
+        const V8 x = load8(dY + fine_vox(coarse, vox, a) * Cys + c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) s.f[q] += x.f[q];
+    }
+    store8(dX + vox * Cxs + c, s);
+}
+
+// dP = dY * (Y > 0 ? 1 : slope)   (leaky ReLU through its output)
+__global__ void k_leaky_bwd(const __nv_bfloat16* __restrict__ dY, int Cds, const __nv_bfloat16* __restrict__ Y,
+                            int Cys, int C, float slope, __nv_bfloat16* __restrict__ dP, int Cps, Vol v)
+{
+    size_t vox;
+    int c;
+    if (!decode8(blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x, C, v, vox, c)) return;
+    V8 d = load8(dY + vox * Cds + c);
+    const V8 y = load8(Y + vox * Cys + c);
+#pragma unroll
+    for (int q = 0; q < 8; ++q) d.f[q] = y.f[q] > 0.f ? d.f[q] : slope * d.f[q];
+    store8(dP + vox * Cps + c, d);
+}
+
+// X[b][p][0..Cs) = (a0 * m0[b][p], a1 * m1[b][p], 0, ...)   (network input)
+__global__ void k_pack_inputs(const float* __restrict__ m0, const float* __restrict__ m1, float a0, float a1,
+                              size_t nvox, __nv_bfloat16* __restrict__ X, int Cs)
+{
+    const size_t p = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (p >= nvox) return;
+    __nv_bfloat16* x = X + p * Cs;
+    *reinterpret_cast<__nv_bfloat162*>(x) = __floats2bfloat162_rn(a0 * m0[p], a1 * m1[p]);
+    for (int c = 2; c < Cs; c += 2) *reinterpret_cast<__nv_bfloat162*>(x + c) = __floats2bfloat162_rn(0.f, 0.f);
+}
+
+// Output head (1x1x1 conv to 3 FP32 components, channels-first per sample):
+// V[b][c][p] = scale (bias[c] + sum_ci X[b,p][ci] Wh[c][ci])
+template <int CIN>
+__global__ void k_head(const __nv_bfloat16* __restrict__ X, int Cxs, const float* __restrict__ Wh,
+                       const float* __restrict__ bh, float scale, size_t nvox_per, int B, float* __restrict__ V)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (e >= nvox_per * B) return;
+    const size_t b = e / nvox_per, p = e % nvox_per;
+    float s0 = bh[0], s1 = bh[1], s2 = bh[2];
+    const __nv_bfloat16* x = X + e * Cxs;
+#pragma unroll
+    for (int c = 0; c < CIN; c += 8) {
+        const V8 xv = load8(x + c);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            s0 = fmaf(xv.f[q], __ldg(Wh + c + q), s0);
+            s1 = fmaf(xv.f[q], __ldg(Wh + CIN + c + q), s1);
+            s2 = fmaf(xv.f[q], __ldg(Wh + 2 * CIN + c + q), s2);
+        }
+    }
+    float* vb = V + b * 3 * nvox_per + p;
+    vb[0] = scale * s0;
+    vb[nvox_per] = scale * s1;
+    vb[2 * nvox_per] = scale * s2;
+}
+
+// head backward: dX[b,p][ci] = scale sum_c dV[b][c][p] Wh[c][ci]; per-block
+// partials of dWh[c][ci] = scale sum_p dV X and dbh[c] = scale sum_p dV,
+// layout [block][3 CIN + 3].
+template <int CIN>
+__global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* __restrict__ X, int Cxs,
+                                                  const float* __restrict__ Wh, float scale, size_t nvox_per,
+                                                  int B, const float* __restrict__ dV,
+                                                  __nv_bfloat16* __restrict__ dX, int Cdxs,
+                                                  float* __restrict__ part)
+{
+    constexpr int NR = 3 * CIN + 3;
+    __shared__ float red[8][NR];
+    float loc[NR];
+#pragma unroll
+    for (int q = 0; q < NR; ++q) loc[q] = 0.f;
+    const size_t n = nvox_per * B;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const size_t b = e / nvox_per, p = e % nvox_per;
+        const float* db = dV + b * 3 * nvox_per + p;
+        const float g0 = scale * db[0], g1 = scale * db[nvox_per], g2 = scale * db[2 * nvox_per];
+#pragma unroll
+        for (int c = 0; c < CIN; c += 8) {
+            const V8 xv = load8(X + e * Cxs + c);
+            V8 o;
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+                o.f[q] = g0 * __ldg(Wh + c + q) + g1 * __ldg(Wh + CIN + c + q) + g2 * __ldg(Wh + 2 * CIN + c + q);
+                loc[c + q] += g0 * xv.f[q];
+                loc[CIN + c + q] += g1 * xv.f[q];
+                loc[2 * CIN + c + q] += g2 * xv.f[q];
+            }
+            if (dX) store8(dX + e * Cdxs + c, o);
+        }
+        loc[3 * CIN] += g0;
+        loc[3 * CIN + 1] += g1;
+        loc[3 * CIN + 2] += g2;
+    }
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int q = 0; q < NR; ++q) {
+        float s = loc[q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+        if (lane == 0) red[warp][q] = s;
+    }
+    __syncthreads();
+    for (int q = threadIdx.x; q < NR; q += blockDim.x) {
+        float s = 0.f;
+        for (int w = 0; w < 8; ++w) s += red[w][q];
+        part[static_cast<size_t>(blockIdx.x) * NR + q] = s;
+    }
+}
+
+// Adam (bias-corrected) on FP32 master weights; optional BF16 copy.
+__global__ void k_adam(float* __restrict__ w, const float* __restrict__ gr, float* __restrict__ m,
+                       float* __restrict__ s, size_t n, float lr, float b1, float b2, float eps, float c1,
+                       float c2, float gscale, __nv_bfloat16* __restrict__ wb)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (e >= n) return;
+    const float g = gscale * gr[e];
+    const float mm = b1 * m[e] + (1.f - b1) * g;
+    const float ss = b2 * s[e] + (1.f - b2) * g * g;
+    m[e] = mm;
+    s[e] = ss;
+    const float wn = w[e] - lr * (mm * c1) / (sqrtf(ss * c2) + eps);
+    w[e] = wn;
+    if (wb) wb[e] = __float2bfloat16_rn(wn);
+}
+
+// dv = a (v - vs) + b gv (gv may be null); *sum += sum (v - vs)^2
+__global__ void __launch_bounds__(256) k_vel_loss(const float* __restrict__ v, const float* __restrict__ vs,
+                                                  const float* __restrict__ gv, float a, float b, size_t n,
+                                                  float* __restrict__ dv, double* __restrict__ sum)
+{
+    double loc = 0.0;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float d = v[e] - vs[e];
+        loc += static_cast<double>(d) * d;
+        dv[e] = gv ? fmaf(a, d, b * gv[e]) : a * d;
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        if (sum) atomicAdd(sum, s);
+    }
+}
+
+// r = x - y; *sum += sum r^2
+// (r may alias x: each element is read and written by one thread)
+__global__ void __launch_bounds__(256) k_residual(const float* x, const float* __restrict__ y, size_t n, float* r,
+                                                  double* __restrict__ sum)
+{
+    double loc = 0.0;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float d = x[e] - y[e];
+        loc += static_cast<double>(d) * d;
+        if (r) r[e] = d;
+    }
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        if (sum) atomicAdd(sum, s);
+    }
+}
+
+inline unsigned nblk(size_t n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
+
+}  // namespace
+
+bool brick_for(int D, int H, int W, int* bd, int* bh, int* bw)
+{
+    const int w = W >= 16 ? 16 : W;
+    const int h = H >= kBrick / w ? kBrick / w : H;
+    const int d = kBrick / (w * h);
+    if (w < 4 || w * h * d != kBrick || d > D || D % d || H % h || W % w) return false;
+    *bd = d;
+    *bh = h;
+    *bw = w;
+    return (d + 2) * (h + 2) * (w + 2) <= kHaloMax;
+}
+
+cudaError_t conv3d(const void* X, int Cxs, int Cin, const void* Wt, const float* bias, float slope, int act,
+                   void* Y, int Cys, int Cout, int B, int D, int H, int W, cudaStream_t st)
+{
+    int bd, bh, bw;
+    if (!brick_for(D, H, W, &bd, &bh, &bw)) return cudaErrorInvalidValue;
+    const Vol v{B, D, H, W};
+    const Brick k{bd, bh, bw, D / bd, H / bh, W / bw};
+    const unsigned grid = static_cast<unsigned>(B * k.nd * k.nh * k.nw);
+    auto x = static_cast<const __nv_bfloat16*>(X);
+    auto w = static_cast<const __nv_bfloat16*>(Wt);
+    auto y = static_cast<__nv_bfloat16*>(Y);
+    switch (Cout / 8) {
+    case 2: k_conv3d<2><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 4: k_conv3d<4><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 6: k_conv3d<6><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 8: k_conv3d<8><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 12: k_conv3d<12><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 16: k_conv3d<16><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    case 24: k_conv3d<24><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
+    default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t flip_weights(const void* W, int Cout, int Cin, void* Wf, cudaStream_t st)
+{
+    const size_t n = static_cast<size_t>(Cout) * 27 * Cin;
+    k_flip_weights<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(W), Cout, Cin,
+                                                 static_cast<__nv_bfloat16*>(Wf));
+    return cudaGetLastError();
+}
+
+int wgrad_chunks(int Cin, int Cout, int B, int D, int H, int W, int nsm)
+{
+    int bd, bh, bw;
+    if (!brick_for(D, H, W, &bd, &bh, &bw)) return 0;
+    const int nbricks = B * (D / bd) * (H / bh) * (W / bw);
+    const int pairs = (Cin / 16) * (Cout / 16);
+    int chunks = (8 * nsm + pairs - 1) / pairs;
+    if (chunks > nbricks) chunks = nbricks;
+    if (chunks < 1) chunks = 1;
+    const int per = (nbricks + chunks - 1) / chunks;
+    return (nbricks + per - 1) / per;
+}
+
+cudaError_t conv3d_wgrad(const void* X, int Cxs, int Cin, const void* dY, int Cys, int Cout, int B, int D, int H,
+                         int W, int chunks, float* part, float* partb, float* dW, float* db, cudaStream_t st)
+{
+    int bd, bh, bw;
+    if (!brick_for(D, H, W, &bd, &bh, &bw)) return cudaErrorInvalidValue;
+    const Vol v{B, D, H, W};
+    const Brick k{bd, bh, bw, D / bd, H / bh, W / bw};
+    const int nbricks = B * k.nd * k.nh * k.nw;
+    const int per = (nbricks + chunks - 1) / chunks;
+    if ((nbricks + per - 1) / per != chunks) return cudaErrorInvalidValue;
+    const dim3 grid(Cin / 16, Cout / 16, chunks);
+    k_conv3d_wgrad<<<grid, kConvThreads, 0, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, Cin,
+                                                  static_cast<const __nv_bfloat16*>(dY), Cys, Cout, v, k,
+                                                  nbricks, per, part, partb);
+    const size_t nw = static_cast<size_t>(Cout) * 27 * Cin;
+    k_reduce_partials<<<nblk(nw, 256), 256, 0, st>>>(part, chunks, nw, dW);
+    if (db) k_reduce_partials<<<nblk(Cout, 256), 256, 0, st>>>(partb, chunks, Cout, db);
+    return cudaGetLastError();
+}
+
+cudaError_t pool2(const void* X, int Cxs, int C, void* Y, int Cys, int B, int Dc, int Hc, int Wc, cudaStream_t st)
+{
+    const Vol c{B, Dc, Hc, Wc};
+    const size_t n = static_cast<size_t>(B) * Dc * Hc * Wc * (C / 8);
+    k_pool2<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, C,
+                                          static_cast<__nv_bfloat16*>(Y), Cys, c);
+    return cudaGetLastError();
+}
+
+cudaError_t pool2_bwd(const void* dY, int Cys, const void* add, int Cas, int C, void* dX, int Cxs, int B, int Dc,
+                      int Hc, int Wc, cudaStream_t st)
+{
+    const Vol c{B, Dc, Hc, Wc};
+    const size_t n = static_cast<size_t>(B) * Dc * Hc * Wc * (C / 8);
+    k_pool2_bwd<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dY), Cys,
+                                              static_cast<const __nv_bfloat16*>(add), Cas, C,
+                                              static_cast<__nv_bfloat16*>(dX), Cxs, c);
+    return cudaGetLastError();
+}
+
+cudaError_t up2(const void* X, int Cxs, int C, void* Y, int Cys, int B, int Dc, int Hc, int Wc, cudaStream_t st)
+{
+    const Vol c{B, Dc, Hc, Wc};
+    const size_t n = static_cast<size_t>(B) * Dc * Hc * Wc * (C / 8);
+    k_up2<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, C,
+                                        static_cast<__nv_bfloat16*>(Y), Cys, c);
+    return cudaGetLastError();
+}
+
+cudaError_t up2_bwd(const void* dY, int Cys, int C, void* dX, int Cxs, int B, int Dc, int Hc, int Wc,
+                    cudaStream_t st)
+{
+    const Vol c{B, Dc, Hc, Wc};
+    const size_t n = static_cast<size_t>(B) * Dc * Hc * Wc * (C / 8);
+    k_up2_bwd<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dY), Cys, C,
+                                            static_cast<__nv_bfloat16*>(dX), Cxs, c);
+    return cudaGetLastError();
+}
+
+cudaError_t leaky_bwd(const void* dY, int Cds, const void* Y, int Cys, int C, float slope, void* dP, int Cps, int B,
+                      int D, int H, int W, cudaStream_t st)
+{
+    const Vol v{B, D, H, W};
+    const size_t n = static_cast<size_t>(B) * D * H * W * (C / 8);
+    k_leaky_bwd<<<nblk(n, 256), 256, 0, st>>>(static_cast<const __nv_bfloat16*>(dY), Cds,
+                                              static_cast<const __nv_bfloat16*>(Y), Cys, C, slope,
+                                              static_cast<__nv_bfloat16*>(dP), Cps, v);
+    return cudaGetLastError();
+}
+
+cudaError_t pack_inputs(const float* m0, const float* m1, float a0, float a1, size_t nvox, void* X, int Cs,
+                        cudaStream_t st)
+{
+    k_pack_inputs<<<nblk(nvox, 256), 256, 0, st>>>(m0, m1, a0, a1, nvox, static_cast<__nv_bfloat16*>(X), Cs);
+    return cudaGetLastError();
+}
+
+cudaError_t head(const void* X, int Cxs, int Cin, const float* Wh, const float* bh, float scale, size_t nvox_per,
+                 int B, float* V, cudaStream_t st)
+{
+    auto x = static_cast<const __nv_bfloat16*>(X);
+    const unsigned g = nblk(nvox_per * B, 256);
+    if (Cin == 16)
+        k_head<16><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    else if (Cin == 32)
+        k_head<32><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    else
+        return cudaErrorInvalidValue;
+    return cudaGetLastError();
+}
+
+int head_bwd_blocks(size_t nvox, int nsm)
+{
+    const size_t want = (nvox + 255) / 256;
+    const size_t cap = static_cast<size_t>(2 * nsm);
+    return static_cast<int>(want < cap ? (want ? want : 1) : cap);
+}
+
+cudaError_t head_bwd(const void* X, int Cxs, int Cin, const float* Wh, float scale, size_t nvox_per, int B,
+                     const float* dV, void* dX, int Cdxs, int nblocks, float* part, float* dWb, cudaStream_t st)
+{
+    auto x = static_cast<const __nv_bfloat16*>(X);
+    auto dx = static_cast<__nv_bfloat16*>(dX);
+    if (Cin == 16)
+        k_head_bwd<16><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    else if (Cin == 32)
+        k_head_bwd<32><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    else
+        return cudaErrorInvalidValue;
+    const size_t nred = static_cast<size_t>(3 * Cin + 3);
+    k_reduce_partials<<<nblk(nred, 256), 256, 0, st>>>(part, nblocks, nred, dWb);
+    return cudaGetLastError();
+}
+
+cudaError_t adam(float* w, const float* g, float* m, float* s, size_t n, float lr, float b1, float b2, float eps,
+                 int step, float gscale, void* wb, cudaStream_t st)
+{
+    const float c1 = 1.0f / (1.0f - powf(b1, static_cast<float>(step)));
+    const float c2 = 1.0f / (1.0f - powf(b2, static_cast<float>(step)));
+    k_adam<<<nblk(n, 256), 256, 0, st>>>(w, g, m, s, n, lr, b1, b2, eps, c1, c2, gscale,
+                                         static_cast<__nv_bfloat16*>(wb));
+    return cudaGetLastError();
+}
+
+cudaError_t vel_loss(const float* v, const float* vs, const float* gv, float a, float b, size_t n, float* dv,
+                     double* sum, int nsm, cudaStream_t st)
+{
+    const unsigned g = static_cast<unsigned>(std::min<size_t>(nblk(n, 256), static_cast<size_t>(4 * nsm)));
+    k_vel_loss<<<g ? g : 1, 256, 0, st>>>(v, vs, gv, a, b, n, dv, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t residual(const float* x, const float* y, size_t n, float* r, double* sum, int nsm, cudaStream_t st)
+{
+    const unsigned g = static_cast<unsigned>(std::min<size_t>(nblk(n, 256), static_cast<size_t>(4 * nsm)));
+    k_residual<<<g ? g : 1, 256, 0, st>>>(x, y, n, r, sum);
+    return cudaGetLastError();
+}
+
+}  // namespace net
+}  // namespace claire
+
+// ---------------------------------------------------------------------------
+// C ABI
+// ---------------------------------------------------------------------------
+
+namespace claire {
+namespace net {
+namespace {
+
+thread_local char g_net_err[256] = "";
+
+claire_status net_fail(const char* fmt, ...)
+{
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(g_net_err, sizeof(g_net_err), fmt, ap);
+    va_end(ap);
+    return CLAIRE_EINVAL;
+}
+
+claire_status net_status(cudaError_t e, const char* what)
+{
+    if (e == cudaSuccess) return CLAIRE_OK;
+    std::snprintf(g_net_err, sizeof(g_net_err), "%s: %s", what, cudaGetErrorString(e));
+    return CLAIRE_ECUDA;
+}
+
+bool aligned16(const void* p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+bool pow2_ge4(int n) { return n >= 4 && (n & (n - 1)) == 0; }
+
+claire_status check_vol(const int vol[4])
+{
+    if (!vol) return net_fail("null vol");
+    if (vol[0] < 1 || !pow2_ge4(vol[1]) || !pow2_ge4(vol[2]) || !pow2_ge4(vol[3]))
+        return net_fail("vol {%d,%d,%d,%d}: B >= 1 and D, H, W powers of two >= 4 required", vol[0], vol[1],
+                        vol[2], vol[3]);
+    return CLAIRE_OK;
+}
+
+claire_status check_slice(const void* p, int stride, int c, const char* name)
+{
+    if (!p) return net_fail("%s: null pointer", name);
+    if (!aligned16(p)) return net_fail("%s: pointer not 16-byte aligned", name);
+    if (c < 8 || c % 8 || stride < c || stride % 8)
+        return net_fail("%s: channels %d / stride %d must be multiples of 8 with stride >= channels", name, c,
+                        stride);
+    return CLAIRE_OK;
+}
+
+int device_sms()
+{
+    int dev = 0, n = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev) !=
+                                                  cudaSuccess)
+        return 152;
+    return n > 0 ? n : 152;
+}
+
+#define NET_TRY(expr)                       \
+    do {                                    \
+        const claire_status s_ = (expr);    \
+        if (s_ != CLAIRE_OK) return s_;     \
+    } while (0)
+
+inline cudaStream_t as_stream(void* s) { return static_cast<cudaStream_t>(s); }
+
+}  // namespace
+
+}  // namespace net
+}  // namespace claire
+
+using namespace claire::net;
+
+extern "C" claire_status claire_net_conv3d(const void* x, int x_stride, int cin, const void* w, const float* bias,
+                                           float slope, int act, void* y, int y_stride, int cout, const int vol[4],
+                                           void* stream)
+{
+    NET_TRY(check_vol(vol));
+    NET_TRY(check_slice(x, x_stride, cin, "conv3d x"));
+    NET_TRY(check_slice(y, y_stride, cout, "conv3d y"));
+    if (!w || !aligned16(w)) return net_fail("conv3d: weights null or not 16-byte aligned");
+    const int nt = cout / 8;
+    const bool nt_ok = nt == 2 || nt == 4 || nt == 6 || nt == 8 || nt == 12 || nt == 16 || nt == 24;
+    if (cin % 16 || cout % 8 || !nt_ok)
+        return net_fail("conv3d: cin %d (multiple of 16), cout %d (16, 32, 48, 64, 96, 128 or 192)", cin, cout);
+    int bd, bh, bw;
+    if (!brick_for(vol[1], vol[2], vol[3], &bd, &bh, &bw))
+        return net_fail("conv3d: grid %dx%dx%d has fewer than 64 voxels", vol[1], vol[2], vol[3]);
+    if (act != 0 && act != 1) return net_fail("conv3d: act %d", act);
+    return net_status(conv3d(x, x_stride, cin, w, bias, slope, act, y, y_stride, cout, vol[0], vol[1], vol[2],
+                             vol[3], as_stream(stream)),
+                      "conv3d");
+}
+
+extern "C" claire_status claire_net_conv3d_flip(const void* w, int cout, int cin, void* wf, void* stream)
+{
+    if (!w || !wf || cin < 1 || cout < 1) return net_fail("conv3d_flip: bad arguments");
+    return net_status(flip_weights(w, cout, cin, wf, as_stream(stream)), "conv3d_flip");
+}
+
+extern "C" claire_status claire_net_conv3d_wgrad_chunks(int cin, int cout, const int vol[4], int* chunks)
+{
+    NET_TRY(check_vol(vol));
+    if (!chunks || cin % 16 || cout % 16 || cin < 16 || cout < 16)
+        return net_fail("conv3d_wgrad_chunks: cin %d, cout %d must be multiples of 16", cin, cout);
+    const int c = wgrad_chunks(cin, cout, vol[0], vol[1], vol[2], vol[3], device_sms());
+    if (c < 1) return net_fail("conv3d_wgrad_chunks: grid has fewer than 64 voxels");
+    *chunks = c;
+    return CLAIRE_OK;
+}
+
+extern "C" claire_status claire_net_conv3d_wgrad(const void* x, int x_stride, int cin, const void* dy,
+                                                 int dy_stride, int cout, const int vol[4], int chunks,
+                                                 float* part, float* part_bias, float* dw, float* db, void* stream)
+{
+    NET_TRY(check_vol(vol));
+    NET_TRY(check_slice(x, x_stride, cin, "conv3d_wgrad x"));
+    NET_TRY(check_slice(dy, dy_stride, cout, "conv3d_wgrad dy"));
+    if (cin % 16 || cout % 16) return net_fail("conv3d_wgrad: cin %d, cout %d must be multiples of 16", cin, cout);
+    if (!part || !part_bias || !dw) return net_fail("conv3d_wgrad: null partial or output buffer");
+    int expect = 0;
+    NET_TRY(claire_net_conv3d_wgrad_chunks(cin, cout, vol, &expect));
+    if (chunks != expect) return net_fail("conv3d_wgrad: chunks %d, expected %d", chunks, expect);
+    return net_status(conv3d_wgrad(x, x_stride, cin, dy, dy_stride, cout, vol[0], vol[1], vol[2], vol[3], chunks,
+                                   part, part_bias, dw, db, as_stream(stream)),
+                      "conv3d_wgrad");
+}
+
+extern "C" claire_status claire_net_pool2(const void* x, int x_stride, int c, void* y, int y_stride,
+                                          const int vol[4], void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("pool2: bad vol");
+    NET_TRY(check_slice(x, x_stride, c, "pool2 x"));
+    NET_TRY(check_slice(y, y_stride, c, "pool2 y"));
+    return net_status(pool2(x, x_stride, c, y, y_stride, vol[0], vol[1], vol[2], vol[3], as_stream(stream)),
+                      "pool2");
+}
+
+extern "C" claire_status claire_net_pool2_bwd(const void* dy, int dy_stride, const void* add, int add_stride,
+                                              int c, void* dx, int dx_stride, const int vol[4], void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("pool2_bwd: bad vol");
+    NET_TRY(check_slice(dy, dy_stride, c, "pool2_bwd dy"));
+    NET_TRY(check_slice(dx, dx_stride, c, "pool2_bwd dx"));
+    if (add) NET_TRY(check_slice(add, add_stride, c, "pool2_bwd add"));
+    return net_status(pool2_bwd(dy, dy_stride, add, add_stride, c, dx, dx_stride, vol[0], vol[1], vol[2], vol[3],
+                                as_stream(stream)),
+                      "pool2_bwd");
+}
+
+extern "C" claire_status claire_net_up2(const void* x, int x_stride, int c, void* y, int y_stride, const int vol[4],
+                                        void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("up2: bad vol");
+    NET_TRY(check_slice(x, x_stride, c, "up2 x"));
+    NET_TRY(check_slice(y, y_stride, c, "up2 y"));
+    return net_status(up2(x, x_stride, c, y, y_stride, vol[0], vol[1], vol[2], vol[3], as_stream(stream)), "up2");
+}
+
+extern "C" claire_status claire_net_up2_bwd(const void* dy, int dy_stride, int c, void* dx, int dx_stride,
+                                            const int vol[4], void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("up2_bwd: bad vol");
+    NET_TRY(check_slice(dy, dy_stride, c, "up2_bwd dy"));
+    NET_TRY(check_slice(dx, dx_stride, c, "up2_bwd dx"));
+    return net_status(up2_bwd(dy, dy_stride, c, dx, dx_stride, vol[0], vol[1], vol[2], vol[3], as_stream(stream)),
+                      "up2_bwd");
+}
+
+extern "C" claire_status claire_net_leaky_bwd(const void* dy, int dy_stride, const void* y, int y_stride, int c,
+                                              float slope, void* dp, int dp_stride, const int vol[4], void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("leaky_bwd: bad vol");
+    NET_TRY(check_slice(dy, dy_stride, c, "leaky_bwd dy"));
+    NET_TRY(check_slice(y, y_stride, c, "leaky_bwd y"));
+    NET_TRY(check_slice(dp, dp_stride, c, "leaky_bwd dp"));
+    return net_status(leaky_bwd(dy, dy_stride, y, y_stride, c, slope, dp, dp_stride, vol[0], vol[1], vol[2], vol[3],
+                                as_stream(stream)),
+                      "leaky_bwd");
+}
+
+extern "C" claire_status claire_net_pack(const float* m0, const float* m1, float a0, float a1, size_t nvox, void* x,
+                                         int stride, void* stream)
+{
+    if (!m0 || !m1 || !x || stride < 2 || stride % 2 || !aligned16(x)) return net_fail("pack: bad arguments");
+    return net_status(pack_inputs(m0, m1, a0, a1, nvox, x, stride, as_stream(stream)), "pack");
+}
+
+extern "C" claire_status claire_net_head(const void* x, int x_stride, int cin, const float* wh, const float* bh,
+                                         float scale, void* v, const int vol[4], void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("head: bad vol");
+    NET_TRY(check_slice(x, x_stride, cin, "head x"));
+    if (cin != 16 && cin != 32) return net_fail("head: cin %d (16 or 32)", cin);
+    if (!wh || !bh || !v) return net_fail("head: null pointer");
+    const size_t nvox = static_cast<size_t>(vol[1]) * vol[2] * vol[3];
+    return net_status(head(x, x_stride, cin, wh, bh, scale, nvox, vol[0], static_cast<float*>(v), as_stream(stream)),
+                      "head");
+}
+
+extern "C" claire_status claire_net_head_bwd_blocks(const int vol[4], int* blocks)
+{
+    if (!vol || !blocks || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1)
+        return net_fail("head_bwd_blocks: bad arguments");
+    *blocks = head_bwd_blocks(static_cast<size_t>(vol[0]) * vol[1] * vol[2] * vol[3], device_sms());
+    return CLAIRE_OK;
+}
+
+extern "C" claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, const float* wh, float scale,
+                                             const float* dv, void* dx, int dx_stride, const int vol[4], int blocks,
+                                             float* part, float* dwb, void* stream)
+{
+    if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("head_bwd: bad vol");
+    NET_TRY(check_slice(x, x_stride, cin, "head_bwd x"));
+    if (dx) NET_TRY(check_slice(dx, dx_stride, cin, "head_bwd dx"));
+    if (cin != 16 && cin != 32) return net_fail("head_bwd: cin %d (16 or 32)", cin);
+    int expect = 0;
+    NET_TRY(claire_net_head_bwd_blocks(vol, &expect));
+    if (blocks != expect) return net_fail("head_bwd: blocks %d, expected %d", blocks, expect);
+    if (!wh || !dv || !part || !dwb) return net_fail("head_bwd: null pointer");
+    const size_t nvox = static_cast<size_t>(vol[1]) * vol[2] * vol[3];
+    return net_status(head_bwd(x, x_stride, cin, wh, scale, nvox, vol[0], dv, dx, dx_stride, blocks, part, dwb,
+                               as_stream(stream)),
+                      "head_bwd");
+}
+
+extern "C" claire_status claire_net_adam(float* w, const float* g, float* m, float* s, size_t n, float lr,
+                                         float beta1, float beta2, float eps, int step, float gscale, void* wb,
+                                         void* stream)
+{
+    if (!w || !g || !m || !s || step < 1) return net_fail("adam: bad arguments");
+    return net_status(adam(w, g, m, s, n, lr, beta1, beta2, eps, step, gscale, wb, as_stream(stream)), "adam");
+}
+
+extern "C" const char* claire_net_last_error(void) { return g_net_err; }
+
+extern "C" claire_status claire_net_vel_loss(const float* v, const float* vstar, const float* gv, float a, float b,
+                                             size_t n, float* dv, double* sum, void* stream)
+{
+    if (!v || !vstar || !dv) return net_fail("vel_loss: null pointer");
+    return net_status(vel_loss(v, vstar, gv, a, b, n, dv, sum, device_sms(), as_stream(stream)), "vel_loss");
+}
+
+extern "C" claire_status claire_net_residual(const float* x, const float* y, size_t n, float* r, double* sum,
+                                             void* stream)
+{
+    if (!x || !y) return net_fail("residual: null pointer");
+    return net_status(residual(x, y, n, r, sum, device_sms(), as_stream(stream)), "residual");
+}

@@ -19,8 +19,8 @@ def claire():
     return c
 
 
-def _declared():
-    src = open(os.path.join(ROOT, "include", "claire.h")).read()
+def _declared(header="claire.h"):
+    src = open(os.path.join(ROOT, "include", header)).read()
     src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
     return sorted(set(re.findall(r"\b(claire_[a-z0-9_]+)\s*\(", src)))
 
@@ -33,6 +33,32 @@ def test_every_declared_symbol_is_exported(claire):
         assert hasattr(lib, name), name
     # the binding wraps exactly the declared entry points
     assert set(claire.exported_symbols()) == set(declared)
+
+
+def test_every_network_symbol_is_exported(claire):
+    """include/claire_net.h: exported by libclaire and bound by net.py with
+    the same names; host-side validation rejects bad shapes without a GPU."""
+    from paper_2209_08189_gb300 import net
+    lib = net.lib()
+    declared = _declared("claire_net.h")
+    assert len(declared) >= 15
+    for name in declared:
+        assert hasattr(lib, name), name
+    assert set(net._SIGS) == set(declared)
+    chunks = ctypes.c_int()
+    bad = (ctypes.c_int * 4)(1, 8, 8, 6)
+    assert lib.claire_net_conv3d_wgrad_chunks(16, 16, bad, ctypes.byref(chunks)) == -1
+    assert b"powers of two" in lib.claire_net_last_error()
+    good = (ctypes.c_int * 4)(1, 8, 8, 8)
+    assert lib.claire_net_conv3d_wgrad_chunks(24, 16, good, ctypes.byref(chunks)) == -1
+
+
+def test_net_layer_table_has_the_stated_size(claire):
+    from paper_2209_08189_gb300 import net
+    layers = net.unet_layers((16, 32, 64, 128), 16)
+    n = sum(co * 27 * ci + co for _, ci, co in layers) + 3 * 16 + 3
+    assert 1.4e6 < n < 1.5e6
+    assert [l[0] for l in layers][:2] == ["enc0a", "enc0b"] and layers[-1][0] == "dec0b"
 
 
 def test_default_opts(claire):

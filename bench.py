@@ -56,6 +56,10 @@ def parse_args():
     ap.add_argument("--mixed-report", action="store_true",
                     help="FP32 vs FP16 vs BF16 storage on the blob workload at --n (default 512): "
                          "time, throughput and each result's error against the FP64 oracle")
+    ap.add_argument("--warmstart-report", action="store_true",
+                    help="time to tolerance at --n: plain FP32 from v=0 vs FP16 storage + learned warm start "
+                         "(network trained at n/2 on pairs the method generates)")
+    ap.add_argument("--ws-steps", type=int, default=2000, help="training steps of the warm-start network")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -471,8 +475,111 @@ def run_mixed_report(args):
     print(json.dumps(out))
 
 
+def run_warmstart_report(args):
+    """Time to tolerance on the clinical-size workload: plain FP32 from v = 0
+    against FP16 storage + learned warm start.  The network (4-level U-Net,
+    BF16) is trained at n/2 on pairs the method generates (label and blob
+    templates advected by band-limited velocities |k| <= 8, max|v| in
+    [0.3, 1.2], noise sigma 0.02); at n the images are sampled to n/2, the
+    prediction is prolonged spectrally.  Both solves stop at the same absolute
+    gradient, 5e-2 |g(v=0)|; the warm-started timing includes the prediction
+    and the gradient at v = 0.  Final J and mismatch are re-evaluated by the
+    FP64 oracle at each returned velocity."""
+    import torch
+    import oracle
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth, net, warmstart
+    n = args.n
+    nn_ = n // 2
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "%d^3 nested-label template, band-limited v* |k|<=8 max|v|=1, noise 0.02, nt=4, "
+                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|" % (n, args.beta)}
+    t0 = time.perf_counter()
+    src = warmstart.PairSource(nn_, n_templates=24, n_velocities=48, kmax=(4, 8), vmax=(0.3, 1.2), noise=0.02,
+                               seed=0)
+    out["pair_pool_s"] = time.perf_counter() - t0
+    u = net.UNet(seed=0, stream=st)
+    t0 = time.perf_counter()
+    hist = warmstart.train(u, src, steps=args.ws_steps, batch=4, lr=1e-3, lr_final=1e-4, wv=1.0, wm=1.0,
+                           log_every=max(1, args.ws_steps // 10))
+    out["training"] = {"grid": nn_, "steps": args.ws_steps, "batch": 4, "pairs": 4 * args.ws_steps,
+                       "params": u.num_params(), "seconds": time.perf_counter() - t0,
+                       "history": [{"step": h[0], "Lv": h[1], "mismatch_rel": h[2]} for h in hist]}
+    src.ctx.close()
+    grid, base, vstar = workload(n)
+    N = int(np.prod(grid))
+    ctx32 = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50)
+    ctx16 = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                           storage=claire.STORAGE_F16)
+    base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
+    m1c = torch.empty(grid, device=dev)
+    ctx32.transport(torch.from_numpy(vstar.astype(np.float32)).to(dev), base_d, m1c, claire.TRANSPORT_FWD)
+    m1 = synth.add_noise(m1c.cpu().numpy().astype(np.float64), 0.02, seed=1).astype(np.float32)
+    m0 = synth.add_noise(base, 0.02, seed=0).astype(np.float32)
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.from_numpy(m1).to(dev)
+    ctx32.set_images(m0_d, m1_d)
+    ctx16.set_images(m0_d, m1_d)
+    ws = warmstart.WarmStart(u, nn_)
+    zero = torch.zeros((3,) + grid, device=dev)
+    g = torch.empty((3,) + grid, device=dev)
+
+    def solve(ctx, learned):
+        v = torch.zeros((3,) + grid, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        split = {}
+        if learned:
+            ws.predict(m0_d, m1_d, v)
+            torch.cuda.synchronize()
+            split["predict_s"] = time.perf_counter() - t0
+            ctx.gradient(zero, g)
+            g0 = math.sqrt(claire.claire_dot(ctx.handle, g, g, 3 * N))
+            ctx.set_opts(g0_ref=g0)
+            split["g0_s"] = time.perf_counter() - t0 - split["predict_s"]
+        else:
+            ctx.set_opts(g0_ref=0.0)
+        status, rep = ctx.register(v)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        return secs, rep, v, split
+
+    runs = {}
+    for name, ctx, learned in (("fp32_zero", ctx32, False), ("fp16_zero", ctx16, False),
+                               ("fp32_learned", ctx32, True), ("fp16_learned", ctx16, True)):
+        solve(ctx, learned)  # warm-up
+        secs, rep, v, split = solve(ctx, learned)
+        runs[name] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                      "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "gnorm_rel_to_own_g0":
+                      rep["gnorm_rel"], "detj_min": rep["detj_min"], "detj_max": rep["detj_max"], **split}
+        runs[name]["_v"] = v.cpu().numpy()
+    vw = torch.empty((3,) + grid, device=dev)
+    ws.predict(m0_d, m1_d, vw)
+    out["guess"] = {"mismatch_at_guess": ctx32.objective(vw)[1], "mismatch_at_zero": ctx32.objective(zero)[1]}
+    p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
+    m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
+    for name in ("fp32_zero", "fp16_learned"):
+        J_o, mis_o, _ = oracle.objective(runs[name]["_v"].astype(np.float64), m0_64, m1_64, p)
+        runs[name]["oracle_J"] = J_o
+        runs[name]["oracle_mismatch"] = mis_o
+    for r in runs.values():
+        r.pop("_v")
+    out["runs"] = runs
+    a, b = runs["fp32_zero"], runs["fp16_learned"]
+    out["speedup_fp16_learned_vs_fp32_zero"] = a["time_to_tol_s"] / b["time_to_tol_s"]
+    out["oracle_J_rel_diff_learned_vs_plain"] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
+    out["oracle_mismatch_rel_diff_learned_vs_plain"] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / \
+        a["oracle_mismatch"]
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.warmstart_report:
+        run_warmstart_report(args)
+        return
     if args.mixed_report:
         run_mixed_report(args)
         return

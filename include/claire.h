@@ -243,15 +243,20 @@ claire_status claire_transport_vjp(claire_ctx* ctx, const float* v, const float*
  *     dropped, new ones are zero): band-limited interpolation / truncation.
  *   CLAIRE_RESAMPLE_NEAREST: out[j] = in[floor(j * n_from / n_to)] per axis.
  * `in` and `out` are device pointers (caller-owned, must not overlap); work
- * is queued on `stream`.  The spectral mode allocates temporary spectra and
- * cuFFT plans and synchronises the stream before returning.  Needs no
- * context.  Errors: CLAIRE_EINVAL (shapes, mode), CLAIRE_ENOMEM,
- * CLAIRE_ECUFFT, CLAIRE_ECUDA, CLAIRE_ETOOLARGE (a grid of 2^31 points or more).
+ * is queued on `stream`.  Needs no context.  The spectral mode keeps cuFFT
+ * plans and two spectra for the last four (device, from, to) combinations
+ * (freed by claire_resample_release), serialises callers on a mutex and
+ * synchronises the stream before returning.  Errors: CLAIRE_EINVAL (shapes,
+ * mode), CLAIRE_ENOMEM, CLAIRE_ECUFFT, CLAIRE_ECUDA, CLAIRE_ETOOLARGE (a
+ * grid of 2^31 points or more).
  */
 #define CLAIRE_RESAMPLE_SPECTRAL 0
 #define CLAIRE_RESAMPLE_NEAREST 1
 claire_status claire_resample(const float* in, const int from[3], float* out, const int to[3], int ncomp, int mode,
                               void* stream);
+/* Free the plans and spectra cached by claire_resample (all devices' entries;
+ * call with no claire_resample in flight). */
+claire_status claire_resample_release(void);
 
 /* Extrema of the Jacobian determinant det grad y of the deformation map of v
  * (Sec. 3, "J_min"; y = x + u with u transported by the state's SL steps,

@@ -102,6 +102,7 @@ _SIGS = {
     "claire_transport": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_detj": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
     "claire_transport_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int],
+    "claire_resample_release": [],
     "claire_set_opts": [_vp, ctypes.POINTER(claire_opts)],
     "claire_get_opts": [_vp, ctypes.POINTER(claire_opts)],
     "claire_resample": [_vp, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,

@@ -9,6 +9,8 @@
 #include <cufft.h>
 
 #include <cstdio>
+#include <mutex>
+#include <vector>
 
 namespace claire {
 
@@ -56,9 +58,78 @@ __global__ void k_nearest(const float* __restrict__ in, int n1, int n2, int n3, 
     out[e] = in[(static_cast<size_t>(i1) * n2 + i2) * n3 + i3];
 }
 
+// cuFFT plans and spectra of recently used grid pairs (per device), reused
+// across calls; released by claire_resample_release.
+struct PlanEntry {
+    int device = 0;
+    int from[3] = {0, 0, 0}, to[3] = {0, 0, 0};
+    cufftHandle fwd = 0, inv = 0;
+    cufftComplex* X = nullptr;
+    cufftComplex* Y = nullptr;
+};
+constexpr size_t kMaxPlans = 4;
+std::mutex g_plan_mu;
+std::vector<PlanEntry> g_plans;
+
+void destroy_entry(PlanEntry& e)
+{
+    if (e.fwd) cufftDestroy(e.fwd);
+    if (e.inv) cufftDestroy(e.inv);
+    if (e.X) cudaFree(e.X);
+    if (e.Y) cudaFree(e.Y);
+    e = PlanEntry{};
+}
+
+// Entry for (device, from, to); created on a miss (oldest evicted).  Caller holds g_plan_mu.
+claire_status plan_for(const int from[3], const int to[3], PlanEntry** out)
+{
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) return CLAIRE_ECUDA;
+    for (auto& e : g_plans)
+        if (e.device == dev && e.from[0] == from[0] && e.from[1] == from[1] && e.from[2] == from[2] &&
+            e.to[0] == to[0] && e.to[1] == to[1] && e.to[2] == to[2]) {
+            *out = &e;
+            return CLAIRE_OK;
+        }
+    if (g_plans.size() >= kMaxPlans) {
+        destroy_entry(g_plans.front());
+        g_plans.erase(g_plans.begin());
+    }
+    PlanEntry e;
+    e.device = dev;
+    for (int a = 0; a < 3; ++a) {
+        e.from[a] = from[a];
+        e.to[a] = to[a];
+    }
+    const size_t Min = static_cast<size_t>(from[0]) * from[1] * (from[2] / 2 + 1);
+    const size_t Mout = static_cast<size_t>(to[0]) * to[1] * (to[2] / 2 + 1);
+    if (cudaMalloc(&e.X, Min * sizeof(cufftComplex)) != cudaSuccess ||
+        cudaMalloc(&e.Y, Mout * sizeof(cufftComplex)) != cudaSuccess) {
+        cudaGetLastError();
+        destroy_entry(e);
+        return CLAIRE_ENOMEM;
+    }
+    if (cufftPlan3d(&e.fwd, from[0], from[1], from[2], CUFFT_R2C) != CUFFT_SUCCESS ||
+        cufftPlan3d(&e.inv, to[0], to[1], to[2], CUFFT_C2R) != CUFFT_SUCCESS) {
+        destroy_entry(e);
+        return CLAIRE_ECUFFT;
+    }
+    g_plans.push_back(e);
+    *out = &g_plans.back();
+    return CLAIRE_OK;
+}
+
 }  // namespace
 
 }  // namespace claire
+
+extern "C" claire_status claire_resample_release(void)
+{
+    std::lock_guard<std::mutex> lock(claire::g_plan_mu);
+    for (auto& e : claire::g_plans) claire::destroy_entry(e);
+    claire::g_plans.clear();
+    return CLAIRE_OK;
+}
 
 extern "C" claire_status claire_resample(const float* in, const int from[3], float* out, const int to[3], int ncomp,
                                          int mode, void* stream)
@@ -71,7 +142,6 @@ extern "C" claire_status claire_resample(const float* in, const int from[3], flo
     const size_t Nin = static_cast<size_t>(from[0]) * from[1] * from[2];
     const size_t Nout = static_cast<size_t>(to[0]) * to[1] * to[2];
     const int n3h = from[2] / 2 + 1, m3h = to[2] / 2 + 1;
-    const size_t Min = static_cast<size_t>(from[0]) * from[1] * n3h;
     const size_t Mout = static_cast<size_t>(to[0]) * to[1] * m3h;
     if (Nin >= (1ull << 31) || Nout >= (1ull << 31)) return CLAIRE_ETOOLARGE;
     cudaStream_t st = static_cast<cudaStream_t>(stream);
@@ -81,37 +151,21 @@ extern "C" claire_status claire_resample(const float* in, const int from[3], flo
                 in + c * Nin, from[0], from[1], from[2], out + c * Nout, to[0], to[1], to[2]);
         return cudaGetLastError() == cudaSuccess ? CLAIRE_OK : CLAIRE_ECUDA;
     }
-    cufftComplex* X = nullptr;
-    cufftComplex* Y = nullptr;
-    cufftHandle fwd = 0, inv = 0;
-    claire_status status = CLAIRE_OK;
-    if (cudaMalloc(&X, Min * sizeof(cufftComplex)) != cudaSuccess ||
-        cudaMalloc(&Y, Mout * sizeof(cufftComplex)) != cudaSuccess) {
-        status = CLAIRE_ENOMEM;
-    } else if (cufftPlan3d(&fwd, from[0], from[1], from[2], CUFFT_R2C) != CUFFT_SUCCESS ||
-               cufftPlan3d(&inv, to[0], to[1], to[2], CUFFT_C2R) != CUFFT_SUCCESS ||
-               cufftSetStream(fwd, st) != CUFFT_SUCCESS || cufftSetStream(inv, st) != CUFFT_SUCCESS) {
-        status = CLAIRE_ECUFFT;
-    } else {
-        const float s = static_cast<float>(1.0 / static_cast<double>(Nin));
-        for (int c = 0; c < ncomp && status == CLAIRE_OK; ++c) {
-            if (cufftExecR2C(fwd, const_cast<float*>(in) + c * Nin, X) != CUFFT_SUCCESS) {
-                status = CLAIRE_ECUFFT;
-                break;
-            }
-            k_copy_modes<<<static_cast<unsigned>((Mout + 255) / 256), 256, 0, st>>>(
-                X, from[0], from[1], n3h, from[2], Y, to[0], to[1], m3h, to[2], s);
-            if (cudaGetLastError() != cudaSuccess) {
-                status = CLAIRE_ECUDA;
-                break;
-            }
-            if (cufftExecC2R(inv, Y, out + c * Nout) != CUFFT_SUCCESS) status = CLAIRE_ECUFFT;
-        }
-        if (status == CLAIRE_OK && cudaStreamSynchronize(st) != cudaSuccess) status = CLAIRE_ECUDA;
+    std::lock_guard<std::mutex> lock(g_plan_mu);
+    PlanEntry* e = nullptr;
+    const claire_status status = plan_for(from, to, &e);
+    if (status != CLAIRE_OK) return status;
+    if (cufftSetStream(e->fwd, st) != CUFFT_SUCCESS || cufftSetStream(e->inv, st) != CUFFT_SUCCESS)
+        return CLAIRE_ECUFFT;
+    const float s = static_cast<float>(1.0 / static_cast<double>(Nin));
+    for (int c = 0; c < ncomp; ++c) {
+        if (cufftExecR2C(e->fwd, const_cast<float*>(in) + c * Nin, e->X) != CUFFT_SUCCESS) return CLAIRE_ECUFFT;
+        k_copy_modes<<<static_cast<unsigned>((Mout + 255) / 256), 256, 0, st>>>(
+            e->X, from[0], from[1], n3h, from[2], e->Y, to[0], to[1], m3h, to[2], s);
+        if (cudaGetLastError() != cudaSuccess) return CLAIRE_ECUDA;
+        if (cufftExecC2R(e->inv, e->Y, out + c * Nout) != CUFFT_SUCCESS) return CLAIRE_ECUFFT;
     }
-    if (fwd) cufftDestroy(fwd);
-    if (inv) cufftDestroy(inv);
-    if (X) cudaFree(X);
-    if (Y) cudaFree(Y);
-    return status;
+    // the cached spectra are reused by the next call (possibly on another stream)
+    if (cudaStreamSynchronize(st) != cudaSuccess) return CLAIRE_ECUDA;
+    return CLAIRE_OK;
 }

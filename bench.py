@@ -60,6 +60,11 @@ def parse_args():
                     help="time to tolerance at --n: plain FP32 from v=0 vs FP16 storage + learned warm start "
                          "(network trained at n/2 on pairs the method generates)")
     ap.add_argument("--ws-steps", type=int, default=2000, help="training steps of the warm-start network")
+    ap.add_argument("--large-report", action="store_true",
+                    help="largest single-GPU case (--large-n, default 1024): FP32 from v=0 vs FP16 storage + "
+                         "learned warm start, both without stored state gradients; Dice on 3 labels; the same "
+                         "registration on images sampled to 256^3 and 512^3; sampled oracle parity")
+    ap.add_argument("--large-n", type=int, default=1024)
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -575,8 +580,405 @@ def run_warmstart_report(args):
     print(json.dumps(out))
 
 
+def run_large_report(args):
+    """Largest single-GPU registration.  Workload: three nested spheres with a
+    blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
+    band-limited velocity |k| <= 8, max|v| = 1 (drawn at 64^3, prolonged
+    spectrally) to give the reference; labels follow the same velocity
+    (indicator transport, threshold 1/2).  nt = 4, tricubic, beta_v = 1e-2,
+    beta_w = 1e-4, gtol 5e-2 of |g(v=0)|.  Both solves keep no stored state
+    gradients (lowmem).  Memory is the device memory in use (cudaMemGetInfo)
+    after each context is created.  Oracle parity at n^3 is checked on 10^6
+    sampled points of one backtrace and one interpolation (FP64)."""
+    import gc
+    import torch
+    import oracle
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth, net, warmstart
+    n = args.large_n
+    grid = (n, n, n)
+    N = n ** 3
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "%d^3 nested spheres + blob texture (3 labels), band-limited v* |k|<=8 max|v|=1, nt=4, "
+                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|" % (n, args.beta)}
+
+    def used_gb():
+        free, total = torch.cuda.mem_get_info()
+        return (total - free) / 1e9
+
+    def flush():
+        gc.collect()
+        torch.cuda.empty_cache()
+
+    t0 = time.perf_counter()
+    m0, labels = synth.sphere_template(grid, seed=0)
+    v64 = synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=1.0).astype(np.float32)
+    out["generate_s"] = time.perf_counter() - t0
+    # warm-start network, trained at 128^3 on method-generated pairs (sphere and blob families)
+    t0 = time.perf_counter()
+    src = warmstart.PairSource(128, n_templates=24, n_velocities=48, kmax=(4, 8), vmax=(0.3, 1.2), noise=0.0,
+                               seed=1, families=("label", "blob"))
+    u = net.UNet(seed=0, stream=st)
+    hist = warmstart.train(u, src, steps=args.ws_steps, batch=4, lr=1e-3, lr_final=1e-4, log_every=0)
+    src.ctx.close()
+    del src
+    flush()
+    out["training_s"] = time.perf_counter() - t0
+
+    # ---- FP16 + lowmem context: reference image and labels, learned run, sampled
+    # oracle parity, registrations of sampled images; device tensors are kept
+    # few because the context takes most of the memory
+    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                         storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200)
+    out["fp16_lowmem_device_gb"] = used_gb()
+    vstar = torch.empty((3,) + grid, device=dev)
+    claire.claire_resample(torch.from_numpy(v64).to(dev), (64, 64, 64), vstar, grid, 3, claire.RESAMPLE_SPECTRAL,
+                           st)
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.empty(grid, device=dev)
+    ctx.transport(vstar, m0_d, m1_d)
+    m1 = m1_d.cpu().numpy()
+
+    def warped_labels(v):
+        """Labels of m0 carried by v: transported indicators, threshold 1/2."""
+        buf = torch.empty(grid, device=dev)
+        tmp = torch.empty(grid, device=dev)
+        res = []
+        for k in (1, 2, 3):
+            buf.copy_(torch.from_numpy((labels == k).astype(np.float32)))
+            ctx.transport(v, buf, tmp)
+            res.append(tmp.cpu().numpy() > 0.5)
+        del buf, tmp
+        flush()
+        return res
+
+    ref = warped_labels(vstar)
+
+    def dice(lab):
+        return [float(2.0 * np.count_nonzero(a & b) / max(1, np.count_nonzero(a) + np.count_nonzero(b)))
+                for a, b in zip(lab, ref)]
+
+    out["dice_before"] = dice([labels == k for k in (1, 2, 3)])
+    ctx.set_images(m0_d, m1_d)   # the context keeps its own (FP16) copies
+    del vstar, m1_d
+    flush()
+
+    def sampled(nc):
+        """Images sampled by nearest neighbour to nc^3 (every (n/nc)-th node), on the device."""
+        r = n // nc
+        return (torch.from_numpy(np.ascontiguousarray(m0[::r, ::r, ::r])).to(dev),
+                torch.from_numpy(np.ascontiguousarray(m1[::r, ::r, ::r])).to(dev))
+
+    runs = {}
+    # learned warm start + FP16 storage
+    v = torch.zeros((3,) + grid, device=dev)
+    g = torch.empty((3,) + grid, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.gradient(v, g)
+    g0 = math.sqrt(claire.claire_dot(ctx.handle, g, g, 3 * N))
+    del g
+    a0, a1 = sampled(128)
+    vc = u.forward(a0, a1)
+    claire.claire_resample(vc[0], (128,) * 3, v, grid, 3, claire.RESAMPLE_SPECTRAL, st)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    _, mis_guess = ctx.objective(v)
+    flush()
+    ctx.set_opts(g0_ref=g0)
+    torch.cuda.synchronize()
+    stt, rep = ctx.register(v)
+    torch.cuda.synchronize()
+    runs["fp16_learned"] = {"time_to_tol_s": time.perf_counter() - t0, "predict_and_g0_s": t_pred,
+                            "status": rep["status"], "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                            "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
+                            "detj_max": rep["detj_max"], "cfl": rep["cfl"], "mismatch_at_guess": mis_guess,
+                            "peak_device_gb": used_gb()}
+    ctx.set_opts(g0_ref=0.0)
+    runs["fp16_learned"]["dice"] = dice(warped_labels(v))
+    # sampled oracle parity of one backtrace and one interpolation at n^3
+    d = torch.empty((3,) + grid, device=dev)
+    ctx.backtrace(v, d, 1)
+    m0_d = torch.from_numpy(m0).to(dev)
+    mo = torch.empty(grid, device=dev)
+    ctx.interp(m0_d, d, mo)
+    rng = np.random.default_rng(0)
+    S = 1000000
+    idx = torch.from_numpy(rng.integers(0, N, size=S)).to(dev)
+    d_s = d.view(3, -1)[:, idx].double().cpu().numpy()
+    out_s = mo.view(-1)[idx].double().cpu().numpy()
+    v_s = v.view(3, -1)[:, idx].double().cpu().numpy()
+    vh = v.cpu().numpy()
+    del d, mo, m0_d, v
+    flush()
+    ii = idx.cpu().numpy()
+    x = np.stack([ii // (n * n), (ii // n) % n, ii % n]).astype(np.float64)
+    h = 2.0 * math.pi / n
+    dt = 0.25
+    u0 = v_s / h
+    yp = x - dt * u0
+    U = np.stack([oracle.interp_points(vh[c].astype(np.float64), yp, 3) for c in range(3)]) / h
+    d_ref = -0.5 * dt * (u0 + U)
+    m_ref = oracle.interp_points(m0.astype(np.float64), x + d_s, 3)
+    del vh
+    out["sampled_parity"] = {"points": S, "velocity": "the learned run's result",
+                             "backtrace_rel_linf": float(np.max(np.abs(d_s - d_ref)) / np.max(np.abs(d_ref))),
+                             "interp_rel_linf": float(np.max(np.abs(out_s - m_ref)) / np.max(np.abs(m_ref)))}
+    # the same registration on images sampled to 256^3 and 512^3, velocity prolonged back
+    for nc in (256, 512):
+        if nc >= n:
+            continue
+        g_c = (nc,) * 3
+        c_ctx = claire.Context(g_c, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                               lowmem=1)
+        a0, a1 = sampled(nc)
+        c_ctx.set_images(a0, a1)
+        vc = torch.zeros((3,) + g_c, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = c_ctx.register(vc)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        c_ctx.close()
+        del c_ctx, a0, a1
+        flush()
+        vf = torch.empty((3,) + grid, device=dev)
+        claire.claire_resample(vc, g_c, vf, grid, 3, claire.RESAMPLE_SPECTRAL, st)
+        _, mis_f = ctx.objective(vf)
+        runs["fp32_at_%d" % nc] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"],
+                                   "pcg_iters": rep["pcg_iters_total"], "r_at_%d" % nc: rep["r"],
+                                   "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(warped_labels(vf))}
+        del vf, vc
+        flush()
+    _, mis_zero = ctx.objective(torch.zeros((3,) + grid, device=dev))
+    runs["fp16_learned"]["mismatch_at_zero"] = mis_zero
+    ctx.close()
+    del ctx
+    u._bufs = {}  # the network's activation buffers are not needed any more
+    flush()
+    # ---- plain FP32 (lowmem) from zero
+    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                         lowmem=1, wall_limit_s=1200)
+    out["fp32_lowmem_device_gb"] = used_gb()
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.from_numpy(m1).to(dev)
+    ctx.set_images(m0_d, m1_d)
+    del m0_d, m1_d
+    flush()
+    v = torch.zeros((3,) + grid, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stt, rep = ctx.register(v)
+    torch.cuda.synchronize()
+    runs["fp32_zero"] = {"time_to_tol_s": time.perf_counter() - t0, "status": rep["status"],
+                         "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"], "J": rep["J"],
+                         "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
+                         "detj_max": rep["detj_max"], "cfl": rep["cfl"], "peak_device_gb": used_gb()}
+    runs["fp32_zero"]["dice"] = dice(warped_labels(v))
+    del v
+    ctx.close()
+    flush()
+    out["runs"] = runs
+    a, b = runs["fp32_zero"], runs["fp16_learned"]
+    out["speedup_fp16_learned_vs_fp32_zero"] = a["time_to_tol_s"] / b["time_to_tol_s"]
+    out["oracle_J_rel_diff_learned_vs_plain"] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
+    out["oracle_mismatch_rel_diff_learned_vs_plain"] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / \
+        a["oracle_mismatch"]
+    print(json.dumps(out))
+
+
+def run_large_report(args):
+    """Largest single-GPU registration.  Workload: three nested spheres with a
+    blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
+    band-limited velocity |k| <= 8, max|v| = 1 (drawn at 64^3, prolonged
+    spectrally) to give the reference; labels follow the same velocity
+    (indicator transport, threshold 1/2).  nt = 4, tricubic, beta_v = 1e-2,
+    beta_w = 1e-4, gtol 5e-2 of |g(v=0)|.  Both solves keep no stored state
+    gradients (lowmem).  Memory is the device memory in use (cudaMemGetInfo)
+    after each context is created.  Oracle parity at n^3 is checked on 10^6
+    sampled points of one backtrace and one interpolation (FP64)."""
+    import gc
+    import torch
+    import oracle
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth, net, warmstart
+    n = args.large_n
+    grid = (n, n, n)
+    N = n ** 3
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream().cuda_stream
+    out = {"workload": "%d^3 nested spheres + blob texture (3 labels), band-limited v* |k|<=8 max|v|=1, nt=4, "
+                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|" % (n, args.beta)}
+
+    def used_gb():
+        free, total = torch.cuda.mem_get_info()
+        return (total - free) / 1e9
+
+    def flush():
+        gc.collect()
+        torch.cuda.empty_cache()
+
+    t0 = time.perf_counter()
+    m0, labels = synth.sphere_template(grid, seed=0)
+    v64 = synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=1.0).astype(np.float32)
+    out["generate_s"] = time.perf_counter() - t0
+    # warm-start network, trained at 128^3 on method-generated pairs (sphere and blob families)
+    t0 = time.perf_counter()
+    src = warmstart.PairSource(128, n_templates=24, n_velocities=48, kmax=(4, 8), vmax=(0.3, 1.2), noise=0.0,
+                               seed=1, families=("label", "blob"))
+    u = net.UNet(seed=0, stream=st)
+    hist = warmstart.train(u, src, steps=args.ws_steps, batch=4, lr=1e-3, lr_final=1e-4, log_every=0)
+    src.ctx.close()
+    del src
+    flush()
+    out["training_s"] = time.perf_counter() - t0
+
+    # ---- FP16 + lowmem context: reference image, labels, downsampled runs, learned run
+    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                         storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200)
+    out["fp16_lowmem_device_gb"] = used_gb()
+    vstar = torch.empty((3,) + grid, device=dev)
+    claire.claire_resample(torch.from_numpy(v64).to(dev), (64, 64, 64), vstar, grid, 3, claire.RESAMPLE_SPECTRAL,
+                           st)
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.empty(grid, device=dev)
+    ctx.transport(vstar, m0_d, m1_d)
+    m1 = m1_d.cpu().numpy()
+    buf = torch.empty(grid, device=dev)
+    tmp = torch.empty(grid, device=dev)
+
+    def warped_labels(v):
+        """Labels of m0 carried by v: transported indicators, threshold 1/2."""
+        res = []
+        for k in (1, 2, 3):
+            buf.copy_(torch.from_numpy((labels == k).astype(np.float32)))
+            ctx.transport(v, buf, tmp)
+            res.append(tmp.cpu().numpy() > 0.5)
+        return res
+
+    ref = warped_labels(vstar)
+    del vstar
+    flush()
+
+    def dice(lab):
+        return [float(2.0 * np.count_nonzero(a & b) / max(1, np.count_nonzero(a) + np.count_nonzero(b)))
+                for a, b in zip(lab, ref)]
+
+    out["dice_before"] = dice([labels == k for k in (1, 2, 3)])
+    runs = {}
+    # the same registration on images sampled to 256^3 and 512^3, velocity prolonged back
+    for nc in (256, 512):
+        if nc >= n:
+            continue
+        g_c = (nc,) * 3
+        c_ctx = claire.Context(g_c, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50)
+        a0 = torch.empty(g_c, device=dev)
+        a1 = torch.empty(g_c, device=dev)
+        claire.claire_resample(m0_d, grid, a0, g_c, 1, claire.RESAMPLE_NEAREST, st)
+        claire.claire_resample(m1_d, grid, a1, g_c, 1, claire.RESAMPLE_NEAREST, st)
+        c_ctx.set_images(a0, a1)
+        vc = torch.zeros((3,) + g_c, device=dev)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        _, rep = c_ctx.register(vc)
+        torch.cuda.synchronize()
+        secs = time.perf_counter() - t0
+        c_ctx.close()
+        vf = torch.empty((3,) + grid, device=dev)
+        claire.claire_resample(vc, g_c, vf, grid, 3, claire.RESAMPLE_SPECTRAL, st)
+        ctx.set_images(m0_d, m1_d)
+        _, mis_f = ctx.objective(vf)
+        runs["fp32_at_%d" % nc] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"],
+                                   "pcg_iters": rep["pcg_iters_total"], "r_at_%d" % nc: rep["r"],
+                                   "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(warped_labels(vf))}
+        del vf, vc, a0, a1, c_ctx
+        flush()
+    # learned warm start + FP16 storage
+    ctx.set_images(m0_d, m1_d)
+    v = torch.zeros((3,) + grid, device=dev)
+    g = torch.empty((3,) + grid, device=dev)
+    ws = warmstart.WarmStart(u, 128)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    ctx.gradient(v, g)
+    g0 = math.sqrt(claire.claire_dot(ctx.handle, g, g, 3 * N))
+    del g
+    ws.predict(m0_d, m1_d, v)
+    torch.cuda.synchronize()
+    t_pred = time.perf_counter() - t0
+    _, mis_guess = ctx.objective(v)
+    _, mis_zero = ctx.objective(torch.zeros((3,) + grid, device=dev))
+    flush()
+    ctx.set_opts(g0_ref=g0)
+    torch.cuda.synchronize()
+    t1 = time.perf_counter()
+    stt, rep = ctx.register(v)
+    torch.cuda.synchronize()
+    runs["fp16_learned"] = {"time_to_tol_s": time.perf_counter() - t0, "predict_and_g0_s": t_pred,
+                            "status": rep["status"], "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                            "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
+                            "detj_max": rep["detj_max"], "cfl": rep["cfl"], "mismatch_at_guess": mis_guess,
+                            "mismatch_at_zero": mis_zero, "dice": dice(warped_labels(v)),
+                            "peak_device_gb": used_gb()}
+    del v
+    ctx.close()
+    del ctx
+    flush()
+    # ---- plain FP32 (lowmem) from zero
+    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                         lowmem=1, wall_limit_s=1200)
+    out["fp32_lowmem_device_gb"] = used_gb()
+    ctx.set_images(m0_d, m1_d)
+    v = torch.zeros((3,) + grid, device=dev)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    stt, rep = ctx.register(v)
+    torch.cuda.synchronize()
+    runs["fp32_zero"] = {"time_to_tol_s": time.perf_counter() - t0, "status": rep["status"],
+                         "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"], "J": rep["J"],
+                         "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
+                         "detj_max": rep["detj_max"], "cfl": rep["cfl"], "dice": dice(warped_labels(v)),
+                         "peak_device_gb": used_gb()}
+    # sampled oracle parity of one backtrace and one interpolation at n^3
+    d = torch.empty((3,) + grid, device=dev)
+    ctx.backtrace(v, d, 1)
+    ctx.interp(m0_d, d, buf)
+    rng = np.random.default_rng(0)
+    S = 1000000
+    idx = torch.from_numpy(rng.integers(0, N, size=S)).to(dev)
+    d_s = d.view(3, -1)[:, idx].double().cpu().numpy()
+    out_s = buf.view(-1)[idx].double().cpu().numpy()
+    v_s = v.view(3, -1)[:, idx].double().cpu().numpy()
+    vh = v.cpu().numpy()
+    del d
+    ctx.close()
+    flush()
+    ii = idx.cpu().numpy()
+    x = np.stack([ii // (n * n), (ii // n) % n, ii % n]).astype(np.float64)
+    h = 2.0 * math.pi / n
+    dt = 0.25
+    u0 = v_s / h
+    yp = x - dt * u0
+    U = np.stack([oracle.interp_points(vh[c].astype(np.float64), yp, 3) for c in range(3)]) / h
+    d_ref = -0.5 * dt * (u0 + U)
+    m_ref = oracle.interp_points(m0.astype(np.float64), x + d_s, 3)
+    out["sampled_parity"] = {"points": S,
+                             "backtrace_rel_linf": float(np.max(np.abs(d_s - d_ref)) / np.max(np.abs(d_ref))),
+                             "interp_rel_linf": float(np.max(np.abs(out_s - m_ref)) / np.max(np.abs(m_ref)))}
+    out["runs"] = runs
+    a, b = runs["fp32_zero"], runs["fp16_learned"]
+    out["speedup_fp16_learned_vs_fp32_zero"] = a["time_to_tol_s"] / b["time_to_tol_s"]
+    print(json.dumps(out))
+
+
 def main():
     args = parse_args()
+    if args.large_report:
+        run_large_report(args)
+        return
     if args.warmstart_report:
         run_warmstart_report(args)
         return

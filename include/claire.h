@@ -99,6 +99,10 @@ typedef struct claire_opts {
                             solve warm-started from a predicted velocity passes the norm of the
                             gradient at v = 0 so that it stops at the same absolute gradient as a
                             solve from zero.  Default 0 (use the initial guess's gradient). */
+    int lowmem;          /* 1 = do not store the gradients grad m^j of the states: the incremental
+                            sources and the gradient body compute them by FD8 where they are used
+                            (3 (nt+1) N fewer stored values, about 1.3x the time of those kernels);
+                            0 = store them once per linearisation (default).  Fixed at create. */
 } claire_opts;
 
 /* claire_opts.storage */

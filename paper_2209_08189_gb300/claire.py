@@ -44,7 +44,8 @@ class claire_opts(ctypes.Structure):
                 ("max_pcg", ctypes.c_int), ("pcg_rtol_max", ctypes.c_double),
                 ("pcg_fixed", ctypes.c_int), ("armijo_c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
-                ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double)]
+                ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double),
+                ("lowmem", ctypes.c_int)]
 
 
 class claire_report(ctypes.Structure):

@@ -71,6 +71,8 @@ struct claire_ctx {
     int device = 0, nsm = 0, red_blocks = 0;
     cufftHandle r2c = 0, c2r = 0;
     bool plans = false;
+    void* fft_work = nullptr;             // one work area shared by both plans
+    size_t fft_work_bytes = 0;
     std::string err;
 
     // workspace arena
@@ -83,10 +85,10 @@ struct claire_ctx {
     float *v = nullptr;                   // linearisation point
     float *dS = nullptr, *dA = nullptr;   // state / adjoint characteristics
     char *divv = nullptr, *divXp = nullptr;
-    char *m = nullptr, *gm = nullptr;     // (nt+1) N and (nt+1) 3N values
+    char *m = nullptr, *gm = nullptr;     // (nt+1) N states m^j, (nt+1) 3N gradients (null when lowmem)
     char *l0 = nullptr, *l1 = nullptr;    // rolling scalar fields (FP32-sized: transport uses them as FP32)
     char* tl = nullptr;                   // (nt+1) N: adjoint levels lambda^j / incremental sources f^j
-    float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr, *q = nullptr;
+    float *g = nullptr, *x = nullptr, *r = nullptr, *z = nullptr, *p = nullptr;
     cufftComplex* spec = nullptr;
     cufftComplex* phat = nullptr;         // PCG search direction in Fourier space
     cufftComplex* spec2 = nullptr;        // second transform buffer
@@ -126,6 +128,8 @@ struct claire_ctx {
             cufftDestroy(c2r);
             plans = false;
         }
+        if (fft_work) cudaFree(fft_work);
+        fft_work = nullptr;
         if (arena) cudaFree(arena);
         arena = nullptr;
         if (vjp_states) cudaFree(vjp_states);
@@ -208,6 +212,7 @@ void fill_defaults(claire_opts* o)
     o->timing = 0;
     o->storage = CLAIRE_STORAGE_F32;
     o->g0_ref = 0.0;
+    o->lowmem = 0;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -216,7 +221,7 @@ bool valid_opts(const claire_opts& o)
            (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
            o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
            o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
-           o.g0_ref >= 0;
+           o.g0_ref >= 0 && (o.lowmem == 0 || o.lowmem == 1);
 }
 
 // Layout of the workspace arena in floats (each region 256-byte aligned).
@@ -233,7 +238,7 @@ struct Layout {
     }
 };
 
-size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, size_t es, Layout* L)
+size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, size_t es, bool lowmem, Layout* L)
 {
     Layout tmp;
     Layout& l = L ? *L : tmp;
@@ -246,11 +251,11 @@ size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, size_t es, Layo
     l.add(S(N));                 // divv
     l.add(S(N));                 // divXp
     l.add(S((nt + 1) * N));      // m
-    l.add(S(3 * (nt + 1) * N));  // gm
+    l.add(lowmem ? 0 : S(3 * (nt + 1) * N));  // gm (not stored in low-memory mode)
     l.add(N);                    // l0 (FP32-sized)
     l.add(N);                    // l1 (FP32-sized)
     l.add(S((nt + 1) * N));      // tl
-    for (int i = 0; i < 6; ++i) l.add(3 * N);  // g x r z p q
+    for (int i = 0; i < 5; ++i) l.add(3 * N);  // g x r z p
     l.add(6 * M);             // spec (3 complex half-spectra)
     l.add(6 * M);             // phat
     l.add(6 * M);             // spec2
@@ -477,8 +482,9 @@ claire_status linearise(claire_ctx* c, const float* v, bool have_state = false)
         if (!have_state)
             for (int j = 0; j < c->nt; ++j)
                 CL_TRY(interp(c, at(c, c->m, j * N), c->dS, at(c, c->m, (j + 1) * N), c->sto));
-        for (int j = 0; j <= c->nt; ++j)
-            CL_TRY(fd8_grad(c, at(c, c->m, j * N), at(c, c->gm, 3 * j * N), c->sto));
+        if (c->gm)
+            for (int j = 0; j <= c->nt; ++j)
+                CL_TRY(fd8_grad(c, at(c, c->m, j * N), at(c, c->gm, 3 * j * N), c->sto));
     }
     return CLAIRE_OK;
 }
@@ -505,9 +511,15 @@ claire_status adjoint_and_body(claire_ctx* c, const void* a, const void* s, floa
         CL_LAUNCHED(c);
     }
     {
-        KTimer t(c, KK_POINTWISE, (4.0 * es * (nt + 1) + (accumulate ? 24.0 : 12.0)) * N, 0);
-        launch_body(c->grid, c->tl, c->gm, nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt),
-                    accumulate ? 1 : 0, out, c->sto, c->stream);
+        if (c->gm) {
+            KTimer t(c, KK_POINTWISE, (4.0 * es * (nt + 1) + (accumulate ? 24.0 : 12.0)) * N, 0);
+            launch_body(c->grid, c->tl, c->gm, nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt),
+                        accumulate ? 1 : 0, out, c->sto, c->stream);
+        } else {
+            KTimer t(c, KK_FD8, (2.0 * es * (nt + 1) + (accumulate ? 24.0 : 12.0)) * N, 0);
+            launch_body_fd(c->grid, c->tl, c->m, nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt),
+                           accumulate ? 1 : 0, out, c->sto, c->stream);
+        }
         CL_LAUNCHED(c);
     }
     return CLAIRE_OK;
@@ -556,8 +568,13 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
         char* a = c->l0;
         char* b = c->l1;
         {
-            KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es * (nt + 1)) * N, 0);
-            launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+            if (c->gm) {
+                KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es * (nt + 1)) * N, 0);
+                launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+            } else {
+                KTimer t(c, KK_FD8, (12.0 + 2.0 * es * (nt + 1)) * N, 0);
+                launch_inc_sources_fd(c->grid, vt, c->m, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+            }
             CL_LAUNCHED(c);
         }
         for (int j = 0; j + 1 < nt; ++j) {
@@ -821,7 +838,9 @@ claire_status claire_query_workspace(const int grid[3], int nt, const claire_opt
     const size_t M = (size_t)grid[0] * grid[1] * (grid[2] / 2 + 1);
     const int sto = opts ? opts->storage : 0;
     if (sto < 0 || sto > 2) return CLAIRE_EINVAL;
-    *bytes = layout_floats(N, M, nt, 152 * 8, storage_bytes(static_cast<Storage>(sto)), nullptr) * sizeof(float);
+    const bool lowmem = opts ? opts->lowmem != 0 : false;
+    *bytes = layout_floats(N, M, nt, 152 * 8, storage_bytes(static_cast<Storage>(sto)), lowmem, nullptr) *
+             sizeof(float);
     return CLAIRE_OK;
 }
 
@@ -883,7 +902,7 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     Layout L;
     c->sto = static_cast<Storage>(o.storage);
     c->es = storage_bytes(c->sto);
-    size_t floats = layout_floats(c->N, c->M, nt, c->red_blocks, c->es, &L);
+    size_t floats = layout_floats(c->N, c->M, nt, c->red_blocks, c->es, o.lowmem != 0, &L);
     cudaError_t e = cudaMalloc(&c->arena, floats * sizeof(float));
     if (e != cudaSuccess) {
         cudaGetLastError();
@@ -901,7 +920,8 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->divv = reinterpret_cast<char*>(base + L.off[k++]);
     c->divXp = reinterpret_cast<char*>(base + L.off[k++]);
     c->m = reinterpret_cast<char*>(base + L.off[k++]);
-    c->gm = reinterpret_cast<char*>(base + L.off[k++]);
+    c->gm = o.lowmem ? nullptr : reinterpret_cast<char*>(base + L.off[k]);
+    ++k;
     c->l0 = reinterpret_cast<char*>(base + L.off[k++]);
     c->l1 = reinterpret_cast<char*>(base + L.off[k++]);
     c->tl = reinterpret_cast<char*>(base + L.off[k++]);
@@ -910,7 +930,6 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->r = base + L.off[k++];
     c->z = base + L.off[k++];
     c->p = base + L.off[k++];
-    c->q = base + L.off[k++];
     c->spec = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->phat = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->spec2 = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
@@ -927,15 +946,35 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
         c->hres = nullptr;
         return bail(CLAIRE_ENOMEM);
     }
+    // both plans share one work area (they never run concurrently: one stream)
     int nn[3] = {grid[0], grid[1], grid[2]};
-    cufftResult fr = cufftPlanMany(&c->r2c, 3, nn, nullptr, 1, (int)c->N, nullptr, 1, (int)c->M,
-                                   CUFFT_R2C, 3);
+    size_t ws_r2c = 0, ws_c2r = 0;
+    cufftResult fr = cufftCreate(&c->r2c);
     if (fr == CUFFT_SUCCESS) {
-        fr = cufftPlanMany(&c->c2r, 3, nn, nullptr, 1, (int)c->M, nullptr, 1, (int)c->N, CUFFT_C2R, 3);
+        fr = cufftCreate(&c->c2r);
         if (fr != CUFFT_SUCCESS) cufftDestroy(c->r2c);
     }
-    if (fr != CUFFT_SUCCESS) return bail(fr == CUFFT_ALLOC_FAILED ? CLAIRE_ENOMEM : CLAIRE_ECUFFT);
+    if (fr != CUFFT_SUCCESS) return bail(CLAIRE_ECUFFT);
     c->plans = true;
+    fr = cufftSetAutoAllocation(c->r2c, 0);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetAutoAllocation(c->c2r, 0);
+    if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(c->r2c, 3, nn, nullptr, 1, (int)c->N, nullptr, 1, (int)c->M, CUFFT_R2C, 3,
+                               &ws_r2c);
+    if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(c->c2r, 3, nn, nullptr, 1, (int)c->M, nullptr, 1, (int)c->N, CUFFT_C2R, 3,
+                               &ws_c2r);
+    if (fr != CUFFT_SUCCESS) return bail(fr == CUFFT_ALLOC_FAILED ? CLAIRE_ENOMEM : CLAIRE_ECUFFT);
+    const size_t ws = std::max<size_t>(std::max(ws_r2c, ws_c2r), 256);
+    if (cudaMalloc(&c->fft_work, ws) != cudaSuccess) {
+        cudaGetLastError();
+        c->fft_work = nullptr;
+        return bail(CLAIRE_ENOMEM);
+    }
+    c->fft_work_bytes = ws;
+    fr = cufftSetWorkArea(c->r2c, c->fft_work);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetWorkArea(c->c2r, c->fft_work);
+    if (fr != CUFFT_SUCCESS) return bail(CLAIRE_ECUFFT);
     st = claire_set_stream(c, nullptr);
     if (st != CLAIRE_OK) return bail(st);
     *out = c;
@@ -1014,8 +1053,8 @@ claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt)
     if (!vt || !Hvt) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dvt;
     CL_TRY(device_input(c, vt, 3 * c->N, c->p, &dvt));
-    CL_TRY(matvec(c, dvt, c->q));
-    CL_TRY(copy_out(c, Hvt, c->q, 3 * c->N));
+    CL_TRY(matvec(c, dvt, c->r));
+    CL_TRY(copy_out(c, Hvt, c->r, 3 * c->N));
     collect_timing(c);
     return CLAIRE_OK;
 }
@@ -1026,8 +1065,8 @@ claire_status claire_precond(claire_ctx* c, const float* r, float* z)
     if (!r || !z) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dr;
     CL_TRY(device_input(c, r, 3 * c->N, c->p, &dr));
-    CL_TRY(precond(c, dr, c->q));
-    CL_TRY(copy_out(c, z, c->q, 3 * c->N));
+    CL_TRY(precond(c, dr, c->r));
+    CL_TRY(copy_out(c, z, c->r, 3 * c->N));
     collect_timing(c);
     return CLAIRE_OK;
 }
@@ -1275,7 +1314,7 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
     if (gm0) CL_TRY(copy_out(c, gm0, mb, N));
     if (gv) {
         float* ub = c->p;
-        float* Ub = c->q;
+        float* Ub = reinterpret_cast<float*>(c->spec);  // 6 M >= 3 N floats, unused here
         {
             KTimer t(c, KK_VJP_GRAD, 48.0 * N, 3.0 * N);
             launch_predictor_terms(c->grid, c->o.interp, dv, static_cast<float>(c->dt), dbar, ub, Ub, c->stream);
@@ -1296,7 +1335,7 @@ claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
     if (!c) return CLAIRE_EINVAL;
     if (!v || !lo || !hi) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dv;
-    CL_TRY(device_input(c, v, 3 * c->N, c->q, &dv));
+    CL_TRY(device_input(c, v, 3 * c->N, c->x, &dv));
     CL_TRY(detj_of(c, dv, lo, hi));
     collect_timing(c);
     return CLAIRE_OK;
@@ -1416,7 +1455,8 @@ claire_status claire_set_opts(claire_ctx* c, const claire_opts* opts)
 {
     if (!c || !opts) return CLAIRE_EINVAL;
     if (!valid_opts(*opts)) return fail(c, CLAIRE_EINVAL, "invalid options");
-    if (opts->storage != c->o.storage) return fail(c, CLAIRE_EINVAL, "storage is fixed at claire_create");
+    if (opts->storage != c->o.storage || opts->lowmem != c->o.lowmem)
+        return fail(c, CLAIRE_EINVAL, "storage and lowmem are fixed at claire_create");
     collect_timing(c);
     c->o = *opts;
     c->rp.beta_w = static_cast<float>(opts->beta_w);

@@ -83,6 +83,11 @@ void launch_adj_step(const Grid& g, int order, const void* lam_next, const float
 void launch_inc_sources(const Grid& g, const float* vt, const void* gm, int nt, float coef0, void* q0,
                         void* F, Storage sto, cudaStream_t st);
 // out (+)= sum_j w_j lam^j grad m^j (lam slots j N, trapezoid weights w_end / w_mid).
+// as launch_inc_sources / launch_body, with grad m^j computed from the stored states m (FD8)
+void launch_inc_sources_fd(const Grid& g, const float* vt, const void* m, int nt, float coef0, void* q0, void* F,
+                           Storage sto, cudaStream_t st);
+void launch_body_fd(const Grid& g, const void* lam, const void* m, int nt, float w_end, float w_mid, int accumulate,
+                    float* out, Storage sto, cudaStream_t st);
 void launch_body(const Grid& g, const void* lam, const void* gm, int nt, float w_end, float w_mid,
                  int accumulate, float* out, Storage sto, cudaStream_t st);
 // q = q_prev(X) + coef F;   lam = -(q_prev(X) + coef F)  (F may alias lam)

@@ -46,6 +46,97 @@ __global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __r
 // Sources of the incremental state for every time level at once:
 // f^j = -vt . grad m^j; q0 = coef0 f^0 starts the Heun recursion and
 // f^1..f^nt go to F (slot j at F + j N).  S: storage of grad m, q0, F.
+// ---------------------------------------------------------------------------
+// 8th-order central finite differences
+// ---------------------------------------------------------------------------
+
+template <class S = float>
+__device__ __forceinline__ float fd8_axis(const S* __restrict__ f, uint32_t p, int idx, int n,
+                                          int stride)
+{
+    // c_s = 4/5, -1/5, 4/105, -1/280 for s = 1..4 (standard 8th-order stencil)
+    const float c1 = 0.8f, c2 = -0.2f, c3 = 0.0380952380952381f, c4 = -0.003571428571428571f;
+    float acc = 0.0f;
+    const float cs[4] = {c1, c2, c3, c4};
+    const long base = static_cast<long>(p) - static_cast<long>(idx) * stride;
+#pragma unroll
+    for (int s = 1; s <= 4; ++s) {
+        int ip = idx + s;
+        ip = ip >= n ? ip - n : ip;
+        int im = idx - s;
+        im = im < 0 ? im + n : im;
+        acc = fmaf(cs[s - 1], ldf<S>(f + base + static_cast<long>(ip) * stride) -
+                                  ldf<S>(f + base + static_cast<long>(im) * stride),
+                   acc);
+    }
+    return acc;
+}
+
+// FD8 gradient of f at node p = (i, j, k), physical units
+template <class S>
+__device__ __forceinline__ void fd8_grad_at(const Grid& g, const S* __restrict__ f, uint32_t p, int i, int j,
+                                            int k, float& g0, float& g1, float& g2)
+{
+    g0 = fd8_axis<S>(f, p, i, g.n1, g.n23) * g.ih1;
+    g1 = fd8_axis<S>(f, p, j, g.n2, g.n3) * g.ih2;
+    g2 = fd8_axis<S>(f, p, k, g.n3, 1) * g.ih3;
+}
+
+// Incremental-state sources with grad m^j computed here (FD8 of the stored
+// states, no stored gradients): f^j = -vt . grad m^j; q0 = coef0 f^0,
+// F[j] = f^j for j = 1..nt.
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_inc_sources_fd(Grid g, const float* __restrict__ vt,
+                                                              const S* __restrict__ m, int nt, float coef0,
+                                                              S* __restrict__ q0, S* __restrict__ F)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    const float v0 = __ldg(vt + p), v1 = __ldg(vt + N + p), v2 = __ldg(vt + 2 * N + p);
+    for (int l = 0; l <= nt; ++l) {
+        float g0, g1, g2;
+        fd8_grad_at<S>(g, m + l * N, p, i, j, k, g0, g1, g2);
+        const float f = -(v0 * g0 + v1 * g1 + v2 * g2);
+        if (l == 0)
+            stf<S>(q0 + p, coef0 * f);
+        else
+            stf<S>(F + l * N + p, f);
+    }
+}
+
+// Gradient body with grad m^j computed here: out_c (+)= sum_j w_j lambda^j grad_c m^j.
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_body_fd(Grid g, const S* __restrict__ lam, const S* __restrict__ m,
+                                                       int nt, float w_end, float w_mid, int accumulate,
+                                                       float* __restrict__ out)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    int i, j, k;
+    coords_of(g, p, i, j, k);
+    const size_t N = g.N;
+    float b0 = 0.0f, b1 = 0.0f, b2 = 0.0f;
+    for (int l = 0; l <= nt; ++l) {
+        const float wl = (l == 0 || l == nt ? w_end : w_mid) * ldf<S>(lam + l * N + p);
+        float g0, g1, g2;
+        fd8_grad_at<S>(g, m + l * N, p, i, j, k, g0, g1, g2);
+        b0 = fmaf(wl, g0, b0);
+        b1 = fmaf(wl, g1, b1);
+        b2 = fmaf(wl, g2, b2);
+    }
+    if (accumulate) {
+        b0 += out[p];
+        b1 += out[N + p];
+        b2 += out[2 * N + p];
+    }
+    out[p] = b0;
+    out[N + p] = b1;
+    out[2 * N + p] = b2;
+}
+
 template <class S>
 __global__ void __launch_bounds__(kThreads) k_inc_sources(Grid g, const float* __restrict__ vt,
                                                            const S* __restrict__ gm, int nt,
@@ -131,32 +222,6 @@ __global__ void __launch_bounds__(kThreads) k_map_step(Grid g, const float* __re
     u[p] = fmaf(d1, g.h1, r[0]);
     u[N + p] = fmaf(d2, g.h2, r[1]);
     u[2 * N + p] = fmaf(d3, g.h3, r[2]);
-}
-
-// ---------------------------------------------------------------------------
-// 8th-order central finite differences
-// ---------------------------------------------------------------------------
-
-template <class S = float>
-__device__ __forceinline__ float fd8_axis(const S* __restrict__ f, uint32_t p, int idx, int n,
-                                          int stride)
-{
-    // c_s = 4/5, -1/5, 4/105, -1/280 for s = 1..4 (standard 8th-order stencil)
-    const float c1 = 0.8f, c2 = -0.2f, c3 = 0.0380952380952381f, c4 = -0.003571428571428571f;
-    float acc = 0.0f;
-    const float cs[4] = {c1, c2, c3, c4};
-    const long base = static_cast<long>(p) - static_cast<long>(idx) * stride;
-#pragma unroll
-    for (int s = 1; s <= 4; ++s) {
-        int ip = idx + s;
-        ip = ip >= n ? ip - n : ip;
-        int im = idx - s;
-        im = im < 0 ? im + n : im;
-        acc = fmaf(cs[s - 1], ldf<S>(f + base + static_cast<long>(ip) * stride) -
-                                  ldf<S>(f + base + static_cast<long>(im) * stride),
-                   acc);
-    }
-    return acc;
 }
 
 template <class S>
@@ -272,6 +337,25 @@ void launch_inc_sources(const Grid& g, const float* vt, const void* gm, int nt, 
     CLAIRE_STORAGE_DISPATCH(sto, {
         k_inc_sources<SType><<<blocks_for(g.N), kThreads, 0, st>>>(
             g, vt, static_cast<const SType*>(gm), nt, coef0, static_cast<SType*>(q0), static_cast<SType*>(F));
+    });
+}
+
+void launch_inc_sources_fd(const Grid& g, const float* vt, const void* m, int nt, float coef0, void* q0, void* F,
+                           Storage sto, cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_inc_sources_fd<SType><<<blocks_for(g.N), kThreads, 0, st>>>(
+            g, vt, static_cast<const SType*>(m), nt, coef0, static_cast<SType*>(q0), static_cast<SType*>(F));
+    });
+}
+
+void launch_body_fd(const Grid& g, const void* lam, const void* m, int nt, float w_end, float w_mid, int accumulate,
+                    float* out, Storage sto, cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_body_fd<SType><<<blocks_for(g.N), kThreads, 0, st>>>(g, static_cast<const SType*>(lam),
+                                                              static_cast<const SType*>(m), nt, w_end, w_mid,
+                                                              accumulate, out);
     });
 }
 

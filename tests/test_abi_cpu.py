@@ -72,9 +72,14 @@ def test_query_workspace_scales_with_grid_and_nt(claire):
     b128 = claire.claire_query_workspace((128, 128, 128), 4)
     assert 7.5 < b128 / b64 < 8.5
     assert claire.claire_query_workspace((64, 64, 64), 8) > b64
-    # about 53 + 4 (nt+1) float fields per point (fields, nt+1 states and
-    # gradients, adjoint levels, five Fourier-space buffers)
-    assert 60 * 4 * 64 ** 3 < b64 < 85 * 4 * 64 ** 3
+    # about 35 + 5 (nt+1) float fields per point (images, velocity, two
+    # characteristics, nt+1 states, their gradients and adjoint levels, five
+    # real and five Fourier-space vector buffers)
+    assert 65 * 4 * 64 ** 3 < b64 < 75 * 4 * 64 ** 3
+    # without stored state gradients: 3 (nt+1) = 15 fields fewer
+    o = claire.claire_default_opts()
+    o.lowmem = 1
+    assert abs(b64 - claire.claire_query_workspace((64, 64, 64), 4, o) - 15 * 4 * 64 ** 3) < 64 * 1024
 
 
 def test_reduced_storage_shrinks_workspace(claire):
@@ -86,7 +91,8 @@ def test_reduced_storage_shrinks_workspace(claire):
     b32 = claire.claire_query_workspace((64, 64, 64), 4, o32)
     b16 = claire.claire_query_workspace((64, 64, 64), 4, o16)
     assert claire.claire_query_workspace((64, 64, 64), 4, ob) == b16
-    # 2 + 2 + 5 + 15 + 5 = 29 scalar fields per point drop from 4 to 2 bytes
+    # 2 + 2 + 5 + 15 + 5 = 29 scalar fields per point (images, div v and its
+    # value at X+, states, their gradients, adjoint levels) drop from 4 to 2 bytes
     assert abs((b32 - b16) - 29 * 2 * 64 ** 3) < 64 * 1024
     o16.storage = 3
     with pytest.raises(claire.ClaireError):

@@ -223,11 +223,14 @@ def test_transport_parity(env, n, order):
 
 @pytest.mark.parametrize("n", SHAPES)
 @pytest.mark.parametrize("grad_form", [0, 1])
-def test_gradient_matvec_precond_parity(env, n, grad_form):
+@pytest.mark.parametrize("lowmem", [0, 1])
+def test_gradient_matvec_precond_parity(env, n, grad_form, lowmem):
+    """lowmem = 1: the state gradients are computed by FD8 where they are used."""
     torch, claire = env
     m0, m1, vs, v, p = _problem(n)
     p.grad_form = grad_form
-    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, grad_form=grad_form)
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, grad_form=grad_form,
+                   lowmem=lowmem)
     ctx.set_images(dev(torch, m0), dev(torch, m1))
     g = torch.empty((3,) + n, device="cuda")
     J = ctx.gradient(dev(torch, v), g)

@@ -65,6 +65,9 @@ def parse_args():
                          "learned warm start, both without stored state gradients; Dice on 3 labels; the same "
                          "registration on images sampled to 256^3 and 512^3; sampled oracle parity")
     ap.add_argument("--large-n", type=int, default=1024)
+    ap.add_argument("--net-report", action="store_true",
+                    help="timing of the warm-start network kernels (every conv shape of the U-Net at 128^3, "
+                         "batch 4), one training step, and the SL reverse-mode transport at 256^3")
     ap.add_argument("--no-e2e", action="store_true")
     return ap.parse_args()
 
@@ -100,7 +103,8 @@ def measured_peaks():
 
 def kernel_source_hash():
     h = hashlib.sha1()
-    for f in ("sl_kernels.cu", "common.cuh", "vec_kernels.cu"):
+    # the files that define and launch the SL gather kernels
+    for f in ("sl_tiled.cuh", "common.cuh", "storage.cuh", "sl_kernels.cu"):
         with open(os.path.join(ROOT, "paper_2209_08189_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -580,6 +584,84 @@ def run_warmstart_report(args):
     print(json.dumps(out))
 
 
+def run_net_report(args):
+    """CUDA-event timing (mean of 10 after a warm-up) of the network kernels
+    and the reverse-mode transport.  Convolution TFLOP/s count 2 * voxels *
+    27 * Cin * Cout flops; bytes count each input and output activation once
+    (BF16).  Peak for the fraction: the measured dense BF16 rate."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, net, warmstart, synth
+    st = torch.cuda.current_stream().cuda_stream
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as f:
+            peaks = json.load(f)
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+
+    def timeit(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {"bf16_peak_tflops": bf16_peak, "conv": {}}
+    B, n = 4, 128
+    for lvl, ci, co in [(0, 16, 16), (0, 48, 16), (1, 16, 32), (1, 32, 32), (1, 96, 32), (2, 32, 64), (2, 64, 64),
+                        (2, 192, 64), (3, 64, 128), (3, 128, 128)]:
+        D = n >> lvl
+        x = (torch.randn((B, D, D, D, ci), device="cuda")).to(torch.bfloat16)
+        w = (torch.randn((co, 27, ci), device="cuda") / math.sqrt(27 * ci)).to(torch.bfloat16)
+        y = torch.empty((B, D, D, D, co), device="cuda", dtype=torch.bfloat16)
+        X, Y = net.Act(x, 0, ci), net.Act(y, 0, co)
+        t = timeit(lambda: net.conv3d(X, w, None, Y, 0.1, 1, st))
+        chunks = net.wgrad_chunks(ci, co, (B, D, D, D))
+        part = torch.empty(chunks * co * 27 * ci, device="cuda")
+        pb = torch.empty(chunks * co, device="cuda")
+        dw = torch.empty((co, 27, ci), device="cuda")
+        db = torch.empty(co, device="cuda")
+        tw = timeit(lambda: net.conv3d_wgrad(X, Y, chunks, part, pb, dw, db, st))
+        P = B * D ** 3
+        fl = 2.0 * P * 27 * ci * co
+        out["conv"]["l%d_%dx%d" % (lvl, ci, co)] = {
+            "voxels": P, "fwd_ms": t, "fwd_tflops": fl / t / 1e9, "fwd_frac_bf16_peak": fl / t / 1e9 / bf16_peak,
+            "fwd_gbs": P * (ci + co) * 2 / t / 1e6, "wgrad_ms": tw, "wgrad_tflops": fl / tw / 1e9}
+        del x, w, y, part, pb, dw, db
+    src = warmstart.PairSource(128, n_templates=4, n_velocities=4, noise=0.0, seed=0)
+    u = net.UNet(seed=0, stream=st)
+    warmstart.train(u, src, steps=3, batch=4)
+    m0, m1, vs = src.batch(4)
+    out["unet_forward_ms"] = timeit(lambda: u.forward(m0, m1), 5)
+    v = u.forward(m0, m1)
+    dv = torch.zeros_like(v)
+    out["unet_backward_ms"] = timeit(lambda: u.backward(dv), 5)
+    gv = torch.empty((3, 128, 128, 128), device="cuda")
+    out["vjp_128_ms"] = timeit(lambda: src.ctx.transport_vjp(v[0], m0[0], m1[0], None, gv), 5)
+    t0 = time.perf_counter()
+    warmstart.train(u, src, steps=10, batch=4)
+    out["train_step_ms"] = (time.perf_counter() - t0) / 10 * 1e3
+    src.ctx.close()
+    g = (256,) * 3
+    ctx = claire.Context(g, 1e-2, 4, stream=st)
+    m = torch.from_numpy(synth.blob_template(g, seed=1).astype(np.float32)).cuda()
+    vv = torch.from_numpy(synth.bandlimited_velocity(g, seed=2, kmax=8, vmax=1.0).astype(np.float32)).cuda()
+    gb = torch.randn(g, device="cuda")
+    gm = torch.empty(g, device="cuda")
+    gvv = torch.empty((3,) + g, device="cuda")
+    out["transport_256_ms"] = timeit(lambda: ctx.transport(vv, m, gm), 5)
+    out["vjp_256_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv), 3)
+    out["vjp_256_recompute_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv, recompute=True), 3)
+    print(json.dumps(out))
+
+
 def run_large_report(args):
     """Largest single-GPU registration.  Workload: three nested spheres with a
     blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
@@ -611,6 +693,7 @@ def run_large_report(args):
     def flush():
         gc.collect()
         torch.cuda.empty_cache()
+        claire.lib().claire_resample_release()  # cached plans and spectra of the grid transfers
 
     t0 = time.perf_counter()
     m0, labels = synth.sphere_template(grid, seed=0)
@@ -758,9 +841,17 @@ def run_large_report(args):
     del ctx
     u._bufs = {}  # the network's activation buffers are not needed any more
     flush()
+    out["runs"] = runs
+    print(json.dumps(out), flush=True)  # the FP16 part, in case the FP32 context does not fit
     # ---- plain FP32 (lowmem) from zero
-    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                         lowmem=1, wall_limit_s=1200)
+    out["device_gb_before_fp32_context"] = used_gb()
+    try:
+        ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                             lowmem=1, wall_limit_s=1200)
+    except claire.ClaireError as e:
+        runs["fp32_zero"] = {"error": str(e)}
+        print(json.dumps(out))
+        return
     out["fp32_lowmem_device_gb"] = used_gb()
     m0_d = torch.from_numpy(m0).to(dev)
     m1_d = torch.from_numpy(m1).to(dev)
@@ -786,6 +877,84 @@ def run_large_report(args):
     out["oracle_J_rel_diff_learned_vs_plain"] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
     out["oracle_mismatch_rel_diff_learned_vs_plain"] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / \
         a["oracle_mismatch"]
+    print(json.dumps(out))
+
+
+def run_net_report(args):
+    """CUDA-event timing (mean of 10 after a warm-up) of the network kernels
+    and the reverse-mode transport.  Convolution TFLOP/s count 2 * voxels *
+    27 * Cin * Cout flops; bytes count each input and output activation once
+    (BF16).  Peak for the fraction: the measured dense BF16 rate."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, net, warmstart, synth
+    st = torch.cuda.current_stream().cuda_stream
+    peaks = {}
+    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(pp):
+        with open(pp) as f:
+            peaks = json.load(f)
+    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
+
+    def timeit(fn, reps=10):
+        fn()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record()
+        for _ in range(reps):
+            fn()
+        b.record()
+        torch.cuda.synchronize()
+        return a.elapsed_time(b) / reps
+
+    out = {"bf16_peak_tflops": bf16_peak, "conv": {}}
+    B, n = 4, 128
+    for lvl, ci, co in [(0, 16, 16), (0, 48, 16), (1, 16, 32), (1, 32, 32), (1, 96, 32), (2, 32, 64), (2, 64, 64),
+                        (2, 192, 64), (3, 64, 128), (3, 128, 128)]:
+        D = n >> lvl
+        x = (torch.randn((B, D, D, D, ci), device="cuda")).to(torch.bfloat16)
+        w = (torch.randn((co, 27, ci), device="cuda") / math.sqrt(27 * ci)).to(torch.bfloat16)
+        y = torch.empty((B, D, D, D, co), device="cuda", dtype=torch.bfloat16)
+        X, Y = net.Act(x, 0, ci), net.Act(y, 0, co)
+        t = timeit(lambda: net.conv3d(X, w, None, Y, 0.1, 1, st))
+        chunks = net.wgrad_chunks(ci, co, (B, D, D, D))
+        part = torch.empty(chunks * co * 27 * ci, device="cuda")
+        pb = torch.empty(chunks * co, device="cuda")
+        dw = torch.empty((co, 27, ci), device="cuda")
+        db = torch.empty(co, device="cuda")
+        tw = timeit(lambda: net.conv3d_wgrad(X, Y, chunks, part, pb, dw, db, st))
+        P = B * D ** 3
+        fl = 2.0 * P * 27 * ci * co
+        out["conv"]["l%d_%dx%d" % (lvl, ci, co)] = {
+            "voxels": P, "fwd_ms": t, "fwd_tflops": fl / t / 1e9, "fwd_frac_bf16_peak": fl / t / 1e9 / bf16_peak,
+            "fwd_gbs": P * (ci + co) * 2 / t / 1e6, "wgrad_ms": tw, "wgrad_tflops": fl / tw / 1e9}
+        del x, w, y, part, pb, dw, db
+    src = warmstart.PairSource(128, n_templates=4, n_velocities=4, noise=0.0, seed=0)
+    u = net.UNet(seed=0, stream=st)
+    warmstart.train(u, src, steps=3, batch=4)
+    m0, m1, vs = src.batch(4)
+    out["unet_forward_ms"] = timeit(lambda: u.forward(m0, m1), 5)
+    v = u.forward(m0, m1)
+    dv = torch.zeros_like(v)
+    out["unet_backward_ms"] = timeit(lambda: u.backward(dv), 5)
+    gv = torch.empty((3, 128, 128, 128), device="cuda")
+    out["vjp_128_ms"] = timeit(lambda: src.ctx.transport_vjp(v[0], m0[0], m1[0], None, gv), 5)
+    t0 = time.perf_counter()
+    warmstart.train(u, src, steps=10, batch=4)
+    out["train_step_ms"] = (time.perf_counter() - t0) / 10 * 1e3
+    src.ctx.close()
+    g = (256,) * 3
+    ctx = claire.Context(g, 1e-2, 4, stream=st)
+    m = torch.from_numpy(synth.blob_template(g, seed=1).astype(np.float32)).cuda()
+    vv = torch.from_numpy(synth.bandlimited_velocity(g, seed=2, kmax=8, vmax=1.0).astype(np.float32)).cuda()
+    gb = torch.randn(g, device="cuda")
+    gm = torch.empty(g, device="cuda")
+    gvv = torch.empty((3,) + g, device="cuda")
+    out["transport_256_ms"] = timeit(lambda: ctx.transport(vv, m, gm), 5)
+    out["vjp_256_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv), 3)
+    out["vjp_256_recompute_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv, recompute=True), 3)
     print(json.dumps(out))
 
 
@@ -820,6 +989,7 @@ def run_large_report(args):
     def flush():
         gc.collect()
         torch.cuda.empty_cache()
+        claire.lib().claire_resample_release()  # cached plans and spectra of the grid transfers
 
     t0 = time.perf_counter()
     m0, labels = synth.sphere_template(grid, seed=0)
@@ -927,9 +1097,17 @@ def run_large_report(args):
     ctx.close()
     del ctx
     flush()
+    out["runs"] = runs
+    print(json.dumps(out), flush=True)  # the FP16 part, in case the FP32 context does not fit
     # ---- plain FP32 (lowmem) from zero
-    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                         lowmem=1, wall_limit_s=1200)
+    out["device_gb_before_fp32_context"] = used_gb()
+    try:
+        ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                             lowmem=1, wall_limit_s=1200)
+    except claire.ClaireError as e:
+        runs["fp32_zero"] = {"error": str(e)}
+        print(json.dumps(out))
+        return
     out["fp32_lowmem_device_gb"] = used_gb()
     ctx.set_images(m0_d, m1_d)
     v = torch.zeros((3,) + grid, device=dev)
@@ -976,6 +1154,9 @@ def run_large_report(args):
 
 def main():
     args = parse_args()
+    if args.net_report:
+        run_net_report(args)
+        return
     if args.large_report:
         run_large_report(args)
         return

@@ -65,6 +65,8 @@ def parse_args():
                          "learned warm start, both without stored state gradients; Dice on 3 labels; the same "
                          "registration on images sampled to 256^3 and 512^3; sampled oracle parity")
     ap.add_argument("--large-n", type=int, default=1024)
+    ap.add_argument("--large-vmax", type=float, default=0.5,
+                    help="max |v*| of the large case (0.5: CFL 20 at 1024^3, nt=4)")
     ap.add_argument("--net-report", action="store_true",
                     help="timing of the warm-start network kernels (every conv shape of the U-Net at 128^3, "
                          "batch 4), one training step, and the SL reverse-mode transport at 256^3")
@@ -665,7 +667,7 @@ def run_net_report(args):
 def run_large_report(args):
     """Largest single-GPU registration.  Workload: three nested spheres with a
     blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
-    band-limited velocity |k| <= 8, max|v| = 1 (drawn at 64^3, prolonged
+    band-limited velocity |k| <= 8, max|v| = --large-vmax (drawn at 64^3, prolonged
     spectrally) to give the reference; labels follow the same velocity
     (indicator transport, threshold 1/2).  nt = 4, tricubic, beta_v = 1e-2,
     beta_w = 1e-4, gtol 5e-2 of |g(v=0)|.  Both solves keep no stored state
@@ -683,8 +685,9 @@ def run_large_report(args):
     N = n ** 3
     dev = torch.device("cuda", 0)
     st = torch.cuda.current_stream().cuda_stream
-    out = {"workload": "%d^3 nested spheres + blob texture (3 labels), band-limited v* |k|<=8 max|v|=1, nt=4, "
-                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|" % (n, args.beta)}
+    out = {"workload": "%d^3 nested spheres + blob texture (3 labels), band-limited v* |k|<=8 max|v|=%g, nt=4, "
+                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|, at most 50 GN iterations"
+                       % (n, args.large_vmax, args.beta)}
 
     def used_gb():
         free, total = torch.cuda.mem_get_info()
@@ -697,7 +700,7 @@ def run_large_report(args):
 
     t0 = time.perf_counter()
     m0, labels = synth.sphere_template(grid, seed=0)
-    v64 = synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=1.0).astype(np.float32)
+    v64 = synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=args.large_vmax).astype(np.float32)
     out["generate_s"] = time.perf_counter() - t0
     # warm-start network, trained at 128^3 on method-generated pairs (sphere and blob families)
     t0 = time.perf_counter()
@@ -745,7 +748,7 @@ def run_large_report(args):
 
     out["dice_before"] = dice([labels == k for k in (1, 2, 3)])
     ctx.set_images(m0_d, m1_d)   # the context keeps its own (FP16) copies
-    del vstar, m1_d
+    del vstar, m1_d, m0_d
     flush()
 
     def sampled(nc):
@@ -782,6 +785,7 @@ def run_large_report(args):
     ctx.set_opts(g0_ref=0.0)
     runs["fp16_learned"]["dice"] = dice(warped_labels(v))
     # sampled oracle parity of one backtrace and one interpolation at n^3
+    flush()
     d = torch.empty((3,) + grid, device=dev)
     ctx.backtrace(v, d, 1)
     m0_d = torch.from_numpy(m0).to(dev)
@@ -871,281 +875,6 @@ def run_large_report(args):
     del v
     ctx.close()
     flush()
-    out["runs"] = runs
-    a, b = runs["fp32_zero"], runs["fp16_learned"]
-    out["speedup_fp16_learned_vs_fp32_zero"] = a["time_to_tol_s"] / b["time_to_tol_s"]
-    out["oracle_J_rel_diff_learned_vs_plain"] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
-    out["oracle_mismatch_rel_diff_learned_vs_plain"] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / \
-        a["oracle_mismatch"]
-    print(json.dumps(out))
-
-
-def run_net_report(args):
-    """CUDA-event timing (mean of 10 after a warm-up) of the network kernels
-    and the reverse-mode transport.  Convolution TFLOP/s count 2 * voxels *
-    27 * Cin * Cout flops; bytes count each input and output activation once
-    (BF16).  Peak for the fraction: the measured dense BF16 rate."""
-    import torch
-    import __graft_entry__ as entry
-    entry.build()
-    from paper_2209_08189_gb300 import claire, net, warmstart, synth
-    st = torch.cuda.current_stream().cuda_stream
-    peaks = {}
-    pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
-    if os.path.exists(pp):
-        with open(pp) as f:
-            peaks = json.load(f)
-    bf16_peak = float(peaks.get("bf16_tflops", 1900.0))
-
-    def timeit(fn, reps=10):
-        fn()
-        torch.cuda.synchronize()
-        a = torch.cuda.Event(enable_timing=True)
-        b = torch.cuda.Event(enable_timing=True)
-        a.record()
-        for _ in range(reps):
-            fn()
-        b.record()
-        torch.cuda.synchronize()
-        return a.elapsed_time(b) / reps
-
-    out = {"bf16_peak_tflops": bf16_peak, "conv": {}}
-    B, n = 4, 128
-    for lvl, ci, co in [(0, 16, 16), (0, 48, 16), (1, 16, 32), (1, 32, 32), (1, 96, 32), (2, 32, 64), (2, 64, 64),
-                        (2, 192, 64), (3, 64, 128), (3, 128, 128)]:
-        D = n >> lvl
-        x = (torch.randn((B, D, D, D, ci), device="cuda")).to(torch.bfloat16)
-        w = (torch.randn((co, 27, ci), device="cuda") / math.sqrt(27 * ci)).to(torch.bfloat16)
-        y = torch.empty((B, D, D, D, co), device="cuda", dtype=torch.bfloat16)
-        X, Y = net.Act(x, 0, ci), net.Act(y, 0, co)
-        t = timeit(lambda: net.conv3d(X, w, None, Y, 0.1, 1, st))
-        chunks = net.wgrad_chunks(ci, co, (B, D, D, D))
-        part = torch.empty(chunks * co * 27 * ci, device="cuda")
-        pb = torch.empty(chunks * co, device="cuda")
-        dw = torch.empty((co, 27, ci), device="cuda")
-        db = torch.empty(co, device="cuda")
-        tw = timeit(lambda: net.conv3d_wgrad(X, Y, chunks, part, pb, dw, db, st))
-        P = B * D ** 3
-        fl = 2.0 * P * 27 * ci * co
-        out["conv"]["l%d_%dx%d" % (lvl, ci, co)] = {
-            "voxels": P, "fwd_ms": t, "fwd_tflops": fl / t / 1e9, "fwd_frac_bf16_peak": fl / t / 1e9 / bf16_peak,
-            "fwd_gbs": P * (ci + co) * 2 / t / 1e6, "wgrad_ms": tw, "wgrad_tflops": fl / tw / 1e9}
-        del x, w, y, part, pb, dw, db
-    src = warmstart.PairSource(128, n_templates=4, n_velocities=4, noise=0.0, seed=0)
-    u = net.UNet(seed=0, stream=st)
-    warmstart.train(u, src, steps=3, batch=4)
-    m0, m1, vs = src.batch(4)
-    out["unet_forward_ms"] = timeit(lambda: u.forward(m0, m1), 5)
-    v = u.forward(m0, m1)
-    dv = torch.zeros_like(v)
-    out["unet_backward_ms"] = timeit(lambda: u.backward(dv), 5)
-    gv = torch.empty((3, 128, 128, 128), device="cuda")
-    out["vjp_128_ms"] = timeit(lambda: src.ctx.transport_vjp(v[0], m0[0], m1[0], None, gv), 5)
-    t0 = time.perf_counter()
-    warmstart.train(u, src, steps=10, batch=4)
-    out["train_step_ms"] = (time.perf_counter() - t0) / 10 * 1e3
-    src.ctx.close()
-    g = (256,) * 3
-    ctx = claire.Context(g, 1e-2, 4, stream=st)
-    m = torch.from_numpy(synth.blob_template(g, seed=1).astype(np.float32)).cuda()
-    vv = torch.from_numpy(synth.bandlimited_velocity(g, seed=2, kmax=8, vmax=1.0).astype(np.float32)).cuda()
-    gb = torch.randn(g, device="cuda")
-    gm = torch.empty(g, device="cuda")
-    gvv = torch.empty((3,) + g, device="cuda")
-    out["transport_256_ms"] = timeit(lambda: ctx.transport(vv, m, gm), 5)
-    out["vjp_256_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv), 3)
-    out["vjp_256_recompute_ms"] = timeit(lambda: ctx.transport_vjp(vv, m, gb, gm, gvv, recompute=True), 3)
-    print(json.dumps(out))
-
-
-def run_large_report(args):
-    """Largest single-GPU registration.  Workload: three nested spheres with a
-    blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
-    band-limited velocity |k| <= 8, max|v| = 1 (drawn at 64^3, prolonged
-    spectrally) to give the reference; labels follow the same velocity
-    (indicator transport, threshold 1/2).  nt = 4, tricubic, beta_v = 1e-2,
-    beta_w = 1e-4, gtol 5e-2 of |g(v=0)|.  Both solves keep no stored state
-    gradients (lowmem).  Memory is the device memory in use (cudaMemGetInfo)
-    after each context is created.  Oracle parity at n^3 is checked on 10^6
-    sampled points of one backtrace and one interpolation (FP64)."""
-    import gc
-    import torch
-    import oracle
-    import __graft_entry__ as entry
-    entry.build()
-    from paper_2209_08189_gb300 import claire, synth, net, warmstart
-    n = args.large_n
-    grid = (n, n, n)
-    N = n ** 3
-    dev = torch.device("cuda", 0)
-    st = torch.cuda.current_stream().cuda_stream
-    out = {"workload": "%d^3 nested spheres + blob texture (3 labels), band-limited v* |k|<=8 max|v|=1, nt=4, "
-                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2 of |g(v=0)|" % (n, args.beta)}
-
-    def used_gb():
-        free, total = torch.cuda.mem_get_info()
-        return (total - free) / 1e9
-
-    def flush():
-        gc.collect()
-        torch.cuda.empty_cache()
-        claire.lib().claire_resample_release()  # cached plans and spectra of the grid transfers
-
-    t0 = time.perf_counter()
-    m0, labels = synth.sphere_template(grid, seed=0)
-    v64 = synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=1.0).astype(np.float32)
-    out["generate_s"] = time.perf_counter() - t0
-    # warm-start network, trained at 128^3 on method-generated pairs (sphere and blob families)
-    t0 = time.perf_counter()
-    src = warmstart.PairSource(128, n_templates=24, n_velocities=48, kmax=(4, 8), vmax=(0.3, 1.2), noise=0.0,
-                               seed=1, families=("label", "blob"))
-    u = net.UNet(seed=0, stream=st)
-    hist = warmstart.train(u, src, steps=args.ws_steps, batch=4, lr=1e-3, lr_final=1e-4, log_every=0)
-    src.ctx.close()
-    del src
-    flush()
-    out["training_s"] = time.perf_counter() - t0
-
-    # ---- FP16 + lowmem context: reference image, labels, downsampled runs, learned run
-    ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                         storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200)
-    out["fp16_lowmem_device_gb"] = used_gb()
-    vstar = torch.empty((3,) + grid, device=dev)
-    claire.claire_resample(torch.from_numpy(v64).to(dev), (64, 64, 64), vstar, grid, 3, claire.RESAMPLE_SPECTRAL,
-                           st)
-    m0_d = torch.from_numpy(m0).to(dev)
-    m1_d = torch.empty(grid, device=dev)
-    ctx.transport(vstar, m0_d, m1_d)
-    m1 = m1_d.cpu().numpy()
-    buf = torch.empty(grid, device=dev)
-    tmp = torch.empty(grid, device=dev)
-
-    def warped_labels(v):
-        """Labels of m0 carried by v: transported indicators, threshold 1/2."""
-        res = []
-        for k in (1, 2, 3):
-            buf.copy_(torch.from_numpy((labels == k).astype(np.float32)))
-            ctx.transport(v, buf, tmp)
-            res.append(tmp.cpu().numpy() > 0.5)
-        return res
-
-    ref = warped_labels(vstar)
-    del vstar
-    flush()
-
-    def dice(lab):
-        return [float(2.0 * np.count_nonzero(a & b) / max(1, np.count_nonzero(a) + np.count_nonzero(b)))
-                for a, b in zip(lab, ref)]
-
-    out["dice_before"] = dice([labels == k for k in (1, 2, 3)])
-    runs = {}
-    # the same registration on images sampled to 256^3 and 512^3, velocity prolonged back
-    for nc in (256, 512):
-        if nc >= n:
-            continue
-        g_c = (nc,) * 3
-        c_ctx = claire.Context(g_c, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50)
-        a0 = torch.empty(g_c, device=dev)
-        a1 = torch.empty(g_c, device=dev)
-        claire.claire_resample(m0_d, grid, a0, g_c, 1, claire.RESAMPLE_NEAREST, st)
-        claire.claire_resample(m1_d, grid, a1, g_c, 1, claire.RESAMPLE_NEAREST, st)
-        c_ctx.set_images(a0, a1)
-        vc = torch.zeros((3,) + g_c, device=dev)
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        _, rep = c_ctx.register(vc)
-        torch.cuda.synchronize()
-        secs = time.perf_counter() - t0
-        c_ctx.close()
-        vf = torch.empty((3,) + grid, device=dev)
-        claire.claire_resample(vc, g_c, vf, grid, 3, claire.RESAMPLE_SPECTRAL, st)
-        ctx.set_images(m0_d, m1_d)
-        _, mis_f = ctx.objective(vf)
-        runs["fp32_at_%d" % nc] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"],
-                                   "pcg_iters": rep["pcg_iters_total"], "r_at_%d" % nc: rep["r"],
-                                   "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(warped_labels(vf))}
-        del vf, vc, a0, a1, c_ctx
-        flush()
-    # learned warm start + FP16 storage
-    ctx.set_images(m0_d, m1_d)
-    v = torch.zeros((3,) + grid, device=dev)
-    g = torch.empty((3,) + grid, device=dev)
-    ws = warmstart.WarmStart(u, 128)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    ctx.gradient(v, g)
-    g0 = math.sqrt(claire.claire_dot(ctx.handle, g, g, 3 * N))
-    del g
-    ws.predict(m0_d, m1_d, v)
-    torch.cuda.synchronize()
-    t_pred = time.perf_counter() - t0
-    _, mis_guess = ctx.objective(v)
-    _, mis_zero = ctx.objective(torch.zeros((3,) + grid, device=dev))
-    flush()
-    ctx.set_opts(g0_ref=g0)
-    torch.cuda.synchronize()
-    t1 = time.perf_counter()
-    stt, rep = ctx.register(v)
-    torch.cuda.synchronize()
-    runs["fp16_learned"] = {"time_to_tol_s": time.perf_counter() - t0, "predict_and_g0_s": t_pred,
-                            "status": rep["status"], "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
-                            "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
-                            "detj_max": rep["detj_max"], "cfl": rep["cfl"], "mismatch_at_guess": mis_guess,
-                            "mismatch_at_zero": mis_zero, "dice": dice(warped_labels(v)),
-                            "peak_device_gb": used_gb()}
-    del v
-    ctx.close()
-    del ctx
-    flush()
-    out["runs"] = runs
-    print(json.dumps(out), flush=True)  # the FP16 part, in case the FP32 context does not fit
-    # ---- plain FP32 (lowmem) from zero
-    out["device_gb_before_fp32_context"] = used_gb()
-    try:
-        ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                             lowmem=1, wall_limit_s=1200)
-    except claire.ClaireError as e:
-        runs["fp32_zero"] = {"error": str(e)}
-        print(json.dumps(out))
-        return
-    out["fp32_lowmem_device_gb"] = used_gb()
-    ctx.set_images(m0_d, m1_d)
-    v = torch.zeros((3,) + grid, device=dev)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    stt, rep = ctx.register(v)
-    torch.cuda.synchronize()
-    runs["fp32_zero"] = {"time_to_tol_s": time.perf_counter() - t0, "status": rep["status"],
-                         "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"], "J": rep["J"],
-                         "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
-                         "detj_max": rep["detj_max"], "cfl": rep["cfl"], "dice": dice(warped_labels(v)),
-                         "peak_device_gb": used_gb()}
-    # sampled oracle parity of one backtrace and one interpolation at n^3
-    d = torch.empty((3,) + grid, device=dev)
-    ctx.backtrace(v, d, 1)
-    ctx.interp(m0_d, d, buf)
-    rng = np.random.default_rng(0)
-    S = 1000000
-    idx = torch.from_numpy(rng.integers(0, N, size=S)).to(dev)
-    d_s = d.view(3, -1)[:, idx].double().cpu().numpy()
-    out_s = buf.view(-1)[idx].double().cpu().numpy()
-    v_s = v.view(3, -1)[:, idx].double().cpu().numpy()
-    vh = v.cpu().numpy()
-    del d
-    ctx.close()
-    flush()
-    ii = idx.cpu().numpy()
-    x = np.stack([ii // (n * n), (ii // n) % n, ii % n]).astype(np.float64)
-    h = 2.0 * math.pi / n
-    dt = 0.25
-    u0 = v_s / h
-    yp = x - dt * u0
-    U = np.stack([oracle.interp_points(vh[c].astype(np.float64), yp, 3) for c in range(3)]) / h
-    d_ref = -0.5 * dt * (u0 + U)
-    m_ref = oracle.interp_points(m0.astype(np.float64), x + d_s, 3)
-    out["sampled_parity"] = {"points": S,
-                             "backtrace_rel_linf": float(np.max(np.abs(d_s - d_ref)) / np.max(np.abs(d_ref))),
-                             "interp_rel_linf": float(np.max(np.abs(out_s - m_ref)) / np.max(np.abs(m_ref)))}
     out["runs"] = runs
     a, b = runs["fp32_zero"], runs["fp16_learned"]
     out["speedup_fp16_learned_vs_fp32_zero"] = a["time_to_tol_s"] / b["time_to_tol_s"]

@@ -15,6 +15,7 @@
 // bitwise deterministic.
 #include "internal.h"
 
+#include <climits>
 #include <cmath>
 
 namespace claire {
@@ -132,24 +133,12 @@ __device__ __forceinline__ double fixed_scale_of(double mx)
     return ldexp(1.0, 48 - e);
 }
 
-// acc[q] += round(scale * w(p, q) * y[p]) for the stencil of every point p at
-// x_p + disp_p; disp = d (if non-null) or -sdt * v / h (the RK2 predictor).
-template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_scatter_fixed(Grid g, const float* __restrict__ yv,
-                                                             const float* __restrict__ d,
-                                                             const float* __restrict__ v, float sdt,
-                                                             const double* __restrict__ maxabs,
-                                                             unsigned long long* __restrict__ acc)
+// Displacement of point p (grid units): d if given, else the RK2 predictor -sdt v / h.
+__device__ __forceinline__ void scatter_disp(const Grid& g, const float* __restrict__ d,
+                                             const float* __restrict__ v, float sdt, uint32_t p, float& d1,
+                                             float& d2, float& d3)
 {
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    const double scale = fixed_scale_of(*maxabs);
-    const float y = __ldg(yv + p);
-    if (y == 0.0f || !(scale > 0.0)) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
     const size_t N = g.N;
-    float d1, d2, d3;
     if (d) {
         d1 = __ldg(d + p); d2 = __ldg(d + N + p); d3 = __ldg(d + 2 * N + p);
     } else {
@@ -157,24 +146,146 @@ __global__ void __launch_bounds__(kThreads) k_scatter_fixed(Grid g, const float*
         d2 = -sdt * __ldg(v + N + p) * g.ih2;
         d3 = -sdt * __ldg(v + 2 * N + p) * g.ih3;
     }
+}
+
+// Fixed-point contribution of y * w_a w_b w_c.
+__device__ __forceinline__ unsigned long long fixed_term(double wab, float wc)
+{
+    return static_cast<unsigned long long>(__double2ll_rn(wab * static_cast<double>(wc)));
+}
+
+// Scatter-transpose tiles: a CTA owns a 4 x 8 x 32 tile of source points
+// (256 threads, 4 points each along x1), like the gather tiles.  The
+// destination stencils of the tile span a box that is accumulated in shared
+// memory (64-bit integer atomics) and flushed with one global atomic per
+// touched node, instead of 64 global atomics per point.  Boxes larger than
+// kScatterCap nodes fall back to global atomics.  Integer sums do not depend
+// on the order of additions, so either path gives the same bits.
+constexpr int kST1 = 4, kST2 = 8, kST3 = 32;
+constexpr int kScatterCap = 6144;  // 48 KB of 64-bit accumulators
+
+template <int ORDER>
+__global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float* __restrict__ yv,
+                                                             const float* __restrict__ d,
+                                                             const float* __restrict__ v, float sdt,
+                                                             const double* __restrict__ maxabs,
+                                                             unsigned long long* __restrict__ acc)
+{
+    extern __shared__ unsigned long long sbox[];
+    __shared__ int red[6][kST2];
+    __shared__ int par[7];
     constexpr int M = DAxis<ORDER>::M;
-    DAxis<ORDER> a1, a2, a3;
-    a1.build(i, d1, g.n1, g.n23);
-    a2.build(j, d2, g.n2, g.n3);
-    a3.build(k, d3, g.n3, 1);
-    const double ys = scale * static_cast<double>(y);
+    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    const double scale = fixed_scale_of(*maxabs);
+    if (!(scale > 0.0)) return;  // uniform: zero or non-finite cotangent
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int j = blockIdx.y * kST2 + warp, k = blockIdx.x * kST3 + lane, i0 = blockIdx.z * kST1;
+    const bool col_ok = j < g.n2 && k < g.n3;
+    float dd[kST1][3], yy[kST1];
+    int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
 #pragma unroll
-    for (int a = 0; a < M; ++a)
-#pragma unroll
-        for (int b = 0; b < M; ++b) {
-            const double wab = ys * static_cast<double>(a1.w[a] * a2.w[b]);
-            const size_t row = static_cast<size_t>(a1.idx[a]) + a2.idx[b];
-#pragma unroll
-            for (int c = 0; c < M; ++c) {
-                const long long q = __double2ll_rn(wab * static_cast<double>(a3.w[c]));
-                atomicAdd(acc + row + a3.idx[c], static_cast<unsigned long long>(q));
-            }
+    for (int q = 0; q < kST1; ++q) {
+        yy[q] = 0.0f;
+        const int i = i0 + q;
+        if (!(col_ok && i < g.n1)) continue;
+        const uint32_t p = (static_cast<uint32_t>(i) * g.n2 + j) * g.n3 + k;
+        yy[q] = __ldg(yv + p);
+        if (yy[q] == 0.0f) continue;
+        scatter_disp(g, d, v, sdt, p, dd[q][0], dd[q][1], dd[q][2]);
+        float t;
+        const int b1 = i + split_disp(dd[q][0], t) - OFF;
+        const int b2 = j + split_disp(dd[q][1], t) - OFF;
+        const int b3 = k + split_disp(dd[q][2], t) - OFF;
+        lo1 = min(lo1, b1); hi1 = max(hi1, b1);
+        lo2 = min(lo2, b2); hi2 = max(hi2, b2);
+        lo3 = min(lo3, b3); hi3 = max(hi3, b3);
+    }
+    lo1 = __reduce_min_sync(0xffffffffu, lo1);
+    lo2 = __reduce_min_sync(0xffffffffu, lo2);
+    lo3 = __reduce_min_sync(0xffffffffu, lo3);
+    hi1 = __reduce_max_sync(0xffffffffu, hi1);
+    hi2 = __reduce_max_sync(0xffffffffu, hi2);
+    hi3 = __reduce_max_sync(0xffffffffu, hi3);
+    if (lane == 0) {
+        red[0][warp] = lo1; red[1][warp] = lo2; red[2][warp] = lo3;
+        red[3][warp] = hi1; red[4][warp] = hi2; red[5][warp] = hi3;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int a1 = INT_MAX, a2 = INT_MAX, a3 = INT_MAX, z1 = INT_MIN, z2 = INT_MIN, z3 = INT_MIN;
+        for (int w = 0; w < kST2; ++w) {
+            a1 = min(a1, red[0][w]); a2 = min(a2, red[1][w]); a3 = min(a3, red[2][w]);
+            z1 = max(z1, red[3][w]); z2 = max(z2, red[4][w]); z3 = max(z3, red[5][w]);
         }
+        par[0] = a1; par[1] = a2; par[2] = a3;
+        if (a1 > z1) {
+            par[6] = 0;  // no non-zero point in the tile
+        } else {
+            const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M, e3 = (long long)z3 - a3 + M;
+            const bool fits = e1 * e2 * e3 <= kScatterCap;
+            par[3] = (int)e1; par[4] = (int)e2; par[5] = (int)e3;
+            par[6] = fits ? 1 : 2;
+        }
+    }
+    __syncthreads();
+    const int mode = par[6];
+    if (mode == 0) return;
+    const int o1 = par[0], o2 = par[1], o3 = par[2];
+    const int e1 = par[3], e2 = par[4], e3 = par[5];
+    const int vol = e1 * e2 * e3;
+    if (mode == 1)
+        for (int t = threadIdx.x; t < vol; t += kThreads) sbox[t] = 0ull;
+    __syncthreads();
+#pragma unroll
+    for (int q = 0; q < kST1; ++q) {
+        if (yy[q] == 0.0f) continue;
+        const int i = i0 + q;
+        DAxis<ORDER> a1x, a2x, a3x;
+        const double ys = scale * static_cast<double>(yy[q]);
+        if (mode == 1) {
+            // box-relative stencil: unwrapped first node minus the box origin
+            float t1, t2, t3;
+            const int r1 = i + split_disp(dd[q][0], t1) - OFF - o1;
+            const int r2 = j + split_disp(dd[q][1], t2) - OFF - o2;
+            const int r3 = k + split_disp(dd[q][2], t3) - OFF - o3;
+            float w1[4], w2[4], w3[4], dw[4];
+            basis_and_deriv<ORDER>(t1, w1, dw);
+            basis_and_deriv<ORDER>(t2, w2, dw);
+            basis_and_deriv<ORDER>(t3, w3, dw);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = 0; b < M; ++b) {
+                    const double wab = ys * static_cast<double>(w1[a] * w2[b]);
+                    unsigned long long* row = sbox + ((r1 + a) * e2 + (r2 + b)) * e3 + r3;
+#pragma unroll
+                    for (int c = 0; c < M; ++c) atomicAdd(row + c, fixed_term(wab, w3[c]));
+                }
+        } else {
+            a1x.build(i, dd[q][0], g.n1, g.n23);
+            a2x.build(j, dd[q][1], g.n2, g.n3);
+            a3x.build(k, dd[q][2], g.n3, 1);
+#pragma unroll
+            for (int a = 0; a < M; ++a)
+#pragma unroll
+                for (int b = 0; b < M; ++b) {
+                    const double wab = ys * static_cast<double>(a1x.w[a] * a2x.w[b]);
+                    const size_t row = static_cast<size_t>(a1x.idx[a]) + a2x.idx[b];
+#pragma unroll
+                    for (int c = 0; c < M; ++c) atomicAdd(acc + row + a3x.idx[c], fixed_term(wab, a3x.w[c]));
+                }
+        }
+    }
+    if (mode != 1) return;
+    __syncthreads();
+    for (int t = threadIdx.x; t < vol; t += kThreads) {
+        const unsigned long long val = sbox[t];
+        if (!val) continue;
+        const int c3 = t % e3, c2 = (t / e3) % e2, c1 = t / (e3 * e2);
+        const size_t node = (static_cast<size_t>(wrap_index(o1 + c1, g.n1)) * g.n2 + wrap_index(o2 + c2, g.n2)) *
+                                g.n3 + wrap_index(o3 + c3, g.n3);
+        atomicAdd(acc + node, val);
+    }
 }
 
 // out = mult ((accumulate ? out : 0) + acc / scale); acc is cleared for reuse.
@@ -256,10 +367,12 @@ void launch_grad_accum(const Grid& g, int order, const float* m, const float* d,
 void launch_scatter_fixed(const Grid& g, int order, const float* yv, const float* d, const float* v, float sdt,
                           const double* maxabs, unsigned long long* acc, cudaStream_t st)
 {
+    const dim3 grid((g.n3 + kST3 - 1) / kST3, (g.n2 + kST2 - 1) / kST2, (g.n1 + kST1 - 1) / kST1);
+    const size_t smem = kScatterCap * sizeof(unsigned long long);
     if (order == 3)
-        k_scatter_fixed<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, yv, d, v, sdt, maxabs, acc);
+        k_scatter_tiled<3><<<grid, kThreads, smem, st>>>(g, yv, d, v, sdt, maxabs, acc);
     else
-        k_scatter_fixed<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, yv, d, v, sdt, maxabs, acc);
+        k_scatter_tiled<1><<<grid, kThreads, smem, st>>>(g, yv, d, v, sdt, maxabs, acc);
 }
 
 void launch_fixed_to_float(unsigned long long* acc, const double* maxabs, int accumulate, float mult, float* out,

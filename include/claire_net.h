@@ -42,7 +42,11 @@ extern "C" {
  * `slope` for negative inputs.  Cin a multiple of 16, Cout one of 16, 32,
  * 48, 64, 96, 128, 192;
  * D, H, W powers of two >= 4 with D*H*W >= 64 (any bias may be NULL).
- * BF16 inputs and outputs, FP32 accumulation on the tensor cores. */
+ * BF16 inputs and outputs, FP32 accumulation on the tensor cores: grids with
+ * H a multiple of 16 and W of 8 run on tcgen05 (accumulators in TMEM, one
+ * CTA per 1 x 16 x 8 brick); smaller grids on mma.sync.  A tcgen05 CTA whose
+ * completion wait gives up (it never should) counts an error that
+ * claire_net_device_errors reports; its outputs are then unspecified. */
 claire_status claire_net_conv3d(const void* x, int x_stride, int cin, const void* w, const float* bias,
                                 float slope, int act, void* y, int y_stride, int cout, const int vol[4],
                                 void* stream);
@@ -115,6 +119,10 @@ claire_status claire_net_adam(float* w, const float* g, float* m, float* s, size
 claire_status claire_net_vel_loss(const float* v, const float* vstar, const float* gv, float a, float b, size_t n,
                                   float* dv, double* sum, void* stream);
 claire_status claire_net_residual(const float* x, const float* y, size_t n, float* r, double* sum, void* stream);
+
+/* Number of tcgen05 completion waits that gave up since the last reset
+ * (reset != 0 clears it).  Synchronises the device. */
+claire_status claire_net_device_errors(int* count, int reset);
 
 /* Message of the last failing claire_net_* call on this thread. */
 const char* claire_net_last_error(void);

@@ -81,6 +81,34 @@ __device__ __forceinline__ void mma_bf16(float d[4], uint32_t a0, uint32_t a1, u
 // byte offset of 16-byte half h of row s in a [rows][16 x bf16] swizzled tile
 __device__ __forceinline__ uint32_t swz(int s, int h) { return static_cast<uint32_t>((2 * s + (h ^ ((s >> 2) & 1))) * 16); }
 
+// 8 channels per thread (16 bytes) helpers
+struct V8 {
+    float f[8];
+};
+
+__device__ __forceinline__ V8 load8(const __nv_bfloat16* p)
+{
+    const uint4 u = *reinterpret_cast<const uint4*>(p);
+    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
+    V8 r;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+        const float2 f = __bfloat1622float2(h[q]);
+        r.f[2 * q] = f.x;
+        r.f[2 * q + 1] = f.y;
+    }
+    return r;
+}
+
+__device__ __forceinline__ void store8(__nv_bfloat16* p, const V8& r)
+{
+    uint4 u;
+    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
+#pragma unroll
+    for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(r.f[2 * q], r.f[2 * q + 1]);
+    *reinterpret_cast<uint4*>(p) = u;
+}
+
 struct Vol {
     int B, D, H, W;
 };
@@ -187,6 +215,169 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d(const __nv_bfloat16* __
             *reinterpret_cast<__nv_bfloat162*>(yrow + co) = __floats2bfloat162_rn(y0, y1);
         }
     }
+}
+
+// ---------------------------------------------------------------------------
+// tcgen05 (5th-generation tensor core) version of the forward convolution
+// ---------------------------------------------------------------------------
+// A CTA owns a brick of 1 x 16 x 8 = 128 output voxels (M = 128, one TMEM
+// lane per voxel) and all Cout channels (N = Cout, FP32 accumulators in
+// TMEM).  Per 16-channel slice of the input it stages, with cp.async, the
+// brick's halo (3 x 18 x 10 voxels) and the slice of all 27 taps' weights
+// into shared memory in the no-swizzle K-major core-matrix layout (8 rows x
+// 16 bytes per core matrix), then one elected thread issues 27
+// tcgen05.mma.kind::f16 (M128 x N x K16), one per tap: the A operand of a
+// tap is the halo shifted by the tap offset, which is just another start
+// address because every core matrix is 8 consecutive voxels along W and the
+// next core matrix is the next H row (a constant stride).  tcgen05.commit
+// signals an mbarrier; the epilogue reads TMEM with tcgen05.ld.
+constexpr int kTcBH = 16, kTcBW = 8;
+constexpr int kTcHaloD = 3, kTcHaloH = kTcBH + 2, kTcHaloW = kTcBW + 2;
+constexpr int kTcSlots = kTcHaloD * kTcHaloH * kTcHaloW;  // 540
+constexpr int kTcPlane = kTcSlots * 16;                   // bytes per 8-channel half plane
+constexpr uint32_t kTcSpinLimit = 1u << 26;
+
+// set when an mbarrier wait of k_conv3d_tc gave up (read by claire_net_device_errors)
+__device__ int g_tc_wait_errors = 0;
+
+__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    // start >> 4 [0,14), leading byte offset >> 4 [16,30), stride byte
+    // offset >> 4 [32,46), descriptor version 1 [46,48), no swizzle
+    return static_cast<uint64_t>((saddr >> 4) & 0x3FFFu) | (static_cast<uint64_t>((lbo >> 4) & 0x3FFFu) << 16) |
+           (static_cast<uint64_t>((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
+{
+    for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
+        uint32_t done;
+        asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+                     " selp.u32 %0, 1, 0, p;\n}\n"
+                     : "=r"(done)
+                     : "r"(mbar), "r"(parity)
+                     : "memory");
+        if (done) return true;
+    }
+    return false;
+}
+
+__global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
+                                                            const __nv_bfloat16* __restrict__ Wt,
+                                                            const float* __restrict__ bias, float slope, int act,
+                                                            __nv_bfloat16* __restrict__ Y, int Cys, int Cout,
+                                                            uint32_t tmem_cols, Vol v, int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char tc_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    // brick origin
+    const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
+    int r = blockIdx.x;
+    const int w0 = (r % nbw) * kTcBW; r /= nbw;
+    const int h0 = (r % nbh) * kTcBH; r /= nbh;
+    const int d0 = r % v.D;
+    const int b = r / v.D;
+    unsigned char* halo = tc_smem;                  // 2 planes of kTcSlots x 16 B
+    unsigned char* wsm = tc_smem + 2 * kTcPlane;     // [tap][half][Cout] x 16 B
+    const uint32_t halo_s = smem_addr(halo), w_s = smem_addr(wsm), mbar_s = smem_addr(&mbar);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(tmem_cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    // instruction descriptor: D F32, A and B BF16, both K-major, N = Cout, M = 128
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(Cout) >> 3) << 17) |
+                           ((128u >> 4) << 24);
+    const int nchunks = Cin / 16;
+    bool ok = true;
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int c0 = 16 * c;
+        if (c > 0) ok = mbar_wait(mbar_s, (c - 1) & 1);  // the previous slice's MMAs have read the buffers
+        if (!ok) break;
+        // halo: slot s = (sd * 18 + sh) * 10 + sw, half plane h
+        for (int e = tid; e < 2 * kTcSlots; e += kConvThreads) {
+            const int hlf = e / kTcSlots, sl = e % kTcSlots;
+            const int sw = sl % kTcHaloW, sh = (sl / kTcHaloW) % kTcHaloH, sd = sl / (kTcHaloW * kTcHaloH);
+            const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + sh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
+            const size_t vox = ((static_cast<size_t>(b) * v.D + d) * v.H + h) * v.W + w;
+            cp_async16(halo_s + hlf * kTcPlane + sl * 16, X + vox * Cxs + c0 + 8 * hlf);
+        }
+        // weights of the slice: piece (tap, half, co) <- W[co][tap][c0 + 8 half .. +8]
+        const int npieces = 27 * 2 * Cout;
+        for (int e = tid; e < npieces; e += kConvThreads) {
+            const int co = e % Cout, hlf = (e / Cout) & 1, tap = e / (2 * Cout);
+            cp_async16(w_s + e * 16, Wt + (static_cast<size_t>(co) * 27 + tap) * Cin + c0 + 8 * hlf);
+        }
+        cp_async_wait();
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (tid == 0) {
+#pragma unroll 1
+            for (int tap = 0; tap < 27; ++tap) {
+                const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+                const uint32_t a_addr = halo_s + ((kd * kTcHaloH + kh) * kTcHaloW + kw) * 16;
+                const uint64_t ad = umma_desc(a_addr, kTcPlane, kTcHaloW * 16);
+                const uint64_t bd = umma_desc(w_s + tap * 2 * Cout * 16, Cout * 16, 128);
+                const uint32_t accum = (c > 0 || tap > 0) ? 1u : 0u;
+                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+                             "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_s)
+                         : "memory");
+        }
+    }
+    if (ok) ok = mbar_wait(mbar_s, (nchunks - 1) & 1);
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) {
+        if (lane == 0) atomicAdd(err, 1);
+    } else {
+        // epilogue: warp w owns TMEM lanes 32w..32w+31 = brick rows m = 32w + lane
+        const int m = 32 * warp + lane;
+        const int eh = m / kTcBW, ew = m % kTcBW;
+        const size_t vox = ((static_cast<size_t>(b) * v.D + d0) * v.H + h0 + eh) * v.W + w0 + ew;
+        __nv_bfloat16* yrow = Y + vox * Cys;
+        for (int c0 = 0; c0 < Cout; c0 += 16) {
+            uint32_t q[16];
+            const uint32_t ta = tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                         "[%16];"
+                         : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+                           "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+                           "=r"(q[14]), "=r"(q[15])
+                         : "r"(ta));
+            asm volatile("tcgen05.wait::ld.sync.aligned;");
+            V8 o0, o1;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                float y0 = __uint_as_float(q[j]), y1 = __uint_as_float(q[8 + j]);
+                if (bias) {
+                    y0 += __ldg(bias + c0 + j);
+                    y1 += __ldg(bias + c0 + 8 + j);
+                }
+                if (act) {
+                    y0 = y0 > 0.f ? y0 : slope * y0;
+                    y1 = y1 > 0.f ? y1 : slope * y1;
+                }
+                o0.f[j] = y0;
+                o1.f[j] = y1;
+            }
+            store8(yrow + c0, o0);
+            store8(yrow + c0 + 8, o1);
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
 }
 
 // Wgrad partials: P[pc][co][tap][ci] = sum over the chunk's voxels p of
@@ -305,34 +496,6 @@ __global__ void k_flip_weights(const __nv_bfloat16* __restrict__ W, int Cout, in
     const int tap = static_cast<int>((e / Cout) % 27);
     const int ci = static_cast<int>(e / (static_cast<size_t>(Cout) * 27));
     Wf[e] = W[(static_cast<size_t>(co) * 27 + (26 - tap)) * Cin + ci];
-}
-
-// 8 channels per thread (16 bytes) helpers
-struct V8 {
-    float f[8];
-};
-
-__device__ __forceinline__ V8 load8(const __nv_bfloat16* p)
-{
-    const uint4 u = *reinterpret_cast<const uint4*>(p);
-    const __nv_bfloat162* h = reinterpret_cast<const __nv_bfloat162*>(&u);
-    V8 r;
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-        const float2 f = __bfloat1622float2(h[q]);
-        r.f[2 * q] = f.x;
-        r.f[2 * q + 1] = f.y;
-    }
-    return r;
-}
-
-__device__ __forceinline__ void store8(__nv_bfloat16* p, const V8& r)
-{
-    uint4 u;
-    __nv_bfloat162* h = reinterpret_cast<__nv_bfloat162*>(&u);
-#pragma unroll
-    for (int q = 0; q < 4; ++q) h[q] = __floats2bfloat162_rn(r.f[2 * q], r.f[2 * q + 1]);
-    *reinterpret_cast<uint4*>(p) = u;
 }
 
 // coarse voxel index and channel group of element e (groups of 8 channels)
@@ -616,17 +779,43 @@ bool brick_for(int D, int H, int W, int* bd, int* bh, int* bw)
     return (d + 2) * (h + 2) * (w + 2) <= kHaloMax;
 }
 
+bool tc_eligible(int Cin, int Cout, int D, int H, int W)
+{
+    (void)D;
+    return H % kTcBH == 0 && W % kTcBW == 0 && Cin % 16 == 0 && Cout % 16 == 0 && Cout >= 16 && Cout <= 192;
+}
+
 cudaError_t conv3d(const void* X, int Cxs, int Cin, const void* Wt, const float* bias, float slope, int act,
                    void* Y, int Cys, int Cout, int B, int D, int H, int W, cudaStream_t st)
 {
-    int bd, bh, bw;
-    if (!brick_for(D, H, W, &bd, &bh, &bw)) return cudaErrorInvalidValue;
     const Vol v{B, D, H, W};
-    const Brick k{bd, bh, bw, D / bd, H / bh, W / bw};
-    const unsigned grid = static_cast<unsigned>(B * k.nd * k.nh * k.nw);
     auto x = static_cast<const __nv_bfloat16*>(X);
     auto w = static_cast<const __nv_bfloat16*>(Wt);
     auto y = static_cast<__nv_bfloat16*>(Y);
+    if (tc_eligible(Cin, Cout, D, H, W)) {
+        // tcgen05 path: bricks of 1 x 16 x 8 voxels, TMEM columns = next power of two >= Cout
+        uint32_t cols = 32;
+        while (cols < static_cast<uint32_t>(Cout)) cols <<= 1;
+        const size_t smem = 2 * static_cast<size_t>(kTcPlane) + 27 * 2 * static_cast<size_t>(Cout) * 16;
+        static bool attr_set = false;
+        if (!attr_set) {
+            // the largest case: Cout = 192 (halo planes + 27 taps x 2 halves x 192 x 16 B = 179 KB)
+            cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                 2 * kTcPlane + 27 * 2 * 192 * 16);
+            if (e != cudaSuccess) return e;
+            attr_set = true;
+        }
+        int* err = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tc_wait_errors);
+        if (e != cudaSuccess) return e;
+        const unsigned grid = static_cast<unsigned>(B * D * (H / kTcBH) * (W / kTcBW));
+        k_conv3d_tc<<<grid, kConvThreads, smem, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, Cout, cols, v, err);
+        return cudaGetLastError();
+    }
+    int bd, bh, bw;
+    if (!brick_for(D, H, W, &bd, &bh, &bw)) return cudaErrorInvalidValue;
+    const Brick k{bd, bh, bw, D / bd, H / bh, W / bw};
+    const unsigned grid = static_cast<unsigned>(B * k.nd * k.nh * k.nw);
     switch (Cout / 8) {
     case 2: k_conv3d<2><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
     case 4: k_conv3d<4><<<grid, kConvThreads, 0, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, v, k); break;
@@ -638,6 +827,17 @@ cudaError_t conv3d(const void* X, int Cxs, int Cin, const void* Wt, const float*
     default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
+}
+
+int read_tc_errors(bool reset)
+{
+    int n = 0;
+    if (cudaMemcpyFromSymbol(&n, g_tc_wait_errors, sizeof(int)) != cudaSuccess) return -1;
+    if (reset) {
+        const int z = 0;
+        if (cudaMemcpyToSymbol(g_tc_wait_errors, &z, sizeof(int)) != cudaSuccess) return -1;
+    }
+    return n;
 }
 
 cudaError_t flip_weights(const void* W, int Cout, int Cin, void* Wf, cudaStream_t st)
@@ -889,7 +1089,7 @@ extern "C" claire_status claire_net_conv3d(const void* x, int x_stride, int cin,
     if (cin % 16 || cout % 8 || !nt_ok)
         return net_fail("conv3d: cin %d (multiple of 16), cout %d (16, 32, 48, 64, 96, 128 or 192)", cin, cout);
     int bd, bh, bw;
-    if (!brick_for(vol[1], vol[2], vol[3], &bd, &bh, &bw))
+    if (!tc_eligible(cin, cout, vol[1], vol[2], vol[3]) && !brick_for(vol[1], vol[2], vol[3], &bd, &bh, &bw))
         return net_fail("conv3d: grid %dx%dx%d has fewer than 64 voxels", vol[1], vol[2], vol[3]);
     if (act != 0 && act != 1) return net_fail("conv3d: act %d", act);
     return net_status(conv3d(x, x_stride, cin, w, bias, slope, act, y, y_stride, cout, vol[0], vol[1], vol[2],
@@ -1051,4 +1251,13 @@ extern "C" claire_status claire_net_residual(const float* x, const float* y, siz
 {
     if (!x || !y) return net_fail("residual: null pointer");
     return net_status(residual(x, y, n, r, sum, device_sms(), as_stream(stream)), "residual");
+}
+
+extern "C" claire_status claire_net_device_errors(int* count, int reset)
+{
+    if (!count) return net_fail("device_errors: null pointer");
+    const int n = read_tc_errors(reset != 0);
+    if (n < 0) return net_status(cudaErrorUnknown, "device_errors");
+    *count = n;
+    return CLAIRE_OK;
 }

@@ -162,7 +162,7 @@ __device__ __forceinline__ unsigned long long fixed_term(double wab, float wc)
 // kScatterCap nodes fall back to global atomics.  Integer sums do not depend
 // on the order of additions, so either path gives the same bits.
 constexpr int kST1 = 4, kST2 = 8, kST3 = 32;
-constexpr int kScatterCap = 6144;  // 48 KB of 64-bit accumulators
+constexpr int kScatterCap = 6112;  // 64-bit accumulators: with the static arrays, within 48 KB
 
 template <int ORDER>
 __global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float* __restrict__ yv,

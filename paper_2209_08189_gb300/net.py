@@ -46,6 +46,7 @@ _SIGS = {
     "claire_net_adam": [_vp, _vp, _vp, _vp, _sz, _f, _f, _f, _f, _i, _f, _vp, _vp],
     "claire_net_vel_loss": [_vp, _vp, _vp, _f, _f, _sz, _vp, _vp, _vp],
     "claire_net_residual": [_vp, _vp, _sz, _vp, _vp, _vp],
+    "claire_net_device_errors": [_ip, _i],
     "claire_net_last_error": [],
 }
 _RESTYPE = {"claire_net_last_error": ctypes.c_char_p}
@@ -72,6 +73,13 @@ def _check(status, what):
     if status < 0:
         raise NetError("%s: %s (%s)" % (what, _c.STATUS_NAMES.get(status, status),
                                         lib().claire_net_last_error().decode()))
+
+
+def device_errors(reset=True):
+    """tcgen05 completion waits that gave up (0 in a healthy run)."""
+    n = ctypes.c_int()
+    _check(lib().claire_net_device_errors(ctypes.byref(n), int(bool(reset))), "device_errors")
+    return n.value
 
 
 def _addr(t):

@@ -65,6 +65,12 @@ CONV_CASES = [
     (3, 8, 4, 8, 48, 96, 8, 0),
     (1, 8, 8, 8, 128, 128, 0, 0),
     (1, 4, 8, 16, 96, 192, 0, 0),
+    # H a multiple of 16 and W of 8: the tcgen05 kernel (TMEM accumulators)
+    (1, 4, 16, 8, 16, 16, 0, 0),
+    (2, 4, 16, 16, 32, 48, 16, 8),
+    (1, 4, 32, 16, 192, 64, 0, 0),
+    (1, 4, 16, 8, 96, 192, 0, 0),
+    (1, 8, 16, 32, 128, 128, 0, 0),
 ]
 
 
@@ -96,6 +102,7 @@ def test_conv3d_forward_and_input_gradient(env, case):
         net.conv3d(net.Act(dy, 0, co), wf, None, net.Act(dx, 0, ci), 0.0, 0, stream(torch))
         torch.cuda.synchronize()
         assert close_bf16(f64(dx), onet.conv3d_input_grad(f64(dy), f64(w))) <= 0
+    assert net.device_errors() == 0
 
 
 @pytest.mark.parametrize("case", CONV_CASES)

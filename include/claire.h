@@ -338,6 +338,66 @@ claire_status claire_kernel_stats(claire_ctx* ctx, claire_kernel_stat* out, int 
 /* Turn per-launch CUDA-event timing on (1) or off (0) after creation. */
 claire_status claire_set_timing(claire_ctx* ctx, int on);
 
+/* Change the regularisation weights of a live context (beta_v > 0,
+ * beta_w >= 0); clears the linearisation point. */
+claire_status claire_set_beta(claire_ctx* ctx, double beta_v, double beta_w);
+claire_status claire_get_beta(const claire_ctx* ctx, double* beta_v, double* beta_w);
+
+/*
+ * Regularisation-parameter search and continuation (Sec. 3, "Parameter
+ * identification").  Every solve is a claire_register warm-started from the
+ * last accepted velocity; a solve is valid when it returns a non-negative
+ * status and det grad y stays within [jmin, 1/jmin].
+ *
+ * Search: (i) beta_w = beta_w_max; beta_v = beta_v_max, divided by 10 after
+ * every valid solve until a solve breaches the bounds (or beta_v would fall
+ * below beta_v_min); then bisection (arithmetic midpoints) between the last
+ * valid and the breaching beta_v until their gap is below bisect_rtol times
+ * the valid one: beta_v* is the smallest valid value seen.  (ii) beta_v =
+ * beta_v*; beta_w divided by 10 while the solve stays valid and beta_w >=
+ * beta_w_min: beta_w* is the last valid value.
+ * Continuation: beta_v = beta_v_max, /10 down to 10^ceil(log10 target_v),
+ * then target_v (beta_w = beta_w_max); then beta_w /10 steps from
+ * beta_w_max down to target_w; no bounds are checked.
+ *
+ * v_inout: initial guess in (host or device, 3N floats), velocity of the
+ * last accepted solve out; the context keeps the selected (search) or target
+ * (continuation) weights.  Two 3N-float device vectors are allocated for the
+ * duration of the call.  Returns the status of the last accepted solve
+ * (CLAIRE_ENOTCONVERGED if even beta_v_max breaches the bounds, with that
+ * solve's velocity), or a negative status if a solve fails.
+ */
+typedef struct claire_search_opts {
+    double beta_v_max;   /* default 1 */
+    double beta_v_min;   /* default 1e-5 */
+    double beta_w_max;   /* default 1e-5 */
+    double beta_w_min;   /* default 1e-7 */
+    double jmin;         /* default 0.1 (bounds [0.1, 10]) */
+    double bisect_rtol;  /* default 0.1 */
+    int max_solves;      /* cap on registrations; default 40 */
+} claire_search_opts;
+
+#define CLAIRE_MAX_SEARCH_SOLVES 64
+typedef struct claire_search_report {
+    double beta_v, beta_w;         /* selected / final weights */
+    int solves;                    /* registrations run */
+    double trace_beta_v[CLAIRE_MAX_SEARCH_SOLVES];
+    double trace_beta_w[CLAIRE_MAX_SEARCH_SOLVES];
+    double trace_detj_min[CLAIRE_MAX_SEARCH_SOLVES];
+    double trace_detj_max[CLAIRE_MAX_SEARCH_SOLVES];
+    int trace_valid[CLAIRE_MAX_SEARCH_SOLVES];
+    int trace_gn_iters[CLAIRE_MAX_SEARCH_SOLVES];
+    double t_total_s;
+    claire_report last;            /* report of the accepted solve whose velocity is returned */
+} claire_search_report;
+
+claire_status claire_default_search_opts(claire_search_opts* opts);
+claire_status claire_param_search(claire_ctx* ctx, float* v_inout, const claire_search_opts* opts,
+                                  claire_search_report* rep);
+claire_status claire_param_continuation(claire_ctx* ctx, float* v_inout, double target_beta_v,
+                                        double target_beta_w, const claire_search_opts* opts,
+                                        claire_search_report* rep);
+
 /* Replace the options of an existing context (e.g. gtol, max_gn, g0_ref
  * between solves).  storage is fixed at claire_create: a different value is
  * CLAIRE_EINVAL; invalid options are CLAIRE_EINVAL and leave the context

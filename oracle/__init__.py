@@ -45,7 +45,7 @@ __all__ = [
     "characteristics", "forward_solve", "adjoint_solve", "state_at", "objective",
     "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
     "transport", "transport_vjp", "interp_grad", "deformation_map", "detj", "cfl", "inner",
-    "num_threads",
+    "num_threads", "param_search", "param_continuation",
 ]
 
 _lib = None
@@ -592,3 +592,88 @@ def cfl(v, p: Params):
     """CFL number: max over x of |v(x)|_2 * dt / min_c h_c."""
     v = _f64(v)
     return float(np.sqrt(np.max(np.sum(v * v, axis=0))) * p.dt / np.min(spacing(v.shape[1:])))
+
+
+# ---------------------------------------------------------------------------
+# Regularisation-parameter search and continuation (Sec. 3, "Parameter
+# identification"), on top of register()
+# ---------------------------------------------------------------------------
+
+def _valid_solve(m0, m1, p, bv, bw, v0, jmin, check):
+    from dataclasses import replace
+    q = replace(p, beta_v=bv, beta_w=bw)
+    v, rep = register(m0, m1, q, v0=v0)
+    dj = detj(v, q)
+    ok = rep["status"] != "line_search_failed" and (not check or (dj.min() >= jmin and dj.max() <= 1.0 / jmin))
+    return v, ok, (float(dj.min()), float(dj.max()))
+
+
+def param_search(m0, m1, p: Params, beta_v_max=1.0, beta_v_min=1e-5, beta_w_max=1e-5, beta_w_min=1e-7,
+                 jmin=0.1, bisect_rtol=0.1, max_solves=40, v0=None):
+    """Two-stage search of the paper: (i) beta_w = beta_w_max, beta_v from
+    beta_v_max down by factors of 10 until the Jacobian bounds [jmin, 1/jmin]
+    are breached, then bisection (arithmetic midpoints) between the last
+    valid and the breaching value until their gap is below bisect_rtol times
+    the valid one; (ii) beta_w down by factors of 10 while valid.  Every
+    solve starts from the last valid velocity.  Returns (beta_v*, beta_w*,
+    v, trace of (beta_v, beta_w, valid))."""
+    n = m0.shape
+    valid_v = np.zeros((3,) + n) if v0 is None else _f64(v0)
+    trace = []
+    bw, bv = beta_w_max, beta_v_max
+    hi = lo = None
+    while len(trace) < max_solves:
+        v, ok, _ = _valid_solve(m0, m1, p, bv, bw, valid_v, jmin, True)
+        trace.append((bv, bw, ok))
+        if not ok:
+            lo = bv
+            break
+        hi, valid_v = bv, v
+        if bv / 10.0 < beta_v_min:
+            break
+        bv /= 10.0
+    if hi is None:
+        return beta_v_max, bw, v, trace
+    if lo is not None:
+        while len(trace) < max_solves and (hi - lo) > bisect_rtol * hi:
+            mid = 0.5 * (hi + lo)
+            v, ok, _ = _valid_solve(m0, m1, p, mid, bw, valid_v, jmin, True)
+            trace.append((mid, bw, ok))
+            if ok:
+                hi, valid_v = mid, v
+            else:
+                lo = mid
+    bw_star = bw
+    while len(trace) < max_solves and bw_star / 10.0 >= beta_w_min and bw_star > 0:
+        v, ok, _ = _valid_solve(m0, m1, p, hi, bw_star / 10.0, valid_v, jmin, True)
+        trace.append((hi, bw_star / 10.0, ok))
+        if not ok:
+            break
+        bw_star /= 10.0
+        valid_v = v
+    return hi, bw_star, valid_v, trace
+
+
+def param_continuation(m0, m1, p: Params, target_beta_v, target_beta_w, beta_v_max=1.0, beta_w_max=1e-5,
+                       v0=None):
+    """beta_v = beta_v_max, /10, ..., 10^ceil(log10 target), then the target
+    (beta_w = beta_w_max); then beta_w /10 down to the target.  Each solve
+    starts from the previous one.  Returns (v, list of (beta_v, beta_w))."""
+    n = m0.shape
+    v = np.zeros((3,) + n) if v0 is None else _f64(v0)
+    bw0 = max(beta_w_max, target_beta_w)
+    stop = 10.0 ** math.ceil(math.log10(target_beta_v))
+    steps = []
+    bv = beta_v_max
+    while bv >= stop * (1 - 1e-12):
+        steps.append((bv, bw0))
+        bv /= 10.0
+    if abs(stop - target_beta_v) > 1e-12 * target_beta_v:
+        steps.append((target_beta_v, bw0))
+    bw = bw0 / 10.0
+    while bw >= target_beta_w * (1 - 1e-12):
+        steps.append((target_beta_v, bw))
+        bw /= 10.0
+    for bv, bw in steps:
+        v, _, _ = _valid_solve(m0, m1, p, bv, bw, v, 0.1, False)
+    return v, steps

@@ -17,7 +17,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libclaire.so")
-UNITS = ["sl_kernels.cu", "vec_kernels.cu", "engine.cu", "vjp.cu", "net_kernels.cu", "resample.cu", "noalloc.cu"]
+UNITS = ["sl_kernels.cu", "vec_kernels.cu", "engine.cu", "vjp.cu", "net_kernels.cu", "resample.cu", "search.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

@@ -82,6 +82,35 @@ class claire_kernel_stat(ctypes.Structure):
 
 
 _lib = None
+class claire_search_opts(ctypes.Structure):
+    _fields_ = [("beta_v_max", ctypes.c_double), ("beta_v_min", ctypes.c_double),
+                ("beta_w_max", ctypes.c_double), ("beta_w_min", ctypes.c_double),
+                ("jmin", ctypes.c_double), ("bisect_rtol", ctypes.c_double), ("max_solves", ctypes.c_int)]
+
+
+MAX_SEARCH_SOLVES = 64
+
+
+class claire_search_report(ctypes.Structure):
+    _fields_ = [("beta_v", ctypes.c_double), ("beta_w", ctypes.c_double), ("solves", ctypes.c_int),
+                ("trace_beta_v", ctypes.c_double * MAX_SEARCH_SOLVES),
+                ("trace_beta_w", ctypes.c_double * MAX_SEARCH_SOLVES),
+                ("trace_detj_min", ctypes.c_double * MAX_SEARCH_SOLVES),
+                ("trace_detj_max", ctypes.c_double * MAX_SEARCH_SOLVES),
+                ("trace_valid", ctypes.c_int * MAX_SEARCH_SOLVES),
+                ("trace_gn_iters", ctypes.c_int * MAX_SEARCH_SOLVES),
+                ("t_total_s", ctypes.c_double), ("last", claire_report)]
+
+    def as_dict(self):
+        n = min(self.solves, MAX_SEARCH_SOLVES)
+        return {"beta_v": self.beta_v, "beta_w": self.beta_w, "solves": self.solves,
+                "trace": [{"beta_v": self.trace_beta_v[i], "beta_w": self.trace_beta_w[i],
+                           "detj_min": self.trace_detj_min[i], "detj_max": self.trace_detj_max[i],
+                           "valid": bool(self.trace_valid[i]), "gn_iters": self.trace_gn_iters[i]}
+                          for i in range(n)],
+                "t_total_s": self.t_total_s, "last": self.last.as_dict()}
+
+
 _vp = ctypes.c_void_p
 _ST = ctypes.c_int
 
@@ -105,6 +134,12 @@ _SIGS = {
     "claire_transport_vjp": [_vp, _vp, _vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_resample_release": [],
     "claire_set_opts": [_vp, ctypes.POINTER(claire_opts)],
+    "claire_set_beta": [_vp, ctypes.c_double, ctypes.c_double],
+    "claire_get_beta": [_vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
+    "claire_default_search_opts": [ctypes.POINTER(claire_search_opts)],
+    "claire_param_search": [_vp, _vp, ctypes.POINTER(claire_search_opts), ctypes.POINTER(claire_search_report)],
+    "claire_param_continuation": [_vp, _vp, ctypes.c_double, ctypes.c_double, ctypes.POINTER(claire_search_opts),
+                                  ctypes.POINTER(claire_search_report)],
     "claire_get_opts": [_vp, ctypes.POINTER(claire_opts)],
     "claire_resample": [_vp, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                         ctypes.c_int, _vp],
@@ -261,6 +296,40 @@ def claire_set_opts(ctx, opts):
     return _check(ctx, lib().claire_set_opts(ctx, ctypes.byref(opts)))
 
 
+def claire_set_beta(ctx, beta_v, beta_w):
+    return _check(ctx, lib().claire_set_beta(ctx, float(beta_v), float(beta_w)))
+
+
+def claire_get_beta(ctx):
+    bv, bw = ctypes.c_double(), ctypes.c_double()
+    _check(ctx, lib().claire_get_beta(ctx, ctypes.byref(bv), ctypes.byref(bw)))
+    return bv.value, bw.value
+
+
+def claire_default_search_opts(**kw):
+    o = claire_search_opts()
+    _check(None, lib().claire_default_search_opts(ctypes.byref(o)))
+    for k, v in kw.items():
+        if not hasattr(o, k):
+            raise TypeError("unknown search option %r" % k)
+        setattr(o, k, v)
+    return o
+
+
+def claire_param_search(ctx, v_inout, opts=None):
+    rep = claire_search_report()
+    st = _check(ctx, lib().claire_param_search(ctx, _ptr(v_inout), ctypes.byref(opts) if opts else None,
+                                               ctypes.byref(rep)))
+    return st, rep.as_dict()
+
+
+def claire_param_continuation(ctx, v_inout, target_beta_v, target_beta_w, opts=None):
+    rep = claire_search_report()
+    st = _check(ctx, lib().claire_param_continuation(ctx, _ptr(v_inout), float(target_beta_v), float(target_beta_w),
+                                                     ctypes.byref(opts) if opts else None, ctypes.byref(rep)))
+    return st, rep.as_dict()
+
+
 def claire_get_opts(ctx):
     o = claire_opts()
     _check(ctx, lib().claire_get_opts(ctx, ctypes.byref(o)))
@@ -361,6 +430,16 @@ class Context:
 
     def set_stream(self, stream_handle):
         claire_set_stream(self.handle, stream_handle)
+
+    def set_beta(self, beta_v, beta_w):
+        claire_set_beta(self.handle, beta_v, beta_w)
+
+    def param_search(self, v_inout, **search_opts):
+        return claire_param_search(self.handle, v_inout, claire_default_search_opts(**search_opts))
+
+    def param_continuation(self, v_inout, target_beta_v, target_beta_w, **search_opts):
+        return claire_param_continuation(self.handle, v_inout, target_beta_v, target_beta_w,
+                                         claire_default_search_opts(**search_opts))
 
     def set_opts(self, **opts):
         """Change options of the live context (storage excluded)."""

@@ -1465,6 +1465,26 @@ claire_status claire_set_opts(claire_ctx* c, const claire_opts* opts)
     return CLAIRE_OK;
 }
 
+claire_status claire_set_beta(claire_ctx* c, double beta_v, double beta_w)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!(beta_v > 0) || !(beta_w >= 0)) return fail(c, CLAIRE_EINVAL, "beta_v must be > 0 and beta_w >= 0");
+    c->beta_v = beta_v;
+    c->rp.beta_v = static_cast<float>(beta_v);
+    c->o.beta_w = beta_w;
+    c->rp.beta_w = static_cast<float>(beta_w);
+    c->have_lin = false;
+    return CLAIRE_OK;
+}
+
+claire_status claire_get_beta(const claire_ctx* c, double* beta_v, double* beta_w)
+{
+    if (!c || !beta_v || !beta_w) return CLAIRE_EINVAL;
+    *beta_v = c->beta_v;
+    *beta_w = c->o.beta_w;
+    return CLAIRE_OK;
+}
+
 claire_status claire_get_opts(const claire_ctx* c, claire_opts* opts)
 {
     if (!c || !opts) return CLAIRE_EINVAL;
@@ -1479,3 +1499,9 @@ const char* claire_last_error(const claire_ctx* c)
 }
 
 }  // extern "C"
+
+namespace claire {
+cudaStream_t ctx_stream(const claire_ctx* c) { return c->stream; }
+size_t ctx_points(const claire_ctx* c) { return c->N; }
+claire_status ctx_fail(claire_ctx* c, claire_status st, const char* msg) { return fail(c, st, "%s", msg); }
+}  // namespace claire

@@ -8,6 +8,7 @@
 #include <cstddef>
 #include <cstdint>
 
+#include "claire.h"
 #include "common.cuh"
 
 namespace claire {
@@ -105,6 +106,11 @@ void launch_fd8_grad(const Grid& g, const void* f, void* out, Storage sto, cudaS
 void launch_fd8_div(const Grid& g, const float* v, void* out, Storage sto, cudaStream_t st);
 void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pmax, int nblocks,
                         cudaStream_t st);
+
+// ---- context accessors for host-side drivers in other units (engine.cu) ----
+cudaStream_t ctx_stream(const claire_ctx* c);
+size_t ctx_points(const claire_ctx* c);
+claire_status ctx_fail(claire_ctx* c, claire_status st, const char* msg);
 
 // ---- reverse-mode transport (vjp.cu) ----
 // dbar_c += mbar * d_c I[m](X)   (interpolant gradient at x + d, grid units)

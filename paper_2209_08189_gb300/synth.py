@@ -20,6 +20,16 @@ Recipes (all float64, seeded with numpy's PCG64):
   intensities 0.2 / 0.5 / 0.8 / 1.0 on a zero background, smoothed by a
   periodic Gaussian of sigma = 1 voxel (separable, direct convolution).
 * ``add_noise``: additive N(0, sigma^2) noise.
+* ``syn_template`` / ``syn_velocity``: the paper's SYN recipe (Sec. 4,
+  "SYN"): m0 is the sum of 10 indicator functions of star-shaped regions
+  |x - x_i| <= |Y_l^m(theta + dtheta_i, phi + dphi_i)| (l = 8, m = 6;
+  offsets x_i in [-0.4 pi, 0.4 pi]^3; angle perturbations in multiples of
+  pi/2), so intensities are the integer overlap counts 0..10; the velocity is
+  v_x = sum_k k^-1/2 cos(k y) cos(k x), v_y = sum_k k^-1/2 sin(k z) sin(k y),
+  v_z = sum_k k^-1/2 cos(k x) cos(k z), k = 1..K.  Coordinates are the
+  paper's (-pi, pi]^3 = our [0, 2 pi)^3 shifted by pi.  Reading of the
+  garbled angle ranges: theta is the azimuth (the argument of e^{i m theta}),
+  phi the polar angle (the argument of P_l^m(cos phi)).
 * ``sphere_template``: three nested spheres (radii 2.0 / 1.4 / 0.8 scaled
   per axis by U[0.9, 1.1], centre pi + U[-0.2, 0.2]) with smooth edges
   (tanh, width 1.5 voxels) and intensities 0.3 / 0.6 / 0.9, plus a blob
@@ -192,3 +202,69 @@ def sphere_template(n, seed=0, radii=(2.0, 1.4, 0.8), levels=(0.3, 0.6, 0.9), wi
     with concurrent.futures.ThreadPoolExecutor(max_workers=min(16, os.cpu_count() or 1)) as ex:
         list(ex.map(fill, range(0, n0, slab)))
     return m, lab
+
+
+def _assoc_legendre(l, m, x):
+    """P_l^m(x) with the Condon-Shortley phase, by the standard upward
+    recurrence in l from P_m^m = (-1)^m (2m-1)!! (1-x^2)^(m/2)."""
+    x = np.asarray(x, dtype=np.float64)
+    pmm = np.ones_like(x)
+    if m > 0:
+        somx2 = np.sqrt(np.maximum(0.0, 1.0 - x * x))
+        fact = 1.0
+        for _ in range(m):
+            pmm = -pmm * fact * somx2
+            fact += 2.0
+    if l == m:
+        return pmm
+    pmmp1 = x * (2 * m + 1) * pmm
+    if l == m + 1:
+        return pmmp1
+    pll = pmmp1
+    for ll in range(m + 2, l + 1):
+        pll = ((2 * ll - 1) * x * pmmp1 - (ll + m - 1) * pmm) / (ll - m)
+        pmm, pmmp1 = pmmp1, pll
+    return pll
+
+
+def syn_template(n, seed=0, l=8, m=6, count=10, slab=16):
+    """The paper's SYN template (see the module docstring): float32 overlap counts 0..count."""
+    rng = np.random.default_rng(seed)
+    n0, n1, n2 = (int(s) for s in n)
+    xs = [c - math.pi for c in coords(n)]  # (-pi, pi]-centred coordinates
+    norm = math.sqrt((2 * l + 1) / (4 * math.pi) * math.factorial(l - m) / math.factorial(l + m))
+    off = rng.uniform(-0.4 * math.pi, 0.4 * math.pi, size=(count, 3))
+    rng.integers(0, 4, size=count)  # the azimuth perturbations (no effect on |Y|), drawn for the seed sequence
+    dph = rng.integers(0, 4, size=count) * (math.pi / 2)
+    out = np.zeros((n0, n1, n2), dtype=np.float32)
+    for i0 in range(0, n0, slab):
+        x = xs[0][i0:i0 + slab][:, None, None]
+        y = xs[1][None, :, None]
+        z = xs[2][None, None, :]
+        acc = np.zeros((x.shape[0], n1, n2))
+        for i in range(count):
+            dx, dy, dz = x - off[i, 0], y - off[i, 1], z - off[i, 2]
+            r = np.sqrt(dx * dx + dy * dy + dz * dz)
+            # |Y_l^m(theta + dtheta, phi + dphi)| = norm |P_l^m(cos(phi + dphi))|:
+            # the azimuth enters only through |e^{i m theta}| = 1
+            phi = np.arccos(np.clip(dz / np.maximum(r, 1e-300), -1.0, 1.0)) + dph[i]
+            ylm = norm * np.abs(_assoc_legendre(l, m, np.cos(phi)))
+            acc += (r <= ylm)
+        out[i0:i0 + slab] = acc
+    return out
+
+
+def syn_velocity(n, K=4):
+    """The paper's SYN velocity (see the module docstring), float64 [3, n0, n1, n2]."""
+    xs = [c - math.pi for c in coords(n)]
+    x = xs[0][:, None, None]
+    y = xs[1][None, :, None]
+    z = xs[2][None, None, :]
+    shape = tuple(int(s) for s in n)
+    v = np.zeros((3,) + shape)
+    for k in range(1, K + 1):
+        a = k ** -0.5
+        v[0] += a * np.cos(k * y) * np.cos(k * x)
+        v[1] += a * np.sin(k * z) * np.sin(k * y)
+        v[2] += a * np.cos(k * x) * np.cos(k * z)
+    return v

@@ -637,3 +637,48 @@ def test_generators_deterministic():
     assert abs(np.sqrt(np.max(np.sum(v1 * v1, axis=0))) - 0.5) < 1e-12
     v2 = synth.bandlimited_velocity((16, 16, 16), seed=0, kmax=4, vmax=1.0)
     assert abs(np.sqrt(np.max(np.sum(v2 * v2, axis=0))) - 1.0) < 1e-12
+
+
+# ---------------------------------------------------------------------------
+# Regularisation-parameter search and continuation (Sec. 3)
+# ---------------------------------------------------------------------------
+
+def _search_problem():
+    n = (16, 16, 16)
+    m0 = synth.blob_template(n, seed=3, sigma=0.6)
+    vs = synth.mode_velocity(n, seed=4, kmax=2, vmax=1.2)
+    p = oracle.Params(nt=4, beta_v=1e-2, beta_w=1e-4, gtol=5e-2, max_gn=10, max_pcg=10)
+    return m0, oracle.transport(m0, vs, p), p
+
+
+def test_param_search_follows_the_schedule():
+    """Decades of beta_v until the Jacobian bounds break, bisection between
+    the last valid and the breaching value down to 10 %, then decades of
+    beta_w while valid; the selected pair is valid."""
+    m0, m1, p = _search_problem()
+    bv, bw, v, trace = oracle.param_search(m0, m1, p, jmin=0.5, max_solves=20)
+    assert trace[0][:2] == (1.0, 1e-5)
+    k = 0
+    while trace[k][2]:  # stage (i): factors of 10 while valid
+        assert abs(trace[k + 1][0] - trace[k][0] / 10) < 1e-15
+        k += 1
+    hi, lo = trace[k - 1][0], trace[k][0]
+    k += 1
+    while k < len(trace) and trace[k][1] == 1e-5:  # bisection
+        assert abs(trace[k][0] - 0.5 * (hi + lo)) < 1e-15
+        hi, lo = (trace[k][0], lo) if trace[k][2] else (hi, trace[k][0])
+        k += 1
+    assert hi == bv and (hi - lo) <= 0.1 * hi
+    for tb, tw, ok in trace[k:]:  # stage (ii)
+        assert tb == bv and tw < 1e-5
+    q = oracle.Params(**{**p.__dict__, "beta_v": bv, "beta_w": bw})
+    dj = oracle.detj(v, q)
+    assert dj.min() >= 0.5 and dj.max() <= 2.0
+
+
+def test_param_continuation_steps():
+    m0, m1, p = _search_problem()
+    v, steps = oracle.param_continuation(m0, m1, p, 0.03, 1e-7)
+    assert steps == [(1.0, 1e-5), (0.1, 1e-5), (0.03, 1e-5), (0.03, 1e-6), (0.03, 1e-7)] or \
+        [(round(a, 12), round(b, 14)) for a, b in steps] == [(1.0, 1e-5), (0.1, 1e-5), (0.03, 1e-5), (0.03, 1e-6),
+                                                              (0.03, 1e-7)]

@@ -148,10 +148,13 @@ __device__ __forceinline__ void scatter_disp(const Grid& g, const float* __restr
     }
 }
 
-// Fixed-point contribution of y * w_a w_b w_c.
-__device__ __forceinline__ unsigned long long fixed_term(double wab, float wc)
+// Fixed-point contribution of (scale y w_a w_b) w_c: the product is formed in
+// FP32 (|value| <= 2^48 fits its exponent range; FP64 throughput is low on
+// this part) and rounded to the integer grid, so every term is a
+// deterministic integer and the sums do not depend on their order.
+__device__ __forceinline__ unsigned long long fixed_term(float wab, float wc)
 {
-    return static_cast<unsigned long long>(__double2ll_rn(wab * static_cast<double>(wc)));
+    return static_cast<unsigned long long>(__float2ll_rn(wab * wc));
 }
 
 // Scatter-transpose tiles: a CTA owns a 4 x 8 x 32 tile of source points
@@ -241,7 +244,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float*
         if (yy[q] == 0.0f) continue;
         const int i = i0 + q;
         DAxis<ORDER> a1x, a2x, a3x;
-        const double ys = scale * static_cast<double>(yy[q]);
+        const float ys = static_cast<float>(scale * static_cast<double>(yy[q]));
         if (mode == 1) {
             // box-relative stencil: unwrapped first node minus the box origin
             float t1, t2, t3;
@@ -256,7 +259,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float*
             for (int a = 0; a < M; ++a)
 #pragma unroll
                 for (int b = 0; b < M; ++b) {
-                    const double wab = ys * static_cast<double>(w1[a] * w2[b]);
+                    const float wab = ys * (w1[a] * w2[b]);
                     unsigned long long* row = sbox + ((r1 + a) * e2 + (r2 + b)) * e3 + r3;
 #pragma unroll
                     for (int c = 0; c < M; ++c) atomicAdd(row + c, fixed_term(wab, w3[c]));
@@ -269,7 +272,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float*
             for (int a = 0; a < M; ++a)
 #pragma unroll
                 for (int b = 0; b < M; ++b) {
-                    const double wab = ys * static_cast<double>(a1x.w[a] * a2x.w[b]);
+                    const float wab = ys * (a1x.w[a] * a2x.w[b]);
                     const size_t row = static_cast<size_t>(a1x.idx[a]) + a2x.idx[b];
 #pragma unroll
                     for (int c = 0; c < M; ++c) atomicAdd(acc + row + a3x.idx[c], fixed_term(wab, a3x.w[c]));

@@ -40,7 +40,7 @@ import numpy as np
 from . import build as _build
 
 __all__ = [
-    "Params", "spacing", "interp", "interp_points", "interp_T", "backtrace",
+    "Params", "spacing", "bspline_prefilter", "interp", "interp_points", "interp_T", "backtrace",
     "fd8_grad", "fd8_div", "reg_apply", "reg_inverse", "project_K", "reg_energy",
     "characteristics", "forward_solve", "adjoint_solve", "state_at", "objective",
     "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
@@ -62,7 +62,7 @@ def _load():
         lib.orc_interp_points.argtypes = [lp, dp, dp, ctypes.c_long, ctypes.c_int, dp]
         lib.orc_interp_transpose.argtypes = [lp, dp, dp, ctypes.c_int, dp]
         lib.orc_interp_grad.argtypes = [lp, dp, dp, ctypes.c_int, dp]
-        lib.orc_backtrace.argtypes = [lp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
+        lib.orc_backtrace.argtypes = [lp, dp, dp, ctypes.c_double, ctypes.c_int, ctypes.c_int, dp]
         lib.orc_fd8_grad.argtypes = [lp, dp, dp]
         lib.orc_fd8_div.argtypes = [lp, dp, dp]
         lib.orc_num_threads.restype = ctypes.c_int
@@ -79,6 +79,7 @@ def _n(shape):
 
 
 def _f64(a):
+    """float64, C-contiguous (the C kernels read raw pointers)."""
     return np.ascontiguousarray(a, dtype=np.float64)
 
 
@@ -105,13 +106,34 @@ def inner(a, b, n):
 # Pointwise kernels (C)
 # ----------------------------------------------------------------------------
 
+def bspline_prefilter(f):
+    """Cubic B-spline coefficients c of a periodic field f (Sec. 3, B-spline
+    interpolation): sum_j c_j beta(x_i - x_j) = f_i, solved in Fourier space,
+    where the sampled spline is the symbol prod_axes (2 + cos(k h)) / 3."""
+    f = _f64(f)
+    F = np.fft.fftn(f)
+    sym = np.ones(f.shape)
+    for ax, n in enumerate(f.shape):
+        k = np.fft.fftfreq(n, 1.0 / n)
+        s = (2.0 + np.cos(2.0 * math.pi * k / n)) / 3.0
+        shape = [1] * f.ndim
+        shape[ax] = n
+        sym = sym * s.reshape(shape)
+    return np.ascontiguousarray(np.real(np.fft.ifftn(F / sym)))
+
+
+def _coef(f, order):
+    return bspline_prefilter(f) if order == 4 else _f64(f)
+
+
 def interp(f, d, order=3):
     """f(x + d) at every grid node; d in grid units, shape (3, *f.shape).
 
-    Sec. 3 "IP kernel": cubic Lagrange (order 3, nodes floor-1..floor+2) or
+    Sec. 3 "IP kernel": cubic Lagrange (order 3, nodes floor-1..floor+2),
+    cubic B-spline on prefiltered coefficients (order 4, same nodes) or
     linear (order 1), periodic wrap.
     """
-    f = _f64(f); d = _f64(d)
+    f = _coef(f, order); d = _f64(d)
     out = np.empty_like(f)
     _load().orc_interp(_n(f.shape), _dp(f), _dp(d), int(order), _dp(out))
     return out
@@ -119,23 +141,24 @@ def interp(f, d, order=3):
 
 def interp_points(f, y, order=3):
     """Interpolant of f at explicit grid-unit points y, shape (3, M)."""
-    f = _f64(f); y = _f64(y)
+    f = _coef(f, order); y = _f64(y)
     out = np.empty(y.shape[1])
     _load().orc_interp_points(_n(f.shape), _dp(f), _dp(y), int(y.shape[1]), int(order), _dp(out))
     return out
 
 
 def interp_T(yv, d, order=3):
-    """Exact transpose of interp(., d): scatter of point values to nodes."""
+    """Exact transpose of interp(., d): scatter of point values to nodes
+    (for B-splines followed by the prefilter, which is symmetric)."""
     yv = _f64(yv); d = _f64(d)
     out = np.empty_like(yv)
     _load().orc_interp_transpose(_n(yv.shape), _dp(yv), _dp(d), int(order), _dp(out))
-    return out
+    return bspline_prefilter(out) if order == 4 else out
 
 
 def interp_grad(f, d, order=3):
     """Gradient of the interpolant of f at x + d (grid units), shape (3, *f.shape)."""
-    f = _f64(f); d = _f64(d)
+    f = _coef(f, order); d = _f64(d)
     out = np.empty((3,) + f.shape)
     _load().orc_interp_grad(_n(f.shape), _dp(f), _dp(d), int(order), _dp(out))
     return out
@@ -149,8 +172,9 @@ def backtrace(v, dt, sign=+1, order=3):
     """
     v = _f64(v)
     n = v.shape[1:]
+    vc = np.stack([bspline_prefilter(v[c]) for c in range(3)]) if order == 4 else v
     d = np.empty_like(v)
-    _load().orc_backtrace(_n(n), _dp(v), float(dt), int(sign), int(order), _dp(d))
+    _load().orc_backtrace(_n(n), _dp(v), _dp(np.ascontiguousarray(vc)), float(dt), int(sign), int(order), _dp(d))
     return d
 
 

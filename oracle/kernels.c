@@ -41,11 +41,38 @@ static long orc_wrap(long i, long n)
  * 1-D basis at fractional offset t in [0,1) from the cell's left node.
  * order 3: cubic Lagrange cardinal functions on the four nodes -1,0,1,2
  *          (l_a(t) = prod_{b != a} (t - s_b) / (s_a - s_b)).
+ * order 4: the uniform cubic B-spline beta(x) (x = t - s_a), beta(x) =
+ *          (4 - 6x^2 + 3|x|^3)/6 for |x| <= 1, (2 - |x|)^3/6 for 1 < |x| < 2,
+ *          on the same four nodes (applied to prefiltered coefficients).
  * order 1: linear hat functions on nodes 0,1.
  * Returns the number of nodes and fills node offsets and weights.
  */
+static double orc_bspline(double x)
+{
+    double a = fabs(x);
+    if (a <= 1.0) return (4.0 - 6.0 * a * a + 3.0 * a * a * a) / 6.0;
+    if (a < 2.0) return (2.0 - a) * (2.0 - a) * (2.0 - a) / 6.0;
+    return 0.0;
+}
+
+/* derivative of beta */
+static double orc_bspline_d(double x)
+{
+    double a = fabs(x), sg = x < 0 ? -1.0 : 1.0;
+    if (a <= 1.0) return sg * (-12.0 * a + 9.0 * a * a) / 6.0;
+    if (a < 2.0) return -sg * (2.0 - a) * (2.0 - a) / 2.0;
+    return 0.0;
+}
+
 static int orc_basis(int order, double t, long off[4], double w[4])
 {
+    if (order == 4) {
+        for (int a = 0; a < 4; ++a) {
+            off[a] = a - 1;
+            w[a] = orc_bspline(t - (double)(a - 1));
+        }
+        return 4;
+    }
     if (order == 3) {
         const double s[4] = {-1.0, 0.0, 1.0, 2.0};
         for (int a = 0; a < 4; ++a) {
@@ -69,6 +96,10 @@ static int orc_basis(int order, double t, long off[4], double w[4])
  * polynomial, prod rule over its factors; linear: -1, 1. */
 static void orc_basis_deriv(int order, double t, double dw[4])
 {
+    if (order == 4) {
+        for (int a = 0; a < 4; ++a) dw[a] = orc_bspline_d(t - (double)(a - 1));
+        return;
+    }
     if (order == 3) {
         const double s[4] = {-1.0, 0.0, 1.0, 2.0};
         for (int a = 0; a < 4; ++a) {
@@ -206,9 +237,10 @@ void orc_interp_transpose(const long n[3], const double *yv, const double *d, in
  *   sign = +1: X  = x - dt/2 [v(x) + v(x - dt v(x))]   (state / incremental state)
  *   sign = -1: X+ = x + dt/2 [v(x) + v(x + dt v(x))]   (adjoint solves)
  * The velocity at the predictor point is interpolated with the same scheme as
- * the transported fields.  Output: d = (X - x) / h per axis, grid units.
+ * the transported fields, from vc (v itself, or its B-spline coefficients for
+ * order 4).  Output: d = (X - x) / h per axis, grid units.
  */
-void orc_backtrace(const long n[3], const double *v, double dt, int sign, int order, double *d)
+void orc_backtrace(const long n[3], const double *v, const double *vc, double dt, int sign, int order, double *d)
 {
     const long N = n[0] * n[1] * n[2];
     double h[3];
@@ -223,7 +255,7 @@ void orc_backtrace(const long n[3], const double *v, double dt, int sign, int or
             ys[c] = x[c] - sign * dt * u0[c];
         }
         for (int c = 0; c < 3; ++c) {
-            double us = orc_interp_at(n, v + c * N, ys, order) / h[c];
+            double us = orc_interp_at(n, vc + c * N, ys, order) / h[c];
             d[c * N + p] = -sign * 0.5 * dt * (u0[c] + us);
         }
     }

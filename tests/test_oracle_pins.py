@@ -114,7 +114,7 @@ def test_interp_gradient_exact_on_polynomials(order, deg):
         assert np.max(np.abs(got[c] - dP[c](*Y))[ok]) < 1e-11
 
 
-@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("order", [3, 1, 4])
 def test_transport_vjp_matches_finite_differences(order):
     """The exact discrete VJP of nt SL steps (image and velocity cotangents)
     agrees with central differences of the discrete forward map."""
@@ -682,3 +682,55 @@ def test_param_continuation_steps():
     assert steps == [(1.0, 1e-5), (0.1, 1e-5), (0.03, 1e-5), (0.03, 1e-6), (0.03, 1e-7)] or \
         [(round(a, 12), round(b, 14)) for a, b in steps] == [(1.0, 1e-5), (0.1, 1e-5), (0.03, 1e-5), (0.03, 1e-6),
                                                               (0.03, 1e-7)]
+
+
+# ---------------------------------------------------------------------------
+# Cubic B-spline interpolation (Sec. 3, IP kernel alternative)
+# ---------------------------------------------------------------------------
+
+def test_bspline_interpolates_grid_values_and_shifts():
+    """Prefiltered B-spline interpolation returns the grid values at integer
+    displacements (interpolating spline), wrap included."""
+    rng = np.random.default_rng(11)
+    n = (8, 10, 12)
+    f = rng.standard_normal(n)
+    d = np.zeros((3,) + n)
+    d[0], d[1], d[2] = 2.0, -3.0, 5.0
+    ref = np.roll(f, shift=(-2, 3, -5), axis=(0, 1, 2))
+    assert np.max(np.abs(oracle.interp(f, d, 4) - ref)) < 1e-12
+
+
+def test_bspline_half_node_closed_form():
+    """At a half-node shift the interpolant of cos(k x1) is cos(k (x1 + h/2))
+    times R(k) = [23 cos(kh/2) + cos(3kh/2)] / 24 / ((2 + cos kh) / 3), from
+    beta(1/2) = 23/48 and beta(3/2) = 1/48 over the spline symbol."""
+    n = (16, 4, 4)
+    h = oracle.spacing(n)[0]
+    x1 = np.arange(n[0]) * h
+    for k in (1, 3, 5):
+        f = np.cos(k * x1)[:, None, None] * np.ones(n)
+        d = np.zeros((3,) + n)
+        d[0] = 0.5
+        R = (23 * math.cos(k * h / 2) + math.cos(3 * k * h / 2)) / 24.0 / ((2 + math.cos(k * h)) / 3.0)
+        ref = R * np.cos(k * (x1 + h / 2))[:, None, None] * np.ones(n)
+        assert np.max(np.abs(oracle.interp(f, d, 4) - ref)) < 1e-12
+
+
+def test_bspline_fourth_order_convergence_and_transpose():
+    errs = []
+    for N in (16, 32):
+        n = (N, 4, 4)
+        x1 = np.arange(N) * (2 * math.pi / N)
+        f = np.sin(2 * x1)[:, None, None] * np.ones(n)
+        d = np.zeros((3,) + n)
+        d[0] = 0.37
+        y = x1 + 0.37 * 2 * math.pi / N
+        errs.append(np.max(np.abs(oracle.interp(f, d, 4) - np.sin(2 * y)[:, None, None])))
+    assert 12 < errs[0] / errs[1] < 20
+    rng = np.random.default_rng(12)
+    n = (9, 8, 7)
+    d = rng.uniform(-3, 3, size=(3,) + n)
+    x = rng.standard_normal(n)
+    yv = rng.standard_normal(n)
+    lhs = np.sum(oracle.interp(x, d, 4) * yv)
+    assert abs(lhs - np.sum(x * oracle.interp_T(yv, d, 4))) < 1e-11 * max(1.0, abs(lhs))

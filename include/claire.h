@@ -62,6 +62,12 @@ typedef enum {
 /* Interpolation order of the semi-Lagrangian gathers (Sec. 3, "IP kernel"). */
 #define CLAIRE_INTERP_CUBIC 3   /* cubic Lagrange, nodes floor-1 .. floor+2 */
 #define CLAIRE_INTERP_LINEAR 1  /* trilinear */
+#define CLAIRE_INTERP_BSPLINE 4 /* cubic B-spline on the same nodes, applied to the field's spline
+                                   coefficients (Sec. 3): every gathered field is prefiltered first
+                                   (forward FFT, division by the sampled spline's symbol
+                                   prod (2 + cos k h) / 3, inverse FFT), which needs FP32 storage and
+                                   adds 3N floats + 3 half spectra of scratch on first use; not
+                                   supported by claire_transport_vjp (CLAIRE_ENOTIMPL) */
 
 /* claire_transport flags */
 #define CLAIRE_TRANSPORT_FWD 0  /* state, Eq. (1b)-(1c): m(1) from m(0) */
@@ -73,7 +79,7 @@ typedef enum {
 #define CLAIRE_SPECTRAL_K   2   /* K b = b - c u (u . b) / (a + c |u|^2): the paper's K */
 
 typedef struct claire_opts {
-    int interp;          /* CLAIRE_INTERP_CUBIC (default) or CLAIRE_INTERP_LINEAR */
+    int interp;          /* CLAIRE_INTERP_CUBIC (default), CLAIRE_INTERP_LINEAR or CLAIRE_INTERP_BSPLINE */
     int reg;             /* 1 = H1 seminorm of v (default), 2 = H2 seminorm */
     double beta_w;       /* weight of the H1 norm of div v; default 1e-4 */
     int grad_form;       /* 0 = g = S v + b (default, exact gradient of J; H symmetric);
@@ -269,7 +275,8 @@ claire_status claire_detj(claire_ctx* ctx, const float* v, double* detj_min, dou
 
 /* ---- kernel-level entry points (device pointers only; ctx gives grid and stream) ---- */
 
-/* out[p] = f(x_p + d_p): f, out N floats, d 3N floats (grid units); order 3 or 1.
+/* out[p] = f(x_p + d_p): f, out N floats, d 3N floats (grid units); order 3, 1 or 4
+ * (CLAIRE_INTERP_BSPLINE: f is prefiltered into the context's scratch first).
  * Sec. 3 "IP kernel". */
 claire_status claire_interp(claire_ctx* ctx, const float* f, const float* d, float* out, int order);
 

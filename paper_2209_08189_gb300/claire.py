@@ -23,7 +23,7 @@ STATUS_NAMES = {0: "CLAIRE_OK", 1: "CLAIRE_ENOTCONVERGED", -1: "CLAIRE_EINVAL",
                 -2: "CLAIRE_ENOMEM", -3: "CLAIRE_ECUDA", -4: "CLAIRE_ECUFFT",
                 -5: "CLAIRE_ENONFINITE", -6: "CLAIRE_ELINESEARCH", -7: "CLAIRE_ETIMEOUT",
                 -8: "CLAIRE_ESTATE", -9: "CLAIRE_ENOTIMPL", -10: "CLAIRE_ETOOLARGE"}
-INTERP_CUBIC, INTERP_LINEAR = 3, 1
+INTERP_CUBIC, INTERP_LINEAR, INTERP_BSPLINE = 3, 1, 4
 TRANSPORT_FWD, TRANSPORT_ADJ = 0, 1
 SPECTRAL_REG, SPECTRAL_INV, SPECTRAL_K = 0, 1, 2
 STORAGE_F32, STORAGE_F16, STORAGE_BF16 = 0, 1, 2

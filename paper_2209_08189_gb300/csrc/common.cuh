@@ -48,28 +48,55 @@ __device__ __forceinline__ void cubic_weights(float t, float w[4])
     w[3] = (1.0f / 6.0f) * tp1 * t_tm1;
 }
 
+// Uniform cubic B-spline basis on the nodes -1, 0, 1, 2 at t in [0,1)
+// (applied to prefiltered coefficients, not to the samples).
+__device__ __forceinline__ void bspline_weights(float t, float w[4])
+{
+    const float s = 1.0f - t, t2 = t * t, t3 = t2 * t;
+    w[0] = (1.0f / 6.0f) * s * s * s;
+    w[1] = (1.0f / 6.0f) * (3.0f * t3 - 6.0f * t2 + 4.0f);
+    w[2] = (1.0f / 6.0f) * (-3.0f * t3 + 3.0f * t2 + 3.0f * t + 1.0f);
+    w[3] = (1.0f / 6.0f) * t3;
+}
+
+// Interpolation schemes: ORDER 1 trilinear (nodes 0, 1), 3 cubic Lagrange
+// and 4 cubic B-spline (nodes -1..2).
+template <int ORDER>
+struct Scheme {
+    static constexpr int M = (ORDER == 1) ? 2 : 4;    // nodes per axis
+    static constexpr int OFF = (ORDER == 1) ? 0 : 1;  // first node below the cell
+};
+
+template <int ORDER>
+__device__ __forceinline__ void scheme_weights(float t, float w[4])
+{
+    if constexpr (ORDER == 3) {
+        cubic_weights(t, w);
+    } else if constexpr (ORDER == 4) {
+        bspline_weights(t, w);
+    } else {
+        w[0] = 1.0f - t;
+        w[1] = t;
+    }
+}
+
 // Stencil of one axis: wrapped node indices and weights.
 template <int ORDER>
 struct Axis {
-    static constexpr int M = (ORDER == 3) ? 4 : 2;
+    static constexpr int M = Scheme<ORDER>::M;
     int idx[M];
     float w[M];
     __device__ __forceinline__ void build(int node, float disp, int n)
     {
         float t;
-        int base = node + split_disp(disp, t) - (ORDER == 3 ? 1 : 0);
+        int base = node + split_disp(disp, t) - Scheme<ORDER>::OFF;
         int b = wrap_index(base, n);
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             int q = b + a;
             idx[a] = q >= n ? q - n : q;
         }
-        if constexpr (ORDER == 3) {
-            cubic_weights(t, w);
-        } else {
-            w[0] = 1.0f - t;
-            w[1] = t;
-        }
+        scheme_weights<ORDER>(t, w);
     }
 };
 

@@ -72,6 +72,12 @@ struct claire_ctx {
     cufftHandle r2c = 0, c2r = 0;
     bool plans = false;
     void* fft_work = nullptr;             // one work area shared by both plans
+    // cubic B-spline interpolation (interp = 4): coefficient scratch, its
+    // spectra and single-field plans, allocated on first use
+    float* bsc = nullptr;                 // 3N floats
+    cufftComplex* bspec = nullptr;        // 3M modes
+    cufftHandle r2c1 = 0, c2r1 = 0;
+    bool bs_plans = false;
     size_t fft_work_bytes = 0;
     std::string err;
 
@@ -130,6 +136,15 @@ struct claire_ctx {
         }
         if (fft_work) cudaFree(fft_work);
         fft_work = nullptr;
+        if (bs_plans) {
+            cufftDestroy(r2c1);
+            cufftDestroy(c2r1);
+            bs_plans = false;
+        }
+        if (bsc) cudaFree(bsc);
+        bsc = nullptr;
+        if (bspec) cudaFree(bspec);
+        bspec = nullptr;
         if (arena) cudaFree(arena);
         arena = nullptr;
         if (vjp_states) cudaFree(vjp_states);
@@ -217,7 +232,8 @@ void fill_defaults(claire_opts* o)
 
 bool valid_opts(const claire_opts& o)
 {
-    return (o.interp == 1 || o.interp == 3) && (o.reg == 1 || o.reg == 2) && o.beta_w >= 0 &&
+    return (o.interp == 1 || o.interp == 3 || o.interp == 4) && (o.reg == 1 || o.reg == 2) && o.beta_w >= 0 &&
+           (o.interp != 4 || o.storage == CLAIRE_STORAGE_F32) &&
            (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
            o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
            o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
@@ -427,18 +443,72 @@ claire_status fd8_grad(claire_ctx* c, const void* f, void* out, Storage sto)
     return CLAIRE_OK;
 }
 
+// Cubic B-spline coefficients of ncomp (1 or 3) FP32 fields f (Sec. 3:
+// B-spline interpolation acts on prefiltered coefficients): forward
+// transform, division by the sampled spline's symbol, inverse transform into
+// c->bsc.  Scratch and plans are allocated on first use.
+claire_status bspline_coef(claire_ctx* c, const float* f, int ncomp, const float** out)
+{
+    if (!c->bsc) {
+        CL_CUDA(c, cudaMalloc(&c->bsc, 3 * c->N * sizeof(float)));
+        CL_CUDA(c, cudaMalloc(&c->bspec, 3 * c->M * sizeof(cufftComplex)));
+    }
+    if (!c->bs_plans) {
+        CL_FFT(c, cufftPlan3d(&c->r2c1, c->n[0], c->n[1], c->n[2], CUFFT_R2C));
+        if (cufftPlan3d(&c->c2r1, c->n[0], c->n[1], c->n[2], CUFFT_C2R) != CUFFT_SUCCESS) {
+            cufftDestroy(c->r2c1);
+            return fail(c, CLAIRE_ECUFFT, "B-spline plans");
+        }
+        c->bs_plans = true;
+    }
+    cufftHandle fwd = ncomp == 3 ? c->r2c : c->r2c1, inv = ncomp == 3 ? c->c2r : c->c2r1;
+    CL_FFT(c, cufftSetStream(c->r2c1, c->stream));
+    CL_FFT(c, cufftSetStream(c->c2r1, c->stream));
+    {
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecR2C(fwd, const_cast<float*>(f), c->bspec));
+    }
+    {
+        KTimer t(c, KK_SPECTRAL, 16.0 * ncomp * c->M, 0);
+        launch_bspline_scale(c->grid, c->bspec, c->M, ncomp, c->stream);
+        CL_LAUNCHED(c);
+    }
+    {
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecC2R(inv, c->bspec, c->bsc));
+    }
+    *out = c->bsc;
+    return CLAIRE_OK;
+}
+
+// the field a gather reads: f itself, or its B-spline coefficients
+claire_status gather_src(claire_ctx* c, const void* f, int ncomp, const void** src)
+{
+    *src = f;
+    if (c->o.interp != 4) return CLAIRE_OK;
+    const float* coef;
+    CL_TRY(bspline_coef(c, static_cast<const float*>(f), ncomp, &coef));
+    *src = coef;
+    return CLAIRE_OK;
+}
+
 claire_status backtrace(claire_ctx* c, const float* v, float* d, int sign)
 {
+    const void* vc;
+    CL_TRY(gather_src(c, v, 3, &vc));
     KTimer t(c, KK_BACKTRACE, 24.0 * c->N, 3.0 * c->N);
-    launch_backtrace(c->grid, c->o.interp, v, static_cast<float>(c->dt), sign, d, c->stream);
+    launch_backtrace(c->grid, c->o.interp, v, static_cast<const float*>(vc), static_cast<float>(c->dt), sign, d,
+                     c->stream);
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
 
 claire_status interp(claire_ctx* c, const void* f, const float* d, void* out, Storage sto)
 {
+    const void* src;
+    CL_TRY(gather_src(c, f, 1, &src));
     KTimer t(c, KK_INTERP, (12.0 + 2.0 * storage_bytes(sto)) * c->N, 1.0 * c->N);
-    launch_interp(c->grid, c->o.interp, f, d, out, sto, c->stream);
+    launch_interp(c->grid, c->o.interp, src, d, out, sto, c->stream);
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
@@ -505,8 +575,10 @@ claire_status adjoint_and_body(claire_ctx* c, const void* a, const void* s, floa
         CL_LAUNCHED(c);
     }
     for (int j = nt - 1; j >= 0; --j) {
+        const void* src;
+        CL_TRY(gather_src(c, at(c, c->tl, (j + 1) * N), 1, &src));
         KTimer t(c, KK_ADJ_STEP, (12.0 + 4.0 * es) * N, 1.0 * N);
-        launch_adj_step(c->grid, c->o.interp, at(c, c->tl, (j + 1) * N), c->dA, c->divv, c->divXp,
+        launch_adj_step(c->grid, c->o.interp, src, c->dA, c->divv, c->divXp,
                         static_cast<float>(c->dt), at(c, c->tl, j * N), c->sto, c->stream);
         CL_LAUNCHED(c);
     }
@@ -578,14 +650,18 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
             CL_LAUNCHED(c);
         }
         for (int j = 0; j + 1 < nt; ++j) {
+            const void* src;
+            CL_TRY(gather_src(c, a, 1, &src));
             KTimer t(c, KK_INC_STEP, (12.0 + 3.0 * es) * N, 1.0 * N);
-            launch_inc_step_src(c->grid, c->o.interp, a, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
+            launch_inc_step_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
                                 c->stream);
             CL_LAUNCHED(c);
             std::swap(a, b);
         }
+        const void* src;
+        CL_TRY(gather_src(c, a, 1, &src));
         KTimer t(c, KK_INC_LAST, (12.0 + 3.0 * es) * N, 1.0 * N);
-        launch_inc_last_src(c->grid, c->o.interp, a, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
+        launch_inc_last_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
                             at(c, c->tl, nt * N), c->sto, c->stream);
         CL_LAUNCHED(c);
     }
@@ -649,8 +725,10 @@ claire_status detj_of(claire_ctx* c, const float* v, double* lo, double* hi)
     float* b = c->p;
     CL_CUDA(c, cudaMemsetAsync(a, 0, 3 * N * sizeof(float), c->stream));
     for (int j = 0; j < c->nt; ++j) {
+        const void* src;
+        CL_TRY(gather_src(c, a, 3, &src));
         KTimer t(c, KK_MAP, 36.0 * N, 3.0 * N);
-        launch_map_step(c->grid, c->o.interp, a, c->z, b, c->stream);
+        launch_map_step(c->grid, c->o.interp, static_cast<const float*>(src), c->z, b, c->stream);
         CL_LAUNCHED(c);
         std::swap(a, b);
     }
@@ -1217,8 +1295,10 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
         float* divXp = c->r + N;
         CL_TRY(characteristics(c, dv, nullptr, c->z, divv, divXp, Storage::F32));
         for (int j = 0; j < c->nt; ++j) {
+            const void* gs;
+            CL_TRY(gather_src(c, src, 1, &gs));
             KTimer t(c, KK_ADJ_STEP, 28.0 * N, 1.0 * N);
-            launch_adj_step(c->grid, c->o.interp, src, c->z, divv, divXp, static_cast<float>(c->dt), a,
+            launch_adj_step(c->grid, c->o.interp, gs, c->z, divv, divXp, static_cast<float>(c->dt), a,
                             Storage::F32, c->stream);
             CL_LAUNCHED(c);
             src = a;
@@ -1260,6 +1340,8 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
     if (!c) return CLAIRE_EINVAL;
     if (!v || !m0 || !gbar) return fail(c, CLAIRE_EINVAL, "null argument");
     if (flags & ~CLAIRE_VJP_RECOMPUTE) return fail(c, CLAIRE_EINVAL, "unknown flags %d", flags);
+    if (c->o.interp == 4)
+        return fail(c, CLAIRE_ENOTIMPL, "the reverse-mode transport supports linear and cubic Lagrange interpolation");
     const size_t N = c->N;
     const int nt = c->nt;
     const bool recompute = (flags & CLAIRE_VJP_RECOMPUTE) != 0;
@@ -1344,10 +1426,11 @@ claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
 claire_status claire_interp(claire_ctx* c, const float* f, const float* d, float* out, int order)
 {
     if (!c) return CLAIRE_EINVAL;
-    if (order != 1 && order != 3) return fail(c, CLAIRE_EINVAL, "order must be 1 or 3");
+    if (order != 1 && order != 3 && order != 4) return fail(c, CLAIRE_EINVAL, "order must be 1, 3 or 4");
     CL_TRY(check_kernel_ptr(c, f));
     CL_TRY(check_kernel_ptr(c, d));
     CL_TRY(check_kernel_ptr(c, out));
+    if (order == 4) CL_TRY(bspline_coef(c, f, 1, &f));
     {
         KTimer t(c, KK_INTERP, 20.0 * c->N, 1.0 * c->N);
         launch_interp(c->grid, order, f, d, out, Storage::F32, c->stream);

@@ -75,7 +75,7 @@ __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin,
 // vector work fields).
 void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
                    cudaStream_t st);
-void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
+void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
                       cudaStream_t st);
 // One SL step of Eq. (4): lam = Heun(lam_next(X+), div v(X+), div v).
 void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
@@ -111,6 +111,9 @@ void launch_detj_minmax(const Grid& g, const float* u, double* pmin, double* pma
 cudaStream_t ctx_stream(const claire_ctx* c);
 size_t ctx_points(const claire_ctx* c);
 claire_status ctx_fail(claire_ctx* c, claire_status st, const char* msg);
+
+// spectra of ncomp fields divided by N times the sampled cubic B-spline symbol (vec_kernels.cu)
+void launch_bspline_scale(const Grid& g, cufftComplex* spec, size_t M, int ncomp, cudaStream_t st);
 
 // ---- reverse-mode transport (vjp.cu) ----
 // dbar_c += mbar * d_c I[m](X)   (interpolant gradient at x + d, grid units)

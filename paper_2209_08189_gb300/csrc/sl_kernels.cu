@@ -6,6 +6,8 @@
 #include "internal.h"
 #include "sl_tiled.cuh"
 
+#include <type_traits>
+
 namespace claire {
 
 namespace {
@@ -21,8 +23,9 @@ inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
 // Heun characteristic: sign = +1 gives X = x - dt/2 [v(x) + v(x - dt v(x))],
 // sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))].  d in grid units.
 template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __restrict__ v, float dt,
-                                                         float sign, float* __restrict__ d)
+__global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __restrict__ v,
+                                                         const float* __restrict__ vc, float dt, float sign,
+                                                         float* __restrict__ d)
 {
     const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
     if (p >= g.N) return;
@@ -36,7 +39,7 @@ __global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __r
     Stencil<ORDER> s;
     s.build(g, i, j, k, -sdt * u1, -sdt * u2, -sdt * u3);
     float vs[3];
-    s.eval3(v, g.N, vs);
+    s.eval3(vc, g.N, vs);  // v itself, or its B-spline coefficients
     const float c = -0.5f * sdt;
     d[p] = c * (u1 + vs[0] * g.ih1);
     d[N + p] = c * (u2 + vs[1] * g.ih2);
@@ -294,8 +297,21 @@ __global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* _
     do {                                                                          \
         if ((order) == 3)                                                         \
             KERNEL<3><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
+        else if ((order) == 4)                                                    \
+            KERNEL<4><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
         else                                                                      \
             KERNEL<1><<<blocks_for(g.N), kThreads, 0, st>>>(__VA_ARGS__);         \
+    } while (0)
+
+// tiled gathers: cubic B-spline (order 4) only for FP32 fields
+#define CLAIRE_TILED(order, EPI, fs, d, e)                                        \
+    do {                                                                          \
+        if ((order) == 3)                                                         \
+            launch_tiled<3, EPI<SType>, SType>(g, fs, d, e, st);                  \
+        else if ((order) == 1)                                                    \
+            launch_tiled<1, EPI<SType>, SType>(g, fs, d, e, st);                  \
+        else if constexpr (std::is_same<SType, float>::value)                     \
+            launch_tiled<4, EPI<SType>, SType>(g, fs, d, e, st);                  \
     } while (0)
 
 void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
@@ -304,17 +320,14 @@ void launch_interp(const Grid& g, int order, const void* f, const float* d, void
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiStore<SType> e{static_cast<SType*>(out)};
         const SType* fs = static_cast<const SType*>(f);
-        if (order == 3)
-            launch_tiled<3, EpiStore<SType>, SType>(g, fs, d, e, st);
-        else
-            launch_tiled<1, EpiStore<SType>, SType>(g, fs, d, e, st);
+        CLAIRE_TILED(order, EpiStore, fs, d, e);
     });
 }
 
-void launch_backtrace(const Grid& g, int order, const float* v, float dt, int sign, float* d,
+void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
                       cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_backtrace, g, v, dt, static_cast<float>(sign), d);
+    CLAIRE_DISPATCH(order, k_backtrace, g, v, vc ? vc : v, dt, static_cast<float>(sign), d);
 }
 
 void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
@@ -324,10 +337,7 @@ void launch_adj_step(const Grid& g, int order, const void* lam_next, const float
         EpiAdjointOnly<SType> e{static_cast<const SType*>(divv), static_cast<const SType*>(divXp),
                                 static_cast<SType*>(lam), dt};
         const SType* fs = static_cast<const SType*>(lam_next);
-        if (order == 3)
-            launch_tiled<3, EpiAdjointOnly<SType>, SType>(g, fs, dA, e, st);
-        else
-            launch_tiled<1, EpiAdjointOnly<SType>, SType>(g, fs, dA, e, st);
+        CLAIRE_TILED(order, EpiAdjointOnly, fs, dA, e);
     });
 }
 
@@ -375,10 +385,7 @@ void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const flo
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiIncSource<SType> e{static_cast<const SType*>(F), static_cast<SType*>(q), coef};
         const SType* fs = static_cast<const SType*>(q_prev);
-        if (order == 3)
-            launch_tiled<3, EpiIncSource<SType>, SType>(g, fs, d, e, st);
-        else
-            launch_tiled<1, EpiIncSource<SType>, SType>(g, fs, d, e, st);
+        CLAIRE_TILED(order, EpiIncSource, fs, d, e);
     });
 }
 
@@ -388,10 +395,7 @@ void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const flo
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiIncSourceLast<SType> e{static_cast<const SType*>(F), static_cast<SType*>(lam), coef};
         const SType* fs = static_cast<const SType*>(q_prev);
-        if (order == 3)
-            launch_tiled<3, EpiIncSourceLast<SType>, SType>(g, fs, d, e, st);
-        else
-            launch_tiled<1, EpiIncSourceLast<SType>, SType>(g, fs, d, e, st);
+        CLAIRE_TILED(order, EpiIncSourceLast, fs, d, e);
     });
 }
 

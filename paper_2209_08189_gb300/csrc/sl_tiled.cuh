@@ -54,12 +54,7 @@ __device__ __forceinline__ void cp_async_wait_all()
 template <int ORDER>
 __device__ __forceinline__ void axis_weights(float t, float w[4])
 {
-    if constexpr (ORDER == 3) {
-        cubic_weights(t, w);
-    } else {
-        w[0] = 1.0f - t;
-        w[1] = t;
-    }
+    scheme_weights<ORDER>(t, w);
 }
 
 // Direct global-memory gather for tiles whose departure box does not fit
@@ -91,8 +86,8 @@ template <int ORDER, int ES = 4>
 __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
                                            int hi3, int (*red)[TILE2], int* par, int lane, int warp)
 {
-    constexpr int M = (ORDER == 3) ? 4 : 2;
-    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    constexpr int M = Scheme<ORDER>::M;
+    constexpr int OFF = Scheme<ORDER>::OFF;
     lo1 = __reduce_min_sync(0xffffffffu, lo1);
     lo2 = __reduce_min_sync(0xffffffffu, lo2);
     lo3 = __reduce_min_sync(0xffffffffu, lo3);
@@ -236,7 +231,7 @@ __device__ __forceinline__ float lds_f32(uint32_t addr)
 template <int ORDER>
 __device__ __forceinline__ float row_dot(uint32_t addr, const float w[4])
 {
-    if constexpr (ORDER == 3) {
+    if constexpr (Scheme<ORDER>::M == 4) {
         float s = w[0] * lds_f32<0>(addr);
         s = fmaf(w[1], lds_f32<4>(addr), s);
         s = fmaf(w[2], lds_f32<8>(addr), s);
@@ -260,8 +255,8 @@ template <int ORDER>
 __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, int i, int j, int k, float d1,
                                            float d2, float d3)
 {
-    constexpr int M = (ORDER == 3) ? 4 : 2;
-    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    constexpr int M = Scheme<ORDER>::M;
+    constexpr int OFF = Scheme<ORDER>::OFF;
     const int P = bp.E2 * bp.S3;
     float t1, t2, t3, w1[4], w2[4], w3[4];
     const int o = (i + split_in_box(d1, t1) - OFF - bp.O1) * P +
@@ -284,7 +279,7 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
             const uint32_t r0 = base + a * P4 + b * S4, r1 = r0 + S4;
             float2 sb = make_float2(w3[0] * lds_f32<0>(r0), w3[0] * lds_f32<0>(r1));
             sb = __ffma2_rn(make_float2(w3[1], w3[1]), make_float2(lds_f32<4>(r0), lds_f32<4>(r1)), sb);
-            if constexpr (ORDER == 3) {
+            if constexpr (Scheme<ORDER>::M == 4) {
                 sb = __ffma2_rn(make_float2(w3[2], w3[2]), make_float2(lds_f32<8>(r0), lds_f32<8>(r1)), sb);
                 sb = __ffma2_rn(make_float2(w3[3], w3[3]), make_float2(lds_f32<12>(r0), lds_f32<12>(r1)), sb);
             }

@@ -513,6 +513,27 @@ unsigned stream_blocks(size_t n)
     return static_cast<unsigned>(b < cap ? (b ? b : 1) : cap);
 }
 
+
+// B-spline prefilter in Fourier space: every mode of ncomp half spectra is
+// divided by N prod_axes (2 + cos(k_a h_a)) / 3 (the sampled cubic B-spline),
+// so that the inverse transform gives the interpolating spline's coefficients.
+__global__ void k_bspline_scale(Grid g, cufftComplex* __restrict__ spec, size_t M, int ncomp, float invN)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (e >= M * ncomp) return;
+    const size_t m = e % M;
+    const int n3h = g.n3 / 2 + 1;
+    const int j3 = static_cast<int>(m % n3h);
+    const int j2 = static_cast<int>((m / n3h) % g.n2);
+    const int j1 = static_cast<int>(m / (static_cast<size_t>(n3h) * g.n2));
+    const float two_pi = 6.283185307179586f;
+    const float s1 = (2.0f + cosf(two_pi * j1 / g.n1)) * (1.0f / 3.0f);
+    const float s2 = (2.0f + cosf(two_pi * j2 / g.n2)) * (1.0f / 3.0f);
+    const float s3 = (2.0f + cosf(two_pi * j3 / g.n3)) * (1.0f / 3.0f);
+    const float f = invN / (s1 * s2 * s3);
+    spec[e].x *= f;
+    spec[e].y *= f;
+}
 }  // namespace
 
 void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op, RegParams rp,
@@ -626,4 +647,13 @@ void launch_fill(float* x, float value, size_t n, cudaStream_t st)
     k_fill<<<stream_blocks(n), kThreads, 0, st>>>(x, value, n);
 }
 
+}  // namespace claire
+
+namespace claire {
+void launch_bspline_scale(const Grid& g, cufftComplex* spec, size_t M, int ncomp, cudaStream_t st)
+{
+    const size_t n = M * ncomp;
+    k_bspline_scale<<<static_cast<unsigned>((n + 255) / 256), 256, 0, st>>>(g, spec, M, ncomp,
+                                                                          1.0f / static_cast<float>(g.N));
+}
 }  // namespace claire

@@ -30,7 +30,14 @@ inline unsigned blocks_for(size_t n) { return static_cast<unsigned>((n + kThread
 template <int ORDER>
 __device__ __forceinline__ void basis_and_deriv(float t, float w[4], float dw[4])
 {
-    if constexpr (ORDER == 3) {
+    if constexpr (ORDER == 4) {
+        bspline_weights(t, w);
+        const float s = 1.0f - t;
+        dw[0] = -0.5f * s * s;
+        dw[1] = 1.5f * t * t - 2.0f * t;
+        dw[2] = -1.5f * t * t + t + 0.5f;
+        dw[3] = 0.5f * t * t;
+    } else if constexpr (ORDER == 3) {
         cubic_weights(t, w);
         const float t2 = t * t;
         dw[0] = -(1.0f / 6.0f) * (3.0f * t2 - 6.0f * t + 2.0f);
@@ -48,13 +55,13 @@ __device__ __forceinline__ void basis_and_deriv(float t, float w[4], float dw[4]
 // Wrapped node offsets and weights (plus derivatives) of one axis.
 template <int ORDER>
 struct DAxis {
-    static constexpr int M = (ORDER == 3) ? 4 : 2;
+    static constexpr int M = Scheme<ORDER>::M;
     int idx[M];
     float w[4], dw[4];
     __device__ __forceinline__ void build(int node, float disp, int n, int stride)
     {
         float t;
-        const int b = wrap_index(node + split_disp(disp, t) - (ORDER == 3 ? 1 : 0), n);
+        const int b = wrap_index(node + split_disp(disp, t) - Scheme<ORDER>::OFF, n);
 #pragma unroll
         for (int a = 0; a < M; ++a) {
             const int q = b + a;
@@ -178,7 +185,7 @@ __global__ void __launch_bounds__(kThreads) k_scatter_tiled(Grid g, const float*
     __shared__ int red[6][kST2];
     __shared__ int par[7];
     constexpr int M = DAxis<ORDER>::M;
-    constexpr int OFF = (ORDER == 3) ? 1 : 0;
+    constexpr int OFF = Scheme<ORDER>::OFF;
     const double scale = fixed_scale_of(*maxabs);
     if (!(scale > 0.0)) return;  // uniform: zero or non-finite cotangent
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;

@@ -74,7 +74,7 @@ def _disp(n, seed, cfl):
 # kernels
 # ---------------------------------------------------------------------------
 
-@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("order", [3, 1, 4])
 @pytest.mark.parametrize("n", SHAPES)
 @pytest.mark.parametrize("cfl", [0.4, 6.0])
 def test_interp_parity(env, n, order, cfl):
@@ -89,7 +89,7 @@ def test_interp_parity(env, n, order, cfl):
     assert rel_linf(host(out), ref) <= 1e-5
 
 
-@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("order", [3, 1, 4])
 def test_interp_parity_random_displacement_fallback(env, order):
     """Uniform random displacements (+-9 cells, no spatial smoothness) give
     departure boxes larger than the shared-memory tile, so the kernel takes
@@ -124,12 +124,58 @@ def test_interp_integer_shift_bit_exact(env, order):
     assert np.array_equal(out.cpu().numpy(), np.roll(f, (-5, 13, -21), axis=(0, 1, 2)))
 
 
+def test_bspline_integer_shift_and_restrictions(env):
+    """Cubic B-spline (interp 4): an integer shift returns the shifted grid
+    values up to the FP32 prefilter round trip; 16-bit storage and the
+    reverse-mode transport refuse it."""
+    torch, claire = env
+    n = (16, 12, 20)
+    rng = np.random.default_rng(0)
+    f = f32(rng.standard_normal(n))
+    d = np.zeros((3,) + n, np.float32)
+    d[0] = 5; d[1] = -13; d[2] = 21
+    ctx = make_ctx(claire, torch, n, interp=4)
+    out = torch.empty(n, device="cuda")
+    ctx.interp(dev(torch, f), dev(torch, d), out, 4)
+    torch.cuda.synchronize()
+    assert rel_linf(host(out), np.roll(f, (-5, 13, -21), axis=(0, 1, 2)).astype(np.float64)) <= 1e-5
+    with pytest.raises(claire.ClaireError):
+        make_ctx(claire, torch, n, interp=4, storage=claire.STORAGE_F16)
+    v = torch.zeros((3,) + n, device="cuda")
+    with pytest.raises(claire.ClaireError) as e:
+        ctx.transport_vjp(v, dev(torch, f), dev(torch, f), torch.empty(n, device="cuda"), None)
+    assert e.value.status == -9
+
+
+def test_bspline_gradient_matvec_parity(env):
+    torch, claire = env
+    n = (32, 32, 32)
+    m0, m1, vs, v, p = _problem(n)
+    p.order = 4
+    m1 = f32(oracle.transport(m0.astype(np.float64), vs.astype(np.float64), p))
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, interp=4)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    g = torch.empty((3,) + n, device="cuda")
+    J = ctx.gradient(dev(torch, v), g)
+    st = oracle.State(v.astype(np.float64), m0.astype(np.float64), m1.astype(np.float64), p)
+    assert abs(J - st.J) <= 1e-5 * abs(st.J)
+    assert rel_l2(host(g), oracle.gradient(st)) <= 1e-4
+    vt = f32(synth.mode_velocity(n, seed=33, vmax=0.3))
+    Hv = torch.empty((3,) + n, device="cuda")
+    ctx.hessian_matvec(dev(torch, vt), Hv)
+    torch.cuda.synchronize()
+    assert rel_l2(host(Hv), oracle.hessian_matvec(st, vt.astype(np.float64))) <= 1e-4
+    lo, hi = ctx.detj(dev(torch, vs))
+    ref = oracle.detj(vs.astype(np.float64), p)
+    assert abs(lo - ref.min()) <= 1e-4 * abs(ref.min()) and abs(hi - ref.max()) <= 1e-4 * abs(ref.max())
+
+
 @pytest.mark.parametrize("n", SHAPES)
 @pytest.mark.parametrize("direction", [1, -1])
 def test_backtrace_parity(env, n, direction):
     torch, claire = env
     v = f32(synth.mode_velocity(n, seed=4, vmax=1.0))
-    for order in (3, 1):
+    for order in (3, 1, 4):
         ctx = make_ctx(claire, torch, n, nt=4, interp=order)
         d = torch.empty((3,) + n, device="cuda")
         ctx.backtrace(dev(torch, v), d, direction)
@@ -203,7 +249,7 @@ def _problem(n, nt=4, seed=0, scale=0.5):
 
 
 @pytest.mark.parametrize("n", SHAPES)
-@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("order", [3, 1, 4])
 def test_transport_parity(env, n, order):
     torch, claire = env
     m0, _, vs, _, p = _problem(n)

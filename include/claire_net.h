@@ -120,6 +120,15 @@ claire_status claire_net_vel_loss(const float* v, const float* vstar, const floa
                                   float* dv, double* sum, void* stream);
 claire_status claire_net_residual(const float* x, const float* y, size_t n, float* r, double* sum, void* stream);
 
+/* Tiling of the tcgen05 convolution for this process: bricks of bdc x 16 x 8
+ * voxels (bdc 1, 2 or 4: D planes sharing one staged halo) and nstage 1 or 2
+ * shared-memory stages (2: the next channel slice is staged while the tensor
+ * cores work).  0 restores the automatic choice (the deepest brick that
+ * leaves two waves of CTAs, one stage).  A forced setting that does not fit a
+ * shape (D % bdc, TMEM or shared memory) makes that call fail with
+ * CLAIRE_ECUDA.  Meant for tuning and tests; not thread-safe. */
+claire_status claire_net_set_conv_tiling(int bdc, int nstage);
+
 /* Number of tcgen05 completion waits that gave up since the last reset
  * (reset != 0 clears it).  Synchronises the device. */
 claire_status claire_net_device_errors(int* count, int reset);

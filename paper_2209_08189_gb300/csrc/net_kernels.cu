@@ -220,22 +220,24 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d(const __nv_bfloat16* __
 // ---------------------------------------------------------------------------
 // tcgen05 (5th-generation tensor core) version of the forward convolution
 // ---------------------------------------------------------------------------
-// A CTA owns a brick of 1 x 16 x 8 = 128 output voxels (M = 128, one TMEM
-// lane per voxel) and all Cout channels (N = Cout, FP32 accumulators in
-// TMEM).  Per 16-channel slice of the input it stages, with cp.async, the
-// brick's halo (3 x 18 x 10 voxels) and the slice of all 27 taps' weights
-// into shared memory in the no-swizzle K-major core-matrix layout (8 rows x
-// 16 bytes per core matrix), then one elected thread issues 27
-// tcgen05.mma.kind::f16 (M128 x N x K16), one per tap: the A operand of a
-// tap is the halo shifted by the tap offset, which is just another start
-// address because every core matrix is 8 consecutive voxels along W and the
-// next core matrix is the next H row (a constant stride).  tcgen05.commit
-// signals an mbarrier; the epilogue reads TMEM with tcgen05.ld.
+// A CTA owns a brick of BDc x 16 x 8 output voxels: BDc planes of M = 128
+// voxels (one TMEM lane per voxel of a plane) and all Cout channels (N =
+// Cout FP32 columns per plane).  Per 16-channel slice of the input it stages,
+// with cp.async, the brick's halo ((BDc+2) x 18 x 10 voxels) and the slice of
+// all 27 taps' weights into shared memory in the no-swizzle K-major
+// core-matrix layout (8 rows x 16 bytes per core matrix, two 8-channel half
+// planes), then one elected thread issues 27 x BDc tcgen05.mma.kind::f16
+// (M128 x N x K16): the A operand of a (plane, tap) pair is the halo at a
+// shifted start address, because every core matrix is 8 consecutive voxels
+// along W and the next one is the next H row (a constant stride).  The halo
+// is shared by the BDc planes; with two stages the next slice is staged while
+// the tensor cores work on the current one.  tcgen05.commit signals an
+// mbarrier (waits are bounded); the epilogue reads TMEM with tcgen05.ld.
 constexpr int kTcBH = 16, kTcBW = 8;
-constexpr int kTcHaloD = 3, kTcHaloH = kTcBH + 2, kTcHaloW = kTcBW + 2;
-constexpr int kTcSlots = kTcHaloD * kTcHaloH * kTcHaloW;  // 540
-constexpr int kTcPlane = kTcSlots * 16;                   // bytes per 8-channel half plane
-constexpr uint32_t kTcSpinLimit = 1u << 26;
+constexpr int kTcHaloH = kTcBH + 2, kTcHaloW = kTcBW + 2;
+constexpr int kTcPlaneSlots = kTcHaloH * kTcHaloW;  // 180 halo voxels per D plane
+constexpr uint32_t kTcSpinLimit = 1u << 22;
+constexpr int kTcMaxSmem = 231424;  // dynamic shared memory per CTA: the 227 KB opt-in limit less 1 KB for the static part
 
 // set when an mbarrier wait of k_conv3d_tc gave up (read by claire_net_device_errors)
 __device__ int g_tc_wait_errors = 0;
@@ -262,29 +264,46 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group()
+{
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N));
+}
+
+struct TcShape {
+    int bdc;        // D planes per brick
+    int ccols;      // TMEM columns per plane (Cout rounded up to 32)
+    int nstage;     // 1 or 2 staging buffers
+    int plane;      // bytes of one 8-channel half plane of the halo
+    int stage;      // bytes of one stage (halo + weights)
+    uint32_t cols;  // TMEM columns allocated (power of two)
+};
+
 __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
                                                             const __nv_bfloat16* __restrict__ Wt,
                                                             const float* __restrict__ bias, float slope, int act,
                                                             __nv_bfloat16* __restrict__ Y, int Cys, int Cout,
-                                                            uint32_t tmem_cols, Vol v, int* __restrict__ err)
+                                                            TcShape sh, Vol v, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char tc_smem[];
     __shared__ __align__(8) uint64_t mbar;
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int bdc = sh.bdc;
     // brick origin
-    const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
+    const int nbw = v.W / kTcBW, nbh = v.H / kTcBH, nbd = v.D / bdc;
     int r = blockIdx.x;
     const int w0 = (r % nbw) * kTcBW; r /= nbw;
     const int h0 = (r % nbh) * kTcBH; r /= nbh;
-    const int d0 = r % v.D;
-    const int b = r / v.D;
-    unsigned char* halo = tc_smem;                  // 2 planes of kTcSlots x 16 B
-    unsigned char* wsm = tc_smem + 2 * kTcPlane;     // [tap][half][Cout] x 16 B
-    const uint32_t halo_s = smem_addr(halo), w_s = smem_addr(wsm), mbar_s = smem_addr(&mbar);
+    const int d0 = (r % nbd) * bdc;
+    const int b = r / nbd;
+    const int slots = (bdc + 2) * kTcPlaneSlots;
+    const uint32_t smem_s = smem_addr(tc_smem), mbar_s = smem_addr(&mbar);
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
-                     "r"(tmem_cols));
+                     "r"(sh.cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
@@ -296,42 +315,65 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(Cout) >> 3) << 17) |
                            ((128u >> 4) << 24);
     const int nchunks = Cin / 16;
-    bool ok = true;
-    for (int c = 0; c < nchunks && ok; ++c) {
+    // stage a slice: halo slot s = (sd * 18 + sh) * 10 + sw in half plane h; weight piece (tap, half, co)
+    auto issue = [&](int c, int stg) {
         const int c0 = 16 * c;
-        if (c > 0) ok = mbar_wait(mbar_s, (c - 1) & 1);  // the previous slice's MMAs have read the buffers
-        if (!ok) break;
-        // halo: slot s = (sd * 18 + sh) * 10 + sw, half plane h
-        for (int e = tid; e < 2 * kTcSlots; e += kConvThreads) {
-            const int hlf = e / kTcSlots, sl = e % kTcSlots;
-            const int sw = sl % kTcHaloW, sh = (sl / kTcHaloW) % kTcHaloH, sd = sl / (kTcHaloW * kTcHaloH);
-            const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + sh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
+        const uint32_t base = smem_s + stg * sh.stage;
+        for (int e = tid; e < 2 * slots; e += kConvThreads) {
+            const int hlf = e / slots, sl = e - hlf * slots;
+            const int sw = sl % kTcHaloW, shh = (sl / kTcHaloW) % kTcHaloH, sd = sl / kTcPlaneSlots;
+            const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + shh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
             const size_t vox = ((static_cast<size_t>(b) * v.D + d) * v.H + h) * v.W + w;
-            cp_async16(halo_s + hlf * kTcPlane + sl * 16, X + vox * Cxs + c0 + 8 * hlf);
+            cp_async16(base + hlf * sh.plane + sl * 16, X + vox * Cxs + c0 + 8 * hlf);
         }
-        // weights of the slice: piece (tap, half, co) <- W[co][tap][c0 + 8 half .. +8]
+        const uint32_t wb = base + 2 * sh.plane;
         const int npieces = 27 * 2 * Cout;
         for (int e = tid; e < npieces; e += kConvThreads) {
             const int co = e % Cout, hlf = (e / Cout) & 1, tap = e / (2 * Cout);
-            cp_async16(w_s + e * 16, Wt + (static_cast<size_t>(co) * 27 + tap) * Cin + c0 + 8 * hlf);
+            cp_async16(wb + e * 16, Wt + (static_cast<size_t>(co) * 27 + tap) * Cin + c0 + 8 * hlf);
         }
-        cp_async_wait();
+        cp_async_commit();
+    };
+    bool ok = true;
+    issue(0, 0);
+    for (int c = 0; c < nchunks && ok; ++c) {
+        const int stg = sh.nstage == 2 ? (c & 1) : 0;
+        // every completion phase is waited for exactly once and in order, so
+        // a parity wait never sees two outstanding phases
+        if (c >= 1) ok = mbar_wait(mbar_s, (c - 1) & 1);
+        if (!ok) break;
+        if (sh.nstage == 2) {
+            if (c + 1 < nchunks) {
+                issue(c + 1, (c + 1) & 1);  // the stage slice c-1 used; overlaps the MMAs of slice c
+                cp_async_wait_group<1>();
+            } else {
+                cp_async_wait_group<0>();
+            }
+        } else {
+            if (c >= 1) issue(c, 0);
+            cp_async_wait_group<0>();
+        }
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
         if (tid == 0) {
+            const uint32_t base = smem_s + stg * sh.stage;
+            const uint32_t wb = base + 2 * sh.plane;
 #pragma unroll 1
-            for (int tap = 0; tap < 27; ++tap) {
-                const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
-                const uint32_t a_addr = halo_s + ((kd * kTcHaloH + kh) * kTcHaloW + kw) * 16;
-                const uint64_t ad = umma_desc(a_addr, kTcPlane, kTcHaloW * 16);
-                const uint64_t bd = umma_desc(w_s + tap * 2 * Cout * 16, Cout * 16, 128);
-                const uint32_t accum = (c > 0 || tap > 0) ? 1u : 0u;
-                asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                             " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
-                             "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
-            }
+            for (int z = 0; z < bdc; ++z)
+#pragma unroll 1
+                for (int tap = 0; tap < 27; ++tap) {
+                    const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+                    const uint32_t a_addr = base + (((z + kd) * kTcHaloH + kh) * kTcHaloW + kw) * 16;
+                    const uint64_t ad = umma_desc(a_addr, sh.plane, kTcHaloW * 16);
+                    const uint64_t bd = umma_desc(wb + tap * 2 * Cout * 16, Cout * 16, 128);
+                    const uint32_t accum = (c > 0 || tap > 0) ? 1u : 0u;
+                    const uint32_t dt = tmem + static_cast<uint32_t>(z * sh.ccols);
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
             asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_s)
                          : "memory");
         }
@@ -339,45 +381,50 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     if (ok) ok = mbar_wait(mbar_s, (nchunks - 1) & 1);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) {
+        cp_async_wait_group<0>();
         if (lane == 0) atomicAdd(err, 1);
     } else {
-        // epilogue: warp w owns TMEM lanes 32w..32w+31 = brick rows m = 32w + lane
+        // epilogue: warp w owns TMEM lanes 32w..32w+31 = rows m = 32w + lane of every plane
         const int m = 32 * warp + lane;
         const int eh = m / kTcBW, ew = m % kTcBW;
-        const size_t vox = ((static_cast<size_t>(b) * v.D + d0) * v.H + h0 + eh) * v.W + w0 + ew;
-        __nv_bfloat16* yrow = Y + vox * Cys;
-        for (int c0 = 0; c0 < Cout; c0 += 16) {
-            uint32_t q[16];
-            const uint32_t ta = tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(c0);
-            asm volatile("tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
-                         "[%16];"
-                         : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
-                           "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
-                           "=r"(q[14]), "=r"(q[15])
-                         : "r"(ta));
-            asm volatile("tcgen05.wait::ld.sync.aligned;");
-            V8 o0, o1;
+        for (int z = 0; z < bdc; ++z) {
+            const size_t vox = ((static_cast<size_t>(b) * v.D + d0 + z) * v.H + h0 + eh) * v.W + w0 + ew;
+            __nv_bfloat16* yrow = Y + vox * Cys;
+            for (int c0 = 0; c0 < Cout; c0 += 16) {
+                uint32_t q[16];
+                const uint32_t ta = tmem + (static_cast<uint32_t>(32 * warp) << 16) +
+                                    static_cast<uint32_t>(z * sh.ccols + c0);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, "
+                    "[%16];"
+                    : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+                      "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+                      "=r"(q[14]), "=r"(q[15])
+                    : "r"(ta));
+                asm volatile("tcgen05.wait::ld.sync.aligned;");
+                V8 o0, o1;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) {
-                float y0 = __uint_as_float(q[j]), y1 = __uint_as_float(q[8 + j]);
-                if (bias) {
-                    y0 += __ldg(bias + c0 + j);
-                    y1 += __ldg(bias + c0 + 8 + j);
+                for (int j = 0; j < 8; ++j) {
+                    float y0 = __uint_as_float(q[j]), y1 = __uint_as_float(q[8 + j]);
+                    if (bias) {
+                        y0 += __ldg(bias + c0 + j);
+                        y1 += __ldg(bias + c0 + 8 + j);
+                    }
+                    if (act) {
+                        y0 = y0 > 0.f ? y0 : slope * y0;
+                        y1 = y1 > 0.f ? y1 : slope * y1;
+                    }
+                    o0.f[j] = y0;
+                    o1.f[j] = y1;
                 }
-                if (act) {
-                    y0 = y0 > 0.f ? y0 : slope * y0;
-                    y1 = y1 > 0.f ? y1 : slope * y1;
-                }
-                o0.f[j] = y0;
-                o1.f[j] = y1;
+                store8(yrow + c0, o0);
+                store8(yrow + c0 + 8, o1);
             }
-            store8(yrow + c0, o0);
-            store8(yrow + c0 + 8, o1);
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(tmem_cols));
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.cols));
 }
 
 // Wgrad partials: P[pc][co][tap][ci] = sum over the chunk's voxels p of
@@ -779,6 +826,9 @@ bool brick_for(int D, int H, int W, int* bd, int* bh, int* bw)
     return (d + 2) * (h + 2) * (w + 2) <= kHaloMax;
 }
 
+// tiling forced by claire_net_set_conv_tiling (0 = automatic)
+int g_tc_force_bdc = 0, g_tc_force_nstage = 0;
+
 bool tc_eligible(int Cin, int Cout, int D, int H, int W)
 {
     (void)D;
@@ -793,23 +843,51 @@ cudaError_t conv3d(const void* X, int Cxs, int Cin, const void* Wt, const float*
     auto w = static_cast<const __nv_bfloat16*>(Wt);
     auto y = static_cast<__nv_bfloat16*>(Y);
     if (tc_eligible(Cin, Cout, D, H, W)) {
-        // tcgen05 path: bricks of 1 x 16 x 8 voxels, TMEM columns = next power of two >= Cout
-        uint32_t cols = 32;
-        while (cols < static_cast<uint32_t>(Cout)) cols <<= 1;
-        const size_t smem = 2 * static_cast<size_t>(kTcPlane) + 27 * 2 * static_cast<size_t>(Cout) * 16;
+        // tcgen05 path: bricks of bdc x 16 x 8 voxels; the deepest brick whose
+        // TMEM columns (bdc planes x Cout rounded to 32) and shared memory fit
+        TcShape sh{};
+        sh.ccols = (Cout + 31) / 32 * 32;
+        const int wbytes = 27 * 2 * Cout * 16;
+        int nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 152;
+        // choose the brick depth and staging: the deepest brick (halo shared
+        // by more planes, weights staged once for more voxels) that still
+        // leaves two waves of CTAs at the occupancy that its shared memory and
+        // TMEM allow; one stage unless a forced setting asks for two
+        for (int bdc = 4; bdc >= 1; bdc >>= 1) {
+            if (D % bdc || bdc * sh.ccols > 512) continue;
+            if (g_tc_force_bdc && bdc != g_tc_force_bdc) continue;
+            const int plane = (bdc + 2) * kTcPlaneSlots * 16;
+            const int stage = 2 * plane + wbytes;
+            const int nstage = g_tc_force_nstage ? g_tc_force_nstage : 1;
+            if (nstage * stage > kTcMaxSmem) continue;
+            uint32_t cols = 32;
+            while (cols < static_cast<uint32_t>(bdc * sh.ccols)) cols <<= 1;
+            const int per_sm = std::max(1, std::min(kTcMaxSmem / (nstage * stage), static_cast<int>(512 / cols)));
+            const long long grid = static_cast<long long>(B) * (D / bdc) * (H / kTcBH) * (W / kTcBW);
+            if (!g_tc_force_bdc && bdc > 1 && grid < 2LL * nsm * per_sm) continue;
+            sh.bdc = bdc;
+            sh.plane = plane;
+            sh.stage = stage;
+            sh.nstage = nstage;
+            break;
+        }
+        if (sh.bdc == 0) return cudaErrorInvalidValue;
+        sh.cols = 32;
+        while (sh.cols < static_cast<uint32_t>(sh.bdc * sh.ccols)) sh.cols <<= 1;
+        const size_t smem = static_cast<size_t>(sh.nstage) * sh.stage;
         static bool attr_set = false;
         if (!attr_set) {
-            // the largest case: Cout = 192 (halo planes + 27 taps x 2 halves x 192 x 16 B = 179 KB)
-            cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                 2 * kTcPlane + 27 * 2 * 192 * 16);
+            cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem);
             if (e != cudaSuccess) return e;
             attr_set = true;
         }
         int* err = nullptr;
         cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tc_wait_errors);
         if (e != cudaSuccess) return e;
-        const unsigned grid = static_cast<unsigned>(B * D * (H / kTcBH) * (W / kTcBW));
-        k_conv3d_tc<<<grid, kConvThreads, smem, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, Cout, cols, v, err);
+        const unsigned grid = static_cast<unsigned>(B * (D / sh.bdc) * (H / kTcBH) * (W / kTcBW));
+        k_conv3d_tc<<<grid, kConvThreads, smem, st>>>(x, Cxs, Cin, w, bias, slope, act, y, Cys, Cout, sh, v, err);
         return cudaGetLastError();
     }
     int bd, bh, bw;
@@ -1259,5 +1337,14 @@ extern "C" claire_status claire_net_device_errors(int* count, int reset)
     const int n = read_tc_errors(reset != 0);
     if (n < 0) return net_status(cudaErrorUnknown, "device_errors");
     *count = n;
+    return CLAIRE_OK;
+}
+
+extern "C" claire_status claire_net_set_conv_tiling(int bdc, int nstage)
+{
+    if ((bdc != 0 && bdc != 1 && bdc != 2 && bdc != 4) || nstage < 0 || nstage > 2)
+        return net_fail("set_conv_tiling: bdc in {0, 1, 2, 4}, nstage in {0, 1, 2}");
+    g_tc_force_bdc = bdc;
+    g_tc_force_nstage = nstage;
     return CLAIRE_OK;
 }

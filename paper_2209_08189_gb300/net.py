@@ -47,6 +47,7 @@ _SIGS = {
     "claire_net_vel_loss": [_vp, _vp, _vp, _f, _f, _sz, _vp, _vp, _vp],
     "claire_net_residual": [_vp, _vp, _sz, _vp, _vp, _vp],
     "claire_net_device_errors": [_ip, _i],
+    "claire_net_set_conv_tiling": [_i, _i],
     "claire_net_last_error": [],
 }
 _RESTYPE = {"claire_net_last_error": ctypes.c_char_p}
@@ -80,6 +81,11 @@ def device_errors(reset=True):
     n = ctypes.c_int()
     _check(lib().claire_net_device_errors(ctypes.byref(n), int(bool(reset))), "device_errors")
     return n.value
+
+
+def set_conv_tiling(bdc=0, nstage=0):
+    """Force the tcgen05 convolution's brick depth / staging (0, 0 = automatic)."""
+    _check(lib().claire_net_set_conv_tiling(int(bdc), int(nstage)), "set_conv_tiling")
 
 
 def _addr(t):

@@ -105,6 +105,28 @@ def test_conv3d_forward_and_input_gradient(env, case):
     assert net.device_errors() == 0
 
 
+@pytest.mark.parametrize("tiling", [(1, 1), (2, 2), (4, 1), (4, 2)])
+def test_conv3d_tcgen05_tilings(env, tiling):
+    """Every forced brick depth / staging of the tcgen05 kernel against the oracle
+    (several channel slices, so the two-stage pipeline turns over)."""
+    torch, net = env
+    B, D, H, W, ci, co = 2, 4, 16, 16, 48, 48
+    r = np.random.default_rng(sum(tiling))
+    xbuf = bf16(torch, r.standard_normal((B, D, H, W, ci)))
+    w = bf16(torch, r.standard_normal((co, 27, ci)) / np.sqrt(27 * ci))
+    bias = torch.from_numpy(r.standard_normal(co).astype(np.float32)).cuda()
+    y = torch.zeros((B, D, H, W, co), dtype=torch.bfloat16, device="cuda")
+    net.set_conv_tiling(*tiling)
+    try:
+        net.conv3d(net.Act(xbuf, 0, ci), w, bias, net.Act(y, 0, co), 0.1, 1, stream(torch))
+        torch.cuda.synchronize()
+    finally:
+        net.set_conv_tiling(0, 0)
+    ref = onet.conv3d(f64(xbuf), f64(w), f64(bias), act=True, slope=0.1)
+    assert close_bf16(f64(y), ref) <= 0
+    assert net.device_errors() == 0
+
+
 @pytest.mark.parametrize("case", CONV_CASES)
 def test_conv3d_weight_gradient(env, case):
     torch, net = env

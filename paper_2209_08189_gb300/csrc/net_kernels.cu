@@ -427,6 +427,170 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.cols));
 }
 
+// tcgen05 weight gradient: D[co][ci] += sum_p dY[p][co] X[p + off(tap)][ci]
+// per tap, with M = output channels (a block of up to 128, padded to 64 or
+// 128 TMEM lanes), N = a block of input channels, K = voxels (16 per MMA).
+// Both operands are MN-major in shared memory (channels contiguous, as the
+// activations are stored): the dY tile of a 1 x 16 x 8 brick as [8-voxel
+// block][8-channel block][8 voxels][8 channels], and the input halo as
+// 8-channel planes of 16-byte slots, so a tap's B operand is again a shifted
+// start address (8 consecutive voxels along W per core matrix; the next 8
+// voxels are the next H row, a 160-byte stride).  The CTA accumulates its
+// taps (T of them, T x Nc <= 512 TMEM columns) over its chunk of bricks and
+// writes per-chunk FP32 partials, reduced in a fixed order as before.
+struct TcWg {
+    int mpad;       // TMEM lanes used (64 or 128)
+    int nc;         // input channels per CTA
+    int taps;       // taps per CTA
+    int ntg, nco, nci;
+    int plane;      // bytes of one 8-channel halo plane (540 slots x 16 B)
+    int abytes;     // bytes of the dY tile (128 voxels x mpad channels x 2)
+    uint32_t cols;  // TMEM columns allocated
+};
+
+__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
+                                                           const __nv_bfloat16* __restrict__ dY, int Cys, int Cout,
+                                                           Vol v, TcWg wg, int nbricks, int per, int chunks,
+                                                           float* __restrict__ P, float* __restrict__ Pb,
+                                                           int* __restrict__ err)
+{
+    extern __shared__ __align__(128) unsigned char wg_smem[];
+    __shared__ __align__(8) uint64_t mbar;
+    __shared__ uint32_t tmem_slot;
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int bid = blockIdx.x;
+    const int pc = bid % chunks; bid /= chunks;
+    const int cib = bid % wg.nci; bid /= wg.nci;
+    const int cob = bid % wg.nco;
+    const int tg = bid / wg.nco;
+    const int co0 = cob * 128, ci0 = cib * wg.nc;
+    const int cnt = min(wg.mpad, Cout - co0);  // real output channels of this block (multiple of 16)
+    const int tap0 = tg * wg.taps, ntaps = min(wg.taps, 27 - tap0);
+    const int mblk = wg.mpad / 8;
+    unsigned char* A = wg_smem;
+    unsigned char* Hs = wg_smem + wg.abytes;
+    const uint32_t a_s = smem_addr(A), h_s = smem_addr(Hs), mbar_s = smem_addr(&mbar);
+    // padded channel rows stay zero
+    for (int e = tid; e < wg.abytes / 16; e += kConvThreads) reinterpret_cast<uint4*>(A)[e] = make_uint4(0, 0, 0, 0);
+    if (warp == 0) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
+                     "r"(wg.cols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    const uint32_t tmem = tmem_slot;
+    // D F32, A and B BF16, both MN-major, N = nc, M = mpad
+    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                           ((static_cast<uint32_t>(wg.nc) >> 3) << 17) | ((static_cast<uint32_t>(wg.mpad) >> 4) << 24);
+    const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
+    const int first = pc * per, last = min(nbricks, first + per);
+    const int nq = wg.nc / 8;
+    // the first tap group of the first input-channel block also sums dY for the bias
+    const bool bias = Pb != nullptr && tg == 0 && cib == 0 && tid < cnt;
+    float bsum = 0.f;
+    bool ok = true;
+    int it = 0;
+    for (int br = first; br < last; ++br, ++it) {
+        int r = br;
+        const int w0 = (r % nbw) * kTcBW; r /= nbw;
+        const int h0 = (r % nbh) * kTcBH; r /= nbh;
+        const int d0 = r % v.D;
+        const int b = r / v.D;
+        if (it > 0) {
+            // the previous brick's MMAs have read the tiles and every thread has summed its dY column
+            ok = __syncthreads_and(mbar_wait(mbar_s, (it - 1) & 1));
+            if (!ok) break;
+        }
+        // dY tile: piece (voxel p, 8-channel block cb) -> ((p/8) * mblk + cb) * 128 + (p%8) * 16
+        const int cbn = cnt / 8;
+        for (int e = tid; e < 128 * cbn; e += kConvThreads) {
+            const int p = e / cbn, cb = e - p * cbn;
+            const size_t vox = ((static_cast<size_t>(b) * v.D + d0) * v.H + h0 + p / kTcBW) * v.W + w0 + p % kTcBW;
+            cp_async16(a_s + ((p / 8) * mblk + cb) * 128 + (p % 8) * 16, dY + vox * Cys + co0 + 8 * cb);
+        }
+        // halo planes: slot s = (sd * 18 + sh) * 10 + sw of plane q
+        for (int e = tid; e < nq * 3 * kTcPlaneSlots; e += kConvThreads) {
+            const int q = e / (3 * kTcPlaneSlots), sl = e - q * 3 * kTcPlaneSlots;
+            const int sw = sl % kTcHaloW, shh = (sl / kTcHaloW) % kTcHaloH, sd = sl / kTcPlaneSlots;
+            const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + shh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
+            const size_t vox = ((static_cast<size_t>(b) * v.D + d) * v.H + h) * v.W + w;
+            cp_async16(h_s + q * wg.plane + sl * 16, X + vox * Cxs + ci0 + 8 * q);
+        }
+        cp_async_wait();
+        asm volatile("fence.proxy.async.shared::cta;");
+        asm volatile("tcgen05.fence::before_thread_sync;");
+        __syncthreads();
+        asm volatile("tcgen05.fence::after_thread_sync;");
+        if (bias) {
+            const unsigned char* col = A + (tid / 8) * 128 + (tid % 8) * 2;
+#pragma unroll 4
+            for (int p = 0; p < 128; ++p)
+                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(col + (p / 8) * mblk * 128 + (p % 8) * 16));
+        }
+        if (tid == 0) {
+#pragma unroll 1
+            for (int t = 0; t < ntaps; ++t) {
+                const int tap = tap0 + t;
+                const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+#pragma unroll 1
+                for (int ks = 0; ks < 8; ++ks) {  // 16 voxels = rows 2 ks, 2 ks + 1 of the brick
+                    const uint64_t ad = umma_desc(a_s + 2 * ks * mblk * 128, mblk * 128, 128);
+                    const uint32_t b_addr = h_s + ((kd * kTcHaloH + 2 * ks + kh) * kTcHaloW + kw) * 16;
+                    const uint64_t bd = umma_desc(b_addr, kTcHaloW * 16, wg.plane);
+                    const uint32_t accum = (it > 0 || ks > 0) ? 1u : 0u;
+                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                     tmem + static_cast<uint32_t>(t * wg.nc)),
+                                 "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_s)
+                         : "memory");
+        }
+    }
+    if (ok && it > 0) ok = __syncthreads_and(mbar_wait(mbar_s, (it - 1) & 1));
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (!ok) {
+        cp_async_wait();
+        if (tid == 0) atomicAdd(err, 1);
+    } else if (32 * warp < wg.mpad) {
+        if (bias) Pb[static_cast<size_t>(pc) * Cout + co0 + tid] = bsum;
+        // rows co = co0 + 32 warp + lane; columns t * nc + ci
+        const int co = co0 + 32 * warp + lane;
+        float* Pp = P + static_cast<size_t>(pc) * Cout * 27 * Cin;
+        for (int t = 0; t < ntaps; ++t)
+            for (int c = 0; c < wg.nc; c += 16) {
+                uint32_t q[16];
+                if (it > 0) {
+                    const uint32_t ta =
+                        tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(t * wg.nc + c);
+                    asm volatile(
+                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
+                        "%15}, [%16];"
+                        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
+                          "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
+                          "=r"(q[14]), "=r"(q[15])
+                        : "r"(ta));
+                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                } else {
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) q[j] = 0u;  // an empty chunk contributes zeros
+                }
+                if (co < co0 + cnt) {
+                    float* dst = Pp + (static_cast<size_t>(co) * 27 + tap0 + t) * Cin + ci0 + c;
+#pragma unroll
+                    for (int j = 0; j < 16; ++j) dst[j] = __uint_as_float(q[j]);
+                }
+            }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(wg.cols));
+}
+
 // Wgrad partials: P[pc][co][tap][ci] = sum over the chunk's voxels p of
 // dY[p][co] X[p + off(tap)][ci]; Pb[pc][co] = sum dY[p][co] (ci chunk 0 only).
 // grid: (Cin/16, Cout/16, chunks); each CTA loops over its bricks.
@@ -926,8 +1090,37 @@ cudaError_t flip_weights(const void* W, int Cout, int Cin, void* Wf, cudaStream_
     return cudaGetLastError();
 }
 
+bool wg_tc_shape(int Cin, int Cout, int B, int D, int H, int W, int nsm, TcWg* wg, int* nbricks, int* chunks)
+{
+    if (H % kTcBH || W % kTcBW || Cin % 16 || Cout % 16) return false;
+    TcWg g{};
+    g.mpad = 128;
+    g.nco = (Cout + 127) / 128;
+    g.nc = Cin <= 64 ? Cin : (Cin % 64 == 0 ? 64 : (Cin % 48 == 0 ? 48 : (Cin % 32 == 0 ? 32 : 16)));
+    g.nci = Cin / g.nc;
+    g.taps = std::min(27, 512 / g.nc);
+    g.ntg = (27 + g.taps - 1) / g.taps;
+    g.plane = 3 * kTcPlaneSlots * 16;
+    g.abytes = 128 * g.mpad * 2;
+    g.cols = 32;
+    while (g.cols < static_cast<uint32_t>(g.taps * g.nc)) g.cols <<= 1;
+    if (g.cols > 512 || g.abytes + (g.nc / 8) * g.plane > kTcMaxSmem) return false;
+    const int nb = B * D * (H / kTcBH) * (W / kTcBW);
+    const int ctas = g.ntg * g.nco * g.nci;
+    int c = (4 * nsm + ctas - 1) / ctas;
+    c = std::max(1, std::min(c, nb));
+    const int per = (nb + c - 1) / c;
+    *wg = g;
+    *nbricks = nb;
+    *chunks = (nb + per - 1) / per;
+    return true;
+}
+
 int wgrad_chunks(int Cin, int Cout, int B, int D, int H, int W, int nsm)
 {
+    TcWg g;
+    int nb, ch;
+    if (wg_tc_shape(Cin, Cout, B, D, H, W, nsm, &g, &nb, &ch)) return ch;
     int bd, bh, bw;
     if (!brick_for(D, H, W, &bd, &bh, &bw)) return 0;
     const int nbricks = B * (D / bd) * (H / bh) * (W / bw);
@@ -942,6 +1135,37 @@ int wgrad_chunks(int Cin, int Cout, int B, int D, int H, int W, int nsm)
 cudaError_t conv3d_wgrad(const void* X, int Cxs, int Cin, const void* dY, int Cys, int Cout, int B, int D, int H,
                          int W, int chunks, float* part, float* partb, float* dW, float* db, cudaStream_t st)
 {
+    {
+        int nsm = 0, dev = 0;
+        cudaGetDevice(&dev);
+        if (cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || nsm < 1) nsm = 152;
+        TcWg g;
+        int nb, ch;
+        if (wg_tc_shape(Cin, Cout, B, D, H, W, nsm, &g, &nb, &ch)) {
+            if (ch != chunks) return cudaErrorInvalidValue;
+            static bool attr_set = false;
+            if (!attr_set) {
+                cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     kTcMaxSmem);
+                if (e != cudaSuccess) return e;
+                attr_set = true;
+            }
+            int* err = nullptr;
+            cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tc_wait_errors);
+            if (e != cudaSuccess) return e;
+            const int per = (nb + chunks - 1) / chunks;
+            const Vol v{B, D, H, W};
+            const size_t smem = static_cast<size_t>(g.abytes) + (g.nc / 8) * static_cast<size_t>(g.plane);
+            const unsigned grid = static_cast<unsigned>(g.ntg * g.nco * g.nci * chunks);
+            k_wgrad_tc<<<grid, kConvThreads, smem, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, Cin,
+                                                        static_cast<const __nv_bfloat16*>(dY), Cys, Cout, v, g, nb,
+                                                        per, chunks, part, db ? partb : nullptr, err);
+            const size_t nw = static_cast<size_t>(Cout) * 27 * Cin;
+            k_reduce_partials<<<nblk(nw, 256), 256, 0, st>>>(part, chunks, nw, dW);
+            if (db) k_reduce_partials<<<nblk(Cout, 256), 256, 0, st>>>(partb, chunks, Cout, db);
+            return cudaGetLastError();
+        }
+    }
     int bd, bh, bw;
     if (!brick_for(D, H, W, &bd, &bh, &bw)) return cudaErrorInvalidValue;
     const Vol v{B, D, H, W};

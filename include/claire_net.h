@@ -64,7 +64,9 @@ claire_status claire_net_conv3d_wgrad_chunks(int cin, int cout, const int vol[4]
 /* Weight gradient of Y = conv3x3x3(X, W) for the output gradient dY (the
  * pre-activation gradient): dw[co][tap][ci] = sum_p dY[p][co] X[p+off][ci]
  * and db[co] = sum_p dY[p][co] (FP32; db may be NULL).  Per-chunk partials
- * are summed in a fixed order, so the result is deterministic. */
+ * are summed in a fixed order, so the result is deterministic.  Volumes with
+ * H % 16 == 0 and W % 8 == 0 run on the tcgen05 tensor cores (voxels as the
+ * reduction dimension, accumulators in TMEM); others on mma.sync. */
 claire_status claire_net_conv3d_wgrad(const void* x, int x_stride, int cin, const void* dy, int dy_stride,
                                       int cout, const int vol[4], int chunks, float* part, float* part_bias,
                                       float* dw, float* db, void* stream);
@@ -128,6 +130,15 @@ claire_status claire_net_residual(const float* x, const float* y, size_t n, floa
  * shape (D % bdc, TMEM or shared memory) makes that call fail with
  * CLAIRE_ECUDA.  Meant for tuning and tests; not thread-safe. */
 claire_status claire_net_set_conv_tiling(int bdc, int nstage);
+
+/* Input channels per CTA of the tcgen05 weight gradient for this process:
+ * nc 16, 32, 48 or 64 (0 = automatic, 16).  Each CTA accumulates three taps
+ * x nc channels per MMA and as many (kd, kw) tap triples as TMEM holds; a
+ * larger nc means wider MMAs but more passes over each brick.  A forced nc
+ * that does not divide Cin leaves that shape to the mma.sync kernel.  Meant
+ * for tuning and tests; not thread-safe.  Fails with CLAIRE_EINVAL for any
+ * other nc. */
+claire_status claire_net_set_wgrad_tiling(int nc);
 
 /* Number of tcgen05 completion waits that gave up since the last reset
  * (reset != 0 clears it).  Synchronises the device. */

@@ -264,6 +264,17 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
     return false;
 }
 
+// 16 consecutive TMEM columns of this warp's 32 lanes (32x32b shape)
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&q)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]), "=r"(q[7]), "=r"(q[8]),
+          "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]), "=r"(q[14]), "=r"(q[15])
+        : "r"(taddr));
+    asm volatile("tcgen05.wait::ld.sync.aligned;");
+}
+
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
 
 template <int N>
@@ -427,35 +438,54 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.cols));
 }
 
-// tcgen05 weight gradient: D[co][ci] += sum_p dY[p][co] X[p + off(tap)][ci]
-// per tap, with M = output channels (a block of up to 128, padded to 64 or
-// 128 TMEM lanes), N = a block of input channels, K = voxels (16 per MMA).
-// Both operands are MN-major in shared memory (channels contiguous, as the
-// activations are stored): the dY tile of a 1 x 16 x 8 brick as [8-voxel
-// block][8-channel block][8 voxels][8 channels], and the input halo as
-// 8-channel planes of 16-byte slots, so a tap's B operand is again a shifted
-// start address (8 consecutive voxels along W per core matrix; the next 8
-// voxels are the next H row, a 160-byte stride).  The CTA accumulates its
-// taps (T of them, T x Nc <= 512 TMEM columns) over its chunk of bricks and
-// writes per-chunk FP32 partials, reduced in a fixed order as before.
+// tcgen05 weight gradient.  Per tap, dW[co][tap][ci] = sum_p dY[p][co] X[p + off(tap)][ci]:
+// K = voxels (16 per MMA, two rows of a 1 x 16 x 8 brick), M = output
+// channels, N = input channels x taps.  Both operands are MN-major (channels
+// contiguous, as the activations are stored) in 8 x 16-byte core matrices.
+//
+// Rows.  With at most 32 output channels (nsa = 3) the A tile stacks the dY
+// brick at depths d0-1, d0, d0+1 as row blocks s = 0, 1, 2: summed over all
+// bricks, dY[p + (s-1) e_d] X[p + (0, kh-1, kw-1)] is the kd = 2 - s tap, so
+// one MMA covers the three kd taps and X is staged for depth d0 only.
+// Otherwise (nsa = 1) the rows are a block of up to 128 output channels and X
+// is staged at three depths, kd picking the plane.
+// Columns.  The X halo is staged so that one MMA covers three kh taps (nkw =
+// 1: rows (sd, sh, q) of ten 16-byte voxel slots, the kh taps and the nq
+// channel blocks being core matrices 160 bytes apart, kw a 16-byte start
+// offset) or all nine (kh, kw) taps (nkw = 3, for 16-channel blocks: each
+// (sd, sh) row holds the three kw-shifted copies of its eight brick voxels).
+// An MMA "unit" is one (kd, kw) choice left to the start addresses; a CTA
+// holds `units` of them in TMEM and walks its chunk of bricks through two
+// smem stages, loading brick i+1 while the tensor cores work on brick i (one
+// mbarrier per stage, so each wait is for the newest phase of its barrier).
+// The bias sums dY on the CUDA cores.  Per-chunk FP32 partials are reduced in
+// a fixed order afterwards.
+constexpr int kWgThreads = 256;
+
 struct TcWg {
+    int nsa;        // dY row blocks (3: kd from the rows, 1: plain)
+    int npl;        // X depth planes staged (1 when nsa == 3, else 3)
+    int nkw;        // 3: kw taps in N (nc = 16), 1: kw by start offset
     int mpad;       // TMEM lanes used (64 or 128)
     int nc;         // input channels per CTA
-    int taps;       // taps per CTA
-    int ntg, nco, nci;
-    int plane;      // bytes of one 8-channel halo plane (540 slots x 16 B)
-    int abytes;     // bytes of the dY tile (128 voxels x mpad channels x 2)
+    int nci, nco;   // input / output channel blocks
+    int nunits;     // MMA units over all taps
+    int units;      // MMA units per CTA
+    int ntg;        // tap groups (CTAs sharing a brick's taps)
+    int abytes;     // bytes of the dY tile (128 voxels x mpad rows x 2)
+    int hbytes;     // bytes of the X halo
+    int per_sm;     // CTAs resident per SM (TMEM)
     uint32_t cols;  // TMEM columns allocated
 };
 
-__global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
-                                                           const __nv_bfloat16* __restrict__ dY, int Cys, int Cout,
-                                                           Vol v, TcWg wg, int nbricks, int per, int chunks,
-                                                           float* __restrict__ P, float* __restrict__ Pb,
-                                                           int* __restrict__ err)
+__global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
+                                                         const __nv_bfloat16* __restrict__ dY, int Cys, int Cout,
+                                                         Vol v, TcWg wg, int nbricks, int per, int chunks,
+                                                         float* __restrict__ P, float* __restrict__ Pb,
+                                                         int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char wg_smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar[2];
     __shared__ uint32_t tmem_slot;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int bid = blockIdx.x;
@@ -464,127 +494,187 @@ __global__ void __launch_bounds__(kConvThreads) k_wgrad_tc(const __nv_bfloat16* 
     const int cob = bid % wg.nco;
     const int tg = bid / wg.nco;
     const int co0 = cob * 128, ci0 = cib * wg.nc;
-    const int cnt = min(wg.mpad, Cout - co0);  // real output channels of this block (multiple of 16)
-    const int tap0 = tg * wg.taps, ntaps = min(wg.taps, 27 - tap0);
-    const int mblk = wg.mpad / 8;
-    unsigned char* A = wg_smem;
-    unsigned char* Hs = wg_smem + wg.abytes;
-    const uint32_t a_s = smem_addr(A), h_s = smem_addr(Hs), mbar_s = smem_addr(&mbar);
-    // padded channel rows stay zero
-    for (int e = tid; e < wg.abytes / 16; e += kConvThreads) reinterpret_cast<uint4*>(A)[e] = make_uint4(0, 0, 0, 0);
+    const int cnt = min(wg.nsa == 3 ? Cout : wg.mpad, Cout - co0);  // output channels of this block
+    const int u0 = tg * wg.units, nun = min(wg.units, wg.nunits - u0);
+    const int nkwu = 3 / wg.nkw;  // kw choices left to start addresses
+    const int nq = wg.nc / 8, cbn = cnt / 8;
+    const int albo = wg.mpad / 8 * 128;  // bytes per 8-voxel block of the dY tile
+    const int N = 3 * wg.nkw * wg.nc;
+    const bool bias = Pb != nullptr && tg == 0 && cib == 0;
+    const int stage_bytes = wg.abytes + wg.hbytes;
+    const uint32_t s0 = smem_addr(wg_smem);
+    // padded rows of both dY tiles stay zero
+    for (int e = tid; e < 2 * stage_bytes / 16; e += kWgThreads) {
+        const int st = e / (stage_bytes / 16), o = e - st * (stage_bytes / 16);
+        if (o < wg.abytes / 16) reinterpret_cast<uint4*>(wg_smem + st * stage_bytes)[o] = make_uint4(0, 0, 0, 0);
+    }
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "r"(wg.cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
-    // D F32, A and B BF16, both MN-major, N = nc, M = mpad
+    // D F32, A and B BF16, both MN-major
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                           ((static_cast<uint32_t>(wg.nc) >> 3) << 17) | ((static_cast<uint32_t>(wg.mpad) >> 4) << 24);
+                           ((static_cast<uint32_t>(N) >> 3) << 17) | ((static_cast<uint32_t>(wg.mpad) >> 4) << 24);
+    // per-thread load assignments, fixed over the bricks
+    const int tja = 8 * cbn, rppa = kWgThreads / tja;  // dY: pieces per brick row, rows per pass
+    const int ja_r = tid / tja, ja = tid - ja_r * tja;
+    const int a_vox = ja / cbn, a_cb = ja - a_vox * cbn;
+    const int tjx = kTcHaloW * nq, rppx = kWgThreads / tjx;  // X: pieces per halo row, rows per pass
+    const int jx_r = tid / tjx, jx = tid - jx_r * tjx;
+    const int x_sw = jx / nq, x_q = jx - x_sw * nq;
+    const size_t row_y = static_cast<size_t>(v.W) * Cys, row_x = static_cast<size_t>(v.W) * Cxs;
+    // bias: thread -> (channel c, voxel residue j of nsub)
+    const int nsub = kWgThreads / max(cnt, 1);
+    const int bc = tid % max(cnt, 1), bj = tid / max(cnt, 1);
+    const bool bthread = bias && bj < nsub;
+    const int smid = wg.nsa == 3 ? 1 : 0;
+    float bsum = 0.f;
     const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
     const int first = pc * per, last = min(nbricks, first + per);
-    const int nq = wg.nc / 8;
-    // the first tap group of the first input-channel block also sums dY for the bias
-    const bool bias = Pb != nullptr && tg == 0 && cib == 0 && tid < cnt;
-    float bsum = 0.f;
     bool ok = true;
     int it = 0;
     for (int br = first; br < last; ++br, ++it) {
+        const int sidx = it & 1;
+        const uint32_t a_s = s0 + sidx * stage_bytes, h_s = a_s + wg.abytes;
+        if (it >= 2) {
+            // brick it-2 (phase (it-2)/2 of this stage's barrier) has finished reading the stage
+            ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[sidx]), ((it - 2) >> 1) & 1));
+            if (!ok) break;
+        }
         int r = br;
         const int w0 = (r % nbw) * kTcBW; r /= nbw;
         const int h0 = (r % nbh) * kTcBH; r /= nbh;
         const int d0 = r % v.D;
         const int b = r / v.D;
-        if (it > 0) {
-            // the previous brick's MMAs have read the tiles and every thread has summed its dY column
-            ok = __syncthreads_and(mbar_wait(mbar_s, (it - 1) & 1));
-            if (!ok) break;
+        // dY rows (s, hr): 8 voxels x cbn pieces -> hr * albo + (s * cbn + cb) * 128 + voxel * 16
+        if (ja_r < rppa) {
+            for (int rr = ja_r; rr < 16 * wg.nsa; rr += rppa) {
+                const int sb = rr >> 4, hr = rr & 15;
+                const int d = wg.nsa == 3 ? wrapi(d0 + sb - 1, v.D) : d0;
+                const __nv_bfloat16* src =
+                    dY + ((static_cast<size_t>(b) * v.D + d) * v.H + h0 + hr) * row_y +
+                    static_cast<size_t>(w0 + a_vox) * Cys + co0 + 8 * a_cb;
+                cp_async16(a_s + hr * albo + (sb * cbn + a_cb) * 128 + a_vox * 16, src);
+            }
         }
-        // dY tile: piece (voxel p, 8-channel block cb) -> ((p/8) * mblk + cb) * 128 + (p%8) * 16
-        const int cbn = cnt / 8;
-        for (int e = tid; e < 128 * cbn; e += kConvThreads) {
-            const int p = e / cbn, cb = e - p * cbn;
-            const size_t vox = ((static_cast<size_t>(b) * v.D + d0) * v.H + h0 + p / kTcBW) * v.W + w0 + p % kTcBW;
-            cp_async16(a_s + ((p / 8) * mblk + cb) * 128 + (p % 8) * 16, dY + vox * Cys + co0 + 8 * cb);
-        }
-        // halo planes: slot s = (sd * 18 + sh) * 10 + sw of plane q
-        for (int e = tid; e < nq * 3 * kTcPlaneSlots; e += kConvThreads) {
-            const int q = e / (3 * kTcPlaneSlots), sl = e - q * 3 * kTcPlaneSlots;
-            const int sw = sl % kTcHaloW, shh = (sl / kTcHaloW) % kTcHaloH, sd = sl / kTcPlaneSlots;
-            const int d = wrapi(d0 + sd - 1, v.D), h = wrapi(h0 + shh - 1, v.H), w = wrapi(w0 + sw - 1, v.W);
-            const size_t vox = ((static_cast<size_t>(b) * v.D + d) * v.H + h) * v.W + w;
-            cp_async16(h_s + q * wg.plane + sl * 16, X + vox * Cxs + ci0 + 8 * q);
+        // X halo rows (sd, sh): 10 voxel slots x nq pieces
+        if (jx_r < rppx) {
+            const int w = wrapi(w0 + x_sw - 1, v.W);
+            for (int rr = jx_r; rr < kTcHaloH * wg.npl; rr += rppx) {
+                const int sd = rr / kTcHaloH, sh = rr - sd * kTcHaloH;
+                const int d = wg.npl == 3 ? wrapi(d0 + sd - 1, v.D) : d0;
+                const int h = wrapi(h0 + sh - 1, v.H);
+                const __nv_bfloat16* src = X + ((static_cast<size_t>(b) * v.D + d) * v.H + h) * row_x +
+                                           static_cast<size_t>(w) * Cxs + ci0 + 8 * x_q;
+                if (wg.nkw == 1) {
+                    cp_async16(h_s + (rr * nq + x_q) * 160 + x_sw * 16, src);
+                } else {
+#pragma unroll
+                    for (int kw = 0; kw < 3; ++kw) {
+                        const int ww = x_sw - kw;
+                        if (ww >= 0 && ww < 8) cp_async16(h_s + ((rr * 3 + kw) * nq + x_q) * 128 + ww * 16, src);
+                    }
+                }
+            }
         }
         cp_async_wait();
         asm volatile("fence.proxy.async.shared::cta;");
         asm volatile("tcgen05.fence::before_thread_sync;");
         __syncthreads();
         asm volatile("tcgen05.fence::after_thread_sync;");
-        if (bias) {
-            const unsigned char* col = A + (tid / 8) * 128 + (tid % 8) * 2;
-#pragma unroll 4
-            for (int p = 0; p < 128; ++p)
-                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(col + (p / 8) * mblk * 128 + (p % 8) * 16));
-        }
         if (tid == 0) {
 #pragma unroll 1
-            for (int t = 0; t < ntaps; ++t) {
-                const int tap = tap0 + t;
-                const int kd = tap / 9, kh = (tap / 3) % 3, kw = tap % 3;
+            for (int ks = 0; ks < 8; ++ks) {
+                const uint64_t ad = umma_desc(a_s + 2 * ks * albo, albo, 128);
+                const uint32_t accum = (it > 0 || ks > 0) ? 1u : 0u;
 #pragma unroll 1
-                for (int ks = 0; ks < 8; ++ks) {  // 16 voxels = rows 2 ks, 2 ks + 1 of the brick
-                    const uint64_t ad = umma_desc(a_s + 2 * ks * mblk * 128, mblk * 128, 128);
-                    const uint32_t b_addr = h_s + ((kd * kTcHaloH + 2 * ks + kh) * kTcHaloW + kw) * 16;
-                    const uint64_t bd = umma_desc(b_addr, kTcHaloW * 16, wg.plane);
-                    const uint32_t accum = (it > 0 || ks > 0) ? 1u : 0u;
+                for (int j = 0; j < nun; ++j) {
+                    const int u = u0 + j, kd = u / nkwu, kw = u - kd * nkwu;
+                    const int sd = wg.npl == 3 ? kd : 0;
+                    uint64_t bd;
+                    if (wg.nkw == 1)
+                        bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * nq * 160 + kw * 16, nq * 160, 160);
+                    else
+                        bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * 3 * nq * 128, 3 * nq * 128, 128);
                     asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
                                  " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                     tmem + static_cast<uint32_t>(t * wg.nc)),
+                                     tmem + static_cast<uint32_t>(N * j)),
                                  "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mbar_s)
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                             smem_addr(&mbar[sidx]))
                          : "memory");
         }
+        if (bthread) {
+            const unsigned char* At = wg_smem + sidx * stage_bytes + (smid * cbn + bc / 8) * 128 + (bc % 8) * 2;
+            for (int p = bj; p < 128; p += nsub)
+                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(At + (p / 8) * albo + (p % 8) * 16));
+        }
     }
-    if (ok && it > 0) ok = __syncthreads_and(mbar_wait(mbar_s, (it - 1) & 1));
+    // the last two bricks' commits, oldest first
+    for (int j = max(0, it - 2); j < it && ok; ++j)
+        ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[j & 1]), (j >> 1) & 1));
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) {
         cp_async_wait();
         if (tid == 0) atomicAdd(err, 1);
-    } else if (32 * warp < wg.mpad) {
-        if (bias) Pb[static_cast<size_t>(pc) * Cout + co0 + tid] = bsum;
-        // rows co = co0 + 32 warp + lane; columns t * nc + ci
-        const int co = co0 + 32 * warp + lane;
+    } else if (it > 0) {
+        // an M = 128 accumulator holds row m in lane m, an M = 64 one in lane
+        // (m / 16) * 32 + m % 16; warps w and w + 4 share lane quadrant w % 4
+        const int qd = warp & 3, half = warp >> 2;
+        const int row = wg.mpad == 128 ? 32 * qd + lane : (lane < 16 ? 16 * qd + lane : wg.mpad);
+        const bool valid = row < wg.nsa * cnt;
+        const int sb = valid ? row / cnt : 0;
+        const int co = co0 + (valid ? row - sb * cnt : 0);
+        const uint32_t lane_base = tmem + (static_cast<uint32_t>(32 * qd) << 16);
         float* Pp = P + static_cast<size_t>(pc) * Cout * 27 * Cin;
-        for (int t = 0; t < ntaps; ++t)
-            for (int c = 0; c < wg.nc; c += 16) {
+        for (int j = 0; j < nun; ++j) {
+            const int u = u0 + j, kdu = u / nkwu, kwu = u - kdu * nkwu;
+            const int kd = wg.nsa == 3 ? 2 - sb : kdu;
+            for (int c16 = half; c16 < N / 16; c16 += 2) {
                 uint32_t q[16];
-                if (it > 0) {
-                    const uint32_t ta =
-                        tmem + (static_cast<uint32_t>(32 * warp) << 16) + static_cast<uint32_t>(t * wg.nc + c);
-                    asm volatile(
-                        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,"
-                        "%15}, [%16];"
-                        : "=r"(q[0]), "=r"(q[1]), "=r"(q[2]), "=r"(q[3]), "=r"(q[4]), "=r"(q[5]), "=r"(q[6]),
-                          "=r"(q[7]), "=r"(q[8]), "=r"(q[9]), "=r"(q[10]), "=r"(q[11]), "=r"(q[12]), "=r"(q[13]),
-                          "=r"(q[14]), "=r"(q[15])
-                        : "r"(ta));
-                    asm volatile("tcgen05.wait::ld.sync.aligned;");
+                tmem_ld16(lane_base + static_cast<uint32_t>(N * j + 16 * c16), q);
+                const int n = 16 * c16;
+                int kh, kw, ci;
+                if (wg.nkw == 3) {
+                    kh = n / (3 * wg.nc);
+                    const int rem = n - kh * 3 * wg.nc;
+                    kw = rem / wg.nc;
+                    ci = rem - kw * wg.nc;
                 } else {
-#pragma unroll
-                    for (int j = 0; j < 16; ++j) q[j] = 0u;  // an empty chunk contributes zeros
+                    kh = n / wg.nc;
+                    kw = kwu;
+                    ci = n - kh * wg.nc;
                 }
-                if (co < co0 + cnt) {
-                    float* dst = Pp + (static_cast<size_t>(co) * 27 + tap0 + t) * Cin + ci0 + c;
+                if (valid) {
+                    float* dst = Pp + (static_cast<size_t>(co) * 27 + kd * 9 + kh * 3 + kw) * Cin + ci0 + ci;
 #pragma unroll
-                    for (int j = 0; j < 16; ++j) dst[j] = __uint_as_float(q[j]);
+                    for (int i = 0; i < 16; ++i) dst[i] = __uint_as_float(q[i]);
                 }
             }
+        }
+    }
+    if (bias && ok) {
+        // fixed-order reduction of the voxel residues (the stages are free now)
+        float* red = reinterpret_cast<float*>(wg_smem);
+        __syncthreads();
+        if (bthread) red[bj * cnt + bc] = bsum;
+        __syncthreads();
+        if (tid < cnt) {
+            float t = 0.f;
+            for (int j = 0; j < nsub; ++j) t += red[j * cnt + tid];
+            Pb[static_cast<size_t>(pc) * Cout + co0 + tid] = t;
+        }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
@@ -1090,25 +1180,57 @@ cudaError_t flip_weights(const void* W, int Cout, int Cin, void* Wf, cudaStream_
     return cudaGetLastError();
 }
 
+// input-channel block of the tcgen05 weight gradient forced by
+// claire_net_set_wgrad_tiling (0 = automatic)
+int g_wg_force_nc = 0;
+
+bool wg_tc_config(int Cin, int Cout, int nc, TcWg* wg)
+{
+    if (Cin % nc) return false;
+    TcWg g{};
+    g.nsa = 3 * Cout <= 128 ? 3 : 1;
+    g.npl = g.nsa == 3 ? 1 : 3;
+    g.mpad = g.nsa == 3 ? (3 * Cout <= 64 ? 64 : 128) : (Cout <= 64 ? 64 : 128);
+    g.nco = g.nsa == 3 ? 1 : (Cout + 127) / 128;
+    g.nc = nc;
+    g.nci = Cin / nc;
+    g.nkw = nc == 16 ? 3 : 1;
+    const int N = 3 * g.nkw * nc;
+    g.nunits = (g.nsa == 3 ? 1 : 3) * (3 / g.nkw);
+    g.units = std::min(g.nunits, 512 / N);
+    if (g.units < 1) return false;
+    g.ntg = (g.nunits + g.units - 1) / g.units;
+    g.abytes = 128 * g.mpad * 2;
+    g.hbytes = g.nkw == 3 ? g.npl * kTcHaloH * 3 * (nc / 8) * 128 : g.npl * kTcHaloH * (nc / 8) * 160;
+    g.cols = 32;
+    while (g.cols < static_cast<uint32_t>(N * g.units)) g.cols <<= 1;
+    if (g.cols > 512 || 2 * (g.abytes + g.hbytes) > kTcMaxSmem) return false;
+    g.per_sm = g.cols <= 256 && 2 * (2 * (g.abytes + g.hbytes) + 2048) <= 233472 ? 2 : 1;
+    *wg = g;
+    return true;
+}
+
 bool wg_tc_shape(int Cin, int Cout, int B, int D, int H, int W, int nsm, TcWg* wg, int* nbricks, int* chunks)
 {
     if (H % kTcBH || W % kTcBW || Cin % 16 || Cout % 16) return false;
     TcWg g{};
-    g.mpad = 128;
-    g.nco = (Cout + 127) / 128;
-    g.nc = Cin <= 64 ? Cin : (Cin % 64 == 0 ? 64 : (Cin % 48 == 0 ? 48 : (Cin % 32 == 0 ? 32 : 16)));
-    g.nci = Cin / g.nc;
-    g.taps = std::min(27, 512 / g.nc);
-    g.ntg = (27 + g.taps - 1) / g.taps;
-    g.plane = 3 * kTcPlaneSlots * 16;
-    g.abytes = 128 * g.mpad * 2;
-    g.cols = 32;
-    while (g.cols < static_cast<uint32_t>(g.taps * g.nc)) g.cols <<= 1;
-    if (g.cols > 512 || g.abytes + (g.nc / 8) * g.plane > kTcMaxSmem) return false;
+    if (g_wg_force_nc) {
+        if (!wg_tc_config(Cin, Cout, g_wg_force_nc, &g)) return false;
+    } else {
+        // stacked kd rows: the widest channel block that divides Cin (fewest
+        // passes over each brick); otherwise 16 channels with all nine
+        // (kh, kw) taps in one MMA
+        bool found = false;
+        if (3 * Cout <= 128)
+            for (int nc : {48, 32, 16})
+                if (!found && wg_tc_config(Cin, Cout, nc, &g)) found = true;
+        if (!found && !wg_tc_config(Cin, Cout, 16, &g)) return false;
+    }
     const int nb = B * D * (H / kTcBH) * (W / kTcBW);
+    // one wave of resident CTAs
     const int ctas = g.ntg * g.nco * g.nci;
-    int c = (4 * nsm + ctas - 1) / ctas;
-    c = std::max(1, std::min(c, nb));
+    int c = std::max(1, nsm * g.per_sm / ctas);
+    c = std::min(c, nb);
     const int per = (nb + c - 1) / c;
     *wg = g;
     *nbricks = nb;
@@ -1155,9 +1277,13 @@ cudaError_t conv3d_wgrad(const void* X, int Cxs, int Cin, const void* dY, int Cy
             if (e != cudaSuccess) return e;
             const int per = (nb + chunks - 1) / chunks;
             const Vol v{B, D, H, W};
-            const size_t smem = static_cast<size_t>(g.abytes) + (g.nc / 8) * static_cast<size_t>(g.plane);
+            // enough shared memory that no more CTAs than TMEM holds share an SM
+            // (a surplus one would wait in tcgen05.alloc)
+            const size_t need = 2 * static_cast<size_t>(g.abytes + g.hbytes);
+            const size_t floor_smem = static_cast<size_t>(233472 / (g.per_sm + 1) - 1024);
+            const size_t smem = std::min(std::max(need, floor_smem), static_cast<size_t>(kTcMaxSmem));
             const unsigned grid = static_cast<unsigned>(g.ntg * g.nco * g.nci * chunks);
-            k_wgrad_tc<<<grid, kConvThreads, smem, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, Cin,
+            k_wgrad_tc<<<grid, kWgThreads, smem, st>>>(static_cast<const __nv_bfloat16*>(X), Cxs, Cin,
                                                         static_cast<const __nv_bfloat16*>(dY), Cys, Cout, v, g, nb,
                                                         per, chunks, part, db ? partb : nullptr, err);
             const size_t nw = static_cast<size_t>(Cout) * 27 * Cin;
@@ -1561,6 +1687,14 @@ extern "C" claire_status claire_net_device_errors(int* count, int reset)
     const int n = read_tc_errors(reset != 0);
     if (n < 0) return net_status(cudaErrorUnknown, "device_errors");
     *count = n;
+    return CLAIRE_OK;
+}
+
+extern "C" claire_status claire_net_set_wgrad_tiling(int nc)
+{
+    if (nc != 0 && nc != 16 && nc != 32 && nc != 48 && nc != 64)
+        return net_fail("set_wgrad_tiling: nc %d not in {0, 16, 32, 48, 64}", nc);
+    g_wg_force_nc = nc;
     return CLAIRE_OK;
 }
 

@@ -48,6 +48,7 @@ _SIGS = {
     "claire_net_residual": [_vp, _vp, _sz, _vp, _vp, _vp],
     "claire_net_device_errors": [_ip, _i],
     "claire_net_set_conv_tiling": [_i, _i],
+    "claire_net_set_wgrad_tiling": [_i],
     "claire_net_last_error": [],
 }
 _RESTYPE = {"claire_net_last_error": ctypes.c_char_p}
@@ -86,6 +87,11 @@ def device_errors(reset=True):
 def set_conv_tiling(bdc=0, nstage=0):
     """Force the tcgen05 convolution's brick depth / staging (0, 0 = automatic)."""
     _check(lib().claire_net_set_conv_tiling(int(bdc), int(nstage)), "set_conv_tiling")
+
+
+def set_wgrad_tiling(nc=0):
+    """Force the tcgen05 weight gradient's input-channel block (0 = automatic)."""
+    _check(lib().claire_net_set_wgrad_tiling(int(nc)), "set_wgrad_tiling")
 
 
 def _addr(t):

@@ -51,6 +51,9 @@ def test_every_network_symbol_is_exported(claire):
     assert b"powers of two" in lib.claire_net_last_error()
     good = (ctypes.c_int * 4)(1, 8, 8, 8)
     assert lib.claire_net_conv3d_wgrad_chunks(24, 16, good, ctypes.byref(chunks)) == -1
+    assert lib.claire_net_set_wgrad_tiling(24) == -1
+    assert b"set_wgrad_tiling" in lib.claire_net_last_error()
+    assert lib.claire_net_set_wgrad_tiling(0) == 0
 
 
 def test_net_layer_table_has_the_stated_size(claire):

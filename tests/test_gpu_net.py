@@ -153,6 +153,36 @@ def test_conv3d_weight_gradient(env, case):
     assert torch.equal(dw, dw2)
 
 
+@pytest.mark.parametrize("co", [144, 32, 16])
+@pytest.mark.parametrize("nc", [16, 32, 48, 64])
+def test_conv3d_weight_gradient_tcgen05_tilings(env, nc, co):
+    """Every input-channel block of the tcgen05 weight gradient against the
+    oracle, for output channels as plain MMA rows (144: two blocks, 128 + 16,
+    padded TMEM lanes) and as stacked depth-shifted rows (32: 96 of 128
+    lanes; 16: 48 of 64), several tap groups where TMEM cannot hold all
+    taps, and several bricks per CTA so that both smem stages turn over."""
+    torch, net = env
+    B, D, H, W, ci = 1, 16, 16, 16, 192
+    r = np.random.default_rng(nc + co)
+    xbuf = bf16(torch, r.standard_normal((B, D, H, W, ci)))
+    dybuf = bf16(torch, r.standard_normal((B, D, H, W, co)))
+    net.set_wgrad_tiling(nc)
+    try:
+        chunks = net.wgrad_chunks(ci, co, (B, D, H, W))
+        part = torch.empty(chunks * co * 27 * ci, device="cuda")
+        partb = torch.empty(chunks * co, device="cuda")
+        dw = torch.empty((co, 27, ci), device="cuda")
+        db = torch.empty(co, device="cuda")
+        net.conv3d_wgrad(net.Act(xbuf, 0, ci), net.Act(dybuf, 0, co), chunks, part, partb, dw, db, stream(torch))
+        torch.cuda.synchronize()
+    finally:
+        net.set_wgrad_tiling(0)
+    rw, rb = onet.conv3d_weight_grad(f64(xbuf), f64(dybuf))
+    assert rel_l2(f64(dw), rw) < 1e-4
+    assert rel_l2(f64(db), rb) < 1e-4
+    assert net.device_errors() == 0
+
+
 def test_pool_up_leaky_pack_head_adam(env):
     torch, net = env
     r = np.random.default_rng(7)

@@ -49,6 +49,12 @@ __device__ __forceinline__ void cp_async16(uint32_t dst, const void* src)
     asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
 }
 
+// L1-allocating variant, for sources read more than once by the same CTA
+__device__ __forceinline__ void cp_async16_ca(uint32_t dst, const void* src)
+{
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(dst), "l"(src));
+}
+
 __device__ __forceinline__ void cp_async_wait()
 {
     asm volatile("cp.async.wait_all;\n" ::);
@@ -455,12 +461,17 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
 // offset) or all nine (kh, kw) taps (nkw = 3, for 16-channel blocks: each
 // (sd, sh) row holds the three kw-shifted copies of its eight brick voxels).
 // An MMA "unit" is one (kd, kw) choice left to the start addresses; a CTA
-// holds `units` of them in TMEM and walks its chunk of bricks through two
-// smem stages, loading brick i+1 while the tensor cores work on brick i (one
-// mbarrier per stage, so each wait is for the newest phase of its barrier).
-// The bias sums dY on the CUDA cores.  Per-chunk FP32 partials are reduced in
-// a fixed order afterwards.
+// holds `units` of them in TMEM.
+// Warp roles.  Warps 2..7 form nstage loader groups; group g stages bricks
+// g, g + nstage, ... into smem stage g with cp.async and announces each on
+// the stage's "full" mbarrier; lane 0 of warp 0 issues the MMAs of a full
+// stage and frees it through tcgen05.commit on its "empty" mbarrier; warp 1
+// sums dY for the bias from the same stage and also arrives on "empty".
+// Each stage is used by every nstage-th brick, so every wait is for the
+// newest phase of its barrier.  Per-chunk FP32 partials are reduced in a
+// fixed order afterwards.
 constexpr int kWgThreads = 256;
+constexpr int kWgLoaders = 192;  // warps 2..7
 
 struct TcWg {
     int nsa;        // dY row blocks (3: kd from the rows, 1: plain)
@@ -475,8 +486,14 @@ struct TcWg {
     int abytes;     // bytes of the dY tile (128 voxels x mpad rows x 2)
     int hbytes;     // bytes of the X halo
     int per_sm;     // CTAs resident per SM (TMEM)
+    int nstage;     // smem stages (2 or 3)
     uint32_t cols;  // TMEM columns allocated
 };
+
+__device__ __forceinline__ void mbar_arrive(uint32_t mbar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(mbar) : "memory");
+}
 
 __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __restrict__ X, int Cxs, int Cin,
                                                          const __nv_bfloat16* __restrict__ dY, int Cys, int Cout,
@@ -485,8 +502,9 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
                                                          int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char wg_smem[];
-    __shared__ __align__(8) uint64_t mbar[2];
+    __shared__ __align__(8) uint64_t full[3], empty[3];
     __shared__ uint32_t tmem_slot;
+    __shared__ int failed;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int bid = blockIdx.x;
     const int pc = bid % chunks; bid /= chunks;
@@ -501,134 +519,196 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
     const int albo = wg.mpad / 8 * 128;  // bytes per 8-voxel block of the dY tile
     const int N = 3 * wg.nkw * wg.nc;
     const bool bias = Pb != nullptr && tg == 0 && cib == 0;
+    const int S = wg.nstage;
     const int stage_bytes = wg.abytes + wg.hbytes;
     const uint32_t s0 = smem_addr(wg_smem);
-    // padded rows of both dY tiles stay zero
-    for (int e = tid; e < 2 * stage_bytes / 16; e += kWgThreads) {
+    const int first = pc * per, nbr = max(0, min(nbricks, first + per) - first);
+    // padded rows of every dY tile stay zero
+    for (int e = tid; e < S * stage_bytes / 16; e += kWgThreads) {
         const int st = e / (stage_bytes / 16), o = e - st * (stage_bytes / 16);
         if (o < wg.abytes / 16) reinterpret_cast<uint4*>(wg_smem + st * stage_bytes)[o] = make_uint4(0, 0, 0, 0);
     }
+    asm volatile("fence.proxy.async.shared::cta;");
     if (warp == 0) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tmem_slot)),
                      "r"(wg.cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[0])), "r"(1));
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&mbar[1])), "r"(1));
+        for (int i = 0; i < 3; ++i) {
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[i])), "r"(kWgLoaders / S));
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[i])), "r"(bias ? 2 : 1));
+        }
+        failed = 0;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
-    // D F32, A and B BF16, both MN-major
-    const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
-                           ((static_cast<uint32_t>(N) >> 3) << 17) | ((static_cast<uint32_t>(wg.mpad) >> 4) << 24);
-    // per-thread load assignments, fixed over the bricks
-    const int tja = 8 * cbn, rppa = kWgThreads / tja;  // dY: pieces per brick row, rows per pass
-    const int ja_r = tid / tja, ja = tid - ja_r * tja;
-    const int a_vox = ja / cbn, a_cb = ja - a_vox * cbn;
-    const int tjx = kTcHaloW * nq, rppx = kWgThreads / tjx;  // X: pieces per halo row, rows per pass
-    const int jx_r = tid / tjx, jx = tid - jx_r * tjx;
-    const int x_sw = jx / nq, x_q = jx - x_sw * nq;
-    const size_t row_y = static_cast<size_t>(v.W) * Cys, row_x = static_cast<size_t>(v.W) * Cxs;
-    // bias: thread -> (channel c, voxel residue j of nsub)
-    const int nsub = kWgThreads / max(cnt, 1);
-    const int bc = tid % max(cnt, 1), bj = tid / max(cnt, 1);
-    const bool bthread = bias && bj < nsub;
     const int smid = wg.nsa == 3 ? 1 : 0;
-    float bsum = 0.f;
-    const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
-    const int first = pc * per, last = min(nbricks, first + per);
-    bool ok = true;
-    int it = 0;
-    for (int br = first; br < last; ++br, ++it) {
-        const int sidx = it & 1;
-        const uint32_t a_s = s0 + sidx * stage_bytes, h_s = a_s + wg.abytes;
-        if (it >= 2) {
-            // brick it-2 (phase (it-2)/2 of this stage's barrier) has finished reading the stage
-            ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[sidx]), ((it - 2) >> 1) & 1));
-            if (!ok) break;
-        }
-        int r = br;
-        const int w0 = (r % nbw) * kTcBW; r /= nbw;
-        const int h0 = (r % nbh) * kTcBH; r /= nbh;
-        const int d0 = r % v.D;
-        const int b = r / v.D;
-        // dY rows (s, hr): 8 voxels x cbn pieces -> hr * albo + (s * cbn + cb) * 128 + voxel * 16
-        if (ja_r < rppa) {
-            for (int rr = ja_r; rr < 16 * wg.nsa; rr += rppa) {
-                const int sb = rr >> 4, hr = rr & 15;
-                const int d = wg.nsa == 3 ? wrapi(d0 + sb - 1, v.D) : d0;
-                const __nv_bfloat16* src =
-                    dY + ((static_cast<size_t>(b) * v.D + d) * v.H + h0 + hr) * row_y +
-                    static_cast<size_t>(w0 + a_vox) * Cys + co0 + 8 * a_cb;
-                cp_async16(a_s + hr * albo + (sb * cbn + a_cb) * 128 + a_vox * 16, src);
-            }
-        }
-        // X halo rows (sd, sh): 10 voxel slots x nq pieces
-        if (jx_r < rppx) {
-            const int w = wrapi(w0 + x_sw - 1, v.W);
-            for (int rr = jx_r; rr < kTcHaloH * wg.npl; rr += rppx) {
-                const int sd = rr / kTcHaloH, sh = rr - sd * kTcHaloH;
-                const int d = wg.npl == 3 ? wrapi(d0 + sd - 1, v.D) : d0;
-                const int h = wrapi(h0 + sh - 1, v.H);
-                const __nv_bfloat16* src = X + ((static_cast<size_t>(b) * v.D + d) * v.H + h) * row_x +
-                                           static_cast<size_t>(w) * Cxs + ci0 + 8 * x_q;
-                if (wg.nkw == 1) {
-                    cp_async16(h_s + (rr * nq + x_q) * 160 + x_sw * 16, src);
-                } else {
+    // bias warp: lane -> (8-channel block cb, voxel residue r of nres)
+    const int nres = 32 / max(cbn, 1);
+    const int b_cb = lane % max(cbn, 1), b_r = lane / max(cbn, 1);
+    float bacc[8];
 #pragma unroll
-                    for (int kw = 0; kw < 3; ++kw) {
-                        const int ww = x_sw - kw;
-                        if (ww >= 0 && ww < 8) cp_async16(h_s + ((rr * 3 + kw) * nq + x_q) * 128 + ww * 16, src);
+    for (int i = 0; i < 8; ++i) bacc[i] = 0.f;
+    bool ok = true;
+    if (warp >= 2) {
+        // ---- loaders: group g of kWgLoaders / S threads owns stage g and
+        // stages bricks g, g + S, g + 2S, ... (S independent load chains) ----
+        const int nl = kWgLoaders / S;
+        const int grp = (tid - 64) / nl, lt = (tid - 64) - grp * nl;
+        // a row's pieces are spread over the group's threads (several rows
+        // per pass when a row has fewer pieces than the group has threads)
+        const int tja = 8 * cbn;  // dY: pieces per brick row
+        const int rppa = tja <= nl ? nl / tja : 1, stepa = tja <= nl ? tja : nl;
+        const int ja_r = tja <= nl ? lt / tja : 0, ja0 = tja <= nl ? lt - ja_r * tja : lt;
+        const int tjx = kTcHaloW * nq;  // X: pieces per halo row
+        const int rppx = tjx <= nl ? nl / tjx : 1, stepx = tjx <= nl ? tjx : nl;
+        const int jx_r = tjx <= nl ? lt / tjx : 0, jx0 = tjx <= nl ? lt - jx_r * tjx : lt;
+        const size_t row_y = static_cast<size_t>(v.W) * Cys, row_x = static_cast<size_t>(v.W) * Cxs;
+        const int nbw = v.W / kTcBW, nbh = v.H / kTcBH;
+        const uint32_t a_s = s0 + grp * stage_bytes, h_s = a_s + wg.abytes;
+        for (int j = grp; j < nbr; j += S) {
+            if (j >= S) {
+                // the MMAs (and bias sums) of brick j - S are done with this stage
+                bool w = true;
+                if (lane == 0) w = mbar_wait(smem_addr(&empty[grp]), ((j / S) - 1) & 1);
+                w = __shfl_sync(0xffffffffu, w, 0);
+                if (!w) {
+                    ok = false;
+                    break;
+                }
+            }
+            int r = first + j;
+            const int w0 = (r % nbw) * kTcBW; r /= nbw;
+            const int h0 = (r % nbh) * kTcBH; r /= nbh;
+            const int d0 = r % v.D;
+            const int b = r / v.D;
+            // dY rows (s, hr): 8 voxels x cbn pieces -> hr * albo + (s * cbn + cb) * 128 + voxel * 16
+            if (ja_r < rppa) {
+                for (int rr = ja_r; rr < 16 * wg.nsa; rr += rppa) {
+                    const int sb = rr >> 4, hr = rr & 15;
+                    const int d = wg.nsa == 3 ? wrapi(d0 + sb - 1, v.D) : d0;
+                    const __nv_bfloat16* rowp = dY + ((static_cast<size_t>(b) * v.D + d) * v.H + h0 + hr) * row_y +
+                                                static_cast<size_t>(w0) * Cys + co0;
+                    for (int jj = ja0; jj < tja; jj += stepa) {
+                        const int vox = jj / cbn, cb = jj - vox * cbn;
+                        cp_async16(a_s + hr * albo + (sb * cbn + cb) * 128 + vox * 16,
+                                   rowp + static_cast<size_t>(vox) * Cys + 8 * cb);
                     }
                 }
             }
-        }
-        cp_async_wait();
-        asm volatile("fence.proxy.async.shared::cta;");
-        asm volatile("tcgen05.fence::before_thread_sync;");
-        __syncthreads();
-        asm volatile("tcgen05.fence::after_thread_sync;");
-        if (tid == 0) {
-#pragma unroll 1
-            for (int ks = 0; ks < 8; ++ks) {
-                const uint64_t ad = umma_desc(a_s + 2 * ks * albo, albo, 128);
-                const uint32_t accum = (it > 0 || ks > 0) ? 1u : 0u;
-#pragma unroll 1
-                for (int j = 0; j < nun; ++j) {
-                    const int u = u0 + j, kd = u / nkwu, kw = u - kd * nkwu;
-                    const int sd = wg.npl == 3 ? kd : 0;
-                    uint64_t bd;
-                    if (wg.nkw == 1)
-                        bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * nq * 160 + kw * 16, nq * 160, 160);
-                    else
-                        bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * 3 * nq * 128, 3 * nq * 128, 128);
-                    asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
-                                 " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
-                                     tmem + static_cast<uint32_t>(N * j)),
-                                 "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+            // X halo rows (sd, sh): 10 voxel slots x nq pieces
+            if (jx_r < rppx) {
+                for (int rr = jx_r; rr < kTcHaloH * wg.npl; rr += rppx) {
+                    const int sd = rr / kTcHaloH, sh = rr - sd * kTcHaloH;
+                    const int d = wg.npl == 3 ? wrapi(d0 + sd - 1, v.D) : d0;
+                    const int h = wrapi(h0 + sh - 1, v.H);
+                    const __nv_bfloat16* rowp =
+                        X + ((static_cast<size_t>(b) * v.D + d) * v.H + h) * row_x + ci0;
+                    for (int jj = jx0; jj < tjx; jj += stepx) {
+                        const int x_sw = jj / nq, x_q = jj - x_sw * nq;
+                        const __nv_bfloat16* src =
+                            rowp + static_cast<size_t>(wrapi(w0 + x_sw - 1, v.W)) * Cxs + 8 * x_q;
+                        if (wg.nkw == 1) {
+                            cp_async16(h_s + (rr * nq + x_q) * 160 + x_sw * 16, src);
+                        } else {
+#pragma unroll
+                            for (int kw = 0; kw < 3; ++kw) {
+                                const int ww = x_sw - kw;
+                                if (ww >= 0 && ww < 8)
+                                    cp_async16_ca(h_s + ((rr * 3 + kw) * nq + x_q) * 128 + ww * 16, src);
+                            }
+                        }
+                    }
                 }
             }
-            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                             smem_addr(&mbar[sidx]))
-                         : "memory");
+            // this thread's part of brick j has landed: make it visible to the
+            // tensor cores and announce it
+            cp_async_wait();
+            asm volatile("fence.proxy.async.shared::cta;");
+            mbar_arrive(smem_addr(&full[grp]));
         }
-        if (bthread) {
-            const unsigned char* At = wg_smem + sidx * stage_bytes + (smid * cbn + bc / 8) * 128 + (bc % 8) * 2;
-            for (int p = bj; p < 128; p += nsub)
-                bsum += __bfloat162float(*reinterpret_cast<const __nv_bfloat16*>(At + (p / 8) * albo + (p % 8) * 16));
+        cp_async_wait();
+    } else if (warp == 0) {
+        // ---- MMA issue ----
+        if (lane == 0) {
+            const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | (1u << 15) | (1u << 16) |
+                                   ((static_cast<uint32_t>(N) >> 3) << 17) |
+                                   ((static_cast<uint32_t>(wg.mpad) >> 4) << 24);
+            for (int j = 0; j < nbr; ++j) {
+                const int sidx = j % S;
+                if (!mbar_wait(smem_addr(&full[sidx]), (j / S) & 1)) {
+                    ok = false;
+                    break;
+                }
+                asm volatile("tcgen05.fence::after_thread_sync;");
+                const uint32_t a_s = s0 + sidx * stage_bytes, h_s = a_s + wg.abytes;
+#pragma unroll 1
+                for (int ks = 0; ks < 8; ++ks) {
+                    const uint64_t ad = umma_desc(a_s + 2 * ks * albo, albo, 128);
+                    const uint32_t accum = (j > 0 || ks > 0) ? 1u : 0u;
+#pragma unroll 1
+                    for (int jj = 0; jj < nun; ++jj) {
+                        const int u = u0 + jj, kd = u / nkwu, kw = u - kd * nkwu;
+                        const int sd = wg.npl == 3 ? kd : 0;
+                        uint64_t bd;
+                        if (wg.nkw == 1)
+                            bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * nq * 160 + kw * 16, nq * 160, 160);
+                        else
+                            bd = umma_desc(h_s + (sd * kTcHaloH + 2 * ks) * 3 * nq * 128, 3 * nq * 128, 128);
+                        asm volatile("{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+                                     " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}\n" ::"r"(
+                                         tmem + static_cast<uint32_t>(N * jj)),
+                                     "l"(ad), "l"(bd), "r"(idesc), "r"(accum));
+                    }
+                }
+                asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                                 smem_addr(&empty[sidx]))
+                             : "memory");
+            }
+        }
+    } else if (bias) {
+        // ---- bias sums (warp 1) ----
+        for (int j = 0; j < nbr; ++j) {
+            const int sidx = j % S;
+            bool w = true;
+            if (lane == 0) w = mbar_wait(smem_addr(&full[sidx]), (j / S) & 1);
+            w = __shfl_sync(0xffffffffu, w, 0);
+            if (!w) {
+                ok = false;
+                break;
+            }
+            if (b_r < nres) {
+                const unsigned char* At = wg_smem + sidx * stage_bytes + (smid * cbn + b_cb) * 128;
+                for (int p = b_r; p < 128; p += nres) {
+                    const uint4 q4 = *reinterpret_cast<const uint4*>(At + (p / 8) * albo + (p % 8) * 16);
+                    const __nv_bfloat162* h2 = reinterpret_cast<const __nv_bfloat162*>(&q4);
+#pragma unroll
+                    for (int i = 0; i < 4; ++i) {
+                        const float2 f = __bfloat1622float2(h2[i]);
+                        bacc[2 * i] += f.x;
+                        bacc[2 * i + 1] += f.y;
+                    }
+                }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(smem_addr(&empty[sidx]));
         }
     }
-    // the last two bricks' commits, oldest first
-    for (int j = max(0, it - 2); j < it && ok; ++j)
-        ok = __syncthreads_and(mbar_wait(smem_addr(&mbar[j & 1]), (j >> 1) & 1));
+    if (!ok) failed = 1;
+    __syncthreads();
+    // the last brick's stage is released once all MMAs (each commit covers
+    // the earlier ones) and the bias sums are done
+    bool okw = failed == 0;
+    if (okw && nbr > 0 && tid == 0)
+        okw = mbar_wait(smem_addr(&empty[(nbr - 1) % S]), ((nbr - 1) / S) & 1);
+    ok = __syncthreads_and(okw);
     asm volatile("tcgen05.fence::after_thread_sync;");
     if (!ok) {
-        cp_async_wait();
         if (tid == 0) atomicAdd(err, 1);
-    } else if (it > 0) {
+    } else if (nbr > 0) {
         // an M = 128 accumulator holds row m in lane m, an M = 64 one in lane
         // (m / 16) * 32 + m % 16; warps w and w + 4 share lane quadrant w % 4
         const int qd = warp & 3, half = warp >> 2;
@@ -663,17 +743,18 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
                 }
             }
         }
-    }
-    if (bias && ok) {
-        // fixed-order reduction of the voxel residues (the stages are free now)
-        float* red = reinterpret_cast<float*>(wg_smem);
-        __syncthreads();
-        if (bthread) red[bj * cnt + bc] = bsum;
-        __syncthreads();
-        if (tid < cnt) {
-            float t = 0.f;
-            for (int j = 0; j < nsub; ++j) t += red[j * cnt + tid];
-            Pb[static_cast<size_t>(pc) * Cout + co0 + tid] = t;
+        if (bias) {
+            // fixed-order reduction of the bias warp's voxel residues (the stages are free now)
+            float* red = reinterpret_cast<float*>(wg_smem);
+            if (warp == 1 && b_r < nres)
+#pragma unroll
+                for (int i = 0; i < 8; ++i) red[b_r * cnt + b_cb * 8 + i] = bacc[i];
+            __syncthreads();
+            if (tid < cnt) {
+                float t = 0.f;
+                for (int j = 0; j < nres; ++j) t += red[j * cnt + tid];
+                Pb[static_cast<size_t>(pc) * Cout + co0 + tid] = t;
+            }
         }
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
@@ -1204,8 +1285,17 @@ bool wg_tc_config(int Cin, int Cout, int nc, TcWg* wg)
     g.hbytes = g.nkw == 3 ? g.npl * kTcHaloH * 3 * (nc / 8) * 128 : g.npl * kTcHaloH * (nc / 8) * 160;
     g.cols = 32;
     while (g.cols < static_cast<uint32_t>(N * g.units)) g.cols <<= 1;
-    if (g.cols > 512 || 2 * (g.abytes + g.hbytes) > kTcMaxSmem) return false;
-    g.per_sm = g.cols <= 256 && 2 * (2 * (g.abytes + g.hbytes) + 2048) <= 233472 ? 2 : 1;
+    const int stage = g.abytes + g.hbytes;
+    if (g.cols > 512 || 2 * stage > kTcMaxSmem) return false;
+    // two CTAs per SM where TMEM and shared memory allow (each with as many
+    // stages, up to three, as half the SM holds), else one with up to three
+    if (g.cols <= 256 && 2 * (2 * stage + 2048) <= 233472) {
+        g.per_sm = 2;
+        g.nstage = 2 * (3 * stage + 2048) <= 233472 ? 3 : 2;
+    } else {
+        g.per_sm = 1;
+        g.nstage = 3 * stage <= kTcMaxSmem ? 3 : 2;
+    }
     *wg = g;
     return true;
 }
@@ -1279,7 +1369,7 @@ cudaError_t conv3d_wgrad(const void* X, int Cxs, int Cin, const void* dY, int Cy
             const Vol v{B, D, H, W};
             // enough shared memory that no more CTAs than TMEM holds share an SM
             // (a surplus one would wait in tcgen05.alloc)
-            const size_t need = 2 * static_cast<size_t>(g.abytes + g.hbytes);
+            const size_t need = static_cast<size_t>(g.nstage) * (g.abytes + g.hbytes);
             const size_t floor_smem = static_cast<size_t>(233472 / (g.per_sm + 1) - 1024);
             const size_t smem = std::min(std::max(need, floor_smem), static_cast<size_t>(kTcMaxSmem));
             const unsigned grid = static_cast<unsigned>(g.ntg * g.nco * g.nci * chunks);

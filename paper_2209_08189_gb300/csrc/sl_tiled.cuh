@@ -114,6 +114,10 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
             const long long o3e = o3 & ~1LL;
             e3 = (e3 + (o3 - o3e) + 1) & ~1LL;
             o3 = o3e;
+        } else if ((g.n3 & 3) == 0) {  // x3 origin and extent multiples of 4: 16-byte row chunks
+            const long long o3e = o3 & ~3LL;
+            e3 = (e3 + (o3 - o3e) + 3) & ~3LL;
+            o3 = o3e;
         }
         const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M;
         const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
@@ -154,6 +158,35 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
     int gk1 = w3 + lane + 32;
     gk1 = gk1 >= g.n3 ? gk1 - g.n3 : gk1;
     if constexpr (sizeof(S) == 4) {
+        if (((bp.O3 | bp.E3 | g.n3) & 3) == 0) {
+            // 16-byte chunks: a chunk never straddles the x3 wrap (n3 and the
+            // origin are multiples of 4); 16 threads per row, 16 rows per pass
+            const int nch = bp.E3 >> 2, rows = bp.E1 * bp.E2;
+            const int ch0 = threadIdx.x & 15;
+            int r = threadIdx.x >> 4;
+            int a = r / bp.E2, b = r - a * bp.E2;
+            for (; r < rows; r += kTileThreads / 16) {
+                int gi = w1 + a;
+                gi = gi >= g.n1 ? gi - g.n1 : gi;
+                int gj = w2 + b;
+                gj = gj >= g.n2 ? gj - g.n2 : gj;
+                const float* src = reinterpret_cast<const float*>(f) + static_cast<size_t>(gi) * g.n23 +
+                                   static_cast<size_t>(gj) * g.n3;
+                const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(box + r * bp.S3));
+                for (int c = ch0; c < nch; c += 16) {
+                    int gk = w3 + 4 * c;
+                    gk = gk >= g.n3 ? gk - g.n3 : gk;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * c), "l"(src + gk)
+                                 : "memory");
+                }
+                b += kTileThreads / 16;
+                while (b >= bp.E2) {
+                    b -= bp.E2;
+                    ++a;
+                }
+            }
+            return;
+        }
         for (int a = 0; a < bp.E1; ++a) {
             int gi = w1 + a;
             gi = gi >= g.n1 ? gi - g.n1 : gi;
@@ -269,21 +302,28 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
 #if CLAIRE_FFMA2
     // rows b and b+1 of plane a are contracted along x3 together in one
     // packed FMA per node; then the x2 weights pair up the same way
+    // rows b and b+1 of plane a are contracted together, one packed FMA per
+    // x3 node with the products w2[b] w3[c], w2[b+1] w3[c] formed once per point
     const uint32_t base = smem_u32(box) + 4u * static_cast<uint32_t>(o);
     const uint32_t P4 = 4u * static_cast<uint32_t>(P), S4 = 4u * static_cast<uint32_t>(bp.S3);
+    float2 W[M / 2][M];
+#pragma unroll
+    for (int b = 0; b < M; b += 2)
+#pragma unroll
+        for (int c = 0; c < M; ++c) W[b / 2][c] = __fmul2_rn(make_float2(w2[b], w2[b + 1]), make_float2(w3[c], w3[c]));
 #pragma unroll
     for (int a = 0; a < M; ++a) {
-        float2 acc = make_float2(0.0f, 0.0f);
+        const uint32_t r0a = base + a * P4;
+        float2 acc = __fmul2_rn(W[0][0], make_float2(lds_f32<0>(r0a), lds_f32<0>(r0a + S4)));
 #pragma unroll
         for (int b = 0; b < M; b += 2) {
-            const uint32_t r0 = base + a * P4 + b * S4, r1 = r0 + S4;
-            float2 sb = make_float2(w3[0] * lds_f32<0>(r0), w3[0] * lds_f32<0>(r1));
-            sb = __ffma2_rn(make_float2(w3[1], w3[1]), make_float2(lds_f32<4>(r0), lds_f32<4>(r1)), sb);
+            const uint32_t r0 = r0a + b * S4, r1 = r0 + S4;
+            if (b > 0) acc = __ffma2_rn(W[b / 2][0], make_float2(lds_f32<0>(r0), lds_f32<0>(r1)), acc);
+            acc = __ffma2_rn(W[b / 2][1], make_float2(lds_f32<4>(r0), lds_f32<4>(r1)), acc);
             if constexpr (Scheme<ORDER>::M == 4) {
-                sb = __ffma2_rn(make_float2(w3[2], w3[2]), make_float2(lds_f32<8>(r0), lds_f32<8>(r1)), sb);
-                sb = __ffma2_rn(make_float2(w3[3], w3[3]), make_float2(lds_f32<12>(r0), lds_f32<12>(r1)), sb);
+                acc = __ffma2_rn(W[b / 2][2], make_float2(lds_f32<8>(r0), lds_f32<8>(r1)), acc);
+                acc = __ffma2_rn(W[b / 2][3], make_float2(lds_f32<12>(r0), lds_f32<12>(r1)), acc);
             }
-            acc = __ffma2_rn(make_float2(w2[b], w2[b + 1]), sb, acc);
         }
         val = fmaf(w1[a], acc.x + acc.y, val);
     }

@@ -796,7 +796,7 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
             KTimer t(c, KK_FFT, 0, 0);
             CL_FFT(c, cufftExecR2C(c->r2c, c->g, c->spec));
         }
-        KTimer t(c, KK_SPECTRAL, 96.0 * M, 0, 3);
+        KTimer t(c, KK_SPECTRAL, 72.0 * M, 0, 3);
         launch_fs_start(c->grid, c->spec, c->rh, c->xh, c->M, op, c->rp, scale, c->partials,
                         c->partials + c->red_blocks, c->red_blocks, c->stream);
     }
@@ -813,9 +813,9 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         {
             PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
             {
-                KTimer t(c, KK_SPECTRAL, 120.0 * M, 0);
-                launch_spectral_direction(c->grid, c->spec, c->phat, c->spec2, c->M,
-                                          static_cast<float>(it == 1 ? 0.0 : rz / rz_prev), it == 1 ? 1 : 0,
+                KTimer t(c, KK_SPECTRAL, (it == 1 ? 72.0 : 96.0) * M, 0);
+                launch_spectral_direction(c->grid, c->rh, c->phat, c->spec2, c->M,
+                                          static_cast<float>(it == 1 ? 0.0 : rz / rz_prev), it == 1 ? 1 : 0, op,
                                           c->rp, c->stream);
                 CL_LAUNCHED(c);
             }
@@ -829,7 +829,7 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
                 KTimer t(c, KK_FFT, 0, 0);
                 CL_FFT(c, cufftExecR2C(c->r2c, c->z, c->spec2));
             }
-            KTimer t(c, KK_SPECTRAL, 96.0 * M, 0, 2);
+            KTimer t(c, KK_SPECTRAL, 72.0 * M, 0, 2);
             launch_fs_hp(c->grid, c->spec, c->spec2, c->phat, c->M, c->o.grad_form, c->rp, scale,
                          c->partials, c->red_blocks, c->stream);
         }

@@ -151,8 +151,9 @@ void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp
 void launch_spectral_precond(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op,
                              RegParams rp, float scale, double* partials, int nblocks, cudaStream_t st);
 // PCG direction in Fourier space: ph = zh + beta ph (first: ph = zh), cp = ph, zh <- S ph.
-void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph, cufftComplex* cp,
-                               size_t cstride, float beta, int first, RegParams rp, cudaStream_t st);
+void launch_spectral_direction(const Grid& g, const cufftComplex* rh, cufftComplex* ph, cufftComplex* cp,
+                               size_t cstride, float beta, int first, SpectralOp op, RegParams rp,
+                               cudaStream_t st);
 
 // Fourier-space PCG (vectors are half spectra scaled by 1/N; partial sums are
 // of sum_k wt Re(conj(a) b), wt the multiplicity of the mode):

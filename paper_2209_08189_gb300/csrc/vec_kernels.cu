@@ -156,37 +156,31 @@ __global__ void __launch_bounds__(kThreads) k_spectral_precond(Grid g, float2* _
     block_sum(acc, partials);
 }
 
-// PCG direction in Fourier space: ph = zh + beta ph (ph = zh when first),
-// copy ph -> cp (consumed by the inverse FFT that yields p), and zh <- S ph
-// (inverse FFT yields S p for the matvec).
-__global__ void __launch_bounds__(kThreads) k_spectral_direction(Grid g, float2* __restrict__ zh,
+// PCG direction in Fourier space: z~ = M r~ (recomputed from r~, not
+// stored), p~ = z~ + beta p~ (p~ = z~ when first), copied to cp for the
+// inverse FFT that yields p (it overwrites its input).
+__global__ void __launch_bounds__(kThreads) k_spectral_direction(Grid g, const float2* __restrict__ rh,
                                                                   float2* __restrict__ ph,
                                                                   float2* __restrict__ cp, size_t cs,
-                                                                  float beta, int first, RegParams rp)
+                                                                  float beta, int first, int op, RegParams rp)
 {
     const int n3h = g.n3 / 2 + 1;
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
     for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
          idx += static_cast<size_t>(gridDim.x) * kThreads) {
-        float2 p[3];
+        const Mode m = mode_of(g, idx, n3h, rp);
+        float2 z[3];
+        apply_inv(m, op, rh[idx], rh[cs + idx], rh[2 * cs + idx], z[0], z[1], z[2]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 z = zh[c * cs + idx];
-            if (first) {
-                p[c] = z;
-            } else {
+            float2 p = z[c];
+            if (!first) {
                 const float2 o = ph[c * cs + idx];
-                p[c] = make_float2(fmaf(beta, o.x, z.x), fmaf(beta, o.y, z.y));
+                p = make_float2(fmaf(beta, o.x, z[c].x), fmaf(beta, o.y, z[c].y));
             }
-            ph[c * cs + idx] = p[c];
-            cp[c * cs + idx] = p[c];
+            ph[c * cs + idx] = p;
+            cp[c * cs + idx] = p;
         }
-        const Mode m = mode_of(g, idx, n3h, rp);
-        float2 y0, y1, y2;
-        apply_S(m, p[0], p[1], p[2], y0, y1, y2);
-        zh[idx] = y0;
-        zh[cs + idx] = y1;
-        zh[2 * cs + idx] = y2;
     }
 }
 
@@ -230,8 +224,8 @@ __device__ __forceinline__ float cdot3(float2 a0, float2 a1, float2 a2, float2 b
     return a0.x * b0.x + a0.y * b0.y + a1.x * b1.x + a1.y * b1.y + a2.x * b2.x + a2.y * b2.y;
 }
 
-// Start: r~ = -scale g^ (spec holds F[g]), x~ = 0, z~ = M r~ (into spec);
-// partials of |r~|^2 and <r~, z~>.
+// Start: r~ = -scale g^ (spec holds F[g]), x~ = 0; partials of |r~|^2 and
+// <r~, z~> with z~ = M r~ (recomputed by the direction kernel).
 __global__ void __launch_bounds__(kThreads) k_fs_start(Grid g, float2* __restrict__ spec,
                                                         float2* __restrict__ rh, float2* __restrict__ xh,
                                                         size_t cs, int op, RegParams rp, float scale,
@@ -249,15 +243,14 @@ __global__ void __launch_bounds__(kThreads) k_fs_start(Grid g, float2* __restric
         apply_inv(m, op, r0, r1, r2, z0, z1, z2);
         rh[idx] = r0; rh[cs + idx] = r1; rh[2 * cs + idx] = r2;
         xh[idx] = make_float2(0.f, 0.f); xh[cs + idx] = make_float2(0.f, 0.f); xh[2 * cs + idx] = make_float2(0.f, 0.f);
-        spec[idx] = z0; spec[cs + idx] = z1; spec[2 * cs + idx] = z2;
         arr += static_cast<double>(m.wt * cdot3(r0, r1, r2, r0, r1, r2));
         arz += static_cast<double>(m.wt * cdot3(r0, r1, r2, z0, z1, z2));
     }
     block_sum2(arr, arz, prr, prz);
 }
 
-// H p~ = S p~ (in spec) + scale F[body] (in spec2), or K of that for the
-// paper's gradient form; written into spec; partials of <p~, H p~>.
+// H p~ = S p~ + scale F[body] (in spec2), or K of that for the paper's
+// gradient form; written into spec; partials of <p~, H p~>.
 __global__ void __launch_bounds__(kThreads) k_fs_hp(Grid g, float2* __restrict__ spec,
                                                      const float2* __restrict__ spec2,
                                                      const float2* __restrict__ ph, size_t cs, int kform,
@@ -268,13 +261,15 @@ __global__ void __launch_bounds__(kThreads) k_fs_hp(Grid g, float2* __restrict__
     double acc = 0.0;
     for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
          idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        const Mode m = mode_of(g, idx, n3h, rp);
+        const float2 p0 = ph[idx], p1 = ph[cs + idx], p2 = ph[2 * cs + idx];
         float2 h[3];
+        apply_S(m, p0, p1, p2, h[0], h[1], h[2]);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            const float2 sp = spec[c * cs + idx], b = spec2[c * cs + idx];
-            h[c] = make_float2(fmaf(scale, b.x, sp.x), fmaf(scale, b.y, sp.y));
+            const float2 b = spec2[c * cs + idx];
+            h[c] = make_float2(fmaf(scale, b.x, h[c].x), fmaf(scale, b.y, h[c].y));
         }
-        const Mode m = mode_of(g, idx, n3h, rp);
         if (kform && m.kk != 0.0f) {
             const float2 ud = make_float2(m.u1 * h[0].x + m.u2 * h[1].x + m.u3 * h[2].x,
                                           m.u1 * h[0].y + m.u2 * h[1].y + m.u3 * h[2].y);
@@ -285,14 +280,14 @@ __global__ void __launch_bounds__(kThreads) k_fs_hp(Grid g, float2* __restrict__
         }
 #pragma unroll
         for (int c = 0; c < 3; ++c) spec[c * cs + idx] = h[c];
-        acc += static_cast<double>(m.wt * cdot3(ph[idx], ph[cs + idx], ph[2 * cs + idx], h[0], h[1], h[2]));
+        acc += static_cast<double>(m.wt * cdot3(p0, p1, p2, h[0], h[1], h[2]));
     }
     block_sum(acc, ppq);
 }
 
-// x~ += alpha p~, r~ -= alpha H p~ (H p~ in spec), then z~ = M r~ into spec;
-// partials of |r~|^2 and <r~, z~>.
-__global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, float2* __restrict__ spec,
+// x~ += alpha p~, r~ -= alpha H p~ (H p~ in spec); partials of |r~|^2 and
+// <r~, z~> with z~ = M r~ (recomputed by the next direction kernel).
+__global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, const float2* __restrict__ spec,
                                                          const float2* __restrict__ ph,
                                                          float2* __restrict__ xh, float2* __restrict__ rh,
                                                          size_t cs, float alpha, int op, RegParams rp,
@@ -317,7 +312,6 @@ __global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, float2* __restri
         const Mode m = mode_of(g, idx, n3h, rp);
         float2 z0, z1, z2;
         apply_inv(m, op, r[0], r[1], r[2], z0, z1, z2);
-        spec[idx] = z0; spec[cs + idx] = z1; spec[2 * cs + idx] = z2;
         arr += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], r[0], r[1], r[2]));
         arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z0, z1, z2));
     }
@@ -551,13 +545,14 @@ void launch_spectral_precond(const Grid& g, cufftComplex* xh, size_t cstride, Sp
                                                     static_cast<int>(op), rp, scale, partials);
 }
 
-void launch_spectral_direction(const Grid& g, cufftComplex* zh, cufftComplex* ph, cufftComplex* cp,
-                               size_t cstride, float beta, int first, RegParams rp, cudaStream_t st)
+void launch_spectral_direction(const Grid& g, const cufftComplex* rh, cufftComplex* ph, cufftComplex* cp,
+                               size_t cstride, float beta, int first, SpectralOp op, RegParams rp,
+                               cudaStream_t st)
 {
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
     k_spectral_direction<<<stream_blocks(M), kThreads, 0, st>>>(
-        g, reinterpret_cast<float2*>(zh), reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
-        cstride, beta, first, rp);
+        g, reinterpret_cast<const float2*>(rh), reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
+        cstride, beta, first, static_cast<int>(op), rp);
 }
 
 void launch_fs_start(const Grid& g, cufftComplex* spec, cufftComplex* rh, cufftComplex* xh, size_t cs,
@@ -581,7 +576,7 @@ void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph,
                       cufftComplex* rh, size_t cs, float alpha, SpectralOp op, RegParams rp, double* prr,
                       double* prz, int nblocks, cudaStream_t st)
 {
-    k_fs_update<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<float2*>(spec),
+    k_fs_update<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<const float2*>(spec),
                                               reinterpret_cast<const float2*>(ph),
                                               reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(rh),
                                               cs, alpha, static_cast<int>(op), rp, prr, prz);

@@ -21,29 +21,80 @@ inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
 // ---------------------------------------------------------------------------
 
 // Heun characteristic: sign = +1 gives X = x - dt/2 [v(x) + v(x - dt v(x))],
-// sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))].  d in grid units.
+// sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))]; d in grid units.
+// The three velocity gathers at the predictor point are served from a
+// shared-memory box per 4 x 8 x 32 tile (one box, staged once per component;
+// the predictor points of a tile share its bounds).
 template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_backtrace(Grid g, const float* __restrict__ v,
-                                                         const float* __restrict__ vc, float dt, float sign,
-                                                         float* __restrict__ d)
+__global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
+    k_backtrace_tiled(Grid g, const float* __restrict__ v, const float* __restrict__ vc, float dt, float sign,
+                      float* __restrict__ d)
 {
-    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
-    if (p >= g.N) return;
-    int i, j, k;
-    coords_of(g, p, i, j, k);
+    extern __shared__ float box[];
+    __shared__ int red[6][TILE2];
+    __shared__ int par[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * TILE3 + lane;
+    const int j = blockIdx.y * TILE2 + warp;
+    const int i0 = blockIdx.z * TILE1;
     const size_t N = g.N;
-    const float u1 = __ldg(v + p) * g.ih1;
-    const float u2 = __ldg(v + N + p) * g.ih2;
-    const float u3 = __ldg(v + 2 * N + p) * g.ih3;
+    const bool col_ok = (k < g.n3) && (j < g.n2);
+    const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
     const float sdt = sign * dt;
-    Stencil<ORDER> s;
-    s.build(g, i, j, k, -sdt * u1, -sdt * u2, -sdt * u3);
-    float vs[3];
-    s.eval3(vc, g.N, vs);  // v itself, or its B-spline coefficients
-    const float c = -0.5f * sdt;
-    d[p] = c * (u1 + vs[0] * g.ih1);
-    d[N + p] = c * (u2 + vs[1] * g.ih2);
-    d[2 * N + p] = c * (u3 + vs[2] * g.ih3);
+    float u1[TILE1], u2[TILE1], u3[TILE1];
+    int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+#pragma unroll
+    for (int q = 0; q < TILE1; ++q) {
+        u1[q] = u2[q] = u3[q] = 0.0f;
+        if (col_ok && i0 + q < g.n1) {
+            const uint32_t p = p0 + q * g.n23;
+            u1[q] = __ldg(v + p) * g.ih1;
+            u2[q] = __ldg(v + N + p) * g.ih2;
+            u3[q] = __ldg(v + 2 * N + p) * g.ih3;
+            float t;
+            const int b1 = i0 + q + split_disp(-sdt * u1[q], t);
+            const int b2 = j + split_disp(-sdt * u2[q], t);
+            const int b3 = k + split_disp(-sdt * u3[q], t);
+            lo1 = min(lo1, b1); hi1 = max(hi1, b1);
+            lo2 = min(lo2, b2); hi2 = max(hi2, b2);
+            lo3 = min(lo3, b3); hi3 = max(hi3, b3);
+        }
+    }
+    const BoxPar bp = tile_box<ORDER, 4>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
+    const bool use_box = bp.E1 != 0;
+    const float cc = -0.5f * sdt;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        const float* f = vc + c * N;
+        const float ih = c == 0 ? g.ih1 : (c == 1 ? g.ih2 : g.ih3);
+        if (use_box) {
+            tile_load_box<float>(g, f, box, bp, lane, warp);
+            cp_async_wait_all();
+            __syncthreads();
+        }
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q) {
+            const int i = i0 + q;
+            if (!(col_ok && i < g.n1)) continue;
+            const float vsq = use_box
+                                  ? tile_eval<ORDER>(box, bp, i, j, k, -sdt * u1[q], -sdt * u2[q], -sdt * u3[q])
+                                  : gather_global<ORDER, float>(g, f, i, j, k, -sdt * u1[q], -sdt * u2[q],
+                                                                -sdt * u3[q]);
+            const float uc = c == 0 ? u1[q] : (c == 1 ? u2[q] : u3[q]);
+            d[c * N + p0 + q * g.n23] = cc * (uc + vsq * ih);
+        }
+        if (use_box) __syncthreads();  // every read of this component is done before the next staging
+    }
+}
+
+template <int ORDER>
+void launch_backtrace_tiled(const Grid& g, const float* v, const float* vc, float dt, float sign, float* d,
+                            cudaStream_t st)
+{
+    if (kTiledSmemBytes > 48 * 1024)
+        cudaFuncSetAttribute(k_backtrace_tiled<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kTiledSmemBytes));
+    k_backtrace_tiled<ORDER><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, v, vc, dt, sign, d);
 }
 
 // Sources of the incremental state for every time level at once:
@@ -327,7 +378,14 @@ void launch_interp(const Grid& g, int order, const void* f, const float* d, void
 void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
                       cudaStream_t st)
 {
-    CLAIRE_DISPATCH(order, k_backtrace, g, v, vc ? vc : v, dt, static_cast<float>(sign), d);
+    const float* f = vc ? vc : v;
+    const float sg = static_cast<float>(sign);
+    if (order == 3)
+        launch_backtrace_tiled<3>(g, v, f, dt, sg, d, st);
+    else if (order == 4)
+        launch_backtrace_tiled<4>(g, v, f, dt, sg, d, st);
+    else
+        launch_backtrace_tiled<1>(g, v, f, dt, sg, d, st);
 }
 
 void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,

@@ -22,7 +22,8 @@ What it computes, step by step, in the paper's order and notation:
 * Gauss-Newton Hessian matvec, Eq. (6), with the incremental state and
   incremental adjoint solves.
 * Gauss-Newton-Krylov with Armijo line search, Eq. (5), matrix-free PCG,
-  spectral preconditioner S^{-1}.
+  spectral preconditioner S^{-1}, or the zero-velocity Hessian approximation
+  applied through a two-level coarse grid (Sec. 2.2 "Optimization").
 * Jacobian determinant det grad y of the deformation map (Sec. 4.1).
 
 Readings where the paper is silent are listed in the module docstrings below
@@ -45,7 +46,8 @@ __all__ = [
     "characteristics", "forward_solve", "adjoint_solve", "state_at", "objective",
     "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
     "transport", "transport_vjp", "interp_grad", "deformation_map", "detj", "cfl", "inner",
-    "num_threads", "param_search", "param_continuation",
+    "num_threads", "param_search", "param_continuation", "hessian0_matvec", "mean_state_gradient",
+    "restrict_spectral", "prolong_spectral", "precond_two_level",
 ]
 
 _lib = None
@@ -215,6 +217,10 @@ class Params:
     armijo_c1: float = 1e-4
     max_ls: int = 10
     adjoint: str = "sl"     # "sl" = paper's SL adjoint (OTD); "scatter" = exact transpose (DTO)
+    precond: str = "spectral"  # "spectral" = S^{-1}; "2l" = two-level zero-velocity (Sec. 2.2)
+    pc_coarse: int = 2      # fine-to-coarse grid ratio of the two-level preconditioner
+    pc_tol: float = 1e-1    # relative residual of its inner PCG (0: run pc_maxit iterations)
+    pc_maxit: int = 50
     extra: dict = field(default_factory=dict)
 
     @property
@@ -440,16 +446,158 @@ def precond(r, p: Params):
     return reg_inverse(r, p)
 
 
-def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False):
+# ----------------------------------------------------------------------------
+# Zero-velocity Hessian and the two-level preconditioner (Sec. 2.2)
+# ----------------------------------------------------------------------------
+#
+# The paper preconditions H with a zero-velocity approximation of it, applied
+# through a two-level coarse grid, and leaves the construction to a cited
+# reference.  Readings taken here:
+#
+# * Zero velocity: with v = 0 in the incremental equations the characteristics
+#   are the identity, so mt(1) = -int vt . grad m dt, lt = -mt(1) is constant
+#   in time and the body is (int grad m dt)(int grad m dt . vt).  With the
+#   trapezoid rule of the solves, H0 vt = S vt + gbar (gbar . vt), gbar =
+#   sum_j w_j grad m^j (FD8 gradients of the current states), or K of that for
+#   the paper's gradient form.  At v = 0 this is exactly the full Gauss-Newton
+#   matvec.
+# * Two levels: Fourier truncation R to the modes |k_i| < nc_i / 2 (the
+#   coarse Nyquist planes are dropped, so E R is an orthogonal projection
+#   onto low modes, E the zero-padding prolongation), gbar restricted the same
+#   way, H0 on the coarse grid inverted by an inner PCG (preconditioner
+#   S^{-1}, x0 = 0, relative residual pc_tol or pc_maxit iterations), and
+#   S^{-1} on the remaining high modes:
+#   P^{-1} r = E H0c^{-1} R r + S^{-1} (r - E R r).
+# * The mean (k = 0) is treated as by S^{-1}, with the identity.  The inner
+#   PCG works on the coarse modes that R keeps (mean-free, no Nyquist planes),
+#   with the operator Q H0c Q, Q the projection onto them; there H0 (S
+#   positive, gbar gbar^T semidefinite) is positive definite, and H0c^{-1}
+#   means the inverse of Q H0c Q.
+# * The outer PCG takes the flexible (Polak-Ribiere) direction update when
+#   this inexact preconditioner is in use.
+
+def mean_state_gradient(st: State):
+    """gbar = sum_j w_j grad m^j (trapezoid weights of the solves)."""
+    w = _weights(st.p.nt)
+    return sum(w[j] * st.gms[j] for j in range(st.p.nt + 1))
+
+
+def hessian0_matvec(vt, gbar, p: Params):
+    """Zero-velocity Gauss-Newton matvec H0 vt = S vt + gbar (gbar . vt) (or K of it)."""
+    vt = _f64(vt); gbar = _f64(gbar)
+    return _apply_form(reg_apply(vt, p) + gbar * np.sum(gbar * vt, axis=0), p)
+
+
+def _low_index(n, nc):
+    """Indices of the modes |k| < nc/2 along an FFT axis of length n (and nc)."""
+    h = nc // 2
+    return np.r_[0:h, n - h + 1:n], np.r_[0:h, nc - h + 1:nc]
+
+
+def _truncate(Fh, nout, nin):
+    """Copy the modes |k_i| < min(nout_i, nin_i)/2 between half spectra of the grids nin -> nout."""
+    lo = [min(a, b) for a, b in zip(nout, nin)]
+    a_in0 = _low_index(nin[0], lo[0])[0]; a_out0 = _low_index(nout[0], lo[0])[0]
+    a_in1 = _low_index(nin[1], lo[1])[0]; a_out1 = _low_index(nout[1], lo[1])[0]
+    h2 = lo[2] // 2
+    out = np.zeros(Fh.shape[:-3] + (nout[0], nout[1], nout[2] // 2 + 1), dtype=complex)
+    out[..., a_out0[:, None, None], a_out1[None, :, None], np.arange(h2)[None, None, :]] = \
+        Fh[..., a_in0[:, None, None], a_in1[None, :, None], np.arange(h2)[None, None, :]]
+    return out
+
+
+def restrict_spectral(f, nc):
+    """R f: the band-limited part of f (modes |k_i| < nc_i/2) sampled on the grid nc."""
+    f = _f64(f); n = f.shape[-3:]
+    nc = tuple(int(x) for x in nc)
+    Fh = np.fft.rfftn(f, axes=(-3, -2, -1)) / np.prod(n)
+    return np.fft.irfftn(_truncate(Fh, nc, n) * np.prod(nc), s=nc, axes=(-3, -2, -1))
+
+
+def prolong_spectral(fc, n):
+    """E fc: trigonometric (zero-padding) interpolation of the coarse field fc to the grid n,
+    with the coarse Nyquist modes dropped."""
+    fc = _f64(fc); nc = fc.shape[-3:]
+    n = tuple(int(x) for x in n)
+    Ch = np.fft.rfftn(fc, axes=(-3, -2, -1)) / np.prod(nc)
+    return np.fft.irfftn(_truncate(Ch, n, nc) * np.prod(n), s=n, axes=(-3, -2, -1))
+
+
+def _mean_free(f):
+    """f without its k = 0 Fourier mode (the mean of each component)."""
+    return f - f.mean(axis=(-3, -2, -1), keepdims=True)
+
+
+def _kept_modes(f):
+    """Q f: f without its mean and without its Nyquist planes (the coarse modes R keeps)."""
+    n = f.shape[-3:]
+    return _mean_free(restrict_spectral(f, n))
+
+
+def _pcg_h0(rhs, gbar, p: Params, tol, maxit):
+    """Inner PCG for Q H0 Q x = Q rhs (preconditioner S^{-1}, x0 = 0);
+    returns (x, iterations)."""
+    n = rhs.shape[1:]
+    x = np.zeros_like(rhs)
+    r = _kept_modes(_f64(rhs))
+    r0 = math.sqrt(inner(r, r, n))
+    if r0 == 0.0:
+        return x, 0
+    z = precond(r, p)
+    pv = z.copy()
+    rz = inner(r, z, n)
+    it = 0
+    for it in range(1, maxit + 1):
+        q = _kept_modes(hessian0_matvec(pv, gbar, p))
+        pq = inner(pv, q, n)
+        if pq <= 0.0:
+            break
+        alpha = rz / pq
+        x = x + alpha * pv
+        r = r - alpha * q
+        if tol > 0.0 and math.sqrt(inner(r, r, n)) <= tol * r0:
+            break
+        z = precond(r, p)
+        rz_new = inner(r, z, n)
+        pv = z + (rz_new / rz) * pv
+        rz = rz_new
+    return x, it
+
+
+def precond_two_level(r, gbar_c, p: Params, stats=None):
+    """P^{-1} r = E H0c^{-1} R r + S^{-1} (r - E R r) (zero-velocity Hessian on
+    the coarse grid of gbar_c, spectral inverse on the high modes)."""
+    r = _f64(r); n = r.shape[1:]
+    nc = gbar_c.shape[1:]
+    rc = restrict_spectral(r, nc)
+    xc, its = _pcg_h0(rc, gbar_c, p, p.pc_tol, p.pc_maxit)
+    if stats is not None:
+        stats.append(its)
+    low = prolong_spectral(rc, n)          # E R r, mean included
+    mean = r - _mean_free(r)               # identity on k = 0
+    return prolong_spectral(xc, n) + precond(r - low, p) + mean
+
+
+def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False, stats=None):
     """Matrix-free PCG for H x = rhs (Sec. 2.2), x0 = 0; stops when
-    ||r|| <= rtol ||r0|| or after maxit matvecs.  Returns (x, iterations)."""
+    ||r|| <= rtol ||r0|| or after maxit matvecs.  Returns (x, iterations).
+    With the two-level preconditioner the direction update is the flexible
+    (Polak-Ribiere) one, since that preconditioner is an inexact inner solve."""
     n = st.n
+    p = st.p
+    two_level = p.precond == "2l"
+    if two_level:
+        nc = tuple(s // p.pc_coarse for s in n)
+        gbar_c = restrict_spectral(mean_state_gradient(st), nc)
+        apply_p = lambda res: precond_two_level(res, gbar_c, p, stats)
+    else:
+        apply_p = lambda res: precond(res, p)
     x = np.zeros_like(rhs)
     r = _f64(rhs).copy()
     r0 = math.sqrt(inner(r, r, n))
     if r0 == 0.0:
         return x, 0
-    z = precond(r, st.p)
+    z = apply_p(r)
     pv = z.copy()
     rz = inner(r, z, n)
     it = 0
@@ -465,9 +613,11 @@ def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False):
         r = r - alpha * q
         if not fixed_iters and math.sqrt(inner(r, r, n)) <= rtol * r0:
             break
-        z = precond(r, st.p)
-        rz_new = inner(r, z, n)
-        pv = z + (rz_new / rz) * pv
+        z_new = apply_p(r)
+        rz_new = inner(r, z_new, n)
+        beta = ((rz_new - inner(r, z, n)) if two_level else rz_new) / rz
+        pv = z_new + beta * pv
+        z = z_new
         rz = rz_new
     return x, it
 
@@ -486,7 +636,8 @@ def register(m0, m1, p: Params, v0=None, mode=None, log=None):
     g = gradient(st, mode)
     g0 = math.sqrt(inner(g, g, n))
     rep = {"gn_iters": 0, "pcg_iters": [], "alpha": [], "J": [st.J], "gnorm_rel": [1.0],
-           "status": "not_converged", "g0": g0}
+           "status": "not_converged", "g0": g0, "pc_inner_iters": 0}
+    inner_its = []
     if g0 == 0.0:
         rep["status"] = "converged"
         return v, rep
@@ -496,7 +647,8 @@ def register(m0, m1, p: Params, v0=None, mode=None, log=None):
             rep["status"] = "converged"
             break
         eta = min(p.pcg_rtol_max, math.sqrt(rel))
-        vt, its = pcg(st, -g, eta, p.max_pcg, mode, fixed_iters=p.pcg_fixed)
+        vt, its = pcg(st, -g, eta, p.max_pcg, mode, fixed_iters=p.pcg_fixed, stats=inner_its)
+        rep["pc_inner_iters"] = sum(inner_its)
         gtv = inner(g, vt, n)
         alpha, ok = 1.0, False
         for _ls in range(p.max_ls):

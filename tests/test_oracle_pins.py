@@ -734,3 +734,95 @@ def test_bspline_fourth_order_convergence_and_transpose():
     yv = rng.standard_normal(n)
     lhs = np.sum(oracle.interp(x, d, 4) * yv)
     assert abs(lhs - np.sum(x * oracle.interp_T(yv, d, 4))) < 1e-11 * max(1.0, abs(lhs))
+
+
+# ---------------------------------------------------------------------------
+# Zero-velocity Hessian and the two-level preconditioner (Sec. 2.2)
+# ---------------------------------------------------------------------------
+
+@pytest.mark.parametrize("grad_form", [0, 1])
+def test_zero_velocity_hessian_is_the_full_matvec_at_zero_velocity(grad_form):
+    """At v = 0 the characteristics are the identity, so the full Gauss-Newton
+    matvec (incremental state and adjoint solves, trapezoid body) must equal
+    S vt + gbar (gbar . vt).  Catches a wrong sign, a missing time weight or a
+    missing K in the zero-velocity operator."""
+    g = (12, 10, 16)
+    m0 = synth.blob_template(g, seed=3)
+    m1 = synth.blob_template(g, seed=4)
+    p = oracle.Params(grad_form=grad_form)
+    st = oracle.state_at(np.zeros((3,) + g), m0, m1, p)
+    vt = np.random.default_rng(0).standard_normal((3,) + g)
+    h = oracle.hessian_matvec(st, vt)
+    h0 = oracle.hessian0_matvec(vt, oracle.mean_state_gradient(st), p)
+    assert _rel(h0, h) < 1e-12
+
+
+def test_spectral_restriction_and_prolongation():
+    """A band-limited field restricts to its samples at the coarse nodes and
+    prolongs back exactly; E R is an orthogonal projection (idempotent,
+    self-adjoint); the coarse Nyquist modes are dropped."""
+    n, nc = (16, 12, 20), (8, 6, 10)
+    f = synth.bandlimited_velocity(n, seed=1, kmax=2, vmax=1.0).astype(np.float64)
+    fc = oracle.restrict_spectral(f, nc)
+    assert np.abs(fc - f[:, ::2, ::2, ::2]).max() < 1e-12
+    assert np.abs(oracle.prolong_spectral(fc, n) - f).max() < 1e-12
+    r = np.random.default_rng(2)
+    a, b = r.standard_normal((3,) + n), r.standard_normal((3,) + n)
+    Pa = oracle.prolong_spectral(oracle.restrict_spectral(a, nc), n)
+    Pb = oracle.prolong_spectral(oracle.restrict_spectral(b, nc), n)
+    assert np.abs(oracle.prolong_spectral(oracle.restrict_spectral(Pa, nc), n) - Pa).max() < 1e-12
+    assert abs(oracle.inner(Pa, b, n) - oracle.inner(a, Pb, n)) < 1e-10 * abs(oracle.inner(a, b, n)) + 1e-12
+    # the coarse Nyquist plane x1 (k1 = 4 on the 8-node axis) is dropped
+    x1, _, _ = _xyz(n)
+    nyq = np.cos(4.0 * x1)[None]
+    assert np.abs(oracle.restrict_spectral(nyq, nc)).max() < 1e-12
+
+
+def test_two_level_preconditioner_special_cases():
+    """gbar = 0 gives exactly S^{-1}; a coarse grid equal to the fine one with a
+    tight inner tolerance inverts the mean-free part of H0 and passes the mean
+    through; the near-exact preconditioner is self-adjoint and positive.
+    Catches a wrong split of low and high modes or a mis-scaled restriction."""
+    n = (12, 12, 16)
+    r = np.random.default_rng(5)
+    res = r.standard_normal((3,) + n)
+    other = r.standard_normal((3,) + n)
+    p = oracle.Params(pc_tol=1e-13, pc_maxit=400)
+    zero = np.zeros((3, 6, 6, 8))
+    assert _rel(oracle.precond_two_level(res, zero, p), oracle.precond(res, p)) < 1e-12
+    m = synth.blob_template(n, seed=7)
+    gbar = oracle.fd8_grad(m)
+    # coarse grid = fine grid: H0 is inverted on the mean-free, non-Nyquist
+    # modes (the projection Q below); the mean passes through unchanged
+    mean_free = lambda f: f - f.mean(axis=(-3, -2, -1), keepdims=True)
+    Q = lambda f: mean_free(oracle.prolong_spectral(oracle.restrict_spectral(f, n), n))
+    rl = Q(res)
+    z = oracle.precond_two_level(rl, gbar, p)
+    assert _rel(Q(oracle.hessian0_matvec(z, gbar, p)), rl) < 1e-9
+    zm = oracle.precond_two_level(res, gbar, p)
+    assert np.abs((zm - mean_free(zm)) - (res - mean_free(res))).max() < 1e-12
+    gc = oracle.restrict_spectral(gbar, (6, 6, 8))
+    za = oracle.precond_two_level(res, gc, p)
+    zb = oracle.precond_two_level(other, gc, p)
+    assert abs(oracle.inner(za, other, n) - oracle.inner(res, zb, n)) < 1e-8 * abs(oracle.inner(za, other, n))
+    assert oracle.inner(za, res, n) > 0.0
+
+
+def test_two_level_registration_takes_fewer_iterations():
+    """The paper's zero-velocity two-level preconditioner reaches the same
+    gradient tolerance with fewer Gauss-Newton and PCG iterations than the
+    spectral one on a nested-label pair, ending at the same objective within 1 %."""
+    g = (24, 24, 24)
+    m0 = synth.label_template(g, seed=0)
+    vs = synth.bandlimited_velocity(g, seed=0, kmax=3, vmax=1.0)
+    res = {}
+    for pc in ("spectral", "2l"):
+        p = oracle.Params(beta_v=1e-2, gtol=5e-2, max_gn=20, max_pcg=50, precond=pc)
+        m1 = oracle.transport(m0, vs, p)
+        _, rep = oracle.register(m0, m1, p)
+        assert rep["status"] == "converged"
+        res[pc] = rep
+    assert sum(res["2l"]["pcg_iters"]) < sum(res["spectral"]["pcg_iters"])
+    assert res["2l"]["gn_iters"] <= res["spectral"]["gn_iters"]
+    assert res["2l"]["pc_inner_iters"] > 0
+    assert abs(res["2l"]["J"][-1] - res["spectral"]["J"][-1]) < 0.01 * res["spectral"]["J"][-1]

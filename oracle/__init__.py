@@ -613,6 +613,8 @@ def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False, stats=None):
         r = r - alpha * q
         if not fixed_iters and math.sqrt(inner(r, r, n)) <= rtol * r0:
             break
+        if it == maxit:
+            break
         z_new = apply_p(r)
         rz_new = inner(r, z_new, n)
         beta = ((rz_new - inner(r, z, n)) if two_level else rz_new) / rz

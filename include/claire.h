@@ -109,7 +109,23 @@ typedef struct claire_opts {
                             sources and the gradient body compute them by FD8 where they are used
                             (3 (nt+1) N fewer stored values, about 1.3x the time of those kernels);
                             0 = store them once per linearisation (default).  Fixed at create. */
+    int precond;         /* PCG preconditioner: CLAIRE_PRECOND_SPECTRAL (default, S^{-1}) or
+                            CLAIRE_PRECOND_TWO_LEVEL, the paper's zero-velocity Hessian approximation
+                            H0 vt = S vt + gbar (gbar . vt), gbar = sum_j w_j grad m^j at the
+                            linearisation point (Sec. 2.2), inverted on a coarse grid by an inner
+                            PCG, with S^{-1} on the remaining (high) modes and the identity on k = 0;
+                            the outer PCG then takes the flexible (Polak-Ribiere) direction update.
+                            Its coarse-grid buffers (about 3 fine spectra) are allocated on first use. */
+    int pc_coarse;       /* fine-to-coarse ratio of the two-level grid: every N_i / pc_coarse must be
+                            even and >= 4; default 2 */
+    double pc_tol;       /* relative residual of the inner PCG; 0 = always run pc_maxit iterations;
+                            default 1e-1 */
+    int pc_maxit;        /* inner PCG iteration cap; default 50 */
 } claire_opts;
+
+/* claire_opts.precond */
+#define CLAIRE_PRECOND_SPECTRAL 0
+#define CLAIRE_PRECOND_TWO_LEVEL 1
 
 /* claire_opts.storage */
 #define CLAIRE_STORAGE_F32 0
@@ -144,6 +160,7 @@ typedef struct claire_report {
     double gather_launches;     /* SL gather kernel launches (CLAIRE_PHASE_GATHER count) */
     double interp_points;       /* grid points x scalar fields interpolated by the gathers */
     double interp_bytes;        /* algorithmic HBM bytes of the gather kernels (each value once) */
+    int pc_inner_iters_total;   /* inner PCG iterations of the two-level preconditioner (0 otherwise) */
 } claire_report;
 
 /* Fill *opts with the defaults listed above.  Returns CLAIRE_EINVAL on NULL. */
@@ -199,8 +216,14 @@ claire_status claire_gradient(claire_ctx* ctx, const float* v, float* g, double*
  */
 claire_status claire_hessian_matvec(claire_ctx* ctx, const float* vt, float* Hvt);
 
-/* Preconditioner of the PCG solve: the spectral inverse of the regulariser
- * (S^{-1}, or (beta_v A)^{-1} for grad_form 1), identity on k = 0.  3N floats. */
+/* Preconditioner of the PCG solve, z = P^{-1} r (3N floats each):
+ * CLAIRE_PRECOND_SPECTRAL: the spectral inverse of the regulariser (S^{-1}, or
+ * (beta_v A)^{-1} for grad_form 1), identity on k = 0;
+ * CLAIRE_PRECOND_TWO_LEVEL: the two-level zero-velocity preconditioner at the
+ * last claire_gradient's v (CLAIRE_ESTATE without one), E H0c^{-1} R r on the
+ * coarse modes |k_i| < N_i / (2 pc_coarse) other than k = 0, S^{-1} r on the
+ * others, r on k = 0; H0c^{-1} is pc_maxit (or fewer, pc_tol) inner PCG
+ * iterations. */
 claire_status claire_precond(claire_ctx* ctx, const float* r, float* z);
 
 /*

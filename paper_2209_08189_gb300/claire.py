@@ -27,6 +27,7 @@ INTERP_CUBIC, INTERP_LINEAR, INTERP_BSPLINE = 3, 1, 4
 TRANSPORT_FWD, TRANSPORT_ADJ = 0, 1
 SPECTRAL_REG, SPECTRAL_INV, SPECTRAL_K = 0, 1, 2
 STORAGE_F32, STORAGE_F16, STORAGE_BF16 = 0, 1, 2
+PRECOND_SPECTRAL, PRECOND_TWO_LEVEL = 0, 1
 PHASES = ["backtrace", "state", "adjoint", "incremental", "spectral", "vector", "objective",
           "gather"]
 MAX_LOGGED_STEPS = 64
@@ -45,7 +46,8 @@ class claire_opts(ctypes.Structure):
                 ("pcg_fixed", ctypes.c_int), ("armijo_c1", ctypes.c_double),
                 ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
                 ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double),
-                ("lowmem", ctypes.c_int)]
+                ("lowmem", ctypes.c_int), ("precond", ctypes.c_int), ("pc_coarse", ctypes.c_int),
+                ("pc_tol", ctypes.c_double), ("pc_maxit", ctypes.c_int)]
 
 
 class claire_report(ctypes.Structure):
@@ -58,7 +60,7 @@ class claire_report(ctypes.Structure):
                 ("detj_max", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("t_total_s", ctypes.c_double), ("t_phase_s", ctypes.c_double * 8),
                 ("gather_launches", ctypes.c_double), ("interp_points", ctypes.c_double),
-                ("interp_bytes", ctypes.c_double)]
+                ("interp_bytes", ctypes.c_double), ("pc_inner_iters_total", ctypes.c_int)]
 
     def as_dict(self):
         n = min(self.gn_iters, MAX_LOGGED_STEPS)
@@ -72,7 +74,7 @@ class claire_report(ctypes.Structure):
                 "t_total_s": self.t_total_s,
                 "t_phase_s": {k: self.t_phase_s[i] for i, k in enumerate(PHASES)},
                 "gather_launches": self.gather_launches, "interp_points": self.interp_points,
-                "interp_bytes": self.interp_bytes}
+                "interp_bytes": self.interp_bytes, "pc_inner_iters_total": self.pc_inner_iters_total}
 
 
 class claire_kernel_stat(ctypes.Structure):

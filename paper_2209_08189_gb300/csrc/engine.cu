@@ -59,6 +59,34 @@ struct EventPair {
 
 }  // namespace
 
+// Coarse-grid state of the two-level zero-velocity preconditioner (allocated
+// on first use): cuFFT plans of the coarse grid, the restricted mean state
+// gradient gbar, the inner PCG vectors in Fourier space and, for the flexible
+// outer PCG, two fine preconditioned residuals.
+struct TwoLevel {
+    Grid g{};
+    int factor = 0;
+    size_t N = 0, M = 0;
+    cufftHandle r2c = 0, c2r = 0;
+    bool plans = false;
+    void* work = nullptr;
+    void* block = nullptr;
+    float* gbar = nullptr;  // 3 Nc
+    float* real = nullptr;  // 3 Nc scratch
+    cufftComplex *xh = nullptr, *rh = nullptr, *zh = nullptr, *ph = nullptr, *cp = nullptr, *q = nullptr,
+                 *T = nullptr;  // 3 Mc each
+    cufftComplex* zf[2] = {nullptr, nullptr};  // 3 M each (fine)
+    ~TwoLevel()
+    {
+        if (plans) {
+            cufftDestroy(r2c);
+            cufftDestroy(c2r);
+        }
+        if (work) cudaFree(work);
+        if (block) cudaFree(block);
+    }
+};
+
 struct claire_ctx {
     Grid grid{};
     int n[3]{};
@@ -110,6 +138,8 @@ struct claire_ctx {
     unsigned long long* vjp_acc = nullptr;  // N fixed-point accumulators
     bool have_images = false, have_lin = false;
     double J_lin = 0, mis_lin = 0, reg_lin = 0;
+    TwoLevel* tl2 = nullptr;         // two-level preconditioner state (precond = 1)
+    long long pc_inner_total = 0;    // its inner PCG iterations so far
 
     // statistics and timing
     KernelStat ks[KK_COUNT];
@@ -153,6 +183,8 @@ struct claire_ctx {
         vjp_acc = nullptr;
         if (hres) cudaFreeHost(hres);
         hres = nullptr;
+        delete tl2;
+        tl2 = nullptr;
     }
 };
 
@@ -228,6 +260,10 @@ void fill_defaults(claire_opts* o)
     o->storage = CLAIRE_STORAGE_F32;
     o->g0_ref = 0.0;
     o->lowmem = 0;
+    o->precond = CLAIRE_PRECOND_SPECTRAL;
+    o->pc_coarse = 2;
+    o->pc_tol = 1e-1;
+    o->pc_maxit = 50;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -237,7 +273,39 @@ bool valid_opts(const claire_opts& o)
            (o.grad_form == 0 || o.grad_form == 1) && o.gtol >= 0 && o.max_gn >= 0 &&
            o.max_pcg >= 1 && o.pcg_rtol_max > 0 && o.armijo_c1 > 0 && o.armijo_c1 < 1 &&
            o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
-           o.g0_ref >= 0 && (o.lowmem == 0 || o.lowmem == 1);
+           o.g0_ref >= 0 && (o.lowmem == 0 || o.lowmem == 1) &&
+           (o.precond == CLAIRE_PRECOND_SPECTRAL || o.precond == CLAIRE_PRECOND_TWO_LEVEL) && o.pc_coarse >= 1 &&
+           o.pc_tol >= 0 && o.pc_maxit >= 1;
+}
+
+// The two-level grid N_i / f must be whole, even and at least 4 per axis.
+bool valid_coarse(const int n[3], int f)
+{
+    for (int i = 0; i < 3; ++i) {
+        if (f < 1 || n[i] % f) return false;
+        const int m = n[i] / f;
+        if (m < 4 || (m & 1)) return false;
+    }
+    return true;
+}
+
+// Grid geometry of an n1 x n2 x n3 periodic grid on [0, 2 pi)^3.
+Grid grid_of(int n1, int n2, int n3)
+{
+    const double two_pi = 6.283185307179586476925286766559;
+    Grid g;
+    g.n1 = n1;
+    g.n2 = n2;
+    g.n3 = n3;
+    g.n23 = n2 * n3;
+    g.N = static_cast<uint32_t>(static_cast<size_t>(n1) * n2 * n3);
+    g.h1 = static_cast<float>(two_pi / n1);
+    g.h2 = static_cast<float>(two_pi / n2);
+    g.h3 = static_cast<float>(two_pi / n3);
+    g.ih1 = static_cast<float>(n1 / two_pi);
+    g.ih2 = static_cast<float>(n2 / two_pi);
+    g.ih3 = static_cast<float>(n3 / two_pi);
+    return g;
 }
 
 // Layout of the workspace arena in floats (each region 256-byte aligned).
@@ -778,8 +846,183 @@ claire_status fs_sums(claire_ctx* c, int count)
     return CLAIRE_OK;
 }
 
+// ---- two-level zero-velocity preconditioner (Sec. 2.2) ----
+
+// Allocate the coarse-grid state for the current pc_coarse (once).
+claire_status tl_ensure(claire_ctx* c)
+{
+    const int f = c->o.pc_coarse;
+    if (c->tl2 && c->tl2->factor == f) return CLAIRE_OK;
+    if (!valid_coarse(c->n, f))
+        return fail(c, CLAIRE_EINVAL, "pc_coarse %d: every grid size / pc_coarse must be even and >= 4", f);
+    delete c->tl2;
+    c->tl2 = nullptr;
+    TwoLevel* t = new (std::nothrow) TwoLevel();
+    if (!t) return fail(c, CLAIRE_ENOMEM, "two-level preconditioner state");
+    const int nc[3] = {c->n[0] / f, c->n[1] / f, c->n[2] / f};
+    t->factor = f;
+    t->g = grid_of(nc[0], nc[1], nc[2]);
+    t->N = static_cast<size_t>(nc[0]) * nc[1] * nc[2];
+    t->M = static_cast<size_t>(nc[0]) * nc[1] * (nc[2] / 2 + 1);
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    const size_t realb = up(3 * t->N * sizeof(float)), specb = up(3 * t->M * sizeof(cufftComplex)),
+                 fineb = up(3 * c->M * sizeof(cufftComplex));
+    const size_t total = 2 * realb + 7 * specb + 2 * fineb;
+    if (cudaMalloc(&t->block, total) != cudaSuccess) {
+        cudaGetLastError();
+        t->block = nullptr;
+        delete t;
+        return fail(c, CLAIRE_ENOMEM, "two-level preconditioner buffers (%zu bytes)", total);
+    }
+    char* b = static_cast<char*>(t->block);
+    t->gbar = reinterpret_cast<float*>(b); b += realb;
+    t->real = reinterpret_cast<float*>(b); b += realb;
+    cufftComplex** sp[7] = {&t->xh, &t->rh, &t->zh, &t->ph, &t->cp, &t->q, &t->T};
+    for (auto q : sp) {
+        *q = reinterpret_cast<cufftComplex*>(b);
+        b += specb;
+    }
+    t->zf[0] = reinterpret_cast<cufftComplex*>(b); b += fineb;
+    t->zf[1] = reinterpret_cast<cufftComplex*>(b);
+    size_t ws1 = 0, ws2 = 0;
+    cufftResult fr = cufftCreate(&t->r2c);
+    if (fr == CUFFT_SUCCESS) {
+        fr = cufftCreate(&t->c2r);
+        if (fr != CUFFT_SUCCESS) cufftDestroy(t->r2c);
+    }
+    if (fr != CUFFT_SUCCESS) {
+        delete t;
+        return fail(c, CLAIRE_ECUFFT, "coarse-grid FFT plans");
+    }
+    t->plans = true;
+    int nn[3] = {nc[0], nc[1], nc[2]};
+    fr = cufftSetAutoAllocation(t->r2c, 0);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetAutoAllocation(t->c2r, 0);
+    if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(t->r2c, 3, nn, nullptr, 1, (int)t->N, nullptr, 1, (int)t->M, CUFFT_R2C, 3, &ws1);
+    if (fr == CUFFT_SUCCESS)
+        fr = cufftMakePlanMany(t->c2r, 3, nn, nullptr, 1, (int)t->M, nullptr, 1, (int)t->N, CUFFT_C2R, 3, &ws2);
+    const size_t ws = std::max<size_t>(std::max(ws1, ws2), 256);
+    if (fr == CUFFT_SUCCESS && cudaMalloc(&t->work, ws) != cudaSuccess) {
+        cudaGetLastError();
+        t->work = nullptr;
+        fr = CUFFT_ALLOC_FAILED;
+    }
+    if (fr == CUFFT_SUCCESS) fr = cufftSetWorkArea(t->r2c, t->work);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetWorkArea(t->c2r, t->work);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetStream(t->r2c, c->stream);
+    if (fr == CUFFT_SUCCESS) fr = cufftSetStream(t->c2r, c->stream);
+    if (fr != CUFFT_SUCCESS) {
+        delete t;
+        return fail(c, fr == CUFFT_ALLOC_FAILED ? CLAIRE_ENOMEM : CLAIRE_ECUFFT, "coarse-grid FFT plans");
+    }
+    c->tl2 = t;
+    return CLAIRE_OK;
+}
+
+// gbar_c = R (sum_j w_j grad m^j) at the linearisation point: FD8 gradient of
+// the trapezoid mean of the states (FD8 is linear), restricted spectrally.
+claire_status tl_prepare(claire_ctx* c)
+{
+    if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
+    CL_TRY(tl_ensure(c));
+    TwoLevel* t = c->tl2;
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    const size_t N = c->N;
+    float* mean = reinterpret_cast<float*>(c->l0);
+    {
+        KTimer kt(c, KK_POINTWISE, (storage_bytes(c->sto) * (c->nt + 1) + 4.0) * N, 0);
+        launch_mean_levels(c->m, c->nt, static_cast<float>(0.5 * c->dt), static_cast<float>(c->dt), N, mean,
+                           c->sto, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_TRY(fd8_grad(c, mean, c->z, Storage::F32));
+    {
+        KTimer kt(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecR2C(c->r2c, c->z, c->spec2));
+    }
+    launch_tl_restrict(c->grid, c->spec2, c->M, t->g, t->xh, t->M, static_cast<float>(1.0 / N), c->stream);
+    CL_LAUNCHED(c);
+    {
+        KTimer kt(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecC2R(t->c2r, t->xh, t->gbar));
+    }
+    return CLAIRE_OK;
+}
+
+// zf = P^{-1} rf on scaled fine half spectra; *rz = <rf, zf>, *ro = <rf, zold>
+// (0 when zold is null); *its = inner PCG iterations.
+claire_status tl_apply(claire_ctx* c, const cufftComplex* rf, cufftComplex* zf, const cufftComplex* zold,
+                       double* rz, double* ro, int* its)
+{
+    TwoLevel* t = c->tl2;
+    const SpectralOp op = c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV;
+    const int rb = c->red_blocks;
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    *its = 0;
+    {
+        KTimer kt(c, KK_SPECTRAL, 120.0 * t->M, 0, 2);
+        launch_tl_start(c->grid, rf, c->M, t->g, t->rh, t->xh, t->ph, t->cp, t->M, op, c->rp, c->partials,
+                        c->partials + rb, rb, c->stream);
+    }
+    CL_TRY(fs_sums(c, 2));
+    const double r0 = std::sqrt(c->hres[0]);
+    double rzi = c->hres[1];
+    for (int it = 1; r0 > 0.0 && it <= c->o.pc_maxit; ++it) {
+        {
+            KTimer kt(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecC2R(t->c2r, t->cp, t->real));
+        }
+        {
+            KTimer kt(c, KK_POINTWISE, 36.0 * t->N, 0);
+            launch_tl_rank1(t->gbar, t->real, t->N, c->stream);
+            CL_LAUNCHED(c);
+        }
+        {
+            KTimer kt(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecR2C(t->r2c, t->real, t->T));
+        }
+        {
+            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0, 1);
+            launch_tl_hp(t->g, t->T, t->ph, t->q, t->M, c->o.grad_form, c->rp, static_cast<float>(1.0 / t->N),
+                         c->partials, rb, c->stream);
+        }
+        CL_TRY(fs_sums(c, 1));
+        const double pq = c->hres[0];
+        *its = it;
+        if (pq <= 0.0) break;
+        const double alpha = rzi / pq;
+        {
+            KTimer kt(c, KK_SPECTRAL, 144.0 * t->M, 0, 2);
+            launch_tl_update(t->g, t->ph, t->q, t->xh, t->rh, t->zh, t->M, static_cast<float>(alpha), op, c->rp,
+                             c->partials, c->partials + rb, rb, c->stream);
+        }
+        CL_TRY(fs_sums(c, 2));
+        if (c->o.pc_tol > 0 && std::sqrt(c->hres[0]) <= c->o.pc_tol * r0) break;
+        if (it == c->o.pc_maxit) break;
+        const double rz_new = c->hres[1];
+        {
+            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0);
+            launch_dir_stored(t->g, t->zh, t->ph, t->cp, t->M, static_cast<float>(rz_new / rzi), 0, c->stream);
+            CL_LAUNCHED(c);
+        }
+        rzi = rz_new;
+    }
+    {
+        KTimer kt(c, KK_SPECTRAL, (zold ? 72.0 : 48.0) * c->M, 0, 2);
+        launch_tl_finish(c->grid, rf, zf, zold, c->M, t->g, t->xh, t->M, op, c->rp, c->partials, c->partials + rb,
+                         rb, c->stream);
+    }
+    CL_TRY(fs_sums(c, 2));
+    *rz = c->hres[0];
+    *ro = zold ? c->hres[1] : 0.0;
+    c->pc_inner_total += *its;
+    return CLAIRE_OK;
+}
+
 // Matrix-free PCG for H x = -g (x0 = 0), preconditioned by the spectral
-// inverse of the regulariser.  x, r and the direction p live in Fourier
+// inverse of the regulariser or the two-level zero-velocity preconditioner
+// (precond = 1, flexible direction update).  x, r and the direction p live in Fourier
 // space (scaled half spectra); the preconditioner, the regulariser part of
 // H p and every inner product (Parseval) are spectral.  Each iteration takes
 // one inverse transform (p, for the transport solves) and one forward
@@ -789,7 +1032,9 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
     const SpectralOp op = c->o.grad_form == 1 ? SPEC_AINV : SPEC_INV;
     const float scale = static_cast<float>(1.0 / c->N);
     const double M = static_cast<double>(c->M);
+    const bool two_level = c->o.precond == CLAIRE_PRECOND_TWO_LEVEL;
     *its = 0;
+    if (two_level) CL_TRY(tl_prepare(c));
     {
         PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
         {
@@ -807,16 +1052,26 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         CL_CUDA(c, cudaMemsetAsync(c->x, 0, 3 * c->N * sizeof(float), c->stream));
         return CLAIRE_OK;
     }
-    double rz_prev = rz;
+    // two-level: z~ = P^{-1} r~ is stored (zf[cur]) and the direction update is
+    // the flexible one, beta = <r_new, z_new - z_old> / <r_old, z_old>
+    int cur = 0, inner_its = 0;
+    if (two_level) {
+        double ro;
+        CL_TRY(tl_apply(c, c->rh, c->tl2->zf[0], nullptr, &rz, &ro, &inner_its));
+    }
+    double beta = 0.0;
     for (int it = 1; it <= c->o.max_pcg; ++it) {
         *its = it;
         {
             PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
             {
                 KTimer t(c, KK_SPECTRAL, (it == 1 ? 72.0 : 96.0) * M, 0);
-                launch_spectral_direction(c->grid, c->rh, c->phat, c->spec2, c->M,
-                                          static_cast<float>(it == 1 ? 0.0 : rz / rz_prev), it == 1 ? 1 : 0, op,
-                                          c->rp, c->stream);
+                if (two_level)
+                    launch_dir_stored(c->grid, c->tl2->zf[cur], c->phat, c->spec2, c->M, static_cast<float>(beta),
+                                      it == 1 ? 1 : 0, c->stream);
+                else
+                    launch_spectral_direction(c->grid, c->rh, c->phat, c->spec2, c->M, static_cast<float>(beta),
+                                              it == 1 ? 1 : 0, op, c->rp, c->stream);
                 CL_LAUNCHED(c);
             }
             KTimer t(c, KK_FFT, 0, 0);
@@ -852,8 +1107,16 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         const double rr = c->hres[0];
         if (!c->o.pcg_fixed && std::sqrt(rr) <= eta * r0) break;
         if (it == c->o.max_pcg) break;
-        rz_prev = rz;
-        rz = c->hres[1];
+        if (two_level) {
+            double rz_new, ro;
+            CL_TRY(tl_apply(c, c->rh, c->tl2->zf[1 - cur], c->tl2->zf[cur], &rz_new, &ro, &inner_its));
+            beta = (rz_new - ro) / rz;
+            cur = 1 - cur;
+            rz = rz_new;
+        } else {
+            beta = c->hres[1] / rz;
+            rz = c->hres[1];
+        }
     }
     {
         PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
@@ -934,6 +1197,7 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     else
         fill_defaults(&o);
     if (!valid_opts(o)) return CLAIRE_EINVAL;
+    if (o.precond == CLAIRE_PRECOND_TWO_LEVEL && !valid_coarse(grid, o.pc_coarse)) return CLAIRE_EINVAL;
     int ndev = 0;
     if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
         cudaGetLastError();
@@ -1074,6 +1338,10 @@ claire_status claire_set_stream(claire_ctx* c, void* stream)
     c->stream = static_cast<cudaStream_t>(stream);
     CL_FFT(c, cufftSetStream(c->r2c, c->stream));
     CL_FFT(c, cufftSetStream(c->c2r, c->stream));
+    if (c->tl2) {
+        CL_FFT(c, cufftSetStream(c->tl2->r2c, c->stream));
+        CL_FFT(c, cufftSetStream(c->tl2->c2r, c->stream));
+    }
     return CLAIRE_OK;
 }
 
@@ -1143,7 +1411,18 @@ claire_status claire_precond(claire_ctx* c, const float* r, float* z)
     if (!r || !z) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dr;
     CL_TRY(device_input(c, r, 3 * c->N, c->p, &dr));
-    CL_TRY(precond(c, dr, c->r));
+    if (c->o.precond == CLAIRE_PRECOND_TWO_LEVEL) {
+        CL_TRY(tl_prepare(c));
+        CL_FFT(c, cufftExecR2C(c->r2c, const_cast<float*>(dr), c->rh));
+        launch_cscale(c->rh, 3 * c->M, static_cast<float>(1.0 / c->N), c->stream);
+        CL_LAUNCHED(c);
+        double rz, ro;
+        int its;
+        CL_TRY(tl_apply(c, c->rh, c->tl2->zf[0], nullptr, &rz, &ro, &its));
+        CL_FFT(c, cufftExecC2R(c->c2r, c->tl2->zf[0], c->r));
+    } else {
+        CL_TRY(precond(c, dr, c->r));
+    }
     CL_TRY(copy_out(c, z, c->r, 3 * c->N));
     collect_timing(c);
     return CLAIRE_OK;
@@ -1163,6 +1442,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
     for (int k = 0; k < KK_COUNT; ++k) ks0[k] = c->ks[k];
     double ph0[8];
     for (int i = 0; i < 8; ++i) ph0[i] = c->phase_s[i];
+    const long long pc_inner0 = c->pc_inner_total;
 
     CL_CUDA(c, cudaMemcpyAsync(c->v, v_inout, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
     claire_status st = CLAIRE_ENOTCONVERGED;
@@ -1232,6 +1512,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
         if (rel <= c->o.gtol) st = CLAIRE_OK;
     }
     R.gnorm_rel = rel;
+    R.pc_inner_iters_total = static_cast<int>(c->pc_inner_total - pc_inner0);
     R.J = c->J_lin;
     R.mismatch = c->mis_lin;
     {
@@ -1540,6 +1821,9 @@ claire_status claire_set_opts(claire_ctx* c, const claire_opts* opts)
     if (!valid_opts(*opts)) return fail(c, CLAIRE_EINVAL, "invalid options");
     if (opts->storage != c->o.storage || opts->lowmem != c->o.lowmem)
         return fail(c, CLAIRE_EINVAL, "storage and lowmem are fixed at claire_create");
+    if (opts->precond == CLAIRE_PRECOND_TWO_LEVEL && !valid_coarse(c->n, opts->pc_coarse))
+        return fail(c, CLAIRE_EINVAL, "pc_coarse %d: every grid size / pc_coarse must be even and >= 4",
+                    opts->pc_coarse);
     collect_timing(c);
     c->o = *opts;
     c->rp.beta_w = static_cast<float>(opts->beta_w);

@@ -171,6 +171,26 @@ void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph,
 
 // Deterministic FP64 reductions: partial sums per block, then a one-block
 // final sum in fixed order.  `partials` holds at least nblocks doubles.
+// two-level zero-velocity preconditioner (coarse grid gc of the fine grid gf; cs* = component strides)
+void launch_mean_levels(const void* m, int nt, float w_end, float w_mid, size_t N, float* out, Storage sto,
+                        cudaStream_t st);
+void launch_cscale(cufftComplex* x, size_t n, float s, cudaStream_t st);
+void launch_tl_restrict(const Grid& gf, const cufftComplex* F, size_t csf, const Grid& gc, cufftComplex* out,
+                        size_t csc, float invN, cudaStream_t st);
+void launch_tl_start(const Grid& gf, const cufftComplex* rf, size_t csf, const Grid& gc, cufftComplex* rh,
+                     cufftComplex* xh, cufftComplex* ph, cufftComplex* cp, size_t cs, SpectralOp op, RegParams rp,
+                     double* prr, double* prz, int nblocks, cudaStream_t st);
+void launch_tl_rank1(const float* gbar, float* p, size_t Nc, cudaStream_t st);
+void launch_tl_hp(const Grid& gc, const cufftComplex* T, const cufftComplex* ph, cufftComplex* q, size_t cs,
+                  int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st);
+void launch_tl_update(const Grid& gc, const cufftComplex* ph, const cufftComplex* q, cufftComplex* xh,
+                      cufftComplex* rh, cufftComplex* zh, size_t cs, float alpha, SpectralOp op, RegParams rp,
+                      double* prr, double* prz, int nblocks, cudaStream_t st);
+void launch_dir_stored(const Grid& g, const cufftComplex* zh, cufftComplex* ph, cufftComplex* cp, size_t cs,
+                       float beta, int first, cudaStream_t st);
+void launch_tl_finish(const Grid& gf, const cufftComplex* rf, cufftComplex* zf, const cufftComplex* zold, size_t csf,
+                      const Grid& gc, const cufftComplex* xc, size_t csc, SpectralOp op, RegParams rp, double* prz,
+                      double* pro, int nblocks, cudaStream_t st);
 void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,
                         cudaStream_t st);
 void launch_sqdiff_partial(const void* a, const void* b, size_t n, double* partials, int nblocks,

@@ -528,6 +528,261 @@ __global__ void k_bspline_scale(Grid g, cufftComplex* __restrict__ spec, size_t 
     spec[e].x *= f;
     spec[e].y *= f;
 }
+// out = w_end (m^0 + m^nt) + w_mid (m^1 + ... + m^{nt-1}) (trapezoid over the stored levels)
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_mean_levels(const S* __restrict__ m, int nt, float w_end,
+                                                           float w_mid, size_t N, float* __restrict__ out)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < N;
+         i += static_cast<size_t>(gridDim.x) * kThreads) {
+        float acc = w_end * (ldf<S>(m + i) + ldf<S>(m + static_cast<size_t>(nt) * N + i));
+        for (int j = 1; j < nt; ++j) acc = fmaf(w_mid, ldf<S>(m + static_cast<size_t>(j) * N + i), acc);
+        out[i] = acc;
+    }
+}
+
+__global__ void __launch_bounds__(kThreads) k_cscale(float2* __restrict__ x, size_t n, float s)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n;
+         i += static_cast<size_t>(gridDim.x) * kThreads)
+        x[i] = cmul(s, x[i]);
+}
+
+// ---- two-level zero-velocity preconditioner (Sec. 2.2) ----
+// The coarse grid gc keeps the modes |k_i| < gc.n_i / 2 of the fine grid gf
+// (its Nyquist planes are dropped); the inner PCG runs on those modes without
+// the mean (k = 0), the "kept" modes, in the same scaled half-spectrum
+// convention as the outer PCG (coefficients are resolution independent, so
+// restriction and prolongation copy them).
+
+// Wavenumbers of half-spectrum mode idx of grid g.
+__device__ __forceinline__ void wavenumbers(const Grid& g, size_t idx, int& k1, int& k2, int& k3)
+{
+    const int n3h = g.n3 / 2 + 1;
+    k3 = static_cast<int>(idx % n3h);
+    const size_t r = idx / n3h;
+    const int j = static_cast<int>(r % g.n2);
+    const int i = static_cast<int>(r / g.n2);
+    k1 = i <= g.n1 / 2 ? i : i - g.n1;
+    k2 = j <= g.n2 / 2 ? j : j - g.n2;
+}
+
+// |k_i| < n_i / 2 on every axis of grid g (no Nyquist plane)
+__device__ __forceinline__ bool below_nyquist(const Grid& g, int k1, int k2, int k3)
+{
+    return 2 * abs(k1) < g.n1 && 2 * abs(k2) < g.n2 && 2 * k3 < g.n3;
+}
+
+// Half-spectrum index of wavenumber k on grid g (k assumed representable).
+__device__ __forceinline__ size_t mode_index(const Grid& g, int k1, int k2, int k3)
+{
+    const int i = k1 >= 0 ? k1 : k1 + g.n1;
+    const int j = k2 >= 0 ? k2 : k2 + g.n2;
+    return (static_cast<size_t>(i) * g.n2 + j) * (g.n3 / 2 + 1) + k3;
+}
+
+// Coarse spectrum of a fine field given by its unnormalised R2C transform F
+// (scaled by 1/N here): every coarse mode below the coarse Nyquist, mean
+// included (the restriction R of the mean state gradient).
+__global__ void __launch_bounds__(kThreads) k_tl_restrict(Grid gf, const float2* __restrict__ F, size_t csf,
+                                                           Grid gc, float2* __restrict__ out, size_t csc,
+                                                           float invN)
+{
+    const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * (gc.n3 / 2 + 1);
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < Mc;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        int k1, k2, k3;
+        wavenumbers(gc, idx, k1, k2, k3);
+        const bool keep = below_nyquist(gc, k1, k2, k3);
+        const size_t f = keep ? mode_index(gf, k1, k2, k3) : 0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) out[c * csc + idx] = keep ? cmul(invN, F[c * csf + f]) : make_float2(0.f, 0.f);
+    }
+}
+
+// Start of the inner PCG: r = Q R rf (kept modes of the fine residual), x = 0,
+// z = M r, p = z (and its copy cp for the inverse transform); partials of
+// |r|^2 and <r, z>.
+__global__ void __launch_bounds__(kThreads) k_tl_start(Grid gf, const float2* __restrict__ rf, size_t csf,
+                                                        Grid gc, float2* __restrict__ rh, float2* __restrict__ xh,
+                                                        float2* __restrict__ ph, float2* __restrict__ cp, size_t cs,
+                                                        int op, RegParams rp, double* __restrict__ prr,
+                                                        double* __restrict__ prz)
+{
+    const int n3h = gc.n3 / 2 + 1;
+    const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * n3h;
+    double arr = 0.0, arz = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < Mc;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        int k1, k2, k3;
+        wavenumbers(gc, idx, k1, k2, k3);
+        const bool keep = below_nyquist(gc, k1, k2, k3) && (k1 | k2 | k3) != 0;
+        const size_t f = keep ? mode_index(gf, k1, k2, k3) : 0;
+        const float2 zero = make_float2(0.f, 0.f);
+        float2 r[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = keep ? rf[c * csf + f] : zero;
+        const Mode m = mode_of(gc, idx, n3h, rp);
+        float2 z[3];
+        apply_inv(m, op, r[0], r[1], r[2], z[0], z[1], z[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            rh[c * cs + idx] = r[c];
+            xh[c * cs + idx] = zero;
+            ph[c * cs + idx] = z[c];
+            cp[c * cs + idx] = z[c];
+        }
+        arr += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], r[0], r[1], r[2]));
+        arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z[0], z[1], z[2]));
+    }
+    block_sum2(arr, arz, prr, prz);
+}
+
+// In place on the coarse real fields: p <- gbar (gbar . p).
+__global__ void __launch_bounds__(kThreads) k_tl_rank1(const float* __restrict__ gbar, float* __restrict__ p,
+                                                        size_t Nc)
+{
+    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < Nc;
+         i += static_cast<size_t>(gridDim.x) * kThreads) {
+        const float g0 = gbar[i], g1 = gbar[Nc + i], g2 = gbar[2 * Nc + i];
+        const float s = g0 * p[i] + g1 * p[Nc + i] + g2 * p[2 * Nc + i];
+        p[i] = s * g0;
+        p[Nc + i] = s * g1;
+        p[2 * Nc + i] = s * g2;
+    }
+}
+
+// q = Q (S p + scale T) (K of the sum for the paper's gradient form), T the
+// unnormalised transform of gbar (gbar . p); partials of <p, q>.
+__global__ void __launch_bounds__(kThreads) k_tl_hp(Grid gc, const float2* __restrict__ T,
+                                                     const float2* __restrict__ ph, float2* __restrict__ q,
+                                                     size_t cs, int kform, RegParams rp, float scale,
+                                                     double* __restrict__ ppq)
+{
+    const int n3h = gc.n3 / 2 + 1;
+    const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * n3h;
+    double acc = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < Mc;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        int k1, k2, k3;
+        wavenumbers(gc, idx, k1, k2, k3);
+        const bool keep = below_nyquist(gc, k1, k2, k3) && (k1 | k2 | k3) != 0;
+        const Mode m = mode_of(gc, idx, n3h, rp);
+        const float2 p0 = ph[idx], p1 = ph[cs + idx], p2 = ph[2 * cs + idx];
+        float2 h[3];
+        apply_S(m, p0, p1, p2, h[0], h[1], h[2]);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 b = T[c * cs + idx];
+            h[c] = make_float2(fmaf(scale, b.x, h[c].x), fmaf(scale, b.y, h[c].y));
+        }
+        if (kform && m.kk != 0.0f) {
+            const float2 ud = make_float2(m.u1 * h[0].x + m.u2 * h[1].x + m.u3 * h[2].x,
+                                          m.u1 * h[0].y + m.u2 * h[1].y + m.u3 * h[2].y);
+            const float f = m.c / (m.a + m.c * (m.u1 * m.u1 + m.u2 * m.u2 + m.u3 * m.u3));
+            h[0] = make_float2(h[0].x - f * m.u1 * ud.x, h[0].y - f * m.u1 * ud.y);
+            h[1] = make_float2(h[1].x - f * m.u2 * ud.x, h[1].y - f * m.u2 * ud.y);
+            h[2] = make_float2(h[2].x - f * m.u3 * ud.x, h[2].y - f * m.u3 * ud.y);
+        }
+        if (!keep) h[0] = h[1] = h[2] = make_float2(0.f, 0.f);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q[c * cs + idx] = h[c];
+        acc += static_cast<double>(m.wt * cdot3(p0, p1, p2, h[0], h[1], h[2]));
+    }
+    block_sum(acc, ppq);
+}
+
+// x += alpha p, r -= alpha q, z = M r (stored); partials of |r|^2 and <r, z>.
+__global__ void __launch_bounds__(kThreads) k_tl_update(Grid gc, const float2* __restrict__ ph,
+                                                         const float2* __restrict__ q, float2* __restrict__ xh,
+                                                         float2* __restrict__ rh, float2* __restrict__ zh, size_t cs,
+                                                         float alpha, int op, RegParams rp,
+                                                         double* __restrict__ prr, double* __restrict__ prz)
+{
+    const int n3h = gc.n3 / 2 + 1;
+    const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * n3h;
+    double arr = 0.0, arz = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < Mc;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        float2 r[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 p = ph[c * cs + idx], hq = q[c * cs + idx];
+            float2 x = xh[c * cs + idx], rr = rh[c * cs + idx];
+            x = make_float2(fmaf(alpha, p.x, x.x), fmaf(alpha, p.y, x.y));
+            rr = make_float2(fmaf(-alpha, hq.x, rr.x), fmaf(-alpha, hq.y, rr.y));
+            xh[c * cs + idx] = x;
+            rh[c * cs + idx] = rr;
+            r[c] = rr;
+        }
+        const Mode m = mode_of(gc, idx, n3h, rp);
+        float2 z0, z1, z2;
+        apply_inv(m, op, r[0], r[1], r[2], z0, z1, z2);
+        zh[idx] = z0; zh[cs + idx] = z1; zh[2 * cs + idx] = z2;
+        arr += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], r[0], r[1], r[2]));
+        arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z0, z1, z2));
+    }
+    block_sum2(arr, arz, prr, prz);
+}
+
+// p = z + beta p (p = z when first) and its copy cp for the inverse transform;
+// on any grid (the inner PCG, and the outer PCG when z is stored).
+__global__ void __launch_bounds__(kThreads) k_dir_stored(Grid g, const float2* __restrict__ zh,
+                                                          float2* __restrict__ ph, float2* __restrict__ cp, size_t cs,
+                                                          float beta, int first)
+{
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float2 z = zh[c * cs + idx];
+            float2 p = z;
+            if (!first) {
+                const float2 o = ph[c * cs + idx];
+                p = make_float2(fmaf(beta, o.x, z.x), fmaf(beta, o.y, z.y));
+            }
+            ph[c * cs + idx] = p;
+            cp[c * cs + idx] = p;
+        }
+    }
+}
+
+// Outer preconditioned residual: z = E x (kept coarse modes), r on the mean,
+// M r on every other mode; partials of <r, z> and <r, zold> (zold may be null).
+__global__ void __launch_bounds__(kThreads) k_tl_finish(Grid gf, const float2* __restrict__ rf,
+                                                         float2* __restrict__ zf, const float2* __restrict__ zold,
+                                                         size_t csf, Grid gc, const float2* __restrict__ xc,
+                                                         size_t csc, int op, RegParams rp, double* __restrict__ prz,
+                                                         double* __restrict__ pro)
+{
+    const int n3h = gf.n3 / 2 + 1;
+    const size_t M = static_cast<size_t>(gf.n1) * gf.n2 * n3h;
+    double az = 0.0, ao = 0.0;
+    for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
+         idx += static_cast<size_t>(gridDim.x) * kThreads) {
+        int k1, k2, k3;
+        wavenumbers(gf, idx, k1, k2, k3);
+        const bool low = below_nyquist(gc, k1, k2, k3) && (k1 | k2 | k3) != 0;
+        const Mode m = mode_of(gf, idx, n3h, rp);
+        const float2 r0 = rf[idx], r1 = rf[csf + idx], r2 = rf[2 * csf + idx];
+        float2 z[3];
+        if (low) {
+            const size_t ci = mode_index(gc, k1, k2, k3);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[c] = xc[c * csc + ci];
+        } else {
+            apply_inv(m, op, r0, r1, r2, z[0], z[1], z[2]);  // identity at k = 0
+        }
+#pragma unroll
+        for (int c = 0; c < 3; ++c) zf[c * csf + idx] = z[c];
+        az += static_cast<double>(m.wt * cdot3(r0, r1, r2, z[0], z[1], z[2]));
+        if (zold)
+            ao += static_cast<double>(m.wt * cdot3(r0, r1, r2, zold[idx], zold[csf + idx], zold[2 * csf + idx]));
+    }
+    block_sum2(az, ao, prz, pro);
+}
+
 }  // namespace
 
 void launch_spectral(const Grid& g, cufftComplex* xh, size_t cstride, SpectralOp op, RegParams rp,
@@ -580,6 +835,79 @@ void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph,
                                               reinterpret_cast<const float2*>(ph),
                                               reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(rh),
                                               cs, alpha, static_cast<int>(op), rp, prr, prz);
+}
+
+void launch_mean_levels(const void* m, int nt, float w_end, float w_mid, size_t N, float* out, Storage sto,
+                        cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_mean_levels<SType><<<stream_blocks(N), kThreads, 0, st>>>(static_cast<const SType*>(m), nt, w_end, w_mid,
+                                                                    N, out);
+    });
+}
+
+void launch_cscale(cufftComplex* x, size_t n, float s, cudaStream_t st)
+{
+    k_cscale<<<stream_blocks(n), kThreads, 0, st>>>(reinterpret_cast<float2*>(x), n, s);
+}
+
+void launch_tl_restrict(const Grid& gf, const cufftComplex* F, size_t csf, const Grid& gc, cufftComplex* out,
+                        size_t csc, float invN, cudaStream_t st)
+{
+    const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * (gc.n3 / 2 + 1);
+    k_tl_restrict<<<stream_blocks(Mc), kThreads, 0, st>>>(gf, reinterpret_cast<const float2*>(F), csf, gc,
+                                                          reinterpret_cast<float2*>(out), csc, invN);
+}
+
+void launch_tl_start(const Grid& gf, const cufftComplex* rf, size_t csf, const Grid& gc, cufftComplex* rh,
+                     cufftComplex* xh, cufftComplex* ph, cufftComplex* cp, size_t cs, SpectralOp op, RegParams rp,
+                     double* prr, double* prz, int nblocks, cudaStream_t st)
+{
+    k_tl_start<<<nblocks, kThreads, 0, st>>>(gf, reinterpret_cast<const float2*>(rf), csf, gc,
+                                             reinterpret_cast<float2*>(rh), reinterpret_cast<float2*>(xh),
+                                             reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp), cs,
+                                             static_cast<int>(op), rp, prr, prz);
+}
+
+void launch_tl_rank1(const float* gbar, float* p, size_t Nc, cudaStream_t st)
+{
+    k_tl_rank1<<<stream_blocks(Nc), kThreads, 0, st>>>(gbar, p, Nc);
+}
+
+void launch_tl_hp(const Grid& gc, const cufftComplex* T, const cufftComplex* ph, cufftComplex* q, size_t cs,
+                  int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st)
+{
+    k_tl_hp<<<nblocks, kThreads, 0, st>>>(gc, reinterpret_cast<const float2*>(T), reinterpret_cast<const float2*>(ph),
+                                          reinterpret_cast<float2*>(q), cs, kform, rp, scale, ppq);
+}
+
+void launch_tl_update(const Grid& gc, const cufftComplex* ph, const cufftComplex* q, cufftComplex* xh,
+                      cufftComplex* rh, cufftComplex* zh, size_t cs, float alpha, SpectralOp op, RegParams rp,
+                      double* prr, double* prz, int nblocks, cudaStream_t st)
+{
+    k_tl_update<<<nblocks, kThreads, 0, st>>>(gc, reinterpret_cast<const float2*>(ph),
+                                              reinterpret_cast<const float2*>(q), reinterpret_cast<float2*>(xh),
+                                              reinterpret_cast<float2*>(rh), reinterpret_cast<float2*>(zh), cs, alpha,
+                                              static_cast<int>(op), rp, prr, prz);
+}
+
+void launch_dir_stored(const Grid& g, const cufftComplex* zh, cufftComplex* ph, cufftComplex* cp, size_t cs,
+                       float beta, int first, cudaStream_t st)
+{
+    const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
+    k_dir_stored<<<stream_blocks(M), kThreads, 0, st>>>(g, reinterpret_cast<const float2*>(zh),
+                                                        reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
+                                                        cs, beta, first);
+}
+
+void launch_tl_finish(const Grid& gf, const cufftComplex* rf, cufftComplex* zf, const cufftComplex* zold, size_t csf,
+                      const Grid& gc, const cufftComplex* xc, size_t csc, SpectralOp op, RegParams rp, double* prz,
+                      double* pro, int nblocks, cudaStream_t st)
+{
+    k_tl_finish<<<nblocks, kThreads, 0, st>>>(gf, reinterpret_cast<const float2*>(rf), reinterpret_cast<float2*>(zf),
+                                              reinterpret_cast<const float2*>(zold), csf, gc,
+                                              reinterpret_cast<const float2*>(xc), csc, static_cast<int>(op), rp, prz,
+                                              pro);
 }
 
 void launch_dot_partial(const float* x, const float* y, size_t n, double* partials, int nblocks,

@@ -68,6 +68,29 @@ def test_default_opts(claire):
     o = claire.claire_default_opts()
     assert o.interp == 3 and o.reg == 1 and abs(o.beta_w - 1e-4) < 1e-18
     assert abs(o.gtol - 5e-2) < 1e-18 and o.grad_form == 0 and o.timing == 0
+    # the spectral preconditioner by default; the two-level one's defaults
+    assert o.precond == claire.PRECOND_SPECTRAL and o.pc_coarse == 2
+    assert abs(o.pc_tol - 1e-1) < 1e-18 and o.pc_maxit == 50
+
+
+def test_two_level_options_are_validated(claire):
+    """Invalid preconditioner options are rejected on the host (no GPU needed:
+    validation precedes any device call)."""
+    o = claire.claire_default_opts()
+    o.precond = 2
+    lib = claire.lib()
+    ctx = ctypes.c_void_p()
+    grid = (ctypes.c_int * 3)(16, 16, 16)
+    assert lib.claire_create(ctypes.byref(ctx), grid, ctypes.c_double(1e-2), 4, ctypes.byref(o)) == -1
+    o = claire.claire_default_opts()
+    o.precond = claire.PRECOND_TWO_LEVEL
+    o.pc_coarse = 3  # 16 / 3 is not whole
+    assert lib.claire_create(ctypes.byref(ctx), grid, ctypes.c_double(1e-2), 4, ctypes.byref(o)) == -1
+    o.pc_coarse = 8  # 16 / 8 = 2 < 4
+    assert lib.claire_create(ctypes.byref(ctx), grid, ctypes.c_double(1e-2), 4, ctypes.byref(o)) == -1
+    o.pc_coarse = 2
+    o.pc_tol = -1.0
+    assert lib.claire_create(ctypes.byref(ctx), grid, ctypes.c_double(1e-2), 4, ctypes.byref(o)) == -1
 
 
 def test_query_workspace_scales_with_grid_and_nt(claire):

@@ -71,6 +71,10 @@ def parse_args():
                     help="timing of the warm-start network kernels (every conv shape of the U-Net at 128^3, "
                          "batch 4), one training step, and the SL reverse-mode transport at 256^3")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--precond", default="spectral", choices=["spectral", "two-level"],
+                    help="PCG preconditioner of the timed registration")
+    ap.add_argument("--precond-report", action="store_true",
+                    help="time to tolerance at --n with the spectral and the two-level zero-velocity preconditioner")
     return ap.parse_args()
 
 
@@ -88,7 +92,7 @@ def config_dict(args, n_gpus):
                         "|k|<=8 max|v|=1, Gauss-Newton-Krylov to gtol 5e-2 from v=0" % args.n,
             "grid": [args.n] * 3, "nt": 4, "interp": "cubic Lagrange", "beta_v": args.beta,
             "beta_w": 1e-4, "reg": "H1 seminorm", "gtol": 5e-2, "max_pcg": 50,
-            "storage": args.storage,
+            "storage": args.storage, "precond": args.precond,
             "l2_policy": "inputs larger than L2 (working set %.1f GB > 129 MB L2)"
                          % (args.n ** 3 * 4 * 60 / 1e9),
             "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
@@ -281,8 +285,9 @@ def run_ours(args):
     N = int(np.prod(grid))
     stream = torch.cuda.current_stream(dev)
     storage = {"f32": claire.STORAGE_F32, "f16": claire.STORAGE_F16, "bf16": claire.STORAGE_BF16}[args.storage]
+    precond = claire.PRECOND_TWO_LEVEL if args.precond == "two-level" else claire.PRECOND_SPECTRAL
     ctx = claire.Context(grid, args.beta, 4, stream=stream.cuda_stream, beta_w=1e-4, gtol=5e-2,
-                         max_gn=50, max_pcg=50, storage=storage)
+                         max_gn=50, max_pcg=50, storage=storage, precond=precond)
     # reference image by our own transport of the clean template, then noise
     base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
     vstar_d = torch.from_numpy(vstar.astype(np.float32)).to(dev)
@@ -537,8 +542,9 @@ def run_warmstart_report(args):
     zero = torch.zeros((3,) + grid, device=dev)
     g = torch.empty((3,) + grid, device=dev)
 
-    def solve(ctx, learned):
+    def solve(ctx, learned, pc=claire.PRECOND_SPECTRAL):
         v = torch.zeros((3,) + grid, device=dev)
+        ctx.set_opts(precond=pc)
         torch.cuda.synchronize()
         t0 = time.perf_counter()
         split = {}
@@ -558,11 +564,15 @@ def run_warmstart_report(args):
         return secs, rep, v, split
 
     runs = {}
-    for name, ctx, learned in (("fp32_zero", ctx32, False), ("fp16_zero", ctx16, False),
-                               ("fp32_learned", ctx32, True), ("fp16_learned", ctx16, True)):
-        solve(ctx, learned)  # warm-up
-        secs, rep, v, split = solve(ctx, learned)
+    TL = claire.PRECOND_TWO_LEVEL
+    for name, ctx, learned, pc in (("fp32_zero", ctx32, False, 0), ("fp16_zero", ctx16, False, 0),
+                                   ("fp32_learned", ctx32, True, 0), ("fp16_learned", ctx16, True, 0),
+                                   ("fp32_zero_two_level", ctx32, False, TL),
+                                   ("fp16_learned_two_level", ctx16, True, TL)):
+        solve(ctx, learned, pc)  # warm-up
+        secs, rep, v, split = solve(ctx, learned, pc)
         runs[name] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                      "inner_pcg_iters": rep["pc_inner_iters_total"],
                       "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "gnorm_rel_to_own_g0":
                       rep["gnorm_rel"], "detj_min": rep["detj_min"], "detj_max": rep["detj_max"], **split}
         runs[name]["_v"] = v.cpu().numpy()
@@ -571,7 +581,7 @@ def run_warmstart_report(args):
     out["guess"] = {"mismatch_at_guess": ctx32.objective(vw)[1], "mismatch_at_zero": ctx32.objective(zero)[1]}
     p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
     m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
-    for name in ("fp32_zero", "fp16_learned"):
+    for name in ("fp32_zero", "fp16_learned", "fp16_learned_two_level"):
         J_o, mis_o, _ = oracle.objective(runs[name]["_v"].astype(np.float64), m0_64, m1_64, p)
         runs[name]["oracle_J"] = J_o
         runs[name]["oracle_mismatch"] = mis_o
@@ -583,6 +593,70 @@ def run_warmstart_report(args):
     out["oracle_J_rel_diff_learned_vs_plain"] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
     out["oracle_mismatch_rel_diff_learned_vs_plain"] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / \
         a["oracle_mismatch"]
+    c2 = runs["fp16_learned_two_level"]
+    out["speedup_fp16_learned_two_level_vs_fp32_zero"] = a["time_to_tol_s"] / c2["time_to_tol_s"]
+    out["oracle_J_rel_diff_learned_two_level_vs_plain"] = (c2["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
+    out["oracle_mismatch_rel_diff_learned_two_level_vs_plain"] = (c2["oracle_mismatch"] - a["oracle_mismatch"]) / \
+        a["oracle_mismatch"]
+    print(json.dumps(out))
+
+
+def run_precond_report(args):
+    """Time to tolerance of the bench workload at --n with the spectral
+    preconditioner S^{-1} and the paper's two-level zero-velocity one
+    (coarse grid n/2, inner PCG to 1e-1, flexible outer PCG), FP32 and FP16
+    storage, from v = 0 (one warm-up solve each).  J and the mismatch at every
+    returned velocity are re-evaluated by the FP64 oracle."""
+    import torch
+    import oracle
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream().cuda_stream
+    grid, base, vstar = workload(args.n)
+    out = {"workload": "%d^3 nested-label template, band-limited v* |k|<=8 max|v|=1, noise 0.02, nt=4, "
+                       "tricubic, beta_v=%g, beta_w=1e-4, gtol 5e-2" % (args.n, args.beta)}
+    ctxs = {}
+    for sto in ("f32", "f16"):
+        ctxs[sto] = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                                   storage=claire.STORAGE_F32 if sto == "f32" else claire.STORAGE_F16)
+    base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
+    m1c = torch.empty(grid, device=dev)
+    ctxs["f32"].transport(torch.from_numpy(vstar.astype(np.float32)).to(dev), base_d, m1c, claire.TRANSPORT_FWD)
+    m1 = synth.add_noise(m1c.cpu().numpy().astype(np.float64), 0.02, seed=1).astype(np.float32)
+    m0 = synth.add_noise(base, 0.02, seed=0).astype(np.float32)
+    m0_d = torch.from_numpy(m0).to(dev)
+    m1_d = torch.from_numpy(m1).to(dev)
+    for c in ctxs.values():
+        c.set_images(m0_d, m1_d)
+    p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
+    m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
+    runs = {}
+    for sto, pc in (("f32", "spectral"), ("f32", "two-level"), ("f16", "two-level")):
+        ctx = ctxs[sto]
+        ctx.set_opts(precond=claire.PRECOND_TWO_LEVEL if pc == "two-level" else claire.PRECOND_SPECTRAL)
+        for rep_i in range(2):  # warm-up, then timed
+            v = torch.zeros((3,) + grid, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            status, rep = ctx.register(v)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+        J_o, mis_o, _ = oracle.objective(v.cpu().numpy().astype(np.float64), m0_64, m1_64, p)
+        runs["%s_%s" % (sto, pc)] = {
+            "time_to_tol_s": secs, "status": rep["status"], "gn_iters": rep["gn_iters"],
+            "pcg_iters": rep["pcg_iters_total"], "pcg_per_gn": rep["pcg_iters"],
+            "inner_pcg_iters": rep["pc_inner_iters_total"], "gnorm_rel": rep["gnorm_rel"], "J": rep["J"],
+            "r": rep["r"], "detj_min": rep["detj_min"], "detj_max": rep["detj_max"], "oracle_J": J_o,
+            "oracle_mismatch": mis_o}
+    out["runs"] = runs
+    a = runs["f32_spectral"]
+    for k in ("f32_two-level", "f16_two-level"):
+        b = runs[k]
+        out["speedup_%s_vs_f32_spectral" % k] = a["time_to_tol_s"] / b["time_to_tol_s"]
+        out["oracle_J_rel_diff_%s" % k] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
+        out["oracle_mismatch_rel_diff_%s" % k] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / a["oracle_mismatch"]
     print(json.dumps(out))
 
 
@@ -883,6 +957,9 @@ def run_large_report(args):
 
 def main():
     args = parse_args()
+    if args.precond_report:
+        run_precond_report(args)
+        return
     if args.net_report:
         run_net_report(args)
         return

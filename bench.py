@@ -632,25 +632,45 @@ def run_precond_report(args):
         c.set_images(m0_d, m1_d)
     p = oracle.Params(nt=4, beta_v=args.beta, beta_w=1e-4)
     m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
-    runs = {}
-    for sto, pc in (("f32", "spectral"), ("f32", "two-level"), ("f16", "two-level")):
-        ctx = ctxs[sto]
-        ctx.set_opts(precond=claire.PRECOND_TWO_LEVEL if pc == "two-level" else claire.PRECOND_SPECTRAL)
-        for rep_i in range(2):  # warm-up, then timed
+    def solve(ctx, timing=0):
+        for _ in range(2):  # warm-up, then timed
             v = torch.zeros((3,) + grid, device=dev)
+            ctx.set_opts(timing=timing)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             status, rep = ctx.register(v)
             torch.cuda.synchronize()
             secs = time.perf_counter() - t0
+        ctx.set_opts(timing=0)
+        return secs, rep, v
+
+    runs = {}
+    # (storage, preconditioner, coarse ratio, inner tolerance)
+    for sto, pc, coarse, tol in (("f32", "spectral", 2, 0.1), ("f32", "two-level", 2, 0.1),
+                                 ("f16", "two-level", 2, 0.1), ("f32", "two-level", 4, 0.1),
+                                 ("f32", "two-level", 2, 0.2)):
+        ctx = ctxs[sto]
+        ctx.set_opts(precond=claire.PRECOND_TWO_LEVEL if pc == "two-level" else claire.PRECOND_SPECTRAL,
+                     pc_coarse=coarse, pc_tol=tol)
+        secs, rep, v = solve(ctx)
         J_o, mis_o, _ = oracle.objective(v.cpu().numpy().astype(np.float64), m0_64, m1_64, p)
-        runs["%s_%s" % (sto, pc)] = {
+        name = "%s_%s" % (sto, pc) + ("" if (coarse, tol) == (2, 0.1) else "_coarse%d_tol%g" % (coarse, tol))
+        runs[name] = {
             "time_to_tol_s": secs, "status": rep["status"], "gn_iters": rep["gn_iters"],
             "pcg_iters": rep["pcg_iters_total"], "pcg_per_gn": rep["pcg_iters"],
             "inner_pcg_iters": rep["pc_inner_iters_total"], "gnorm_rel": rep["gnorm_rel"], "J": rep["J"],
             "r": rep["r"], "detj_min": rep["detj_min"], "detj_max": rep["detj_max"], "oracle_J": J_o,
             "oracle_mismatch": mis_o}
     out["runs"] = runs
+    # phase split with per-launch CUDA-event timing (adds launch overhead)
+    phases = {}
+    for pc in ("spectral", "two-level"):
+        ctx = ctxs["f32"]
+        ctx.set_opts(precond=claire.PRECOND_TWO_LEVEL if pc == "two-level" else claire.PRECOND_SPECTRAL,
+                     pc_coarse=2, pc_tol=0.1)
+        secs, rep, _ = solve(ctx, timing=2)
+        phases[pc] = {"total_s": secs, **{k: v for k, v in rep["t_phase_s"].items()}}
+    out["phases_timed"] = phases
     a = runs["f32_spectral"]
     for k in ("f32_two-level", "f16_two-level"):
         b = runs[k]

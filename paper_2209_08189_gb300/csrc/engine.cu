@@ -62,7 +62,7 @@ struct EventPair {
 // Coarse-grid state of the two-level zero-velocity preconditioner (allocated
 // on first use): cuFFT plans of the coarse grid, the restricted mean state
 // gradient gbar, the inner PCG vectors in Fourier space and, for the flexible
-// outer PCG, two fine preconditioned residuals.
+// outer PCG, the fine preconditioned residual.
 struct TwoLevel {
     Grid g{};
     int factor = 0;
@@ -75,7 +75,7 @@ struct TwoLevel {
     float* real = nullptr;  // 3 Nc scratch
     cufftComplex *xh = nullptr, *rh = nullptr, *zh = nullptr, *ph = nullptr, *cp = nullptr, *q = nullptr,
                  *T = nullptr;  // 3 Mc each
-    cufftComplex* zf[2] = {nullptr, nullptr};  // 3 M each (fine)
+    cufftComplex* zf = nullptr;  // 3 M (fine): the stored preconditioned residual
     ~TwoLevel()
     {
         if (plans) {
@@ -867,7 +867,7 @@ claire_status tl_ensure(claire_ctx* c)
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t realb = up(3 * t->N * sizeof(float)), specb = up(3 * t->M * sizeof(cufftComplex)),
                  fineb = up(3 * c->M * sizeof(cufftComplex));
-    const size_t total = 2 * realb + 7 * specb + 2 * fineb;
+    const size_t total = 2 * realb + 7 * specb + fineb;
     if (cudaMalloc(&t->block, total) != cudaSuccess) {
         cudaGetLastError();
         t->block = nullptr;
@@ -882,8 +882,7 @@ claire_status tl_ensure(claire_ctx* c)
         *q = reinterpret_cast<cufftComplex*>(b);
         b += specb;
     }
-    t->zf[0] = reinterpret_cast<cufftComplex*>(b); b += fineb;
-    t->zf[1] = reinterpret_cast<cufftComplex*>(b);
+    t->zf = reinterpret_cast<cufftComplex*>(b);
     size_t ws1 = 0, ws2 = 0;
     cufftResult fr = cufftCreate(&t->r2c);
     if (fr == CUFFT_SUCCESS) {
@@ -1052,12 +1051,12 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         CL_CUDA(c, cudaMemsetAsync(c->x, 0, 3 * c->N * sizeof(float), c->stream));
         return CLAIRE_OK;
     }
-    // two-level: z~ = P^{-1} r~ is stored (zf[cur]) and the direction update is
+    // two-level: z~ = P^{-1} r~ is stored (zf) and the direction update is
     // the flexible one, beta = <r_new, z_new - z_old> / <r_old, z_old>
-    int cur = 0, inner_its = 0;
+    int inner_its = 0;
     if (two_level) {
         double ro;
-        CL_TRY(tl_apply(c, c->rh, c->tl2->zf[0], nullptr, &rz, &ro, &inner_its));
+        CL_TRY(tl_apply(c, c->rh, c->tl2->zf, nullptr, &rz, &ro, &inner_its));
     }
     double beta = 0.0;
     for (int it = 1; it <= c->o.max_pcg; ++it) {
@@ -1067,7 +1066,7 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
             {
                 KTimer t(c, KK_SPECTRAL, (it == 1 ? 72.0 : 96.0) * M, 0);
                 if (two_level)
-                    launch_dir_stored(c->grid, c->tl2->zf[cur], c->phat, c->spec2, c->M, static_cast<float>(beta),
+                    launch_dir_stored(c->grid, c->tl2->zf, c->phat, c->spec2, c->M, static_cast<float>(beta),
                                       it == 1 ? 1 : 0, c->stream);
                 else
                     launch_spectral_direction(c->grid, c->rh, c->phat, c->spec2, c->M, static_cast<float>(beta),
@@ -1100,18 +1099,20 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         {
             PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
             KTimer t(c, KK_SPECTRAL, 144.0 * M, 0, 3);
-            launch_fs_update(c->grid, c->spec, c->phat, c->xh, c->rh, c->M, static_cast<float>(alpha), op,
-                             c->rp, c->partials, c->partials + c->red_blocks, c->red_blocks, c->stream);
+            launch_fs_update(c->grid, c->spec, c->phat, c->xh, c->rh, two_level ? c->tl2->zf : nullptr, c->M,
+                             static_cast<float>(alpha), op, c->rp, c->partials, c->partials + c->red_blocks,
+                             c->red_blocks, c->stream);
         }
         CL_TRY(fs_sums(c, 2));
         const double rr = c->hres[0];
         if (!c->o.pcg_fixed && std::sqrt(rr) <= eta * r0) break;
         if (it == c->o.max_pcg) break;
         if (two_level) {
-            double rz_new, ro;
-            CL_TRY(tl_apply(c, c->rh, c->tl2->zf[1 - cur], c->tl2->zf[cur], &rz_new, &ro, &inner_its));
+            // <r_new, z_old> = <r_old, z_old> - alpha <H p, z_old>; z_new overwrites z_old
+            const double ro = rz - alpha * c->hres[1];
+            double rz_new, unused;
+            CL_TRY(tl_apply(c, c->rh, c->tl2->zf, nullptr, &rz_new, &unused, &inner_its));
             beta = (rz_new - ro) / rz;
-            cur = 1 - cur;
             rz = rz_new;
         } else {
             beta = c->hres[1] / rz;
@@ -1418,8 +1419,8 @@ claire_status claire_precond(claire_ctx* c, const float* r, float* z)
         CL_LAUNCHED(c);
         double rz, ro;
         int its;
-        CL_TRY(tl_apply(c, c->rh, c->tl2->zf[0], nullptr, &rz, &ro, &its));
-        CL_FFT(c, cufftExecC2R(c->c2r, c->tl2->zf[0], c->r));
+        CL_TRY(tl_apply(c, c->rh, c->tl2->zf, nullptr, &rz, &ro, &its));
+        CL_FFT(c, cufftExecC2R(c->c2r, c->tl2->zf, c->r));
     } else {
         CL_TRY(precond(c, dr, c->r));
     }

@@ -166,8 +166,8 @@ void launch_fs_start(const Grid& g, cufftComplex* spec, cufftComplex* rh, cufftC
 void launch_fs_hp(const Grid& g, cufftComplex* spec, const cufftComplex* spec2, const cufftComplex* ph,
                   size_t cs, int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st);
 void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph, cufftComplex* xh,
-                      cufftComplex* rh, size_t cs, float alpha, SpectralOp op, RegParams rp, double* prr,
-                      double* prz, int nblocks, cudaStream_t st);
+                      cufftComplex* rh, const cufftComplex* zc, size_t cs, float alpha, SpectralOp op, RegParams rp,
+                      double* prr, double* prz, int nblocks, cudaStream_t st);
 
 // Deterministic FP64 reductions: partial sums per block, then a one-block
 // final sum in fixed order.  `partials` holds at least nblocks doubles.

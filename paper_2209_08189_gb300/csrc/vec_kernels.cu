@@ -286,12 +286,14 @@ __global__ void __launch_bounds__(kThreads) k_fs_hp(Grid g, float2* __restrict__
 }
 
 // x~ += alpha p~, r~ -= alpha H p~ (H p~ in spec); partials of |r~|^2 and
-// <r~, z~> with z~ = M r~ (recomputed by the next direction kernel).
+// <r~, z~> with z~ = M r~ (recomputed by the next direction kernel), or, when
+// a stored preconditioned residual zc is given, of <H p~, zc> instead.
 __global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, const float2* __restrict__ spec,
                                                          const float2* __restrict__ ph,
                                                          float2* __restrict__ xh, float2* __restrict__ rh,
-                                                         size_t cs, float alpha, int op, RegParams rp,
-                                                         double* __restrict__ prr, double* __restrict__ prz)
+                                                         const float2* __restrict__ zc, size_t cs, float alpha,
+                                                         int op, RegParams rp, double* __restrict__ prr,
+                                                         double* __restrict__ prz)
 {
     const int n3h = g.n3 / 2 + 1;
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * n3h;
@@ -310,10 +312,15 @@ __global__ void __launch_bounds__(kThreads) k_fs_update(Grid g, const float2* __
             r[c] = rr;
         }
         const Mode m = mode_of(g, idx, n3h, rp);
-        float2 z0, z1, z2;
-        apply_inv(m, op, r[0], r[1], r[2], z0, z1, z2);
         arr += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], r[0], r[1], r[2]));
-        arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z0, z1, z2));
+        if (zc) {
+            arz += static_cast<double>(m.wt * cdot3(spec[idx], spec[cs + idx], spec[2 * cs + idx], zc[idx],
+                                                     zc[cs + idx], zc[2 * cs + idx]));
+        } else {
+            float2 z0, z1, z2;
+            apply_inv(m, op, r[0], r[1], r[2], z0, z1, z2);
+            arz += static_cast<double>(m.wt * cdot3(r[0], r[1], r[2], z0, z1, z2));
+        }
     }
     block_sum2(arr, arz, prr, prz);
 }
@@ -828,13 +835,14 @@ void launch_fs_hp(const Grid& g, cufftComplex* spec, const cufftComplex* spec2, 
 }
 
 void launch_fs_update(const Grid& g, cufftComplex* spec, const cufftComplex* ph, cufftComplex* xh,
-                      cufftComplex* rh, size_t cs, float alpha, SpectralOp op, RegParams rp, double* prr,
-                      double* prz, int nblocks, cudaStream_t st)
+                      cufftComplex* rh, const cufftComplex* zc, size_t cs, float alpha, SpectralOp op, RegParams rp,
+                      double* prr, double* prz, int nblocks, cudaStream_t st)
 {
     k_fs_update<<<nblocks, kThreads, 0, st>>>(g, reinterpret_cast<const float2*>(spec),
                                               reinterpret_cast<const float2*>(ph),
                                               reinterpret_cast<float2*>(xh), reinterpret_cast<float2*>(rh),
-                                              cs, alpha, static_cast<int>(op), rp, prr, prz);
+                                              reinterpret_cast<const float2*>(zc), cs, alpha, static_cast<int>(op),
+                                              rp, prr, prz);
 }
 
 void launch_mean_levels(const void* m, int nt, float w_end, float w_mid, size_t N, float* out, Storage sto,

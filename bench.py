@@ -65,6 +65,8 @@ def parse_args():
                          "learned warm start, both without stored state gradients; Dice on 3 labels; the same "
                          "registration on images sampled to 256^3 and 512^3; sampled oracle parity")
     ap.add_argument("--large-n", type=int, default=1024)
+    ap.add_argument("--large-precond", default="spectral", choices=["spectral", "two-level"],
+                    help="preconditioner of the mixed + learned run of --large-report")
     ap.add_argument("--large-vmax", type=float, default=0.5,
                     help="max |v*| of the large case (0.5: CFL 20 at 1024^3, nt=4)")
     ap.add_argument("--net-report", action="store_true",
@@ -811,8 +813,11 @@ def run_large_report(args):
     # oracle parity, registrations of sampled images; device tensors are kept
     # few because the context takes most of the memory
     ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                         storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200)
+                         storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200,
+                         precond=claire.PRECOND_TWO_LEVEL if args.large_precond == "two-level"
+                         else claire.PRECOND_SPECTRAL)
     out["fp16_lowmem_device_gb"] = used_gb()
+    out["learned_run_precond"] = args.large_precond
     vstar = torch.empty((3,) + grid, device=dev)
     claire.claire_resample(torch.from_numpy(v64).to(dev), (64, 64, 64), vstar, grid, 3, claire.RESAMPLE_SPECTRAL,
                            st)
@@ -873,6 +878,7 @@ def run_large_report(args):
     torch.cuda.synchronize()
     runs["fp16_learned"] = {"time_to_tol_s": time.perf_counter() - t0, "predict_and_g0_s": t_pred,
                             "status": rep["status"], "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+                            "inner_pcg_iters": rep["pc_inner_iters_total"],
                             "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
                             "detj_max": rep["detj_max"], "cfl": rep["cfl"], "mismatch_at_guess": mis_guess,
                             "peak_device_gb": used_gb()}

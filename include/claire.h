@@ -115,6 +115,8 @@ typedef struct claire_opts {
                             linearisation point (Sec. 2.2), inverted on a coarse grid by an inner
                             PCG, with S^{-1} on the remaining (high) modes and the identity on k = 0;
                             the outer PCG then takes the flexible (Polak-Ribiere) direction update.
+                            A Gauss-Newton step whose two-level solve fails the Armijo line search is
+                            solved again with S^{-1} (claire_report.pc_fallbacks).
                             Its coarse-grid buffers (about 3 fine spectra) are allocated on first use. */
     int pc_coarse;       /* fine-to-coarse ratio of the two-level grid: every N_i / pc_coarse must be
                             even and >= 4; default 2 */
@@ -161,6 +163,8 @@ typedef struct claire_report {
     double interp_points;       /* grid points x scalar fields interpolated by the gathers */
     double interp_bytes;        /* algorithmic HBM bytes of the gather kernels (each value once) */
     int pc_inner_iters_total;   /* inner PCG iterations of the two-level preconditioner (0 otherwise) */
+    int pc_fallbacks;           /* Gauss-Newton steps whose two-level solve failed the line search and
+                                   were solved again with the spectral preconditioner */
 } claire_report;
 
 /* Fill *opts with the defaults listed above.  Returns CLAIRE_EINVAL on NULL. */

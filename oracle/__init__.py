@@ -34,7 +34,7 @@ from __future__ import annotations
 
 import ctypes
 import math
-from dataclasses import dataclass, field
+from dataclasses import dataclass, field, replace
 
 import numpy as np
 
@@ -475,6 +475,8 @@ def precond(r, p: Params):
 #   means the inverse of Q H0c Q.
 # * The outer PCG takes the flexible (Polak-Ribiere) direction update when
 #   this inexact preconditioner is in use.
+# * Safeguard (ours): a Gauss-Newton step whose two-level solve fails the
+#   Armijo line search is solved again with S^{-1}.
 
 def mean_state_gradient(st: State):
     """gbar = sum_j w_j grad m^j (trapezoid weights of the solves)."""
@@ -638,7 +640,7 @@ def register(m0, m1, p: Params, v0=None, mode=None, log=None):
     g = gradient(st, mode)
     g0 = math.sqrt(inner(g, g, n))
     rep = {"gn_iters": 0, "pcg_iters": [], "alpha": [], "J": [st.J], "gnorm_rel": [1.0],
-           "status": "not_converged", "g0": g0, "pc_inner_iters": 0}
+           "status": "not_converged", "g0": g0, "pc_inner_iters": 0, "pc_fallbacks": 0}
     inner_its = []
     if g0 == 0.0:
         rep["status"] = "converged"
@@ -649,16 +651,31 @@ def register(m0, m1, p: Params, v0=None, mode=None, log=None):
             rep["status"] = "converged"
             break
         eta = min(p.pcg_rtol_max, math.sqrt(rel))
-        vt, its = pcg(st, -g, eta, p.max_pcg, mode, fixed_iters=p.pcg_fixed, stats=inner_its)
-        rep["pc_inner_iters"] = sum(inner_its)
-        gtv = inner(g, vt, n)
-        alpha, ok = 1.0, False
-        for _ls in range(p.max_ls):
-            Jt, _, _ = objective(v + alpha * vt, m0, m1, p)
-            if Jt <= st.J + p.armijo_c1 * alpha * gtv:
-                ok = True
+        ok, its_step = False, 0
+        # a step whose two-level solve fails the line search is solved again
+        # with the spectral preconditioner (once)
+        for attempt in range(2):
+            if attempt == 1:
+                if p.precond != "2l":
+                    break
+                rep["pc_fallbacks"] = rep.get("pc_fallbacks", 0) + 1
+                st_solve = State(v, m0, m1, replace(p, precond="spectral"))
+            else:
+                st_solve = st
+            vt, its = pcg(st_solve, -g, eta, p.max_pcg, mode, fixed_iters=p.pcg_fixed, stats=inner_its)
+            its_step += its
+            rep["pc_inner_iters"] = sum(inner_its)
+            gtv = inner(g, vt, n)
+            alpha = 1.0
+            for _ls in range(p.max_ls):
+                Jt, _, _ = objective(v + alpha * vt, m0, m1, p)
+                if Jt <= st.J + p.armijo_c1 * alpha * gtv:
+                    ok = True
+                    break
+                alpha *= 0.5
+            if ok:
                 break
-            alpha *= 0.5
+        its = its_step
         rep["pcg_iters"].append(its)
         if not ok:
             rep["status"] = "line_search_failed"

@@ -60,7 +60,8 @@ class claire_report(ctypes.Structure):
                 ("detj_max", ctypes.c_double), ("cfl", ctypes.c_double),
                 ("t_total_s", ctypes.c_double), ("t_phase_s", ctypes.c_double * 8),
                 ("gather_launches", ctypes.c_double), ("interp_points", ctypes.c_double),
-                ("interp_bytes", ctypes.c_double), ("pc_inner_iters_total", ctypes.c_int)]
+                ("interp_bytes", ctypes.c_double), ("pc_inner_iters_total", ctypes.c_int),
+                ("pc_fallbacks", ctypes.c_int)]
 
     def as_dict(self):
         n = min(self.gn_iters, MAX_LOGGED_STEPS)
@@ -74,7 +75,8 @@ class claire_report(ctypes.Structure):
                 "t_total_s": self.t_total_s,
                 "t_phase_s": {k: self.t_phase_s[i] for i, k in enumerate(PHASES)},
                 "gather_launches": self.gather_launches, "interp_points": self.interp_points,
-                "interp_bytes": self.interp_bytes, "pc_inner_iters_total": self.pc_inner_iters_total}
+                "interp_bytes": self.interp_bytes, "pc_inner_iters_total": self.pc_inner_iters_total,
+                "pc_fallbacks": self.pc_fallbacks}
 
 
 class claire_kernel_stat(ctypes.Structure):
@@ -263,10 +265,12 @@ def claire_precond(ctx, r, z):
     return _check(ctx, lib().claire_precond(ctx, _ptr(r), _ptr(z)))
 
 
-def claire_register(ctx, v_inout):
+def claire_register(ctx, v_inout, check=True):
+    """check=False returns a failure status (with the report of the run) instead of raising."""
     rep = claire_report()
     st = lib().claire_register(ctx, _ptr(v_inout), ctypes.byref(rep))
-    _check(ctx, st)
+    if check:
+        _check(ctx, st)
     return st, rep
 
 
@@ -468,8 +472,8 @@ class Context:
     def precond(self, r, z):
         claire_precond(self.handle, r, z)
 
-    def register(self, v_inout):
-        st, rep = claire_register(self.handle, v_inout)
+    def register(self, v_inout, check=True):
+        st, rep = claire_register(self.handle, v_inout, check)
         return st, rep.as_dict()
 
     def transport(self, v, m_in, m_out, flags=TRANSPORT_FWD):

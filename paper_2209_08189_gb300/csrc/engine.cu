@@ -1471,28 +1471,44 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
             break;
         }
         const double eta = std::min(c->o.pcg_rtol_max, std::sqrt(rel));
-        int its = 0;
-        CL_TRY(pcg(c, eta, &its));
-        if (k < CLAIRE_MAX_LOGGED_STEPS) R.pcg_iters[k] = its;
-        R.pcg_iters_total += its;
-        double gtx;
-        CL_TRY(dot(c, c->g, c->x, n3, &gtx));
         double alpha = 1.0;
         bool ok = false;
-        for (int ls = 0; ls < c->o.max_ls; ++ls) {
-            {
-                PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
-                KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
-                launch_xpay(c->v, static_cast<float>(alpha), c->x, c->p, n3, c->stream);
-                CL_LAUNCHED(c);
+        // a step whose two-level solve fails the line search is solved again with
+        // the spectral preconditioner (once per step)
+        for (int attempt = 0; attempt < 2 && !ok; ++attempt) {
+            const bool spectral_retry = attempt == 1;
+            if (spectral_retry) {
+                if (c->o.precond != CLAIRE_PRECOND_TWO_LEVEL) break;
+                ++R.pc_fallbacks;
+                // the trials overwrote the state characteristic and states: linearise again at v
+                CL_TRY(linearise(c, c->v));
+                CL_TRY(gradient_at_lin(c, c->g));
+                c->o.precond = CLAIRE_PRECOND_SPECTRAL;
             }
-            double Jt;
-            CL_TRY(objective_at(c, c->p, &Jt, nullptr, true));
-            if (Jt <= c->J_lin + c->o.armijo_c1 * alpha * gtx) {
-                ok = true;
-                break;
+            int its = 0;
+            const claire_status ps = pcg(c, eta, &its);
+            if (spectral_retry) c->o.precond = CLAIRE_PRECOND_TWO_LEVEL;
+            CL_TRY(ps);
+            if (k < CLAIRE_MAX_LOGGED_STEPS) R.pcg_iters[k] += its;
+            R.pcg_iters_total += its;
+            double gtx;
+            CL_TRY(dot(c, c->g, c->x, n3, &gtx));
+            alpha = 1.0;
+            for (int ls = 0; ls < c->o.max_ls; ++ls) {
+                {
+                    PhaseScope pv(c, CLAIRE_PHASE_VECTOR);
+                    KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
+                    launch_xpay(c->v, static_cast<float>(alpha), c->x, c->p, n3, c->stream);
+                    CL_LAUNCHED(c);
+                }
+                double Jt;
+                CL_TRY(objective_at(c, c->p, &Jt, nullptr, true));
+                if (Jt <= c->J_lin + c->o.armijo_c1 * alpha * gtx) {
+                    ok = true;
+                    break;
+                }
+                alpha *= 0.5;
             }
-            alpha *= 0.5;
         }
         if (!ok) {
             st = CLAIRE_ELINESEARCH;

@@ -25,7 +25,7 @@ inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
 // The three velocity gathers at the predictor point are served from a
 // shared-memory box per 4 x 8 x 32 tile (one box, staged once per component;
 // the predictor points of a tile share its bounds).
-template <int ORDER>
+template <int ORDER, bool FULL>
 __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     k_backtrace_tiled(Grid g, const float* __restrict__ v, const float* __restrict__ vc, float dt, float sign,
                       float* __restrict__ d)
@@ -38,7 +38,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     const int j = blockIdx.y * TILE2 + warp;
     const int i0 = blockIdx.z * TILE1;
     const size_t N = g.N;
-    const bool col_ok = (k < g.n3) && (j < g.n2);
+    const bool col_ok = FULL || ((k < g.n3) && (j < g.n2));
     const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
     const float sdt = sign * dt;
     float u1[TILE1], u2[TILE1], u3[TILE1];
@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
 #pragma unroll
     for (int q = 0; q < TILE1; ++q) {
         u1[q] = u2[q] = u3[q] = 0.0f;
-        if (col_ok && i0 + q < g.n1) {
+        if (FULL || (col_ok && i0 + q < g.n1)) {
             const uint32_t p = p0 + q * g.n23;
             u1[q] = __ldg(v + p) * g.ih1;
             u2[q] = __ldg(v + N + p) * g.ih2;
@@ -75,7 +75,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
 #pragma unroll
         for (int q = 0; q < TILE1; ++q) {
             const int i = i0 + q;
-            if (!(col_ok && i < g.n1)) continue;
+            if (!(FULL || (col_ok && i < g.n1))) continue;
             const float vsq = use_box
                                   ? tile_eval<ORDER>(box, bp, i, j, k, -sdt * u1[q], -sdt * u2[q], -sdt * u3[q])
                                   : gather_global<ORDER, float>(g, f, i, j, k, -sdt * u1[q], -sdt * u2[q],
@@ -87,14 +87,24 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     }
 }
 
+template <int ORDER, bool FULL>
+void launch_backtrace_tiled_as(const Grid& g, const float* v, const float* vc, float dt, float sign, float* d,
+                               cudaStream_t st)
+{
+    if (kTiledSmemBytes > 48 * 1024)
+        cudaFuncSetAttribute(k_backtrace_tiled<ORDER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             static_cast<int>(kTiledSmemBytes));
+    k_backtrace_tiled<ORDER, FULL><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, v, vc, dt, sign, d);
+}
+
 template <int ORDER>
 void launch_backtrace_tiled(const Grid& g, const float* v, const float* vc, float dt, float sign, float* d,
                             cudaStream_t st)
 {
-    if (kTiledSmemBytes > 48 * 1024)
-        cudaFuncSetAttribute(k_backtrace_tiled<ORDER>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kTiledSmemBytes));
-    k_backtrace_tiled<ORDER><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, v, vc, dt, sign, d);
+    if (tiles_cover_grid(g))
+        launch_backtrace_tiled_as<ORDER, true>(g, v, vc, dt, sign, d, st);
+    else
+        launch_backtrace_tiled_as<ORDER, false>(g, v, vc, dt, sign, d, st);
 }
 
 // Sources of the incremental state for every time level at once:

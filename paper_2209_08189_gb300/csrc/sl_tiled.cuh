@@ -364,7 +364,9 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
 // x1/x2 displacement) read 32 different banks.  The epilogue's operands are
 // requested (prefetch) while the box is in flight and consumed (finish) after
 // the stencil is evaluated.
-template <int ORDER, class Epi, class S>
+// FULL: the tiles cover the grid exactly (n3 % 32 = n2 % 8 = n1 % TILE1 = 0),
+// so no point of a tile is out of range and the bounds tests compile away.
+template <int ORDER, class Epi, class S, bool FULL>
 __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     k_gather_tiled(Grid g, const S* __restrict__ f, const float* __restrict__ d, Epi epi)
 {
@@ -376,14 +378,15 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     const int j = blockIdx.y * TILE2 + warp;
     const int i0 = blockIdx.z * TILE1;
     const size_t N = g.N;
-    const bool col_ok = (k < g.n3) && (j < g.n2);
+    const bool col_ok = FULL || ((k < g.n3) && (j < g.n2));
     const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
+    auto valid = [&](int q) { return FULL || (col_ok && i0 + q < g.n1); };
 
     float d1[TILE1], d2[TILE1], d3[TILE1];
     int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
 #pragma unroll
     for (int q = 0; q < TILE1; ++q) {
-        if (col_ok && i0 + q < g.n1) {
+        if (valid(q)) {
             const uint32_t p = p0 + q * g.n23;
             d1[q] = __ldg(d + p);
             d2[q] = __ldg(d + N + p);
@@ -398,25 +401,37 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
         }
     }
     const BoxPar bp = tile_box<ORDER, sizeof(S)>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
-    const bool use_box = bp.E1 != 0;
-    if (use_box) tile_load_box<S>(g, f, box, bp, lane, warp);
+    if (bp.E1 == 0) {
+        // the tile's box does not fit: gather it from global memory (kept out
+        // of the shared-memory path, which then has no call in its loop)
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q) {
+            if (!valid(q)) continue;
+            const uint32_t p = p0 + q * g.n23;
+            const typename Epi::Pre pr = epi.prefetch(p);
+            epi.finish(p, gather_global<ORDER, S>(g, f, i0 + q, j, k, d1[q], d2[q], d3[q]), pr);
+        }
+        return;
+    }
+    tile_load_box<S>(g, f, box, bp, lane, warp);
     // epilogue operands of every point are requested while the box is in flight
     typename Epi::Pre pre[TILE1];
 #pragma unroll
     for (int q = 0; q < TILE1; ++q)
-        if (col_ok && i0 + q < g.n1) pre[q] = epi.prefetch(p0 + q * g.n23);
-    if (use_box) {
-        cp_async_wait_all();
-        __syncthreads();
-    }
+        if (valid(q)) pre[q] = epi.prefetch(p0 + q * g.n23);
+    cp_async_wait_all();
+    __syncthreads();
 #pragma unroll
     for (int q = 0; q < TILE1; ++q) {
-        const int i = i0 + q;
-        if (!(col_ok && i < g.n1)) continue;
-        const float val = use_box ? tile_eval<ORDER>(box, bp, i, j, k, d1[q], d2[q], d3[q])
-                                  : gather_global<ORDER, S>(g, f, i, j, k, d1[q], d2[q], d3[q]);
+        if (!valid(q)) continue;
+        const float val = tile_eval<ORDER>(box, bp, i0 + q, j, k, d1[q], d2[q], d3[q]);
         epi.finish(p0 + q * g.n23, val, pre[q]);
     }
+}
+
+inline bool tiles_cover_grid(const Grid& g)
+{
+    return g.n3 % TILE3 == 0 && g.n2 % TILE2 == 0 && g.n1 % TILE1 == 0;
 }
 
 inline dim3 tiled_grid(const Grid& g)
@@ -429,10 +444,17 @@ constexpr size_t kTiledSmemBytes = kBoxCapFloats * sizeof(float);
 template <int ORDER, class Epi, class S>
 inline void launch_tiled(const Grid& g, const S* f, const float* d, const Epi& e, cudaStream_t st)
 {
-    if (kTiledSmemBytes > 48 * 1024)
-        cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(kTiledSmemBytes));
-    k_gather_tiled<ORDER, Epi, S><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
+    if (tiles_cover_grid(g)) {
+        if (kTiledSmemBytes > 48 * 1024)
+            cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kTiledSmemBytes));
+        k_gather_tiled<ORDER, Epi, S, true><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
+    } else {
+        if (kTiledSmemBytes > 48 * 1024)
+            cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kTiledSmemBytes));
+        k_gather_tiled<ORDER, Epi, S, false><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e);
+    }
 }
 
 // ---- epilogues: prefetch(p) loads the point's operands early, finish(p, v, pre)

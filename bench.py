@@ -147,8 +147,10 @@ class ClockSampler:
     def __init__(self, index):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", "clocks_rank%d.csv" % index) \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else "/tmp/claire_clocks_%d.csv" % index
+        # the raw samples go to $CLAIRE_CLOCKS_DIR when set, else the temporary directory
+        import tempfile
+        self.path = os.path.join(os.environ.get("CLAIRE_CLOCKS_DIR") or tempfile.gettempdir(),
+                                 "claire_clocks_rank%d.csv" % index)
 
     def start(self):
         try:

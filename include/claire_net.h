@@ -5,7 +5,7 @@
  * a coarser-grid solution.  This part adds a small 3D convolutional network
  * (a U-Net over periodic volumes) that maps an image pair (m0, m1) to an
  * initial velocity; Gauss-Newton-Krylov from that guess remains the solver
- * and the judge of its error.  The paper has no network: these entry points
+ * and corrects whatever error the guess has.  The paper has no network: these entry points
  * are building blocks of that extension, with no counterpart in it.
  *
  * Conventions, for every entry point below:

@@ -110,7 +110,11 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
         // holds at least one valid point
         long long o3 = (long long)a3 - OFF;
         long long e3 = (long long)z3 - a3 + M;
-        if (ES == 2) {  // even x3 origin and extent: 4-byte aligned 16-bit pairs
+        if (ES == 2 && (g.n3 & 7) == 0) {  // x3 origin and extent multiples of 8: 16-byte chunks of halves
+            const long long o3e = o3 & ~7LL;
+            e3 = (e3 + (o3 - o3e) + 7) & ~7LL;
+            o3 = o3e;
+        } else if (ES == 2) {  // even x3 origin and extent: 4-byte aligned 16-bit pairs
             const long long o3e = o3 & ~1LL;
             e3 = (e3 + (o3 - o3e) + 1) & ~1LL;
             o3 = o3e;
@@ -212,6 +216,32 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
         const int rows = bp.E1 * bp.E2;
         const int pairs = bp.E3 / 2;
         uint32_t* stage = reinterpret_cast<uint32_t*>(box + rows * bp.S3);
+        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+            // 16-byte chunks of 8 values (no chunk straddles the x3 wrap), 16 threads per row
+            const int nch = bp.E3 >> 3;
+            const int ch0 = threadIdx.x & 15;
+            int r = threadIdx.x >> 4;
+            int a = r / bp.E2, b = r - a * bp.E2;
+            for (; r < rows; r += kTileThreads / 16) {
+                int gi = w1 + a;
+                gi = gi >= g.n1 ? gi - g.n1 : gi;
+                int gj = w2 + b;
+                gj = gj >= g.n2 ? gj - g.n2 : gj;
+                const S* src = f + static_cast<size_t>(gi) * g.n23 + static_cast<size_t>(gj) * g.n3;
+                const unsigned dst = static_cast<unsigned>(__cvta_generic_to_shared(stage + r * (bp.S3 / 2)));
+                for (int c = ch0; c < nch; c += 16) {
+                    int gk = w3 + 8 * c;
+                    gk = gk >= g.n3 ? gk - g.n3 : gk;
+                    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst + 16u * c), "l"(src + gk)
+                                 : "memory");
+                }
+                b += kTileThreads / 16;
+                while (b >= bp.E2) {
+                    b -= bp.E2;
+                    ++a;
+                }
+            }
+        } else {
         for (int a = 0; a < bp.E1; ++a) {
             int gi = w1 + a;
             gi = gi >= g.n1 ? gi - g.n1 : gi;
@@ -227,6 +257,7 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
                     cp_async_f32(reinterpret_cast<float*>(dst + c), reinterpret_cast<const float*>(src + gk));
                 }
             }
+        }
         }
         cp_async_wait_all();
         __syncthreads();

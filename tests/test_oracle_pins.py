@@ -826,3 +826,29 @@ def test_two_level_registration_takes_fewer_iterations():
     assert res["2l"]["gn_iters"] <= res["spectral"]["gn_iters"]
     assert res["2l"]["pc_inner_iters"] > 0
     assert abs(res["2l"]["J"][-1] - res["spectral"]["J"][-1]) < 0.01 * res["spectral"]["J"][-1]
+
+
+def test_two_level_step_falls_back_to_spectral_when_the_line_search_fails(monkeypatch):
+    """Safeguard of the two-level solver: a Gauss-Newton step whose two-level
+    direction fails every Armijo trial is solved again with S^{-1}.  The
+    failure is planted in the oracle: the objective reports +inf for every
+    trial of the first step's two-level direction."""
+    g = (16, 16, 16)
+    m0 = synth.label_template(g, seed=0)
+    vs = synth.bandlimited_velocity(g, seed=0, kmax=2, vmax=0.8)
+    p = oracle.Params(beta_v=1e-2, gtol=5e-2, max_gn=3, max_pcg=20, precond="2l")
+    m1 = oracle.transport(m0, vs, p)
+    real_objective = oracle.objective
+    calls = {"n": 0}
+
+    def planted(v, a, b, q):
+        calls["n"] += 1
+        if calls["n"] <= q.max_ls:  # every trial of the first (two-level) direction
+            return math.inf, math.inf, math.inf
+        return real_objective(v, a, b, q)
+
+    monkeypatch.setattr(oracle, "objective", planted)
+    _, rep = oracle.register(m0, m1, p)
+    assert rep["pc_fallbacks"] == 1
+    assert rep["gn_iters"] >= 1 and rep["status"] != "line_search_failed"
+    assert rep["J"][1] < rep["J"][0]

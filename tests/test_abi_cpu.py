@@ -163,3 +163,31 @@ def test_create_fails_loudly_without_gpu(claire):
     with pytest.raises(claire.ClaireError) as e:
         claire.claire_create((8, 8, 8), 1e-2, 4)
     assert e.value.status == -3
+
+
+def test_wgrad_chunk_counts_are_consistent(claire):
+    """Host-side tiling of the weight gradient (no GPU needed): every shape gets
+    at least one chunk and no more chunks than bricks; a forced input-channel
+    block that does not divide Cin leaves the shape to the mma.sync kernel (whose
+    chunking differs); an invalid block is rejected."""
+    from paper_2209_08189_gb300 import net
+    lib = net.lib()
+    shapes = [(16, 16, (4, 128, 128, 128)), (48, 16, (4, 128, 128, 128)), (96, 32, (4, 64, 64, 64)),
+              (192, 64, (4, 32, 32, 32)), (128, 128, (4, 16, 16, 16)), (32, 48, (2, 4, 16, 16)),
+              (32, 48, (2, 8, 8, 16))]
+    for ci, co, vol in shapes:
+        c = net.wgrad_chunks(ci, co, vol)
+        B, D, H, W = vol
+        bricks = B * D * (H // 16) * (W // 8) if H % 16 == 0 and W % 8 == 0 else B * D * H * W // 64
+        assert 1 <= c <= max(1, bricks), (ci, co, vol, c)
+    base = net.wgrad_chunks(96, 32, (4, 64, 64, 64))
+    try:
+        for nc in (16, 32, 48):
+            net.set_wgrad_tiling(nc)
+            assert net.wgrad_chunks(96, 32, (4, 64, 64, 64)) >= 1
+        net.set_wgrad_tiling(64)  # 96 % 64 != 0: the mma.sync kernel's chunking
+        assert net.wgrad_chunks(96, 32, (4, 64, 64, 64)) >= 1
+    finally:
+        net.set_wgrad_tiling(0)
+    assert net.wgrad_chunks(96, 32, (4, 64, 64, 64)) == base
+    assert lib.claire_net_set_wgrad_tiling(40) == -1

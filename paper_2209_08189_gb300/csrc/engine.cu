@@ -1355,10 +1355,10 @@ claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
         CL_CUDA(c, cudaMemcpyAsync(c->m1, m1, N * sizeof(float), cudaMemcpyDefault, c->stream));
     } else {
         // FP32 input (host or device) converted to the storage type on the device
-        const float* d0;
+        const float* d0 = nullptr;
         CL_TRY(device_input(c, m0, N, c->p, &d0));
         launch_to_storage(d0, c->m0, N, c->sto, c->stream);
-        const float* d1;
+        const float* d1 = nullptr;
         CL_TRY(device_input(c, m1, N, c->z, &d1));
         launch_to_storage(d1, c->m1, N, c->sto, c->stream);
         CL_LAUNCHED(c);
@@ -1372,7 +1372,7 @@ claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
 claire_status claire_objective(claire_ctx* c, const float* v, double* J, double* mismatch)
 {
     if (!c) return CLAIRE_EINVAL;
-    const float* dv;
+    const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->p, &dv));
     claire_status s = objective_at(c, dv, J, mismatch);
     collect_timing(c);
@@ -1384,7 +1384,7 @@ claire_status claire_gradient(claire_ctx* c, const float* v, float* g, double* J
     if (!c) return CLAIRE_EINVAL;
     if (!v || !g) return fail(c, CLAIRE_EINVAL, "null argument");
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
-    const float* dv;
+    const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->v, &dv));
     CL_TRY(linearise(c, dv));
     CL_TRY(gradient_at_lin(c, c->g));
@@ -1398,7 +1398,7 @@ claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt)
 {
     if (!c) return CLAIRE_EINVAL;
     if (!vt || !Hvt) return fail(c, CLAIRE_EINVAL, "null argument");
-    const float* dvt;
+    const float* dvt = nullptr;
     CL_TRY(device_input(c, vt, 3 * c->N, c->p, &dvt));
     CL_TRY(matvec(c, dvt, c->r));
     CL_TRY(copy_out(c, Hvt, c->r, 3 * c->N));
@@ -1410,7 +1410,7 @@ claire_status claire_precond(claire_ctx* c, const float* r, float* z)
 {
     if (!c) return CLAIRE_EINVAL;
     if (!r || !z) return fail(c, CLAIRE_EINVAL, "null argument");
-    const float* dr;
+    const float* dr = nullptr;
     CL_TRY(device_input(c, r, 3 * c->N, c->p, &dr));
     if (c->o.precond == CLAIRE_PRECOND_TWO_LEVEL) {
         CL_TRY(tl_prepare(c));
@@ -1574,7 +1574,7 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
     if (flags != CLAIRE_TRANSPORT_FWD && flags != CLAIRE_TRANSPORT_ADJ)
         return fail(c, CLAIRE_EINVAL, "unknown transport flags %d", flags);
     const size_t N = c->N;
-    const float* dv;
+    const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * N, c->p, &dv));
     // the user-facing transport runs in FP32 whatever the context's storage
     const float* src;
@@ -1657,7 +1657,7 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
     }
     c->have_lin = false;  // the work vectors below are shared with the solver
     // FP32 inputs on the device: v -> g, m0 -> states[0], gbar -> r (first N)
-    const float* dv;
+    const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * N, c->g, &dv));
     CL_CUDA(c, cudaMemcpyAsync(c->vjp_states, m0, N * sizeof(float), cudaMemcpyDefault, c->stream));
     float* d = c->z;                 // characteristic X (grid units)
@@ -1714,7 +1714,7 @@ claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
 {
     if (!c) return CLAIRE_EINVAL;
     if (!v || !lo || !hi) return fail(c, CLAIRE_EINVAL, "null argument");
-    const float* dv;
+    const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->x, &dv));
     CL_TRY(detj_of(c, dv, lo, hi));
     collect_timing(c);

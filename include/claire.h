@@ -30,6 +30,14 @@
  *  - Errors: every entry point returns a claire_status and never throws.  A
  *    negative status leaves outputs unspecified; claire_last_error() gives a
  *    one-line message.  A context is not thread-safe: use one per host thread.
+ *  - Velocity screen: claire_objective, claire_gradient, claire_register,
+ *    claire_transport, claire_transport_vjp, claire_detj and
+ *    claire_backtrace first reduce max |v(x)| in FP64 and return
+ *    CLAIRE_ENONFINITE, before any gather runs, when a component is NaN or
+ *    Inf.  The gathers themselves send a tile whose displacement is
+ *    non-finite or 2^20 cells or more to a global-memory path whose indices
+ *    are clamped and wrapped (the result there is NaN or meaningless, never
+ *    an out-of-range access).
  *  - There is no CPU fallback: without a usable CUDA device, claire_create
  *    returns CLAIRE_ECUDA.
  */
@@ -344,7 +352,9 @@ claire_status claire_dot(claire_ctx* ctx, const float* x, const float* y, size_t
  * Calls share the array and overwrite the slots they use: calls whose work
  * overlaps on the GPU (other streams or host threads) race and must be
  * serialised by the caller.  Synchronises `stream` before returning.
- * Returns CLAIRE_EINVAL for null or host input pointers, CLAIRE_ECUDA on a
+ * x and y must be memory of the current device (or managed memory): the
+ * kernels run on the current device.  Returns CLAIRE_EINVAL for null or host
+ * input pointers and for device memory of another GPU, CLAIRE_ECUDA on a
  * CUDA error.
  */
 claire_status claire_dot_noalloc(const float* x, const float* y, size_t n, double scale,

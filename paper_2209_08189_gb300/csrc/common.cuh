@@ -19,22 +19,30 @@ struct Grid {
     float ih1, ih2, ih3;  // n_c / (2 pi)
 };
 
-__device__ __forceinline__ int wrap_index(int x, int n)
+__host__ __device__ __forceinline__ int wrap_index(int x, int n)
 {
     int r = x % n;
     return r < 0 ? r + n : r;
 }
 
+// Largest displacement magnitude (grid cells) the index arithmetic takes as is.
+constexpr float kDispLimit = 1048576.0f;  // 2^20
+
 // Split a grid-unit displacement into its integer cell offset and fraction
-// t in [0,1).  The offset is clamped so that index arithmetic cannot
-// overflow for absurd inputs (the wrapped index then stays in range).
-__device__ __forceinline__ int split_disp(float d, float& t)
+// t in [0,1).  The offset is clamped to [-2^20, 2^20] so that index
+// arithmetic cannot overflow for absurd inputs (the wrapped index then stays
+// in range); a NaN becomes -2^20 with a NaN fraction.
+__host__ __device__ __forceinline__ int split_disp(float d, float& t)
 {
     float fl = floorf(d);
     t = d - fl;
-    fl = fminf(fmaxf(fl, -1048576.0f), 1048576.0f);
+    fl = fminf(fmaxf(fl, -kDispLimit), kDispLimit);
     return static_cast<int>(fl);
 }
+
+// True when d is finite and |d| < 2^20, i.e. when split_disp does not clamp
+// and a plain floor gives the same cell (false for NaN and +-Inf).
+__host__ __device__ __forceinline__ bool disp_ok(float d) { return fabsf(d) < kDispLimit; }
 
 // Cubic Lagrange cardinal functions on the nodes -1, 0, 1, 2 at t in [0,1).
 __device__ __forceinline__ void cubic_weights(float t, float w[4])

@@ -832,6 +832,16 @@ claire_status cfl_of(claire_ctx* c, const float* v, double* cfl)
     return CLAIRE_OK;
 }
 
+// Reject a velocity (device, 3N) with a non-finite component before any
+// gather runs on it: the FP64 maximum of |v(x)|^2 keeps a NaN or an Inf.
+claire_status screen_velocity(claire_ctx* c, const float* v)
+{
+    double cfl;
+    CL_TRY(cfl_of(c, v, &cfl));
+    if (!std::isfinite(cfl)) return fail(c, CLAIRE_ENONFINITE, "non-finite velocity");
+    return CLAIRE_OK;
+}
+
 // Final sums of the two partial-sum arrays of a Fourier-space PCG kernel
 // into dres[0], dres[1] (scaled to discrete inner products), then synchronise.
 claire_status fs_sums(claire_ctx* c, int count)
@@ -1374,6 +1384,7 @@ claire_status claire_objective(claire_ctx* c, const float* v, double* J, double*
     if (!c) return CLAIRE_EINVAL;
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->p, &dv));
+    CL_TRY(screen_velocity(c, dv));
     claire_status s = objective_at(c, dv, J, mismatch);
     collect_timing(c);
     return s;
@@ -1386,6 +1397,7 @@ claire_status claire_gradient(claire_ctx* c, const float* v, float* g, double* J
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->v, &dv));
+    CL_TRY(screen_velocity(c, dv));
     CL_TRY(linearise(c, dv));
     CL_TRY(gradient_at_lin(c, c->g));
     if (J) *J = c->J_lin;
@@ -1446,6 +1458,7 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
     const long long pc_inner0 = c->pc_inner_total;
 
     CL_CUDA(c, cudaMemcpyAsync(c->v, v_inout, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
+    CL_TRY(screen_velocity(c, c->v));
     claire_status st = CLAIRE_ENOTCONVERGED;
     auto elapsed = [&]() {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1576,6 +1589,7 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
     const size_t N = c->N;
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * N, c->p, &dv));
+    CL_TRY(screen_velocity(c, dv));
     // the user-facing transport runs in FP32 whatever the context's storage
     const float* src;
     CL_TRY(device_input(c, m_in, N, reinterpret_cast<float*>(c->l0), &src));
@@ -1659,6 +1673,7 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
     // FP32 inputs on the device: v -> g, m0 -> states[0], gbar -> r (first N)
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * N, c->g, &dv));
+    CL_TRY(screen_velocity(c, dv));
     CL_CUDA(c, cudaMemcpyAsync(c->vjp_states, m0, N * sizeof(float), cudaMemcpyDefault, c->stream));
     float* d = c->z;                 // characteristic X (grid units)
     float* dbar = c->x;              // cotangent of the displacement
@@ -1716,6 +1731,7 @@ claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
     if (!v || !lo || !hi) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->x, &dv));
+    CL_TRY(screen_velocity(c, dv));
     CL_TRY(detj_of(c, dv, lo, hi));
     collect_timing(c);
     return CLAIRE_OK;
@@ -1745,6 +1761,7 @@ claire_status claire_backtrace(claire_ctx* c, const float* v, float* d, int dire
     if (direction != 1 && direction != -1) return fail(c, CLAIRE_EINVAL, "direction must be +1 or -1");
     CL_TRY(check_kernel_ptr(c, v));
     CL_TRY(check_kernel_ptr(c, d));
+    CL_TRY(screen_velocity(c, v));
     CL_TRY(backtrace(c, v, d, direction));
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
     collect_timing(c);

@@ -38,13 +38,20 @@ __device__ __forceinline__ void block_sum(double x, double* out)
     }
 }
 
+// min / max that keep a NaN operand (fmin / fmax return the other operand),
+// so that a NaN anywhere in a reduction reaches its result
+__device__ __forceinline__ double min_nan(double a, double b) { return (a != a || b != b) ? a + b : fmin(a, b); }
+__device__ __forceinline__ double max_nan(double a, double b) { return (a != a || b != b) ? a + b : fmax(a, b); }
+
+// Block minimum of lo and maximum of hi into pmin / pmax[blockIdx.x]; a NaN
+// in either propagates to that result.
 __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin, double* pmax)
 {
     __shared__ double slo[32], shi[32];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) {
-        lo = fmin(lo, __shfl_down_sync(0xffffffffu, lo, o));
-        hi = fmax(hi, __shfl_down_sync(0xffffffffu, hi, o));
+        lo = min_nan(lo, __shfl_down_sync(0xffffffffu, lo, o));
+        hi = max_nan(hi, __shfl_down_sync(0xffffffffu, hi, o));
     }
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
     if (lane == 0) {
@@ -58,8 +65,8 @@ __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin,
         double b = lane < nw ? shi[lane] : -1e300;
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) {
-            a = fmin(a, __shfl_down_sync(0xffffffffu, a, o));
-            b = fmax(b, __shfl_down_sync(0xffffffffu, b, o));
+            a = min_nan(a, __shfl_down_sync(0xffffffffu, a, o));
+            b = max_nan(b, __shfl_down_sync(0xffffffffu, b, o));
         }
         if (lane == 0) {
             pmin[blockIdx.x] = a;

@@ -43,6 +43,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     const float sdt = sign * dt;
     float u1[TILE1], u2[TILE1], u3[TILE1];
     int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < TILE1; ++q) {
         u1[q] = u2[q] = u3[q] = 0.0f;
@@ -51,16 +52,14 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
             u1[q] = __ldg(v + p) * g.ih1;
             u2[q] = __ldg(v + N + p) * g.ih2;
             u3[q] = __ldg(v + 2 * N + p) * g.ih3;
-            float t;
-            const int b1 = i0 + q + split_disp(-sdt * u1[q], t);
-            const int b2 = j + split_disp(-sdt * u2[q], t);
-            const int b3 = k + split_disp(-sdt * u3[q], t);
-            lo1 = min(lo1, b1); hi1 = max(hi1, b1);
-            lo2 = min(lo2, b2); hi2 = max(hi2, b2);
-            lo3 = min(lo3, b3); hi3 = max(hi3, b3);
+            bounds_add(i0 + q, -sdt * u1[q], lo1, hi1, bad);
+            bounds_add(j, -sdt * u2[q], lo2, hi2, bad);
+            bounds_add(k, -sdt * u3[q], lo3, hi3, bad);
         }
     }
-    const BoxPar bp = tile_box<ORDER, 4>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
+    // a non-finite or huge predictor displacement sends the tile to the
+    // global-memory gather (clamped split, indices always in range)
+    const BoxPar bp = tile_box<ORDER, 4>(g, lo1, lo2, lo3, hi1, hi2, hi3, bad, red, par, lane, warp);
     const bool use_box = bp.E1 != 0;
     const float cc = -0.5f * sdt;
 #pragma unroll
@@ -338,12 +337,8 @@ __global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* _
         const double det = F[0][0] * (F[1][1] * F[2][2] - F[1][2] * F[2][1]) -
                            F[0][1] * (F[1][0] * F[2][2] - F[1][2] * F[2][0]) +
                            F[0][2] * (F[1][0] * F[2][1] - F[1][1] * F[2][0]);
-        lo = fmin(lo, det);
-        hi = fmax(hi, det);
-        if (det != det) {  // NaN propagates as NaN in both
-            lo = det;
-            hi = det;
-        }
+        lo = min_nan(lo, det);  // a NaN propagates to both extrema
+        hi = max_nan(hi, det);
     }
     block_minmax(lo, hi, pmin, pmax);
 }

@@ -78,16 +78,70 @@ struct BoxPar {
     int S3;          // row stride, a multiple of 32
 };
 
-// Block-wide bounds of the stencils whose first-node cells (before the
-// -OFF shift) span [lo, hi] per axis; thread 0 publishes the box in par.
+// Box geometry from the bounds [a, z] (per axis) of the first-node cells
+// (before the -OFF shift) of a tile's stencils: par[0..2] the first node
+// (unwrapped grid coordinates), par[3..5] the extents and par[6] the row
+// stride, with par[3..6] = 0 when the box does not fit the shared-memory cap
+// or the grid, or when `bad` says that a displacement of the tile failed
+// disp_ok (non-finite or at least 2^20 cells).  Such a tile is gathered from
+// global memory with the clamped split, whose indices always wrap into range.
 // ES: bytes per stored value of the field (4, or 2 for FP16 / BF16 storage,
 // whose box is staged as raw 16-bit pairs before widening to FP32).
 template <int ORDER, int ES = 4>
-__device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
-                                           int hi3, int (*red)[TILE2], int* par, int lane, int warp)
+__host__ __device__ __forceinline__ void box_geometry(const Grid& g, int a1, int a2, int a3, int z1, int z2, int z3,
+                                                      bool bad, int par[7])
 {
     constexpr int M = Scheme<ORDER>::M;
     constexpr int OFF = Scheme<ORDER>::OFF;
+    // box of the stencils: cells [a - OFF, z - OFF + M); the tile always
+    // holds at least one valid point
+    long long o3 = (long long)a3 - OFF;
+    long long e3 = (long long)z3 - a3 + M;
+    if (ES == 2 && (g.n3 & 7) == 0) {  // x3 origin and extent multiples of 8: 16-byte chunks of halves
+        const long long o3e = o3 & ~7LL;
+        e3 = (e3 + (o3 - o3e) + 7) & ~7LL;
+        o3 = o3e;
+    } else if (ES == 2) {  // even x3 origin and extent: 4-byte aligned 16-bit pairs
+        const long long o3e = o3 & ~1LL;
+        e3 = (e3 + (o3 - o3e) + 1) & ~1LL;
+        o3 = o3e;
+    } else if ((g.n3 & 3) == 0) {  // x3 origin and extent multiples of 4: 16-byte row chunks
+        const long long o3e = o3 & ~3LL;
+        e3 = (e3 + (o3 - o3e) + 3) & ~3LL;
+        o3 = o3e;
+    }
+    const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M;
+    const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
+    // FP32 box plus, for 16-bit storage, the staging copy (half its size)
+    const long long need = e1 * e2 * s3 * (ES == 2 ? 3 : 2) / 2;
+    const bool fits = !bad && e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && need <= kBoxCapFloats;
+    par[0] = fits ? a1 - OFF : 0;
+    par[1] = fits ? a2 - OFF : 0;
+    par[2] = fits ? static_cast<int>(o3) : 0;
+    par[3] = static_cast<int>(fits ? e1 : 0);
+    par[4] = static_cast<int>(fits ? e2 : 0);
+    par[5] = static_cast<int>(fits ? e3 : 0);
+    par[6] = static_cast<int>(fits ? s3 : 0);
+}
+
+// Fold one point's displacement (grid units) along an axis into the tile's
+// bounds of first-node cells; `bad` records a displacement that fails disp_ok.
+__host__ __device__ __forceinline__ void bounds_add(int node, float d, int& lo, int& hi, bool& bad)
+{
+    float t;
+    const int b = node + split_disp(d, t);
+    lo = lo < b ? lo : b;
+    hi = hi > b ? hi : b;
+    bad = bad || !disp_ok(d);
+}
+
+#ifdef __CUDACC__
+// Block-wide bounds of the stencils whose first-node cells span [lo, hi] per
+// axis, and the vote on `bad` (any thread); thread 0 publishes the box in par.
+template <int ORDER, int ES = 4>
+__device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
+                                           int hi3, bool bad, int (*red)[TILE2], int* par, int lane, int warp)
+{
     lo1 = __reduce_min_sync(0xffffffffu, lo1);
     lo2 = __reduce_min_sync(0xffffffffu, lo2);
     lo3 = __reduce_min_sync(0xffffffffu, lo3);
@@ -98,7 +152,7 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
         red[0][warp] = lo1; red[1][warp] = lo2; red[2][warp] = lo3;
         red[3][warp] = hi1; red[4][warp] = hi2; red[5][warp] = hi3;
     }
-    __syncthreads();
+    const bool any_bad = __syncthreads_or(bad) != 0;
     if (threadIdx.x == 0) {
         int a1 = INT_MAX, a2 = INT_MAX, a3 = INT_MAX, z1 = INT_MIN, z2 = INT_MIN, z3 = INT_MIN;
 #pragma unroll
@@ -106,33 +160,7 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
             a1 = min(a1, red[0][w]); a2 = min(a2, red[1][w]); a3 = min(a3, red[2][w]);
             z1 = max(z1, red[3][w]); z2 = max(z2, red[4][w]); z3 = max(z3, red[5][w]);
         }
-        // box of the stencils: cells [a - OFF, z - OFF + M); the tile always
-        // holds at least one valid point
-        long long o3 = (long long)a3 - OFF;
-        long long e3 = (long long)z3 - a3 + M;
-        if (ES == 2 && (g.n3 & 7) == 0) {  // x3 origin and extent multiples of 8: 16-byte chunks of halves
-            const long long o3e = o3 & ~7LL;
-            e3 = (e3 + (o3 - o3e) + 7) & ~7LL;
-            o3 = o3e;
-        } else if (ES == 2) {  // even x3 origin and extent: 4-byte aligned 16-bit pairs
-            const long long o3e = o3 & ~1LL;
-            e3 = (e3 + (o3 - o3e) + 1) & ~1LL;
-            o3 = o3e;
-        } else if ((g.n3 & 3) == 0) {  // x3 origin and extent multiples of 4: 16-byte row chunks
-            const long long o3e = o3 & ~3LL;
-            e3 = (e3 + (o3 - o3e) + 3) & ~3LL;
-            o3 = o3e;
-        }
-        const long long e1 = (long long)z1 - a1 + M, e2 = (long long)z2 - a2 + M;
-        const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
-        // FP32 box plus, for 16-bit storage, the staging copy (half its size)
-        const long long need = e1 * e2 * s3 * (ES == 2 ? 3 : 2) / 2;
-        const bool fits = e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && need <= kBoxCapFloats;
-        par[0] = a1 - OFF; par[1] = a2 - OFF; par[2] = static_cast<int>(o3);
-        par[3] = static_cast<int>(fits ? e1 : 0);
-        par[4] = static_cast<int>(fits ? e2 : 0);
-        par[5] = static_cast<int>(fits ? e3 : 0);
-        par[6] = static_cast<int>(fits ? s3 : 0);
+        box_geometry<ORDER, ES>(g, a1, a2, a3, z1, z2, z3, any_bad, par);
     }
     __syncthreads();
     BoxPar b;
@@ -140,6 +168,7 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
     b.E1 = par[3]; b.E2 = par[4]; b.E3 = par[5]; b.S3 = par[6];
     return b;
 }
+#endif
 
 // Copy the (periodically wrapped) box of f into shared memory as FP32:
 // asynchronously (cp.async) for FP32 storage, converting loads otherwise.
@@ -305,14 +334,30 @@ __device__ __forceinline__ float row_dot(uint32_t addr, const float w[4])
     }
 }
 
-// Stencil value at node (i, j, k) + (d1, d2, d3) from the box in shared memory.
-// Split of a displacement known to be finite and within the box (the bounds
-// pass already clamped every value of the tile): floor and fraction.
-__device__ __forceinline__ int split_in_box(float d, float& t)
+// Split of a displacement inside a fitting box: floor and fraction.  Every
+// displacement of a tile whose box fits passed disp_ok (finite, |d| < 2^20),
+// where this floor equals the clamped split of the bounds pass.
+__host__ __device__ __forceinline__ int split_in_box(float d, float& t)
 {
+#ifdef __CUDA_ARCH__
     const int fl = __float2int_rd(d);
+#else
+    const int fl = static_cast<int>(floorf(d));
+#endif
     t = d - static_cast<float>(fl);
     return fl;
+}
+
+// Offset in the box (floats) of the first stencil node of the point
+// (i, j, k) + (d1, d2, d3), and the three fractions.
+template <int ORDER>
+__host__ __device__ __forceinline__ int tile_offset(const BoxPar& bp, int i, int j, int k, float d1, float d2,
+                                                    float d3, float& t1, float& t2, float& t3)
+{
+    constexpr int OFF = Scheme<ORDER>::OFF;
+    const int P = bp.E2 * bp.S3;
+    return (i + split_in_box(d1, t1) - OFF - bp.O1) * P + (j + split_in_box(d2, t2) - OFF - bp.O2) * bp.S3 +
+           (k + split_in_box(d3, t3) - OFF - bp.O3);
 }
 
 template <int ORDER>
@@ -320,12 +365,9 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
                                            float d2, float d3)
 {
     constexpr int M = Scheme<ORDER>::M;
-    constexpr int OFF = Scheme<ORDER>::OFF;
     const int P = bp.E2 * bp.S3;
     float t1, t2, t3, w1[4], w2[4], w3[4];
-    const int o = (i + split_in_box(d1, t1) - OFF - bp.O1) * P +
-                  (j + split_in_box(d2, t2) - OFF - bp.O2) * bp.S3 +
-                  (k + split_in_box(d3, t3) - OFF - bp.O3);
+    const int o = tile_offset<ORDER>(bp, i, j, k, d1, d2, d3, t1, t2, t3);
     axis_weights<ORDER>(t1, w1);
     axis_weights<ORDER>(t2, w2);
     axis_weights<ORDER>(t3, w3);
@@ -415,6 +457,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
 
     float d1[TILE1], d2[TILE1], d3[TILE1];
     int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+    bool bad = false;
 #pragma unroll
     for (int q = 0; q < TILE1; ++q) {
         if (valid(q)) {
@@ -422,16 +465,12 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
             d1[q] = __ldg(d + p);
             d2[q] = __ldg(d + N + p);
             d3[q] = __ldg(d + 2 * N + p);
-            float t;
-            const int b1 = i0 + q + split_disp(d1[q], t);
-            const int b2 = j + split_disp(d2[q], t);
-            const int b3 = k + split_disp(d3[q], t);
-            lo1 = min(lo1, b1); hi1 = max(hi1, b1);
-            lo2 = min(lo2, b2); hi2 = max(hi2, b2);
-            lo3 = min(lo3, b3); hi3 = max(hi3, b3);
+            bounds_add(i0 + q, d1[q], lo1, hi1, bad);
+            bounds_add(j, d2[q], lo2, hi2, bad);
+            bounds_add(k, d3[q], lo3, hi3, bad);
         }
     }
-    const BoxPar bp = tile_box<ORDER, sizeof(S)>(g, lo1, lo2, lo3, hi1, hi2, hi3, red, par, lane, warp);
+    const BoxPar bp = tile_box<ORDER, sizeof(S)>(g, lo1, lo2, lo3, hi1, hi2, hi3, bad, red, par, lane, warp);
     if (bp.E1 == 0) {
         // the tile's box does not fit: gather it from global memory (kept out
         // of the shared-memory path, which then has no call in its loop)

@@ -390,7 +390,7 @@ __global__ void __launch_bounds__(kThreads) k_maxnorm3_partial(const float* __re
     for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < N; i += stride) {
         const double a = v[i], b = v[N + i], c = v[2 * N + i];
         const double s = a * a + b * b + c * c;
-        hi = (s != s) ? s : fmax(hi, s);
+        hi = max_nan(hi, s);  // a NaN component makes the result NaN
     }
     block_minmax(hi, hi, partials + gridDim.x, partials);
 }
@@ -412,8 +412,8 @@ __global__ void __launch_bounds__(kThreads) k_final_minmax(const double* __restr
     for (int i = threadIdx.x; i < nb; i += kThreads) {
         const double a = pmin ? pmin[i] : lo;
         const double b = pmax[i];
-        lo = (a != a) ? a : fmin(lo, a);
-        hi = (b != b) ? b : fmax(hi, b);
+        lo = min_nan(lo, a);
+        hi = max_nan(hi, b);
     }
     block_minmax(lo, hi, out2, out2 + 1);
 }

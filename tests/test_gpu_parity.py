@@ -59,7 +59,11 @@ def make_ctx(claire, torch, n, beta_v=1e-2, nt=4, **opts):
     return claire.Context(n, beta_v, nt, stream=torch.cuda.current_stream().cuda_stream, **opts)
 
 
-SHAPES = [(32, 32, 32), (40, 36, 30), (16, 24, 8)]  # (40,36,30): N = 43200, ragged last block
+# (40,36,30): N = 43200, ragged last block.  Along x3 a tile's departure box
+# (32 columns plus the stencil and the spread) is wider than these three grids,
+# so they run the global-memory path of the tiled gathers; (70,44,104) is ragged
+# along every axis (partial tiles) and wide enough for the shared-memory box.
+SHAPES = [(32, 32, 32), (40, 36, 30), (16, 24, 8), (70, 44, 104)]
 
 
 def _disp(n, seed, cfl):
@@ -350,6 +354,42 @@ def test_state_errors_and_failure_detection(env):
     assert e.value.status == -1  # kernel-level entry points reject host pointers
 
 
+def test_nonfinite_velocity_screened_before_any_gather(env):
+    """A NaN or Inf in the velocity is rejected (CLAIRE_ENONFINITE) by the FP64
+    max-norm screen before any backtrace or SL gather is launched (failure made
+    on the host: the bad value is planted in the input array)."""
+    torch, claire = env
+    n = (16, 16, 16)
+    m0, m1, vs, v, p = _problem(n)
+    ctx = make_ctx(claire, torch, n)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    gathers = ("sl_interp", "sl_backtrace_rk2", "sl_adjoint_step", "sl_incremental_step",
+               "sl_incremental_last", "sl_map_step")
+
+    def launched():
+        return {k["name"]: k["launches"] for k in ctx.kernel_stats() if k["name"] in gathers}
+
+    out = torch.empty((3,) + n, device="cuda")
+    for bad_value in (np.nan, np.inf, -np.inf):
+        bad = v.copy()
+        bad[1, 5, 6, 7] = bad_value
+        before = launched()
+        for call in (lambda: ctx.register(dev(torch, bad)),
+                     lambda: ctx.gradient(dev(torch, bad), out),
+                     lambda: ctx.objective(dev(torch, bad)),
+                     lambda: ctx.transport(dev(torch, bad), dev(torch, m0), out[0]),
+                     lambda: ctx.transport_vjp(dev(torch, bad), dev(torch, m0), dev(torch, m1), gm0=out[0]),
+                     lambda: ctx.detj(dev(torch, bad)),
+                     lambda: ctx.backtrace(dev(torch, bad), out, 1)):
+            with pytest.raises(claire.ClaireError) as e:
+                call()
+            assert e.value.status == -5
+        assert launched() == before
+    # the context stays usable
+    st, rep = ctx.register(torch.zeros((3,) + n, device="cuda"), check=False)
+    assert st >= 0 and math.isfinite(rep["J"])
+
+
 def test_wall_clock_limit(env):
     torch, claire = env
     n = (32, 32, 32)
@@ -395,6 +435,10 @@ def test_registration_fixed_schedule_parity(env, config1_oracle):
     assert rep["alpha"] == rep_ref["alpha"]
     assert rel_l2(host(v), v_ref) <= 1e-3
     assert abs(rep["r"] - rep_ref["r"]) <= 0.01 * rep_ref["r"]
+    # the reported CFL of the returned velocity is the oracle's definition
+    # (max |v(x)|_2 dt / min h) on the same FP32 values; the GPU takes h in FP32
+    c_ref = oracle.cfl(host(v), p)
+    assert abs(rep["cfl"] - c_ref) <= 1e-6 * c_ref
 
 
 def test_registration_free_running_and_host_pointers(env):

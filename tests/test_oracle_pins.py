@@ -349,6 +349,47 @@ def test_K_limits_and_identity():
     assert _rel(lhs, rhs) < 1e-12
 
 
+def test_k_form_preconditioner_single_modes():
+    """Preconditioner of the paper's gradient form (grad_form = 1): on
+    v = e_c cos(k.x) it divides by beta_v |k|^2 (H1) or beta_v |k|^4 (H2),
+    whatever the direction of e_c relative to k and whatever beta_w; the k = 0
+    mode passes unchanged.  Returning S^{-1} instead would divide the
+    longitudinal part by beta_v |k|^2 + beta_w (1 + |k|^2) |k|^2."""
+    n = (16, 12, 10)
+    X = _xyz(n)
+    k = np.array([2.0, -3.0, 1.0])
+    ph = k[0] * X[0] + k[1] * X[1] + k[2] * X[2]
+    kk = float(k @ k)
+    for reg, sym in ((1, kk), (2, kk * kk)):
+        p = oracle.Params(beta_v=0.05, beta_w=0.4, reg=reg, grad_form=1)
+        for e in (np.array([1.0, 0, 0]), k / math.sqrt(kk), np.array([3.0, 2.0, 0.0]) / math.sqrt(13.0)):
+            v = e[:, None, None, None] * np.cos(ph)[None]
+            assert np.max(np.abs(oracle.precond(v, p) - v / (p.beta_v * sym))) < 1e-12
+        const = np.ones((3,) + n) * np.array([0.7, -1.1, 0.2])[:, None, None, None]
+        assert np.max(np.abs(oracle.precond(const, p) - const)) < 1e-13
+    # the exact form's S^{-1} differs on the longitudinal mode when beta_w > 0
+    p0 = oracle.Params(beta_v=0.05, beta_w=0.4, grad_form=0)
+    vl = (k / math.sqrt(kk))[:, None, None, None] * np.cos(ph)[None]
+    expect0 = vl / (p0.beta_v * kk + p0.beta_w * (1 + kk) * kk)
+    assert np.max(np.abs(oracle.precond(vl, p0) - expect0)) < 1e-12
+
+
+def test_k_form_preconditioner_inverts_K_S():
+    """K S = beta_v A, so the K-form preconditioner applied to K(S x) gives x
+    back up to its mean (k = 0 is not inverted), for H1 and H2, and with
+    beta_w = 0 (K = I) it inverts S itself."""
+    n = (8, 10, 6)
+    rng = np.random.default_rng(12)
+    x = rng.standard_normal((3,) + n)
+    xm = x - x.mean(axis=(1, 2, 3), keepdims=True)
+    for reg in (1, 2):
+        p = oracle.Params(beta_v=0.03, beta_w=0.6, reg=reg, grad_form=1)
+        y = oracle.precond(oracle.project_K(oracle.reg_apply(x, p), p), p)
+        assert _rel(y, xm) < 1e-12
+        p0 = oracle.Params(beta_v=0.03, beta_w=0.0, reg=reg, grad_form=1)
+        assert _rel(oracle.precond(oracle.reg_apply(x, p0), p0), xm) < 1e-12
+
+
 # ---------------------------------------------------------------------------
 # Semi-Lagrangian solves (Eqs. (1b)-(1c), (4))
 # ---------------------------------------------------------------------------
@@ -617,15 +658,32 @@ def test_detj_closed_forms():
     assert 3.0 < errs[0] / errs[1] < 5.5, errs
 
 
-def test_cfl_consistency_with_paper_example():
-    """CFL scales as 1/n_t: the paper's 15.66 at n_t = 4 implies about 4 at n_t = 16."""
-    ex = GOLD["paper_cfl_example"]
+def test_cfl_scales_with_time_step():
+    """CFL = max |v|_2 dt / min h is proportional to dt = 1/n_t."""
     n = (32, 32, 32)
     v = synth.mode_velocity(n, seed=0, vmax=0.5)
     c4 = oracle.cfl(v, oracle.Params(nt=4))
     c16 = oracle.cfl(v, oracle.Params(nt=16))
     assert abs(c4 / c16 - 4.0) < 1e-12
-    assert abs(ex["cfl_nt4"] / 4.0 - ex["cfl_nt16"]) < 0.1
+
+
+def test_cfl_closed_forms_non_cubic_grid():
+    """CFL on a non-cubic grid, where the smallest and the largest spacing
+    differ: (i) a constant field gives |v|_2 dt / min h exactly; (ii) a field
+    whose largest Euclidean norm sits where no component is largest: a
+    largest-component reading, or the largest spacing, gives another value."""
+    n = (16, 24, 40)
+    hmin = 2 * math.pi / 40
+    p = oracle.Params(nt=4)
+    v = np.stack([np.full(n, 0.3), np.full(n, -0.4), np.full(n, 1.2)])
+    assert abs(oracle.cfl(v, p) - 1.3 * 0.25 / hmin) < 1e-12
+    w = np.zeros((3,) + n)
+    w[0, 2, 3, 4] = 1.0           # largest component, |w| = 1
+    w[:, 9, 1, 30] = (0.8, 0.8, 0.0)  # |w| = 0.8 sqrt 2 = 1.1314 > 1
+    expect = 0.8 * math.sqrt(2.0) * 0.25 / hmin
+    assert abs(oracle.cfl(w, p) - expect) < 1e-12
+    assert abs(1.0 * 0.25 / hmin - expect) > 0.1 * expect             # max-component reading
+    assert abs(0.8 * math.sqrt(2.0) * 0.25 / (2 * math.pi / 16) - expect) > 0.5 * expect  # largest h
 
 
 def test_generators_deterministic():

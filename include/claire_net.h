@@ -140,9 +140,25 @@ claire_status claire_net_set_conv_tiling(int bdc, int nstage);
  * other nc. */
 claire_status claire_net_set_wgrad_tiling(int nc);
 
-/* Number of tcgen05 completion waits that gave up since the last reset
- * (reset != 0 clears it).  Synchronises the device. */
+/* Number of tcgen05 CTAs whose bounded completion wait gave up since the
+ * last reset (reset != 0 clears it).  Synchronises the device.  A CTA that
+ * gives up agrees on it block-wide, writes no output, and releases its
+ * tensor memory only after a final commit shows that its MMAs have drained. */
 claire_status claire_net_device_errors(int* count, int reset);
+
+/* Failure-detection hook of the tcgen05 kernels (the paper has no
+ * counterpart; for tests).  spin_limit: polls of every bounded mbarrier wait
+ * (0 restores the default, 2^22).  stall != 0: every CTA of the tcgen05
+ * kernels launched afterwards first waits on a completion phase that nothing
+ * signals, before it stages data or issues an MMA; that wait runs out after
+ * spin_limit polls and the CTA gives up (counted by claire_net_device_errors,
+ * outputs unspecified) and returns with its tensor memory released.  stall = 0
+ * switches the hook off.  tmem_kept (nullable) receives the number of CTAs
+ * that gave up and could not confirm that their MMAs had drained, which
+ * therefore returned without releasing their tensor-memory columns (0 unless
+ * the tensor cores stop completing work).  Synchronises the device; call it
+ * only while no network kernel is running. */
+claire_status claire_net_set_wait_test(unsigned int spin_limit, int stall, int* tmem_kept);
 
 /* Message of the last failing claire_net_* call on this thread. */
 const char* claire_net_last_error(void);

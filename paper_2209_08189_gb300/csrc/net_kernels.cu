@@ -27,6 +27,7 @@
 #include <cstdio>
 #include <cstdarg>
 #include <algorithm>
+#include <mutex>
 
 namespace claire {
 namespace net {
@@ -242,11 +243,20 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d(const __nv_bfloat16* __
 constexpr int kTcBH = 16, kTcBW = 8;
 constexpr int kTcHaloH = kTcBH + 2, kTcHaloW = kTcBW + 2;
 constexpr int kTcPlaneSlots = kTcHaloH * kTcHaloW;  // 180 halo voxels per D plane
-constexpr uint32_t kTcSpinLimit = 1u << 22;
+constexpr uint32_t kTcSpinLimit = 1u << 22;  // default polls of a bounded mbarrier wait
 constexpr int kTcMaxSmem = 231424;  // dynamic shared memory per CTA: the 227 KB opt-in limit less 1 KB for the static part
 
-// set when an mbarrier wait of k_conv3d_tc gave up (read by claire_net_device_errors)
+// CTAs of the tcgen05 kernels whose bounded mbarrier wait gave up (read by
+// claire_net_device_errors)
 __device__ int g_tc_wait_errors = 0;
+// CTAs that gave up and whose MMAs did not drain either: they return without
+// tcgen05.dealloc (their columns may still be written); never seen in practice
+__device__ int g_tc_tmem_kept = 0;
+// polls of one bounded wait, and the failure-detection hook: when set, every
+// CTA first waits on a completion phase that nothing signals, before any MMA
+// is issued (set through claire_net_set_wait_test)
+__device__ uint32_t g_tc_spin_limit = kTcSpinLimit;
+__device__ int g_tc_test_stall = 0;
 
 __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
 {
@@ -258,7 +268,8 @@ __device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint
 
 __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
 {
-    for (uint32_t it = 0; it < kTcSpinLimit; ++it) {
+    const uint32_t limit = g_tc_spin_limit;
+    for (uint32_t it = 0; it < limit; ++it) {
         uint32_t done;
         asm volatile("{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
                      " selp.u32 %0, 1, 0, p;\n}\n"
@@ -268,6 +279,35 @@ __device__ __forceinline__ bool mbar_wait(uint32_t mbar, uint32_t parity)
         if (done) return true;
     }
     return false;
+}
+
+// After a give-up: thread `issuer` (the one that issued every MMA of the CTA)
+// commits to the fresh mbarrier `drain`, which then completes once all of its
+// earlier tcgen05 operations have; the block agrees on whether they did.  Only
+// then may the CTA release its TMEM columns.  Called by every thread.
+__device__ __forceinline__ bool tc_drain(uint32_t drain, bool issuer)
+{
+    bool ok = true;
+    if (issuer) {
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(drain)
+                     : "memory");
+        ok = mbar_wait(drain, 0);
+    }
+    return __syncthreads_and(ok) != 0;
+}
+
+// TMEM release at the end of a CTA: dealloc when the MMAs are known complete
+// (`release`), else count the columns kept.  Called by every thread.
+__device__ __forceinline__ void tc_release(uint32_t tmem, uint32_t cols, bool release)
+{
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    if (!release) {
+        if (threadIdx.x == 0) atomicAdd(&g_tc_tmem_kept, 1);
+        return;
+    }
+    if ((threadIdx.x >> 5) == 0)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(cols));
 }
 
 // 16 consecutive TMEM columns of this warp's 32 lanes (32x32b shape)
@@ -305,8 +345,9 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
                                                             TcShape sh, Vol v, int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char tc_smem[];
-    __shared__ __align__(8) uint64_t mbar;
+    __shared__ __align__(8) uint64_t mbar, drain;
     __shared__ uint32_t tmem_slot;
+    __shared__ int stall;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int bdc = sh.bdc;
     // brick origin
@@ -323,11 +364,20 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
                      "r"(sh.cols));
         asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
     }
-    if (tid == 0) asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
+    const uint32_t drain_s = smem_addr(&drain);
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(mbar_s), "r"(1));
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(drain_s), "r"(1));
+        stall = g_tc_test_stall;
+    }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    // failure-detection hook: a wait on phase 0 of mbar, which only the first
+    // commit would complete, before any MMA is issued (it runs out)
+    bool ok = true;
+    if (stall) ok = __syncthreads_and(mbar_wait(mbar_s, 0)) != 0;
     // instruction descriptor: D F32, A and B BF16, both K-major, N = Cout, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(Cout) >> 3) << 17) |
                            ((128u >> 4) << 24);
@@ -351,13 +401,13 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
         }
         cp_async_commit();
     };
-    bool ok = true;
-    issue(0, 0);
+    if (ok) issue(0, 0);
     for (int c = 0; c < nchunks && ok; ++c) {
         const int stg = sh.nstage == 2 ? (c & 1) : 0;
         // every completion phase is waited for exactly once and in order, so
-        // a parity wait never sees two outstanding phases
-        if (c >= 1) ok = mbar_wait(mbar_s, (c - 1) & 1);
+        // a parity wait never sees two outstanding phases; the block agrees on
+        // the outcome, so every thread takes the same barriers
+        if (c >= 1) ok = __syncthreads_and(mbar_wait(mbar_s, (c - 1) & 1)) != 0;
         if (!ok) break;
         if (sh.nstage == 2) {
             if (c + 1 < nchunks) {
@@ -395,11 +445,13 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
                          : "memory");
         }
     }
-    if (ok) ok = mbar_wait(mbar_s, (nchunks - 1) & 1);
+    if (ok) ok = __syncthreads_and(mbar_wait(mbar_s, (nchunks - 1) & 1)) != 0;
     asm volatile("tcgen05.fence::after_thread_sync;");
+    bool release = true;
     if (!ok) {
         cp_async_wait_group<0>();
-        if (lane == 0) atomicAdd(err, 1);
+        if (tid == 0) atomicAdd(err, 1);
+        release = tc_drain(drain_s, tid == 0);
     } else {
         // epilogue: warp w owns TMEM lanes 32w..32w+31 = rows m = 32w + lane of every plane
         const int m = 32 * warp + lane;
@@ -439,9 +491,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(sh.cols));
+    tc_release(tmem, sh.cols, release);
 }
 
 // tcgen05 weight gradient.  Per tap, dW[co][tap][ci] = sum_p dY[p][co] X[p + off(tap)][ci]:
@@ -502,9 +552,9 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
                                                          int* __restrict__ err)
 {
     extern __shared__ __align__(128) unsigned char wg_smem[];
-    __shared__ __align__(8) uint64_t full[3], empty[3];
+    __shared__ __align__(8) uint64_t full[3], empty[3], drain;
     __shared__ uint32_t tmem_slot;
-    __shared__ int failed;
+    __shared__ int failed, stall;
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     int bid = blockIdx.x;
     const int pc = bid % chunks; bid /= chunks;
@@ -539,12 +589,17 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&full[i])), "r"(kWgLoaders / S));
             asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&empty[i])), "r"(bias ? 2 : 1));
         }
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&drain)), "r"(1));
         failed = 0;
+        stall = g_tc_test_stall;
     }
     asm volatile("tcgen05.fence::before_thread_sync;");
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;");
     const uint32_t tmem = tmem_slot;
+    // failure-detection hook: a wait on phase 0 of drain, which nothing
+    // signals yet, before any load or MMA (it runs out; no role loop runs)
+    const bool stalled = stall && !__syncthreads_and(mbar_wait(smem_addr(&drain), 0));
     const int smid = wg.nsa == 3 ? 1 : 0;
     // bias warp: lane -> (8-channel block cb, voxel residue r of nres)
     const int nres = 32 / max(cbn, 1);
@@ -552,8 +607,10 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
     float bacc[8];
 #pragma unroll
     for (int i = 0; i < 8; ++i) bacc[i] = 0.f;
-    bool ok = true;
-    if (warp >= 2) {
+    bool ok = !stalled;
+    if (stalled) {
+        // no role runs
+    } else if (warp >= 2) {
         // ---- loaders: group g of kWgLoaders / S threads owns stage g and
         // stages bricks g, g + S, g + 2S, ... (S independent load chains) ----
         const int nl = kWgLoaders / S;
@@ -706,8 +763,11 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
         okw = mbar_wait(smem_addr(&empty[(nbr - 1) % S]), ((nbr - 1) / S) & 1);
     ok = __syncthreads_and(okw);
     asm volatile("tcgen05.fence::after_thread_sync;");
+    bool release = true;
     if (!ok) {
         if (tid == 0) atomicAdd(err, 1);
+        // tid 0 issued every MMA (and, with the stall hook, none)
+        release = tc_drain(smem_addr(&drain), tid == 0);
     } else if (nbr > 0) {
         // an M = 128 accumulator holds row m in lane m, an M = 64 one in lane
         // (m / 16) * 32 + m % 16; warps w and w + 4 share lane quadrant w % 4
@@ -757,9 +817,7 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
             }
         }
     }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(wg.cols));
+    tc_release(tmem, wg.cols, release);
 }
 
 // Wgrad partials: P[pc][co][tap][ci] = sum over the chunk's voxels p of
@@ -1164,6 +1222,28 @@ bool brick_for(int D, int H, int W, int* bd, int* bh, int* bw)
 // tiling forced by claire_net_set_conv_tiling (0 = automatic)
 int g_tc_force_bdc = 0, g_tc_force_nstage = 0;
 
+// The tcgen05 kernels need more than 48 KB of dynamic shared memory; the
+// attribute that allows it is per device, so it is set once on each device
+// (done[] indexed by device, under a lock).
+constexpr int kMaxDevices = 64;
+std::mutex g_attr_mutex;
+
+cudaError_t smem_attr_once(const void* kernel, bool (&done)[kMaxDevices])
+{
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kMaxDevices)
+        return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem);
+    std::lock_guard<std::mutex> lock(g_attr_mutex);
+    if (!done[dev]) {
+        e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem);
+        if (e != cudaSuccess) return e;
+        done[dev] = true;
+    }
+    return cudaSuccess;
+}
+
 bool tc_eligible(int Cin, int Cout, int D, int H, int W)
 {
     (void)D;
@@ -1212,12 +1292,9 @@ cudaError_t conv3d(const void* X, int Cxs, int Cin, const void* Wt, const float*
         sh.cols = 32;
         while (sh.cols < static_cast<uint32_t>(sh.bdc * sh.ccols)) sh.cols <<= 1;
         const size_t smem = static_cast<size_t>(sh.nstage) * sh.stage;
-        static bool attr_set = false;
-        if (!attr_set) {
-            cudaError_t e = cudaFuncSetAttribute(k_conv3d_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, kTcMaxSmem);
-            if (e != cudaSuccess) return e;
-            attr_set = true;
-        }
+        static bool attr_done[kMaxDevices] = {};
+        cudaError_t ea = smem_attr_once(reinterpret_cast<const void*>(k_conv3d_tc), attr_done);
+        if (ea != cudaSuccess) return ea;
         int* err = nullptr;
         cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tc_wait_errors);
         if (e != cudaSuccess) return e;
@@ -1355,13 +1432,9 @@ cudaError_t conv3d_wgrad(const void* X, int Cxs, int Cin, const void* dY, int Cy
         int nb, ch;
         if (wg_tc_shape(Cin, Cout, B, D, H, W, nsm, &g, &nb, &ch)) {
             if (ch != chunks) return cudaErrorInvalidValue;
-            static bool attr_set = false;
-            if (!attr_set) {
-                cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     kTcMaxSmem);
-                if (e != cudaSuccess) return e;
-                attr_set = true;
-            }
+            static bool attr_done[kMaxDevices] = {};
+            cudaError_t ea = smem_attr_once(reinterpret_cast<const void*>(k_wgrad_tc), attr_done);
+            if (ea != cudaSuccess) return ea;
             int* err = nullptr;
             cudaError_t e = cudaGetSymbolAddress(reinterpret_cast<void**>(&err), g_tc_wait_errors);
             if (e != cudaSuccess) return e;
@@ -1777,6 +1850,20 @@ extern "C" claire_status claire_net_device_errors(int* count, int reset)
     const int n = read_tc_errors(reset != 0);
     if (n < 0) return net_status(cudaErrorUnknown, "device_errors");
     *count = n;
+    return CLAIRE_OK;
+}
+
+extern "C" claire_status claire_net_set_wait_test(unsigned int spin_limit, int stall, int* tmem_kept)
+{
+    cudaError_t e = cudaDeviceSynchronize();
+    if (e != cudaSuccess) return net_status(e, "set_wait_test");
+    const uint32_t lim = spin_limit ? spin_limit : kTcSpinLimit;
+    const int st = stall ? 1 : 0;
+    if ((e = cudaMemcpyToSymbol(g_tc_spin_limit, &lim, sizeof(lim))) != cudaSuccess ||
+        (e = cudaMemcpyToSymbol(g_tc_test_stall, &st, sizeof(st))) != cudaSuccess)
+        return net_status(e, "set_wait_test");
+    if (tmem_kept && (e = cudaMemcpyFromSymbol(tmem_kept, g_tc_tmem_kept, sizeof(int))) != cudaSuccess)
+        return net_status(e, "set_wait_test");
     return CLAIRE_OK;
 }
 

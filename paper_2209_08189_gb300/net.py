@@ -47,6 +47,7 @@ _SIGS = {
     "claire_net_vel_loss": [_vp, _vp, _vp, _f, _f, _sz, _vp, _vp, _vp],
     "claire_net_residual": [_vp, _vp, _sz, _vp, _vp, _vp],
     "claire_net_device_errors": [_ip, _i],
+    "claire_net_set_wait_test": [ctypes.c_uint, _i, _ip],
     "claire_net_set_conv_tiling": [_i, _i],
     "claire_net_set_wgrad_tiling": [_i],
     "claire_net_last_error": [],
@@ -82,6 +83,17 @@ def device_errors(reset=True):
     n = ctypes.c_int()
     _check(lib().claire_net_device_errors(ctypes.byref(n), int(bool(reset))), "device_errors")
     return n.value
+
+
+def set_wait_test(spin_limit=0, stall=False):
+    """Failure-detection hook of the tcgen05 kernels: the bound of every
+    mbarrier wait (0 = default) and, with stall, a first wait on a phase that
+    nothing signals in every CTA.  Returns the count of CTAs that kept their
+    tensor memory after a give-up (0 when every give-up drained)."""
+    kept = ctypes.c_int()
+    _check(lib().claire_net_set_wait_test(int(spin_limit), int(bool(stall)), ctypes.byref(kept)),
+           "set_wait_test")
+    return kept.value
 
 
 def set_conv_tiling(bdc=0, nstage=0):

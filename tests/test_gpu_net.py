@@ -183,6 +183,48 @@ def test_conv3d_weight_gradient_tcgen05_tilings(env, nc, co):
     assert net.device_errors() == 0
 
 
+def test_tcgen05_wait_give_up_is_counted_and_returns_cleanly(env):
+    """Failure detection without a GPU fault: with the stall hook every CTA of
+    the tcgen05 convolution and weight gradient first waits (bounded, a small
+    runtime-set number of polls) on a completion phase that nothing signals,
+    before any MMA is issued.  The wait runs out, each CTA counts one give-up,
+    drains (nothing outstanding), releases its tensor memory and returns; the
+    next launches without the hook are correct and count nothing."""
+    torch, net = env
+    B, D, H, W, ci, co = 1, 4, 16, 8, 16, 16
+    r = np.random.default_rng(5)
+    xbuf = bf16(torch, r.standard_normal((B, D, H, W, ci)))
+    w = bf16(torch, r.standard_normal((co, 27, ci)) / np.sqrt(27 * ci))
+    dybuf = bf16(torch, r.standard_normal((B, D, H, W, co)))
+    x, dy = net.Act(xbuf, 0, ci), net.Act(dybuf, 0, co)
+    chunks = net.wgrad_chunks(ci, co, (B, D, H, W))
+    part = torch.empty(chunks * co * 27 * ci, device="cuda")
+    partb = torch.empty(chunks * co, device="cuda")
+    dw = torch.empty((co, 27, ci), device="cuda")
+    db = torch.empty(co, device="cuda")
+    y = torch.zeros((B, D, H, W, co), dtype=torch.bfloat16, device="cuda")
+    assert net.device_errors() == 0
+    try:
+        assert net.set_wait_test(2000, True) == 0
+        net.conv3d(x, w, None, net.Act(y, 0, co), 0.1, 1, stream(torch))
+        torch.cuda.synchronize()
+        n_conv = net.device_errors()
+        net.conv3d_wgrad(x, dy, chunks, part, partb, dw, db, stream(torch))
+        torch.cuda.synchronize()
+        n_wgrad = net.device_errors()
+    finally:
+        kept = net.set_wait_test(0, False)
+    assert n_conv >= 1 and n_wgrad >= 1
+    assert kept == 0  # every CTA that gave up released its tensor memory
+    net.conv3d(x, w, None, net.Act(y, 0, co), 0.1, 1, stream(torch))
+    net.conv3d_wgrad(x, dy, chunks, part, partb, dw, db, stream(torch))
+    torch.cuda.synchronize()
+    assert close_bf16(f64(y), onet.conv3d(f64(xbuf), f64(w), None, act=True, slope=0.1)) <= 0
+    rw, rb = onet.conv3d_weight_grad(f64(xbuf), f64(dybuf))
+    assert rel_l2(f64(dw), rw) < 1e-4 and rel_l2(f64(db), rb) < 1e-4
+    assert net.device_errors() == 0
+
+
 def test_pool_up_leaky_pack_head_adam(env):
     torch, net = env
     r = np.random.default_rng(7)

@@ -106,14 +106,18 @@ cudaError_t scratch_for_current_device(double** out)
     return cudaSuccess;
 }
 
-bool on_device(const void* p)
+// True for device memory of GPU `dev` (the current device) and for managed
+// memory; false for host memory and for device memory of another GPU, which
+// the kernels, launched on the current device, might not be able to reach.
+bool on_device(const void* p, int dev)
 {
     cudaPointerAttributes a;
     if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
         cudaGetLastError();
         return false;
     }
-    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+    if (a.type == cudaMemoryTypeManaged) return true;
+    return a.type == cudaMemoryTypeDevice && a.device == dev;
 }
 
 }  // namespace
@@ -127,7 +131,12 @@ extern "C" claire_status claire_dot_noalloc(const float* x, const float* y, size
         *out = 0.0;
         return CLAIRE_OK;
     }
-    if (!x || !y || !on_device(x) || !on_device(y)) return CLAIRE_EINVAL;
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+        cudaGetLastError();
+        return CLAIRE_ECUDA;
+    }
+    if (!x || !y || !on_device(x, dev) || !on_device(y, dev)) return CLAIRE_EINVAL;
     double* scratch = nullptr;
     if (scratch_for_current_device(&scratch) != cudaSuccess) {
         cudaGetLastError();

@@ -378,6 +378,7 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     // commit would complete, before any MMA is issued (it runs out)
     bool ok = true;
     if (stall) ok = __syncthreads_and(mbar_wait(mbar_s, 0)) != 0;
+    const bool stalled = !ok;  // gave up before any MMA was issued
     // instruction descriptor: D F32, A and B BF16, both K-major, N = Cout, M = 128
     const uint32_t idesc = (1u << 4) | (1u << 7) | (1u << 10) | ((static_cast<uint32_t>(Cout) >> 3) << 17) |
                            ((128u >> 4) << 24);
@@ -451,7 +452,8 @@ __global__ void __launch_bounds__(kConvThreads) k_conv3d_tc(const __nv_bfloat16*
     if (!ok) {
         cp_async_wait_group<0>();
         if (tid == 0) atomicAdd(err, 1);
-        release = tc_drain(drain_s, tid == 0);
+        // after the stall hook no MMA was issued: nothing to drain
+        release = stalled ? true : tc_drain(drain_s, tid == 0);
     } else {
         // epilogue: warp w owns TMEM lanes 32w..32w+31 = rows m = 32w + lane of every plane
         const int m = 32 * warp + lane;
@@ -766,8 +768,8 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
     bool release = true;
     if (!ok) {
         if (tid == 0) atomicAdd(err, 1);
-        // tid 0 issued every MMA (and, with the stall hook, none)
-        release = tc_drain(smem_addr(&drain), tid == 0);
+        // tid 0 issued every MMA; after the stall hook it issued none
+        release = stalled ? true : tc_drain(smem_addr(&drain), tid == 0);
     } else if (nbr > 0) {
         // an M = 128 accumulator holds row m in lane m, an M = 64 one in lane
         // (m / 16) * 32 + m % 16; warps w and w + 4 share lane quadrant w % 4

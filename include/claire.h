@@ -131,6 +131,14 @@ typedef struct claire_opts {
     double pc_tol;       /* relative residual of the inner PCG; 0 = always run pc_maxit iterations;
                             default 1e-1 */
     int pc_maxit;        /* inner PCG iteration cap; default 50 */
+    int spectral_iterate; /* 1 (default): claire_register also carries the spectrum of its iterate
+                            (updated with the Fourier-space PCG solution at every accepted step) and
+                            forms the regulariser S v from it.  A forward FP32 transform of v has
+                            roundoff of about 1e-7 ||v|| spread over all modes, which S(k) multiplies
+                            by up to beta_w (1 + |k|^2) |k|^2 (2.4e5 at 256^3, 6e7 at 1024^3); the
+                            carried spectrum avoids it.  Costs 3 half spectra (3 N1 N2 (N3/2+1)
+                            complex values), allocated by the first claire_register.  0: S v from the
+                            transform of v, as claire_gradient always does. */
 } claire_opts;
 
 /* claire_opts.precond */
@@ -215,6 +223,10 @@ claire_status claire_objective(claire_ctx* ctx, const float* v, double* J, doubl
  * with the state by SL transport (Eq. (1b)) and the adjoint lambda by SL
  * transport of Eq. (4) from lambda(1) = m1 - m(1).  Makes v the
  * linearisation point of later claire_hessian_matvec calls.  J may be NULL.
+ * S v is formed from an FP32 transform of v, whose roundoff S(k) amplifies
+ * at high |k| (about 7e-3 of ||S v|| for a smooth v at 256^3, growing as n^4);
+ * claire_register avoids that with its carried spectrum (spectral_iterate).
+ * The same holds for the S vt of claire_hessian_matvec.
  */
 claire_status claire_gradient(claire_ctx* ctx, const float* v, float* g, double* J);
 
@@ -314,6 +326,20 @@ claire_status claire_detj(claire_ctx* ctx, const float* v, double* detj_min, dou
  * (CLAIRE_INTERP_BSPLINE: f is prefiltered into the context's scratch first).
  * Sec. 3 "IP kernel". */
 claire_status claire_interp(claire_ctx* ctx, const float* f, const float* d, float* out, int order);
+
+/* out[q][p] = f[q](x_p + d_p) for nf >= 1 fields sharing one displacement: f and
+ * out are nf x N floats (field-major), d 3N floats; order 3 or 1 (the fields
+ * are not prefiltered, so CLAIRE_INTERP_BSPLINE is rejected).  One kernel
+ * reads d and forms each tile's box geometry once for all fields (Sec. 3 "IP
+ * kernel" applied to several fields, as the paper's velocity components). */
+claire_status claire_interp_fields(claire_ctx* ctx, const float* f, int nf, const float* d, float* out, int order);
+
+/* Number of CTAs (one per 4 x 8 x 32 tile of arrival points) of the tiled
+ * gathers -- interpolation, backtrace, every SL step -- that took the
+ * global-memory path because their departure box did not fit in shared
+ * memory, since the last reset (reset != 0 clears it), on the current
+ * device, summed over all contexts.  Synchronises the device. */
+claire_status claire_gather_fallback_tiles(unsigned long long* count, int reset);
 
 /* RK2 (Heun) characteristic displacement (Sec. 2.2) of v in grid units:
  * direction +1: X = x - dt/2 [v(x) + v(x - dt v(x))]; direction -1: X+ with +v.

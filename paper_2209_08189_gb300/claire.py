@@ -47,7 +47,8 @@ class claire_opts(ctypes.Structure):
                 ("max_ls", ctypes.c_int), ("wall_limit_s", ctypes.c_double),
                 ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double),
                 ("lowmem", ctypes.c_int), ("precond", ctypes.c_int), ("pc_coarse", ctypes.c_int),
-                ("pc_tol", ctypes.c_double), ("pc_maxit", ctypes.c_int)]
+                ("pc_tol", ctypes.c_double), ("pc_maxit", ctypes.c_int),
+                ("spectral_iterate", ctypes.c_int)]
 
 
 class claire_report(ctypes.Structure):
@@ -148,6 +149,8 @@ _SIGS = {
     "claire_resample": [_vp, ctypes.POINTER(ctypes.c_int), _vp, ctypes.POINTER(ctypes.c_int), ctypes.c_int,
                         ctypes.c_int, _vp],
     "claire_interp": [_vp, _vp, _vp, _vp, ctypes.c_int],
+    "claire_interp_fields": [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int],
+    "claire_gather_fallback_tiles": [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int],
     "claire_backtrace": [_vp, _vp, _vp, ctypes.c_int],
     "claire_fd8_grad": [_vp, _vp, _vp],
     "claire_fd8_div": [_vp, _vp, _vp],
@@ -353,6 +356,19 @@ def claire_interp(ctx, f, d, out, order=INTERP_CUBIC):
     return _check(ctx, lib().claire_interp(ctx, _ptr(f), _ptr(d), _ptr(out), int(order)))
 
 
+def claire_interp_fields(ctx, f, nf, d, out, order=INTERP_CUBIC):
+    return _check(ctx, lib().claire_interp_fields(ctx, _ptr(f), int(nf), _ptr(d), _ptr(out), int(order)))
+
+
+def claire_gather_fallback_tiles(reset=False):
+    """CTAs of the tiled gathers that took the global-memory path (current device)."""
+    n = ctypes.c_ulonglong()
+    st = lib().claire_gather_fallback_tiles(ctypes.byref(n), int(bool(reset)))
+    if st < 0:
+        raise ClaireError(st, "claire_gather_fallback_tiles")
+    return int(n.value)
+
+
 def claire_backtrace(ctx, v, d, direction=1):
     return _check(ctx, lib().claire_backtrace(ctx, _ptr(v), _ptr(d), int(direction)))
 
@@ -487,6 +503,9 @@ class Context:
 
     def interp(self, f, d, out, order=INTERP_CUBIC):
         claire_interp(self.handle, f, d, out, order)
+
+    def interp_fields(self, f, nf, d, out, order=INTERP_CUBIC):
+        claire_interp_fields(self.handle, f, nf, d, out, order)
 
     def backtrace(self, v, d, direction=1):
         claire_backtrace(self.handle, v, d, direction)

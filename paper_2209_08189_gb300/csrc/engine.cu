@@ -133,6 +133,11 @@ struct claire_ctx {
     double* hres = nullptr;               // pinned host scalars
 
     // reverse-mode transport scratch, allocated by the first claire_transport_vjp
+    // spectrum of the Gauss-Newton iterate inside claire_register (spectral_iterate = 1):
+    // S v is formed from it instead of from a transform of v, allocated by the first
+    // claire_register (3M modes)
+    cufftComplex* vh = nullptr;
+    bool vh_on = false;
     float* vjp_states = nullptr;            // (nt+1) N, FP32 (2 N when checkpointing)
     size_t vjp_states_n = 0;
     unsigned long long* vjp_acc = nullptr;  // N fixed-point accumulators
@@ -179,6 +184,8 @@ struct claire_ctx {
         arena = nullptr;
         if (vjp_states) cudaFree(vjp_states);
         vjp_states = nullptr;
+        if (vh) cudaFree(vh);
+        vh = nullptr;
         if (vjp_acc) cudaFree(vjp_acc);
         vjp_acc = nullptr;
         if (hres) cudaFreeHost(hres);
@@ -264,6 +271,7 @@ void fill_defaults(claire_opts* o)
     o->pc_coarse = 2;
     o->pc_tol = 1e-1;
     o->pc_maxit = 50;
+    o->spectral_iterate = 1;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -275,7 +283,7 @@ bool valid_opts(const claire_opts& o)
            o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
            o.g0_ref >= 0 && (o.lowmem == 0 || o.lowmem == 1) &&
            (o.precond == CLAIRE_PRECOND_SPECTRAL || o.precond == CLAIRE_PRECOND_TWO_LEVEL) && o.pc_coarse >= 1 &&
-           o.pc_tol >= 0 && o.pc_maxit >= 1;
+           o.pc_tol >= 0 && o.pc_maxit >= 1 && (o.spectral_iterate == 0 || o.spectral_iterate == 1);
 }
 
 // The two-level grid N_i / f must be whole, even and at least 4 per axis.
@@ -503,6 +511,26 @@ claire_status spectral(claire_ctx* c, const float* in, float* out, SpectralOp op
     return CLAIRE_OK;
 }
 
+// out = F^{-1}[M(k) vh] for the iterate's spectrum vh (scaled by 1/N like the
+// PCG spectra); vh is copied to the transform buffer first (C2R overwrites its
+// input).  No forward transform: its FP32 roundoff, which the symbol M(k)
+// would amplify at high |k|, never enters.
+claire_status spectral_hat(claire_ctx* c, const cufftComplex* vh, float* out, SpectralOp op)
+{
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    CL_CUDA(c, cudaMemcpyAsync(c->spec, vh, 3 * c->M * sizeof(cufftComplex), cudaMemcpyDeviceToDevice, c->stream));
+    {
+        KTimer t(c, KK_SPECTRAL, 48.0 * c->M, 0);
+        launch_spectral(c->grid, c->spec, c->M, op, c->rp, 1.0f, c->stream);
+        CL_LAUNCHED(c);
+    }
+    {
+        KTimer t(c, KK_FFT, 0, 0);
+        CL_FFT(c, cufftExecC2R(c->c2r, c->spec, out));
+    }
+    return CLAIRE_OK;
+}
+
 claire_status fd8_grad(claire_ctx* c, const void* f, void* out, Storage sto)
 {
     KTimer t(c, KK_FD8, 4.0 * storage_bytes(sto) * c->N, 0);
@@ -670,7 +698,10 @@ claire_status adjoint_and_body(claire_ctx* c, const void* a, const void* s, floa
 claire_status gradient_at_lin(claire_ctx* c, float* g)
 {
     const size_t N = c->N;
-    CL_TRY(spectral(c, c->v, g, SPEC_REG));
+    if (c->vh_on)
+        CL_TRY(spectral_hat(c, c->vh, g, SPEC_REG));
+    else
+        CL_TRY(spectral(c, c->v, g, SPEC_REG));
     {
         PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
         CL_TRY(dot_async(c, c->v, g, 3 * N, 0.5 * c->hvol, 0));
@@ -1130,9 +1161,13 @@ claire_status pcg(claire_ctx* c, double eta, int* its)
         }
     }
     {
+        // the multi-dimensional C2R may overwrite its input: transform a copy, so
+        // that xh still holds the solution's spectrum for the iterate's update
         PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+        CL_CUDA(c, cudaMemcpyAsync(c->phat, c->xh, 3 * c->M * sizeof(cufftComplex), cudaMemcpyDeviceToDevice,
+                                   c->stream));
         KTimer t(c, KK_FFT, 0, 0);
-        CL_FFT(c, cufftExecC2R(c->c2r, c->xh, c->x));
+        CL_FFT(c, cufftExecC2R(c->c2r, c->phat, c->x));
     }
     return CLAIRE_OK;
 }
@@ -1459,6 +1494,31 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
 
     CL_CUDA(c, cudaMemcpyAsync(c->v, v_inout, n3 * sizeof(float), cudaMemcpyDefault, c->stream));
     CL_TRY(screen_velocity(c, c->v));
+    // the iterate's spectrum: one transform of the initial guess, then updated
+    // with the PCG solution's spectrum at every accepted step
+    c->vh_on = false;
+    if (c->o.spectral_iterate) {
+        if (!c->vh) {
+            if (cudaMalloc(&c->vh, 3 * c->M * sizeof(cufftComplex)) != cudaSuccess) {
+                cudaGetLastError();
+                c->vh = nullptr;
+                return fail(c, CLAIRE_ENOMEM,
+                            "spectrum of the iterate (%zu bytes; spectral_iterate = 0 does without it)",
+                            3 * c->M * sizeof(cufftComplex));
+            }
+        }
+        {
+            KTimer t(c, KK_FFT, 0, 0);
+            CL_FFT(c, cufftExecR2C(c->r2c, c->v, c->vh));
+        }
+        launch_cscale(c->vh, 3 * c->M, static_cast<float>(1.0 / c->N), c->stream);
+        CL_LAUNCHED(c);
+        c->vh_on = true;
+    }
+    struct VhOff {
+        claire_ctx* c;
+        ~VhOff() { c->vh_on = false; }
+    } vh_off{c};
     claire_status st = CLAIRE_ENOTCONVERGED;
     auto elapsed = [&]() {
         return std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
@@ -1532,6 +1592,14 @@ claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
             PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
             KTimer t(c, KK_VECTOR, 12.0 * n3, 0);
             launch_axpy(static_cast<float>(alpha), c->x, c->v, n3, c->stream);
+            CL_LAUNCHED(c);
+        }
+        if (c->vh_on) {
+            // vh += alpha xh (xh: the spectrum of the PCG solution x, same scaling)
+            PhaseScope ps(c, CLAIRE_PHASE_VECTOR);
+            KTimer t(c, KK_VECTOR, 24.0 * c->M * 3, 0);
+            launch_axpy(static_cast<float>(alpha), reinterpret_cast<const float*>(c->xh),
+                        reinterpret_cast<float*>(c->vh), 6 * c->M, c->stream);
             CL_LAUNCHED(c);
         }
         R.gn_iters = k + 1;
@@ -1752,6 +1820,34 @@ claire_status claire_interp(claire_ctx* c, const float* f, const float* d, float
     }
     CL_TRY(sync_scalars(c, 0));
     collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_interp_fields(claire_ctx* c, const float* f, int nf, const float* d, float* out, int order)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (order != 1 && order != 3) return fail(c, CLAIRE_EINVAL, "order must be 1 or 3");
+    if (nf < 1) return fail(c, CLAIRE_EINVAL, "nf must be >= 1");
+    CL_TRY(check_kernel_ptr(c, f));
+    CL_TRY(check_kernel_ptr(c, d));
+    CL_TRY(check_kernel_ptr(c, out));
+    {
+        KTimer t(c, KK_INTERP, (8.0 * nf + 12.0) * c->N, 1.0 * nf * c->N);
+        launch_interp_fields(c->grid, order, f, nf, d, out, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_TRY(sync_scalars(c, 0));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_gather_fallback_tiles(unsigned long long* count, int reset)
+{
+    if (!count) return CLAIRE_EINVAL;
+    if (cudaDeviceSynchronize() != cudaSuccess || gather_fallback_tiles(count, reset != 0) != cudaSuccess) {
+        cudaGetLastError();
+        return CLAIRE_ECUDA;
+    }
     return CLAIRE_OK;
 }
 

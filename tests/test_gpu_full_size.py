@@ -6,8 +6,11 @@ ORACLE's FP64 transport of the clean template, N(0, 0.02^2) noise on both
 images (seeds 0 / 1), beta_v = 1e-2, beta_w = 1e-4.  Compared element by
 element with the FP64 oracle on the same FP32 bits:
   * the full-field reduced gradient (Eq. (3)) and Gauss-Newton Hessian matvec
-    (Eq. (6)) at v = v*/2: relative L2 1e-4 (2 nt SL steps of ~1e-6 rounding
-    each, amplified by the cancellation in m1 - m(1));
+    (Eq. (6)) at v = v*/2, split as S x + body: the body (the SL transport
+    part) at relative L2 1e-4 (2 nt SL steps of ~1e-6 rounding each, amplified
+    by the cancellation in m1 - m(1)); S x, formed from an FP32 transform of x,
+    within twice the transform roundoff the symbol S(k) amplifies at high |k|
+    (fft_roundoff_bound; about 7e-3 of ||S x|| here);
   * a fixed-schedule registration (Eq. (5)), 2 Gauss-Newton x 5 PCG steps from
     v = 0: identical Armijo steps, final velocity relative L2 1e-3 and final
     relative mismatch within 1 % (stated requirements).
@@ -20,6 +23,8 @@ import pytest
 import __graft_entry__ as entry
 import oracle
 from paper_2209_08189_gb300 import synth
+
+from fp32_bounds import fft_roundoff_bound, split_check
 
 pytestmark = pytest.mark.gpu
 
@@ -67,19 +72,26 @@ def test_headline_256_gradient_and_matvec(env, headline):
     vt = f32(synth.bandlimited_velocity(N256, seed=5, kmax=8, vmax=0.3))
     ctx = _ctx(claire, torch, p)
     ctx.set_images(torch.from_numpy(m0).cuda(), torch.from_numpy(m1).cuda())
+    vd, vtd = torch.from_numpy(v).cuda(), torch.from_numpy(vt).cuda()
     g = torch.empty((3,) + N256, device="cuda")
-    J = ctx.gradient(torch.from_numpy(v).cuda(), g)
+    J = ctx.gradient(vd, g)
     Hv = torch.empty_like(g)
-    ctx.hessian_matvec(torch.from_numpy(vt).cuda(), Hv)
+    ctx.hessian_matvec(vtd, Hv)
+    sv = torch.empty_like(g)
+    ctx.spectral(vd, sv, claire.SPECTRAL_REG)   # the same S v the gradient formed
     torch.cuda.synchronize()
-    g_gpu = g.cpu().numpy().astype(np.float64)
-    h_gpu = Hv.cpu().numpy().astype(np.float64)
+    g_gpu, sv_gpu = g.cpu().numpy().astype(np.float64), sv.cpu().numpy().astype(np.float64)
+    ctx.spectral(vtd, sv, claire.SPECTRAL_REG)
+    torch.cuda.synchronize()
+    h_gpu, svt_gpu = Hv.cpu().numpy().astype(np.float64), sv.cpu().numpy().astype(np.float64)
     ctx.close()
-    del g, Hv
+    del g, Hv, sv, vd, vtd
     st = oracle.State(v.astype(np.float64), m0.astype(np.float64), m1.astype(np.float64), p)
     assert abs(J - st.J) <= 1e-5 * abs(st.J)
-    assert rel_l2(g_gpu, oracle.gradient(st)) <= 1e-4
-    assert rel_l2(h_gpu, oracle.hessian_matvec(st, vt.astype(np.float64))) <= 1e-4
+    split_check(g_gpu, sv_gpu, oracle.gradient(st), st.reg_v, fft_roundoff_bound(N256, p, v))
+    vt64 = vt.astype(np.float64)
+    split_check(h_gpu, svt_gpu, oracle.hessian_matvec(st, vt64), oracle.reg_apply(vt64, p),
+                 fft_roundoff_bound(N256, p, vt))
 
 
 def test_headline_256_registration_fixed_schedule(env, headline):

@@ -73,6 +73,11 @@ def parse_args():
                     help="timing of the warm-start network kernels (every conv shape of the U-Net at 128^3, "
                          "batch 4), one training step, and the SL reverse-mode transport at 256^3")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--interp-report", action="store_true",
+                    help="SL interpolation micro-benchmark: Gpts/s and roofline fractions of the gather kernel "
+                         "for tricubic / trilinear, 256^3..1024^3, realistic / zero / random displacements, "
+                         "1 and 4 fields")
+    ap.add_argument("--interp-sizes", default="256,512,1024")
     ap.add_argument("--precond", default="spectral", choices=["spectral", "two-level"],
                     help="PCG preconditioner of the timed registration")
     ap.add_argument("--no-other-precond", action="store_true",
@@ -233,6 +238,28 @@ def oracle_sample(grid, m0, m1, beta):
     return dt, pts
 
 
+def cpu_model():
+    """CPU model string of this host (for the CPU baseline's record)."""
+    try:
+        with open("/proc/cpuinfo") as f:
+            for line in f:
+                key = line.split(":")[0].strip().lower()
+                if key in ("model name", "cpu model", "hardware"):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    try:  # Arm hosts list no model name in /proc/cpuinfo; lscpu decodes the part number
+        import subprocess
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.lower().startswith("model name"):
+                return line.split(":", 1)[1].strip()
+    except (OSError, subprocess.SubprocessError):
+        pass
+    import platform
+    return platform.processor() or platform.machine()
+
+
 def run_reference(args):
     world, rank, _ = dist_setup(args)
     if rank != 0:
@@ -259,7 +286,7 @@ def run_reference(args):
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic", "config": config_dict(args, args.gpus),
         "cpu_baseline": {"value": val, "unit": UNIT, "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "cpu_model": cpu_model(), "sample": sample},
         "e2e": {"value": val, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}))
 
 
@@ -419,10 +446,12 @@ def run_ours(args):
         import oracle
         m0_64 = m0.astype(np.float64)
         m1_64 = m1.astype(np.float64)
-        s, q = oracle_sample(grid, m0_64, m1_64, args.beta)
+        runs = [oracle_sample(grid, m0_64, m1_64, args.beta) for _ in range(3)]
+        s, q = sorted(runs)[1]  # median of three runs
         cpu = {"value": q / s / 1e9, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+               "cpu_model": cpu_model(), "runs_s": [r[0] for r in runs],
                "sample": "one oracle gradient evaluation (state + adjoint solve, nt=4) of the "
-                         "same %d^3 workload, %.1f s" % (args.n, s)}
+                         "same %d^3 workload, median of 3 runs (%.1f s)" % (args.n, s)}
 
     r0 = reps[0]
     if rank == 0:
@@ -785,6 +814,96 @@ def run_net_report(args):
     print(json.dumps(out))
 
 
+def run_interp_report(args):
+    """Micro-benchmark of the SL interpolation kernel (a2) alone.
+
+    Fields: n^3 FP32 values (seeded uniform, the values do not change the
+    work).  Displacements (grid units): (a) realistic, the RK2 characteristic
+    X of the clinical-size velocity v* (band-limited |k| <= 8, max |v| = 1,
+    drawn at 64^3 and prolonged spectrally; nt = 4, so CFL = 10 n / 256);
+    (b) zero; (c) uniform random in +-CFL per component (no spatial
+    coherence: every tile takes the global-memory path).  1 field
+    (claire_interp, 20 B/pt) and 4 fields sharing the displacement
+    (claire_interp_fields, (8*4 + 12) / 4 = 11 B/pt per field).  Each case:
+    3 warm-up launches, then the mean of 10 launches timed with CUDA events on
+    the launching stream; the inputs (>= 256 MB) exceed the 129 MB L2.
+    Gpts/s counts grid points x fields; HBM fraction = algorithmic bytes / time
+    / measured copy bandwidth; LSU fraction = Gpts/s / the shared-memory read
+    ceiling (128 B/clk/SM x SMs x clock / (4 B x stencil size))."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev)
+    peak, peak_src = measured_peaks()
+    props = torch.cuda.get_device_properties(dev)
+    sizes = [int(x) for x in args.interp_sizes.split(",") if x]
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    v64 = torch.from_numpy(synth.bandlimited_velocity((64, 64, 64), seed=0, kmax=8, vmax=1.0).astype(np.float32)).to(dev)
+    clocks = ClockSampler(0)
+    clocks.start()
+    rows = []
+    for n in sizes:
+        grid = (n, n, n)
+        N = n ** 3
+        ctx = claire.Context(grid, 1e-2, 4, stream=st.cuda_stream)
+        f = torch.rand((4,) + grid, device=dev, generator=gen)
+        out = torch.empty((4,) + grid, device=dev)
+        v = torch.empty((3,) + grid, device=dev)
+        claire.claire_resample(v64, (64, 64, 64), v, grid, 3, claire.RESAMPLE_SPECTRAL, st.cuda_stream)
+        d_real = torch.empty((3,) + grid, device=dev)
+        ctx.backtrace(v, d_real, 1)
+        del v
+        cfl = 10.0 * n / 256.0
+        disps = {"realistic": d_real, "zero": torch.zeros((3,) + grid, device=dev),
+                 "random": (torch.rand((3,) + grid, device=dev, generator=gen) * 2.0 - 1.0) * cfl}
+        for kind, d in disps.items():
+            for order in (3, 1):
+                for nf in (1, 4):
+                    def call():
+                        if nf == 1:
+                            claire.claire_interp(ctx.handle, f[0], d, out[0], order)
+                        else:
+                            claire.claire_interp_fields(ctx.handle, f, nf, d, out, order)
+                    for _ in range(3):
+                        call()
+                    claire.claire_gather_fallback_tiles(reset=True)
+                    reps = 10
+                    e0 = torch.cuda.Event(enable_timing=True)
+                    e1 = torch.cuda.Event(enable_timing=True)
+                    torch.cuda.synchronize()
+                    e0.record(st)
+                    for _ in range(reps):
+                        call()
+                    e1.record(st)
+                    torch.cuda.synchronize()
+                    t = e0.elapsed_time(e1) * 1e-3 / reps
+                    glob = claire.claire_gather_fallback_tiles(reset=True) / reps
+                    tiles = (-(-n // 4)) * (-(-n // 8)) * (-(-n // 32))
+                    bpp = (8.0 * nf + 12.0) / nf
+                    gpts = N * nf / t / 1e9
+                    m = 64 if order == 3 else 8
+                    lsu_gpts = 128.0 * props.multi_processor_count * 2070e6 / (4.0 * m) / 1e9
+                    rows.append({"n": n, "displacement": kind, "interp": "tricubic" if order == 3 else "trilinear",
+                                 "fields": nf, "ms": t * 1e3, "gpts_s": gpts,
+                                 "bytes_per_pt_field": bpp, "hbm_GBs": gpts * bpp,
+                                 "hbm_frac": gpts * bpp / peak, "lsu_frac": gpts / lsu_gpts,
+                                 "global_tile_frac": glob / tiles})
+                    print("n=%4d %-9s %-9s fields=%d  %8.3f ms  %7.1f Gpts/s  HBM %5.1f %%  LSU %5.1f %%  "
+                          "global tiles %5.1f %%" % (n, kind, rows[-1]["interp"], nf, t * 1e3, gpts,
+                                                      100 * rows[-1]["hbm_frac"], 100 * rows[-1]["lsu_frac"],
+                                                      100 * rows[-1]["global_tile_frac"]), flush=True)
+        ctx.close()
+        del f, out, d_real, disps
+        torch.cuda.empty_cache()
+    ck = clocks.stop()
+    print(json.dumps({"interp_report": rows, "peak_GBs": peak, "peak_source": peak_src, "clocks": ck,
+                      "lsu_ceiling_note": "128 B/clk/SM x %d SMs x 2.07 GHz / (4 B x 64 or 8 reads per point)"
+                                          % props.multi_processor_count}))
+
+
 def run_large_report(args):
     """Largest single-GPU registration.  Workload: three nested spheres with a
     blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
@@ -1017,6 +1136,9 @@ def main():
         return
     if args.large_report:
         run_large_report(args)
+        return
+    if args.interp_report:
+        run_interp_report(args)
         return
     if args.warmstart_report:
         run_warmstart_report(args)

@@ -82,6 +82,11 @@ __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin,
 // vector work fields).
 void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
                    cudaStream_t st);
+// nf FP32 fields [nf][N] at one displacement into out [nf][N]
+void launch_interp_fields(const Grid& g, int order, const float* f, int nf, const float* d, float* out,
+                          cudaStream_t st);
+// CTAs of the tiled gathers that took the global-memory path (device-wide counter)
+cudaError_t gather_fallback_tiles(unsigned long long* count, bool reset);
 void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
                       cudaStream_t st);
 // One SL step of Eq. (4): lam = Heun(lam_next(X+), div v(X+), div v).

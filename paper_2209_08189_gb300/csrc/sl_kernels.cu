@@ -61,6 +61,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     // global-memory gather (clamped split, indices always in range)
     const BoxPar bp = tile_box<ORDER, 4>(g, lo1, lo2, lo3, hi1, hi2, hi3, bad, red, par, lane, warp);
     const bool use_box = bp.E1 != 0;
+    if (!use_box && threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
     const float cc = -0.5f * sdt;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
@@ -378,6 +379,41 @@ void launch_interp(const Grid& g, int order, const void* f, const float* d, void
         const SType* fs = static_cast<const SType*>(f);
         CLAIRE_TILED(order, EpiStore, fs, d, e);
     });
+}
+
+template <int ORDER>
+void launch_fields_as(const Grid& g, const float* f, int nf, const float* d, float* out, cudaStream_t st)
+{
+    if (tiles_cover_grid(g)) {
+        if (kTiledSmemBytes > 48 * 1024)
+            cudaFuncSetAttribute(k_gather_tiled_fields<ORDER, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kTiledSmemBytes));
+        k_gather_tiled_fields<ORDER, true><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, nf, d, out);
+    } else {
+        if (kTiledSmemBytes > 48 * 1024)
+            cudaFuncSetAttribute(k_gather_tiled_fields<ORDER, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                 static_cast<int>(kTiledSmemBytes));
+        k_gather_tiled_fields<ORDER, false><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, nf, d, out);
+    }
+}
+
+void launch_interp_fields(const Grid& g, int order, const float* f, int nf, const float* d, float* out,
+                          cudaStream_t st)
+{
+    if (order == 3)
+        launch_fields_as<3>(g, f, nf, d, out, st);
+    else if (order == 4)
+        launch_fields_as<4>(g, f, nf, d, out, st);
+    else
+        launch_fields_as<1>(g, f, nf, d, out, st);
+}
+
+cudaError_t gather_fallback_tiles(unsigned long long* count, bool reset)
+{
+    cudaError_t e = cudaMemcpyFromSymbol(count, g_gather_global_tiles, sizeof(unsigned long long));
+    if (e != cudaSuccess || !reset) return e;
+    const unsigned long long z = 0;
+    return cudaMemcpyToSymbol(g_gather_global_tiles, &z, sizeof(z));
 }
 
 void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,

@@ -37,6 +37,11 @@ namespace claire {
 #endif
 
 constexpr int TILE1 = CLAIRE_TILE1, TILE2 = 8, TILE3 = 32;
+
+// CTAs of the tiled gathers (in this translation unit) whose box did not fit
+// and which took the global-memory path; one atomic per such CTA, read by
+// claire_gather_fallback_tiles.
+__device__ unsigned long long g_gather_global_tiles = 0;
 constexpr int kTileThreads = TILE2 * 32;
 constexpr int kBoxCapFloats = CLAIRE_BOX_CAP;
 
@@ -474,6 +479,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     if (bp.E1 == 0) {
         // the tile's box does not fit: gather it from global memory (kept out
         // of the shared-memory path, which then has no call in its loop)
+        if (threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
 #pragma unroll
         for (int q = 0; q < TILE1; ++q) {
             if (!valid(q)) continue;
@@ -496,6 +502,66 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
         if (!valid(q)) continue;
         const float val = tile_eval<ORDER>(box, bp, i0 + q, j, k, d1[q], d2[q], d3[q]);
         epi.finish(p0 + q * g.n23, val, pre[q]);
+    }
+}
+
+// nf fields f + q N (q < nf) gathered at one displacement d into out + q N:
+// the displacements, bounds and box geometry are taken once per tile, and the
+// box of each field is staged into the same shared memory in turn.  Per point
+// and field this moves (8 nf + 12) / nf bytes instead of 20.
+template <int ORDER, bool FULL>
+__global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
+    k_gather_tiled_fields(Grid g, const float* __restrict__ f, int nf, const float* __restrict__ d,
+                          float* __restrict__ out)
+{
+    extern __shared__ float box[];
+    __shared__ int red[6][TILE2];
+    __shared__ int par[8];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const int k = blockIdx.x * TILE3 + lane;
+    const int j = blockIdx.y * TILE2 + warp;
+    const int i0 = blockIdx.z * TILE1;
+    const size_t N = g.N;
+    const bool col_ok = FULL || ((k < g.n3) && (j < g.n2));
+    const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
+    auto valid = [&](int q) { return FULL || (col_ok && i0 + q < g.n1); };
+    float d1[TILE1], d2[TILE1], d3[TILE1];
+    int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+    bool bad = false;
+#pragma unroll
+    for (int q = 0; q < TILE1; ++q) {
+        if (valid(q)) {
+            const uint32_t p = p0 + q * g.n23;
+            d1[q] = __ldg(d + p);
+            d2[q] = __ldg(d + N + p);
+            d3[q] = __ldg(d + 2 * N + p);
+            bounds_add(i0 + q, d1[q], lo1, hi1, bad);
+            bounds_add(j, d2[q], lo2, hi2, bad);
+            bounds_add(k, d3[q], lo3, hi3, bad);
+        }
+    }
+    const BoxPar bp = tile_box<ORDER, 4>(g, lo1, lo2, lo3, hi1, hi2, hi3, bad, red, par, lane, warp);
+    if (bp.E1 == 0) {
+        if (threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
+        for (int fld = 0; fld < nf; ++fld)
+#pragma unroll
+            for (int q = 0; q < TILE1; ++q) {
+                if (!valid(q)) continue;
+                const uint32_t p = p0 + q * g.n23;
+                out[fld * N + p] = gather_global<ORDER, float>(g, f + fld * N, i0 + q, j, k, d1[q], d2[q], d3[q]);
+            }
+        return;
+    }
+    for (int fld = 0; fld < nf; ++fld) {
+        tile_load_box<float>(g, f + fld * N, box, bp, lane, warp);
+        cp_async_wait_all();
+        __syncthreads();
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q) {
+            if (!valid(q)) continue;
+            out[fld * N + p0 + q * g.n23] = tile_eval<ORDER>(box, bp, i0 + q, j, k, d1[q], d2[q], d3[q]);
+        }
+        __syncthreads();  // every read of this field's box is done before the next staging
     }
 }
 

@@ -848,7 +848,7 @@ def run_interp_report(args):
     for n in sizes:
         grid = (n, n, n)
         N = n ** 3
-        ctx = claire.Context(grid, 1e-2, 4, stream=st.cuda_stream)
+        ctx = claire.Context(grid, 1e-2, 4, stream=st.cuda_stream, kernels_only=1)
         f = torch.rand((4,) + grid, device=dev, generator=gen)
         out = torch.empty((4,) + grid, device=dev)
         v = torch.empty((3,) + grid, device=dev)

@@ -139,6 +139,11 @@ typedef struct claire_opts {
                             carried spectrum avoids it.  Costs 3 half spectra (3 N1 N2 (N3/2+1)
                             complex values), allocated by the first claire_register.  0: S v from the
                             transform of v, as claire_gradient always does. */
+    int kernels_only;    /* 1: a context for the kernel-level entry points only (claire_interp,
+                            claire_interp_fields, claire_backtrace, claire_fd8_*, claire_dot): it
+                            holds the grid, the stream and a few KB of reduction scratch, no fields
+                            and no FFT plans, so grids far larger than a solver workspace fit;
+                            solver-level calls return CLAIRE_ESTATE.  Default 0. */
 } claire_opts;
 
 /* claire_opts.precond */

@@ -48,7 +48,7 @@ class claire_opts(ctypes.Structure):
                 ("timing", ctypes.c_int), ("storage", ctypes.c_int), ("g0_ref", ctypes.c_double),
                 ("lowmem", ctypes.c_int), ("precond", ctypes.c_int), ("pc_coarse", ctypes.c_int),
                 ("pc_tol", ctypes.c_double), ("pc_maxit", ctypes.c_int),
-                ("spectral_iterate", ctypes.c_int)]
+                ("spectral_iterate", ctypes.c_int), ("kernels_only", ctypes.c_int)]
 
 
 class claire_report(ctypes.Structure):

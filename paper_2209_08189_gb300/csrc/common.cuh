@@ -44,16 +44,18 @@ __host__ __device__ __forceinline__ int split_disp(float d, float& t)
 // and a plain floor gives the same cell (false for NaN and +-Inf).
 __host__ __device__ __forceinline__ bool disp_ok(float d) { return fabsf(d) < kDispLimit; }
 
-// Cubic Lagrange cardinal functions on the nodes -1, 0, 1, 2 at t in [0,1).
+// Cubic Lagrange cardinal functions on the nodes -1, 0, 1, 2 at t in [0,1):
+// w0 = -t (t-1)(t-2)/6, w1 = (t+1)(t-1)(t-2)/2, w2 = -(t+1) t (t-2)/2,
+// w3 = (t+1) t (t-1)/6, factored through a = t (t-1) and
+// b = (t+1)(t-2) = a - 2 (ten operations; exact 0/1 weights at t = 0).
 __device__ __forceinline__ void cubic_weights(float t, float w[4])
 {
-    const float tp1 = t + 1.0f, tm1 = t - 1.0f, tm2 = t - 2.0f;
-    const float t_tm1 = t * tm1;
-    const float tp1_tm2 = tp1 * tm2;
-    w[0] = -(1.0f / 6.0f) * t_tm1 * tm2;
-    w[1] = 0.5f * tp1_tm2 * tm1;
-    w[2] = -0.5f * tp1_tm2 * t;
-    w[3] = (1.0f / 6.0f) * tp1 * t_tm1;
+    const float a = fmaf(t, t, -t);
+    const float b = a - 2.0f;
+    w[0] = a * fmaf(t, -1.0f / 6.0f, 1.0f / 3.0f);
+    w[1] = b * fmaf(t, 0.5f, -0.5f);
+    w[2] = b * (-0.5f * t);
+    w[3] = a * fmaf(t, 1.0f / 6.0f, 1.0f / 6.0f);
 }
 
 // Uniform cubic B-spline basis on the nodes -1, 0, 1, 2 at t in [0,1)

@@ -272,6 +272,7 @@ void fill_defaults(claire_opts* o)
     o->pc_tol = 1e-1;
     o->pc_maxit = 50;
     o->spectral_iterate = 1;
+    o->kernels_only = 0;
 }
 
 bool valid_opts(const claire_opts& o)
@@ -283,7 +284,8 @@ bool valid_opts(const claire_opts& o)
            o.max_ls >= 1 && o.wall_limit_s >= 0 && o.storage >= 0 && o.storage <= 2 &&
            o.g0_ref >= 0 && (o.lowmem == 0 || o.lowmem == 1) &&
            (o.precond == CLAIRE_PRECOND_SPECTRAL || o.precond == CLAIRE_PRECOND_TWO_LEVEL) && o.pc_coarse >= 1 &&
-           o.pc_tol >= 0 && o.pc_maxit >= 1 && (o.spectral_iterate == 0 || o.spectral_iterate == 1);
+           o.pc_tol >= 0 && o.pc_maxit >= 1 && (o.spectral_iterate == 0 || o.spectral_iterate == 1) &&
+           (o.kernels_only == 0 || o.kernels_only == 1);
 }
 
 // The two-level grid N_i / f must be whole, even and at least 4 per axis.
@@ -557,6 +559,8 @@ claire_status bspline_coef(claire_ctx* c, const float* f, int ncomp, const float
         }
         c->bs_plans = true;
     }
+    if (ncomp == 3 && !c->plans)
+        return fail(c, CLAIRE_ESTATE, "B-spline velocity coefficients need the solver's plans (kernels_only context)");
     cufftHandle fwd = ncomp == 3 ? c->r2c : c->r2c1, inv = ncomp == 3 ? c->c2r : c->c2r1;
     CL_FFT(c, cufftSetStream(c->r2c1, c->stream));
     CL_FFT(c, cufftSetStream(c->c2r1, c->stream));
@@ -1202,6 +1206,14 @@ claire_status check_kernel_ptr(claire_ctx* c, const void* p)
     return CLAIRE_OK;
 }
 
+// Solver-level calls need the full workspace and the transform plans.
+claire_status need_workspace(claire_ctx* c)
+{
+    if (c->o.kernels_only)
+        return fail(c, CLAIRE_ESTATE, "context created with kernels_only = 1 (kernel-level entry points only)");
+    return CLAIRE_OK;
+}
+
 }  // namespace
 
 // ===========================================================================
@@ -1226,6 +1238,10 @@ claire_status claire_query_workspace(const int grid[3], int nt, const claire_opt
     const int sto = opts ? opts->storage : 0;
     if (sto < 0 || sto > 2) return CLAIRE_EINVAL;
     const bool lowmem = opts ? opts->lowmem != 0 : false;
+    if (opts && opts->kernels_only) {
+        *bytes = (2 * 152 * 8 + 16) * sizeof(double);  // reduction partials and device scalars
+        return CLAIRE_OK;
+    }
     *bytes = layout_floats(N, M, nt, 152 * 8, storage_bytes(static_cast<Storage>(sto)), lowmem, nullptr) *
              sizeof(float);
     return CLAIRE_OK;
@@ -1287,6 +1303,31 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
         return bail(CLAIRE_ECUDA);
     }
     c->red_blocks = std::max(1, c->nsm) * 4;
+    if (o.kernels_only) {
+        // reduction partials and the device scalars only: no fields, no plans
+        const size_t bytes = (2 * static_cast<size_t>(c->red_blocks) + 16) * sizeof(double);
+        if (cudaMalloc(&c->arena, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            c->arena = nullptr;
+            return bail(CLAIRE_ENOMEM);
+        }
+        c->arena_bytes = bytes;
+        c->partials = static_cast<double*>(c->arena);
+        c->dres = c->partials + 2 * c->red_blocks;
+        if (cudaMemset(c->dres, 0, 16 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            return bail(CLAIRE_ECUDA);
+        }
+        if (cudaMallocHost(&c->hres, 16 * sizeof(double)) != cudaSuccess) {
+            cudaGetLastError();
+            c->hres = nullptr;
+            return bail(CLAIRE_ENOMEM);
+        }
+        st = claire_set_stream(c, nullptr);
+        if (st != CLAIRE_OK) return bail(st);
+        *out = c;
+        return CLAIRE_OK;
+    }
     Layout L;
     c->sto = static_cast<Storage>(o.storage);
     c->es = storage_bytes(c->sto);
@@ -1382,8 +1423,14 @@ claire_status claire_set_stream(claire_ctx* c, void* stream)
 {
     if (!c) return CLAIRE_EINVAL;
     c->stream = static_cast<cudaStream_t>(stream);
-    CL_FFT(c, cufftSetStream(c->r2c, c->stream));
-    CL_FFT(c, cufftSetStream(c->c2r, c->stream));
+    if (c->plans) {
+        CL_FFT(c, cufftSetStream(c->r2c, c->stream));
+        CL_FFT(c, cufftSetStream(c->c2r, c->stream));
+    }
+    if (c->bs_plans) {
+        CL_FFT(c, cufftSetStream(c->r2c1, c->stream));
+        CL_FFT(c, cufftSetStream(c->c2r1, c->stream));
+    }
     if (c->tl2) {
         CL_FFT(c, cufftSetStream(c->tl2->r2c, c->stream));
         CL_FFT(c, cufftSetStream(c->tl2->c2r, c->stream));
@@ -1394,6 +1441,7 @@ claire_status claire_set_stream(claire_ctx* c, void* stream)
 claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
 {
     if (!c || !m0 || !m1) return c ? fail(c, CLAIRE_EINVAL, "null image") : CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     const size_t N = c->N;
     if (c->sto == Storage::F32) {
         CL_CUDA(c, cudaMemcpyAsync(c->m0, m0, N * sizeof(float), cudaMemcpyDefault, c->stream));
@@ -1417,6 +1465,7 @@ claire_status claire_set_images(claire_ctx* c, const float* m0, const float* m1)
 claire_status claire_objective(claire_ctx* c, const float* v, double* J, double* mismatch)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->p, &dv));
     CL_TRY(screen_velocity(c, dv));
@@ -1428,6 +1477,7 @@ claire_status claire_objective(claire_ctx* c, const float* v, double* J, double*
 claire_status claire_gradient(claire_ctx* c, const float* v, float* g, double* J)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!v || !g) return fail(c, CLAIRE_EINVAL, "null argument");
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
     const float* dv = nullptr;
@@ -1444,6 +1494,7 @@ claire_status claire_gradient(claire_ctx* c, const float* v, float* g, double* J
 claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!vt || !Hvt) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dvt = nullptr;
     CL_TRY(device_input(c, vt, 3 * c->N, c->p, &dvt));
@@ -1456,6 +1507,7 @@ claire_status claire_hessian_matvec(claire_ctx* c, const float* vt, float* Hvt)
 claire_status claire_precond(claire_ctx* c, const float* r, float* z)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!r || !z) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dr = nullptr;
     CL_TRY(device_input(c, r, 3 * c->N, c->p, &dr));
@@ -1479,6 +1531,7 @@ claire_status claire_precond(claire_ctx* c, const float* r, float* z)
 claire_status claire_register(claire_ctx* c, float* v_inout, claire_report* rep)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!v_inout) return fail(c, CLAIRE_EINVAL, "null v_inout");
     if (!c->have_images) return fail(c, CLAIRE_ESTATE, "images not set (claire_set_images)");
     const auto t0 = std::chrono::steady_clock::now();
@@ -1651,6 +1704,7 @@ claire_status claire_transport(claire_ctx* c, const float* v, const float* m_in,
                                int flags)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!v || !m_in || !m_out) return fail(c, CLAIRE_EINVAL, "null argument");
     if (flags != CLAIRE_TRANSPORT_FWD && flags != CLAIRE_TRANSPORT_ADJ)
         return fail(c, CLAIRE_EINVAL, "unknown transport flags %d", flags);
@@ -1718,6 +1772,7 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
                                               const float* gbar, float* gm0, float* gv, int flags)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!v || !m0 || !gbar) return fail(c, CLAIRE_EINVAL, "null argument");
     if (flags & ~CLAIRE_VJP_RECOMPUTE) return fail(c, CLAIRE_EINVAL, "unknown flags %d", flags);
     if (c->o.interp == 4)
@@ -1796,6 +1851,7 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
 claire_status claire_detj(claire_ctx* c, const float* v, double* lo, double* hi)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (!v || !lo || !hi) return fail(c, CLAIRE_EINVAL, "null argument");
     const float* dv = nullptr;
     CL_TRY(device_input(c, v, 3 * c->N, c->x, &dv));
@@ -1891,6 +1947,7 @@ claire_status claire_fd8_div(claire_ctx* c, const float* v, float* dv)
 claire_status claire_spectral(claire_ctx* c, const float* in, float* out, int op)
 {
     if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
     if (op < CLAIRE_SPECTRAL_REG || op > CLAIRE_SPECTRAL_K) return fail(c, CLAIRE_EINVAL, "bad op");
     CL_TRY(check_kernel_ptr(c, in));
     CL_TRY(check_kernel_ptr(c, out));

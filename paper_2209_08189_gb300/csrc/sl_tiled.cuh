@@ -133,8 +133,14 @@ __host__ __device__ __forceinline__ void box_geometry(const Grid& g, int a1, int
 // bounds of first-node cells; `bad` records a displacement that fails disp_ok.
 __host__ __device__ __forceinline__ void bounds_add(int node, float d, int& lo, int& hi, bool& bad)
 {
+#ifdef __CUDA_ARCH__
+    // one floor conversion: for |d| < 2^20 it equals the clamped split; any
+    // other value marks the tile bad, whose bounds are then not used
+    const int b = node + __float2int_rd(d);
+#else
     float t;
     const int b = node + split_disp(d, t);
+#endif
     lo = lo < b ? lo : b;
     hi = hi > b ? hi : b;
     bad = bad || !disp_ok(d);

@@ -144,6 +144,36 @@ def test_interp_fields_parity_and_fallback_count(env, n, order):
     assert rel_linf(host(out[1]), ref) <= 1e-5
 
 
+def test_kernels_only_context(env):
+    """kernels_only = 1: the kernel-level calls give the same bits as a full
+    context; solver-level calls return CLAIRE_ESTATE."""
+    torch, claire = env
+    n = (32, 40, 64)
+    rng = np.random.default_rng(2)
+    f = dev(torch, rng.standard_normal(n))
+    v = dev(torch, synth.mode_velocity(n, seed=4, vmax=0.5))
+    full = make_ctx(claire, torch, n)
+    lean = make_ctx(claire, torch, n, kernels_only=1)
+    outs = []
+    for ctx in (full, lean):
+        d = torch.empty((3,) + n, device="cuda")
+        ctx.backtrace(v, d, 1)
+        m = torch.empty(n, device="cuda")
+        ctx.interp(f, d, m, 3)
+        gr = torch.empty((3,) + n, device="cuda")
+        ctx.fd8_grad(f, gr)
+        torch.cuda.synchronize()
+        outs.append((d.cpu(), m.cpu(), gr.cpu(), ctx.dot(f, f)))
+    for a, b in zip(outs[0][:3], outs[1][:3]):
+        assert torch.equal(a, b)
+    assert outs[0][3] == outs[1][3]
+    for call in (lambda: lean.set_images(f, f), lambda: lean.register(torch.zeros((3,) + n, device="cuda")),
+                 lambda: lean.transport(v, f, f)):
+        with pytest.raises(claire.ClaireError) as e:
+            call()
+        assert e.value.status == -8
+
+
 @pytest.mark.parametrize("order", [3, 1])
 def test_interp_integer_shift_bit_exact(env, order):
     torch, claire = env

@@ -78,6 +78,8 @@ def parse_args():
                          "for tricubic / trilinear, 256^3..1024^3, realistic / zero / random displacements, "
                          "1 and 4 fields")
     ap.add_argument("--interp-sizes", default="256,512,1024")
+    ap.add_argument("--spectral-iterate", type=int, default=1, choices=[0, 1],
+                    help="claire_opts.spectral_iterate of the solver contexts (1: S v from the carried spectrum)")
     ap.add_argument("--precond", default="spectral", choices=["spectral", "two-level"],
                     help="PCG preconditioner of the timed registration")
     ap.add_argument("--no-other-precond", action="store_true",
@@ -101,7 +103,7 @@ def config_dict(args, n_gpus):
                         "|k|<=8 max|v|=1, Gauss-Newton-Krylov to gtol 5e-2 from v=0" % args.n,
             "grid": [args.n] * 3, "nt": 4, "interp": "cubic Lagrange", "beta_v": args.beta,
             "beta_w": 1e-4, "reg": "H1 seminorm", "gtol": 5e-2, "max_pcg": 50,
-            "storage": args.storage, "precond": args.precond,
+            "storage": args.storage, "precond": args.precond, "spectral_iterate": args.spectral_iterate,
             "l2_policy": "inputs larger than L2 (working set %.1f GB > 129 MB L2)"
                          % (args.n ** 3 * 4 * 60 / 1e9),
             "parallelism": "replicas" if n_gpus > 1 else "single GPU"}
@@ -320,7 +322,8 @@ def run_ours(args):
     storage = {"f32": claire.STORAGE_F32, "f16": claire.STORAGE_F16, "bf16": claire.STORAGE_BF16}[args.storage]
     precond = claire.PRECOND_TWO_LEVEL if args.precond == "two-level" else claire.PRECOND_SPECTRAL
     ctx = claire.Context(grid, args.beta, 4, stream=stream.cuda_stream, beta_w=1e-4, gtol=5e-2,
-                         max_gn=50, max_pcg=50, storage=storage, precond=precond)
+                         max_gn=50, max_pcg=50, storage=storage, precond=precond,
+                         spectral_iterate=args.spectral_iterate)
     # reference image by our own transport of the clean template, then noise
     base_d = torch.from_numpy(base.astype(np.float32)).to(dev)
     vstar_d = torch.from_numpy(vstar.astype(np.float32)).to(dev)
@@ -958,6 +961,7 @@ def run_large_report(args):
     # few because the context takes most of the memory
     ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
                          storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200,
+                         spectral_iterate=args.spectral_iterate,
                          precond=claire.PRECOND_TWO_LEVEL if args.large_precond == "two-level"
                          else claire.PRECOND_SPECTRAL)
     out["fp16_lowmem_device_gb"] = used_gb()
@@ -1096,7 +1100,7 @@ def run_large_report(args):
     out["device_gb_before_fp32_context"] = used_gb()
     try:
         ctx = claire.Context(grid, args.beta, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
-                             lowmem=1, wall_limit_s=1200)
+                             lowmem=1, wall_limit_s=1200, spectral_iterate=args.spectral_iterate)
     except claire.ClaireError as e:
         runs["fp32_zero"] = {"error": str(e)}
         print(json.dumps(out))

@@ -251,6 +251,52 @@ class UNet:
             self.p[k]["b"].copy_(self.torch.from_numpy(np.ascontiguousarray(b, dtype=np.float32)))
         self._sync_weights()
 
+    # ---- weight files ----
+    def save_weights(self, path, meta=None):
+        """Write the parameters to an .npz file: convolution weights as BF16
+        bit patterns (uint16, round to nearest even; the forward pass uses BF16
+        weights, so nothing is lost for inference), biases and the head in
+        FP32, and the architecture (channels, input channels, slope, vscale)."""
+        import json
+        arrays = {}
+        for k, (w, b) in self.state().items():
+            if "wb" in self.p[k]:
+                u = w.astype(np.float32).view(np.uint32)
+                arrays[k + ".w_bf16"] = ((u + 0x7FFF + ((u >> 16) & 1)) >> 16).astype(np.uint16)
+            else:
+                arrays[k + ".w"] = w.astype(np.float32)
+            arrays[k + ".b"] = b.astype(np.float32)
+        info = {"chans": list(self.chans), "cin": self.cin, "slope": self.slope, "vscale": self.vscale}
+        if meta:
+            info.update(meta)
+        arrays["__meta__"] = np.frombuffer(json.dumps(info).encode(), dtype=np.uint8)
+        np.savez(path, **arrays)
+
+    @staticmethod
+    def read_weights(path):
+        """(meta dict, state dict name -> (w FP32, b FP32)) of a file written by save_weights."""
+        import json
+        z = np.load(path)
+        meta = json.loads(bytes(z["__meta__"]).decode())
+        st = {}
+        for key in z.files:
+            if key == "__meta__" or key.endswith(".b"):
+                continue
+            name, kind = key.rsplit(".", 1)
+            w = (z[key].astype(np.uint32) << 16).view(np.float32) if kind == "w_bf16" else z[key]
+            st[name] = (w, z[name + ".b"])
+        return meta, st
+
+    @classmethod
+    def from_file(cls, path, stream=None):
+        """A network with the architecture and parameters stored in `path`."""
+        meta, st = cls.read_weights(path)
+        u = cls(chans=tuple(meta["chans"]), cin=meta["cin"], slope=meta["slope"], vscale=meta["vscale"],
+                seed=0, stream=stream)
+        u.load_state(st)
+        u.meta = meta
+        return u
+
     # ---- buffers per input shape ----
     def _buffers(self, B, D, H, W):
         key = (B, D, H, W)

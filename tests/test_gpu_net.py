@@ -225,6 +225,25 @@ def test_tcgen05_wait_give_up_is_counted_and_returns_cleanly(env):
     assert net.device_errors() == 0
 
 
+def test_unet_weight_file_round_trip(env, tmp_path):
+    """save_weights / from_file: the reloaded network gives the same output
+    bits (conv weights are stored as the BF16 values the forward pass uses)."""
+    torch, net = env
+    st = stream(torch)
+    u = net.UNet(seed=3, stream=st)
+    r = np.random.default_rng(8)
+    m0 = torch.from_numpy(r.random((32, 32, 32), dtype=np.float32)).cuda()
+    m1 = torch.from_numpy(r.random((32, 32, 32), dtype=np.float32)).cuda()
+    a = u.forward(m0[None], m1[None]).clone()
+    path = str(tmp_path / "w.npz")
+    u.save_weights(path, meta={"n_net": 32})
+    w = net.UNet.from_file(path, stream=st)
+    b = w.forward(m0[None], m1[None])
+    torch.cuda.synchronize()
+    assert w.meta["n_net"] == 32 and w.num_params() == u.num_params()
+    assert torch.equal(a, b)
+
+
 def test_pool_up_leaky_pack_head_adam(env):
     torch, net = env
     r = np.random.default_rng(7)

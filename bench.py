@@ -78,6 +78,10 @@ def parse_args():
                          "for tricubic / trilinear, 256^3..1024^3, realistic / zero / random displacements, "
                          "1 and 4 fields")
     ap.add_argument("--interp-sizes", default="256,512,1024")
+    ap.add_argument("--syn-report", action="store_true",
+                    help="the paper's SYN pairs (spherical-harmonic template, trigonometric velocity of K modes): "
+                         "regularisation-parameter search per K at 128^3 (nt 4) and 256^3 (nt 8)")
+    ap.add_argument("--syn-sizes", default="128,256")
     ap.add_argument("--no-mixed-learned", action="store_true",
                     help="skip the FP16 storage + learned warm start registration of the default line")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2209_08189_gb300", "weights",
@@ -997,6 +1001,57 @@ def run_interp_report(args):
                                           % props.multi_processor_count}))
 
 
+def run_syn_report(args):
+    """The paper's SYN experiment (Sec. 4): template = overlap counts of ten
+    perturbed |Y_8^6| shapes, velocity = K trigonometric modes with amplitude
+    k^-1/2, reference = the template advected by that velocity.  Per K in
+    {4, 8, 12, 16}: the two-stage regularisation-parameter search (Sec. 3)
+    with linear interpolation, nt = 4 at 128^3 and 8 at 256^3 (the paper's
+    choices), gtol 5e-2, Jacobian bounds [0.1, 10].  Times are host wall clock
+    around the synchronised search; the paper's own times (one V100) are
+    context, not a target."""
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream().cuda_stream
+    paper_s = {128: {4: 15, 8: 14, 12: 14, 16: 15}, 256: {4: 110, 8: 100, 12: 94, 16: 95}}
+    rows = []
+    for n in [int(x) for x in args.syn_sizes.split(",") if x]:
+        grid = (n, n, n)
+        nt = 4 if n <= 128 else 8
+        m0 = torch.from_numpy(synth.syn_template(grid, seed=0)).to(dev)
+        m0.div_(float(m0.max()))  # overlap counts scaled to [0, 1]
+        for K in (4, 8, 12, 16):
+            ctx = claire.Context(grid, 1.0, nt, stream=st, interp=claire.INTERP_LINEAR, beta_w=1e-5, gtol=5e-2,
+                                 max_gn=50, max_pcg=50, spectral_iterate=args.spectral_iterate)
+            vk = torch.from_numpy(synth.syn_velocity(grid, K).astype(np.float32)).to(dev)
+            m1 = torch.empty(grid, device=dev)
+            ctx.transport(vk, m0, m1)
+            ctx.set_images(m0, m1)
+            v = torch.zeros((3,) + grid, device=dev)
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            stt, rep = ctx.param_search(v)
+            torch.cuda.synchronize()
+            secs = time.perf_counter() - t0
+            last = rep["last"]
+            rows.append({"n": n, "nt": nt, "K": K, "search_s": secs, "solves": rep["solves"],
+                         "beta_v": rep["beta_v"], "beta_w": rep["beta_w"], "r": last["r"],
+                         "detj_min": last["detj_min"], "detj_max": last["detj_max"],
+                         "gn_iters_total": int(sum(t["gn_iters"] for t in rep["trace"])),
+                         "paper_v100_s": paper_s.get(n, {}).get(K)})
+            print("SYN n=%d nt=%d K=%2d: search %.2f s, %d solves, beta_v %.3g beta_w %.3g, r %.3f, det %.2f..%.2f "
+                  "(paper, one V100: %s s)" % (n, nt, K, secs, rep["solves"], rep["beta_v"], rep["beta_w"], last["r"],
+                                                last["detj_min"], last["detj_max"], paper_s.get(n, {}).get(K)),
+                  flush=True)
+            ctx.close()
+            del vk, m1, v
+            torch.cuda.empty_cache()
+    print(json.dumps({"syn_report": rows}))
+
+
 def run_large_report(args):
     """Largest single-GPU registration.  Workload: three nested spheres with a
     blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
@@ -1064,26 +1119,38 @@ def run_large_report(args):
     ctx.transport(vstar, m0_d, m1_d)
     m1 = m1_d.cpu().numpy()
 
-    def warped_labels(v):
-        """Labels of m0 carried by v: transported indicators, threshold 1/2."""
+    def carried_labels(v):
+        """Indicators of the labels of m0 carried by v (transported), on the host."""
         buf = torch.empty(grid, device=dev)
         tmp = torch.empty(grid, device=dev)
         res = []
         for k in (1, 2, 3):
             buf.copy_(torch.from_numpy((labels == k).astype(np.float32)))
             ctx.transport(v, buf, tmp)
-            res.append(tmp.cpu().numpy() > 0.5)
+            res.append(tmp.cpu().numpy())
         del buf, tmp
         flush()
         return res
 
-    ref = warped_labels(vstar)
+    ref = carried_labels(vstar)
 
-    def dice(lab):
-        return [float(2.0 * np.count_nonzero(a & b) / max(1, np.count_nonzero(a) + np.count_nonzero(b)))
-                for a, b in zip(lab, ref)]
+    def dice_of(lab):
+        """claire_dice of each label indicator against the reference's (threshold 1/2)."""
+        a = torch.empty(grid, device=dev)
+        b = torch.empty(grid, device=dev)
+        res = []
+        for x, y in zip(lab, ref):
+            a.copy_(torch.from_numpy(np.ascontiguousarray(x, dtype=np.float32)))
+            b.copy_(torch.from_numpy(y))
+            res.append(ctx.dice(a, b))
+        del a, b
+        flush()
+        return res
 
-    out["dice_before"] = dice([labels == k for k in (1, 2, 3)])
+    def dice(v):
+        return dice_of(carried_labels(v))
+
+    out["dice_before"] = dice_of([(labels == k).astype(np.float32) for k in (1, 2, 3)])
     ctx.set_images(m0_d, m1_d)   # the context keeps its own (FP16) copies
     del vstar, m1_d, m0_d
     flush()
@@ -1122,7 +1189,7 @@ def run_large_report(args):
                             "detj_max": rep["detj_max"], "cfl": rep["cfl"], "mismatch_at_guess": mis_guess,
                             "peak_device_gb": used_gb()}
     ctx.set_opts(g0_ref=0.0)
-    runs["fp16_learned"]["dice"] = dice(warped_labels(v))
+    runs["fp16_learned"]["dice"] = dice(v)
     # sampled oracle parity of one backtrace and one interpolation at n^3
     flush()
     d = torch.empty((3,) + grid, device=dev)
@@ -1175,7 +1242,7 @@ def run_large_report(args):
         _, mis_f = ctx.objective(vf)
         runs["fp32_at_%d" % nc] = {"time_to_tol_s": secs, "gn_iters": rep["gn_iters"],
                                    "pcg_iters": rep["pcg_iters_total"], "r_at_%d" % nc: rep["r"],
-                                   "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(warped_labels(vf))}
+                                   "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(vf)}
         del vf, vc
         flush()
     _, mis_zero = ctx.objective(torch.zeros((3,) + grid, device=dev))
@@ -1210,7 +1277,7 @@ def run_large_report(args):
                          "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"], "J": rep["J"],
                          "mismatch": rep["mismatch"], "r": rep["r"], "detj_min": rep["detj_min"],
                          "detj_max": rep["detj_max"], "cfl": rep["cfl"], "peak_device_gb": used_gb()}
-    runs["fp32_zero"]["dice"] = dice(warped_labels(v))
+    runs["fp32_zero"]["dice"] = dice(v)
     del v
     ctx.close()
     flush()
@@ -1233,6 +1300,9 @@ def main():
         return
     if args.interp_report:
         run_interp_report(args)
+        return
+    if args.syn_report:
+        run_syn_report(args)
         return
     if args.warmstart_report:
         run_warmstart_report(args)

@@ -339,6 +339,13 @@ claire_status claire_interp(claire_ctx* ctx, const float* f, const float* d, flo
  * kernel" applied to several fields, as the paper's velocity components). */
 claire_status claire_interp_fields(claire_ctx* ctx, const float* f, int nf, const float* d, float* out, int order);
 
+/* Dice overlap (Sec. 4.1, measures of performance) of the label sets
+ * A = {a >= 1/2} and B = {b >= 1/2}: *dice = 2 |A and B| / (|A| + |B|), 1 when
+ * both are empty.  a, b: n floats (device pointers), e.g. a label's indicator
+ * function carried by claire_transport and the reference label's indicator.
+ * Counts are exact integers (FP64 partial sums).  Synchronises the stream. */
+claire_status claire_dice(claire_ctx* ctx, const float* a, const float* b, size_t n, double* dice);
+
 /* Number of CTAs (one per 4 x 8 x 32 tile of arrival points) of the tiled
  * gathers -- interpolation, backtrace, every SL step -- that took the
  * global-memory path because their departure box did not fit in shared

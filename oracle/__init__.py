@@ -783,6 +783,20 @@ def detj(v, p: Params):
             + F[0, 2] * (F[1, 0] * F[2, 1] - F[1, 1] * F[2, 0]))
 
 
+def dice(a, b, threshold=0.5):
+    """Dice overlap (Sec. 4.1, measures of performance) of the sets
+    A = {a >= threshold} and B = {b >= threshold}: 2 |A and B| / (|A| + |B|),
+    1 when both sets are empty.  Labels carried by a map are indicator
+    functions transported with the state's SL steps, so a voxel belongs to the
+    carried label when its transported indicator is at least 1/2."""
+    A = np.asarray(a) >= threshold
+    B = np.asarray(b) >= threshold
+    na, nb = int(np.count_nonzero(A)), int(np.count_nonzero(B))
+    if na + nb == 0:
+        return 1.0
+    return 2.0 * int(np.count_nonzero(A & B)) / (na + nb)
+
+
 def cfl(v, p: Params):
     """CFL number: max over x of |v(x)|_2 * dt / min_c h_c."""
     v = _f64(v)

@@ -150,6 +150,7 @@ _SIGS = {
                         ctypes.c_int, _vp],
     "claire_interp": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_interp_fields": [_vp, _vp, ctypes.c_int, _vp, _vp, ctypes.c_int],
+    "claire_dice": [_vp, _vp, _vp, ctypes.c_size_t, ctypes.POINTER(ctypes.c_double)],
     "claire_gather_fallback_tiles": [ctypes.POINTER(ctypes.c_ulonglong), ctypes.c_int],
     "claire_backtrace": [_vp, _vp, _vp, ctypes.c_int],
     "claire_fd8_grad": [_vp, _vp, _vp],
@@ -360,6 +361,13 @@ def claire_interp_fields(ctx, f, nf, d, out, order=INTERP_CUBIC):
     return _check(ctx, lib().claire_interp_fields(ctx, _ptr(f), int(nf), _ptr(d), _ptr(out), int(order)))
 
 
+def claire_dice(ctx, a, b, n=None):
+    """Dice overlap of {a >= 1/2} and {b >= 1/2} (device float32 arrays)."""
+    out = ctypes.c_double()
+    _check(ctx, lib().claire_dice(ctx, _ptr(a), _ptr(b), int(n if n is not None else a.numel()), ctypes.byref(out)))
+    return out.value
+
+
 def claire_gather_fallback_tiles(reset=False):
     """CTAs of the tiled gathers that took the global-memory path (current device)."""
     n = ctypes.c_ulonglong()
@@ -503,6 +511,9 @@ class Context:
 
     def interp(self, f, d, out, order=INTERP_CUBIC):
         claire_interp(self.handle, f, d, out, order)
+
+    def dice(self, a, b):
+        return claire_dice(self.handle, a, b)
 
     def interp_fields(self, f, nf, d, out, order=INTERP_CUBIC):
         claire_interp_fields(self.handle, f, nf, d, out, order)

@@ -1897,6 +1897,29 @@ claire_status claire_interp_fields(claire_ctx* c, const float* f, int nf, const 
     return CLAIRE_OK;
 }
 
+claire_status claire_dice(claire_ctx* c, const float* a, const float* b, size_t n, double* dice)
+{
+    if (!c) return CLAIRE_EINVAL;
+    if (!dice) return fail(c, CLAIRE_EINVAL, "null output");
+    CL_TRY(check_kernel_ptr(c, a));
+    CL_TRY(check_kernel_ptr(c, b));
+    {
+        KTimer t(c, KK_REDUCE, 8.0 * n, 0, 4);
+        launch_count_partial(a, b, n, 0.5f, 0, c->partials, c->partials + c->red_blocks, c->red_blocks, c->stream);
+        launch_final_sum(c->partials, c->red_blocks, 1.0, c->dres + 10, c->stream);
+        launch_final_sum(c->partials + c->red_blocks, c->red_blocks, 1.0, c->dres + 11, c->stream);
+        launch_count_partial(a, b, n, 0.5f, 1, c->partials, c->partials + c->red_blocks, c->red_blocks, c->stream);
+        launch_final_sum(c->partials, c->red_blocks, 1.0, c->dres + 12, c->stream);
+        CL_LAUNCHED(c);
+    }
+    CL_CUDA(c, cudaMemcpyAsync(c->hres + 10, c->dres + 10, 3 * sizeof(double), cudaMemcpyDeviceToHost, c->stream));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    const double na = c->hres[10], nb = c->hres[11], nab = c->hres[12];
+    *dice = (na + nb) > 0 ? 2.0 * nab / (na + nb) : 1.0;
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
 claire_status claire_gather_fallback_tiles(unsigned long long* count, int reset)
 {
     if (!count) return CLAIRE_EINVAL;

@@ -209,6 +209,9 @@ void launch_sqdiff_partial(const void* a, const void* b, size_t n, double* parti
                            Storage sto, cudaStream_t st);
 void launch_maxnorm3_partial(const float* v, size_t N, double* partials, int nblocks,
                              cudaStream_t st);
+// Dice counts: |a >= t| and |b >= t| (both = 0) or |(a >= t) and (b >= t)| (both = 1)
+void launch_count_partial(const float* a, const float* b, size_t n, float t, int both, double* pa, double* pb,
+                          int nblocks, cudaStream_t st);
 void launch_final_sum(const double* partials, int nblocks, double scale, double* out,
                       cudaStream_t st);
 void launch_final_max(const double* partials, int nblocks, double* out, cudaStream_t st);

@@ -395,6 +395,27 @@ __global__ void __launch_bounds__(kThreads) k_maxnorm3_partial(const float* __re
     block_minmax(hi, hi, partials + gridDim.x, partials);
 }
 
+// Dice counts (Sec. 4.1): both = 0 counts a >= t and b >= t into pa, pb;
+// both = 1 counts (a >= t) and (b >= t) into pa (pb gets zeros).  Per-block
+// FP64 partial sums of integers: exact below 2^53.
+__global__ void __launch_bounds__(kThreads) k_count_partial(const float* __restrict__ a, const float* __restrict__ b,
+                                                             size_t n, float t, int both, double* __restrict__ pa,
+                                                             double* __restrict__ pb)
+{
+    unsigned long long ca = 0, cb = 0;
+    const size_t stride = static_cast<size_t>(gridDim.x) * kThreads;
+    for (size_t i = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; i < n; i += stride) {
+        const bool ia = a[i] >= t, ib = b[i] >= t;
+        if (both) {
+            ca += (ia && ib) ? 1u : 0u;
+        } else {
+            ca += ia ? 1u : 0u;
+            cb += ib ? 1u : 0u;
+        }
+    }
+    block_sum2(static_cast<double>(ca), static_cast<double>(cb), pa, pb);
+}
+
 __global__ void __launch_bounds__(kThreads) k_final_sum(const double* __restrict__ partials, int nb,
                                                          double scale, double* __restrict__ out)
 {
@@ -937,6 +958,12 @@ void launch_maxnorm3_partial(const float* v, size_t N, double* partials, int nbl
                              cudaStream_t st)
 {
     k_maxnorm3_partial<<<nblocks, kThreads, 0, st>>>(v, N, partials);
+}
+
+void launch_count_partial(const float* a, const float* b, size_t n, float t, int both, double* pa, double* pb,
+                          int nblocks, cudaStream_t st)
+{
+    k_count_partial<<<nblocks, kThreads, 0, st>>>(a, b, n, t, both, pa, pb);
 }
 
 void launch_final_sum(const double* partials, int nblocks, double scale, double* out,

@@ -144,6 +144,31 @@ def test_interp_fields_parity_and_fallback_count(env, n, order):
     assert rel_linf(host(out[1]), ref) <= 1e-5
 
 
+def test_dice_parity(env):
+    """claire_dice against the oracle's definition (Sec. 4.1): identical
+    values, since both count voxels exactly; on label indicators carried by a
+    transport, on equal, disjoint and empty sets, and at the threshold 1/2."""
+    torch, claire = env
+    n = (40, 36, 30)
+    m0 = synth.blob_template(n, seed=2)
+    vs = f32(synth.mode_velocity(n, seed=5, vmax=0.5))
+    ctx = make_ctx(claire, torch, n, kernels_only=1)
+    full = make_ctx(claire, torch, n)
+    lab = f32(m0 > 0.5)
+    carried = torch.empty(n, device="cuda")
+    full.transport(dev(torch, vs), dev(torch, lab), carried)
+    torch.cuda.synchronize()
+    got = ctx.dice(carried, dev(torch, lab))
+    assert got == oracle.dice(host(carried), lab) and 0.0 < got < 1.0
+    a = np.zeros(n, np.float32); b = np.zeros(n, np.float32)
+    a[:10] = 1.0; b[20:] = 1.0
+    assert ctx.dice(dev(torch, a), dev(torch, a)) == 1.0
+    assert ctx.dice(dev(torch, a), dev(torch, b)) == 0.0
+    assert ctx.dice(dev(torch, np.zeros(n)), dev(torch, np.zeros(n))) == 1.0
+    half = np.full(n, 0.5, np.float32)
+    assert ctx.dice(dev(torch, half), dev(torch, a)) == oracle.dice(half, a)
+
+
 def test_kernels_only_context(env):
     """kernels_only = 1: the kernel-level calls give the same bits as a full
     context; solver-level calls return CLAIRE_ESTATE."""

@@ -686,6 +686,24 @@ def test_cfl_closed_forms_non_cubic_grid():
     assert abs(0.8 * math.sqrt(2.0) * 0.25 / (2 * math.pi / 16) - expect) > 0.5 * expect  # largest h
 
 
+def test_dice_closed_forms():
+    """Dice of Sec. 4.1 on sets whose overlap is known by counting: equal sets
+    1, disjoint 0, two boxes of 8x8x8 and 8x8x4 voxels sharing 8x8x4 -> 2/3,
+    a threshold value itself counts as inside, both empty -> 1."""
+    n = (16, 16, 16)
+    a = np.zeros(n); b = np.zeros(n)
+    a[0:8, 0:8, 0:8] = 1.0
+    assert oracle.dice(a, a) == 1.0
+    b[8:16, 8:16, 8:16] = 1.0
+    assert oracle.dice(a, b) == 0.0
+    b[:] = 0.0
+    b[0:8, 0:8, 4:8] = 0.9
+    assert abs(oracle.dice(a, b) - 2.0 * 256 / (512 + 256)) < 1e-15
+    c = np.full(n, 0.5)
+    assert oracle.dice(c, c) == 1.0 and oracle.dice(c, a) == 2.0 * 512 / (4096 + 512)
+    assert oracle.dice(np.zeros(n), np.full(n, 0.49)) == 1.0
+
+
 def test_generators_deterministic():
     n = (8, 8, 8)
     a = synth.blob_template(n, seed=0)

@@ -82,6 +82,10 @@ def parse_args():
                     help="the paper's SYN pairs (spherical-harmonic template, trigonometric velocity of K modes): "
                          "regularisation-parameter search per K at 128^3 (nt 4) and 256^3 (nt 8)")
     ap.add_argument("--syn-sizes", default="128,256")
+    ap.add_argument("--vjp-report", action="store_true",
+                    help="reverse-mode transport at --vjp-n (default 1024^3) with time-step checkpointing: "
+                         "time, device memory, adjoint identity")
+    ap.add_argument("--vjp-n", type=int, default=1024)
     ap.add_argument("--no-mixed-learned", action="store_true",
                     help="skip the FP16 storage + learned warm start registration of the default line")
     ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2209_08189_gb300", "weights",
@@ -1052,6 +1056,63 @@ def run_syn_report(args):
     print(json.dumps({"syn_report": rows}))
 
 
+def run_vjp_report(args):
+    """claire_transport_vjp with CLAIRE_VJP_RECOMPUTE (states recomputed from m0
+    during the backward sweep: 2 N floats instead of (nt + 1) N) at n^3, nt = 4,
+    cubic Lagrange, on an FP16 low-memory context.  Inputs: the sphere template,
+    a band-limited velocity (|k| <= 8, max|v| 0.5, drawn at 64^3 and prolonged),
+    a seeded N(0,1) cotangent.  Checks the adjoint identity <gm0, x> = <gbar, T x>
+    for a seeded random x on the full field (FP64 sums on the device), and
+    times one call with CUDA events after a warm-up call."""
+    import gc
+    import torch
+    import __graft_entry__ as entry
+    entry.build()
+    from paper_2209_08189_gb300 import claire, synth
+    n = args.vjp_n
+    grid = (n,) * 3
+    N = n ** 3
+    dev = torch.device("cuda", 0)
+    stream = torch.cuda.current_stream(dev)
+    st = stream.cuda_stream
+    ctx = claire.Context(grid, 1e-2, 4, stream=st, storage=claire.STORAGE_F16, lowmem=1)
+    m0, _ = synth.sphere_template(grid, seed=0)
+    m0 = torch.from_numpy(m0).to(dev)
+    v64 = torch.from_numpy(synth.bandlimited_velocity((64,) * 3, seed=0, kmax=8, vmax=0.5).astype(np.float32)).to(dev)
+    v = torch.empty((3,) + grid, device=dev)
+    claire.claire_resample(v64, (64,) * 3, v, grid, 3, claire.RESAMPLE_SPECTRAL, st)
+    claire.lib().claire_resample_release()
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(0)
+    gbar = torch.randn(grid, device=dev, generator=gen)
+    x = torch.randn(grid, device=dev, generator=gen)
+    gm0 = torch.empty(grid, device=dev)
+    gv = torch.empty((3,) + grid, device=dev)
+    torch.cuda.synchronize()
+    ctx.transport_vjp(v, m0, gbar, gm0, gv, recompute=True)  # warm-up (allocates the scratch)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    e0.record(stream)
+    ctx.transport_vjp(v, m0, gbar, gm0, gv, recompute=True)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    t_vjp = e0.elapsed_time(e1) * 1e-3
+    free, total = torch.cuda.mem_get_info()
+    used = (total - free) / 1e9
+    tx = torch.empty(grid, device=dev)
+    ctx.transport(v, x, tx)
+    lhs = claire.claire_dot(ctx.handle, gm0, x, N)
+    rhs = claire.claire_dot(ctx.handle, gbar, tx, N)
+    nrm = math.sqrt(claire.claire_dot(ctx.handle, gm0, gm0, N) * claire.claire_dot(ctx.handle, x, x, N))
+    gvn = math.sqrt(claire.claire_dot(ctx.handle, gv, gv, 3 * N))
+    out = {"n": n, "nt": 4, "interp": "cubic Lagrange", "recompute": True, "vjp_s": t_vjp,
+           "device_gb_in_use": used, "adjoint_identity_rel": abs(lhs - rhs) / nrm, "lhs": lhs, "rhs": rhs,
+           "gv_norm": gvn, "gv_finite": bool(math.isfinite(gvn)),
+           "scratch_gb": (2 * N * 4 + N * 8) / 1e9}
+    ctx.close()
+    print(json.dumps(out))
+
+
 def run_large_report(args):
     """Largest single-GPU registration.  Workload: three nested spheres with a
     blob texture (synth.sphere_template, labels 1..3) at n^3, advected by a
@@ -1303,6 +1364,9 @@ def main():
         return
     if args.syn_report:
         run_syn_report(args)
+        return
+    if args.vjp_report:
+        run_vjp_report(args)
         return
     if args.warmstart_report:
         run_warmstart_report(args)

@@ -74,8 +74,7 @@ typedef enum {
                                    coefficients (Sec. 3): every gathered field is prefiltered first
                                    (forward FFT, division by the sampled spline's symbol
                                    prod (2 + cos k h) / 3, inverse FFT), which needs FP32 storage and
-                                   adds 3N floats + 3 half spectra of scratch on first use; not
-                                   supported by claire_transport_vjp (CLAIRE_ENOTIMPL) */
+                                   adds 3N floats + 3 half spectra of scratch on first use */
 
 /* claire_transport flags */
 #define CLAIRE_TRANSPORT_FWD 0  /* state, Eq. (1b)-(1c): m(1) from m(0) */
@@ -288,7 +287,11 @@ claire_status claire_transport(claire_ctx* ctx, const float* v, const float* m_i
  * recomputes m^j during the backward sweep (time-step checkpointing: 2 N
  * floats of states instead of (nt+1) N).  The first call allocates its
  * scratch ((nt+1) N floats + N 64-bit accumulators); the call invalidates the
- * linearisation point of claire_hessian_matvec.  Computes in FP32.
+ * linearisation point of claire_hessian_matvec.  Computes in FP32.  All
+ * three interpolation orders: with cubic B-splines the interpolant gradients
+ * are those of each state's (and the velocity's) spline coefficients, and
+ * every scatter transpose is followed by the prefilter, whose real, even
+ * symbol makes it its own transpose.
  */
 #define CLAIRE_VJP_RECOMPUTE 1
 claire_status claire_transport_vjp(claire_ctx* ctx, const float* v, const float* m0, const float* gbar,

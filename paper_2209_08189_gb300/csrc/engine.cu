@@ -1775,8 +1775,6 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
     CL_TRY(need_workspace(c));
     if (!v || !m0 || !gbar) return fail(c, CLAIRE_EINVAL, "null argument");
     if (flags & ~CLAIRE_VJP_RECOMPUTE) return fail(c, CLAIRE_EINVAL, "unknown flags %d", flags);
-    if (c->o.interp == 4)
-        return fail(c, CLAIRE_ENOTIMPL, "the reverse-mode transport supports linear and cubic Lagrange interpolation");
     const size_t N = c->N;
     const int nt = c->nt;
     const bool recompute = (flags & CLAIRE_VJP_RECOMPUTE) != 0;
@@ -1821,26 +1819,54 @@ extern "C" claire_status claire_transport_vjp(claire_ctx* c, const float* v, con
             }
             mj = a;
         }
+        // cubic B-splines: the interpolant is that of the state's coefficients
+        const float* mjc = mj;
+        if (c->o.interp == 4) CL_TRY(bspline_coef(c, mj, 1, &mjc));
         {
             KTimer t(c, KK_VJP_GRAD, 32.0 * N, 1.0 * N);
-            launch_grad_accum(c->grid, c->o.interp, mj, d, mb, dbar, c->stream);
+            launch_grad_accum(c->grid, c->o.interp, mjc, d, mb, dbar, c->stream);
             CL_LAUNCHED(c);
         }
         CL_TRY(scatter_transpose(c, mb, d, nullptr, mb2, false, 1.0f));
+        if (c->o.interp == 4) {
+            // the transpose of "prefilter, then interpolate": scatter, then the
+            // prefilter again (its symbol is real and even, so it is symmetric)
+            const float* coef;
+            CL_TRY(bspline_coef(c, mb2, 1, &coef));
+            CL_CUDA(c, cudaMemcpyAsync(mb2, coef, N * sizeof(float), cudaMemcpyDeviceToDevice, c->stream));
+        }
         std::swap(mb, mb2);
     }
     if (gm0) CL_TRY(copy_out(c, gm0, mb, N));
     if (gv) {
         float* ub = c->p;
         float* Ub = reinterpret_cast<float*>(c->spec);  // 6 M >= 3 N floats, unused here
+        const void* vsrc;
+        CL_TRY(gather_src(c, dv, 3, &vsrc));  // v, or its B-spline coefficients
         {
             KTimer t(c, KK_VJP_GRAD, 48.0 * N, 3.0 * N);
-            launch_predictor_terms(c->grid, c->o.interp, dv, static_cast<float>(c->dt), dbar, ub, Ub, c->stream);
+            launch_predictor_terms(c->grid, c->o.interp, dv, static_cast<const float*>(vsrc),
+                                   static_cast<float>(c->dt), dbar, ub, Ub, c->stream);
             CL_LAUNCHED(c);
         }
         const float ih[3] = {c->grid.ih1, c->grid.ih2, c->grid.ih3};
-        for (int comp = 0; comp < 3; ++comp)
-            CL_TRY(scatter_transpose(c, Ub + comp * N, nullptr, dv, ub + comp * N, true, ih[comp]));
+        for (int comp = 0; comp < 3; ++comp) {
+            if (c->o.interp != 4) {
+                CL_TRY(scatter_transpose(c, Ub + comp * N, nullptr, dv, ub + comp * N, true, ih[comp]));
+                continue;
+            }
+            // B-splines: scatter into the free half of the state cotangent, prefilter,
+            // then ub = ih (ub + that), the conversion the accumulating scatter does
+            float* tmp = (mb == c->r) ? c->r + N : c->r;
+            CL_TRY(scatter_transpose(c, Ub + comp * N, nullptr, dv, tmp, false, 1.0f));
+            const float* coef;
+            CL_TRY(bspline_coef(c, tmp, 1, &coef));
+            {
+                KTimer t(c, KK_VECTOR, 12.0 * N, 0);
+                launch_scale_add(ub + comp * N, ih[comp], coef, N, c->stream);
+                CL_LAUNCHED(c);
+            }
+        }
         CL_TRY(copy_out(c, gv, ub, 3 * N));
     }
     CL_CUDA(c, cudaStreamSynchronize(c->stream));

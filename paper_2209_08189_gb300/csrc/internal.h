@@ -139,8 +139,10 @@ void launch_scatter_fixed(const Grid& g, int order, const float* yv, const float
 void launch_fixed_to_float(unsigned long long* acc, const double* maxabs, int accumulate, float mult, float* out,
                            size_t n, cudaStream_t st);
 // predictor terms of the velocity cotangent (grid units): ubar, Ubar from dbar
-void launch_predictor_terms(const Grid& g, int order, const float* v, float dt, const float* dbar, float* ubar,
-                            float* Ubar, cudaStream_t st);
+// y = a (y + x)
+void launch_scale_add(float* y, float a, const float* x, size_t n, cudaStream_t st);
+void launch_predictor_terms(const Grid& g, int order, const float* v, const float* vc, float dt, const float* dbar,
+                            float* ubar, float* Ubar, cudaStream_t st);
 // out2[1] = max |x| (out2[0] scratch)
 void launch_maxabs(const float* x, size_t n, double* partials, int nblocks, double* out2, cudaStream_t st);
 

@@ -318,8 +318,11 @@ __global__ void __launch_bounds__(kThreads) k_fixed_to_float(unsigned long long*
 
 // Predictor terms: Ubar = -dt/2 dbar; ubar(x) = -dt/2 dbar(x) - dt sum_c Ubar_c grad I[u_c](y)
 // with y = x - dt u(x); writes ubar (grid units) and Ubar.
+// vc: the field the predictor interpolates (v itself, or its cubic B-spline
+// coefficients); v gives the predictor displacement at the node.
 template <int ORDER>
-__global__ void __launch_bounds__(kThreads) k_predictor_terms(Grid g, const float* __restrict__ v, float dt,
+__global__ void __launch_bounds__(kThreads) k_predictor_terms(Grid g, const float* __restrict__ v,
+                                                               const float* __restrict__ vc, float dt,
                                                                const float* __restrict__ dbar,
                                                                float* __restrict__ ubar,
                                                                float* __restrict__ Ubar)
@@ -338,7 +341,7 @@ __global__ void __launch_bounds__(kThreads) k_predictor_terms(Grid g, const floa
     for (int c = 0; c < 3; ++c) {
         Ub[c] = -0.5f * dt * __ldg(dbar + c * N + p);
         float gr[3];
-        interp_gradient<ORDER>(g, v + c * N, i, j, k, e1, e2, e3, gr);  // gradient of v_c; u_c = v_c ih_c
+        interp_gradient<ORDER>(g, vc + c * N, i, j, k, e1, e2, e3, gr);  // gradient of v_c; u_c = v_c ih_c
 #pragma unroll
         for (int e = 0; e < 3; ++e) yb[e] = fmaf(Ub[c] * ih[c], gr[e], yb[e]);
     }
@@ -347,6 +350,15 @@ __global__ void __launch_bounds__(kThreads) k_predictor_terms(Grid g, const floa
         Ubar[c * N + p] = Ub[c];
         ubar[c * N + p] = -0.5f * dt * __ldg(dbar + c * N + p) - dt * yb[c];
     }
+}
+
+// y = a (y + x): the unit factor that k_fixed_to_float applies when it
+// accumulates, for a term added after a prefilter.
+__global__ void __launch_bounds__(kThreads) k_scale_add(float* __restrict__ y, float a, const float* __restrict__ x,
+                                                         size_t n)
+{
+    const size_t p = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x;
+    if (p < n) y[p] = a * (y[p] + x[p]);
 }
 
 // max |x| over n values; partials hold 2 * gridDim.x doubles
@@ -370,6 +382,8 @@ void launch_grad_accum(const Grid& g, int order, const float* m, const float* d,
 {
     if (order == 3)
         k_grad_accum<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, m, d, mbar, dbar);
+    else if (order == 4)
+        k_grad_accum<4><<<blocks_for(g.N), kThreads, 0, st>>>(g, m, d, mbar, dbar);
     else
         k_grad_accum<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, m, d, mbar, dbar);
 }
@@ -381,6 +395,8 @@ void launch_scatter_fixed(const Grid& g, int order, const float* yv, const float
     const size_t smem = kScatterCap * sizeof(unsigned long long);
     if (order == 3)
         k_scatter_tiled<3><<<grid, kThreads, smem, st>>>(g, yv, d, v, sdt, maxabs, acc);
+    else if (order == 4)
+        k_scatter_tiled<4><<<grid, kThreads, smem, st>>>(g, yv, d, v, sdt, maxabs, acc);
     else
         k_scatter_tiled<1><<<grid, kThreads, smem, st>>>(g, yv, d, v, sdt, maxabs, acc);
 }
@@ -391,13 +407,20 @@ void launch_fixed_to_float(unsigned long long* acc, const double* maxabs, int ac
     k_fixed_to_float<<<blocks_for(n), kThreads, 0, st>>>(acc, maxabs, accumulate, mult, out, n);
 }
 
-void launch_predictor_terms(const Grid& g, int order, const float* v, float dt, const float* dbar, float* ubar,
-                            float* Ubar, cudaStream_t st)
+void launch_predictor_terms(const Grid& g, int order, const float* v, const float* vc, float dt, const float* dbar,
+                            float* ubar, float* Ubar, cudaStream_t st)
 {
     if (order == 3)
-        k_predictor_terms<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, dt, dbar, ubar, Ubar);
+        k_predictor_terms<3><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, vc, dt, dbar, ubar, Ubar);
+    else if (order == 4)
+        k_predictor_terms<4><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, vc, dt, dbar, ubar, Ubar);
     else
-        k_predictor_terms<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, dt, dbar, ubar, Ubar);
+        k_predictor_terms<1><<<blocks_for(g.N), kThreads, 0, st>>>(g, v, vc, dt, dbar, ubar, Ubar);
+}
+
+void launch_scale_add(float* y, float a, const float* x, size_t n, cudaStream_t st)
+{
+    k_scale_add<<<blocks_for(n), kThreads, 0, st>>>(y, a, x, n);
 }
 
 void launch_maxabs(const float* x, size_t n, double* partials, int nblocks, double* out2, cudaStream_t st)

@@ -11,7 +11,9 @@ Tolerances: the image cotangent is nt scatter transposes of FP32 weights
 (each output a sum of <= 64 FP32 products, summed exactly in 64-bit fixed
 point): relative L2 1e-5.  The velocity cotangent adds the interpolant
 gradient of each state (64-term FP32 sums of derivative weights) times the
-cotangent and the predictor terms: relative L2 1e-4.
+cotangent and the predictor terms: relative L2 1e-4.  Cubic B-splines add one
+FP32 prefilter (a forward and an inverse transform, symbol at most 27) per
+step and per predictor component, which stays within the same bounds.
 """
 import numpy as np
 import pytest
@@ -61,7 +63,10 @@ def inputs(n, seed, vmax=1.0):
     return f32(m0), f32(v), f32(gbar)
 
 
-@pytest.mark.parametrize("order", [3, 1])
+TOL = {3: (1e-5, 1e-4), 1: (1e-5, 1e-4), 4: (1e-5, 1e-4)}
+
+
+@pytest.mark.parametrize("order", [3, 1, 4])
 @pytest.mark.parametrize("n", [(32, 32, 32), (40, 36, 30), (16, 24, 8)])
 def test_vjp_matches_oracle(env, n, order):
     torch, claire = env
@@ -75,8 +80,8 @@ def test_vjp_matches_oracle(env, n, order):
     rm0, rv = oracle.transport_vjp(m0, v, gbar, oracle.Params(nt=nt, order=order))
     e_m, e_v = rel_l2(host(gm0), rm0), rel_l2(host(gv), rv)
     print("order %d grid %s: gm0 rel L2 %.2e, gv rel L2 %.2e" % (order, n, e_m, e_v))
-    assert e_m < 1e-5
-    assert e_v < 1e-4
+    assert e_m < TOL[order][0]
+    assert e_v < TOL[order][1]
 
 
 def test_vjp_bitwise_deterministic_and_checkpointing(env):
@@ -99,7 +104,7 @@ def test_vjp_bitwise_deterministic_and_checkpointing(env):
         assert torch.equal(b, outs[0][1])
 
 
-@pytest.mark.parametrize("order", [3, 1])
+@pytest.mark.parametrize("order", [3, 1, 4])
 def test_vjp_finite_differences_of_gpu_forward(env, order):
     """Directional derivatives of the mismatch L(m0, v) = 1/2 |m(1) - m1|^2
     (gbar = m(1) - m1) agree with central differences of the GPU forward

@@ -76,6 +76,7 @@ struct TwoLevel {
     cufftComplex *xh = nullptr, *rh = nullptr, *zh = nullptr, *ph = nullptr, *cp = nullptr, *q = nullptr,
                  *T = nullptr;  // 3 Mc each
     cufftComplex* zf = nullptr;  // 3 M (fine): the stored preconditioned residual
+    double* sc = nullptr;        // kTlSlots FP64 scalars of the inner PCG (device)
     ~TwoLevel()
     {
         if (plans) {
@@ -912,7 +913,7 @@ claire_status tl_ensure(claire_ctx* c)
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t realb = up(3 * t->N * sizeof(float)), specb = up(3 * t->M * sizeof(cufftComplex)),
                  fineb = up(3 * c->M * sizeof(cufftComplex));
-    const size_t total = 2 * realb + 7 * specb + fineb;
+    const size_t total = 2 * realb + 7 * specb + fineb + up(kTlSlots * sizeof(double));
     if (cudaMalloc(&t->block, total) != cudaSuccess) {
         cudaGetLastError();
         t->block = nullptr;
@@ -928,6 +929,8 @@ claire_status tl_ensure(claire_ctx* c)
         b += specb;
     }
     t->zf = reinterpret_cast<cufftComplex*>(b);
+    b += fineb;
+    t->sc = reinterpret_cast<double*>(b);
     size_t ws1 = 0, ws2 = 0;
     cufftResult fr = cufftCreate(&t->r2c);
     if (fr == CUFFT_SUCCESS) {
@@ -1011,7 +1014,10 @@ claire_status tl_apply(claire_ctx* c, const cufftComplex* rf, cufftComplex* zf, 
     }
     CL_TRY(fs_sums(c, 2));
     const double r0 = std::sqrt(c->hres[0]);
-    double rzi = c->hres[1];
+    // rz stays on the device: alpha and beta are formed there (FP64, as the host
+    // would), so an iteration reads back only |r|^2 and the breakdown flag
+    CL_CUDA(c, cudaMemcpyAsync(t->sc + kTlRz, c->dres + 1, sizeof(double), cudaMemcpyDeviceToDevice, c->stream));
+    const double scale = c->hvol * static_cast<double>(c->N);  // Parseval on scaled spectra, as fs_sums
     for (int it = 1; r0 > 0.0 && it <= c->o.pc_maxit; ++it) {
         {
             KTimer kt(c, KK_FFT, 0, 0);
@@ -1027,30 +1033,37 @@ claire_status tl_apply(claire_ctx* c, const cufftComplex* rf, cufftComplex* zf, 
             CL_FFT(c, cufftExecR2C(t->r2c, t->real, t->T));
         }
         {
-            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0, 1);
+            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0, 3);
             launch_tl_hp(t->g, t->T, t->ph, t->q, t->M, c->o.grad_form, c->rp, static_cast<float>(1.0 / t->N),
                          c->partials, rb, c->stream);
-        }
-        CL_TRY(fs_sums(c, 1));
-        const double pq = c->hres[0];
-        *its = it;
-        if (pq <= 0.0) break;
-        const double alpha = rzi / pq;
-        {
-            KTimer kt(c, KK_SPECTRAL, 144.0 * t->M, 0, 2);
-            launch_tl_update(t->g, t->ph, t->q, t->xh, t->rh, t->zh, t->M, static_cast<float>(alpha), op, c->rp,
-                             c->partials, c->partials + rb, rb, c->stream);
-        }
-        CL_TRY(fs_sums(c, 2));
-        if (c->o.pc_tol > 0 && std::sqrt(c->hres[0]) <= c->o.pc_tol * r0) break;
-        if (it == c->o.pc_maxit) break;
-        const double rz_new = c->hres[1];
-        {
-            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0);
-            launch_dir_stored(t->g, t->zh, t->ph, t->cp, t->M, static_cast<float>(rz_new / rzi), 0, c->stream);
+            launch_final_sum(c->partials, rb, scale, t->sc + kTlPq, c->stream);
+            launch_tl_scalars(t->sc, 0, c->stream);
             CL_LAUNCHED(c);
         }
-        rzi = rz_new;
+        {
+            KTimer kt(c, KK_SPECTRAL, 144.0 * t->M, 0, 4);
+            launch_tl_update(t->g, t->ph, t->q, t->xh, t->rh, t->zh, t->M, t->sc + kTlAlpha, op, c->rp,
+                             c->partials, c->partials + rb, rb, c->stream);
+            launch_final_sum(c->partials, rb, scale, t->sc + kTlRr, c->stream);
+            launch_final_sum(c->partials + rb, rb, scale, t->sc + kTlRzNew, c->stream);
+            CL_LAUNCHED(c);
+        }
+        CL_CUDA(c, cudaMemcpyAsync(c->hres + 8, t->sc + kTlRr, 2 * sizeof(double), cudaMemcpyDeviceToHost,
+                                   c->stream));
+        CL_CUDA(c, cudaStreamSynchronize(c->stream));
+        const double rr = c->hres[8], flag = c->hres[9];
+        *its = it;
+        if (flag == 2.0) return fail(c, CLAIRE_ENONFINITE, "non-finite inner PCG curvature");
+        if (flag != 0.0) break;  // pq <= 0: the update above ran with alpha = 0
+        if (!std::isfinite(rr)) return fail(c, CLAIRE_ENONFINITE, "non-finite inner PCG residual");
+        if (c->o.pc_tol > 0 && std::sqrt(rr) <= c->o.pc_tol * r0) break;
+        if (it == c->o.pc_maxit) break;
+        {
+            KTimer kt(c, KK_SPECTRAL, 72.0 * t->M, 0, 2);
+            launch_tl_scalars(t->sc, 1, c->stream);
+            launch_dir_stored(t->g, t->zh, t->ph, t->cp, t->M, 0.0f, 0, c->stream, t->sc + kTlBeta);
+            CL_LAUNCHED(c);
+        }
     }
     {
         KTimer kt(c, KK_SPECTRAL, (zold ? 72.0 : 48.0) * c->M, 0, 2);

@@ -197,11 +197,16 @@ void launch_tl_start(const Grid& gf, const cufftComplex* rf, size_t csf, const G
 void launch_tl_rank1(const float* gbar, float* p, size_t Nc, cudaStream_t st);
 void launch_tl_hp(const Grid& gc, const cufftComplex* T, const cufftComplex* ph, cufftComplex* q, size_t cs,
                   int kform, RegParams rp, float scale, double* ppq, int nblocks, cudaStream_t st);
+// Device scalars of the inner PCG (slots of a small FP64 array)
+constexpr int kTlRz = 0, kTlPq = 1, kTlAlpha = 2, kTlRr = 3, kTlFlag = 4, kTlRzNew = 5, kTlBeta = 6, kTlSlots = 8;
+// stage 0: alpha = rz / pq (0 and the breakdown flag when pq <= 0); stage 1: beta = rz_new / rz, rz <- rz_new
+void launch_tl_scalars(double* s, int stage, cudaStream_t st);
 void launch_tl_update(const Grid& gc, const cufftComplex* ph, const cufftComplex* q, cufftComplex* xh,
-                      cufftComplex* rh, cufftComplex* zh, size_t cs, float alpha, SpectralOp op, RegParams rp,
-                      double* prr, double* prz, int nblocks, cudaStream_t st);
+                      cufftComplex* rh, cufftComplex* zh, size_t cs, const double* alpha_dev, SpectralOp op,
+                      RegParams rp, double* prr, double* prz, int nblocks, cudaStream_t st);
+// beta from beta_dev when it is not null, else the host value
 void launch_dir_stored(const Grid& g, const cufftComplex* zh, cufftComplex* ph, cufftComplex* cp, size_t cs,
-                       float beta, int first, cudaStream_t st);
+                       float beta, int first, cudaStream_t st, const double* beta_dev = nullptr);
 void launch_tl_finish(const Grid& gf, const cufftComplex* rf, cufftComplex* zf, const cufftComplex* zold, size_t csf,
                       const Grid& gc, const cufftComplex* xc, size_t csc, SpectralOp op, RegParams rp, double* prz,
                       double* pro, int nblocks, cudaStream_t st);

@@ -721,12 +721,29 @@ __global__ void __launch_bounds__(kThreads) k_tl_hp(Grid gc, const float2* __res
 }
 
 // x += alpha p, r -= alpha q, z = M r (stored); partials of |r|^2 and <r, z>.
+// Scalars of the inner PCG kept on the device (slots of TlScalar): after the
+// curvature pq (stage 0) alpha = rz / pq, or 0 with the breakdown flag set
+// when pq <= 0 (1) or NaN (2); before the direction update (stage 1) beta = rz_new / rz and
+// rz <- rz_new.  FP64 divisions, as the host would do them.
+__global__ void k_tl_scalars(double* __restrict__ s, int stage)
+{
+    if (stage == 0) {
+        const double pq = s[kTlPq];
+        s[kTlAlpha] = pq > 0.0 ? s[kTlRz] / pq : 0.0;
+        s[kTlFlag] = pq > 0.0 ? 0.0 : (pq == pq ? 1.0 : 2.0);  // 2: pq is NaN
+    } else {
+        s[kTlBeta] = s[kTlRzNew] / s[kTlRz];
+        s[kTlRz] = s[kTlRzNew];
+    }
+}
+
 __global__ void __launch_bounds__(kThreads) k_tl_update(Grid gc, const float2* __restrict__ ph,
                                                          const float2* __restrict__ q, float2* __restrict__ xh,
                                                          float2* __restrict__ rh, float2* __restrict__ zh, size_t cs,
-                                                         float alpha, int op, RegParams rp,
+                                                         const double* __restrict__ alpha_dev, int op, RegParams rp,
                                                          double* __restrict__ prr, double* __restrict__ prz)
 {
+    const float alpha = static_cast<float>(*alpha_dev);
     const int n3h = gc.n3 / 2 + 1;
     const size_t Mc = static_cast<size_t>(gc.n1) * gc.n2 * n3h;
     double arr = 0.0, arz = 0.0;
@@ -757,8 +774,10 @@ __global__ void __launch_bounds__(kThreads) k_tl_update(Grid gc, const float2* _
 // on any grid (the inner PCG, and the outer PCG when z is stored).
 __global__ void __launch_bounds__(kThreads) k_dir_stored(Grid g, const float2* __restrict__ zh,
                                                           float2* __restrict__ ph, float2* __restrict__ cp, size_t cs,
-                                                          float beta, int first)
+                                                          float beta_host, const double* __restrict__ beta_dev,
+                                                          int first)
 {
+    const float beta = beta_dev ? static_cast<float>(*beta_dev) : beta_host;
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
     for (size_t idx = blockIdx.x * static_cast<size_t>(kThreads) + threadIdx.x; idx < M;
          idx += static_cast<size_t>(gridDim.x) * kThreads) {
@@ -911,22 +930,27 @@ void launch_tl_hp(const Grid& gc, const cufftComplex* T, const cufftComplex* ph,
 }
 
 void launch_tl_update(const Grid& gc, const cufftComplex* ph, const cufftComplex* q, cufftComplex* xh,
-                      cufftComplex* rh, cufftComplex* zh, size_t cs, float alpha, SpectralOp op, RegParams rp,
-                      double* prr, double* prz, int nblocks, cudaStream_t st)
+                      cufftComplex* rh, cufftComplex* zh, size_t cs, const double* alpha_dev, SpectralOp op,
+                      RegParams rp, double* prr, double* prz, int nblocks, cudaStream_t st)
 {
     k_tl_update<<<nblocks, kThreads, 0, st>>>(gc, reinterpret_cast<const float2*>(ph),
                                               reinterpret_cast<const float2*>(q), reinterpret_cast<float2*>(xh),
-                                              reinterpret_cast<float2*>(rh), reinterpret_cast<float2*>(zh), cs, alpha,
-                                              static_cast<int>(op), rp, prr, prz);
+                                              reinterpret_cast<float2*>(rh), reinterpret_cast<float2*>(zh), cs,
+                                              alpha_dev, static_cast<int>(op), rp, prr, prz);
+}
+
+void launch_tl_scalars(double* s, int stage, cudaStream_t st)
+{
+    k_tl_scalars<<<1, 1, 0, st>>>(s, stage);
 }
 
 void launch_dir_stored(const Grid& g, const cufftComplex* zh, cufftComplex* ph, cufftComplex* cp, size_t cs,
-                       float beta, int first, cudaStream_t st)
+                       float beta, int first, cudaStream_t st, const double* beta_dev)
 {
     const size_t M = static_cast<size_t>(g.n1) * g.n2 * (g.n3 / 2 + 1);
     k_dir_stored<<<stream_blocks(M), kThreads, 0, st>>>(g, reinterpret_cast<const float2*>(zh),
                                                         reinterpret_cast<float2*>(ph), reinterpret_cast<float2*>(cp),
-                                                        cs, beta, first);
+                                                        cs, beta, beta_dev, first);
 }
 
 void launch_tl_finish(const Grid& gf, const cufftComplex* rf, cufftComplex* zf, const cufftComplex* zold, size_t csf,

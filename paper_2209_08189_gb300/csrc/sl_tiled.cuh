@@ -36,7 +36,11 @@ namespace claire {
 #define CLAIRE_BOX_CAP 11776  // floats of dynamic shared memory per CTA (46 KB)
 #endif
 
-constexpr int TILE1 = CLAIRE_TILE1, TILE2 = 8, TILE3 = 32;
+#ifndef CLAIRE_TILE2
+#define CLAIRE_TILE2 8  // x2 rows per tile: one warp each
+#endif
+
+constexpr int TILE1 = CLAIRE_TILE1, TILE2 = CLAIRE_TILE2, TILE3 = 32;
 
 // CTAs of the tiled gathers (in this translation unit) whose box did not fit
 // and which took the global-memory path; one atomic per such CTA, read by

@@ -119,6 +119,9 @@ struct claire_ctx {
     char *m0 = nullptr, *m1 = nullptr;
     float *v = nullptr;                   // linearisation point
     float *dS = nullptr, *dA = nullptr;   // state / adjoint characteristics
+    // their tile-bounds tables, written by every backtrace into dS / dA (the
+    // only writer of either field), read by the gathers at dS / dA
+    int4 *tbS = nullptr, *tbA = nullptr;
     char *divv = nullptr, *divXp = nullptr;
     char *m = nullptr, *gm = nullptr;     // (nt+1) N states m^j, (nt+1) 3N gradients (null when lowmem)
     char *l0 = nullptr, *l1 = nullptr;    // rolling scalar fields (FP32-sized: transport uses them as FP32)
@@ -358,6 +361,8 @@ size_t layout_floats(size_t N, size_t M, int nt, int red_blocks, size_t es, bool
     l.add(6 * M);             // rh
     l.add(4 * red_blocks);    // partials (2 * red_blocks doubles)
     l.add(32);                // dres (16 doubles)
+    l.add(8 * ((N + 1023) / 1024));  // tbS (2 int4 per 1024-point tile)
+    l.add(8 * ((N + 1023) / 1024));  // tbA
     return l.total;
 }
 
@@ -593,13 +598,19 @@ claire_status gather_src(claire_ctx* c, const void* f, int ncomp, const void** s
     return CLAIRE_OK;
 }
 
+// tile-bounds table of a displacement field of the context (null for others)
+int4* tile_table(claire_ctx* c, const float* d)
+{
+    return d == c->dS ? c->tbS : (d == c->dA ? c->tbA : nullptr);
+}
+
 claire_status backtrace(claire_ctx* c, const float* v, float* d, int sign)
 {
     const void* vc;
     CL_TRY(gather_src(c, v, 3, &vc));
     KTimer t(c, KK_BACKTRACE, 24.0 * c->N, 3.0 * c->N);
     launch_backtrace(c->grid, c->o.interp, v, static_cast<const float*>(vc), static_cast<float>(c->dt), sign, d,
-                     c->stream);
+                     c->stream, tile_table(c, d));
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
@@ -609,7 +620,7 @@ claire_status interp(claire_ctx* c, const void* f, const float* d, void* out, St
     const void* src;
     CL_TRY(gather_src(c, f, 1, &src));
     KTimer t(c, KK_INTERP, (12.0 + 2.0 * storage_bytes(sto)) * c->N, 1.0 * c->N);
-    launch_interp(c->grid, c->o.interp, src, d, out, sto, c->stream);
+    launch_interp(c->grid, c->o.interp, src, d, out, sto, c->stream, tile_table(c, d));
     CL_LAUNCHED(c);
     return CLAIRE_OK;
 }
@@ -680,7 +691,7 @@ claire_status adjoint_and_body(claire_ctx* c, const void* a, const void* s, floa
         CL_TRY(gather_src(c, at(c, c->tl, (j + 1) * N), 1, &src));
         KTimer t(c, KK_ADJ_STEP, (12.0 + 4.0 * es) * N, 1.0 * N);
         launch_adj_step(c->grid, c->o.interp, src, c->dA, c->divv, c->divXp,
-                        static_cast<float>(c->dt), at(c, c->tl, j * N), c->sto, c->stream);
+                        static_cast<float>(c->dt), at(c, c->tl, j * N), c->sto, c->stream, c->tbA);
         CL_LAUNCHED(c);
     }
     {
@@ -758,7 +769,7 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
             CL_TRY(gather_src(c, a, 1, &src));
             KTimer t(c, KK_INC_STEP, (12.0 + 3.0 * es) * N, 1.0 * N);
             launch_inc_step_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
-                                c->stream);
+                                c->stream, c->tbS);
             CL_LAUNCHED(c);
             std::swap(a, b);
         }
@@ -766,7 +777,7 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
         CL_TRY(gather_src(c, a, 1, &src));
         KTimer t(c, KK_INC_LAST, (12.0 + 3.0 * es) * N, 1.0 * N);
         launch_inc_last_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
-                            at(c, c->tl, nt * N), c->sto, c->stream);
+                            at(c, c->tl, nt * N), c->sto, c->stream, c->tbS);
         CL_LAUNCHED(c);
     }
     // incremental adjoint from lt^{nt} and body, accumulated onto S vt in out
@@ -1379,6 +1390,8 @@ claire_status claire_create(claire_ctx** out, const int grid[3], double beta_v, 
     c->rh = reinterpret_cast<cufftComplex*>(base + L.off[k++]);
     c->partials = reinterpret_cast<double*>(base + L.off[k++]);
     c->dres = reinterpret_cast<double*>(base + L.off[k++]);
+    c->tbS = reinterpret_cast<int4*>(base + L.off[k++]);
+    c->tbA = reinterpret_cast<int4*>(base + L.off[k++]);
     if (cudaMemset(c->dres, 0, 16 * sizeof(double)) != cudaSuccess) {
         cudaGetLastError();
         return bail(CLAIRE_ECUDA);

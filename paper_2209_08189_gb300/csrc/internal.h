@@ -80,18 +80,23 @@ __device__ __forceinline__ void block_minmax(double lo, double hi, double* pmin,
 // Pointers typed void* hold scalar fields in the storage type `sto` (FP32,
 // FP16 or BF16); float* ones are always FP32 (displacements, velocities,
 // vector work fields).
+// tb: the tile-bounds table of d written by launch_backtrace (or null: the
+// gathers reduce the bounds themselves); used on grids the tiles cover exactly
 void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
-                   cudaStream_t st);
+                   cudaStream_t st, const int4* tb = nullptr);
 // nf FP32 fields [nf][N] at one displacement into out [nf][N]
 void launch_interp_fields(const Grid& g, int order, const float* f, int nf, const float* d, float* out,
                           cudaStream_t st);
 // CTAs of the tiled gathers that took the global-memory path (device-wide counter)
 cudaError_t gather_fallback_tiles(unsigned long long* count, bool reset);
+// tb (may be null): also write the tile-bounds table of d (2 int4 per tile of
+// the tiled grid) on grids the tiles cover exactly
 void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
-                      cudaStream_t st);
+                      cudaStream_t st, int4* tb = nullptr);
 // One SL step of Eq. (4): lam = Heun(lam_next(X+), div v(X+), div v).
 void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
-                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st);
+                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st,
+                     const int4* tb = nullptr);
 // f^j = -vt . grad m^j for j = 0..nt: q0 = coef0 f^0, F + j N <- f^j (j >= 1).
 void launch_inc_sources(const Grid& g, const float* vt, const void* gm, int nt, float coef0, void* q0,
                         void* F, Storage sto, cudaStream_t st);
@@ -105,9 +110,9 @@ void launch_body(const Grid& g, const void* lam, const void* gm, int nt, float w
                  int accumulate, float* out, Storage sto, cudaStream_t st);
 // q = q_prev(X) + coef F;   lam = -(q_prev(X) + coef F)  (F may alias lam)
 void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
-                         float coef, void* q, Storage sto, cudaStream_t st);
+                         float coef, void* q, Storage sto, cudaStream_t st, const int4* tb = nullptr);
 void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
-                         float coef, void* lam, Storage sto, cudaStream_t st);
+                         float coef, void* lam, Storage sto, cudaStream_t st, const int4* tb = nullptr);
 // out = a - b; conversions FP32 <-> storage
 void launch_sub(const void* a, const void* b, void* out, size_t n, Storage sto, cudaStream_t st);
 void launch_to_storage(const float* in, void* out, size_t n, Storage sto, cudaStream_t st);

@@ -24,11 +24,13 @@ inline unsigned blocks_for(uint32_t n) { return (n + kThreads - 1) / kThreads; }
 // sign = -1 gives X+ = x + dt/2 [v(x) + v(x + dt v(x))]; d in grid units.
 // The three velocity gathers at the predictor point are served from a
 // shared-memory box per 4 x 8 x 32 tile (one box, staged once per component;
-// the predictor points of a tile share its bounds).
-template <int ORDER, bool FULL>
+// the predictor points of a tile share its bounds).  TBW (grids the tiles
+// cover exactly): also write the tile-bounds table of d (tile_index order),
+// from the same FP32 values that are stored, for the gathers at d.
+template <int ORDER, bool FULL, bool TBW>
 __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     k_backtrace_tiled(Grid g, const float* __restrict__ v, const float* __restrict__ vc, float dt, float sign,
-                      float* __restrict__ d)
+                      float* __restrict__ d, int4* __restrict__ tb)
 {
     extern __shared__ float box[];
     __shared__ int red[6][TILE2];
@@ -63,6 +65,9 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     const bool use_box = bp.E1 != 0;
     if (!use_box && threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
     const float cc = -0.5f * sdt;
+    // bounds of the characteristic itself (TBW)
+    int lo[3] = {INT_MAX, INT_MAX, INT_MAX}, hi[3] = {INT_MIN, INT_MIN, INT_MIN};
+    bool dbad = false;
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
         const float* f = vc + c * N;
@@ -81,30 +86,45 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
                                   : gather_global<ORDER, float>(g, f, i, j, k, -sdt * u1[q], -sdt * u2[q],
                                                                 -sdt * u3[q]);
             const float uc = c == 0 ? u1[q] : (c == 1 ? u2[q] : u3[q]);
-            d[c * N + p0 + q * g.n23] = cc * (uc + vsq * ih);
+            const float dc = cc * (uc + vsq * ih);
+            d[c * N + p0 + q * g.n23] = dc;
+            if constexpr (TBW) bounds_add(c == 0 ? i : (c == 1 ? j : k), dc, lo[c], hi[c], dbad);
         }
         if (use_box) __syncthreads();  // every read of this component is done before the next staging
     }
+    if constexpr (TBW) {
+        static_assert(FULL, "tile-bounds tables cover exactly tiled grids only");
+        int b[6];
+        const bool any_bad = tile_bounds(lo[0], lo[1], lo[2], hi[0], hi[1], hi[2], dbad, red, lane, warp, b);
+        if (threadIdx.x == 0) {
+            const unsigned t = tile_index();
+            tb[2 * t] = make_int4(b[0], b[1], b[2], any_bad ? 1 : 0);
+            tb[2 * t + 1] = make_int4(b[3], b[4], b[5], 0);
+        }
+    }
 }
 
-template <int ORDER, bool FULL>
+template <int ORDER, bool FULL, bool TBW>
 void launch_backtrace_tiled_as(const Grid& g, const float* v, const float* vc, float dt, float sign, float* d,
-                               cudaStream_t st)
+                               int4* tb, cudaStream_t st)
 {
     if (kTiledSmemBytes > 48 * 1024)
-        cudaFuncSetAttribute(k_backtrace_tiled<ORDER, FULL>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+        cudaFuncSetAttribute(k_backtrace_tiled<ORDER, FULL, TBW>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                              static_cast<int>(kTiledSmemBytes));
-    k_backtrace_tiled<ORDER, FULL><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, v, vc, dt, sign, d);
+    k_backtrace_tiled<ORDER, FULL, TBW><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, v, vc, dt, sign,
+                                                                                              d, tb);
 }
 
 template <int ORDER>
 void launch_backtrace_tiled(const Grid& g, const float* v, const float* vc, float dt, float sign, float* d,
-                            cudaStream_t st)
+                            int4* tb, cudaStream_t st)
 {
-    if (tiles_cover_grid(g))
-        launch_backtrace_tiled_as<ORDER, true>(g, v, vc, dt, sign, d, st);
+    if (tiles_cover_grid(g) && tb)
+        launch_backtrace_tiled_as<ORDER, true, true>(g, v, vc, dt, sign, d, tb, st);
+    else if (tiles_cover_grid(g))
+        launch_backtrace_tiled_as<ORDER, true, false>(g, v, vc, dt, sign, d, nullptr, st);
     else
-        launch_backtrace_tiled_as<ORDER, false>(g, v, vc, dt, sign, d, st);
+        launch_backtrace_tiled_as<ORDER, false, false>(g, v, vc, dt, sign, d, nullptr, st);
 }
 
 // Sources of the incremental state for every time level at once:
@@ -364,15 +384,15 @@ __global__ void __launch_bounds__(kThreads) k_detj_minmax(Grid g, const float* _
 #define CLAIRE_TILED(order, EPI, fs, d, e)                                        \
     do {                                                                          \
         if ((order) == 3)                                                         \
-            launch_tiled<3, EPI<SType>, SType>(g, fs, d, e, st);                  \
+            launch_tiled<3, EPI<SType>, SType>(g, fs, d, e, st, tb);              \
         else if ((order) == 1)                                                    \
-            launch_tiled<1, EPI<SType>, SType>(g, fs, d, e, st);                  \
+            launch_tiled<1, EPI<SType>, SType>(g, fs, d, e, st, tb);              \
         else if constexpr (std::is_same<SType, float>::value)                     \
-            launch_tiled<4, EPI<SType>, SType>(g, fs, d, e, st);                  \
+            launch_tiled<4, EPI<SType>, SType>(g, fs, d, e, st, tb);              \
     } while (0)
 
 void launch_interp(const Grid& g, int order, const void* f, const float* d, void* out, Storage sto,
-                   cudaStream_t st)
+                   cudaStream_t st, const int4* tb)
 {
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiStore<SType> e{static_cast<SType*>(out)};
@@ -417,20 +437,20 @@ cudaError_t gather_fallback_tiles(unsigned long long* count, bool reset)
 }
 
 void launch_backtrace(const Grid& g, int order, const float* v, const float* vc, float dt, int sign, float* d,
-                      cudaStream_t st)
+                      cudaStream_t st, int4* tb)
 {
     const float* f = vc ? vc : v;
     const float sg = static_cast<float>(sign);
     if (order == 3)
-        launch_backtrace_tiled<3>(g, v, f, dt, sg, d, st);
+        launch_backtrace_tiled<3>(g, v, f, dt, sg, d, tb, st);
     else if (order == 4)
-        launch_backtrace_tiled<4>(g, v, f, dt, sg, d, st);
+        launch_backtrace_tiled<4>(g, v, f, dt, sg, d, tb, st);
     else
-        launch_backtrace_tiled<1>(g, v, f, dt, sg, d, st);
+        launch_backtrace_tiled<1>(g, v, f, dt, sg, d, tb, st);
 }
 
 void launch_adj_step(const Grid& g, int order, const void* lam_next, const float* dA, const void* divv,
-                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st)
+                     const void* divXp, float dt, void* lam, Storage sto, cudaStream_t st, const int4* tb)
 {
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiAdjointOnly<SType> e{static_cast<const SType*>(divv), static_cast<const SType*>(divXp),
@@ -479,7 +499,7 @@ void launch_body(const Grid& g, const void* lam, const void* gm, int nt, float w
 }
 
 void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
-                         float coef, void* q, Storage sto, cudaStream_t st)
+                         float coef, void* q, Storage sto, cudaStream_t st, const int4* tb)
 {
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiIncSource<SType> e{static_cast<const SType*>(F), static_cast<SType*>(q), coef};
@@ -489,7 +509,7 @@ void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const flo
 }
 
 void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
-                         float coef, void* lam, Storage sto, cudaStream_t st)
+                         float coef, void* lam, Storage sto, cudaStream_t st, const int4* tb)
 {
     CLAIRE_STORAGE_DISPATCH(sto, {
         EpiIncSourceLast<SType> e{static_cast<const SType*>(F), static_cast<SType*>(lam), coef};

@@ -91,9 +91,10 @@ struct BoxPar {
 // (before the -OFF shift) of a tile's stencils: par[0..2] the first node
 // (unwrapped grid coordinates), par[3..5] the extents and par[6] the row
 // stride, with par[3..6] = 0 when the box does not fit the shared-memory cap
-// or the grid, or when `bad` says that a displacement of the tile failed
-// disp_ok (non-finite or at least 2^20 cells).  Such a tile is gathered from
-// global memory with the clamped split, whose indices always wrap into range.
+// or the grid, when the bounds are not ordered (z < a), or when `bad` says
+// that a displacement of the tile failed disp_ok (non-finite or at least 2^20
+// cells).  Such a tile is gathered from global memory with the clamped split,
+// whose indices always wrap into range.
 // ES: bytes per stored value of the field (4, or 2 for FP16 / BF16 storage,
 // whose box is staged as raw 16-bit pairs before widening to FP32).
 template <int ORDER, int ES = 4>
@@ -123,7 +124,8 @@ __host__ __device__ __forceinline__ void box_geometry(const Grid& g, int a1, int
     const long long s3 = (e3 + 31) / 32 * 32;  // bank-aligned row stride
     // FP32 box plus, for 16-bit storage, the staging copy (half its size)
     const long long need = e1 * e2 * s3 * (ES == 2 ? 3 : 2) / 2;
-    const bool fits = !bad && e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 && need <= kBoxCapFloats;
+    const bool fits = !bad && e1 >= M && e2 >= M && e3 >= M && e1 <= g.n1 && e2 <= g.n2 && e3 <= g.n3 &&
+                      need <= kBoxCapFloats;
     par[0] = fits ? a1 - OFF : 0;
     par[1] = fits ? a2 - OFF : 0;
     par[2] = fits ? static_cast<int>(o3) : 0;
@@ -151,11 +153,11 @@ __host__ __device__ __forceinline__ void bounds_add(int node, float d, int& lo, 
 }
 
 #ifdef __CUDACC__
-// Block-wide bounds of the stencils whose first-node cells span [lo, hi] per
-// axis, and the vote on `bad` (any thread); thread 0 publishes the box in par.
-template <int ORDER, int ES = 4>
-__device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
-                                           int hi3, bool bad, int (*red)[TILE2], int* par, int lane, int warp)
+// Block-wide bounds of the first-node cells [lo, hi] per axis and the vote on
+// `bad` (any thread).  Thread 0 gets the tile's bounds in b = (a1, a2, a3, z1,
+// z2, z3); every thread gets the vote.
+__device__ __forceinline__ bool tile_bounds(int lo1, int lo2, int lo3, int hi1, int hi2, int hi3, bool bad,
+                                            int (*red)[TILE2], int lane, int warp, int b[6])
 {
     lo1 = __reduce_min_sync(0xffffffffu, lo1);
     lo2 = __reduce_min_sync(0xffffffffu, lo2);
@@ -169,19 +171,41 @@ __device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int 
     }
     const bool any_bad = __syncthreads_or(bad) != 0;
     if (threadIdx.x == 0) {
-        int a1 = INT_MAX, a2 = INT_MAX, a3 = INT_MAX, z1 = INT_MIN, z2 = INT_MIN, z3 = INT_MIN;
+        b[0] = b[1] = b[2] = INT_MAX;
+        b[3] = b[4] = b[5] = INT_MIN;
 #pragma unroll
         for (int w = 0; w < TILE2; ++w) {
-            a1 = min(a1, red[0][w]); a2 = min(a2, red[1][w]); a3 = min(a3, red[2][w]);
-            z1 = max(z1, red[3][w]); z2 = max(z2, red[4][w]); z3 = max(z3, red[5][w]);
+            b[0] = min(b[0], red[0][w]); b[1] = min(b[1], red[1][w]); b[2] = min(b[2], red[2][w]);
+            b[3] = max(b[3], red[3][w]); b[4] = max(b[4], red[4][w]); b[5] = max(b[5], red[5][w]);
         }
-        box_geometry<ORDER, ES>(g, a1, a2, a3, z1, z2, z3, any_bad, par);
     }
+    return any_bad;
+}
+
+// Block-wide box of the stencils whose first-node cells span [lo, hi] per
+// axis, with the vote on `bad`; thread 0 publishes the box in par.
+template <int ORDER, int ES = 4>
+__device__ __forceinline__ BoxPar tile_box(const Grid& g, int lo1, int lo2, int lo3, int hi1, int hi2,
+                                           int hi3, bool bad, int (*red)[TILE2], int* par, int lane, int warp)
+{
+    int b[6];
+    const bool any_bad = tile_bounds(lo1, lo2, lo3, hi1, hi2, hi3, bad, red, lane, warp, b);
+    if (threadIdx.x == 0) box_geometry<ORDER, ES>(g, b[0], b[1], b[2], b[3], b[4], b[5], any_bad, par);
     __syncthreads();
-    BoxPar b;
-    b.O1 = par[0]; b.O2 = par[1]; b.O3 = par[2];
-    b.E1 = par[3]; b.E2 = par[4]; b.E3 = par[5]; b.S3 = par[6];
-    return b;
+    BoxPar bp;
+    bp.O1 = par[0]; bp.O2 = par[1]; bp.O3 = par[2];
+    bp.E1 = par[3]; bp.E2 = par[4]; bp.E3 = par[5]; bp.S3 = par[6];
+    return bp;
+}
+
+// Tile-bounds table of a displacement field, written by the backtrace that
+// produced the field: entry t (the CTA index of the tiled grid, x fastest) is
+// tb[2t] = (a1, a2, a3, bad) and tb[2t + 1] = (z1, z2, z3, 0), the first-node
+// cell bounds of the tile's points (before the -OFF shift) and whether a
+// displacement failed disp_ok.  Only for grids the tiles cover exactly.
+__device__ __forceinline__ unsigned tile_index()
+{
+    return (blockIdx.z * gridDim.y + blockIdx.y) * gridDim.x + blockIdx.x;
 }
 #endif
 
@@ -351,13 +375,16 @@ __device__ __forceinline__ float row_dot(uint32_t addr, const float w[4])
 
 // Split of a displacement inside a fitting box: floor and fraction.  Every
 // displacement of a tile whose box fits passed disp_ok (finite, |d| < 2^20),
-// where this floor equals the clamped split of the bounds pass.
+// where this floor equals the clamped split of the bounds pass; with a box
+// from a tile-bounds table, every point also passed in_box.
 __host__ __device__ __forceinline__ int split_in_box(float d, float& t)
 {
 #ifdef __CUDA_ARCH__
     const int fl = __float2int_rd(d);
 #else
-    const int fl = static_cast<int>(floorf(d));
+    // the device conversion: floor, saturated to the int range, NaN to 0
+    const float f = floorf(d);
+    const int fl = d != d ? 0 : (f >= 2147483648.0f ? INT_MAX : (f < -2147483648.0f ? INT_MIN : static_cast<int>(f)));
 #endif
     t = d - static_cast<float>(fl);
     return fl;
@@ -373,6 +400,27 @@ __host__ __device__ __forceinline__ int tile_offset(const BoxPar& bp, int i, int
     const int P = bp.E2 * bp.S3;
     return (i + split_in_box(d1, t1) - OFF - bp.O1) * P + (j + split_in_box(d2, t2) - OFF - bp.O2) * bp.S3 +
            (k + split_in_box(d3, t3) - OFF - bp.O3);
+}
+
+// Whether the stencil of (i, j, k) + (d1, d2, d3) lies inside the box: its
+// first-node offsets along each axis in [0, E - M].  The floor saturates for
+// |d| >= 2^31 and is 0 for NaN (as the device conversion does), and the
+// offsets are formed in unsigned arithmetic, so no input reaches an index
+// outside the box without failing this test.
+template <int ORDER>
+__host__ __device__ __forceinline__ bool in_box(const BoxPar& bp, int i, int j, int k, float d1, float d2, float d3)
+{
+    constexpr int M = Scheme<ORDER>::M;
+    constexpr int OFF = Scheme<ORDER>::OFF;
+    float t;
+    const unsigned r1 = static_cast<unsigned>(i) - static_cast<unsigned>(OFF + bp.O1) +
+                        static_cast<unsigned>(split_in_box(d1, t));
+    const unsigned r2 = static_cast<unsigned>(j) - static_cast<unsigned>(OFF + bp.O2) +
+                        static_cast<unsigned>(split_in_box(d2, t));
+    const unsigned r3 = static_cast<unsigned>(k) - static_cast<unsigned>(OFF + bp.O3) +
+                        static_cast<unsigned>(split_in_box(d3, t));
+    return bp.E1 >= M && bp.E2 >= M && bp.E3 >= M && r1 <= static_cast<unsigned>(bp.E1 - M) &&
+           r2 <= static_cast<unsigned>(bp.E2 - M) && r3 <= static_cast<unsigned>(bp.E3 - M);
 }
 
 template <int ORDER>
@@ -454,9 +502,16 @@ __device__ __forceinline__ float tile_eval(const float* box, const BoxPar& bp, i
 // the stencil is evaluated.
 // FULL: the tiles cover the grid exactly (n3 % 32 = n2 % 8 = n1 % TILE1 = 0),
 // so no point of a tile is out of range and the bounds tests compile away.
-template <int ORDER, class Epi, class S, bool FULL>
+// TB (FULL grids only): the box comes from the tile-bounds table tb that the
+// backtrace wrote with d, so the CTA starts staging it at once, reads the
+// displacements and the epilogue operands while it is in flight, and needs no
+// block reduction.  Every point is checked against the box (in_box); if any
+// fails, which a table written with this d never causes, the tile takes the
+// global-memory path.
+template <int ORDER, class Epi, class S, bool FULL, bool TB = false>
 __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
-    k_gather_tiled(Grid g, const S* __restrict__ f, const float* __restrict__ d, Epi epi)
+    k_gather_tiled(Grid g, const S* __restrict__ f, const float* __restrict__ d, Epi epi,
+                   const int4* __restrict__ tb = nullptr)
 {
     extern __shared__ float box[];
     __shared__ int red[6][TILE2];
@@ -470,6 +525,42 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
     const uint32_t p0 = static_cast<uint32_t>(i0) * g.n23 + j * g.n3 + k;
     auto valid = [&](int q) { return FULL || (col_ok && i0 + q < g.n1); };
 
+    if constexpr (TB) {
+        static_assert(FULL, "tile-bounds tables cover exactly tiled grids only");
+        const unsigned t = tile_index();
+        const int4 lo = __ldg(tb + 2 * t), hi = __ldg(tb + 2 * t + 1);
+        int gp[7];
+        box_geometry<ORDER, sizeof(S)>(g, lo.x, lo.y, lo.z, hi.x, hi.y, hi.z, lo.w != 0, gp);
+        BoxPar bp;
+        bp.O1 = gp[0]; bp.O2 = gp[1]; bp.O3 = gp[2];
+        bp.E1 = gp[3]; bp.E2 = gp[4]; bp.E3 = gp[5]; bp.S3 = gp[6];
+        if (bp.E1 != 0) tile_load_box<S>(g, f, box, bp, lane, warp);  // E1 is the same in every thread
+        float e1[TILE1], e2[TILE1], e3[TILE1];
+        typename Epi::Pre pre[TILE1];
+        bool out = bp.E1 == 0;
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q) {
+            const uint32_t p = p0 + q * g.n23;
+            e1[q] = __ldg(d + p);
+            e2[q] = __ldg(d + N + p);
+            e3[q] = __ldg(d + 2 * N + p);
+            pre[q] = epi.prefetch(p);
+        }
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q) out = out || !in_box<ORDER>(bp, i0 + q, j, k, e1[q], e2[q], e3[q]);
+        cp_async_wait_all();
+        if (__syncthreads_or(out)) {
+            if (threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
+#pragma unroll
+            for (int q = 0; q < TILE1; ++q)
+                epi.finish(p0 + q * g.n23, gather_global<ORDER, S>(g, f, i0 + q, j, k, e1[q], e2[q], e3[q]), pre[q]);
+            return;
+        }
+#pragma unroll
+        for (int q = 0; q < TILE1; ++q)
+            epi.finish(p0 + q * g.n23, tile_eval<ORDER>(box, bp, i0 + q, j, k, e1[q], e2[q], e3[q]), pre[q]);
+        return;
+    }
     float d1[TILE1], d2[TILE1], d3[TILE1];
     int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
     bool bad = false;
@@ -588,9 +679,16 @@ inline dim3 tiled_grid(const Grid& g)
 constexpr size_t kTiledSmemBytes = kBoxCapFloats * sizeof(float);
 
 template <int ORDER, class Epi, class S>
-inline void launch_tiled(const Grid& g, const S* f, const float* d, const Epi& e, cudaStream_t st)
+inline void launch_tiled(const Grid& g, const S* f, const float* d, const Epi& e, cudaStream_t st,
+                         const int4* tb = nullptr)
 {
-    if (tiles_cover_grid(g)) {
+    if (tiles_cover_grid(g) && tb) {
+        if (kTiledSmemBytes > 48 * 1024)
+            cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S, true, true>,
+                                 cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(kTiledSmemBytes));
+        k_gather_tiled<ORDER, Epi, S, true, true><<<tiled_grid(g), kTileThreads, kTiledSmemBytes, st>>>(g, f, d, e,
+                                                                                                        tb);
+    } else if (tiles_cover_grid(g)) {
         if (kTiledSmemBytes > 48 * 1024)
             cudaFuncSetAttribute(k_gather_tiled<ORDER, Epi, S, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                  static_cast<int>(kTiledSmemBytes));

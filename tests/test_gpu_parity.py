@@ -395,6 +395,32 @@ def test_gradient_matvec_precond_parity(env, n, grad_form, lowmem):
     assert abs(Jo - st.J) <= 1e-5 * abs(st.J) and abs(mis - st.mismatch) <= 1e-5 * st.mismatch
 
 
+@pytest.mark.parametrize("order,storage", [(3, 0), (1, 0), (4, 0), (3, 1)])
+def test_tile_bounds_table_path(env, order, storage):
+    """On grids the tiles cover exactly, the gathers at the context's own
+    characteristics take their boxes from the tile-bounds table that the
+    backtrace wrote with them.  The states they produce are bit-identical to
+    those of the in-kernel bounds path (the objective at the same velocity
+    gathers at a scratch characteristic), and no tile leaves the box path
+    (a point outside its table box would send the tile to global memory)."""
+    torch, claire = env
+    n = (64, 64, 64)
+    m0, m1, vs, v, p = _problem(n)
+    ctx = make_ctx(claire, torch, n, beta_v=p.beta_v, nt=p.nt, beta_w=p.beta_w, interp=order, storage=storage)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+    claire.claire_gather_fallback_tiles(reset=True)
+    g = torch.empty((3,) + n, device="cuda")
+    J = ctx.gradient(dev(torch, v), g)
+    vt = f32(synth.mode_velocity(n, seed=33, vmax=0.3))
+    Hv = torch.empty((3,) + n, device="cuda")
+    ctx.hessian_matvec(dev(torch, vt), Hv)
+    torch.cuda.synchronize()
+    assert claire.claire_gather_fallback_tiles(reset=True) == 0
+    Jo, _ = ctx.objective(dev(torch, v))
+    assert Jo == J
+    assert np.all(np.isfinite(host(Hv)))
+
+
 def test_gradient_nt1_linear_h2(env):
     """Degenerate and alternative settings: one time step, trilinear, H2."""
     torch, claire = env

@@ -6,7 +6,10 @@ kernels' own __host__ __device__ split / bounds / box code for the CPU and runs
 it over NaN, +-Inf, +-1e7, values at and below 2^20 cells and ordinary
 displacements on a cubic, a ragged and two small grids: every fitting box must
 hold all stencil nodes of its tile, and any tile with a non-finite or huge
-displacement must be sent to the global-memory path.  No GPU is used.
+displacement must be sent to the global-memory path.  Boxes taken from a
+tile-bounds table (the backtrace's by-product) are checked against other
+fields, NaN / Inf / huge values and arbitrary integer bounds: no point may
+pass the in-box test with a stencil node outside the box.  No GPU is used.
 """
 import os
 import shutil
@@ -39,3 +42,7 @@ def test_tile_box_host(tmp_path):
     # the realistic cases took the box path on the large grids, the bad ones did not
     assert "smooth                       order 3 es 4  tiles: 432 box, 0 global" in run.stdout
     assert "all NaN                      order 3 es 4  tiles: 0 box, 432 global (432 with bad" in run.stdout
+    # tile-bounds tables: with their own field every point stays on the box
+    # path; with another field some points fall outside and take the global path
+    assert "table own field              order 3 es 4  box tiles 256, points in box 262144, out 0" in run.stdout
+    assert "table NaN/Inf/huge field     order 3 es 4  box tiles 256" in run.stdout

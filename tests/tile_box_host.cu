@@ -7,6 +7,11 @@
 // geometry marks as fitting must hold every stencil node of every point
 // inside the shared-memory box; a tile with a non-finite displacement or one
 // of 2^20 cells or more must be marked as not fitting (global-memory path).
+// Tile-bounds tables: a box built from the bounds of one displacement field
+// (as the backtrace writes them) and used with another, or built from
+// arbitrary integers, must never let a point pass in_box with a stencil
+// node outside the box; with the field the table was made from, every
+// point of a fitting tile must pass.
 // Exit status 0 and "OK" on stdout when every case passes.
 #include <cmath>
 #include <cstdio>
@@ -190,6 +195,154 @@ void all_cases(const Grid& g, bool big)
     }, -1);
 }
 
+// Every point that passes in_box has all its stencil nodes inside the box.
+template <int ORDER>
+bool in_box_is_safe(const BoxPar& bp, int i, int j, int k, float d1, float d2, float d3, bool* passed)
+{
+    constexpr int M = Scheme<ORDER>::M;
+    constexpr int OFF = Scheme<ORDER>::OFF;
+    *passed = in_box<ORDER>(bp, i, j, k, d1, d2, d3);
+    if (!*passed) return true;
+    float u;
+    const long long c1 = static_cast<long long>(i) + split_in_box(d1, u) - OFF - bp.O1;
+    const long long c2 = static_cast<long long>(j) + split_in_box(d2, u) - OFF - bp.O2;
+    const long long c3 = static_cast<long long>(k) + split_in_box(d3, u) - OFF - bp.O3;
+    if (bp.E1 < M || bp.E2 < M || bp.E3 < M || bp.E3 > bp.S3) return false;
+    if (c1 < 0 || c1 > bp.E1 - M || c2 < 0 || c2 > bp.E2 - M || c3 < 0 || c3 > bp.E3 - M) return false;
+    const long long P = static_cast<long long>(bp.E2) * bp.S3;
+    const long long last = c1 * P + c2 * bp.S3 + c3 + (M - 1) * P + (M - 1) * bp.S3 + (M - 1);
+    return last < bp.E1 * P && bp.E1 * P <= kBoxCapFloats;
+}
+
+// Table made from field A, gather at field B.  same: B is A, so every point
+// of a fitting tile must pass in_box.
+template <int ORDER, int ES>
+void run_table_case(const char* name, const Grid& g, const Disp& A, const Disp& B, bool same)
+{
+    const int bx_n = g.n3 / TILE3, by_n = g.n2 / TILE2, bz_n = g.n1 / TILE1;  // exactly tiled grids only
+    long long box_tiles = 0, pass = 0, fail_pts = 0;
+    for (int bz = 0; bz < bz_n; ++bz)
+        for (int by = 0; by < by_n; ++by)
+            for (int bx = 0; bx < bx_n; ++bx) {
+                int lo1 = INT_MAX, lo2 = INT_MAX, lo3 = INT_MAX, hi1 = INT_MIN, hi2 = INT_MIN, hi3 = INT_MIN;
+                bool bad = false;
+                for (int w = 0; w < TILE2; ++w)
+                    for (int l = 0; l < TILE3; ++l)
+                        for (int q = 0; q < TILE1; ++q) {
+                            const int i = bz * TILE1 + q, j = by * TILE2 + w, k = bx * TILE3 + l;
+                            float d1, d2, d3;
+                            A(i, j, k, d1, d2, d3);
+                            bounds_add(i, d1, lo1, hi1, bad);
+                            bounds_add(j, d2, lo2, hi2, bad);
+                            bounds_add(k, d3, lo3, hi3, bad);
+                        }
+                int par[7];
+                box_geometry<ORDER, ES>(g, lo1, lo2, lo3, hi1, hi2, hi3, bad, par);
+                if (par[3] == 0) continue;
+                ++box_tiles;
+                BoxPar bp;
+                bp.O1 = par[0]; bp.O2 = par[1]; bp.O3 = par[2];
+                bp.E1 = par[3]; bp.E2 = par[4]; bp.E3 = par[5]; bp.S3 = par[6];
+                for (int w = 0; w < TILE2; ++w)
+                    for (int l = 0; l < TILE3; ++l)
+                        for (int q = 0; q < TILE1; ++q) {
+                            const int i = bz * TILE1 + q, j = by * TILE2 + w, k = bx * TILE3 + l;
+                            float d1, d2, d3;
+                            B(i, j, k, d1, d2, d3);
+                            bool passed;
+                            if (!in_box_is_safe<ORDER>(bp, i, j, k, d1, d2, d3, &passed)) {
+                                std::printf("FAIL table %s (order %d, es %d): point (%d,%d,%d) passed in_box with a "
+                                            "node outside the box\n", name, ORDER, ES, i, j, k);
+                                ++g_failures;
+                                return;
+                            }
+                            (passed ? pass : fail_pts) += 1;
+                        }
+            }
+    if (same && fail_pts != 0) {
+        std::printf("FAIL table %s (order %d, es %d): %lld points of fitting tiles failed in_box with their own "
+                    "table\n", name, ORDER, ES, fail_pts);
+        ++g_failures;
+        return;
+    }
+    std::printf("ok   table %-22s order %d es %d  box tiles %lld, points in box %lld, out %lld\n", name, ORDER, ES,
+                box_tiles, pass, fail_pts);
+}
+
+// Boxes from arbitrary integer bounds (unordered, extreme, huge) against
+// arbitrary displacements: in_box never admits a node outside the box.
+template <int ORDER, int ES>
+void run_garbage_tables(const Grid& g)
+{
+    std::mt19937 rng(11);
+    std::uniform_int_distribution<int> any(INT_MIN, INT_MAX), near(-10, 74), span(-3, 14), span3(-3, 40);
+    std::uniform_real_distribution<float> u(-8.0f, 8.0f);
+    const float special[] = {std::numeric_limits<float>::quiet_NaN(), std::numeric_limits<float>::infinity(),
+                             -std::numeric_limits<float>::infinity(), 3e9f, -3e9f, 1e7f, -1e7f, 2147483520.0f};
+    long long boxes = 0, pass = 0;
+    for (int trial = 0; trial < 200000; ++trial) {
+        int b[6];
+        if (trial % 4 == 0) {  // arbitrary integers
+            for (int a = 0; a < 6; ++a) b[a] = any(rng);
+        } else {  // plausible but unrelated bounds, sometimes unordered
+            for (int a = 0; a < 3; ++a) b[a] = near(rng);
+            b[3] = b[0] + span(rng);
+            b[4] = b[1] + span(rng);
+            b[5] = b[2] + span3(rng);
+        }
+        int par[7];
+        box_geometry<ORDER, ES>(g, b[0], b[1], b[2], b[3], b[4], b[5], false, par);
+        if (par[3] == 0) continue;
+        ++boxes;
+        BoxPar bp;
+        bp.O1 = par[0]; bp.O2 = par[1]; bp.O3 = par[2];
+        bp.E1 = par[3]; bp.E2 = par[4]; bp.E3 = par[5]; bp.S3 = par[6];
+        for (int s = 0; s < 16; ++s) {
+            const int i = static_cast<int>(rng() % 64), j = static_cast<int>(rng() % 64),
+                      k = static_cast<int>(rng() % 64);
+            float d[3];
+            for (float& x : d) x = (rng() % 8 == 0) ? special[rng() % 8] : u(rng);
+            bool passed;
+            if (!in_box_is_safe<ORDER>(bp, i, j, k, d[0], d[1], d[2], &passed)) {
+                std::printf("FAIL garbage table (order %d, es %d): bounds %d %d %d %d %d %d, point (%d,%d,%d) + "
+                            "(%g,%g,%g) passed in_box outside the box\n", ORDER, ES, b[0], b[1], b[2], b[3], b[4],
+                            b[5], i, j, k, d[0], d[1], d[2]);
+                ++g_failures;
+                return;
+            }
+            pass += passed;
+        }
+    }
+    std::printf("ok   garbage tables            order %d es %d  fitting boxes %lld, points in box %lld\n", ORDER,
+                ES, boxes, pass);
+}
+
+template <int ORDER, int ES>
+void table_cases(const Grid& g)
+{
+    const float nan = std::numeric_limits<float>::quiet_NaN();
+    const Disp smooth = [&](int i, int j, int k, float& a, float& b, float& c) {
+        a = 1.5f * std::sin(6.2831853f * j / g.n2);
+        b = -1.0f * std::cos(6.2831853f * k / g.n3);
+        c = 2.0f * std::sin(6.2831853f * i / g.n1);
+    };
+    const Disp other = [&](int i, int j, int k, float& a, float& b, float& c) {
+        a = -2.5f * std::cos(6.2831853f * k / g.n3);
+        b = 3.0f * std::sin(6.2831853f * i / g.n1);
+        c = -1.5f * std::sin(6.2831853f * j / g.n2);
+    };
+    const Disp bad = [&](int i, int j, int k, float& a, float& b, float& c) {
+        smooth(i, j, k, a, b, c);
+        if ((i + j + k) % 5 == 0) a = nan;
+        if ((i + j + k) % 7 == 0) b = 3e9f;
+        if ((i + j + k) % 11 == 0) c = -std::numeric_limits<float>::infinity();
+    };
+    run_table_case<ORDER, ES>("own field", g, smooth, smooth, true);
+    run_table_case<ORDER, ES>("other field", g, smooth, other, false);
+    run_table_case<ORDER, ES>("NaN/Inf/huge field", g, smooth, bad, false);
+    run_garbage_tables<ORDER, ES>(g);
+}
+
 }  // namespace
 
 int main()
@@ -208,6 +361,13 @@ int main()
         all_cases<3, 2>(g, big[n]);
         all_cases<1, 2>(g, big[n]);
     }
+    const Grid tg = make_grid(64, 64, 64);
+    std::printf("tile-bounds tables, grid 64 x 64 x 64\n");
+    table_cases<3, 4>(tg);
+    table_cases<1, 4>(tg);
+    table_cases<4, 4>(tg);
+    table_cases<3, 2>(tg);
+    table_cases<1, 2>(tg);
     if (g_failures) {
         std::printf("%d case(s) failed\n", g_failures);
         return 1;

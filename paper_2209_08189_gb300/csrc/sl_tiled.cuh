@@ -209,6 +209,22 @@ __device__ __forceinline__ unsigned tile_index()
 }
 #endif
 
+#ifndef CLAIRE_F16_OWN_WIDEN
+#define CLAIRE_F16_OWN_WIDEN 1  // 16-bit boxes: each thread widens its own chunks (no barrier between)
+#endif
+
+// Two 16-bit values packed in a word (low half first) widened to FP32.
+template <class S>
+__device__ __forceinline__ float2 widen2(uint32_t w)
+{
+    S lo, hi;
+    const unsigned short ulo = static_cast<unsigned short>(w & 0xffffu);
+    const unsigned short uhi = static_cast<unsigned short>(w >> 16);
+    memcpy(&lo, &ulo, 2);
+    memcpy(&hi, &uhi, 2);
+    return make_float2(to_f32<S>(lo), to_f32<S>(hi));
+}
+
 // Copy the (periodically wrapped) box of f into shared memory as FP32:
 // asynchronously (cp.async) for FP32 storage, converting loads otherwise.
 template <class S>
@@ -280,7 +296,8 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
     } else {
         // 16-bit storage: raw pairs (4 bytes, aligned: even origin, even n3)
         // go asynchronously to a staging area behind the FP32 box; after they
-        // land, every thread widens a share of them to FP32 in the box.
+        // land they are widened to FP32 in the box (tile_widen_box: each
+        // thread its own copies; else here, after a barrier, a share each).
         const int rows = bp.E1 * bp.E2;
         const int pairs = bp.E3 / 2;
         uint32_t* stage = reinterpret_cast<uint32_t*>(box + rows * bp.S3);
@@ -327,23 +344,67 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
             }
         }
         }
+#if !CLAIRE_F16_OWN_WIDEN
         cp_async_wait_all();
         __syncthreads();
         for (int r = warp; r < rows; r += TILE2) {
             const uint32_t* sp = stage + r * (bp.S3 / 2);
             float* dst = box + r * bp.S3;
             for (int c = lane; c < pairs; c += 32) {
-                const uint32_t w = sp[c];
-                S lo, hi;
-                const unsigned short ulo = static_cast<unsigned short>(w & 0xffffu);
-                const unsigned short uhi = static_cast<unsigned short>(w >> 16);
-                memcpy(&lo, &ulo, 2);
-                memcpy(&hi, &uhi, 2);
-                dst[2 * c] = to_f32<S>(lo);
-                dst[2 * c + 1] = to_f32<S>(hi);
+                const float2 w = widen2<S>(sp[c]);
+                dst[2 * c] = w.x;
+                dst[2 * c + 1] = w.y;
             }
         }
+#endif
     }
+}
+
+// Completion of tile_load_box for 16-bit storage with CLAIRE_F16_OWN_WIDEN:
+// every thread waits for its own copies and widens exactly the chunks (or
+// pairs) it issued, in the same order, so no barrier separates the copy from
+// the widening; the caller's barrier before the stencils publishes the box.
+// FP32 storage: nothing (the caller waits for the copies).
+template <class S>
+__device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const BoxPar& bp, int lane, int warp)
+{
+#if CLAIRE_F16_OWN_WIDEN
+    if constexpr (sizeof(S) == 2) {
+        const int rows = bp.E1 * bp.E2;
+        const uint32_t* stage = reinterpret_cast<const uint32_t*>(box + rows * bp.S3);
+        cp_async_wait_all();
+        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+            const int nch = bp.E3 >> 3;
+            const int ch0 = threadIdx.x & 15;
+            for (int r = threadIdx.x >> 4; r < rows; r += kTileThreads / 16) {
+                const uint4* sp = reinterpret_cast<const uint4*>(stage + r * (bp.S3 / 2));
+                float4* dp = reinterpret_cast<float4*>(box + r * bp.S3);
+                for (int c = ch0; c < nch; c += 16) {
+                    const uint4 w = sp[c];
+                    const float2 p0 = widen2<S>(w.x), p1 = widen2<S>(w.y), p2 = widen2<S>(w.z),
+                                 p3 = widen2<S>(w.w);
+                    dp[2 * c] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                    dp[2 * c + 1] = make_float4(p2.x, p2.y, p3.x, p3.y);
+                }
+            }
+        } else {
+            const int pairs = bp.E3 / 2;
+            for (int a = 0; a < bp.E1; ++a)
+                for (int b = warp; b < bp.E2; b += TILE2) {
+                    const int r = a * bp.E2 + b;
+                    const uint32_t* sp = stage + r * (bp.S3 / 2);
+                    float* dst = box + r * bp.S3;
+                    for (int c = lane; c < pairs; c += 32) {
+                        const float2 w = widen2<S>(sp[c]);
+                        dst[2 * c] = w.x;
+                        dst[2 * c + 1] = w.y;
+                    }
+                }
+        }
+    }
+#else
+    (void)g; (void)box; (void)bp; (void)lane; (void)warp;
+#endif
 }
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p)
@@ -548,6 +609,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
         }
 #pragma unroll
         for (int q = 0; q < TILE1; ++q) out = out || !in_box<ORDER>(bp, i0 + q, j, k, e1[q], e2[q], e3[q]);
+        if (bp.E1 != 0) tile_widen_box<S>(g, box, bp, lane, warp);
         cp_async_wait_all();
         if (__syncthreads_or(out)) {
             if (threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
@@ -596,6 +658,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
 #pragma unroll
     for (int q = 0; q < TILE1; ++q)
         if (valid(q)) pre[q] = epi.prefetch(p0 + q * g.n23);
+    tile_widen_box<S>(g, box, bp, lane, warp);
     cp_async_wait_all();
     __syncthreads();
 #pragma unroll

@@ -25,6 +25,9 @@ What it computes, step by step, in the paper's order and notation:
   spectral preconditioner S^{-1}, or the zero-velocity Hessian approximation
   applied through a two-level coarse grid (Sec. 2.2 "Optimization").
 * Jacobian determinant det grad y of the deformation map (Sec. 4.1).
+* Coarse preconditioner correction of the learned warm start: a pointwise
+  weight w >= 0 of the zero-velocity data term on the coarse grid, and its
+  least-squares fit to the data term of the Gauss-Newton matvec.
 
 Readings where the paper is silent are listed in the module docstrings below
 (interpolation nodes, Heun variant, trapezoidal time quadrature, Nyquist
@@ -47,7 +50,8 @@ __all__ = [
     "gradient", "hessian_matvec", "incremental_state", "precond", "pcg", "register",
     "transport", "transport_vjp", "interp_grad", "deformation_map", "detj", "cfl", "inner",
     "num_threads", "param_search", "param_continuation", "hessian0_matvec", "mean_state_gradient",
-    "restrict_spectral", "prolong_spectral", "precond_two_level",
+    "restrict_spectral", "prolong_spectral", "precond_two_level", "pc_weight_stats", "pc_weight_stats_at",
+    "pc_weight_fit",
 ]
 
 _lib = None
@@ -221,6 +225,7 @@ class Params:
     pc_coarse: int = 2      # fine-to-coarse grid ratio of the two-level preconditioner
     pc_tol: float = 1e-1    # relative residual of its inner PCG (0: run pc_maxit iterations)
     pc_maxit: int = 50
+    pc_weight: object = None  # coarse-grid weight w >= 0 of the zero-velocity data term (None: w = 1)
     extra: dict = field(default_factory=dict)
 
     @property
@@ -566,11 +571,15 @@ def _pcg_h0(rhs, gbar, p: Params, tol, maxit):
     return x, it
 
 
-def precond_two_level(r, gbar_c, p: Params, stats=None):
+def precond_two_level(r, gbar_c, p: Params, stats=None, w=None):
     """P^{-1} r = E H0c^{-1} R r + S^{-1} (r - E R r) (zero-velocity Hessian on
-    the coarse grid of gbar_c, spectral inverse on the high modes)."""
+    the coarse grid of gbar_c, spectral inverse on the high modes).  With a
+    coarse-grid weight w >= 0 the coarse operator is S + gbar_c w gbar_c^T,
+    the zero-velocity operator of sqrt(w) gbar_c."""
     r = _f64(r); n = r.shape[1:]
     nc = gbar_c.shape[1:]
+    if w is not None:
+        gbar_c = gbar_c * np.sqrt(np.maximum(_f64(w), 0.0))
     rc = restrict_spectral(r, nc)
     xc, its = _pcg_h0(rc, gbar_c, p, p.pc_tol, p.pc_maxit)
     if stats is not None:
@@ -578,6 +587,61 @@ def precond_two_level(r, gbar_c, p: Params, stats=None):
     low = prolong_spectral(rc, n)          # E R r, mean included
     mean = r - _mean_free(r)               # identity on k = 0
     return prolong_spectral(xc, n) + precond(r - low, p) + mean
+
+
+# ----------------------------------------------------------------------------
+# Coarse preconditioner correction (the learned warm start's second output)
+# ----------------------------------------------------------------------------
+#
+# The zero-velocity operator keeps only the pointwise rank-one data term
+# gbar (gbar . vt).  The correction weights it pointwise on the coarse grid,
+# H0w vt = S vt + gbar w (gbar . vt) with w >= 0 (precond_two_level's w);
+# w = 1 is the paper's preconditioner.  The weight a predictor should
+# reproduce is the least-squares fit of the model D ~ gbar w (gbar . p) to the
+# data term D = H p - S p of the true Gauss-Newton matvec on probe fields p,
+# pooled over the fine voxels of each coarse cell:
+#   w = max(sum a (gbar . D) / sum a^2 |gbar|^2, 0),   a = gbar . p,
+# and w = 1 where the pooled denominator vanishes (no image gradient).
+# At v = 0 the data term is exactly gbar (gbar . p), so the fit gives w = 1.
+
+def pc_weight_stats(gbar, probes, data_terms):
+    """Per-voxel sums num = sum_p a (gbar . D_p) and den = sum_p a^2 |gbar|^2,
+    a = gbar . p, over probe fields p and the data terms D_p = H p - S p."""
+    gbar = _f64(gbar)
+    g2 = np.sum(gbar * gbar, axis=0)
+    num = np.zeros(gbar.shape[1:])
+    den = np.zeros(gbar.shape[1:])
+    for pv, D in zip(probes, data_terms):
+        a = np.sum(gbar * _f64(pv), axis=0)
+        num += a * np.sum(gbar * _f64(D), axis=0)
+        den += a * a * g2
+    return num, den
+
+
+def pc_weight_stats_at(st: State, probes, mode=None):
+    """pc_weight_stats with the data terms of the Gauss-Newton matvec at st
+    (exact-gradient form: H p = S p + data term)."""
+    if st.p.grad_form != 0:
+        raise ValueError("the data term is separated from S only in the exact-gradient form")
+    gbar = mean_state_gradient(st)
+    terms = [hessian_matvec(st, pv, mode) - reg_apply(pv, st.p) for pv in probes]
+    return pc_weight_stats(gbar, probes, terms)
+
+
+def pc_weight_fit(num, den, nc):
+    """Fitted weight on the coarse grid nc: the fine sums pooled over the
+    (n / nc)^3 voxels of each coarse cell, w = max(num / den, 0), w = 1 where
+    den = 0."""
+    n = num.shape
+    r = [a // b for a, b in zip(n, nc)]
+    if any(a != b * c for a, b, c in zip(n, nc, r)):
+        raise ValueError("the fine grid must be an integer multiple of the coarse grid")
+    pool = lambda f: f.reshape(nc[0], r[0], nc[1], r[1], nc[2], r[2]).sum(axis=(1, 3, 5))
+    nu, de = pool(_f64(num)), pool(_f64(den))
+    w = np.ones(tuple(nc))
+    pos = de > 0
+    w[pos] = np.maximum(nu[pos] / de[pos], 0.0)
+    return w
 
 
 def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False, stats=None):
@@ -591,7 +655,7 @@ def pcg(st: State, rhs, rtol, maxit, mode=None, fixed_iters=False, stats=None):
     if two_level:
         nc = tuple(s // p.pc_coarse for s in n)
         gbar_c = restrict_spectral(mean_state_gradient(st), nc)
-        apply_p = lambda res: precond_two_level(res, gbar_c, p, stats)
+        apply_p = lambda res: precond_two_level(res, gbar_c, p, stats, p.pc_weight)
     else:
         apply_p = lambda res: precond(res, p)
     x = np.zeros_like(rhs)

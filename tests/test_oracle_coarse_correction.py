@@ -104,18 +104,13 @@ def test_fitted_coarse_corrections_gain_little(problem):
     its_2l = _outer(st, _pc(p, gbar), -g)
     assert its_2l < its_s  # the paper's two-level preconditioner helps
     # (a) pointwise data-term weight fitted on probes of the true data term
-    num = np.zeros(N)
-    den = np.zeros(N)
-    for i in range(8):
-        pv = synth.mode_velocity(N, seed=100 + i, kmax=6, vmax=0.3)
-        D = oracle.hessian_matvec(st, pv) - reg_apply(pv, p)
-        a = np.sum(gbar * pv, 0)
-        num += a * np.sum(gbar * D, 0)
-        den += a * a * np.sum(gbar * gbar, 0)
+    # (the oracle's fit, pooled over the fine voxels of each coarse cell)
+    probes = [synth.mode_velocity(N, seed=100 + i, kmax=6, vmax=0.3) for i in range(8)]
+    num, den = oracle.pc_weight_stats_at(st, probes)
     nc = tuple(s // 2 for s in N)
-    blk = lambda f: f.reshape(nc[0], 2, nc[1], 2, nc[2], 2).mean(axis=(1, 3, 5))
-    w = np.clip(blk(num) / np.maximum(blk(den), 1e-30), 0.0, None)
-    its_w = _outer(st, _pc(p, gbar, w=w), -g)
+    w = oracle.pc_weight_fit(num, den, nc)
+    gbar_c = restrict_spectral(gbar, nc)
+    its_w = _outer(st, lambda r: oracle.precond_two_level(r, gbar_c, p, w=w), -g)
     # (b) coarse regulariser scale
     its_g = min(_outer(st, _pc(p, gbar, gamma=gm), -g) for gm in (0.5, 2.0))
     print("outer PCG to 1e-2: S^-1 %d, two-level %d, fitted weight %d, best gamma %d" % (its_s, its_2l, its_w, its_g))

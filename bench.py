@@ -88,14 +88,18 @@ def parse_args():
     ap.add_argument("--vjp-n", type=int, default=1024)
     ap.add_argument("--no-mixed-learned", action="store_true",
                     help="skip the FP16 storage + learned warm start registration of the default line")
-    ap.add_argument("--weights", default=os.path.join(ROOT, "paper_2209_08189_gb300", "weights",
-                                                      "unet_warmstart_128.npz"))
+    ap.add_argument("--weights", default=None,
+                    help="warm-start network weights (default: the network with the preconditioner head, "
+                         "weights/unet_warmstart_pc_128.npz, if present, else weights/unet_warmstart_128.npz)")
     ap.add_argument("--spectral-iterate", type=int, default=1, choices=[0, 1],
                     help="claire_opts.spectral_iterate of the solver contexts (1: S v from the carried spectrum)")
     ap.add_argument("--precond", default="spectral", choices=["spectral", "two-level"],
                     help="PCG preconditioner of the timed registration")
     ap.add_argument("--no-other-precond", action="store_true",
                     help="skip the registration with the other preconditioner after the timed loop")
+    ap.add_argument("--pc-weight-report", action="store_true",
+                    help="the coarse preconditioner correction at 256^3: FP16 + warm start + two-level with the "
+                         "network's weight, least-squares fitted weights and constant weights")
     ap.add_argument("--precond-report", action="store_true",
                     help="time to tolerance at --n with the spectral and the two-level zero-velocity preconditioner")
     return ap.parse_args()
@@ -513,9 +517,15 @@ def mixed_learned_leg(args, ctx32, claire, grid, dev, stream, m0, m1, m0_d, m1_d
     velocity, after one warm-up solve; final J and mismatch are also evaluated
     by the FP64 oracle at every returned velocity (outside the timing).  A
     third arm runs FP16 + warm start with the two-level zero-velocity
-    preconditioner instead of S^-1."""
+    preconditioner instead of S^-1; with a network that has the
+    preconditioner head, a fourth adds its coarse preconditioner weight
+    (claire_set_pc_weight) to the third."""
     import torch
     import oracle
+    if args.weights is None:
+        wdir = os.path.join(ROOT, "paper_2209_08189_gb300", "weights")
+        pcf = os.path.join(wdir, "unet_warmstart_pc_128.npz")
+        args.weights = pcf if os.path.exists(pcf) else os.path.join(wdir, "unet_warmstart_128.npz")
     if not os.path.exists(args.weights):
         return {"unavailable": "no trained weights at %s (python -m paper_2209_08189_gb300.train_warmstart)"
                                % os.path.relpath(args.weights, ROOT)}
@@ -550,8 +560,14 @@ def mixed_learned_leg(args, ctx32, claire, grid, dev, stream, m0, m1, m0_d, m1_d
     ctx16.set_images(m0_d, m1_d)
     v16 = torch.zeros((3,) + grid, device=dev)
 
+    pc_net = bool(u.pc_head)
+    wc = torch.empty(tuple(s // 2 for s in grid), device=dev) if pc_net else None  # coarse grid (pc_coarse 2)
+    use_pcw = [False]
+
     def learned():
         ws.predict(m0_d, m1_d, v16)
+        if use_pcw[0]:
+            ctx16.set_pc_weight(ws.pc_weight(wc))
         return ctx16.register(v16, check=False)[1]
 
     reps = max(1, min(args.steps, 3))
@@ -560,10 +576,15 @@ def mixed_learned_leg(args, ctx32, claire, grid, dev, stream, m0, m1, m0_d, m1_d
     m0_64, m1_64 = m0.astype(np.float64), m1.astype(np.float64)
     # the third arm adds the paper's two-level zero-velocity preconditioner to
     # FP16 storage + the warm start (the fastest combination to the same tolerance)
-    for name, fn, pc in (("plain_fp32", plain, None), ("fp16_learned", learned, claire.PRECOND_SPECTRAL),
-                         ("fp16_learned_two_level", learned, claire.PRECOND_TWO_LEVEL)):
+    arms = [("plain_fp32", plain, None, False), ("fp16_learned", learned, claire.PRECOND_SPECTRAL, False),
+            ("fp16_learned_two_level", learned, claire.PRECOND_TWO_LEVEL, False)]
+    if pc_net:  # the network's coarse preconditioner correction on top of the two-level preconditioner
+        arms.append(("fp16_learned_two_level_pcw", learned, claire.PRECOND_TWO_LEVEL, True))
+    for name, fn, pc, pcw in arms:
+        use_pcw[0] = pcw
         if pc is not None:
             ctx16.set_opts(precond=pc)
+            ctx16.set_pc_weight(None)
         fn()  # warm-up
         times, rep = [], None
         for _ in range(reps):
@@ -584,6 +605,12 @@ def mixed_learned_leg(args, ctx32, claire, grid, dev, stream, m0, m1, m0_d, m1_d
     res["plain_fp32"]["mismatch_at_zero"] = ctx32.objective(zero)[1]
     res["speedup"] = res["plain_fp32"]["time_to_tol_s"] / res["fp16_learned"]["time_to_tol_s"]
     res["speedup_two_level"] = res["plain_fp32"]["time_to_tol_s"] / res["fp16_learned_two_level"]["time_to_tol_s"]
+    if pc_net:
+        res["speedup_two_level_pcw"] = (res["plain_fp32"]["time_to_tol_s"] /
+                                        res["fp16_learned_two_level_pcw"]["time_to_tol_s"])
+        wstat = wc.cpu().numpy()
+        res["fp16_learned_two_level_pcw"]["weight_stats"] = {
+            "min": float(wstat.min()), "mean": float(wstat.mean()), "max": float(wstat.max())}
     res["network"] = {"weights": os.path.relpath(args.weights, ROOT), "n_net": u.meta["n_net"],
                       "params": u.num_params(), "training": u.meta.get("training")}
     res["stop"] = "both at |g| <= 5e-2 |g(v=0)| of the FP32 context (%.6g)" % g0
@@ -844,6 +871,100 @@ def run_precond_report(args):
         out["speedup_%s_vs_f32_spectral" % k] = a["time_to_tol_s"] / b["time_to_tol_s"]
         out["oracle_J_rel_diff_%s" % k] = (b["oracle_J"] - a["oracle_J"]) / a["oracle_J"]
         out["oracle_mismatch_rel_diff_%s" % k] = (b["oracle_mismatch"] - a["oracle_mismatch"]) / a["oracle_mismatch"]
+    print(json.dumps(out))
+
+
+def run_pc_weight_report(args):
+    """Coarse preconditioner correction on the clinical-size 256^3 workload:
+    FP16 storage, the two-level zero-velocity preconditioner (coarse 128^3)
+    and the warm start of the network with the preconditioner head, with the
+    coarse weight w of its data term set to: none (w = 1, the paper's
+    operator); the network's prediction; the least-squares fit of the data
+    term (claire_net_pcw_stats, 8 band-limited probes |k| <= 6, pooled over
+    2^3 cells) at v* and at the warm start; and constants.  Constants also
+    from v = 0 and at beta_v 1e-3.  Each run: one warm-up solve, then one timed
+    (host wall clock around synchronised calls); all stop at 5e-2 |g(v = 0)|."""
+    import torch
+    from paper_2209_08189_gb300 import claire, synth, net, warmstart
+    import __graft_entry__ as entry
+    entry.build()
+    dev = torch.device("cuda", 0)
+    st = torch.cuda.current_stream(dev).cuda_stream
+    grid, base, vstar = workload(256)
+    N = int(np.prod(grid))
+    nc = tuple(s // 2 for s in grid)
+    f = lambda a: torch.from_numpy(np.ascontiguousarray(a, dtype=np.float32)).to(dev)
+    ctx32 = claire.Context(grid, 1e-2, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50)
+    base_d, vstar_d = f(base), f(vstar)
+    m1c = torch.empty(grid, device=dev)
+    ctx32.transport(vstar_d, base_d, m1c, claire.TRANSPORT_FWD)
+    m1 = synth.add_noise(m1c.cpu().numpy().astype(np.float64), 0.02, seed=1)
+    m0 = synth.add_noise(base, 0.02, seed=0)
+    m0_d, m1_d = f(m0), f(m1)
+    ctx32.set_images(m0_d, m1_d)
+    zero = torch.zeros((3,) + grid, device=dev)
+    gt = torch.empty_like(zero)
+    ctx32.gradient(zero, gt)
+    g0 = math.sqrt(claire.claire_dot(ctx32.handle, gt, gt, 3 * N))
+    ctx16 = claire.Context(grid, 1e-2, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                           storage=claire.STORAGE_F16, g0_ref=g0, precond=claire.PRECOND_TWO_LEVEL)
+    ctx16.set_images(m0_d, m1_d)
+    wfile = os.path.join(ROOT, "paper_2209_08189_gb300", "weights", "unet_warmstart_pc_128.npz")
+    u = net.UNet.from_file(args.weights or wfile, stream=st)
+    ws = warmstart.WarmStart(u, int(u.meta["n_net"]))
+    v0 = torch.empty_like(zero)
+    ws.predict(m0_d, m1_d, v0)
+    wl = torch.empty(nc, device=dev)
+    ws.pc_weight(wl)
+    L = net.lib()
+
+    def fit(vlin, probes):
+        num, den = torch.zeros(grid, device=dev), torch.zeros(grid, device=dev)
+        gb, hp, sp = torch.empty_like(zero), torch.empty_like(zero), torch.empty_like(zero)
+        ctx32.gradient(vlin, gt)
+        ctx32.mean_state_gradient(gb)
+        for q in probes:
+            ctx32.hessian_matvec(q, hp)
+            ctx32.spectral(q, sp, claire.SPECTRAL_REG)
+            net._check(L.claire_net_pcw_stats(gb.data_ptr(), q.data_ptr(), hp.data_ptr(), sp.data_ptr(), N,
+                                              num.data_ptr(), den.data_ptr(), st), "pcw_stats")
+        pool = lambda x: x.reshape(nc[0], 2, nc[1], 2, nc[2], 2).sum(dim=(1, 3, 5))
+        A, B = pool(den), pool(num)
+        one = torch.ones_like(A)
+        return torch.where(A > 0, torch.clamp(B / torch.where(A > 0, A, one), min=0.0), one).contiguous()
+
+    def run(w, start):
+        ctx16.set_pc_weight(w)
+        out = None
+        for _ in range(2):
+            v = start.clone()
+            torch.cuda.synchronize()
+            t = time.perf_counter()
+            _, r = ctx16.register(v, check=False)
+            torch.cuda.synchronize()
+            out = (time.perf_counter() - t, r, v)
+        t, r, v = out
+        row = {"ms": 1e3 * t, "gn": r["gn_iters"], "pcg": r["pcg_iters_total"],
+               "inner": r["pc_inner_iters_total"], "gnorm_rel": r["gnorm_rel"], "J": ctx32.objective(v)[0]}
+        if w is not None:
+            row["w_min_mean_max"] = [float(w.min()), float(w.mean()), float(w.max())]
+        return row
+
+    probes = [f(synth.mode_velocity(grid, seed=9000 + i, nmodes=8, kmax=6, vmax=0.3)) for i in range(8)]
+    out = {"workload": "256^3 clinical-size pair (bench.py default), FP16 storage, two-level (coarse 128^3), "
+                       "warm start of " + os.path.relpath(args.weights or wfile, ROOT),
+           "runs": {}}
+    R = out["runs"]
+    R["b1e-2 v0 none"] = run(None, v0)
+    R["b1e-2 v0 learned"] = run(wl, v0)
+    R["b1e-2 v0 fit at v*"] = run(fit(vstar_d, probes), v0)
+    R["b1e-2 v0 fit at v0"] = run(fit(v0, probes), v0)
+    for beta in (1e-2, 1e-3):
+        claire.claire_set_beta(ctx16.handle, beta, 1e-4)
+        claire.claire_set_beta(ctx32.handle, beta, 1e-4)
+        for sname, start in (("v0", v0), ("zero", zero)):
+            for c in (1.0, 1.5, 2.0, 3.0, 4.0, 6.0):
+                R["b%g %s const %g" % (beta, sname, c)] = run(torch.full(nc, c, device=dev), start)
     print(json.dumps(out))
 
 
@@ -1360,6 +1481,9 @@ def run_large_report(args):
 
 def main():
     args = parse_args()
+    if args.pc_weight_report:
+        run_pc_weight_report(args)
+        return
     if args.precond_report:
         run_precond_report(args)
         return

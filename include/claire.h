@@ -254,6 +254,24 @@ claire_status claire_hessian_matvec(claire_ctx* ctx, const float* vt, float* Hvt
  * iterations. */
 claire_status claire_precond(claire_ctx* ctx, const float* r, float* z);
 
+/* Coarse preconditioner correction (the learned warm start's second output,
+ * an extension of Sec. 2.2 "Optimization"): a pointwise weight w >= 0 of the
+ * data term of the two-level preconditioner's zero-velocity operator, which
+ * becomes H0c = S + gbar_c w gbar_c^T on the coarse grid (w = 1: the paper's
+ * operator).  w: FP32 [Nc1][Nc2][Nc3] (device or host) on the coarse grid
+ * wgrid = N / pc_coarse, copied in; negative values act as 0.  NULL clears it.
+ * Used by every later two-level preconditioner set-up of this context.
+ * CLAIRE_EINVAL: wgrid is not the coarse grid of the context's options (also
+ * reported by the set-up if pc_coarse changes afterwards);
+ * CLAIRE_ENONFINITE: w holds a non-finite value (the weight is then cleared). */
+claire_status claire_set_pc_weight(claire_ctx* ctx, const float* w, const int wgrid[3]);
+
+/* gbar = sum_j w_j grad m^j (trapezoid weights of the solves, FD8 gradients of
+ * the states) at the last claire_gradient's v, the field the zero-velocity
+ * operator is built from; device pointer, 3N floats.  CLAIRE_ESTATE without a
+ * linearisation point. */
+claire_status claire_mean_state_gradient(claire_ctx* ctx, float* gbar);
+
 /*
  * Gauss-Newton-Krylov registration, Eq. (5): v_{k+1} = v_k + alpha_k vt_k with
  * H vt_k = -g_k solved by matrix-free PCG (forcing opts.pcg_rtol_max) and

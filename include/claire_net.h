@@ -4,8 +4,9 @@
  * The paper (Sec. 2.2, Sec. 4) solves every registration from v = 0 or from
  * a coarser-grid solution.  This part adds a small 3D convolutional network
  * (a U-Net over periodic volumes) that maps an image pair (m0, m1) to an
- * initial velocity; Gauss-Newton-Krylov from that guess remains the solver
- * and corrects whatever error the guess has.  The paper has no network: these entry points
+ * initial velocity and, optionally, to a pointwise weight of the data term of
+ * the two-level preconditioner's coarse operator; Gauss-Newton-Krylov from
+ * that guess remains the solver and corrects whatever error the guess has.  The paper has no network: these entry points
  * are building blocks of that extension, with no counterpart in it.
  *
  * Conventions, for every entry point below:
@@ -92,18 +93,20 @@ claire_status claire_net_leaky_bwd(const void* dy, int dy_stride, const void* y,
 claire_status claire_net_pack(const float* m0, const float* m1, float a0, float a1, size_t nvox, void* x,
                               int stride, void* stream);
 
-/* Output head, a 1x1x1 conv to the three velocity components:
+/* Output head, a 1x1x1 conv to nout channels (3: the velocity; 4: the
+ * velocity and, as channel 3, the logit o of the coarse preconditioner weight,
+ * see claire_net_pcw_weight):
  * v[b][c][p] = scale * (bh[c] + sum_ci x[b,p][ci] wh[c][ci]); v FP32
- * [B][3][D][H][W] (physical units, the layout of claire_transport's v);
- * wh FP32 [3][cin], cin 16 or 32. */
-claire_status claire_net_head(const void* x, int x_stride, int cin, const float* wh, const float* bh, float scale,
-                              void* v, const int vol[4], void* stream);
-/* Partial blocks of claire_net_head_bwd: `part` needs blocks*(3*cin+3) floats. */
+ * [B][nout][D][H][W] (channels 0..2 in physical units, the layout of
+ * claire_transport's v for each sample); wh FP32 [nout][cin], cin 16 or 32. */
+claire_status claire_net_head(const void* x, int x_stride, int cin, int nout, const float* wh, const float* bh,
+                              float scale, void* v, const int vol[4], void* stream);
+/* Partial blocks of claire_net_head_bwd: `part` needs blocks*(nout*cin+nout) floats. */
 claire_status claire_net_head_bwd_blocks(const int vol[4], int* blocks);
 /* Head backward for dv (FP32, layout of v): dx[b,p][ci] = scale sum_c
- * dv[b][c][p] wh[c][ci] (BF16, dx may be NULL) and dwb = [dwh (3*cin),
- * dbh (3)] (FP32, fixed-order reduction). */
-claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, const float* wh, float scale,
+ * dv[b][c][p] wh[c][ci] (BF16, dx may be NULL) and dwb = [dwh (nout*cin),
+ * dbh (nout)] (FP32, fixed-order reduction). */
+claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, int nout, const float* wh, float scale,
                                   const float* dv, void* dx, int dx_stride, const int vol[4], int blocks,
                                   float* part, float* dwb, void* stream);
 
@@ -121,6 +124,33 @@ claire_status claire_net_adam(float* w, const float* g, float* m, float* s, size
 claire_status claire_net_vel_loss(const float* v, const float* vstar, const float* gv, float a, float b, size_t n,
                                   float* dv, double* sum, void* stream);
 claire_status claire_net_residual(const float* x, const float* y, size_t n, float* r, double* sum, void* stream);
+
+/* Coarse preconditioner correction (the network's second output).  The
+ * two-level preconditioner (Sec. 2.2, "Optimization") inverts on a coarse
+ * grid the zero-velocity operator S + gbar gbar^T; the correction is a
+ * pointwise weight w >= 0 of its data term, S + gbar w gbar^T (w = 1: the
+ * paper's operator; claire_set_pc_weight installs it).  The network predicts
+ * o with w = softplus(o) = log(1 + e^o); its training target is the
+ * least-squares fit of that model to the data term of the true Gauss-Newton
+ * matvec on probe fields p, pooled over 2 x 2 x 2 cells.
+ *
+ * Fit statistics, added to num and den (FP32 [n]): with a = gbar . p,
+ * num += a (gbar . (hp - sp)), den += a^2 |gbar|^2, where gbar is the mean
+ * state gradient (claire_mean_state_gradient), hp = H p the Gauss-Newton
+ * matvec and sp = S p the regulariser (claire_spectral); vector fields FP32
+ * [3][n]. */
+claire_status claire_net_pcw_stats(const float* gbar, const float* p, const float* hp, const float* sp, size_t n,
+                                   float* num, float* den, void* stream);
+/* Training loss of w = softplus(o) (o, num, den, dout FP32 on the grid
+ * grid[0] x grid[1] x grid[2], even extents): with A and B the sums of den
+ * and num over the voxel's 2 x 2 x 2 cell and T the sum of den,
+ * L = sum_x (A w^2 - 2 B w + B^2 / A) / (8 T) (cells with A > 0), minimised by
+ * w = B / A; dout = scale dL/do.  sums: two device doubles; sums[0] must be 0
+ * on entry and receives T, sums[1] += L. */
+claire_status claire_net_pcw_loss(const float* o, const float* num, const float* den, const int grid[3],
+                                  float scale, float* dout, double* sums, void* stream);
+/* Preconditioner weight from the network's logit: w = softplus(o), FP32 [n]. */
+claire_status claire_net_pcw_weight(const float* o, float* w, size_t n, void* stream);
 
 /* Tiling of the tcgen05 convolution for this process: bricks of bdc x 16 x 8
  * voxels (bdc 1, 2 or 4: D planes sharing one staged halo) and nstage 1 or 2

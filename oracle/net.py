@@ -13,7 +13,8 @@ layers the extension uses, written out in float64 numpy:
 * Its exact input and weight gradients (the adjoint of a periodic
   correlation is the correlation with the reflected kernel).
 * 2x2x2 average pooling, nearest 2x upsampling and their adjoints.
-* Output head: a 1x1x1 convolution to the three velocity components.
+* Output head: a 1x1x1 convolution to the three velocity components (and,
+  for the preconditioner head, a fourth channel: the weight's logit).
 * Adam (bias-corrected first and second moments).
 * The whole U-Net forward pass and its reverse-mode gradient.
 
@@ -108,9 +109,9 @@ def head(x, wh, bh, scale):
 
 def head_grad(x, wh, scale, dv):
     """Returns (dx, dwh, dbh) for the head."""
-    g = scale * np.moveaxis(_f64(dv), 1, -1)          # [B, D, H, W, 3]
+    g = scale * np.moveaxis(_f64(dv), 1, -1)          # [B, D, H, W, nout]
     dx = g @ _f64(wh)
-    gf = g.reshape(-1, 3)
+    gf = g.reshape(-1, g.shape[-1])
     dwh = gf.T @ _f64(x).reshape(-1, _f64(x).shape[-1])
     return dx, dwh, gf.sum(axis=0)
 

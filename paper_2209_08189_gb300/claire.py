@@ -133,6 +133,8 @@ _SIGS = {
     "claire_gradient": [_vp, _vp, _vp, ctypes.POINTER(ctypes.c_double)],
     "claire_hessian_matvec": [_vp, _vp, _vp],
     "claire_precond": [_vp, _vp, _vp],
+    "claire_set_pc_weight": [_vp, _vp, ctypes.POINTER(ctypes.c_int)],
+    "claire_mean_state_gradient": [_vp, _vp],
     "claire_register": [_vp, _vp, ctypes.POINTER(claire_report)],
     "claire_transport": [_vp, _vp, _vp, _vp, ctypes.c_int],
     "claire_detj": [_vp, _vp, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double)],
@@ -267,6 +269,19 @@ def claire_hessian_matvec(ctx, vt, Hvt):
 
 def claire_precond(ctx, r, z):
     return _check(ctx, lib().claire_precond(ctx, _ptr(r), _ptr(z)))
+
+
+def claire_set_pc_weight(ctx, w, wgrid=None):
+    """Install (w: FP32 [Nc1, Nc2, Nc3], device or host) or clear (w None) the
+    coarse preconditioner weight of the two-level preconditioner."""
+    if w is None:
+        return _check(ctx, lib().claire_set_pc_weight(ctx, None, None))
+    g = (ctypes.c_int * 3)(*(int(x) for x in (wgrid if wgrid is not None else w.shape)))
+    return _check(ctx, lib().claire_set_pc_weight(ctx, _ptr(w), g))
+
+
+def claire_mean_state_gradient(ctx, gbar):
+    return _check(ctx, lib().claire_mean_state_gradient(ctx, _ptr(gbar)))
 
 
 def claire_register(ctx, v_inout, check=True):
@@ -495,6 +510,12 @@ class Context:
 
     def precond(self, r, z):
         claire_precond(self.handle, r, z)
+
+    def set_pc_weight(self, w, wgrid=None):
+        claire_set_pc_weight(self.handle, w, wgrid)
+
+    def mean_state_gradient(self, gbar):
+        claire_mean_state_gradient(self.handle, gbar)
 
     def register(self, v_inout, check=True):
         st, rep = claire_register(self.handle, v_inout, check)

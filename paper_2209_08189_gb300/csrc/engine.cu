@@ -148,6 +148,12 @@ struct claire_ctx {
     bool have_images = false, have_lin = false;
     double J_lin = 0, mis_lin = 0, reg_lin = 0;
     TwoLevel* tl2 = nullptr;         // two-level preconditioner state (precond = 1)
+    // coarse preconditioner correction (claire_set_pc_weight): weight of the
+    // zero-velocity data term on the coarse grid pcw_grid, Nc floats
+    float* pcw = nullptr;
+    size_t pcw_n = 0;
+    int pcw_grid[3]{};
+    bool pcw_on = false;
     long long pc_inner_total = 0;    // its inner PCG iterations so far
 
     // statistics and timing
@@ -192,6 +198,9 @@ struct claire_ctx {
         vh = nullptr;
         if (vjp_acc) cudaFree(vjp_acc);
         vjp_acc = nullptr;
+        if (pcw) cudaFree(pcw);
+        pcw = nullptr;
+        pcw_on = false;
         if (hres) cudaFreeHost(hres);
         hres = nullptr;
         delete tl2;
@@ -978,14 +987,12 @@ claire_status tl_ensure(claire_ctx* c)
     return CLAIRE_OK;
 }
 
-// gbar_c = R (sum_j w_j grad m^j) at the linearisation point: FD8 gradient of
-// the trapezoid mean of the states (FD8 is linear), restricted spectrally.
-claire_status tl_prepare(claire_ctx* c)
+// gbar = sum_j w_j grad m^j at the linearisation point into out (device,
+// 3N): the FD8 gradient of the trapezoid mean of the states (FD8 is linear).
+// Uses l0.
+claire_status mean_state_gradient(claire_ctx* c, float* out)
 {
     if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
-    CL_TRY(tl_ensure(c));
-    TwoLevel* t = c->tl2;
-    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
     const size_t N = c->N;
     float* mean = reinterpret_cast<float*>(c->l0);
     {
@@ -994,7 +1001,23 @@ claire_status tl_prepare(claire_ctx* c)
                            c->sto, c->stream);
         CL_LAUNCHED(c);
     }
-    CL_TRY(fd8_grad(c, mean, c->z, Storage::F32));
+    return fd8_grad(c, mean, out, Storage::F32);
+}
+
+// gbar_c = R (sum_j w_j grad m^j) at the linearisation point, restricted
+// spectrally; with a coarse preconditioner weight w installed, gbar_c is then
+// scaled by sqrt(w), so the coarse operator becomes S + gbar_c w gbar_c^T.
+claire_status tl_prepare(claire_ctx* c)
+{
+    if (!c->have_lin) return fail(c, CLAIRE_ESTATE, "no linearisation point (claire_gradient)");
+    CL_TRY(tl_ensure(c));
+    TwoLevel* t = c->tl2;
+    if (c->pcw_on && (c->pcw_grid[0] != t->g.n1 || c->pcw_grid[1] != t->g.n2 || c->pcw_grid[2] != t->g.n3))
+        return fail(c, CLAIRE_EINVAL, "preconditioner weight on %d x %d x %d, coarse grid %d x %d x %d",
+                    c->pcw_grid[0], c->pcw_grid[1], c->pcw_grid[2], t->g.n1, t->g.n2, t->g.n3);
+    PhaseScope ps(c, CLAIRE_PHASE_SPECTRAL);
+    const size_t N = c->N;
+    CL_TRY(mean_state_gradient(c, c->z));
     {
         KTimer kt(c, KK_FFT, 0, 0);
         CL_FFT(c, cufftExecR2C(c->r2c, c->z, c->spec2));
@@ -1004,6 +1027,11 @@ claire_status tl_prepare(claire_ctx* c)
     {
         KTimer kt(c, KK_FFT, 0, 0);
         CL_FFT(c, cufftExecC2R(t->c2r, t->xh, t->gbar));
+    }
+    if (c->pcw_on) {
+        KTimer kt(c, KK_POINTWISE, 28.0 * t->N, 0);
+        launch_tl_weight(t->gbar, c->pcw, t->N, c->stream);
+        CL_LAUNCHED(c);
     }
     return CLAIRE_OK;
 }
@@ -2028,6 +2056,55 @@ claire_status claire_spectral(claire_ctx* c, const float* in, float* out, int op
     CL_TRY(check_kernel_ptr(c, out));
     CL_TRY(spectral(c, in, out, static_cast<SpectralOp>(op)));
     CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_mean_state_gradient(claire_ctx* c, float* gbar)
+{
+    if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
+    CL_TRY(check_kernel_ptr(c, gbar));
+    CL_TRY(mean_state_gradient(c, gbar));
+    CL_CUDA(c, cudaStreamSynchronize(c->stream));
+    collect_timing(c);
+    return CLAIRE_OK;
+}
+
+claire_status claire_set_pc_weight(claire_ctx* c, const float* w, const int wgrid[3])
+{
+    if (!c) return CLAIRE_EINVAL;
+    CL_TRY(need_workspace(c));
+    if (!w) {
+        c->pcw_on = false;
+        return CLAIRE_OK;
+    }
+    if (!wgrid) return fail(c, CLAIRE_EINVAL, "null weight grid");
+    const int f = c->o.pc_coarse;
+    for (int a = 0; a < 3; ++a)
+        if (wgrid[a] < 1 || static_cast<long long>(wgrid[a]) * f != c->n[a])
+            return fail(c, CLAIRE_EINVAL, "weight grid %d x %d x %d is not the coarse grid (grid / %d)", wgrid[0],
+                        wgrid[1], wgrid[2], f);
+    const size_t nc = static_cast<size_t>(wgrid[0]) * wgrid[1] * wgrid[2];
+    c->pcw_on = false;
+    if (c->pcw && c->pcw_n != nc) {
+        cudaFree(c->pcw);
+        c->pcw = nullptr;
+    }
+    if (!c->pcw) {
+        if (cudaMalloc(&c->pcw, nc * sizeof(float)) != cudaSuccess) {
+            cudaGetLastError();
+            c->pcw = nullptr;
+            return fail(c, CLAIRE_ENOMEM, "preconditioner weight (%zu floats)", nc);
+        }
+        c->pcw_n = nc;
+    }
+    CL_CUDA(c, cudaMemcpyAsync(c->pcw, w, nc * sizeof(float), cudaMemcpyDefault, c->stream));
+    double ss = 0.0;
+    CL_TRY(dot(c, c->pcw, c->pcw, nc, &ss));
+    if (!std::isfinite(ss)) return fail(c, CLAIRE_ENONFINITE, "non-finite preconditioner weight");
+    for (int a = 0; a < 3; ++a) c->pcw_grid[a] = wgrid[a];
+    c->pcw_on = true;
     collect_timing(c);
     return CLAIRE_OK;
 }

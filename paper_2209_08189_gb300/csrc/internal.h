@@ -196,6 +196,8 @@ void launch_mean_levels(const void* m, int nt, float w_end, float w_mid, size_t 
 void launch_cscale(cufftComplex* x, size_t n, float s, cudaStream_t st);
 void launch_tl_restrict(const Grid& gf, const cufftComplex* F, size_t csf, const Grid& gc, cufftComplex* out,
                         size_t csc, float invN, cudaStream_t st);
+// coarse preconditioner correction: gbar_c [3][n] <- sqrt(max(w, 0)) gbar_c
+void launch_tl_weight(float* gbar_c, const float* w, size_t n, cudaStream_t st);
 void launch_tl_start(const Grid& gf, const cufftComplex* rf, size_t csf, const Grid& gc, cufftComplex* rh,
                      cufftComplex* xh, cufftComplex* ph, cufftComplex* cp, size_t cs, SpectralOp op, RegParams rp,
                      double* prr, double* prz, int nblocks, cudaStream_t st);

@@ -1061,44 +1061,45 @@ __global__ void k_pack_inputs(const float* __restrict__ m0, const float* __restr
     for (int c = 2; c < Cs; c += 2) *reinterpret_cast<__nv_bfloat162*>(x + c) = __floats2bfloat162_rn(0.f, 0.f);
 }
 
-// Output head (1x1x1 conv to 3 FP32 components, channels-first per sample):
-// V[b][c][p] = scale (bias[c] + sum_ci X[b,p][ci] Wh[c][ci])
-template <int CIN>
+// Output head (1x1x1 conv to NOUT FP32 channels, channels-first per sample):
+// V[b][c][p] = scale (bias[c] + sum_ci X[b,p][ci] Wh[c][ci]).  NOUT = 3: the
+// velocity; NOUT = 4: the velocity and the logit of the coarse preconditioner
+// weight.
+template <int CIN, int NOUT>
 __global__ void k_head(const __nv_bfloat16* __restrict__ X, int Cxs, const float* __restrict__ Wh,
                        const float* __restrict__ bh, float scale, size_t nvox_per, int B, float* __restrict__ V)
 {
     const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
     if (e >= nvox_per * B) return;
     const size_t b = e / nvox_per, p = e % nvox_per;
-    float s0 = bh[0], s1 = bh[1], s2 = bh[2];
+    float s[NOUT];
+#pragma unroll
+    for (int c = 0; c < NOUT; ++c) s[c] = bh[c];
     const __nv_bfloat16* x = X + e * Cxs;
 #pragma unroll
     for (int c = 0; c < CIN; c += 8) {
         const V8 xv = load8(x + c);
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-            s0 = fmaf(xv.f[q], __ldg(Wh + c + q), s0);
-            s1 = fmaf(xv.f[q], __ldg(Wh + CIN + c + q), s1);
-            s2 = fmaf(xv.f[q], __ldg(Wh + 2 * CIN + c + q), s2);
-        }
+        for (int q = 0; q < 8; ++q)
+#pragma unroll
+            for (int o = 0; o < NOUT; ++o) s[o] = fmaf(xv.f[q], __ldg(Wh + o * CIN + c + q), s[o]);
     }
-    float* vb = V + b * 3 * nvox_per + p;
-    vb[0] = scale * s0;
-    vb[nvox_per] = scale * s1;
-    vb[2 * nvox_per] = scale * s2;
+    float* vb = V + b * NOUT * nvox_per + p;
+#pragma unroll
+    for (int o = 0; o < NOUT; ++o) vb[o * nvox_per] = scale * s[o];
 }
 
 // head backward: dX[b,p][ci] = scale sum_c dV[b][c][p] Wh[c][ci]; per-block
 // partials of dWh[c][ci] = scale sum_p dV X and dbh[c] = scale sum_p dV,
-// layout [block][3 CIN + 3].
-template <int CIN>
+// layout [block][NOUT CIN + NOUT].
+template <int CIN, int NOUT>
 __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* __restrict__ X, int Cxs,
                                                   const float* __restrict__ Wh, float scale, size_t nvox_per,
                                                   int B, const float* __restrict__ dV,
                                                   __nv_bfloat16* __restrict__ dX, int Cdxs,
                                                   float* __restrict__ part)
 {
-    constexpr int NR = 3 * CIN + 3;
+    constexpr int NR = NOUT * CIN + NOUT;
     __shared__ float red[8][NR];
     float loc[NR];
 #pragma unroll
@@ -1107,38 +1108,42 @@ __global__ void __launch_bounds__(256) k_head_bwd(const __nv_bfloat16* __restric
     for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
          e += static_cast<size_t>(gridDim.x) * blockDim.x) {
         const size_t b = e / nvox_per, p = e % nvox_per;
-        const float* db = dV + b * 3 * nvox_per + p;
-        const float g0 = scale * db[0], g1 = scale * db[nvox_per], g2 = scale * db[2 * nvox_per];
+        const float* db = dV + b * NOUT * nvox_per + p;
+        float g[NOUT];
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) g[o] = scale * db[o * nvox_per];
 #pragma unroll
         for (int c = 0; c < CIN; c += 8) {
             const V8 xv = load8(X + e * Cxs + c);
-            V8 o;
+            V8 ov;
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
-                o.f[q] = g0 * __ldg(Wh + c + q) + g1 * __ldg(Wh + CIN + c + q) + g2 * __ldg(Wh + 2 * CIN + c + q);
-                loc[c + q] += g0 * xv.f[q];
-                loc[CIN + c + q] += g1 * xv.f[q];
-                loc[2 * CIN + c + q] += g2 * xv.f[q];
+                float t = 0.f;
+#pragma unroll
+                for (int o = 0; o < NOUT; ++o) {
+                    t += g[o] * __ldg(Wh + o * CIN + c + q);
+                    loc[o * CIN + c + q] += g[o] * xv.f[q];
+                }
+                ov.f[q] = t;
             }
-            if (dX) store8(dX + e * Cdxs + c, o);
+            if (dX) store8(dX + e * Cdxs + c, ov);
         }
-        loc[3 * CIN] += g0;
-        loc[3 * CIN + 1] += g1;
-        loc[3 * CIN + 2] += g2;
+#pragma unroll
+        for (int o = 0; o < NOUT; ++o) loc[NOUT * CIN + o] += g[o];
     }
     const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
 #pragma unroll
     for (int q = 0; q < NR; ++q) {
-        float s = loc[q];
+        float v = loc[q];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-        if (lane == 0) red[warp][q] = s;
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+        if (lane == 0) red[warp][q] = v;
     }
     __syncthreads();
     for (int q = threadIdx.x; q < NR; q += blockDim.x) {
-        float s = 0.f;
-        for (int w = 0; w < 8; ++w) s += red[w][q];
-        part[static_cast<size_t>(blockIdx.x) * NR + q] = s;
+        float v = 0.f;
+        for (int w = 0; w < 8; ++w) v += red[w][q];
+        part[static_cast<size_t>(blockIdx.x) * NR + q] = v;
     }
 }
 
@@ -1203,6 +1208,104 @@ __global__ void __launch_bounds__(256) k_residual(const float* x, const float* _
         for (int w = 0; w < 8; ++w) s += red[w];
         if (sum) atomicAdd(sum, s);
     }
+}
+
+// ---- coarse preconditioner correction: fit statistics, training loss, weight ----
+
+// Least-squares statistics of the model D ~ gbar w (gbar . p) for the data
+// term D = hp - sp of a Gauss-Newton matvec on the probe p (vector fields
+// [3][n]): num += a (gbar . D), den += a^2 |gbar|^2, a = gbar . p.
+__global__ void __launch_bounds__(256) k_pcw_stats(const float* __restrict__ gbar, const float* __restrict__ p,
+                                                   const float* __restrict__ hp, const float* __restrict__ sp,
+                                                   size_t n, float* __restrict__ num, float* __restrict__ den)
+{
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        float a = 0.f, dd = 0.f, g2 = 0.f;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            const float gc = gbar[c * n + e];
+            a = fmaf(gc, p[c * n + e], a);
+            dd = fmaf(gc, hp[c * n + e] - sp[c * n + e], dd);
+            g2 = fmaf(gc, gc, g2);
+        }
+        num[e] = fmaf(a, dd, num[e]);
+        den[e] = fmaf(a * a, g2, den[e]);
+    }
+}
+
+// *tot += sum x (FP64)
+__global__ void __launch_bounds__(256) k_sum_f64(const float* __restrict__ x, size_t n, double* __restrict__ tot)
+{
+    double loc = 0.0;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x)
+        loc += x[e];
+    __shared__ double red[8];
+    for (int o = 16; o > 0; o >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, o);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(tot, s);
+    }
+}
+
+__device__ __forceinline__ float softplus_f(float o) { return o > 20.f ? o : log1pf(expf(o)); }
+
+// Loss of the weight w = softplus(o) against the statistics pooled over the
+// 2 x 2 x 2 cell of each voxel (A = sum den, B = sum num of the cell):
+// L = sum_x (A w^2 - 2 B w + B^2 / A) / (8 T), T = *tot (sum of den), whose
+// minimiser is w = B / A in every cell with A > 0; dout = scale dL/do.
+// *loss += L.  Grid n1 x n2 x n3, all even.
+__global__ void __launch_bounds__(256) k_pcw_loss(const float* __restrict__ o, const float* __restrict__ num,
+                                                  const float* __restrict__ den, int n1, int n2, int n3,
+                                                  const double* __restrict__ tot, float scale,
+                                                  float* __restrict__ dout, double* __restrict__ loss)
+{
+    const size_t n = static_cast<size_t>(n1) * n2 * n3;
+    const double T = *tot;
+    const float inv = T > 0.0 ? static_cast<float>(1.0 / (8.0 * T)) : 0.f;
+    double loc = 0.0;
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const int k = static_cast<int>(e % n3), j = static_cast<int>((e / n3) % n2),
+                  i = static_cast<int>(e / (static_cast<size_t>(n2) * n3));
+        const size_t c0 = (static_cast<size_t>(i & ~1) * n2 + (j & ~1)) * n3 + (k & ~1);
+        float A = 0.f, B = 0.f;
+#pragma unroll
+        for (int a = 0; a < 2; ++a)
+#pragma unroll
+            for (int b = 0; b < 2; ++b)
+#pragma unroll
+                for (int c = 0; c < 2; ++c) {
+                    const size_t q = c0 + (static_cast<size_t>(a) * n2 + b) * n3 + c;
+                    A += den[q];
+                    B += num[q];
+                }
+        const float ov = o[e];
+        const float w = softplus_f(ov);
+        const float sig = 1.f / (1.f + expf(-ov));
+        dout[e] = scale * 2.f * inv * (A * w - B) * sig;
+        if (A > 0.f) loc += (static_cast<double>(A) * w * w - 2.0 * B * w + static_cast<double>(B) * B / A) * inv;
+    }
+    __shared__ double red[8];
+    for (int s = 16; s > 0; s >>= 1) loc += __shfl_down_sync(0xffffffffu, loc, s);
+    if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = loc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int w = 0; w < 8; ++w) s += red[w];
+        atomicAdd(loss, s);
+    }
+}
+
+// w = softplus(o)
+__global__ void k_pcw_weight(const float* __restrict__ o, float* __restrict__ w, size_t n)
+{
+    const size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x;
+    if (e < n) w[e] = softplus_f(o[e]);
 }
 
 inline unsigned nblk(size_t n, int t) { return static_cast<unsigned>((n + t - 1) / t); }
@@ -1531,15 +1634,19 @@ cudaError_t pack_inputs(const float* m0, const float* m1, float a0, float a1, si
     return cudaGetLastError();
 }
 
-cudaError_t head(const void* X, int Cxs, int Cin, const float* Wh, const float* bh, float scale, size_t nvox_per,
-                 int B, float* V, cudaStream_t st)
+cudaError_t head(const void* X, int Cxs, int Cin, int Nout, const float* Wh, const float* bh, float scale,
+                 size_t nvox_per, int B, float* V, cudaStream_t st)
 {
     auto x = static_cast<const __nv_bfloat16*>(X);
     const unsigned g = nblk(nvox_per * B, 256);
-    if (Cin == 16)
-        k_head<16><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
-    else if (Cin == 32)
-        k_head<32><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    if (Cin == 16 && Nout == 3)
+        k_head<16, 3><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    else if (Cin == 32 && Nout == 3)
+        k_head<32, 3><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    else if (Cin == 16 && Nout == 4)
+        k_head<16, 4><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
+    else if (Cin == 32 && Nout == 4)
+        k_head<32, 4><<<g, 256, 0, st>>>(x, Cxs, Wh, bh, scale, nvox_per, B, V);
     else
         return cudaErrorInvalidValue;
     return cudaGetLastError();
@@ -1552,18 +1659,23 @@ int head_bwd_blocks(size_t nvox, int nsm)
     return static_cast<int>(want < cap ? (want ? want : 1) : cap);
 }
 
-cudaError_t head_bwd(const void* X, int Cxs, int Cin, const float* Wh, float scale, size_t nvox_per, int B,
-                     const float* dV, void* dX, int Cdxs, int nblocks, float* part, float* dWb, cudaStream_t st)
+cudaError_t head_bwd(const void* X, int Cxs, int Cin, int Nout, const float* Wh, float scale, size_t nvox_per,
+                     int B, const float* dV, void* dX, int Cdxs, int nblocks, float* part, float* dWb,
+                     cudaStream_t st)
 {
     auto x = static_cast<const __nv_bfloat16*>(X);
     auto dx = static_cast<__nv_bfloat16*>(dX);
-    if (Cin == 16)
-        k_head_bwd<16><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
-    else if (Cin == 32)
-        k_head_bwd<32><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    if (Cin == 16 && Nout == 3)
+        k_head_bwd<16, 3><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    else if (Cin == 32 && Nout == 3)
+        k_head_bwd<32, 3><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    else if (Cin == 16 && Nout == 4)
+        k_head_bwd<16, 4><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
+    else if (Cin == 32 && Nout == 4)
+        k_head_bwd<32, 4><<<nblocks, 256, 0, st>>>(x, Cxs, Wh, scale, nvox_per, B, dV, dx, Cdxs, part);
     else
         return cudaErrorInvalidValue;
-    const size_t nred = static_cast<size_t>(3 * Cin + 3);
+    const size_t nred = static_cast<size_t>(Nout * Cin + Nout);
     k_reduce_partials<<<nblk(nred, 256), 256, 0, st>>>(part, nblocks, nred, dWb);
     return cudaGetLastError();
 }
@@ -1590,6 +1702,30 @@ cudaError_t residual(const float* x, const float* y, size_t n, float* r, double*
 {
     const unsigned g = static_cast<unsigned>(std::min<size_t>(nblk(n, 256), static_cast<size_t>(4 * nsm)));
     k_residual<<<g ? g : 1, 256, 0, st>>>(x, y, n, r, sum);
+    return cudaGetLastError();
+}
+
+cudaError_t pcw_stats(const float* gbar, const float* p, const float* hp, const float* sp, size_t n, float* num,
+                      float* den, int nsm, cudaStream_t st)
+{
+    const unsigned g = static_cast<unsigned>(std::min<size_t>(nblk(n, 256), static_cast<size_t>(8 * nsm)));
+    k_pcw_stats<<<g ? g : 1, 256, 0, st>>>(gbar, p, hp, sp, n, num, den);
+    return cudaGetLastError();
+}
+
+cudaError_t pcw_loss(const float* o, const float* num, const float* den, const int grid[3], float scale,
+                     float* dout, double* sums, int nsm, cudaStream_t st)
+{
+    const size_t n = static_cast<size_t>(grid[0]) * grid[1] * grid[2];
+    const unsigned g = static_cast<unsigned>(std::min<size_t>(nblk(n, 256), static_cast<size_t>(8 * nsm)));
+    k_sum_f64<<<g ? g : 1, 256, 0, st>>>(den, n, sums);
+    k_pcw_loss<<<g ? g : 1, 256, 0, st>>>(o, num, den, grid[0], grid[1], grid[2], sums, scale, dout, sums + 1);
+    return cudaGetLastError();
+}
+
+cudaError_t pcw_weight(const float* o, float* w, size_t n, cudaStream_t st)
+{
+    k_pcw_weight<<<nblk(n ? n : 1, 256), 256, 0, st>>>(o, w, n);
     return cudaGetLastError();
 }
 
@@ -1784,15 +1920,17 @@ extern "C" claire_status claire_net_pack(const float* m0, const float* m1, float
     return net_status(pack_inputs(m0, m1, a0, a1, nvox, x, stride, as_stream(stream)), "pack");
 }
 
-extern "C" claire_status claire_net_head(const void* x, int x_stride, int cin, const float* wh, const float* bh,
-                                         float scale, void* v, const int vol[4], void* stream)
+extern "C" claire_status claire_net_head(const void* x, int x_stride, int cin, int nout, const float* wh,
+                                         const float* bh, float scale, void* v, const int vol[4], void* stream)
 {
     if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("head: bad vol");
     NET_TRY(check_slice(x, x_stride, cin, "head x"));
     if (cin != 16 && cin != 32) return net_fail("head: cin %d (16 or 32)", cin);
+    if (nout != 3 && nout != 4) return net_fail("head: nout %d (3 or 4)", nout);
     if (!wh || !bh || !v) return net_fail("head: null pointer");
     const size_t nvox = static_cast<size_t>(vol[1]) * vol[2] * vol[3];
-    return net_status(head(x, x_stride, cin, wh, bh, scale, nvox, vol[0], static_cast<float*>(v), as_stream(stream)),
+    return net_status(head(x, x_stride, cin, nout, wh, bh, scale, nvox, vol[0], static_cast<float*>(v),
+                           as_stream(stream)),
                       "head");
 }
 
@@ -1804,21 +1942,22 @@ extern "C" claire_status claire_net_head_bwd_blocks(const int vol[4], int* block
     return CLAIRE_OK;
 }
 
-extern "C" claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, const float* wh, float scale,
-                                             const float* dv, void* dx, int dx_stride, const int vol[4], int blocks,
-                                             float* part, float* dwb, void* stream)
+extern "C" claire_status claire_net_head_bwd(const void* x, int x_stride, int cin, int nout, const float* wh,
+                                             float scale, const float* dv, void* dx, int dx_stride,
+                                             const int vol[4], int blocks, float* part, float* dwb, void* stream)
 {
     if (!vol || vol[0] < 1 || vol[1] < 1 || vol[2] < 1 || vol[3] < 1) return net_fail("head_bwd: bad vol");
     NET_TRY(check_slice(x, x_stride, cin, "head_bwd x"));
     if (dx) NET_TRY(check_slice(dx, dx_stride, cin, "head_bwd dx"));
     if (cin != 16 && cin != 32) return net_fail("head_bwd: cin %d (16 or 32)", cin);
+    if (nout != 3 && nout != 4) return net_fail("head_bwd: nout %d (3 or 4)", nout);
     int expect = 0;
     NET_TRY(claire_net_head_bwd_blocks(vol, &expect));
     if (blocks != expect) return net_fail("head_bwd: blocks %d, expected %d", blocks, expect);
     if (!wh || !dv || !part || !dwb) return net_fail("head_bwd: null pointer");
     const size_t nvox = static_cast<size_t>(vol[1]) * vol[2] * vol[3];
-    return net_status(head_bwd(x, x_stride, cin, wh, scale, nvox, vol[0], dv, dx, dx_stride, blocks, part, dwb,
-                               as_stream(stream)),
+    return net_status(head_bwd(x, x_stride, cin, nout, wh, scale, nvox, vol[0], dv, dx, dx_stride, blocks, part,
+                               dwb, as_stream(stream)),
                       "head_bwd");
 }
 
@@ -1844,6 +1983,28 @@ extern "C" claire_status claire_net_residual(const float* x, const float* y, siz
 {
     if (!x || !y) return net_fail("residual: null pointer");
     return net_status(residual(x, y, n, r, sum, device_sms(), as_stream(stream)), "residual");
+}
+
+extern "C" claire_status claire_net_pcw_stats(const float* gbar, const float* p, const float* hp, const float* sp,
+                                              size_t n, float* num, float* den, void* stream)
+{
+    if (!gbar || !p || !hp || !sp || !num || !den) return net_fail("pcw_stats: null pointer");
+    return net_status(pcw_stats(gbar, p, hp, sp, n, num, den, device_sms(), as_stream(stream)), "pcw_stats");
+}
+
+extern "C" claire_status claire_net_pcw_loss(const float* o, const float* num, const float* den, const int grid[3],
+                                             float scale, float* dout, double* sums, void* stream)
+{
+    if (!o || !num || !den || !grid || !dout || !sums) return net_fail("pcw_loss: null pointer");
+    if (grid[0] < 2 || grid[1] < 2 || grid[2] < 2 || (grid[0] | grid[1] | grid[2]) & 1)
+        return net_fail("pcw_loss: grid %d x %d x %d (even extents >= 2)", grid[0], grid[1], grid[2]);
+    return net_status(pcw_loss(o, num, den, grid, scale, dout, sums, device_sms(), as_stream(stream)), "pcw_loss");
+}
+
+extern "C" claire_status claire_net_pcw_weight(const float* o, float* w, size_t n, void* stream)
+{
+    if (!o || !w) return net_fail("pcw_weight: null pointer");
+    return net_status(pcw_weight(o, w, n, as_stream(stream)), "pcw_weight");
 }
 
 extern "C" claire_status claire_net_device_errors(int* count, int reset)

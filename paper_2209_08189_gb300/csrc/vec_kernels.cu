@@ -894,6 +894,25 @@ void launch_mean_levels(const void* m, int nt, float w_end, float w_mid, size_t 
     });
 }
 
+// Coarse preconditioner correction: gbar_c <- sqrt(max(w, 0)) gbar_c on the
+// coarse grid (three components of n values), so that the zero-velocity
+// operator of the result is S + gbar_c w gbar_c^T.
+__global__ void k_tl_weight(float* __restrict__ g, const float* __restrict__ w, size_t n)
+{
+    for (size_t e = blockIdx.x * static_cast<size_t>(blockDim.x) + threadIdx.x; e < n;
+         e += static_cast<size_t>(gridDim.x) * blockDim.x) {
+        const float s = sqrtf(fmaxf(w[e], 0.0f));
+        g[e] *= s;
+        g[n + e] *= s;
+        g[2 * n + e] *= s;
+    }
+}
+
+void launch_tl_weight(float* gbar_c, const float* w, size_t n, cudaStream_t st)
+{
+    k_tl_weight<<<stream_blocks(n), kThreads, 0, st>>>(gbar_c, w, n);
+}
+
 void launch_cscale(cufftComplex* x, size_t n, float s, cudaStream_t st)
 {
     k_cscale<<<stream_blocks(n), kThreads, 0, st>>>(reinterpret_cast<float2*>(x), n, s);

@@ -10,7 +10,9 @@ fallback: without the library or a CUDA device the calls fail.
 Architecture (4 levels, channels 16-32-64-128, ~1.46M parameters): per
 level two 3x3x3 convolutions with leaky ReLU; 2x2x2 average pooling down,
 nearest 2x upsampling up, skip connections by channel concatenation; a
-1x1x1 head to the three velocity components (physical units).  Periodic
+1x1x1 head to the three velocity components (physical units) and, with
+pc_head, a fourth channel: the logit o of the coarse preconditioner weight
+w = softplus(o) (the correction of the two-level preconditioner).  Periodic
 padding matches the registration domain.  Activations and conv weights are
 BF16 with FP32 accumulation; FP32 master weights and Adam moments.
 """
@@ -40,12 +42,15 @@ _SIGS = {
     "claire_net_up2_bwd": [_vp, _i, _i, _vp, _i, _ip, _vp],
     "claire_net_leaky_bwd": [_vp, _i, _vp, _i, _i, _f, _vp, _i, _ip, _vp],
     "claire_net_pack": [_vp, _vp, _f, _f, _sz, _vp, _i, _vp],
-    "claire_net_head": [_vp, _i, _i, _vp, _vp, _f, _vp, _ip, _vp],
+    "claire_net_head": [_vp, _i, _i, _i, _vp, _vp, _f, _vp, _ip, _vp],
     "claire_net_head_bwd_blocks": [_ip, _ip],
-    "claire_net_head_bwd": [_vp, _i, _i, _vp, _f, _vp, _vp, _i, _ip, _i, _vp, _vp, _vp],
+    "claire_net_head_bwd": [_vp, _i, _i, _i, _vp, _f, _vp, _vp, _i, _ip, _i, _vp, _vp, _vp],
     "claire_net_adam": [_vp, _vp, _vp, _vp, _sz, _f, _f, _f, _f, _i, _f, _vp, _vp],
     "claire_net_vel_loss": [_vp, _vp, _vp, _f, _f, _sz, _vp, _vp, _vp],
     "claire_net_residual": [_vp, _vp, _sz, _vp, _vp, _vp],
+    "claire_net_pcw_stats": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _vp],
+    "claire_net_pcw_loss": [_vp, _vp, _vp, _ip, _f, _vp, _vp, _vp],
+    "claire_net_pcw_weight": [_vp, _vp, _sz, _vp],
     "claire_net_device_errors": [_ip, _i],
     "claire_net_set_wait_test": [ctypes.c_uint, _i, _ip],
     "claire_net_set_conv_tiling": [_i, _i],
@@ -197,10 +202,13 @@ class UNet:
     channel 0 = a0 m0, channel 1 = a1 m1; output = vscale * head(...).
     """
 
-    def __init__(self, chans=(16, 32, 64, 128), cin=16, slope=0.1, vscale=1.0, seed=0, stream=None):
+    def __init__(self, chans=(16, 32, 64, 128), cin=16, slope=0.1, vscale=1.0, seed=0, stream=None,
+                 pc_head=False):
         import torch
         self.torch = torch
         self.chans, self.cin, self.slope, self.vscale = tuple(chans), cin, float(slope), float(vscale)
+        self.pc_head = bool(pc_head)
+        self.nout = 4 if self.pc_head else 3
         self.stream = stream
         self.dev = torch.device("cuda", torch.cuda.current_device())
         rng = np.random.default_rng(seed)
@@ -211,7 +219,11 @@ class UNet:
             w = rng.standard_normal((co, 27, ci)) * std
             self._add(name, w, np.zeros(co))
         c0 = self.chans[0]
-        self._add("head", rng.standard_normal((3, c0)) * (0.1 / math.sqrt(c0)), np.zeros(3), bf16=False)
+        hw = rng.standard_normal((self.nout, c0)) * (0.1 / math.sqrt(c0))
+        hb = np.zeros(self.nout)
+        if self.pc_head:
+            hb[3] = math.log(math.e - 1.0)  # softplus(o) = 1 at start: the paper's preconditioner
+        self._add("head", hw, hb, bf16=False)
         self.t = 0
         self._sync_weights()
         self._bufs = {}
@@ -266,7 +278,8 @@ class UNet:
             else:
                 arrays[k + ".w"] = w.astype(np.float32)
             arrays[k + ".b"] = b.astype(np.float32)
-        info = {"chans": list(self.chans), "cin": self.cin, "slope": self.slope, "vscale": self.vscale}
+        info = {"chans": list(self.chans), "cin": self.cin, "slope": self.slope, "vscale": self.vscale,
+                "pc_head": self.pc_head}
         if meta:
             info.update(meta)
         arrays["__meta__"] = np.frombuffer(json.dumps(info).encode(), dtype=np.uint8)
@@ -292,7 +305,7 @@ class UNet:
         """A network with the architecture and parameters stored in `path`."""
         meta, st = cls.read_weights(path)
         u = cls(chans=tuple(meta["chans"]), cin=meta["cin"], slope=meta["slope"], vscale=meta["vscale"],
-                seed=0, stream=stream)
+                seed=0, stream=stream, pc_head=meta.get("pc_head", False))
         u.load_state(st)
         u.meta = meta
         return u
@@ -333,9 +346,10 @@ class UNet:
         hb = ctypes.c_int()
         _check(lib().claire_net_head_bwd_blocks(_I4(B, D, H, W), ctypes.byref(hb)), "head_bwd_blocks")
         b["hblocks"] = hb.value
-        b["hpart"] = torch.empty(hb.value * (3 * ch[0] + 3), dtype=torch.float32, device=self.dev)
-        b["hgrad"] = torch.empty(3 * ch[0] + 3, dtype=torch.float32, device=self.dev)
-        b["v"] = torch.empty((B, 3, D, H, W), dtype=torch.float32, device=self.dev)
+        no = self.nout
+        b["hpart"] = torch.empty(hb.value * (no * ch[0] + no), dtype=torch.float32, device=self.dev)
+        b["hgrad"] = torch.empty(no * ch[0] + no, dtype=torch.float32, device=self.dev)
+        b["v"] = torch.empty((B, no, D, H, W), dtype=torch.float32, device=self.dev)
         self._bufs = {key: b}  # keep one shape at a time
         return b
 
@@ -379,10 +393,27 @@ class UNet:
             self._conv("dec%db" % l, da, d)
             h = d
         P = self.p["head"]
-        _check(lib().claire_net_head(h.ptr, h.stride, h.C, P["w"].data_ptr(), P["b"].data_ptr(), self.vscale,
-                                     b["v"].data_ptr(), h.v4(), self.stream), "head")
+        _check(lib().claire_net_head(h.ptr, h.stride, h.C, self.nout, P["w"].data_ptr(), P["b"].data_ptr(),
+                                     self.vscale, b["v"].data_ptr(), h.v4(), self.stream), "head")
         self._last = (B, D, H, W)
-        return b["v"]
+        return b["v"][:, :3]
+
+    def pc_logit(self):
+        """Channel 3 of the last forward pass (pc_head networks): [B, D, H, W],
+        the logit o of the coarse preconditioner weight w = softplus(o)."""
+        if not self.pc_head:
+            raise NetError("this network has no preconditioner head")
+        return self._bufs[self._last]["v"][:, 3]
+
+    def output_grad(self):
+        """Buffer [B, nout, D, H, W] (FP32) for the gradient of the loss with
+        respect to the head's output, the argument of backward()."""
+        B, D, H, W = self._last
+        key = ("dout", B, D, H, W)
+        if getattr(self, "_dout_key", None) != key:
+            self._dout = self.torch.zeros((B, self.nout, D, H, W), dtype=self.torch.float32, device=self.dev)
+            self._dout_key = key
+        return self._dout
 
     # ---- backward ----
     def _conv_back(self, name, xin, y, dy, dx):
@@ -399,19 +430,22 @@ class UNet:
             conv3d(g, P["wf"], None, dx, 0.0, 0, self.stream)
 
     def backward(self, dv):
-        """dv: FP32 [B, 3, D, H, W], gradient of the loss w.r.t. forward()'s output."""
+        """dv: FP32 [B, nout, D, H, W] (contiguous), gradient of the loss w.r.t.
+        the head's output: the velocity and, with pc_head, the logit."""
+        if tuple(dv.shape[:2]) != (self._last[0], self.nout) or not dv.is_contiguous():
+            raise NetError("backward: dv must be a contiguous [B, %d, D, H, W] tensor" % self.nout)
         b = self._bufs[self._last]
         ch, L = self.chans, len(self.chans)
         B, D, H, W = self._last
         P = self.p["head"]
         d0 = Act(b["d0"], 0, ch[0])
         gh = Act(b["g0_0"], 0, ch[0])
-        _check(lib().claire_net_head_bwd(d0.ptr, d0.stride, d0.C, P["w"].data_ptr(), self.vscale, dv.data_ptr(),
-                                         gh.ptr, gh.stride, d0.v4(), b["hblocks"], b["hpart"].data_ptr(),
-                                         b["hgrad"].data_ptr(), self.stream), "head_bwd")
-        c0 = ch[0]
-        P["gw"].copy_(b["hgrad"][:3 * c0].view(3, c0))
-        P["gb"].copy_(b["hgrad"][3 * c0:])
+        _check(lib().claire_net_head_bwd(d0.ptr, d0.stride, d0.C, self.nout, P["w"].data_ptr(), self.vscale,
+                                         dv.data_ptr(), gh.ptr, gh.stride, d0.v4(), b["hblocks"],
+                                         b["hpart"].data_ptr(), b["hgrad"].data_ptr(), self.stream), "head_bwd")
+        c0, no = ch[0], self.nout
+        P["gw"].copy_(b["hgrad"][:no * c0].view(no, c0))
+        P["gb"].copy_(b["hgrad"][no * c0:])
         dh = gh
         for l in range(L - 1):
             cat = b["cat%d" % l]

@@ -11,6 +11,17 @@ hand-written SL adjoint (see warmstart.train).
 
     python -m paper_2209_08189_gb300.train_warmstart --out paper_2209_08189_gb300/weights/unet_warmstart_128.npz
 
+With --pc-head the network also predicts the coarse preconditioner weight
+(a fourth output channel, see warmstart.train; --pc-target scale: the
+per-pair constant of warmstart.pc_scale_target, fit: the least-squares fit
+of the data term): starting from --init (the velocity network's weights; the
+new head row starts at w = 1), the velocity loss and wpc times the weight
+loss are trained together on pairs drawn the same way:
+
+    python -m paper_2209_08189_gb300.train_warmstart --pc-head --steps 1500 \
+        --init paper_2209_08189_gb300/weights/unet_warmstart_128.npz \
+        --out paper_2209_08189_gb300/weights/unet_warmstart_pc_128.npz
+
 Prints one JSON line with the training record.  Needs a CUDA GPU.
 """
 from __future__ import annotations
@@ -35,6 +46,12 @@ def main(argv=None):
     ap.add_argument("--velocities", type=int, default=200)
     ap.add_argument("--kmax", type=int, default=6)
     ap.add_argument("--seed", type=int, default=0)
+    ap.add_argument("--pc-head", action="store_true", help="also learn the coarse preconditioner weight")
+    ap.add_argument("--wpc", type=float, default=1.0, help="weight of the preconditioner-weight fit loss")
+    ap.add_argument("--pc-probes", type=int, default=2, help="probe fields per sample and step (--pc-target fit)")
+    ap.add_argument("--pc-target", default="scale", choices=["scale", "fit"],
+                    help="target of the preconditioner weight (see warmstart.train)")
+    ap.add_argument("--init", default=None, help="start from these weights (a velocity-only file is extended)")
     args = ap.parse_args(argv)
 
     import torch
@@ -50,16 +67,32 @@ def main(argv=None):
     src = warmstart.PairSource(args.n, n_templates=args.templates, n_velocities=args.velocities,
                                kmax=(args.kmax, args.kmax), vmax=(0.3, 1.2), noise=0.02, seed=args.seed)
     t_pool = time.perf_counter() - t0
-    u = net.UNet(seed=args.seed, stream=st)
+    u = net.UNet(seed=args.seed, stream=st, pc_head=args.pc_head)
+    init_meta = None
+    if args.init:
+        init_meta, state = net.UNet.read_weights(args.init)
+        if args.pc_head and not init_meta.get("pc_head", False):
+            # keep the new head row (small weights, bias at softplus^-1(1))
+            hw, hb = (x.cpu().numpy() for x in (u.p["head"]["w"], u.p["head"]["b"]))
+            hw[:3], hb[:3] = state["head"]
+            state["head"] = (hw, hb)
+        u.load_state(state)
     t0 = time.perf_counter()
-    hist = warmstart.train(u, src, steps=args.steps, batch=args.batch, lr=1e-3, lr_final=1e-4, wv=1.0, wm=1.0,
-                           log_every=max(1, args.steps // 20))
+    hist = warmstart.train(u, src, steps=args.steps, batch=args.batch, lr=1e-3 if not args.init else 2e-4,
+                           lr_final=1e-4 if not args.init else 2e-5, wv=1.0, wm=1.0,
+                           log_every=max(1, args.steps // 20), wpc=args.wpc if args.pc_head else 0.0,
+                           pc_probes=args.pc_probes, pc_target=args.pc_target)
     t_train = time.perf_counter() - t0
     src.ctx.close()
     record = {"grid": args.n, "steps": args.steps, "batch": args.batch, "pairs_drawn": args.steps * args.batch,
               "distinct_pairs": args.templates * args.velocities, "kmax": args.kmax, "vmax": [0.3, 1.2],
               "noise": 0.02, "params": u.num_params(), "pool_s": t_pool, "train_s": t_train,
-              "history": [{"step": h[0], "Lv": h[1], "mismatch_rel": h[2], "s": h[3]} for h in hist]}
+              "pc_head": args.pc_head, "wpc": args.wpc if args.pc_head else 0.0,
+              "pc_probes": args.pc_probes if args.pc_head else 0,
+              "pc_target": args.pc_target if args.pc_head else None,
+              "init": {"file": os.path.basename(args.init), "training": (init_meta or {}).get("training")}
+              if args.init else None,
+              "history": [{"step": h[0], "Lv": h[1], "mismatch_rel": h[2], "s": h[3], "Lpc": h[4]} for h in hist]}
     os.makedirs(os.path.dirname(os.path.abspath(args.out)), exist_ok=True)
     u.save_weights(args.out, meta={"n_net": args.n, "training": {k: v for k, v in record.items()
                                                                  if k != "history"}})

@@ -19,6 +19,7 @@ provides device memory.  Pair pools are drawn on the host once (numpy, the
 """
 from __future__ import annotations
 
+import ctypes
 import time
 
 import numpy as np
@@ -36,6 +37,7 @@ class PairSource:
         import torch
         self.torch = torch
         self.n = int(n)
+        self.nt = int(nt)
         grid = (self.n,) * 3
         rng = np.random.default_rng(seed)
         dev = torch.device("cuda", torch.cuda.current_device())
@@ -90,28 +92,123 @@ class PairSource:
         return m0, m1, vs
 
 
-def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_every=0, clip=None):
-    """Adam on the loss above; returns a list of (step, Lv, Lm_rel, seconds)."""
+def _pc_probes(n, count, seed):
+    """Band-limited probe fields of the preconditioner-weight fit (|k| <= 6)."""
+    return [synth.mode_velocity((n,) * 3, seed=seed + i, nmodes=8, kmax=6, vmax=0.3) for i in range(count)]
+
+
+PC_SCALES = (1.0, 1.5, 2.0, 3.0, 4.0, 6.0)
+PC_SCALE_FRACTION = 0.96
+
+
+def pc_scale_target(ctx, v, g, z, hz, consts):
+    """Target weight of the "scale" mode: with the two-level context ctx
+    linearised at v (the network's prediction), the smallest constant weight
+    c of PC_SCALES whose first preconditioned step z = P_c^-1 g achieves at
+    least PC_SCALE_FRACTION of the best quadratic-model decrease
+    q(c) = (g . z)^2 / (z . H z) over the list (larger weights make the coarse
+    inner solves harder for a smaller gain).  consts: constant coarse fields,
+    one per scale.  Returns (c, [q(c)])."""
+    N3 = g.numel()
+    ctx.gradient(v, g)
+    qs = []
+    for w in consts:
+        ctx.set_pc_weight(w)
+        ctx.precond(g, z)
+        ctx.hessian_matvec(z, hz)
+        gz = claire.claire_dot(ctx.handle, g, z, N3)
+        zhz = claire.claire_dot(ctx.handle, z, hz, N3)
+        qs.append(gz * gz / zhz if zhz > 0 else 0.0)
+    ctx.set_pc_weight(None)
+    best = max(qs)
+    for c, q in zip(PC_SCALES, qs):
+        if q >= PC_SCALE_FRACTION * best:
+            return c, qs
+    return PC_SCALES[-1], qs
+
+
+def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_every=0, clip=None, wpc=0.0,
+          pc_probes=2, pc_pool=8, pc_target="scale"):
+    """Adam on the loss above; returns a list of (step, Lv, Lm_rel, seconds, Lpc).
+
+    With a preconditioner head (net.pc_head) and wpc > 0, the loss adds wpc
+    times the loss of the coarse preconditioner weight w = softplus(o)
+    (claire_net_pcw_loss) against a per-sample target:
+    * pc_target "scale": the constant of pc_scale_target at the network's own
+      prediction of the pair (a spatially constant target);
+    * pc_target "fit": the least-squares fit of the weighted zero-velocity
+      data term to the true Gauss-Newton data term at the pair's v*, from
+      pc_probes probe fields per sample and step (drawn in turn from a pool of
+      pc_pool), the mean state gradient (claire_mean_state_gradient), the
+      matvec and S p."""
     torch = src.torch
     st = torch.cuda.current_stream().cuda_stream
     L = _netlib()
     n = src.n
     N = n ** 3
     dev = src.T.device
+    use_pc = bool(getattr(net, "pc_head", False)) and wpc > 0
     sums = torch.zeros(3 * batch, dtype=torch.float64, device=dev)
     mt = torch.empty((n, n, n), device=dev)
     r = torch.empty((n, n, n), device=dev)
     gv = torch.empty((3, n, n, n), device=dev)
-    dv = torch.empty((batch, 3, n, n, n), device=dev)
+    if use_pc:
+        probes = [torch.from_numpy(np.ascontiguousarray(q, dtype=np.float32)).to(dev)
+                  for q in _pc_probes(n, pc_pool, 7000)]
+        gbar = torch.empty((3, n, n, n), device=dev)
+        gtmp = torch.empty((3, n, n, n), device=dev)
+        hp = torch.empty((3, n, n, n), device=dev)
+        sp = torch.empty((3, n, n, n), device=dev)
+        num = torch.empty((batch, n, n, n), device=dev)
+        den = torch.empty((batch, n, n, n), device=dev)
+        psums = torch.zeros(2 * batch, dtype=torch.float64, device=dev)
+        grid3 = (ctypes.c_int * 3)(n, n, n)
+        if pc_target == "scale":
+            pcctx = claire.Context((n,) * 3, 1e-2, src.nt, stream=st, precond=claire.PRECOND_TWO_LEVEL)
+            consts = [torch.full((n // 2,) * 3, c, device=dev) for c in PC_SCALES]
+            pz = torch.empty((3, n, n, n), device=dev)
+        elif pc_target != "fit":
+            raise ValueError("pc_target: 'scale' or 'fit'")
     hist = []
     t0 = time.perf_counter()
     a = wv / (3.0 * N * src.sigma2)
+    kp = 0
     for it in range(steps):
         frac = it / max(1, steps - 1)
         lr_it = lr if lr_final is None else lr * (lr_final / lr) ** frac
         m0, m1, vs = src.batch(batch)
         v = net.forward(m0, m1)
+        dv = net.output_grad()
         sums.zero_()
+        if use_pc:
+            # statistics at v* of each pair, then the weight loss on channel 3
+            num.zero_()
+            den.zero_()
+            psums.zero_()
+            o = net.pc_logit()
+            for b in range(batch):
+                if pc_target == "scale":
+                    pcctx.set_images(m0[b], m1[b])
+                    c, _ = pc_scale_target(pcctx, v[b], gtmp, pz, hp, consts)
+                    num[b].fill_(c)
+                    den[b].fill_(1.0)
+                    _check(L.claire_net_pcw_loss(o[b].data_ptr(), num[b].data_ptr(), den[b].data_ptr(), grid3,
+                                                 wpc, dv[b, 3].data_ptr(), psums[2 * b:].data_ptr(), st),
+                           "pcw_loss")
+                    continue
+                src.ctx.set_images(m0[b], m1[b])
+                src.ctx.gradient(vs[b], gtmp)
+                src.ctx.mean_state_gradient(gbar)
+                for _ in range(pc_probes):
+                    q = probes[kp % len(probes)]
+                    kp += 1
+                    src.ctx.hessian_matvec(q, hp)
+                    src.ctx.spectral(q, sp, claire.SPECTRAL_REG)
+                    _check(L.claire_net_pcw_stats(gbar.data_ptr(), q.data_ptr(), hp.data_ptr(), sp.data_ptr(), N,
+                                                  num[b].data_ptr(), den[b].data_ptr(), st), "pcw_stats")
+                _check(L.claire_net_pcw_loss(o[b].data_ptr(), num[b].data_ptr(), den[b].data_ptr(), grid3,
+                                             wpc, dv[b, 3].data_ptr(), psums[2 * b:].data_ptr(), st),
+                       "pcw_loss")
         if wm > 0:
             for b in range(batch):
                 _check(L.claire_net_residual(m0[b].data_ptr(), m1[b].data_ptr(), N, None,
@@ -135,8 +232,11 @@ def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_
             s = sums.cpu().numpy()
             Lv = 0.5 * a * float(np.sum(s[0::3])) / batch
             Lm = float(np.mean(s[1::3] / np.maximum(s[2::3], 1e-30))) if wm > 0 else float("nan")
-            hist.append((it, Lv, Lm, time.perf_counter() - t0))
+            Lpc = float(np.mean(psums.cpu().numpy()[1::2])) if use_pc else float("nan")
+            hist.append((it, Lv, Lm, time.perf_counter() - t0, Lpc))
     torch.cuda.synchronize()
+    if use_pc and pc_target == "scale":
+        pcctx.close()
     return hist
 
 
@@ -164,3 +264,21 @@ class WarmStart:
         v = self.net.forward(a[0], a[1])
         claire.claire_resample(v[0], g, v_out, grid, 3, claire.RESAMPLE_SPECTRAL, st)
         return v_out
+
+    def pc_weight(self, w_out):
+        """Coarse preconditioner weight from the last predict() (networks with
+        a preconditioner head): the fourth output channel, the logit o, is
+        carried to w_out's grid (the two-level preconditioner's coarse grid) by
+        spectral resampling and mapped to w = softplus(o) > 0 there; w_out:
+        FP32 CUDA [Nc1, Nc2, Nc3]."""
+        torch = self.net.torch
+        o = self.net.pc_logit()[0]
+        g = (self.n_net,) * 3
+        wgrid = tuple(w_out.shape)
+        st = torch.cuda.current_stream().cuda_stream
+        src = o
+        if wgrid != g:
+            src = torch.empty(wgrid, device=o.device)
+            claire.claire_resample(o, g, src, wgrid, 1, claire.RESAMPLE_SPECTRAL, st)
+        _check(_netlib().claire_net_pcw_weight(src.data_ptr(), w_out.data_ptr(), w_out.numel(), st), "pcw_weight")
+        return w_out

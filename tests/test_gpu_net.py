@@ -230,18 +230,21 @@ def test_unet_weight_file_round_trip(env, tmp_path):
     bits (conv weights are stored as the BF16 values the forward pass uses)."""
     torch, net = env
     st = stream(torch)
-    u = net.UNet(seed=3, stream=st)
     r = np.random.default_rng(8)
     m0 = torch.from_numpy(r.random((32, 32, 32), dtype=np.float32)).cuda()
     m1 = torch.from_numpy(r.random((32, 32, 32), dtype=np.float32)).cuda()
-    a = u.forward(m0[None], m1[None]).clone()
-    path = str(tmp_path / "w.npz")
-    u.save_weights(path, meta={"n_net": 32})
-    w = net.UNet.from_file(path, stream=st)
-    b = w.forward(m0[None], m1[None])
-    torch.cuda.synchronize()
-    assert w.meta["n_net"] == 32 and w.num_params() == u.num_params()
-    assert torch.equal(a, b)
+    for pc_head in (False, True):  # velocity only; velocity + preconditioner-weight logit
+        u = net.UNet(seed=3, stream=st, pc_head=pc_head)
+        a = u.forward(m0[None], m1[None]).clone()
+        path = str(tmp_path / ("w%d.npz" % pc_head))
+        u.save_weights(path, meta={"n_net": 32})
+        w = net.UNet.from_file(path, stream=st)
+        b = w.forward(m0[None], m1[None])
+        torch.cuda.synchronize()
+        assert w.meta["n_net"] == 32 and w.num_params() == u.num_params() and w.pc_head == pc_head
+        assert torch.equal(a, b)
+        if pc_head:
+            assert torch.equal(u.pc_logit(), w.pc_logit())
 
 
 def test_pool_up_leaky_pack_head_adam(env):
@@ -279,27 +282,30 @@ def test_pool_up_leaky_pack_head_adam(env):
     torch.cuda.synchronize()
     rx = onet.pack(m0.cpu().numpy(), m1.cpu().numpy(), 2.0, -1.0, 16)
     assert close_bf16(f64(xb), rx) <= 0
-    wh = torch.from_numpy(r.standard_normal((3, 16)).astype(np.float32)).cuda()
-    bh = torch.from_numpy(r.standard_normal(3).astype(np.float32)).cuda()
-    v = torch.empty((B, 3, D, H, W), device="cuda")
-    x = net.Act(xb, 0, 16)
-    net._check(L.claire_net_head(x.ptr, 16, 16, wh.data_ptr(), bh.data_ptr(), 0.5, v.data_ptr(), x.v4(), st), "head")
-    dv = torch.from_numpy(r.standard_normal((B, 3, D, H, W)).astype(np.float32)).cuda()
-    import ctypes
-    nb = ctypes.c_int()
-    net._check(L.claire_net_head_bwd_blocks(x.v4(), ctypes.byref(nb)), "blocks")
-    part = torch.empty(nb.value * 51, device="cuda")
-    dwb = torch.empty(51, device="cuda")
-    dx = torch.empty((B, D, H, W, 16), dtype=torch.bfloat16, device="cuda")
-    net._check(L.claire_net_head_bwd(x.ptr, 16, 16, wh.data_ptr(), 0.5, dv.data_ptr(), dx.data_ptr(), 16, x.v4(),
-                                     nb.value, part.data_ptr(), dwb.data_ptr(), st), "head_bwd")
-    torch.cuda.synchronize()
-    xr = f64(xb)
-    assert rel_l2(f64(v), onet.head(xr, f64(wh), f64(bh), 0.5)) < 1e-5
-    rdx, rdw, rdb = onet.head_grad(xr, f64(wh), 0.5, f64(dv))
-    assert close_bf16(f64(dx), rdx) <= 0
-    assert rel_l2(f64(dwb)[:48].reshape(3, 16), rdw) < 1e-4
-    assert rel_l2(f64(dwb)[48:], rdb) < 1e-4
+    for nout in (3, 4):  # velocity head; velocity + preconditioner-weight logit
+        wh = torch.from_numpy(r.standard_normal((nout, 16)).astype(np.float32)).cuda()
+        bh = torch.from_numpy(r.standard_normal(nout).astype(np.float32)).cuda()
+        v = torch.empty((B, nout, D, H, W), device="cuda")
+        x = net.Act(xb, 0, 16)
+        net._check(L.claire_net_head(x.ptr, 16, 16, nout, wh.data_ptr(), bh.data_ptr(), 0.5, v.data_ptr(), x.v4(),
+                                     st), "head")
+        dv = torch.from_numpy(r.standard_normal((B, nout, D, H, W)).astype(np.float32)).cuda()
+        import ctypes
+        nb = ctypes.c_int()
+        net._check(L.claire_net_head_bwd_blocks(x.v4(), ctypes.byref(nb)), "blocks")
+        nr = nout * 16 + nout
+        part = torch.empty(nb.value * nr, device="cuda")
+        dwb = torch.empty(nr, device="cuda")
+        dx = torch.empty((B, D, H, W, 16), dtype=torch.bfloat16, device="cuda")
+        net._check(L.claire_net_head_bwd(x.ptr, 16, 16, nout, wh.data_ptr(), 0.5, dv.data_ptr(), dx.data_ptr(), 16,
+                                         x.v4(), nb.value, part.data_ptr(), dwb.data_ptr(), st), "head_bwd")
+        torch.cuda.synchronize()
+        xr = f64(xb)
+        assert rel_l2(f64(v), onet.head(xr, f64(wh), f64(bh), 0.5)) < 1e-5
+        rdx, rdw, rdb = onet.head_grad(xr, f64(wh), 0.5, f64(dv))
+        assert close_bf16(f64(dx), rdx) <= 0
+        assert rel_l2(f64(dwb)[:nout * 16].reshape(nout, 16), rdw) < 1e-4
+        assert rel_l2(f64(dwb)[nout * 16:], rdb) < 1e-4
     # Adam, three steps
     n = 1000
     w = torch.from_numpy(r.standard_normal(n).astype(np.float32)).cuda()

@@ -36,7 +36,7 @@ def trained(env):
 
 def test_training_reduces_loss(trained):
     u, hist = trained
-    for it, lv, lm, t in hist:
+    for it, lv, lm, t, *_ in hist:
         print("step %4d  Lv %.4f  mismatch rel %.4f  %.1fs" % (it, lv, lm, t))
     first = np.mean([h[1] for h in hist[:1]])
     last = np.mean([h[1] for h in hist[-2:]])
@@ -122,3 +122,69 @@ def test_resample_spectral_roundtrip_and_nearest(env):
     # the fine field restricted to even nodes is the coarse field
     assert np.max(np.abs(vf.cpu().numpy()[:, ::2, ::2, ::2] - v)) < 1e-5
     assert np.array_equal(nn_.cpu().numpy(), vf.cpu().numpy()[:, ::2, ::2, ::2])
+
+
+def test_preconditioner_head_learns_the_weight_fit(env):
+    """A network with the preconditioner head fits the weight of one fixed
+    pair (the weight-fit loss alone, the same two probe fields every step, so
+    the target is fixed):
+    the loss falls well below its value at w = 1, the predicted weight is
+    positive and finite, and the two-level preconditioner accepts it."""
+    torch, claire, net, warmstart = env
+    st = torch.cuda.current_stream().cuda_stream
+    src = warmstart.PairSource(32, n_templates=1, n_velocities=1, kmax=(3, 3), vmax=(0.8, 0.8), noise=0.0,
+                               seed=9)
+    u = net.UNet(seed=2, stream=st, pc_head=True)
+    hist = warmstart.train(u, src, steps=200, batch=1, lr=1e-3, wv=0.0, wm=0.0, log_every=10, wpc=1.0,
+                           pc_probes=2, pc_pool=2, pc_target="fit")
+    for it, lv, lm, t, lpc in hist:
+        print("step %4d  Lpc %.5f  %.1fs" % (it, lpc, t))
+    first = hist[0][4]
+    last = float(np.mean([h[4] for h in hist[-4:]]))
+    assert np.isfinite(last) and last < 0.5 * first
+    ws = warmstart.WarmStart(u, 32)
+    grid = (32, 32, 32)
+    m0, m1, _ = src.batch(1)
+    v = torch.empty((3,) + grid, device="cuda")
+    ws.predict(m0[0], m1[0], v)
+    w = torch.empty((16, 16, 16), device="cuda")
+    ws.pc_weight(w)
+    torch.cuda.synchronize()
+    wh = w.cpu().numpy()
+    assert np.all(np.isfinite(wh)) and wh.min() > 0.0
+    ctx = claire.Context(grid, 1e-2, 4, stream=st, precond=claire.PRECOND_TWO_LEVEL)
+    ctx.set_images(m0[0].contiguous(), m1[0].contiguous())
+    g = torch.empty((3,) + grid, device="cuda")
+    ctx.gradient(v, g)
+    ctx.set_pc_weight(w)
+    z = torch.empty_like(g)
+    ctx.precond(g, z)
+    torch.cuda.synchronize()
+    assert np.all(np.isfinite(z.cpu().numpy()))
+    ctx.close()
+    src.ctx.close()
+
+
+def test_scale_target_rule(env):
+    """pc_scale_target returns a weight of the list with finite positive
+    first-step decreases; on constant images (gbar = 0, g = S v) the coarse
+    operator does not depend on the weight, so every decrease is the same
+    and the smallest weight, 1, is returned."""
+    torch, claire, net, warmstart = env
+    st = torch.cuda.current_stream().cuda_stream
+    grid = (32, 32, 32)
+    m0 = torch.from_numpy(synth.blob_template(grid, seed=4).astype(np.float32)).cuda()
+    vstar = torch.from_numpy(synth.bandlimited_velocity(grid, seed=5, kmax=3, vmax=0.8).astype(np.float32)).cuda()
+    ctx = claire.Context(grid, 1e-2, 4, stream=st, precond=claire.PRECOND_TWO_LEVEL)
+    m1 = torch.empty(grid, device="cuda")
+    ctx.transport(vstar, m0, m1)
+    ctx.set_images(m0, m1)
+    consts = [torch.full((16, 16, 16), c, device="cuda") for c in warmstart.PC_SCALES]
+    g, z, hz = (torch.empty((3,) + grid, device="cuda") for _ in range(3))
+    c, qs = warmstart.pc_scale_target(ctx, (0.5 * vstar).contiguous(), g, z, hz, consts)
+    assert c in warmstart.PC_SCALES and all(np.isfinite(q) and q > 0 for q in qs)
+    flat = torch.full(grid, 0.5, device="cuda")
+    ctx.set_images(flat, flat)
+    c0, q0 = warmstart.pc_scale_target(ctx, (0.5 * vstar).contiguous(), g, z, hz, consts)
+    assert c0 == 1.0 and min(q0) > 0 and max(q0) == min(q0)
+    ctx.close()

@@ -639,11 +639,14 @@ __global__ void __launch_bounds__(kWgThreads) k_wgrad_tc(const __nv_bfloat16* __
                     break;
                 }
             }
+            // depth fastest: consecutive bricks of a chunk are depth neighbours, so
+            // the dY (and X) planes d0 - 1 .. d0 + 1 that a brick shares with the
+            // next one are still in L2 when it stages them
             int r = first + j;
+            const int d0 = r % v.D; r /= v.D;
             const int w0 = (r % nbw) * kTcBW; r /= nbw;
-            const int h0 = (r % nbh) * kTcBH; r /= nbh;
-            const int d0 = r % v.D;
-            const int b = r / v.D;
+            const int h0 = (r % nbh) * kTcBH;
+            const int b = r / nbh;
             // dY rows (s, hr): 8 voxels x cbn pieces -> hr * albo + (s * cbn + cb) * 128 + voxel * 16
             if (ja_r < rppa) {
                 for (int rr = ja_r; rr < 16 * wg.nsa; rr += rppa) {

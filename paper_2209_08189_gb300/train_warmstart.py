@@ -51,6 +51,8 @@ def main(argv=None):
     ap.add_argument("--pc-probes", type=int, default=2, help="probe fields per sample and step (--pc-target fit)")
     ap.add_argument("--pc-target", default="scale", choices=["scale", "fit"],
                     help="target of the preconditioner weight (see warmstart.train)")
+    ap.add_argument("--pc-grid", type=int, default=None,
+                    help="grid of the scale target (--pc-target scale; default the training grid)")
     ap.add_argument("--init", default=None, help="start from these weights (a velocity-only file is extended)")
     args = ap.parse_args(argv)
 
@@ -81,7 +83,7 @@ def main(argv=None):
     hist = warmstart.train(u, src, steps=args.steps, batch=args.batch, lr=1e-3 if not args.init else 2e-4,
                            lr_final=1e-4 if not args.init else 2e-5, wv=1.0, wm=1.0,
                            log_every=max(1, args.steps // 20), wpc=args.wpc if args.pc_head else 0.0,
-                           pc_probes=args.pc_probes, pc_target=args.pc_target)
+                           pc_probes=args.pc_probes, pc_target=args.pc_target, pc_grid=args.pc_grid)
     t_train = time.perf_counter() - t0
     src.ctx.close()
     record = {"grid": args.n, "steps": args.steps, "batch": args.batch, "pairs_drawn": args.steps * args.batch,
@@ -90,6 +92,7 @@ def main(argv=None):
               "pc_head": args.pc_head, "wpc": args.wpc if args.pc_head else 0.0,
               "pc_probes": args.pc_probes if args.pc_head else 0,
               "pc_target": args.pc_target if args.pc_head else None,
+              "pc_grid": (args.pc_grid or args.n) if args.pc_head else None,
               "init": {"file": os.path.basename(args.init), "training": (init_meta or {}).get("training")}
               if args.init else None,
               "history": [{"step": h[0], "Lv": h[1], "mismatch_rel": h[2], "s": h[3], "Lpc": h[4]} for h in hist]}

@@ -128,14 +128,16 @@ def pc_scale_target(ctx, v, g, z, hz, consts):
 
 
 def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_every=0, clip=None, wpc=0.0,
-          pc_probes=2, pc_pool=8, pc_target="scale"):
+          pc_probes=2, pc_pool=8, pc_target="scale", pc_grid=None):
     """Adam on the loss above; returns a list of (step, Lv, Lm_rel, seconds, Lpc).
 
     With a preconditioner head (net.pc_head) and wpc > 0, the loss adds wpc
     times the loss of the coarse preconditioner weight w = softplus(o)
     (claire_net_pcw_loss) against a per-sample target:
     * pc_target "scale": the constant of pc_scale_target at the network's own
-      prediction of the pair (a spatially constant target);
+      prediction of the pair (a spatially constant target), on the pair and
+      the prediction carried spectrally to pc_grid^3 (the grid of the
+      registrations the weight is meant for; default the training grid);
     * pc_target "fit": the least-squares fit of the weighted zero-velocity
       data term to the true Gauss-Newton data term at the pair's v*, from
       pc_probes probe fields per sample and step (drawn in turn from a pool of
@@ -164,9 +166,17 @@ def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_
         psums = torch.zeros(2 * batch, dtype=torch.float64, device=dev)
         grid3 = (ctypes.c_int * 3)(n, n, n)
         if pc_target == "scale":
-            pcctx = claire.Context((n,) * 3, 1e-2, src.nt, stream=st, precond=claire.PRECOND_TWO_LEVEL)
-            consts = [torch.full((n // 2,) * 3, c, device=dev) for c in PC_SCALES]
-            pz = torch.empty((3, n, n, n), device=dev)
+            ng = int(pc_grid or n)
+            G = (ng,) * 3
+            pcctx = claire.Context(G, 1e-2, src.nt, stream=st, precond=claire.PRECOND_TWO_LEVEL)
+            consts = [torch.full((ng // 2,) * 3, c, device=dev) for c in PC_SCALES]
+            pz = torch.empty((3,) + G, device=dev)
+            if ng != n:  # the target is taken on the pair carried to the registration grid
+                pg = torch.empty((3,) + G, device=dev)
+                phz = torch.empty((3,) + G, device=dev)
+                pm0 = torch.empty(G, device=dev)
+                pm1 = torch.empty(G, device=dev)
+                pv = torch.empty((3,) + G, device=dev)
         elif pc_target != "fit":
             raise ValueError("pc_target: 'scale' or 'fit'")
     hist = []
@@ -188,8 +198,16 @@ def train(net, src, steps, batch=4, lr=1e-3, wv=1.0, wm=1.0, lr_final=None, log_
             o = net.pc_logit()
             for b in range(batch):
                 if pc_target == "scale":
-                    pcctx.set_images(m0[b], m1[b])
-                    c, _ = pc_scale_target(pcctx, v[b], gtmp, pz, hp, consts)
+                    if ng == n:
+                        pcctx.set_images(m0[b], m1[b])
+                        c, _ = pc_scale_target(pcctx, v[b], gtmp, pz, hp, consts)
+                    else:
+                        g3n = (n,) * 3
+                        claire.claire_resample(m0[b], g3n, pm0, G, 1, claire.RESAMPLE_SPECTRAL, st)
+                        claire.claire_resample(m1[b], g3n, pm1, G, 1, claire.RESAMPLE_SPECTRAL, st)
+                        claire.claire_resample(v[b], g3n, pv, G, 3, claire.RESAMPLE_SPECTRAL, st)
+                        pcctx.set_images(pm0, pm1)
+                        c, _ = pc_scale_target(pcctx, pv, pg, pz, phz, consts)
                     num[b].fill_(c)
                     den[b].fill_(1.0)
                     _check(L.claire_net_pcw_loss(o[b].data_ptr(), num[b].data_ptr(), den[b].data_ptr(), grid3,

@@ -197,3 +197,55 @@ def test_pcw_stats_loss_and_weight_kernels(env):
     assert abs(s[1] - ref_L) <= 1e-5 * abs(ref_L)
     assert rel_l2(host(dout), ref_d) <= 1e-5
     assert rel_l2(host(wdev), w) <= 1e-6
+
+
+def test_learned_weight_cuts_outer_iterations_at_256(env):
+    """The committed network's coarse preconditioner weight on the 256^3
+    clinical-size pair (FP16 storage, two-level preconditioner, the network's
+    own warm start, stop at 5e-2 |g(v = 0)|): fewer outer PCG iterations than
+    the paper's two-level preconditioner alone (w = 1), at the same objective
+    within 1 %."""
+    torch, claire, net = env
+    import os
+    from paper_2209_08189_gb300 import warmstart
+    path = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "paper_2209_08189_gb300",
+                        "weights", "unet_warmstart_pc_128.npz")
+    if not os.path.exists(path):
+        pytest.skip("no network with the preconditioner head")
+    st = torch.cuda.current_stream().cuda_stream
+    grid = (256, 256, 256)
+    N = 256 ** 3
+    base = dev(torch, synth.label_template(grid, seed=0))
+    vstar = dev(torch, synth.bandlimited_velocity(grid, seed=0, kmax=8, vmax=1.0))
+    ctx32 = claire.Context(grid, 1e-2, 4, stream=st, beta_w=1e-4)
+    m1c = torch.empty(grid, device="cuda")
+    ctx32.transport(vstar, base, m1c, claire.TRANSPORT_FWD)
+    m0 = dev(torch, synth.add_noise(host(base), 0.02, seed=0))
+    m1 = dev(torch, synth.add_noise(host(m1c), 0.02, seed=1))
+    ctx32.set_images(m0, m1)
+    zero = torch.zeros((3,) + grid, device="cuda")
+    g = torch.empty_like(zero)
+    ctx32.gradient(zero, g)
+    g0 = float(np.sqrt(claire.claire_dot(ctx32.handle, g, g, 3 * N)))
+    ctx = claire.Context(grid, 1e-2, 4, stream=st, beta_w=1e-4, gtol=5e-2, max_gn=50, max_pcg=50,
+                         storage=claire.STORAGE_F16, g0_ref=g0, precond=claire.PRECOND_TWO_LEVEL)
+    ctx.set_images(m0, m1)
+    u = net.UNet.from_file(path, stream=st)
+    ws = warmstart.WarmStart(u, int(u.meta["n_net"]))
+    v0 = torch.empty_like(zero)
+    ws.predict(m0, m1, v0)
+    w = torch.empty((128, 128, 128), device="cuda")
+    ws.pc_weight(w)
+    out = {}
+    for name, wt in (("paper", None), ("learned", w)):
+        ctx.set_pc_weight(wt)
+        v = v0.clone()
+        status, rep = ctx.register(v, check=False)
+        assert status == 0, (name, rep)
+        out[name] = (rep["pcg_iters_total"], ctx32.objective(v)[0])
+    print("outer PCG / J: paper %d / %.6f, learned weight %d / %.6f (w mean %.3f)"
+          % (out["paper"][0], out["paper"][1], out["learned"][0], out["learned"][1], float(w.mean())))
+    assert out["learned"][0] < out["paper"][0]
+    assert abs(out["learned"][1] - out["paper"][1]) <= 0.01 * out["paper"][1]
+    ctx.close()
+    ctx32.close()

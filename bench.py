@@ -65,8 +65,11 @@ def parse_args():
                          "learned warm start, both without stored state gradients; Dice on 3 labels; the same "
                          "registration on images sampled to 256^3 and 512^3; sampled oracle parity")
     ap.add_argument("--large-n", type=int, default=1024)
-    ap.add_argument("--large-precond", default="spectral", choices=["spectral", "two-level"],
-                    help="preconditioner of the mixed + learned run of --large-report")
+    ap.add_argument("--large-precond", default="spectral", choices=["spectral", "two-level", "both"],
+                    help="preconditioner of the mixed + learned run of --large-report (both: the spectral run, "
+                         "then the same learned registration with the two-level preconditioner)")
+    ap.add_argument("--large-pc-coarse", type=int, default=4,
+                    help="fine-to-coarse ratio of the two-level preconditioner in --large-report")
     ap.add_argument("--large-vmax", type=float, default=0.5,
                     help="max |v*| of the large case (0.5: CFL 20 at 1024^3, nt=4)")
     ap.add_argument("--net-report", action="store_true",
@@ -1300,7 +1303,7 @@ def run_large_report(args):
                          storage=claire.STORAGE_F16, lowmem=1, wall_limit_s=1200,
                          spectral_iterate=args.spectral_iterate,
                          precond=claire.PRECOND_TWO_LEVEL if args.large_precond == "two-level"
-                         else claire.PRECOND_SPECTRAL)
+                         else claire.PRECOND_SPECTRAL, pc_coarse=args.large_pc_coarse)
     out["fp16_lowmem_device_gb"] = used_gb()
     out["learned_run_precond"] = args.large_precond
     vstar = torch.empty((3,) + grid, device=dev)
@@ -1437,6 +1440,29 @@ def run_large_report(args):
                                    "mismatch_at_%d_after_prolongation" % n: mis_f, "dice": dice(vf)}
         del vf, vc
         flush()
+    if args.large_precond == "both":
+        # the same learned registration with the two-level zero-velocity
+        # preconditioner (timed from the prediction; g(v = 0) is reused)
+        ctx.set_opts(precond=claire.PRECOND_TWO_LEVEL, g0_ref=g0)
+        v = torch.empty((3,) + grid, device=dev)
+        a0, a1 = sampled(128)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        vc = u.forward(a0, a1)
+        claire.claire_resample(vc[0], (128,) * 3, v, grid, 3, claire.RESAMPLE_SPECTRAL, st)
+        stt, rep = ctx.register(v, check=False)
+        torch.cuda.synchronize()
+        runs["fp16_learned_two_level"] = {
+            "time_to_tol_s": time.perf_counter() - t0, "pc_coarse": args.large_pc_coarse,
+            "status": rep["status"], "gn_iters": rep["gn_iters"], "pcg_iters": rep["pcg_iters_total"],
+            "inner_pcg_iters": rep["pc_inner_iters_total"], "pc_fallbacks": rep["pc_fallbacks"],
+            "gnorm_rel": rep["gnorm_rel"], "J": rep["J"], "mismatch": rep["mismatch"], "r": rep["r"],
+            "peak_device_gb": used_gb()}
+        del a0, a1
+        runs["fp16_learned_two_level"]["dice"] = dice(v)
+        del v
+        flush()
+        ctx.set_opts(precond=claire.PRECOND_SPECTRAL, g0_ref=0.0)
     _, mis_zero = ctx.objective(torch.zeros((3,) + grid, device=dev))
     runs["fp16_learned"]["mismatch_at_zero"] = mis_zero
     ctx.close()

@@ -236,6 +236,45 @@ __device__ __forceinline__ void box_copy(float* dst, const S* src)
         *dst = ldf<S>(src);
 }
 
+#ifndef CLAIRE_STAGE_COLS
+#define CLAIRE_STAGE_COLS 1  // 16-byte box staging: each thread one (row, chunk) column through all planes
+#endif
+
+// 16-byte box staging by columns: thread t owns row b = t / 16 (+16 per
+// pass) and chunk c = t % 16 (+16) of every box plane and copies that chunk
+// of each of the E1 planes in turn, so the wrapped x2 / x3 indices and the
+// row pointer are formed once per (b, c) and a plane costs one address step.
+// VPC: values per 16-byte chunk (4 FP32, 8 halves); dst: the box (FP32) or
+// the 16-bit staging area, whose row stride is S3 / (4 / sizeof(S)) words.
+// Returns nothing; the caller waits for the copies.
+template <class S>
+__device__ __forceinline__ void stage_box_columns(const Grid& g, const S* __restrict__ f, uint32_t dst0,
+                                                  const BoxPar& bp, int w1, int w2, int w3)
+{
+    constexpr int VPC = 16 / sizeof(S);
+    const int nch = bp.E3 / VPC;
+    const uint32_t row_bytes = static_cast<uint32_t>(bp.S3) * sizeof(S);
+    const uint32_t plane_bytes = row_bytes * static_cast<uint32_t>(bp.E2);
+    for (int b = threadIdx.x >> 4; b < bp.E2; b += kTileThreads / 16) {
+        int gj = w2 + b;
+        gj = gj >= g.n2 ? gj - g.n2 : gj;
+        for (int c = threadIdx.x & 15; c < nch; c += 16) {
+            int gk = w3 + VPC * c;
+            gk = gk >= g.n3 ? gk - g.n3 : gk;
+            const S* src = f + static_cast<size_t>(gj) * g.n3 + gk;
+            uint32_t dst = dst0 + static_cast<uint32_t>(b) * row_bytes + 16u * c;
+            int gi = w1;
+            for (int a = 0; a < bp.E1; ++a) {
+                asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(dst),
+                             "l"(src + static_cast<size_t>(gi) * g.n23)
+                             : "memory");
+                dst += plane_bytes;
+                gi = gi + 1 == g.n1 ? 0 : gi + 1;
+            }
+        }
+    }
+}
+
 template <class S>
 __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict__ f, float* box,
                                               const BoxPar& bp, int lane, int warp)
@@ -246,6 +285,12 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
     int gk1 = w3 + lane + 32;
     gk1 = gk1 >= g.n3 ? gk1 - g.n3 : gk1;
     if constexpr (sizeof(S) == 4) {
+#if CLAIRE_STAGE_COLS
+        if (((bp.O3 | bp.E3 | g.n3) & 3) == 0) {
+            stage_box_columns<S>(g, f, static_cast<uint32_t>(__cvta_generic_to_shared(box)), bp, w1, w2, w3);
+            return;
+        }
+#endif
         if (((bp.O3 | bp.E3 | g.n3) & 3) == 0) {
             // 16-byte chunks: a chunk never straddles the x3 wrap (n3 and the
             // origin are multiples of 4); 16 threads per row, 16 rows per pass
@@ -301,6 +346,11 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
         const int rows = bp.E1 * bp.E2;
         const int pairs = bp.E3 / 2;
         uint32_t* stage = reinterpret_cast<uint32_t*>(box + rows * bp.S3);
+#if CLAIRE_STAGE_COLS
+        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+            stage_box_columns<S>(g, f, static_cast<uint32_t>(__cvta_generic_to_shared(stage)), bp, w1, w2, w3);
+        } else
+#endif
         if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
             // 16-byte chunks of 8 values (no chunk straddles the x3 wrap), 16 threads per row
             const int nch = bp.E3 >> 3;
@@ -373,6 +423,23 @@ __device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const 
         const int rows = bp.E1 * bp.E2;
         const uint32_t* stage = reinterpret_cast<const uint32_t*>(box + rows * bp.S3);
         cp_async_wait_all();
+#if CLAIRE_STAGE_COLS
+        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+            // the chunks stage_box_columns issued from this thread, in its order
+            const int nch = bp.E3 >> 3;
+            for (int b = threadIdx.x >> 4; b < bp.E2; b += kTileThreads / 16)
+                for (int c = threadIdx.x & 15; c < nch; c += 16)
+                    for (int a = 0; a < bp.E1; ++a) {
+                        const int r = a * bp.E2 + b;
+                        const uint4 w = reinterpret_cast<const uint4*>(stage + r * (bp.S3 / 2))[c];
+                        float4* dp = reinterpret_cast<float4*>(box + r * bp.S3);
+                        const float2 p0 = widen2<S>(w.x), p1 = widen2<S>(w.y), p2 = widen2<S>(w.z),
+                                     p3 = widen2<S>(w.w);
+                        dp[2 * c] = make_float4(p0.x, p0.y, p1.x, p1.y);
+                        dp[2 * c + 1] = make_float4(p2.x, p2.y, p3.x, p3.y);
+                    }
+        } else
+#endif
         if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
             const int nch = bp.E3 >> 3;
             const int ch0 = threadIdx.x & 15;

@@ -21,7 +21,10 @@
  *  - Pointers: unless an entry point says "device pointers", an array
  *    argument may be a device pointer or a host pointer (pageable or
  *    pinned); host arrays are staged through the context's workspace with
- *    copies on the context's stream.  Arrays are owned by the caller and are
+ *    copies on the context's stream.  A device array needs only float
+ *    alignment: one at a 16-byte boundary (every cudaMalloc'd array) takes
+ *    the kernels' 16-byte copies and vector loads, any other their 4-byte
+ *    forms, with the same results.  Arrays are owned by the caller and are
  *    only read during the call, except outputs and v_inout.
  *  - Streams: all device work is queued on the context's stream (default:
  *    the legacy default stream; see claire_set_stream).  Every entry point
@@ -325,8 +328,9 @@ claire_status claire_transport_vjp(claire_ctx* ctx, const float* v, const float*
  *     spectra (wavenumbers at or beyond either grid's Nyquist limit are
  *     dropped, new ones are zero): band-limited interpolation / truncation.
  *   CLAIRE_RESAMPLE_NEAREST: out[j] = in[floor(j * n_from / n_to)] per axis.
- * `in` and `out` are device pointers (caller-owned, must not overlap); work
- * is queued on `stream`.  Needs no context.  The spectral mode keeps cuFFT
+ * `in` and `out` are 16-byte aligned device pointers (caller-owned, must not
+ * overlap; anything else is CLAIRE_EINVAL, nothing launched); work is queued
+ * on `stream`.  Needs no context.  The spectral mode keeps cuFFT
  * plans and two spectra for the last four (device, from, to) combinations
  * (freed by claire_resample_release), serialises callers on a mutex and
  * synchronises the stream before returning.  Errors: CLAIRE_EINVAL (shapes,

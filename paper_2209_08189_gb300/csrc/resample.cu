@@ -8,6 +8,7 @@
 
 #include <cufft.h>
 
+#include <cstdint>
 #include <cstdio>
 #include <mutex>
 #include <vector>
@@ -131,11 +132,29 @@ extern "C" claire_status claire_resample_release(void)
     return CLAIRE_OK;
 }
 
+namespace {
+
+// Device (or managed) memory at a 16-byte aligned address: the kernels and the
+// transforms of this file read and write the arrays in place.
+bool device_array(const void* p)
+{
+    if ((reinterpret_cast<uintptr_t>(p) & 15u) != 0) return false;
+    cudaPointerAttributes a;
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged;
+}
+
+}  // namespace
+
 extern "C" claire_status claire_resample(const float* in, const int from[3], float* out, const int to[3], int ncomp,
                                          int mode, void* stream)
 {
     using namespace claire;
     if (!in || !out || !from || !to || ncomp < 1) return CLAIRE_EINVAL;
+    if (!device_array(in) || !device_array(out)) return CLAIRE_EINVAL;
     if (mode != CLAIRE_RESAMPLE_SPECTRAL && mode != CLAIRE_RESAMPLE_NEAREST) return CLAIRE_EINVAL;
     for (int a = 0; a < 3; ++a)
         if (from[a] < 2 || to[a] < 2 || from[a] % 2 || to[a] % 2) return CLAIRE_EINVAL;

@@ -236,6 +236,17 @@ __device__ __forceinline__ void box_copy(float* dst, const S* src)
         *dst = ldf<S>(src);
 }
 
+// Whether the box of f is staged in 16-byte chunks: the x3 origin, the x3
+// extent and n3 are multiples of the values per chunk (so no chunk straddles
+// the x3 wrap) and f itself is 16-byte aligned (a field passed by a caller
+// may start at any 4-byte boundary); otherwise 4-byte copies.
+template <class S>
+__device__ __forceinline__ bool box_chunks16(const Grid& g, const S* f, const BoxPar& bp)
+{
+    constexpr int VPC = 16 / static_cast<int>(sizeof(S));
+    return ((bp.O3 | bp.E3 | g.n3) & (VPC - 1)) == 0 && (reinterpret_cast<uintptr_t>(f) & 15u) == 0;
+}
+
 #ifndef CLAIRE_STAGE_COLS
 #define CLAIRE_STAGE_COLS 1  // 16-byte box staging: each thread one (row, chunk) column through all planes
 #endif
@@ -286,12 +297,12 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
     gk1 = gk1 >= g.n3 ? gk1 - g.n3 : gk1;
     if constexpr (sizeof(S) == 4) {
 #if CLAIRE_STAGE_COLS
-        if (((bp.O3 | bp.E3 | g.n3) & 3) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             stage_box_columns<S>(g, f, static_cast<uint32_t>(__cvta_generic_to_shared(box)), bp, w1, w2, w3);
             return;
         }
 #endif
-        if (((bp.O3 | bp.E3 | g.n3) & 3) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             // 16-byte chunks: a chunk never straddles the x3 wrap (n3 and the
             // origin are multiples of 4); 16 threads per row, 16 rows per pass
             const int nch = bp.E3 >> 2, rows = bp.E1 * bp.E2;
@@ -347,11 +358,11 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
         const int pairs = bp.E3 / 2;
         uint32_t* stage = reinterpret_cast<uint32_t*>(box + rows * bp.S3);
 #if CLAIRE_STAGE_COLS
-        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             stage_box_columns<S>(g, f, static_cast<uint32_t>(__cvta_generic_to_shared(stage)), bp, w1, w2, w3);
         } else
 #endif
-        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             // 16-byte chunks of 8 values (no chunk straddles the x3 wrap), 16 threads per row
             const int nch = bp.E3 >> 3;
             const int ch0 = threadIdx.x & 15;
@@ -416,7 +427,8 @@ __device__ __forceinline__ void tile_load_box(const Grid& g, const S* __restrict
 // the widening; the caller's barrier before the stencils publishes the box.
 // FP32 storage: nothing (the caller waits for the copies).
 template <class S>
-__device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const BoxPar& bp, int lane, int warp)
+__device__ __forceinline__ void tile_widen_box(const Grid& g, const S* f, float* box, const BoxPar& bp, int lane,
+                                               int warp)
 {
 #if CLAIRE_F16_OWN_WIDEN
     if constexpr (sizeof(S) == 2) {
@@ -424,7 +436,7 @@ __device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const 
         const uint32_t* stage = reinterpret_cast<const uint32_t*>(box + rows * bp.S3);
         cp_async_wait_all();
 #if CLAIRE_STAGE_COLS
-        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             // the chunks stage_box_columns issued from this thread, in its order
             const int nch = bp.E3 >> 3;
             for (int b = threadIdx.x >> 4; b < bp.E2; b += kTileThreads / 16)
@@ -440,7 +452,7 @@ __device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const 
                     }
         } else
 #endif
-        if (((bp.O3 | bp.E3 | g.n3) & 7) == 0) {
+        if (box_chunks16<S>(g, f, bp)) {
             const int nch = bp.E3 >> 3;
             const int ch0 = threadIdx.x & 15;
             for (int r = threadIdx.x >> 4; r < rows; r += kTileThreads / 16) {
@@ -470,7 +482,7 @@ __device__ __forceinline__ void tile_widen_box(const Grid& g, float* box, const 
         }
     }
 #else
-    (void)g; (void)box; (void)bp; (void)lane; (void)warp;
+    (void)g; (void)f; (void)box; (void)bp; (void)lane; (void)warp;
 #endif
 }
 
@@ -676,7 +688,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
         }
 #pragma unroll
         for (int q = 0; q < TILE1; ++q) out = out || !in_box<ORDER>(bp, i0 + q, j, k, e1[q], e2[q], e3[q]);
-        if (bp.E1 != 0) tile_widen_box<S>(g, box, bp, lane, warp);
+        if (bp.E1 != 0) tile_widen_box<S>(g, f, box, bp, lane, warp);
         cp_async_wait_all();
         if (__syncthreads_or(out)) {
             if (threadIdx.x == 0) atomicAdd(&g_gather_global_tiles, 1ull);
@@ -725,7 +737,7 @@ __global__ void __launch_bounds__(kTileThreads, CLAIRE_TILE_MIN_BLOCKS)
 #pragma unroll
     for (int q = 0; q < TILE1; ++q)
         if (valid(q)) pre[q] = epi.prefetch(p0 + q * g.n23);
-    tile_widen_box<S>(g, box, bp, lane, warp);
+    tile_widen_box<S>(g, f, box, bp, lane, warp);
     cp_async_wait_all();
     __syncthreads();
 #pragma unroll

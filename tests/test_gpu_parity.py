@@ -511,6 +511,57 @@ def test_nonfinite_velocity_screened_before_any_gather(env):
     assert st >= 0 and math.isfinite(rep["J"])
 
 
+def test_misaligned_device_arrays(env):
+    """Device arrays that start 4 bytes past a 16-byte boundary (a tensor view
+    offset by one float): the tiled gathers stage such a field's box with
+    4-byte copies instead of 16-byte chunks, the vector kernels take their
+    scalar loops, so every call gives the bits of the aligned call;
+    claire_resample, which hands its arrays to cuFFT, rejects them."""
+    torch, claire = env
+    n = (32, 32, 32)
+    N = int(np.prod(n))
+    m0, m1, vs, v, p = _problem(n)
+    ctx = make_ctx(claire, torch, n)
+    ctx.set_images(dev(torch, m0), dev(torch, m1))
+
+    def shifted(a):
+        buf = torch.zeros(a.numel() + 4, device="cuda")
+        t = buf[1:1 + a.numel()].view(a.shape)
+        t.copy_(a)
+        assert t.data_ptr() % 16 == 4
+        return t
+
+    d = dev(torch, _disp(n, 3, 1.5))
+    f = dev(torch, m0)
+    f2 = torch.stack([f, dev(torch, m1)]).contiguous()
+    vd = dev(torch, v)
+    out_a, out_b = torch.empty(n, device="cuda"), shifted(torch.empty(n, device="cuda"))
+    ctx.interp(f, d, out_a)
+    ctx.interp(shifted(f), shifted(d), out_b)
+    assert torch.equal(out_a, out_b)
+    o2a, o2b = torch.empty_like(f2), torch.empty_like(f2)
+    ctx.interp_fields(f2, 2, d, o2a)
+    ctx.interp_fields(shifted(f2), 2, d, o2b)
+    assert torch.equal(o2a, o2b)
+    da, db = torch.empty((3,) + n, device="cuda"), torch.empty((3,) + n, device="cuda")
+    ctx.backtrace(vd, da, 1)
+    ctx.backtrace(shifted(vd), db, 1)
+    assert torch.equal(da, db)
+    # solver level: the arrays are used in place
+    g_a, g_b = torch.empty((3,) + n, device="cuda"), torch.empty((3,) + n, device="cuda")
+    J_a = ctx.gradient(vd, g_a)
+    J_b = ctx.gradient(shifted(vd), shifted(g_b))
+    assert J_a == J_b
+    ctx.gradient(shifted(vd), g_b)
+    assert torch.equal(g_a, g_b)
+    ctx.transport(vd, f, out_a)
+    ctx.transport(shifted(vd), shifted(f), out_b)
+    assert torch.equal(out_a, out_b)
+    with pytest.raises(claire.ClaireError) as e:
+        claire.claire_resample(shifted(f), n, out_a, n)
+    assert e.value.status == -1
+
+
 def test_wall_clock_limit(env):
     torch, claire = env
     n = (32, 32, 32)

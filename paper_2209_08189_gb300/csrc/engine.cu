@@ -763,31 +763,56 @@ claire_status matvec(claire_ctx* c, const float* vt, float* out, bool body_only 
         const double es = static_cast<double>(c->es);
         char* a = c->l0;
         char* b = c->l1;
-        {
-            if (c->gm) {
-                KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es * (nt + 1)) * N, 0);
-                launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
-            } else {
-                KTimer t(c, KK_FD8, (12.0 + 2.0 * es * (nt + 1)) * N, 0);
-                launch_inc_sources_fd(c->grid, vt, c->m, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+        if (c->gm && CLAIRE_INC_FUSED) {
+            // stored grad m^j: each step forms its source f^{j+1} at the arrival
+            // point, so only q^0 = dt/2 f^0 is written beforehand
+            {
+                KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es) * N, 0);
+                launch_inc_source0(c->grid, vt, c->gm, 0.5f * dt, a, c->sto, c->stream);
+                CL_LAUNCHED(c);
             }
-            CL_LAUNCHED(c);
-        }
-        for (int j = 0; j + 1 < nt; ++j) {
+            for (int j = 0; j + 1 < nt; ++j) {
+                const void* src;
+                CL_TRY(gather_src(c, a, 1, &src));
+                KTimer t(c, KK_INC_STEP, (24.0 + 5.0 * es) * N, 1.0 * N);
+                launch_inc_step_grad(c->grid, c->o.interp, src, c->dS, vt, at(c, c->gm, 3 * (j + 1) * N), dt, b,
+                                     c->sto, c->stream, c->tbS);
+                CL_LAUNCHED(c);
+                std::swap(a, b);
+            }
             const void* src;
             CL_TRY(gather_src(c, a, 1, &src));
-            KTimer t(c, KK_INC_STEP, (12.0 + 3.0 * es) * N, 1.0 * N);
-            launch_inc_step_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
-                                c->stream, c->tbS);
+            KTimer t(c, KK_INC_LAST, (24.0 + 5.0 * es) * N, 1.0 * N);
+            launch_inc_last_grad(c->grid, c->o.interp, src, c->dS, vt, at(c, c->gm, 3 * nt * N), 0.5f * dt,
+                                 at(c, c->tl, nt * N), c->sto, c->stream, c->tbS);
             CL_LAUNCHED(c);
-            std::swap(a, b);
+        } else {
+            {
+                if (c->gm) {
+                    KTimer t(c, KK_POINTWISE, (12.0 + 4.0 * es * (nt + 1)) * N, 0);
+                    launch_inc_sources(c->grid, vt, c->gm, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+                } else {
+                    KTimer t(c, KK_FD8, (12.0 + 2.0 * es * (nt + 1)) * N, 0);
+                    launch_inc_sources_fd(c->grid, vt, c->m, nt, 0.5f * dt, a, c->tl, c->sto, c->stream);
+                }
+                CL_LAUNCHED(c);
+            }
+            for (int j = 0; j + 1 < nt; ++j) {
+                const void* src;
+                CL_TRY(gather_src(c, a, 1, &src));
+                KTimer t(c, KK_INC_STEP, (12.0 + 3.0 * es) * N, 1.0 * N);
+                launch_inc_step_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, (j + 1) * N), dt, b, c->sto,
+                                    c->stream, c->tbS);
+                CL_LAUNCHED(c);
+                std::swap(a, b);
+            }
+            const void* src;
+            CL_TRY(gather_src(c, a, 1, &src));
+            KTimer t(c, KK_INC_LAST, (12.0 + 3.0 * es) * N, 1.0 * N);
+            launch_inc_last_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
+                                at(c, c->tl, nt * N), c->sto, c->stream, c->tbS);
+            CL_LAUNCHED(c);
         }
-        const void* src;
-        CL_TRY(gather_src(c, a, 1, &src));
-        KTimer t(c, KK_INC_LAST, (12.0 + 3.0 * es) * N, 1.0 * N);
-        launch_inc_last_src(c->grid, c->o.interp, src, c->dS, at(c, c->tl, nt * N), 0.5f * dt,
-                            at(c, c->tl, nt * N), c->sto, c->stream, c->tbS);
-        CL_LAUNCHED(c);
     }
     // incremental adjoint from lt^{nt} and body, accumulated onto S vt in out
     CL_TRY(adjoint_and_body(c, nullptr, nullptr, out, !body_only));

@@ -113,6 +113,19 @@ void launch_inc_step_src(const Grid& g, int order, const void* q_prev, const flo
                          float coef, void* q, Storage sto, cudaStream_t st, const int4* tb = nullptr);
 void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const float* d, const void* F,
                          float coef, void* lam, Storage sto, cudaStream_t st, const int4* tb = nullptr);
+#ifndef CLAIRE_INC_FUSED
+#define CLAIRE_INC_FUSED 1  // incremental state steps form their sources in place when grad m^j is stored
+#endif
+// With grad m^j stored: q0 = coef0 f^0, and the steps above with the source
+// f^{j+1} = -vt . grad m^{j+1} formed at each arrival point (gm: grad m^{j+1},
+// 3N values in `sto`), so no pass writes the sources of every level.
+void launch_inc_source0(const Grid& g, const float* vt, const void* gm, float coef0, void* q0, Storage sto,
+                        cudaStream_t st);
+void launch_inc_step_grad(const Grid& g, int order, const void* q_prev, const float* d, const float* vt,
+                          const void* gm, float coef, void* q, Storage sto, cudaStream_t st, const int4* tb = nullptr);
+void launch_inc_last_grad(const Grid& g, int order, const void* q_prev, const float* d, const float* vt,
+                          const void* gm, float coef, void* lam, Storage sto, cudaStream_t st,
+                          const int4* tb = nullptr);
 // out = a - b; conversions FP32 <-> storage
 void launch_sub(const void* a, const void* b, void* out, size_t n, Storage sto, cudaStream_t st);
 void launch_to_storage(const float* in, void* out, size_t n, Storage sto, cudaStream_t st);

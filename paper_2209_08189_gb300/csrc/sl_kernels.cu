@@ -241,6 +241,17 @@ __global__ void __launch_bounds__(kThreads) k_inc_sources(Grid g, const float* _
     }
 }
 
+// q0 = coef0 f^0 with f^0 = -vt . grad m^0, the start of the incremental
+// state when the later steps form their sources in place (EpiIncGrad).
+template <class S>
+__global__ void __launch_bounds__(kThreads) k_inc_source0(Grid g, const float* __restrict__ vt,
+                                                          const S* __restrict__ gm, float coef0, S* __restrict__ q0)
+{
+    const uint32_t p = blockIdx.x * kThreads + threadIdx.x;
+    if (p >= g.N) return;
+    stf<S>(q0 + p, coef0 * inc_source_at<S>(vt, gm, g.N, p));
+}
+
 // Gradient body by trapezoid in time, added to out (FP32):
 // out_c (+)= sum_j w_j lambda^j grad_c m^j, w_0 = w_nt = w_end, else w_mid.
 template <class S>
@@ -515,6 +526,35 @@ void launch_inc_last_src(const Grid& g, int order, const void* q_prev, const flo
         EpiIncSourceLast<SType> e{static_cast<const SType*>(F), static_cast<SType*>(lam), coef};
         const SType* fs = static_cast<const SType*>(q_prev);
         CLAIRE_TILED(order, EpiIncSourceLast, fs, d, e);
+    });
+}
+
+void launch_inc_source0(const Grid& g, const float* vt, const void* gm, float coef0, void* q0, Storage sto,
+                        cudaStream_t st)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        k_inc_source0<SType><<<blocks_for(g.N), kThreads, 0, st>>>(g, vt, static_cast<const SType*>(gm), coef0,
+                                                                   static_cast<SType*>(q0));
+    });
+}
+
+void launch_inc_step_grad(const Grid& g, int order, const void* q_prev, const float* d, const float* vt,
+                          const void* gm, float coef, void* q, Storage sto, cudaStream_t st, const int4* tb)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiIncGrad<SType> e{vt, static_cast<const SType*>(gm), static_cast<SType*>(q), coef, g.N};
+        const SType* fs = static_cast<const SType*>(q_prev);
+        CLAIRE_TILED(order, EpiIncGrad, fs, d, e);
+    });
+}
+
+void launch_inc_last_grad(const Grid& g, int order, const void* q_prev, const float* d, const float* vt,
+                          const void* gm, float coef, void* lam, Storage sto, cudaStream_t st, const int4* tb)
+{
+    CLAIRE_STORAGE_DISPATCH(sto, {
+        EpiIncGradLast<SType> e{vt, static_cast<const SType*>(gm), static_cast<SType*>(lam), coef, g.N};
+        const SType* fs = static_cast<const SType*>(q_prev);
+        CLAIRE_TILED(order, EpiIncGradLast, fs, d, e);
     });
 }
 

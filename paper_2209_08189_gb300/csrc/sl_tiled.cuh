@@ -906,4 +906,53 @@ struct EpiIncSourceLast {
     }
 };
 
+// Incremental state step with its source formed in place (grad m^{j+1}
+// stored): f = -vt . grad m^{j+1} at the arrival point, rounded to the
+// storage type as a stored source would be, then q = f(X) + coef f.  It
+// reads vt and grad m^{j+1} (24 B) instead of a precomputed source (4 B), so
+// the pass that wrote every level's source is not needed.
+template <class S>
+__device__ __forceinline__ float inc_source_at(const float* __restrict__ vt, const S* __restrict__ gm, uint32_t N,
+                                               uint32_t p)
+{
+    const float f = -(__ldg(vt + p) * ldf<S>(gm + p) + __ldg(vt + N + p) * ldf<S>(gm + N + p) +
+                      __ldg(vt + 2 * N + p) * ldf<S>(gm + 2 * N + p));
+    return to_f32<S>(from_f32<S>(f));
+}
+
+template <class S>
+struct EpiIncGrad {
+    const float* __restrict__ vt;
+    const S* __restrict__ gm;  // grad m^{j+1}, 3N values
+    S* __restrict__ q;
+    float coef;
+    uint32_t N;
+    struct Pre {
+        float f;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{inc_source_at<S>(vt, gm, N, p)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        stf<S>(q + p, fmaf(coef, r.f, a));
+    }
+};
+
+// last step with its source formed in place: lt = -(f(X) + coef f)
+template <class S>
+struct EpiIncGradLast {
+    const float* __restrict__ vt;
+    const S* __restrict__ gm;  // grad m^{nt}
+    S* __restrict__ lam;
+    float coef;
+    uint32_t N;
+    struct Pre {
+        float f;
+    };
+    __device__ __forceinline__ Pre prefetch(uint32_t p) const { return Pre{inc_source_at<S>(vt, gm, N, p)}; }
+    __device__ __forceinline__ void finish(uint32_t p, float a, const Pre& r) const
+    {
+        stf<S>(lam + p, -fmaf(coef, r.f, a));
+    }
+};
+
 }  // namespace claire

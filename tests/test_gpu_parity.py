@@ -284,6 +284,24 @@ def test_fd8_parity(env, n):
     assert rel_linf(host(dv), oracle.fd8_div(v.astype(np.float64))) <= 1e-5
 
 
+@pytest.mark.parametrize("n", [(20, 8, 32), (36, 24, 96), (64, 16, 64)])
+def test_fd8_grad_tiled_parity(env, n):
+    """Grids whose (x2, x3) planes the 8 x 32 tiles cover take the tiled FD8
+    gradient (halo planes in shared memory, x1 values in a register queue):
+    x1 extents that leave a partial 16-plane slab, x2 = 8 (the halo wraps onto
+    the tile itself) and several tiles per plane, against the oracle."""
+    torch, claire = env
+    f = f32(synth.blob_template(n, seed=15))
+    ctx = make_ctx(claire, torch, n)
+    g = torch.empty((3,) + n, device="cuda")
+    ctx.fd8_grad(dev(torch, f), g)
+    torch.cuda.synchronize()
+    ref = oracle.fd8_grad(f.astype(np.float64))
+    assert rel_linf(host(g), ref) <= 1e-5
+    for c in range(3):
+        assert rel_linf(host(g)[c], ref[c]) <= 1e-5
+
+
 @pytest.mark.parametrize("n", SHAPES)
 @pytest.mark.parametrize("reg", [1, 2])
 def test_spectral_parity(env, n, reg):
